@@ -1,0 +1,212 @@
+"""Pins for the oracle's plain CG and def-CG (Algorithm 1, Sec. 2.2).
+
+Each check compares the oracle with something other than itself: a dense
+factorisation, a hand-derived exact run, a property CG must have in exact
+arithmetic (finite termination, W^T r_j = 0, A-conjugacy), or CG on the
+reduced spectrum.
+"""
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import dcg_synth as S
+from oracle import dcg_oracle as O
+
+
+def _spd(n, seed, lo=1.0, hi=50.0):
+    eigs = np.geomspace(lo, hi, n)
+    return S.spd_with_spectrum(eigs, seed=seed)
+
+
+def test_cg_two_by_two_exact_run():
+    # A = [[4,1],[1,3]], b = [1,2], x_{-1} = 0. Worked by hand in exact fractions:
+    # r0 = p0 = (1,2), A p0 = (6,7), d0 = 20, rho0 = 5, alpha0 = 1/4,
+    # x1 = (1/4, 1/2), r1 = (-1/2, 1/4), rho1 = 5/16, beta0 = 1/16,
+    # p1 = (-7/16, 3/8); CG ends after 2 steps at A^{-1} b = (1/11, 7/11).
+    A = np.array([[4.0, 1.0], [1.0, 3.0]])
+    b = np.array([1.0, 2.0])
+    res = O.cg(A, b, tol=1e-14, keep_iterates=True)
+    assert res.iters == 2
+    np.testing.assert_allclose(res.x_history[1], [0.25, 0.5], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(res.r_history[1], [-0.5, 0.25], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(res.p_history[1], [-7 / 16, 3 / 8], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(res.x, [1 / 11, 7 / 11], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("n", [1, 7, 64])
+def test_cg_matches_cholesky(n):
+    A, _ = _spd(n, seed=n)
+    b = np.random.default_rng(n).standard_normal(n)
+    x_ref = sla.cho_solve(sla.cho_factor(A), b)
+    res = O.cg(A, b, tol=1e-14)
+    assert res.status == O.STATUS_OK
+    assert np.linalg.norm(res.x - x_ref) <= 1e-12 * np.linalg.norm(x_ref)
+
+
+def test_cg_terminates_in_distinct_eigenvalue_count():
+    # A has 5 distinct eigenvalues (with multiplicity): exact CG stops after 5 steps.
+    eigs = np.repeat([1.0, 2.0, 5.0, 11.0, 23.0], [10, 7, 9, 6, 8])
+    A, _ = S.spd_with_spectrum(eigs, seed=3)
+    b = np.random.default_rng(1).standard_normal(eigs.size)
+    res = O.cg(A, b, tol=1e-11)
+    assert res.iters <= 5
+    assert O.true_relres(A, b, res.x) <= 1e-11
+
+
+def test_cg_at_most_n_steps():
+    # finite termination in n steps (exact arithmetic); a mild spectrum keeps
+    # FP64 rounding from delaying it
+    n = 24
+    A, _ = _spd(n, seed=5, hi=8.0)
+    b = np.random.default_rng(2).standard_normal(n)
+    res = O.cg(A, b, tol=1e-10)
+    assert res.iters <= n
+    assert res.relres_true <= 1e-10
+
+
+def test_zero_rhs_returns_zero():
+    A, _ = _spd(8, seed=1)
+    for fn in (O.cg, O.defcg):
+        res = fn(A, np.zeros(8), tol=1e-8)
+        assert res.iters == 0 and not np.any(res.x)
+
+
+@pytest.mark.parametrize("n,k", [(5, 2), (40, 3), (64, 8)])
+def test_defcg_matches_cholesky(n, k):
+    A, _ = _spd(n, seed=10 + n)
+    rng = np.random.default_rng(n)
+    b = rng.standard_normal(n)
+    W = rng.standard_normal((n, k))
+    x_ref = sla.cho_solve(sla.cho_factor(A), b)
+    res = O.defcg(A, b, W=W, tol=1e-14)
+    assert res.status == O.STATUS_OK
+    assert np.linalg.norm(res.x - x_ref) <= 1e-12 * np.linalg.norm(x_ref)
+
+
+def test_defcg_warm_start_matches_cholesky():
+    n, k = 50, 4
+    A, _ = _spd(n, seed=77)
+    rng = np.random.default_rng(3)
+    b, x0, W = rng.standard_normal(n), rng.standard_normal(n), rng.standard_normal((n, k))
+    res = O.defcg(A, b, x_init=x0, W=W, tol=1e-13)
+    x_ref = sla.cho_solve(sla.cho_factor(A), b)
+    assert np.linalg.norm(res.x - x_ref) <= 1e-11 * np.linalg.norm(x_ref)
+    assert res.matvecs_setup == k + 1
+
+
+def test_defcg_residuals_orthogonal_to_W_and_directions_conjugate():
+    # Eq. 5 with conjugacy (Sec. 2.2): W^T r_j = 0 for all j, (AW)^T p_j = 0,
+    # and successive directions are A-conjugate.
+    n, k = 80, 5
+    A, _ = _spd(n, seed=21, hi=200.0)
+    rng = np.random.default_rng(4)
+    b, W = rng.standard_normal(n), rng.standard_normal((n, k))
+    res = O.defcg(A, b, W=W, tol=1e-10, keep_iterates=True)
+    AW = A @ W
+    # rounding leaves W^T r_j at the eps * |W| |b| level (absolute, not
+    # relative to the shrinking |r_j|); a missing line-3 projection gives O(1)
+    for r, p in zip(res.r_history, res.p_history):
+        assert np.linalg.norm(W.T @ r) <= 1e-12 * np.linalg.norm(W) * np.linalg.norm(b)
+        assert np.linalg.norm(AW.T @ p) <= 1e-9 * np.linalg.norm(AW) * np.linalg.norm(p)
+    P = res.p_history
+    for j in range(min(len(P) - 1, 12)):
+        c = P[j] @ (A @ P[j + 1])
+        assert abs(c) <= 1e-9 * np.sqrt((P[j] @ A @ P[j]) * (P[j + 1] @ A @ P[j + 1]))
+
+
+def test_defcg_k0_reproduces_cg_bitwise():
+    # Algorithm 1 differs from CG only in lines 3 and 11 (Sec. 2.2): with W
+    # empty every iterate must be identical.
+    n = 60
+    A, _ = _spd(n, seed=8, hi=300.0)
+    b = np.random.default_rng(9).standard_normal(n)
+    a = O.cg(A, b, tol=1e-9, keep_iterates=True)
+    d = O.defcg(A, b, W=None, tol=1e-9, keep_iterates=True)
+    assert a.iters == d.iters
+    for u, v in zip(a.x_history, d.x_history):
+        assert np.array_equal(u, v)
+    for u, v in zip(a.p_history, d.p_history):
+        assert np.array_equal(u, v)
+    assert np.array_equal(a.x, d.x)
+    assert a.history == d.history
+
+
+def test_exact_eigenvectors_reduce_to_cg_on_remaining_spectrum():
+    # Deflating an exact invariant subspace W = Q_S leaves CG on diag(Lambda \ S)
+    # with right-hand side Q_{S^c}^T b: same residual norms, same iteration count.
+    # a mild bulk plus six large outliers (the shape of K + noise I); on a
+    # mild bulk FP64 CG keeps orthogonality, so the identity holds to rounding
+    n = 70
+    eigs = np.concatenate([np.linspace(1.0, 6.0, n - 6), np.geomspace(50.0, 400.0, 6)])
+    A, Q = S.spd_with_spectrum(eigs, seed=31)
+    S_idx = np.arange(n - 6, n)           # the 6 largest, as the experiment deflates
+    C_idx = np.arange(0, n - 6)
+    b = np.random.default_rng(5).standard_normal(n)
+    tau = 1e-9 * np.linalg.norm(b)
+    res = O.defcg(A, b, W=Q[:, S_idx], tol=tau / np.linalg.norm(b))
+    bp = Q[:, C_idx].T @ b
+    red = O.cg(np.diag(eigs[C_idx]), bp, tol=tau / np.linalg.norm(bp))
+    assert res.iters == red.iters
+    h1 = np.array(res.history) * np.linalg.norm(b)
+    h2 = np.array(red.history) * np.linalg.norm(bp)
+    np.testing.assert_allclose(h1, h2, rtol=1e-7, atol=1e-12 * np.linalg.norm(b))
+    # and the deflated run beats plain CG on the full spectrum
+    full = O.cg(A, b, tol=tau / np.linalg.norm(b))
+    assert res.iters < full.iters
+
+
+def test_defcg_rank_deficient_W_drops_direction():
+    # Reading R6: a duplicated column of W makes E singular; it is dropped.
+    n = 30
+    A, _ = _spd(n, seed=2)
+    rng = np.random.default_rng(6)
+    W = rng.standard_normal((n, 3))
+    W = np.column_stack([W, W[:, 0]])
+    b = rng.standard_normal(n)
+    res = O.defcg(A, b, W=W, tol=1e-12)
+    assert res.k_used == 3
+    assert O.true_relres(A, b, res.x) <= 1e-12
+
+
+def test_refinement_keeps_solution():
+    n, k = 64, 4
+    A, _ = _spd(n, seed=12, hi=1e4)
+    rng = np.random.default_rng(7)
+    b, W = rng.standard_normal(n), rng.standard_normal((n, k))
+    res = O.defcg(A, b, W=W, tol=1e-11, refine_every=5)
+    x_ref = sla.cho_solve(sla.cho_factor(A), b)
+    assert res.relres_true <= 1e-11
+    assert np.linalg.norm(res.x - x_ref) <= 1e-7 * np.linalg.norm(x_ref)
+    assert res.matvecs_check >= res.iters // 5
+
+
+def test_window_first_and_last():
+    n = 50
+    A, _ = _spd(n, seed=13, hi=500.0)
+    b = np.random.default_rng(8).standard_normal(n)
+    first = O.defcg(A, b, tol=1e-10, ell=6, window="first", keep_iterates=True)
+    last = O.defcg(A, b, tol=1e-10, ell=6, window="last", keep_iterates=True)
+    assert len(first.P) == 6 and len(last.P) == 6
+    for j in range(6):
+        assert np.array_equal(first.P[j], first.p_history[j])
+        np.testing.assert_allclose(first.Q[j], A @ first.p_history[j], rtol=1e-13, atol=1e-13)
+    J = last.iters
+    for j in range(6):
+        assert np.array_equal(last.P[j], last.p_history[J - 6 + j])
+
+
+def test_maxiter_status():
+    A, _ = _spd(40, seed=3, hi=1e4)
+    b = np.random.default_rng(1).standard_normal(40)
+    res = O.defcg(A, b, tol=1e-12, max_iter=3)
+    assert res.status == O.STATUS_MAXITER and res.iters == 3
+
+
+def test_breakdown_on_indefinite():
+    eigs = np.array([-1.0, 1.0, 2.0, 3.0])
+    A, _ = S.spd_with_spectrum(eigs, seed=0)
+    # b along the negative eigenvector gives d_0 = p^T A p < 0
+    _, Q = S.spd_with_spectrum(eigs, seed=0)
+    res = O.defcg(A, Q[:, 0], tol=1e-10)
+    assert res.status == O.STATUS_BREAKDOWN
