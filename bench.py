@@ -1,0 +1,426 @@
+"""Benchmark: time-to-1e-6-residual per sequence of def-CG (k = 32 recycled
+harmonic Ritz vectors from the last 64 directions) vs plain CG on the stored
+dense FP32 workload: 20 RBF systems A_t = K_t + 1e-3 I, n = 16384, X ~ N(0,1)
+in R^{16384 x 16}, lengthscale l_t = 0.8 (1 + 0.05 t), b_t ~ N(0,1).
+
+A step is one whole sequence (A1-A9 of the hot path): per system, form A_t on
+the GPU (reported separately, excluded from the metric), solve with def-CG
+(start-of-solve product, projection, the graph-captured loop, true-residual
+confirmation) and extract the next W by harmonic Ritz.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU: replicas only (independent sequences per rank, no collective).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import dcg_synth as S  # noqa: E402
+
+METRIC = "time-to-1e-6-residual per sequence and matvecs/sec, def-CG vs plain CG, % of roofline"
+CFG = S.DENSE_16384
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_sequence(P, torch, solver, Xd, bs_dev, A, T, deflate, ev_pool):
+    """One sequence; returns per-system infos and device-timed (form, solve) ms."""
+    infos = []
+    form_ms = 0.0
+    solve_ms = 0.0
+    stream = torch.cuda.current_stream()
+    for t in range(T):
+        e0, e1, e2 = ev_pool[3 * t], ev_pool[3 * t + 1], ev_pool[3 * t + 2]
+        e0.record(stream)
+        P.form_rbf_dense(Xd, CFG.lengthscale(t), CFG.signal_var, CFG.noise, out=A)
+        e1.record(stream)
+        solver.set_operator_dense(A)
+        x, info = solver.solve(bs_dev[t])
+        if deflate:
+            solver.update_subspace()
+        e2.record(stream)
+        infos.append(info)
+    torch.cuda.synchronize()
+    for t in range(T):
+        form_ms += ev_pool[3 * t].elapsed_time(ev_pool[3 * t + 1])
+        solve_ms += ev_pool[3 * t + 1].elapsed_time(ev_pool[3 * t + 2])
+    return infos, form_ms, solve_ms
+
+
+def launches_of(infos, deflate):
+    total = 0
+    for i in infos:
+        checks = i["matvecs_check"] - (1 if i["status"] != 0 else 0)
+        fin = 1 if i["status"] != 0 else 0
+        total += 1                       # form A_t
+        total += 8 + 1                   # start of solve + loop gate
+        total += 3 * i["iters"] + 3 * checks
+        total += 2 + fin                 # final gate, final residual, finalize
+        if deflate:
+            total += 8                   # harmonic Ritz extraction
+    return total
+
+
+def gpu_arm(args):
+    import torch
+
+    import paper_1706_00241_gb300 as P
+    from paper_1706_00241_gb300 import build as B
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    B.build()
+    n, T = CFG.n, CFG.T
+    X, bs = S.draw_sequence(CFG)
+    X32 = X.astype(np.float32)
+    b32 = [b.astype(np.float32) for b in bs]
+    Xd = torch.tensor(X32, device="cuda")
+    bs_dev = [torch.tensor(b, device="cuda") for b in b32]
+    A = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    ev_pool = [torch.cuda.Event(enable_timing=True) for _ in range(3 * T)]
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def make(deflate):
+        return P.DefCG(n, CFG.k if deflate else 0, CFG.ell if deflate else 0, CFG.tol,
+                       max_iter=20000, window="last", select="largest")
+
+    # warm-up (builds the graph, first-touch of buffers)
+    solver = make(True)
+    for _ in range(args.warmup):
+        solver.set_subspace(torch.zeros((0, n), device="cuda"))
+        run_sequence(P, torch, solver, Xd, bs_dev, A, T, True, ev_pool)
+
+    # timed region: K whole sequences
+    seq_solve_ms, seq_form_ms, all_infos = [], [], []
+    with ClockSampler(local) as clk:
+        barrier()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record()
+        for _ in range(args.steps):
+            solver.set_subspace(torch.zeros((0, n), device="cuda"))
+            infos, fm, sm = run_sequence(P, torch, solver, Xd, bs_dev, A, T, True, ev_pool)
+            seq_solve_ms.append(sm)
+            seq_form_ms.append(fm)
+            all_infos.append(infos)
+        t_end.record()
+        barrier()
+    step_ms = t_start.elapsed_time(t_end) / args.steps
+    solve_ms_mean = float(np.mean(seq_solve_ms))
+    if world > 1:
+        tt = torch.tensor([solve_ms_mean, step_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        solve_ms_mean, step_ms = float(tt[0]), float(tt[1])
+    infos = all_infos[-1]
+    loop_mv = sum(i["iters"] for i in infos)
+    check_mv = sum(i["matvecs_check"] for i in infos)
+    setup_cols = sum(i["matvecs_setup"] for i in infos)
+    ok = all(i["status"] == 0 and i["relres_true"] <= CFG.tol for i in infos)
+
+    # plain CG on the same sequence (same GPU, same kernels, k = 0)
+    plain = make(False)
+    run_sequence(P, torch, plain, Xd, bs_dev, A, T, False, ev_pool)
+    pinfos, _, plain_ms = run_sequence(P, torch, plain, Xd, bs_dev, A, T, False, ev_pool)
+    plain_mv = sum(i["iters"] + i["matvecs_check"] for i in pinfos)
+    plain.close()
+
+    # roofline of the dominant kernel: the TMA GEMV q = A p, timed with CUDA
+    # events on the solver's stream (same launch configuration as in the loop)
+    hbm_peak, peak_kind = peaks()
+    stream = torch.cuda.current_stream()
+    p = bs_dev[0].clone()
+    q = torch.empty_like(p)
+    P.form_rbf_dense(Xd, CFG.lengthscale(T - 1), CFG.signal_var, CFG.noise, out=A)
+    solver.set_operator_dense(A)
+    for _ in range(3):
+        solver.matvec(p, q, want_pAp=False)
+    reps = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        solver.matvec(p, q, want_pAp=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gemv_ms = e0.elapsed_time(e1) / reps
+    gemv_bytes = 4.0 * n * n + 8.0 * n        # A once, p read and q written
+    achieved = gemv_bytes / (gemv_ms * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers: X and b_t from
+    # pinned host memory, x_t back to pinned host memory, inside the timing
+    Xh = torch.tensor(X32).pin_memory()
+    bh = [torch.tensor(b).pin_memory() for b in b32]
+    xh = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(T)]
+    solver.set_subspace(torch.zeros((0, n), device="cuda"))
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    Xd2 = Xh.to("cuda", non_blocking=True)
+    e2e_infos = []
+    for t in range(T):
+        P.form_rbf_dense(Xd2, CFG.lengthscale(t), CFG.signal_var, CFG.noise, out=A)
+        solver.set_operator_dense(A)
+        bd = bh[t].to("cuda", non_blocking=True)
+        x, info = solver.solve(bd)
+        solver.update_subspace()
+        xh[t].copy_(x, non_blocking=True)
+        e2e_infos.append(info)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - w0
+    solver.close()
+
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "gemv_dense_n16384.md")
+    if os.path.exists(tf):
+        for line in open(tf):
+            if line.startswith("dram_bytes_per_launch:"):
+                try:
+                    traffic = float(line.split(":")[1])
+                except ValueError:
+                    traffic = None
+
+    seq_s = solve_ms_mean / 1e3
+    value = seq_s / world
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "s/sequence",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": step_ms,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded dcg_synth draws standing in for the paper's MNIST workload)",
+        "config": {
+            "workload": CFG.name, "n": n, "d": CFG.d, "systems": T, "k": CFG.k, "ell": CFG.ell,
+            "window": "last", "tol": CFG.tol, "operator": "stored dense fp32 (1 GiB > L2)",
+            "l2": "inputs larger than L2 (A is 1 GiB per system)", "parallelism": f"replicas x{world}",
+        },
+        "defcg": {
+            "s_per_sequence": seq_s, "iters": loop_mv, "check_matvecs": check_mv,
+            "setup_columns": setup_cols, "matvecs_per_s": (loop_mv + check_mv) / seq_s,
+            "all_converged": ok, "iters_per_system": [i["iters"] for i in infos],
+            "form_ms_per_sequence": float(np.mean(seq_form_ms)),
+        },
+        "plain_cg": {
+            "s_per_sequence": plain_ms / 1e3, "iters": sum(i["iters"] for i in pinfos),
+            "matvecs_per_s": plain_mv / (plain_ms / 1e3),
+            "iters_per_system": [i["iters"] for i in pinfos],
+        },
+        "speedup_vs_plain_cg": (plain_ms / 1e3) / seq_s,
+        "roofline": {
+            "kernel": "k_rowop_tma<false> (q = A p, fused p^T q)",
+            "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": traffic,
+            "algorithmic_bytes_per_launch": gemv_bytes, "launch_ms": gemv_ms,
+        },
+        "e2e": {
+            "value": e2e_s, "unit": "s/sequence",
+            "h2d_bytes_per_step": int(X32.nbytes + T * n * 4),
+            "d2h_bytes_per_step": int(T * n * 4),
+        },
+        "gpu_launches": launches_of(infos, True) * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(samples=2)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def _golden_total_matvecs():
+    g = os.path.join(ROOT, "tests", "golden", "dense_16384_oracle.json")
+    if os.path.exists(g):
+        d = json.load(open(g))
+        return d["total_defcg_matvecs"], "tests/golden/dense_16384_oracle.json"
+    return None, None
+
+
+class OracleSample:
+    """Oracle inputs for the first systems of the sequence, formed once
+    (formation is excluded from the metric, as on the GPU)."""
+
+    def __init__(self, systems=2):
+        from oracle import dcg_oracle as O
+        self.O = O
+        X, bs = S.draw_sequence(CFG, T=systems)
+        X64 = X.astype(np.float32).astype(np.float64)
+        self.A = [O.rbf_gram(X64, CFG.lengthscale(t), CFG.signal_var, CFG.noise) for t in range(systems)]
+        self.b = [b.astype(np.float32).astype(np.float64) for b in bs]
+        self.W = [None]
+        for t in range(systems - 1):   # the W each sampled system starts from
+            res = O.defcg(self.A[t], self.b[t], W=self.W[-1], tol=CFG.tol, ell=CFG.ell, window="last")
+            self.W.append(O.harmonic_ritz(res.W, res.AW, res.P, res.Q, CFG.k).W)
+
+    def time_system(self, t):
+        O = self.O
+        w0 = time.perf_counter()
+        res = O.defcg(self.A[t], self.b[t], W=self.W[t], tol=CFG.tol, ell=CFG.ell, window="last")
+        O.harmonic_ritz(res.W, res.AW, res.P, res.Q, CFG.k)
+        return time.perf_counter() - w0, res.matvecs
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def extrapolate(solve_s, mv, sampled):
+    total, src = _golden_total_matvecs()
+    if total:
+        return solve_s / mv * total, (f"extrapolated by matvec count to the oracle's full-sequence total "
+                                      f"{total} ({src})")
+    return solve_s * CFG.T / sampled, "extrapolated by system count (no golden)"
+
+
+def cpu_baseline(samples=2):
+    """Oracle def-CG + harmonic Ritz on systems 0 .. samples-1 of the sequence,
+    timed and extrapolated to the whole sequence."""
+    smp = OracleSample(samples)
+    solve_s, mv = 0.0, 0
+    for t in range(samples):
+        dt, m = smp.time_system(t)
+        solve_s += dt
+        mv += m
+    est, how = extrapolate(solve_s, mv, samples)
+    return {"value": est, "unit": "s/sequence", "cores": _cores(), "kind": "oracle",
+            "sample": f"systems 0..{samples - 1} of the n=16384 sequence, FP64 numpy def-CG + harmonic "
+                      f"Ritz ({solve_s:.2f} s, {mv} matvecs), {how}; formation of A_t excluded as on the GPU"}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    smp = OracleSample(2)
+    vals = []
+    for s in range(args.warmup + args.steps):
+        dt, mv = smp.time_system(1)
+        if s >= args.warmup:
+            vals.append(extrapolate(dt, mv, 1)[0])
+    value = float(np.mean(vals))
+    how = extrapolate(1.0, 1, 1)[1]
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s/sequence", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": CFG.name, "n": CFG.n, "systems": CFG.T, "k": CFG.k, "ell": CFG.ell},
+        "cpu_baseline": {"value": value, "unit": "s/sequence", "cores": _cores(), "kind": "oracle",
+                         "sample": "per step: FP64 numpy def-CG + harmonic Ritz on system 1 of the n=16384 "
+                                   "sequence (W recycled from system 0), " + how},
+        "e2e": {"value": value, "unit": "s/sequence", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * dcg.h -- C ABI of the GB300 deflated-CG library.
+ *
+ * Method: de Roos & Hennig, "Krylov Subspace Recycling for Fast Iterative
+ * Least-Squares in Machine Learning" (arXiv 1706.00241).
+ *   - Eq. 1: a sequence of SPD systems A^(i) x^(i) = b^(i).
+ *   - Algorithm 1 (Sec. 2.2): Deflated-CG(k, ell)(A, b, x_{-1}, W, (AW), tol).
+ *   - Sec. 2.3, Eq. 7: harmonic projection G u = theta F u, F = (AZ)^T Z,
+ *     G = (AZ)^T AZ, Z = [W, P_ell]; the next W is Z U for k chosen u.
+ *   - Sec. 3: the RBF kernel k(x_i, x_j) = s^2 exp(-|x_i - x_j|^2 / (2 l^2)).
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are CUDA device addresses on the device that was current
+ *     when the context was created. Host pointers are ordinary host memory.
+ *     Which one an argument is, is stated per argument ("device" / "host").
+ *   - Vectors are float32, length n, contiguous. Matrices of vectors (W, the
+ *     stored directions) are column-major n x c with leading dimension n.
+ *   - Dense operators are row-major float32 with leading dimension lda
+ *     (lda >= n, lda % 4 == 0, base address 16-byte aligned).
+ *   - "stream" is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream. All device work of a context is ordered on its stream.
+ *   - Ownership: buffers passed in stay owned by the caller. Operator buffers
+ *     are borrowed until the next dcg_set_operator_* call or dcg_destroy; the
+ *     caller keeps them alive and unchanged during dcg_solve.
+ *   - Errors: every call returns a dcg_status; nothing aborts or exits. A
+ *     context-level message is kept for dcg_last_error(). After an error
+ *     inside dcg_solve, x holds the last iterate.
+ *   - Thread safety: a context must not be used by two host threads at once.
+ */
+#ifndef DCG_H
+#define DCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dcg_status {
+  DCG_OK = 0,
+  DCG_ERR_INVALID_ARG = 1,       /* bad size, pointer, alignment or enum      */
+  DCG_ERR_NOMEM = 2,             /* device allocation failed                  */
+  DCG_ERR_CUDA = 3,              /* a CUDA runtime call failed                */
+  DCG_ERR_BREAKDOWN = 4,         /* p^T A p <= 0 or not finite: A not SPD     */
+  DCG_ERR_SUBSPACE_SINGULAR = 5, /* E = W^T A W or F not positive definite    */
+  DCG_ERR_MAXITER = 6,           /* max_iter reached before tol               */
+  DCG_ERR_TIMEOUT = 7,           /* a bounded device-side wait gave up        */
+  DCG_ERR_STATE = 8,             /* call out of order (e.g. no operator set)  */
+  DCG_ERR_UNSUPPORTED = 9        /* configuration this build does not handle  */
+} dcg_status;
+
+typedef enum dcg_window {         /* which directions feed the next W (Alg. 1 l.13) */
+  DCG_WINDOW_FIRST = 0,           /* p_0 .. p_{ell-1}, as the paper stores        */
+  DCG_WINDOW_LAST = 1             /* the final ell directions of the solve        */
+} dcg_window;
+
+typedef enum dcg_select {         /* which harmonic Ritz values are kept (Sec. 2.3) */
+  DCG_SELECT_LARGEST = 0,
+  DCG_SELECT_SMALLEST = 1
+} dcg_select;
+
+typedef enum dcg_xformat {        /* element format of X for the matrix-free operator */
+  DCG_X_FP32 = 0,                 /* Gram tiles in split TF32 (three products)     */
+  DCG_X_BF16 = 1,                 /* X rounded to bfloat16; exact BF16 products    */
+  DCG_X_TF32 = 2                  /* X rounded to TF32; one TF32 product           */
+} dcg_xformat;
+
+typedef struct dcg_config {
+  int64_t n;            /* system size                                           */
+  int32_t k;            /* deflation vectors carried between systems (k >= 0)    */
+  int32_t ell;          /* directions stored per solve for extraction (ell >= 0) */
+  int32_t window;       /* dcg_window                                            */
+  int32_t select;       /* dcg_select                                            */
+  int32_t refine_every; /* m: replace r by b - A x every m iterations; 0 = never
+                           (the final true-residual confirmation always runs)    */
+  int32_t max_iter;     /* iteration cap per solve (> 0)                         */
+  int32_t warm_start;   /* 0: x_{-1} = 0 and the input x is ignored; 1: x is x_{-1} */
+  int32_t reproject;    /* 1: take mu from (AW)^T (beta p + r) every iteration   */
+  int32_t record_history; /* 1: keep |r_j| / |b| per iteration (dcg_get_history) */
+  int32_t reserved[7];  /* must be zero                                          */
+  double tol;           /* relative residual target |b - A x| <= tol |b|         */
+} dcg_config;
+
+typedef struct dcg_solve_info {
+  int32_t status;          /* dcg_status of the solve                             */
+  int32_t iters;           /* CG iterations (one A p each)                        */
+  int32_t matvecs_loop;    /* = iters                                             */
+  int32_t matvecs_setup;   /* columns of the start-of-solve product A [x_{-1} | W] */
+  int32_t matvecs_check;   /* true-residual evaluations (confirmation + refinement) */
+  int32_t k_used;          /* deflation vectors used in this solve                */
+  int32_t stored;          /* directions stored for the next extraction           */
+  int32_t reserved;
+  double relres_recursive; /* |r_j| / |b| of the recursion at exit                */
+  double relres_true;      /* |b - A x| / |b| with float64 accumulation           */
+  double ms_total;         /* device time of the whole solve (CUDA events)        */
+  double ms_setup;         /* start-of-solve product, E and its factor, x_0, p_0  */
+} dcg_solve_info;
+
+typedef struct dcg_ctx dcg_ctx;
+
+/* ------------------------------------------------------------------------ */
+/* Status strings                                                            */
+/* ------------------------------------------------------------------------ */
+
+/* Static description of a status code. Never NULL. */
+const char* dcg_status_string(dcg_status s);
+
+/* Last error message of a context (empty string if none); ctx may be NULL,
+ * in which case the message of the last failed dcg_create is returned. The
+ * pointer stays valid until the next call on the context. */
+const char* dcg_last_error(const dcg_ctx* ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* dcg_create: a solver for def-CG(k, ell) (Algorithm 1) on systems of size n.
+ *   cfg    host, read once.
+ *   stream cudaStream_t (void*) on which all work of the context runs.
+ *   out    host; receives the context.
+ * Allocates on the current device: W, AW (n x k), the direction store P, AP
+ * (n x ell), x, r, p, A p, b and small float64 workspaces. W starts empty
+ * (k_active = 0), so the first solve is plain CG (Fig. 1 caption).
+ * Errors: INVALID_ARG (n < 1, k < 0, ell < 0, k > n, ell > n, max_iter < 1,
+ * tol <= 0, k > 0 with ell + k < k, reserved nonzero), NOMEM, CUDA,
+ * UNSUPPORTED (k > 128 or ell > 256: limits of the small dense kernels). */
+dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** out);
+
+/* Frees everything the context owns. NULL is allowed. Synchronizes its stream. */
+dcg_status dcg_destroy(dcg_ctx* ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Operators (L0 of the method: A applied as A v)                            */
+/* ------------------------------------------------------------------------ */
+
+/* Stored dense operator: A (device, row-major float32, n x n, leading
+ * dimension lda, lda % 4 == 0, 16-byte aligned) is borrowed. Call again after
+ * changing A's contents: the next solve then recomputes A W (Algorithm 1
+ * takes AW as an input; it is stale once A changes).
+ * Errors: INVALID_ARG (NULL, misaligned, lda < n or lda % 4 != 0), CUDA. */
+dcg_status dcg_set_operator_dense(dcg_ctx* ctx, const float* A, int64_t lda);
+
+/* Matrix-free RBF operator A = K + noise I, K_ij = signal_var *
+ * exp(-|x_i - x_j|^2 / (2 lengthscale^2)) (Sec. 3 kernel).
+ *   X        device, row-major float32 n x d (row i is x_i); copied into the
+ *            context's own padded buffer in the requested format, so X is
+ *            not borrowed.
+ *   d        1 <= d <= 64.
+ *   xformat  dcg_xformat; fixes how X_I X_J^T tiles are formed on the tensor
+ *            cores (the operator is the one defined by the rounded X).
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+dcg_status dcg_set_operator_rbf(dcg_ctx* ctx, const float* X, int32_t d, int32_t xformat,
+                                double lengthscale, double signal_var, double noise);
+
+/* Change only the RBF hyperparameters of the current matrix-free operator
+ * (the lengthscale path of a sequence). Marks A W stale. Errors: STATE. */
+dcg_status dcg_set_rbf_params(dcg_ctx* ctx, double lengthscale, double signal_var, double noise);
+
+/* Forms a stored RBF operator (A1): A[i*lda + j] = signal_var *
+ * exp(-|x_i - x_j|^2 / (2 l^2)) + noise * [i == j], float32, computed from X
+ * (device, row-major float32 n x d) with float32 difference-form distances.
+ * A: device, n x lda. No context needed; runs on `stream`.
+ * Errors: INVALID_ARG, CUDA. */
+dcg_status dcg_form_rbf_dense(const float* X, int64_t n, int32_t d, double lengthscale,
+                              double signal_var, double noise, float* A, int64_t lda,
+                              void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Solve (Algorithm 1)                                                       */
+/* ------------------------------------------------------------------------ */
+
+/* dcg_solve: runs Deflated-CG(k, ell)(A, b, x_{-1}, W, AW, tol).
+ *   b    device, n floats (read).
+ *   x    device, n floats; in: x_{-1} if cfg.warm_start, else ignored;
+ *        out: the solution (or the last iterate on error).
+ *   info host, may be NULL.
+ * Steps (all on the device, one host synchronisation at the end):
+ *   A [x_{-1} | W] in one pass; E = W^T (AW) in float64 and its Cholesky
+ *   factor; x_0 = x_{-1} + W E^{-1} W^T r_{-1} (line 3); p_0 = r_0 - W mu_0
+ *   (line 4); then the loop of lines 5-14 as a CUDA graph with a device-side
+ *   while node. Stops when |r_j| <= tol |b|, confirmed by a true residual
+ *   b - A x with float64 accumulation (replaced and continued if above tol).
+ *   The last ell (or first ell) directions p_j and A p_j are kept for
+ *   dcg_update_subspace.
+ * Returns the solve status (also in info->status): OK, MAXITER, BREAKDOWN,
+ * SUBSPACE_SINGULAR, STATE (no operator), INVALID_ARG, CUDA. */
+dcg_status dcg_solve(dcg_ctx* ctx, const float* b, float* x, dcg_solve_info* info);
+
+/* dcg_update_subspace: harmonic-Ritz extraction (Sec. 2.3, Eq. 7) from the
+ * last solve: Z = [W, P], AZ = [AW, AP], F = Z^T AZ (symmetrised),
+ * G = AZ^T AZ, G u = theta F u in float64, keep min(k, cols(Z)) values
+ * (largest or smallest per cfg.select), W <- Z U with unit columns whose
+ * largest-magnitude entry is positive.
+ *   k_new host, may be NULL; receives the new number of columns of W.
+ * Errors: STATE (no completed solve since the last update), SUBSPACE_SINGULAR
+ * (F not positive definite even after dropping directions), CUDA. */
+dcg_status dcg_update_subspace(dcg_ctx* ctx, int32_t* k_new);
+
+/* Harmonic Ritz values of the last update, descending (float64, host).
+ *   theta host, capacity cap; m host: number of values (cols(Z)). */
+dcg_status dcg_get_ritz_values(dcg_ctx* ctx, double* theta, int32_t cap, int32_t* m);
+
+/* Prior knowledge for the next solve or a checkpoint restore (Fig. 1 caption):
+ * W device, column-major n x k (0 <= k <= cfg.k), copied. */
+dcg_status dcg_set_subspace(dcg_ctx* ctx, const float* W, int32_t k);
+
+/* Copies the current W (device, column-major n x k_active) into W (device,
+ * capacity n x cfg.k) and its column count into *k (host). */
+dcg_status dcg_get_subspace(dcg_ctx* ctx, float* W, int32_t* k);
+
+/* Residual history |r_j| / |b|, j = 0..iters, of the last solve when
+ * cfg.record_history is set. relres: host, capacity cap; count: host. */
+dcg_status dcg_get_history(dcg_ctx* ctx, double* relres, int32_t cap, int32_t* count);
+
+/* ------------------------------------------------------------------------ */
+/* Single steps of the hot path, for testing and measurement                 */
+/* ------------------------------------------------------------------------ */
+
+/* One operator application q = A p with the fused product p^T q (line 6).
+ *   p, q device n floats; pAp host, may be NULL (then no synchronisation).
+ * Errors: STATE (no operator), INVALID_ARG, CUDA. */
+dcg_status dcg_matvec(dcg_ctx* ctx, const float* p, float* q, double* pAp);
+
+/* Multi-vector product Y = A V in one pass over the operator (the start-of-
+ * solve product of Algorithm 1 line 3 with AW).
+ *   V device, column-major n x c; Y device, column-major n x c; 1 <= c <= 129. */
+dcg_status dcg_apply_block(dcg_ctx* ctx, const float* V, int32_t c, float* Y);
+
+/* Synchronises the context's stream. */
+dcg_status dcg_sync(dcg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DCG_H */

@@ -1,0 +1,627 @@
+// C ABI of the deflated-CG library (declarations and contracts in include/dcg.h).
+//
+// A context owns its device workspace and a CUDA graph of one whole solve of
+// Algorithm 1: the start-of-solve product and E = W^T A W, lines 3-4, then a
+// device-side WHILE node over the iteration (operator, phase 1, an IF node for
+// the true-residual check / refinement, phase 2), an IF node for the final true
+// residual, and the finishing kernel. The graph is built once per operator and
+// replayed for every solve; kernels read the per-solve values (k, warm start,
+// tolerances) from the device state, so nothing is re-captured between solves.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "dcg_kernels.cuh"
+
+using namespace dcg;
+
+enum OpKind { OP_NONE = 0, OP_DENSE = 1, OP_RBF = 2 };
+
+struct dcg_ctx {
+  dcg_config cfg;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+  std::vector<void*> allocs;
+
+  Ws w{};
+  DevState* st = nullptr;     // device
+  DevState* h_st = nullptr;   // pinned host copy
+  int* h_small = nullptr;     // pinned: ritz k_out, status
+  double* gramE_part = nullptr;
+
+  // harmonic Ritz buffers
+  double *F = nullptr, *G = nullptr, *Vd = nullptr, *theta = nullptr, *ritz_part = nullptr, *colscale = nullptr;
+  float *Vj = nullptr, *U = nullptr, *Wout = nullptr;
+  int *k_out = nullptr, *ritz_status = nullptr;
+  int k_active = 0;
+  int m_last = 0;        // number of harmonic Ritz values of the last update
+  bool have_solve = false;
+  int last_iters = 0;
+
+  // operator
+  int op = OP_NONE;
+  const float* A = nullptr;
+  int64_t lda = 0;
+  CUtensorMap tmap;
+
+  // standalone matvec scratch
+  double* mv_partials = nullptr;
+  double* mv_result = nullptr;
+  unsigned int* mv_ticket = nullptr;
+
+  // solve graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_valid = false;
+  Handles h{};
+  int grid_rows = 1, grid_iter = 1;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+};
+
+static std::string g_create_err;
+static std::mutex g_mu;
+static EncodeTiledFn g_encode = nullptr;
+
+static dcg_status fail(dcg_ctx* c, dcg_status s, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_create_err = msg;
+  return s;
+}
+
+static dcg_status cuda_fail(dcg_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return fail(c, DCG_ERR_NOMEM, m);
+  return fail(c, DCG_ERR_CUDA, m);
+}
+
+#define CK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+  } while (0)
+
+static EncodeTiledFn get_encode() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  return g_encode;
+}
+
+template <typename T>
+static cudaError_t dalloc(dcg_ctx* c, T** p, size_t count) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(T) + 16);
+  if (e != cudaSuccess) return e;
+  c->allocs.push_back(v);
+  *p = static_cast<T*>(v);
+  return cudaMemsetAsync(v, 0, count * sizeof(T) + 16, c->stream);
+}
+
+extern "C" const char* dcg_status_string(dcg_status s) {
+  switch (s) {
+    case DCG_OK: return "ok";
+    case DCG_ERR_INVALID_ARG: return "invalid argument";
+    case DCG_ERR_NOMEM: return "out of device memory";
+    case DCG_ERR_CUDA: return "CUDA error";
+    case DCG_ERR_BREAKDOWN: return "breakdown: p^T A p <= 0 (operator not SPD)";
+    case DCG_ERR_SUBSPACE_SINGULAR: return "deflation subspace singular";
+    case DCG_ERR_MAXITER: return "maximum iterations reached";
+    case DCG_ERR_TIMEOUT: return "device-side wait timed out";
+    case DCG_ERR_STATE: return "call out of order";
+    case DCG_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* dcg_last_error(const dcg_ctx* c) {
+  return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+static void destroy_graph(dcg_ctx* c) {
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->exec = nullptr;
+  c->graph = nullptr;
+  c->graph_valid = false;
+}
+
+extern "C" dcg_status dcg_destroy(dcg_ctx* c) {
+  if (!c) return DCG_OK;
+  cudaStreamSynchronize(c->stream);
+  destroy_graph(c);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->h_st) cudaFreeHost(c->h_st);
+  if (c->h_small) cudaFreeHost(c->h_small);
+  for (auto& s : c->cap)
+    if (s) cudaStreamDestroy(s);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->ev2) cudaEventDestroy(c->ev2);
+  delete c;
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** out) {
+  if (!cfg || !out) return fail(nullptr, DCG_ERR_INVALID_ARG, "cfg and out must not be NULL");
+  *out = nullptr;
+  const dcg_config& g = *cfg;
+  for (int i = 0; i < 7; ++i)
+    if (g.reserved[i]) return fail(nullptr, DCG_ERR_INVALID_ARG, "reserved fields must be zero");
+  if (g.n < 1 || g.n > (int64_t(1) << 30)) return fail(nullptr, DCG_ERR_INVALID_ARG, "n out of range");
+  if (g.k < 0 || g.ell < 0 || g.k > g.n || g.ell > g.n) return fail(nullptr, DCG_ERR_INVALID_ARG, "k, ell out of range");
+  if (g.max_iter < 1) return fail(nullptr, DCG_ERR_INVALID_ARG, "max_iter must be >= 1");
+  if (!(g.tol > 0.0)) return fail(nullptr, DCG_ERR_INVALID_ARG, "tol must be > 0");
+  if (g.window != DCG_WINDOW_FIRST && g.window != DCG_WINDOW_LAST)
+    return fail(nullptr, DCG_ERR_INVALID_ARG, "bad window");
+  if (g.select != DCG_SELECT_LARGEST && g.select != DCG_SELECT_SMALLEST)
+    return fail(nullptr, DCG_ERR_INVALID_ARG, "bad select");
+  if (g.refine_every < 0) return fail(nullptr, DCG_ERR_INVALID_ARG, "refine_every must be >= 0");
+  if (g.k > 96 || g.ell > kMaxEll)
+    return fail(nullptr, DCG_ERR_UNSUPPORTED, "k <= 96 and ell <= 128 in this build");
+
+  dcg_ctx* c = new dcg_ctx();
+  c->cfg = g;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->err.clear();
+  auto bail = [&](dcg_status s) {
+    g_create_err = c->err;
+    dcg_destroy(c);
+    return s;
+  };
+#define CKC(call)                                              \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return bail(cuda_fail(c, e_, #call)); \
+  } while (0)
+  CKC(cudaGetDevice(&c->device));
+  CKC(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  for (auto& s : c->cap) CKC(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  CKC(cudaEventCreate(&c->ev0));
+  CKC(cudaEventCreate(&c->ev1));
+  CKC(cudaEventCreate(&c->ev2));
+  CKC(rowop_configure());
+  CKC(chol_configure(96));
+  CKC(ritz_configure());
+
+  const int n = int(g.n), kmax = g.k, ellmax = g.ell;
+  c->grid_rows = rowop_grid(n, c->num_sms);
+  c->grid_iter = std::max(1, std::min(c->num_sms, (n + 63) / 64));
+  Ws& w = c->w;
+  w.n = n;
+  w.kmax = kmax;
+  w.ellmax = ellmax;
+  w.tol = g.tol;
+  CKC(dalloc(c, &w.XW, size_t(n) * (1 + kmax)));
+  CKC(dalloc(c, &w.Y, size_t(n) * (1 + kmax)));
+  CKC(dalloc(c, &w.r, size_t(n)));
+  CKC(dalloc(c, &w.p, size_t(n)));
+  CKC(dalloc(c, &w.q, size_t(n)));
+  CKC(dalloc(c, &w.b, size_t(n)));
+  CKC(dalloc(c, &w.P, size_t(n) * std::max(ellmax, 1)));
+  CKC(dalloc(c, &w.Q, size_t(n) * std::max(ellmax, 1)));
+  const int kk = std::max(kmax, 1);
+  CKC(dalloc(c, &w.E, size_t(kk) * kk));
+  CKC(dalloc(c, &w.Linv, size_t(kk) * kk));
+  CKC(dalloc(c, &w.h, size_t(kk)));
+  CKC(dalloc(c, &w.hp, size_t(kk)));
+  CKC(dalloc(c, &w.mu, size_t(kk)));
+  CKC(dalloc(c, &w.gamma, size_t(kk)));
+  CKC(dalloc(c, &w.mu_f, size_t(kk)));
+  CKC(dalloc(c, &w.gamma_f, size_t(kk)));
+  CKC(dalloc(c, &w.partials, size_t(std::max(c->grid_iter, c->grid_rows)) * kReduceSlots));
+  const int hist_cap = g.record_history ? g.max_iter + 2 : 1;
+  CKC(dalloc(c, &w.hist, size_t(hist_cap)));
+  CKC(dalloc(c, &c->st, 1));
+  w.st = c->st;
+  CKC(dalloc(c, &c->gramE_part, gram_partials_doubles(n, kk, c->num_sms)));
+  const int m = kmax + ellmax;
+  const int mm = std::max(m, 1);
+  CKC(dalloc(c, &c->F, size_t(mm) * mm));
+  CKC(dalloc(c, &c->G, size_t(mm) * mm));
+  CKC(dalloc(c, &c->Vd, size_t(mm) * mm));
+  CKC(dalloc(c, &c->Vj, size_t(mm) * mm));
+  CKC(dalloc(c, &c->theta, size_t(mm)));
+  CKC(dalloc(c, &c->U, size_t(mm) * kk));
+  CKC(dalloc(c, &c->Wout, size_t(n) * kk));
+  CKC(dalloc(c, &c->colscale, size_t(kk)));
+  CKC(dalloc(c, &c->k_out, 1));
+  CKC(dalloc(c, &c->ritz_status, 1));
+  CKC(dalloc(c, &c->ritz_part, gram_partials_doubles(n, mm, c->num_sms)));
+  CKC(dalloc(c, &c->mv_partials, size_t(c->grid_rows) + 1));
+  CKC(dalloc(c, &c->mv_result, 1));
+  CKC(dalloc(c, &c->mv_ticket, 1));
+  CKC(cudaMallocHost(&c->h_st, sizeof(DevState)));
+  CKC(cudaMallocHost(&c->h_small, 4 * sizeof(int)));
+  memset(c->h_st, 0, sizeof(DevState));
+  CKC(cudaStreamSynchronize(c->stream));
+#undef CKC
+  *out = c;
+  return DCG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Operators
+// ---------------------------------------------------------------------------
+extern "C" dcg_status dcg_set_operator_dense(dcg_ctx* c, const float* A, int64_t lda) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  if (!A) return fail(c, DCG_ERR_INVALID_ARG, "A is NULL");
+  if (lda < c->cfg.n || (lda % 4) != 0) return fail(c, DCG_ERR_INVALID_ARG, "lda must be >= n and a multiple of 4");
+  if ((reinterpret_cast<uintptr_t>(A) & 15) != 0) return fail(c, DCG_ERR_INVALID_ARG, "A must be 16-byte aligned");
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return fail(c, DCG_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  const bool same = (c->op == OP_DENSE && c->A == A && c->lda == lda);
+  if (!same) {
+    CUtensorMap m;
+    if (!make_rowop_tmap(&m, A, c->cfg.n, lda, enc)) return fail(c, DCG_ERR_INVALID_ARG, "tensor map encode failed");
+    c->tmap = m;
+    c->A = A;
+    c->lda = lda;
+    c->op = OP_DENSE;
+    destroy_graph(c);
+  }
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_set_operator_rbf(dcg_ctx* c, const float* X, int32_t d, int32_t xformat, double l,
+                                           double s2, double noise) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  (void)X; (void)d; (void)xformat; (void)l; (void)s2; (void)noise;
+  return fail(c, DCG_ERR_UNSUPPORTED, "matrix-free RBF operator not available in this build");
+}
+
+extern "C" dcg_status dcg_set_rbf_params(dcg_ctx* c, double l, double s2, double noise) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  (void)l; (void)s2; (void)noise;
+  return fail(c, DCG_ERR_STATE, "no matrix-free operator set");
+}
+
+extern "C" dcg_status dcg_form_rbf_dense(const float* X, int64_t n, int32_t d, double l, double s2, double noise,
+                                         float* A, int64_t lda, void* stream) {
+  if (!X || !A || n < 1 || d < 1 || d > 256 || lda < n || !(l > 0.0)) return DCG_ERR_INVALID_ARG;
+  if (n > (int64_t(1) << 30)) return DCG_ERR_INVALID_ARG;
+  cudaError_t e = launch_form_rbf(X, int(n), d, l, s2, noise, A, lda, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? DCG_OK : DCG_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Operator launches (one place per operator kind)
+// ---------------------------------------------------------------------------
+static cudaError_t op_matvec(dcg_ctx* c, const float* p, float* q, double* result, double* partials,
+                             unsigned int* ticket, DevState* st, cudaStream_t s) {
+  RowOpArgs a{};
+  a.v = p;
+  a.out = q;
+  a.n = c->w.n;
+  a.partials = partials;
+  a.ticket = ticket;
+  a.result = result;
+  a.st = st;
+  a.skip_if_done = st ? 1 : 0;
+  return launch_rowop(&c->tmap, a, false, c->grid_rows, s);
+}
+
+static cudaError_t op_resid(dcg_ctx* c, int mode, int skip_if_done, cudaStream_t s) {
+  RowOpArgs a{};
+  a.v = c->w.XW;
+  a.out = c->w.r;
+  a.b = c->w.b;
+  a.n = c->w.n;
+  a.partials = c->mv_partials;
+  a.ticket = &c->st->ticket[T_CHECK_RES];
+  a.result = nullptr;
+  a.st = c->st;
+  a.skip_if_done = skip_if_done;
+  a.resid_mode = mode;
+  return launch_rowop(&c->tmap, a, true, c->grid_rows, s);
+}
+
+static cudaError_t op_block(dcg_ctx* c, const float* V, int ncols, float* Y, DevState* st, cudaStream_t s) {
+  ApplyBlockArgs a{};
+  a.A = c->A;
+  a.lda = c->lda;
+  a.V = V;
+  a.Y = Y;
+  a.n = c->w.n;
+  a.c = ncols;
+  a.st = st;
+  a.skip_if_done = st ? 1 : 0;
+  return launch_apply_block(a, st ? c->w.kmax + 1 : ncols, s);
+}
+
+// ---------------------------------------------------------------------------
+// Solve graph
+// ---------------------------------------------------------------------------
+static cudaError_t add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                   cudaGraph_t* body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
+  if (e != cudaSuccess) return e;
+  std::vector<cudaGraphNode_t> d(deps, deps + ndeps);
+  cudaGraphNodeParams prm = {cudaGraphNodeTypeConditional};
+  prm.conditional.handle = h;
+  prm.conditional.type = type;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, cg, d.data(), nullptr, d.size(), &prm);
+  if (e != cudaSuccess) return e;
+  *body = prm.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// The check / refinement branch: r = b - A x (float64 accumulation); if the
+// solve is not finished, re-deflate x, r against W and refresh rho, beta, mu.
+static cudaError_t capture_check_branch(dcg_ctx* c, cudaStream_t s, int pre_loop) {
+  cudaError_t e;
+  if ((e = op_resid(c, -1, 1, s)) != cudaSuccess) return e;
+  if ((e = launch_check_dots(c->w, c->grid_iter, s)) != cudaSuccess) return e;
+  return launch_check_update(c->w, c->grid_iter, pre_loop, 0, c->h, s);
+}
+
+static dcg_status build_graph(dcg_ctx* c) {
+  destroy_graph(c);
+  CK(cudaGraphCreate(&c->graph, 0));
+  Handles& h = c->h;
+  CK(cudaGraphConditionalHandleCreate(&h.pre, c->graph, 0, cudaGraphCondAssignDefault));
+  CK(cudaGraphConditionalHandleCreate(&h.loop, c->graph, 1, cudaGraphCondAssignDefault));
+  CK(cudaGraphConditionalHandleCreate(&h.chk, c->graph, 0, cudaGraphCondAssignDefault));
+  CK(cudaGraphConditionalHandleCreate(&h.fin, c->graph, 0, cudaGraphCondAssignDefault));
+  Ws& w = c->w;
+  cudaStream_t s0 = c->cap[0], s1 = c->cap[1], s2 = c->cap[2];
+  CK(cudaStreamBeginCaptureToGraph(s0, c->graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  auto run = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  // Start of solve: A [x_{-1} | W], r_{-1}, E and its factor, x_0, p_0.
+  run(op_block(c, w.XW, 0, w.Y, c->st, s0));
+  run(launch_setup_r(w, c->grid_iter, s0));
+  run(launch_gram_E(w, c->gramE_part, c->num_sms, s0));
+  run(launch_chol_E(w, s0));
+  run(launch_check_dots(w, c->grid_iter, s0));
+  run(launch_check_update(w, c->grid_iter, 0, 1, h, s0));
+  run(launch_phase2_setup(w, c->grid_iter, s0));
+  // IF |r_0| <= tol |b|: confirm with the true residual.
+  cudaGraph_t body = nullptr;
+  run(add_conditional(s0, h.pre, cudaGraphCondTypeIf, &body));
+  if (e == cudaSuccess) {
+    run(cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    run(capture_check_branch(c, s1, 1));
+    cudaGraph_t tmp;
+    run(cudaStreamEndCapture(s1, &tmp));
+  }
+  run(launch_loop_gate(w, h, s0));
+  // WHILE not done: one iteration of lines 5-14.
+  run(add_conditional(s0, h.loop, cudaGraphCondTypeWhile, &body));
+  if (e == cudaSuccess) {
+    run(cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    run(op_matvec(c, w.p, w.q, &c->st->d, c->mv_partials, &c->st->ticket[T_MATVEC], c->st, s1));
+    run(launch_phase1(w, c->grid_iter, h, s1));
+    cudaGraph_t inner = nullptr;
+    run(add_conditional(s1, h.chk, cudaGraphCondTypeIf, &inner));
+    if (e == cudaSuccess) {
+      run(cudaStreamBeginCaptureToGraph(s2, inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      run(capture_check_branch(c, s2, 0));
+      cudaGraph_t tmp;
+      run(cudaStreamEndCapture(s2, &tmp));
+    }
+    run(launch_phase2(w, c->grid_iter, h, s1));
+    cudaGraph_t tmp;
+    run(cudaStreamEndCapture(s1, &tmp));
+  }
+  // IF the final iterate has no true residual yet (max_iter, breakdown): form it.
+  run(launch_final_gate(w, h, s0));
+  run(add_conditional(s0, h.fin, cudaGraphCondTypeIf, &body));
+  if (e == cudaSuccess) {
+    run(cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    run(op_resid(c, 3, 0, s1));
+    cudaGraph_t tmp;
+    run(cudaStreamEndCapture(s1, &tmp));
+  }
+  run(launch_finalize(w, c->grid_iter, s0));
+  cudaGraph_t g2 = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s0, &g2);
+  if (e != cudaSuccess) return cuda_fail(c, e, "capturing the solve graph");
+  if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
+  CK(cudaGraphInstantiate(&c->exec, c->graph, 0));
+  c->graph_valid = true;
+  return DCG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Solve
+// ---------------------------------------------------------------------------
+extern "C" dcg_status dcg_solve(dcg_ctx* c, const float* b, float* x, dcg_solve_info* info) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  if (!b || !x) return fail(c, DCG_ERR_INVALID_ARG, "b and x must not be NULL");
+  if (c->op == OP_NONE) return fail(c, DCG_ERR_STATE, "no operator set");
+  if (!c->graph_valid) {
+    dcg_status s = build_graph(c);
+    if (s != DCG_OK) return s;
+  }
+  const int n = c->w.n;
+  DevState* hs = c->h_st;
+  memset(hs, 0, sizeof(DevState));
+  hs->max_iter = c->cfg.max_iter;
+  hs->refine_every = c->cfg.refine_every;
+  hs->k = c->k_active;
+  hs->ell = c->cfg.ell;
+  hs->window = c->cfg.window;
+  hs->reproject = c->cfg.reproject;
+  hs->hist_on = c->cfg.record_history;
+  hs->hist_cap = c->cfg.record_history ? c->cfg.max_iter + 2 : 0;
+  hs->warm_start = c->cfg.warm_start;
+  hs->status = DCG_OK;
+  cudaStream_t s = c->stream;
+  CK(cudaMemcpyAsync(c->st, hs, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->w.b, b, size_t(n) * 4, cudaMemcpyDeviceToDevice, s));
+  if (c->cfg.warm_start)
+    CK(cudaMemcpyAsync(c->w.XW, x, size_t(n) * 4, cudaMemcpyDeviceToDevice, s));
+  else
+    CK(cudaMemsetAsync(c->w.XW, 0, size_t(n) * 4, s));
+  CK(cudaEventRecord(c->ev0, s));
+  CK(cudaGraphLaunch(c->exec, s));
+  CK(cudaEventRecord(c->ev1, s));
+  CK(cudaMemcpyAsync(x, c->w.XW, size_t(n) * 4, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(hs, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  c->have_solve = (hs->status == DCG_OK || hs->status == DCG_ERR_MAXITER);
+  c->last_iters = hs->iter;
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->status = hs->status;
+    info->iters = hs->iter;
+    info->matvecs_loop = hs->iter;
+    info->matvecs_setup = hs->k + hs->warm_start;
+    info->matvecs_check = hs->matvecs_check;
+    info->k_used = hs->k;
+    info->stored = hs->nstored;
+    info->relres_recursive = hs->bnorm2 > 0.0 ? sqrt(hs->rho / hs->bnorm2) : 0.0;
+    info->relres_true = hs->relres_true;
+    info->ms_total = ms;
+  }
+  if (hs->status != DCG_OK) {
+    char buf[160];
+    snprintf(buf, sizeof(buf), "solve ended with status %d (%s) after %d iterations%s", hs->status,
+             dcg_status_string(dcg_status(hs->status)), hs->iter,
+             hs->status == DCG_ERR_TIMEOUT ? " (bounded wait gave up)" : "");
+    c->err = buf;
+  }
+  return dcg_status(hs->status);
+}
+
+extern "C" dcg_status dcg_update_subspace(dcg_ctx* c, int32_t* k_new) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  if (!c->have_solve) return fail(c, DCG_ERR_STATE, "no completed solve since the last update");
+  const int kk = c->k_active, ns = c->h_st->nstored;
+  const int m = kk + ns;
+  int knew = std::min(c->cfg.k, m);
+  if (c->cfg.k == 0 || m == 0) {
+    c->have_solve = false;
+    c->m_last = 0;
+    if (k_new) *k_new = c->k_active;
+    return DCG_OK;
+  }
+  RitzArgs a{};
+  a.n = c->w.n;
+  a.k_act = kk;
+  a.nstored = ns;
+  a.k_want = c->cfg.k;
+  a.select = c->cfg.select;
+  a.W = c->w.XW + c->w.n;
+  a.AW = c->w.Y + c->w.n;
+  a.P = c->w.P;
+  a.Q = c->w.Q;
+  a.F = c->F;
+  a.G = c->G;
+  a.part = c->ritz_part;
+  a.Vj = c->Vj;
+  a.Vd = c->Vd;
+  a.theta = c->theta;
+  a.U = c->U;
+  a.Wout = c->Wout;
+  a.k_out = c->k_out;
+  a.status = c->ritz_status;
+  a.colscale = c->colscale;
+  cudaStream_t s = c->stream;
+  CK(launch_ritz(a, c->num_sms, c->w.XW + c->w.n, s));
+  CK(cudaMemcpyAsync(c->h_small, c->k_out, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->h_small + 1, c->ritz_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  c->have_solve = false;
+  if (c->h_small[1] != DCG_OK) return fail(c, dcg_status(c->h_small[1]), "harmonic Ritz: F not positive definite");
+  knew = c->h_small[0];
+  c->k_active = knew;
+  c->m_last = m;
+  if (k_new) *k_new = knew;
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_get_ritz_values(dcg_ctx* c, double* theta, int32_t cap, int32_t* m) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  if (m) *m = c->m_last;
+  if (!theta || cap <= 0 || c->m_last == 0) return DCG_OK;
+  const int cnt = std::min(cap, c->m_last);
+  CK(cudaMemcpyAsync(theta, c->theta, size_t(cnt) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_set_subspace(dcg_ctx* c, const float* W, int32_t k) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  if (k < 0 || k > c->cfg.k) return fail(c, DCG_ERR_INVALID_ARG, "k must be in [0, cfg.k]");
+  if (k > 0 && !W) return fail(c, DCG_ERR_INVALID_ARG, "W is NULL");
+  if (k > 0)
+    CK(cudaMemcpyAsync(c->w.XW + c->w.n, W, size_t(c->w.n) * k * 4, cudaMemcpyDeviceToDevice, c->stream));
+  c->k_active = k;
+  c->have_solve = false;
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_get_subspace(dcg_ctx* c, float* W, int32_t* k) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  if (k) *k = c->k_active;
+  if (W && c->k_active > 0) {
+    CK(cudaMemcpyAsync(W, c->w.XW + c->w.n, size_t(c->w.n) * c->k_active * 4, cudaMemcpyDeviceToDevice,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_get_history(dcg_ctx* c, double* relres, int32_t cap, int32_t* count) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  if (!c->cfg.record_history) return fail(c, DCG_ERR_STATE, "record_history is off");
+  const int cnt = std::min(cap, c->last_iters + 1);
+  if (count) *count = c->last_iters + 1;
+  if (relres && cnt > 0) {
+    CK(cudaMemcpyAsync(relres, c->w.hist, size_t(cnt) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_matvec(dcg_ctx* c, const float* p, float* q, double* pAp) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  if (c->op == OP_NONE) return fail(c, DCG_ERR_STATE, "no operator set");
+  if (!p || !q || (reinterpret_cast<uintptr_t>(p) & 15)) return fail(c, DCG_ERR_INVALID_ARG, "p, q: 16-byte aligned device vectors");
+  CK(op_matvec(c, p, q, c->mv_result, c->mv_partials, c->mv_ticket, nullptr, c->stream));
+  if (pAp) {
+    CK(cudaMemcpyAsync(pAp, c->mv_result, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_apply_block(dcg_ctx* c, const float* V, int32_t ncols, float* Y) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  if (c->op == OP_NONE) return fail(c, DCG_ERR_STATE, "no operator set");
+  if (!V || !Y || ncols < 1 || ncols > kMaxBlockCols) return fail(c, DCG_ERR_INVALID_ARG, "bad block arguments");
+  CK(op_block(c, V, ncols, Y, nullptr, c->stream));
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_sync(dcg_ctx* c) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  return DCG_OK;
+}

@@ -1,0 +1,180 @@
+// Shared device-side definitions of the deflated-CG library: the per-context
+// device state, bounded mbarrier/TMA helpers (inline PTX for sm_103a) and
+// block reductions. Host orchestration lives in dcg_api.cu.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dcg.h"
+
+namespace dcg {
+
+constexpr int kMaxK = 128;        // deflation vectors (columns of W)
+constexpr int kMaxEll = 128;      // stored directions
+constexpr int kMaxM = kMaxK + kMaxEll;
+constexpr int kMaxBlockCols = 129;  // columns of one multi-vector product
+constexpr int kReduceSlots = 2 * kMaxK + 8;  // per-CTA partial sums of one reduction
+constexpr long long kSpinLimit = 1ll << 22;  // bounded waits: polls before giving up
+
+// Ticket counters for the "last CTA finishes the reduction" pattern, one per
+// reduction site so that consecutive kernels never share a counter.
+enum Ticket : int {
+  T_MATVEC = 0, T_SETUP_G, T_SETUP_H, T_PHASE1, T_CHECK_RES, T_CHECK_G, T_CHECK_H,
+  T_FINAL, T_GALERKIN, T_COUNT
+};
+
+// Device-resident solver state. Written only by kernels (and once per solve
+// by the host, before the graph launch).
+struct DevState {
+  double rho;        // r^T r of the current residual
+  double rho_new;    // r^T r after the x, r update of this iteration
+  double d;          // p^T A p of the current direction (Algorithm 1 line 6)
+  double alpha;
+  double beta;
+  double bnorm2;     // |b|^2
+  double thresh2;    // (tol |b|)^2
+  double rho_true;   // |b - A x|^2 of the last true-residual evaluation
+  double relres_true;
+  int iter;          // completed iterations
+  int max_iter;
+  int status;        // dcg_status
+  int done;          // 1 once the loop must stop
+  int mode;          // 0 none, 1 convergence check, 2 periodic refinement
+  int refine_every;
+  int k;             // active deflation vectors this solve
+  int ell;
+  int window;        // dcg_window
+  int nstored;       // directions stored in this solve (<= ell)
+  int head;          // next ring slot (window LAST)
+  int matvecs_check;
+  int reproject;
+  int hist_on;
+  int hist_cap;
+  int true_valid;    // relres_true describes the final x
+  int warm_start;
+  int zero_rhs;
+  int timeout_site;  // nonzero: which bounded wait gave up
+  unsigned int ticket[T_COUNT];
+};
+
+// --------------------------------------------------------------------------
+// Reductions
+// --------------------------------------------------------------------------
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Last-CTA detection: every CTA calls this after writing its partials with a
+// __threadfence(); exactly one CTA (the last to arrive) gets true and resets
+// the counter for the next launch. No CTA waits on another.
+__device__ __forceinline__ bool arrive_last(unsigned int* counter) {
+  __shared__ unsigned int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int prev = atomicAdd(counter, 1u);
+    s_last = (prev == gridDim.x * gridDim.y * gridDim.z - 1) ? 1u : 0u;
+    if (s_last) *counter = 0u;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+// --------------------------------------------------------------------------
+// mbarrier and TMA (bulk tensor copy) helpers, sm_90+ PTX used on sm_103a
+// --------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbarrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the given phase parity; gives up after kSpinLimit polls and
+// returns false (the caller records a timeout and leaves).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+  for (long long i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
+// 2-D tiled TMA load of box {x, y} at coordinates (x0, y0) into shared memory,
+// completing on an mbarrier. x0 * sizeof(elem) must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* map, uint64_t* bar, int x0,
+                                            int y0) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x0), "r"(y0)
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// --------------------------------------------------------------------------
+// Small float64 helpers shared by the iteration kernels
+// --------------------------------------------------------------------------
+
+// y = L^{-T} (L^{-1} h) with Linv the lower-triangular inverse Cholesky factor
+// of E (k x k, row-major). Run by one warp; h, y in shared memory; k <= kMaxK.
+__device__ __forceinline__ void apply_Einv_warp(const double* __restrict__ Linv, int k, const double* h,
+                                                double* tmp, double* y) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < k; i += 32) {  // tmp = Linv h
+    double s = 0.0;
+    for (int j = 0; j <= i; ++j) s = fma(Linv[i * k + j], h[j], s);
+    tmp[i] = s;
+  }
+  __syncwarp();
+  for (int i = lane; i < k; i += 32) {  // y = Linv^T tmp
+    double s = 0.0;
+    for (int j = i; j < k; ++j) s = fma(Linv[j * k + i], tmp[j], s);
+    y[i] = s;
+  }
+  __syncwarp();
+}
+
+}  // namespace dcg

@@ -1,0 +1,127 @@
+// Kernel argument structs and host-side launchers shared between the CUDA
+// translation units of the library. Every launcher enqueues on the given
+// stream and returns the launch error (no synchronisation).
+#pragma once
+
+#include <type_traits>
+
+#include "dcg_common.cuh"
+
+namespace dcg {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Context workspace as seen by the kernels. Column c of W is XW + (1 + c) n,
+// column 0 of XW is the iterate x; Y mirrors it with A x_{-1} and AW.
+struct Ws {
+  int n;
+  int kmax;
+  int ellmax;
+  float* XW;       // n x (1 + kmax)
+  float* Y;        // n x (1 + kmax)
+  float* r;
+  float* p;
+  float* q;
+  float* b;
+  float* P;        // n x ellmax stored directions
+  float* Q;        // n x ellmax stored A p
+  double* E;       // kmax x kmax, W^T A W
+  double* Linv;    // kmax x kmax, inverse Cholesky factor of E (row-major, lower)
+  double* h;       // kmax: (AW)^T r
+  double* hp;      // kmax: (AW)^T p
+  double* mu;      // kmax
+  double* gamma;   // kmax
+  float* mu_f;     // kmax
+  float* gamma_f;  // kmax
+  double* partials;  // grid x kReduceSlots
+  double* hist;    // hist_cap
+  DevState* st;
+  double tol;
+};
+
+// Conditional-node handles of the solve graph (see dcg_api.cu).
+struct Handles {
+  cudaGraphConditionalHandle pre;    // IF: convergence check before the loop
+  cudaGraphConditionalHandle loop;   // WHILE: the iteration
+  cudaGraphConditionalHandle chk;    // IF inside the loop: check / refinement
+  cudaGraphConditionalHandle fin;    // IF after the loop: final true residual
+};
+
+struct RowOpArgs {
+  const float* v;        // p (matvec) or x (residual)
+  float* out;            // q (matvec) or r (residual)
+  const float* b;        // residual only
+  int n;
+  double* partials;      // >= grid doubles
+  unsigned int* ticket;
+  double* result;        // matvec: p^T q; residual without state: |r|^2
+  DevState* st;          // residual: updates rho_true etc.; may be null
+  int skip_if_done;
+  int resid_mode;        // 1 check, 2 refinement, 3 final, -1: read st->mode
+};
+
+struct ApplyBlockArgs {
+  const float* A;
+  int64_t lda;
+  const float* V;
+  float* Y;
+  int n;
+  int c;
+  DevState* st;          // if set: c = k + warm_start, columns start at x or W
+  int skip_if_done;
+};
+
+// ---- dense operator (k_dense.cu)
+size_t rowop_smem_bytes();
+cudaError_t rowop_configure();
+int rowop_grid(int n, int num_sms);
+bool make_rowop_tmap(CUtensorMap* map, const float* A, int64_t n, int64_t lda, EncodeTiledFn encode);
+cudaError_t launch_rowop(const CUtensorMap* tmap, const RowOpArgs& a, bool resid, int grid, cudaStream_t s);
+cudaError_t launch_apply_block(const ApplyBlockArgs& a, int cmax, cudaStream_t s);
+cudaError_t launch_form_rbf(const float* X, int n, int d, double l, double s2, double noise, float* A, int64_t lda,
+                            cudaStream_t s);
+
+// ---- iteration kernels (k_iter.cu)
+cudaError_t launch_setup_r(const Ws& w, int grid, cudaStream_t s);
+cudaError_t launch_gram_E(const Ws& w, double* part, int num_sms, cudaStream_t s);
+cudaError_t launch_chol_E(const Ws& w, cudaStream_t s);
+cudaError_t launch_check_dots(const Ws& w, int grid, cudaStream_t s);
+cudaError_t launch_check_update(const Ws& w, int grid, int pre_loop, int setup, Handles h, cudaStream_t s);
+cudaError_t launch_phase1(const Ws& w, int grid, Handles h, cudaStream_t s);
+cudaError_t launch_phase2(const Ws& w, int grid, Handles h, cudaStream_t s);
+cudaError_t launch_phase2_setup(const Ws& w, int grid, cudaStream_t s);
+cudaError_t launch_loop_gate(const Ws& w, Handles h, cudaStream_t s);
+cudaError_t launch_final_gate(const Ws& w, Handles h, cudaStream_t s);
+cudaError_t launch_finalize(const Ws& w, int grid, cudaStream_t s);
+
+// ---- harmonic Ritz (k_ritz.cu)
+struct RitzArgs {
+  int n;
+  int k_act;        // columns of W in Z
+  int nstored;      // columns of P in Z
+  int k_want;
+  int select;       // dcg_select
+  const float* W;   // n x k_act
+  const float* AW;
+  const float* P;   // n x nstored
+  const float* Q;
+  double* F;        // m x m
+  double* G;
+  double* part;     // gram partials
+  float* Vj;        // m x m Jacobi eigenvectors (float32)
+  double* Vd;       // m x m float64 scratch
+  double* theta;    // m, descending
+  float* U;         // m x k_want (column-major, leading dimension m)
+  float* Wout;      // n x k_want
+  int* k_out;       // device int: columns produced
+  int* status;      // device int: dcg_status of the extraction
+  double* colscale; // k_want: 1 / |w_j| with sign
+};
+size_t gram_partials_doubles(int n, int m, int num_sms);
+cudaError_t launch_ritz(const RitzArgs& a, int num_sms, float* dstW, cudaStream_t s);
+cudaError_t ritz_configure();
+cudaError_t chol_configure(int kmax);
+
+}  // namespace dcg

@@ -1,0 +1,522 @@
+// Small dense kernels:
+//   * Gram products C = A^T B of tall column blocks (E = W^T (AW) for line 3 of
+//     Algorithm 1; F = Z^T (AZ) and G = (AZ)^T (AZ) for Eq. 7), float32
+//     products summed in float32 over short row runs and in float64 across them.
+//   * Cholesky factor of E and its inverse (float64, one CTA).
+//   * Harmonic Ritz extraction (Sec. 2.3, Eq. 7): diagonal scaling, Cholesky
+//     reduction C = L^{-1} G L^{-T} in float64, cyclic Jacobi eigen-solve of C,
+//     selection of k values (reading R4), U = S L^{-T} V, W = Z U with unit
+//     columns whose largest-magnitude entry is positive (reading R5).
+#include "dcg_kernels.cuh"
+
+namespace dcg {
+
+// --------------------------------------------------------------------------
+// Gram products
+// --------------------------------------------------------------------------
+struct GramArgs {
+  int n;
+  const float* a1; int ka1; const float* a2; int ka2;   // A-side columns
+  const float* b1; int kb1; const float* b2; int kb2;   // B-side columns
+  double* part;    // splits x ma x mb
+  int chunk;       // rows per split
+  DevState* st;    // E mode: ka1 = kb1 = st->k
+};
+
+constexpr int GR_T = 32;     // output tile edge
+constexpr int GR_RUN = 256;  // rows summed in float32 before a float64 flush
+
+__device__ __forceinline__ const float* gram_col(const float* c1, int k1, const float* c2, int j, int n) {
+  return j < k1 ? c1 + int64_t(j) * n : c2 + int64_t(j - k1) * n;
+}
+
+__global__ void __launch_bounds__(256) k_gram(GramArgs g) {
+  __shared__ float As[GR_T][GR_T + 1];
+  __shared__ float Bs[GR_T][GR_T + 1];
+  int ka1 = g.ka1, ka2 = g.ka2, kb1 = g.kb1, kb2 = g.kb2;
+  if (g.st) {
+    if (g.st->done) return;
+    ka1 = kb1 = g.st->k;
+    ka2 = kb2 = 0;
+  }
+  const int ma = ka1 + ka2, mb = kb1 + kb2;
+  const int tb_count = (mb + GR_T - 1) / GR_T;
+  const int ta = blockIdx.x / max(tb_count, 1), tb = blockIdx.x % max(tb_count, 1);
+  if (ma == 0 || mb == 0 || ta * GR_T >= ma) return;
+  const int n = g.n;
+  const int r0 = blockIdx.y * g.chunk, r1 = min(n, r0 + g.chunk);
+  const int t = threadIdx.x;
+  const int oi = t / 8, oj = (t % 8) * 4;  // 32 x 32 outputs, 4 per thread
+  double accd[4] = {0.0, 0.0, 0.0, 0.0};
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  int run = 0;
+  for (int rb = r0; rb < r1; rb += GR_T) {
+    for (int idx = t; idx < GR_T * GR_T; idx += 256) {
+      const int c = idx / GR_T, rr = idx % GR_T;
+      const int row = rb + rr;
+      const int ja = ta * GR_T + c, jb = tb * GR_T + c;
+      As[rr][c] = (row < r1 && ja < ma) ? gram_col(g.a1, ka1, g.a2, ja, n)[row] : 0.f;
+      Bs[rr][c] = (row < r1 && jb < mb) ? gram_col(g.b1, kb1, g.b2, jb, n)[row] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < GR_T; ++rr) {
+      const float av = As[rr][oi];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(av, Bs[rr][oj + q], acc[q]);
+    }
+    __syncthreads();
+    run += GR_T;
+    if (run >= GR_RUN) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        accd[q] += double(acc[q]);
+        acc[q] = 0.f;
+      }
+      run = 0;
+    }
+  }
+  const int i = ta * GR_T + oi;
+  double* out = g.part + int64_t(blockIdx.y) * ma * mb;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = tb * GR_T + oj + q;
+    if (i < ma && j < mb) out[int64_t(i) * mb + j] = accd[q] + double(acc[q]);
+  }
+}
+
+// out[i*mb + j] = sum over splits (fixed order); E mode reads the size from st.
+__global__ void k_gram_reduce(const double* part, int splits, int ma, int mb, double* out, const DevState* st) {
+  if (st) {
+    if (st->done) return;
+    ma = mb = st->k;
+  }
+  const int total = ma * mb;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int sp = 0; sp < splits; ++sp) s += part[int64_t(sp) * total + idx];
+    out[idx] = s;
+  }
+}
+
+static int gram_splits(int n, int tiles, int num_sms) {
+  int splits = (2 * num_sms + tiles - 1) / max(tiles, 1);
+  const int max_splits = (n + GR_T - 1) / GR_T;
+  if (splits > max_splits) splits = max_splits;
+  return splits < 1 ? 1 : splits;
+}
+
+size_t gram_partials_doubles(int n, int m, int num_sms) {
+  const int tiles = ((m + GR_T - 1) / GR_T) * ((m + GR_T - 1) / GR_T);
+  return size_t(gram_splits(n, tiles, num_sms)) * m * m;
+}
+
+static cudaError_t launch_gram(const GramArgs& g0, int ma_max, int mb_max, int num_sms, double* out,
+                               const DevState* st, cudaStream_t s) {
+  GramArgs g = g0;
+  const int tiles = ((ma_max + GR_T - 1) / GR_T) * ((mb_max + GR_T - 1) / GR_T);
+  const int splits = gram_splits(g.n, tiles, num_sms);
+  int chunk = (g.n + splits - 1) / splits;
+  chunk = (chunk + GR_T - 1) / GR_T * GR_T;
+  g.chunk = chunk;
+  const int used = (g.n + chunk - 1) / chunk;
+  k_gram<<<dim3(tiles, used), 256, 0, s>>>(g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_gram_reduce<<<64, 256, 0, s>>>(g.part, used, ma_max, mb_max, out, st);
+  return cudaGetLastError();
+}
+
+// E = W^T (AW), k read from the device state (graph launch, per-solve k).
+cudaError_t launch_gram_E(const Ws& w, double* part, int num_sms, cudaStream_t s) {
+  GramArgs g{};
+  g.n = w.n;
+  g.a1 = w.XW + w.n;
+  g.b1 = w.Y + w.n;
+  g.part = part;
+  g.st = w.st;
+  if (w.kmax == 0) return cudaSuccess;
+  return launch_gram(g, w.kmax, w.kmax, num_sms, w.E, w.st, s);
+}
+
+// --------------------------------------------------------------------------
+// Cholesky E = L L^T (symmetrised) and Linv = L^{-1}; float64, one CTA.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_chol_E(Ws w) {
+  DevState* st = w.st;
+  if (st->done) return;
+  const int k = st->k;
+  if (k == 0) return;
+  extern __shared__ double shd[];
+  double* L = shd;          // k x k
+  double* X = shd + k * k;  // k x k, inverse
+  __shared__ int s_fail;
+  if (threadIdx.x == 0) s_fail = 0;
+  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+    const int i = idx / k, j = idx % k;
+    L[idx] = 0.5 * (w.E[i * k + j] + w.E[j * k + i]);
+  }
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      double s = L[j * k + j];
+      for (int p = 0; p < j; ++p) s -= L[j * k + p] * L[j * k + p];
+      if (!(s > 0.0) || !isfinite(s)) {
+        s_fail = 1;
+        s = 1.0;
+      }
+      L[j * k + j] = sqrt(s);
+    }
+    __syncthreads();
+    const double ljj = L[j * k + j];
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) {
+      double s = L[i * k + j];
+      for (int p = 0; p < j; ++p) s -= L[i * k + p] * L[j * k + p];
+      L[i * k + j] = s / ljj;
+    }
+    __syncthreads();
+  }
+  if (s_fail) {
+    if (threadIdx.x == 0) {
+      st->status = DCG_ERR_SUBSPACE_SINGULAR;
+      st->done = 1;
+    }
+    return;
+  }
+  // column-parallel forward substitution L X = I
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    for (int i = 0; i < c; ++i) X[i * k + c] = 0.0;
+    X[c * k + c] = 1.0 / L[c * k + c];
+    for (int i = c + 1; i < k; ++i) {
+      double s = 0.0;
+      for (int j = c; j < i; ++j) s += L[i * k + j] * X[j * k + c];
+      X[i * k + c] = -s / L[i * k + i];
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) w.Linv[idx] = X[idx];
+}
+
+cudaError_t launch_chol_E(const Ws& w, cudaStream_t s) {
+  if (w.kmax == 0) return cudaSuccess;
+  const size_t smem = size_t(2) * w.kmax * w.kmax * sizeof(double);
+  k_chol_E<<<1, 256, smem, s>>>(w);
+  return cudaGetLastError();
+}
+
+cudaError_t chol_configure(int kmax) {
+  const size_t smem = size_t(2) * kmax * kmax * sizeof(double);
+  return cudaFuncSetAttribute(k_chol_E, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+}
+
+// --------------------------------------------------------------------------
+// Harmonic Ritz eigen-solve (one CTA of 1024 threads).
+// F, G: m x m float64 (row-major) from the Gram kernels. Work arrays in the
+// same buffers: F becomes its Cholesky factor L, G the scaled G' and then
+// Y = L^{-1} G'; C (float32, shared memory) = L^{-1} G' L^{-T}.
+// --------------------------------------------------------------------------
+constexpr int EIG_THREADS = 1024;
+constexpr int EIG_MAX_SWEEPS = 30;
+
+__device__ void jacobi_pair(int m2, int r, int i, int& p, int& q) {
+  // circle method: s_0 = 0, s_j = 1 + ((j - 1 + r) mod (m2 - 1))
+  auto pos = [&](int j) { return j == 0 ? 0 : 1 + ((j - 1 + r) % (m2 - 1)); };
+  p = pos(i);
+  q = pos(m2 - 1 - i);
+}
+
+__global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, int k_new) {
+  extern __shared__ float C[];  // m x m
+  __shared__ float cs_c[kMaxM / 2 + 1], cs_s[kMaxM / 2 + 1];
+  __shared__ int pp[kMaxM / 2 + 1], qq[kMaxM / 2 + 1];
+  __shared__ double scale[kMaxM];
+  __shared__ int s_fail, s_changed;
+  __shared__ float th[kMaxM];
+  __shared__ int rank_of[kMaxM];
+  double* F = a.F;
+  double* G = a.G;
+  const int t = threadIdx.x;
+  if (t == 0) s_fail = 0;
+  // 1. diagonal scaling S = diag(F_jj^{-1/2}) and symmetrisation (in place)
+  for (int j = t; j < m; j += blockDim.x) {
+    const double f = F[j * m + j];
+    scale[j] = f > 0.0 ? 1.0 / sqrt(f) : 0.0;
+  }
+  __syncthreads();
+  for (int idx = t; idx < m * m; idx += blockDim.x) {
+    const int i = idx / m, j = idx % m;
+    if (i < j) continue;
+    const double sij = scale[i] * scale[j];
+    const double f = 0.5 * (F[i * m + j] + F[j * m + i]) * sij;
+    const double g = 0.5 * (G[i * m + j] + G[j * m + i]) * sij;
+    F[i * m + j] = f;
+    F[j * m + i] = f;
+    G[i * m + j] = g;
+    G[j * m + i] = g;
+  }
+  __syncthreads();
+  // 2. Cholesky F' = L L^T (lower part of F)
+  for (int j = 0; j < m; ++j) {
+    if (t == 0) {
+      double s = F[j * m + j];
+      for (int p = 0; p < j; ++p) s -= F[j * m + p] * F[j * m + p];
+      if (!(s > 1e-14) || !isfinite(s)) {
+        s_fail = 1;
+        s = 1.0;
+      }
+      F[j * m + j] = sqrt(s);
+    }
+    __syncthreads();
+    const double ljj = F[j * m + j];
+    for (int i = j + 1 + t; i < m; i += blockDim.x) {
+      double s = F[i * m + j];
+      for (int p = 0; p < j; ++p) s -= F[i * m + p] * F[j * m + p];
+      F[i * m + j] = s / ljj;
+    }
+    __syncthreads();
+  }
+  if (s_fail) {
+    if (t == 0) {
+      *a.status = DCG_ERR_SUBSPACE_SINGULAR;
+      *a.k_out = 0;
+    }
+    return;
+  }
+  // 3. Y = L^{-1} G' (forward substitution, one column of G' per thread)
+  for (int c = t; c < m; c += blockDim.x) {
+    for (int i = 0; i < m; ++i) {
+      double s = G[i * m + c];
+      for (int j = 0; j < i; ++j) s -= F[i * m + j] * G[j * m + c];
+      G[i * m + c] = s / F[i * m + i];
+    }
+  }
+  __syncthreads();
+  // 4. C = L^{-1} Y^T (Y^T = G' L^{-T}, so C = L^{-1} G' L^{-T}); row c of Y
+  //    is solved per thread; C written to shared memory in float32.
+  //    Column c of C solves L x = (row c of Y)^T.
+  double* Xc = a.Vd;  // m x m scratch (column-major by c)
+  for (int c = t; c < m; c += blockDim.x) {
+    for (int i = 0; i < m; ++i) {
+      double s = G[c * m + i];
+      for (int j = 0; j < i; ++j) s -= F[i * m + j] * Xc[int64_t(c) * m + j];
+      Xc[int64_t(c) * m + i] = s / F[i * m + i];
+    }
+  }
+  __syncthreads();
+  for (int idx = t; idx < m * m; idx += blockDim.x) {
+    const int i = idx / m, j = idx % m;
+    C[i * m + j] = float(0.5 * (Xc[int64_t(j) * m + i] + Xc[int64_t(i) * m + j]));
+  }
+  // V = I
+  float* V = a.Vj;
+  for (int idx = t; idx < m * m; idx += blockDim.x) V[idx] = (idx / m == idx % m) ? 1.f : 0.f;
+  __syncthreads();
+
+  // 5. cyclic Jacobi (circle-method ordering; rotations of disjoint pairs applied together)
+  const int m2 = (m + 1) & ~1;
+  const int half = m2 / 2;
+  for (int sweep = 0; sweep < EIG_MAX_SWEEPS; ++sweep) {
+    if (t == 0) s_changed = 0;
+    __syncthreads();
+    for (int r = 0; r < m2 - 1; ++r) {
+      if (t < half) {
+        int p, q;
+        jacobi_pair(m2, r, t, p, q);
+        if (p > q) {
+          const int tmp = p;
+          p = q;
+          q = tmp;
+        }
+        float c = 1.f, s = 0.f;
+        if (q < m) {
+          const float apq = C[p * m + q];
+          const float app = C[p * m + p], aqq = C[q * m + q];
+          if (fabsf(apq) > 4e-7f * sqrtf(fabsf(app * aqq)) && apq != 0.f) {
+            const float tau = (aqq - app) / (2.f * apq);
+            const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = rsqrtf(1.f + tt * tt);
+            s = tt * c;
+            s_changed = 1;
+          }
+        }
+        pp[t] = p;
+        qq[t] = q;
+        cs_c[t] = c;
+        cs_s[t] = s;
+      }
+      __syncthreads();
+      // rows p, q of C  <- J^T C
+      for (int idx = t; idx < half * m; idx += blockDim.x) {
+        const int pr = idx / m, j = idx % m;
+        const int p = pp[pr], q = qq[pr];
+        if (q >= m || cs_s[pr] == 0.f) continue;
+        const float c = cs_c[pr], s = cs_s[pr];
+        const float a_p = C[p * m + j], a_q = C[q * m + j];
+        C[p * m + j] = c * a_p - s * a_q;
+        C[q * m + j] = s * a_p + c * a_q;
+      }
+      __syncthreads();
+      // columns p, q of C and V  <- C J, V J
+      for (int idx = t; idx < half * m; idx += blockDim.x) {
+        const int pr = idx / m, i = idx % m;
+        const int p = pp[pr], q = qq[pr];
+        if (q >= m || cs_s[pr] == 0.f) continue;
+        const float c = cs_c[pr], s = cs_s[pr];
+        const float a_p = C[i * m + p], a_q = C[i * m + q];
+        C[i * m + p] = c * a_p - s * a_q;
+        C[i * m + q] = s * a_p + c * a_q;
+        const float v_p = V[i * m + p], v_q = V[i * m + q];
+        V[i * m + p] = c * v_p - s * v_q;
+        V[i * m + q] = s * v_p + c * v_q;
+      }
+      __syncthreads();
+    }
+    if (!s_changed) break;
+  }
+  // 6. order the values (descending, ties by lower index) and select
+  for (int i = t; i < m; i += blockDim.x) th[i] = C[i * m + i];
+  __syncthreads();
+  for (int i = t; i < m; i += blockDim.x) {
+    int rk = 0;
+    for (int j = 0; j < m; ++j) rk += (th[j] > th[i]) || (th[j] == th[i] && j < i);
+    rank_of[i] = rk;
+    a.theta[rk] = double(th[i]);
+  }
+  __syncthreads();
+  // 7. U[:, c] = S L^{-T} v_sel(c): back substitution L^T y = v, then scale
+  for (int c = t; c < k_new; c += blockDim.x) {
+    int sel = -1;
+    const int want = (a.select == DCG_SELECT_SMALLEST) ? (m - 1 - c) : c;
+    for (int i = 0; i < m; ++i)
+      if (rank_of[i] == want) sel = i;
+    double* y = Xc + int64_t(c) * m;
+    for (int i = m - 1; i >= 0; --i) {
+      double s = double(V[i * m + sel]);
+      for (int j = i + 1; j < m; ++j) s -= F[j * m + i] * y[j];
+      y[i] = s / F[i * m + i];
+    }
+    for (int i = 0; i < m; ++i) a.U[int64_t(c) * m + i] = float(scale[i] * y[i]);
+  }
+  if (t == 0) {
+    *a.status = DCG_OK;
+    *a.k_out = k_new;
+  }
+}
+
+// W_out[:, c] = Z U[:, c] for c < k_new (Z = [W | P]); thread per row, 32
+// output columns per pass.
+__global__ void __launch_bounds__(256) k_zu(RitzArgs a, int m, int k_new) {
+  extern __shared__ float Us[];  // m x 32
+  if (*a.status != DCG_OK) return;
+  const int n = a.n;
+  for (int c0 = 0; c0 < k_new; c0 += 32) {
+    const int cw = min(32, k_new - c0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < m * 32; idx += blockDim.x) {
+      const int i = idx / 32, c = idx % 32;
+      Us[idx] = c < cw ? a.U[int64_t(c0 + c) * m + i] : 0.f;
+    }
+    __syncthreads();
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+      float acc[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+      for (int i = 0; i < m; ++i) {
+        const float z = gram_col(a.W, a.k_act, a.P, i, n)[row];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = fmaf(z, Us[i * 32 + c], acc[c]);
+      }
+      for (int c = 0; c < cw; ++c) a.Wout[int64_t(c0 + c) * n + row] = acc[c];
+    }
+  }
+}
+
+// Column norm and sign pivot (largest magnitude, lowest index) of W_out[:, c].
+__global__ void __launch_bounds__(256) k_colnorm(RitzArgs a) {
+  if (*a.status != DCG_OK) return;
+  const int c = blockIdx.x, n = a.n;
+  const float* col = a.Wout + int64_t(c) * n;
+  double ss = 0.0;
+  float best = -1.f;
+  int bi = 0x7fffffff;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float v = col[i];
+    ss += double(v) * double(v);
+    const float av = fabsf(v);
+    if (av > best || (av == best && i < bi)) {
+      best = av;
+      bi = i;
+    }
+  }
+  __shared__ double s_ss[256];
+  __shared__ float s_b[256];
+  __shared__ int s_i[256];
+  s_ss[threadIdx.x] = ss;
+  s_b[threadIdx.x] = best;
+  s_i[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s_ss[threadIdx.x] += s_ss[threadIdx.x + o];
+      const float b2 = s_b[threadIdx.x + o];
+      const int i2 = s_i[threadIdx.x + o];
+      if (b2 > s_b[threadIdx.x] || (b2 == s_b[threadIdx.x] && i2 < s_i[threadIdx.x])) {
+        s_b[threadIdx.x] = b2;
+        s_i[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double nrm = sqrt(s_ss[0]);
+    const double sgn = col[s_i[0]] < 0.f ? -1.0 : 1.0;
+    a.colscale[c] = nrm > 0.0 ? sgn / nrm : 0.0;
+  }
+}
+
+// W (columns 1.. of XW) <- W_out * colscale
+__global__ void __launch_bounds__(256) k_colscale(RitzArgs a, float* dstW, int k_new) {
+  if (*a.status != DCG_OK) return;
+  const int n = a.n;
+  const int64_t total = int64_t(n) * k_new;
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(idx / n);
+    dstW[idx] = float(double(a.Wout[idx]) * a.colscale[c]);
+  }
+}
+
+cudaError_t ritz_configure() {
+  const int smem = kMaxM * kMaxM * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_ritz_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_zu, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxM * 32 * 4);
+}
+
+cudaError_t launch_ritz(const RitzArgs& a, int num_sms, float* dstW, cudaStream_t s) {
+  const int m = a.k_act + a.nstored;
+  const int k_new = min(a.k_want, m);
+  if (m == 0 || k_new == 0) return cudaSuccess;
+  GramArgs g{};
+  g.n = a.n;
+  // F = Z^T (AZ)
+  g.a1 = a.W; g.ka1 = a.k_act; g.a2 = a.P; g.ka2 = a.nstored;
+  g.b1 = a.AW; g.kb1 = a.k_act; g.b2 = a.Q; g.kb2 = a.nstored;
+  g.part = a.part;
+  cudaError_t e = launch_gram(g, m, m, num_sms, a.F, nullptr, s);
+  if (e != cudaSuccess) return e;
+  // G = (AZ)^T (AZ)
+  g.a1 = a.AW; g.ka1 = a.k_act; g.a2 = a.Q; g.ka2 = a.nstored;
+  e = launch_gram(g, m, m, num_sms, a.G, nullptr, s);
+  if (e != cudaSuccess) return e;
+  k_ritz_eig<<<1, EIG_THREADS, size_t(m) * m * sizeof(float), s>>>(a, m, k_new);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_zu<<<num_sms, 256, size_t(m) * 32 * sizeof(float), s>>>(a, m, k_new);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_colnorm<<<k_new, 256, 0, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_colscale<<<num_sms * 2, 256, 0, s>>>(a, dstW, k_new);
+  return cudaGetLastError();
+}
+
+}  // namespace dcg

@@ -1,0 +1,192 @@
+"""Python face of the deflated-CG library: torch tensors supply device memory
+and the stream; every step of the solve runs in the library's CUDA kernels.
+
+Method: Algorithm 1 (def-CG(k, ell)) with harmonic-Ritz recycling (Sec. 2.3,
+Eq. 7) of de Roos & Hennig, arXiv 1706.00241.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dev_f32(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+class DefCG:
+    """A def-CG(k, ell) solver context for systems of size n on the current GPU.
+
+    Parameters follow ``dcg_config`` in include/dcg.h: ``window`` is "last" or
+    "first" (Algorithm 1 line 13), ``select`` "largest" or "smallest"
+    (Sec. 2.3), ``refine_every`` the residual-replacement period (0 = only the
+    final true-residual confirmation).
+    """
+
+    def __init__(self, n: int, k: int, ell: int, tol: float, max_iter: int | None = None,
+                 window: str = "last", select: str = "largest", refine_every: int = 0,
+                 warm_start: bool = False, reproject: bool = False,
+                 record_history: bool = False, stream=None):
+        self.lib = _lib.load()
+        self.n, self.k, self.ell = int(n), int(k), int(ell)
+        cfg = _lib.DcgConfig()
+        cfg.n = self.n
+        cfg.k = self.k
+        cfg.ell = self.ell
+        cfg.window = _lib.WINDOW[window]
+        cfg.select = _lib.SELECT[select]
+        cfg.refine_every = int(refine_every)
+        cfg.max_iter = int(max_iter if max_iter is not None else 10 * self.n)
+        cfg.warm_start = int(bool(warm_start))
+        cfg.reproject = int(bool(reproject))
+        cfg.record_history = int(bool(record_history))
+        cfg.tol = float(tol)
+        self.cfg = cfg
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._ctx = ctypes.c_void_p()
+        st = self.lib.dcg_create(ctypes.byref(cfg), ctypes.c_void_p(_stream_handle(self.stream)),
+                                 ctypes.byref(self._ctx))
+        _lib.check(st, None, "dcg_create")
+        self._op_ref = None
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self.lib.dcg_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st, what):
+        _lib.check(st, self._ctx, what)
+
+    # -- operators ----------------------------------------------------------
+    def set_operator_dense(self, A: torch.Tensor, lda: int | None = None):
+        """Borrow a stored row-major float32 operator (n x n, or n x lda)."""
+        _dev_f32(A, "A")
+        lda = A.shape[1] if lda is None else lda
+        self._op_ref = A
+        self._check(self.lib.dcg_set_operator_dense(self._ctx, ctypes.c_void_p(A.data_ptr()), lda),
+                    "dcg_set_operator_dense")
+
+    # -- solve --------------------------------------------------------------
+    def solve(self, b: torch.Tensor, x: torch.Tensor | None = None, raise_on_error: bool = True):
+        """Runs Algorithm 1 on (A, b); returns (x, info dict)."""
+        _dev_f32(b, "b")
+        if x is None:
+            x = torch.zeros_like(b)
+        _dev_f32(x, "x")
+        info = _lib.DcgSolveInfo()
+        st = self.lib.dcg_solve(self._ctx, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                ctypes.byref(info))
+        d = info.as_dict()
+        d["status_name"] = _lib.STATUS_NAMES.get(st, str(st))
+        if raise_on_error and st not in (_lib.DCG_OK,):
+            self._check(st, "dcg_solve")
+        return x, d
+
+    def update_subspace(self) -> int:
+        """Harmonic-Ritz extraction of the next W (Sec. 2.3); returns its width."""
+        k = ctypes.c_int32(0)
+        self._check(self.lib.dcg_update_subspace(self._ctx, ctypes.byref(k)), "dcg_update_subspace")
+        return k.value
+
+    def ritz_values(self) -> np.ndarray:
+        m = ctypes.c_int32(0)
+        self._check(self.lib.dcg_get_ritz_values(self._ctx, None, 0, ctypes.byref(m)), "dcg_get_ritz_values")
+        out = np.zeros(max(m.value, 1), dtype=np.float64)
+        if m.value:
+            self._check(self.lib.dcg_get_ritz_values(
+                self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), m.value, ctypes.byref(m)),
+                "dcg_get_ritz_values")
+        return out[:m.value]
+
+    def get_subspace(self) -> torch.Tensor:
+        """Current W as a (k_active, n) tensor (row j is column j of W)."""
+        k = ctypes.c_int32(0)
+        self._check(self.lib.dcg_get_subspace(self._ctx, None, ctypes.byref(k)), "dcg_get_subspace")
+        W = torch.empty((max(k.value, 0), self.n), dtype=torch.float32, device="cuda")
+        if k.value:
+            self._check(self.lib.dcg_get_subspace(self._ctx, ctypes.c_void_p(W.data_ptr()), ctypes.byref(k)),
+                        "dcg_get_subspace")
+        return W
+
+    def set_subspace(self, W: torch.Tensor):
+        """Sets W from a (k, n) tensor (row j is column j of W)."""
+        _dev_f32(W, "W")
+        k = W.shape[0] if W.dim() == 2 else 0
+        self._check(self.lib.dcg_set_subspace(self._ctx, ctypes.c_void_p(W.data_ptr() if k else 0), k),
+                    "dcg_set_subspace")
+
+    def history(self) -> np.ndarray:
+        cnt = ctypes.c_int32(0)
+        self._check(self.lib.dcg_get_history(self._ctx, None, 0, ctypes.byref(cnt)), "dcg_get_history")
+        out = np.zeros(max(cnt.value, 1), dtype=np.float64)
+        self._check(self.lib.dcg_get_history(self._ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             cnt.value, ctypes.byref(cnt)), "dcg_get_history")
+        return out[:cnt.value]
+
+    # -- single steps -------------------------------------------------------
+    def matvec(self, p: torch.Tensor, q: torch.Tensor | None = None, want_pAp: bool = True):
+        """q = A p with the fused p^T q (Algorithm 1 line 6)."""
+        _dev_f32(p, "p")
+        if q is None:
+            q = torch.empty_like(p)
+        d = ctypes.c_double(0.0)
+        self._check(self.lib.dcg_matvec(self._ctx, ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(q.data_ptr()),
+                                        ctypes.byref(d) if want_pAp else None), "dcg_matvec")
+        return q, (d.value if want_pAp else None)
+
+    def apply_block(self, V: torch.Tensor, Y: torch.Tensor | None = None) -> torch.Tensor:
+        """Y = A V for a (c, n) tensor V (row j is column j), in one pass over A."""
+        _dev_f32(V, "V")
+        if Y is None:
+            Y = torch.empty_like(V)
+        self._check(self.lib.dcg_apply_block(self._ctx, ctypes.c_void_p(V.data_ptr()), V.shape[0],
+                                             ctypes.c_void_p(Y.data_ptr())), "dcg_apply_block")
+        return Y
+
+    def sync(self):
+        self._check(self.lib.dcg_sync(self._ctx), "dcg_sync")
+
+
+def form_rbf_dense(X: torch.Tensor, lengthscale: float, signal_var: float, noise: float,
+                   out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """A = s^2 exp(-|x_i - x_j|^2 / (2 l^2)) + noise I as a dense float32 matrix (Sec. 3)."""
+    lib = _lib.load()
+    _dev_f32(X, "X")
+    n, d = X.shape
+    if out is None:
+        out = torch.empty((n, n), dtype=torch.float32, device=X.device)
+    st = lib.dcg_form_rbf_dense(ctypes.c_void_p(X.data_ptr()), n, d, float(lengthscale), float(signal_var),
+                                float(noise), ctypes.c_void_p(out.data_ptr()), out.shape[1],
+                                ctypes.c_void_p(_stream_handle(stream)))
+    _lib.check(st, None, "dcg_form_rbf_dense")
+    return out

@@ -1,0 +1,74 @@
+"""CPU checks of the boundary: the library builds, loads, and exports every
+entry point include/dcg.h declares; the binding declares each of them."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\**(dcg_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1706_00241_gb300 import build
+    return build.build()
+
+
+def test_header_declares_core_calls():
+    names = _declared()
+    for core in ("dcg_create", "dcg_solve", "dcg_update_subspace", "dcg_destroy",
+                 "dcg_set_operator_dense", "dcg_set_subspace", "dcg_get_subspace"):
+        assert core in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header(lib_path):
+    from paper_1706_00241_gb300 import _lib
+    assert set(_lib.SIGNATURES) == _declared()
+    lib = _lib.load()
+    assert lib.dcg_status_string(0) == b"ok"
+    assert b"breakdown" in lib.dcg_status_string(4)
+
+
+def test_config_struct_layout():
+    from paper_1706_00241_gb300 import _lib
+    # int64 n, nine int32 fields, int32 reserved[7], then a double: 8 + 64 + 8
+    assert ctypes.sizeof(_lib.DcgConfig) == 80
+    assert _lib.DcgConfig.tol.offset == 72
+    assert ctypes.sizeof(_lib.DcgSolveInfo) == 64
+
+
+def test_create_rejects_bad_config_without_gpu(lib_path):
+    # argument validation happens before any CUDA call
+    from paper_1706_00241_gb300 import _lib
+    lib = _lib.load()
+    cfg = _lib.DcgConfig()
+    cfg.n = 0
+    cfg.max_iter = 10
+    cfg.tol = 1e-6
+    ctx = ctypes.c_void_p()
+    assert lib.dcg_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) == 1
+    assert b"n out of range" in lib.dcg_last_error(None)
+    cfg.n = 10
+    cfg.tol = 0.0
+    assert lib.dcg_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) == 1
+    cfg.tol = 1e-6
+    cfg.k = 200
+    assert lib.dcg_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) in (1, 9)

@@ -1,0 +1,346 @@
+"""GPU parity of the stored-operator path against the FP64 oracle.
+
+Every test calls the CUDA path through the C ABI (paper_1706_00241_gb300 is a
+ctypes binding) and compares with ``oracle/`` on the same seeded inputs from
+``dcg_synth``. Tolerances are stated per test with the arithmetic behind them.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import dcg_synth as S
+from oracle import dcg_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def dcg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1706_00241_gb300 import build
+    build.build()
+    import paper_1706_00241_gb300 as P
+    return P
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+def padded(A32, lda):
+    n = A32.shape[0]
+    out = np.zeros((n, lda), dtype=np.float32)
+    out[:, :n] = A32
+    return out
+
+
+def rbf_problem(n, d, l, noise, seed=0):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    return X
+
+
+# ---------------------------------------------------------------------------
+# A1: forming the RBF operator
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,d", [(1, 3), (67, 5), (1000, 8), (1030, 16)])
+def test_form_rbf_matches_oracle(dcg, n, d):
+    X = rbf_problem(n, d, 1.0, 1e-2)
+    l, s2, noise = 1.3, 0.9, 1e-2
+    lda = (n + 3) // 4 * 4
+    A = torch.zeros((n, lda), dtype=torch.float32, device="cuda")
+    dcg.form_rbf_dense(dev(X), l, s2, noise, out=A)
+    torch.cuda.synchronize()
+    got = A.cpu().numpy()[:, :n].astype(np.float64)
+    ref = O.rbf_gram(X.astype(np.float64), l, s2, noise)
+    # float32 distances (d terms) and expf: a few ulp of the entry plus the
+    # float32 rounding of |x_i - x_j|^2 amplified by |dK/d(sq)| = K / (2 l^2)
+    sq_scale = 4.0 * np.max(np.sum(X.astype(np.float64) ** 2, axis=1))
+    tol = 1e-6 * np.abs(ref) + 4e-7 * sq_scale / (2 * l * l) * np.abs(ref) + 1e-7
+    assert np.all(np.abs(got - ref) <= tol)
+
+
+# ---------------------------------------------------------------------------
+# A5: the matvec q = A p with the fused p^T A p
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 5, 257, 1001, 2049, 4099, 9000])
+def test_matvec_matches_oracle(dcg, n):
+    rng = np.random.default_rng(n)
+    lda = (n + 3) // 4 * 4
+    A32 = rng.standard_normal((n, n)).astype(np.float32)
+    A32 = (A32 + A32.T) * 0.5
+    p = rng.standard_normal(n).astype(np.float32)
+    Ad = dev(padded(A32, lda))
+    with dcg.DefCG(n, 0, 0, 1e-6) as s:
+        s.set_operator_dense(Ad, lda)
+        q, pAp = s.matvec(dev(p))
+        q = q.cpu().numpy().astype(np.float64)
+    A64, p64 = A32.astype(np.float64), p.astype(np.float64)
+    ref = A64 @ p64
+    # float32 products summed in float32 over <= n/512 + 8 terms per thread,
+    # then a 256-way tree: error <= (n/512 + 16) * eps32 * sum_j |a_ij p_j|
+    bound = (n / 512 + 16) * 6e-8 * (np.abs(A64) @ np.abs(p64))
+    assert np.all(np.abs(q - ref) <= bound + 1e-30)
+    # p^T q is summed in float64 from the float32 q the kernel stored
+    assert abs(pAp - p64 @ q) <= 1e-12 * (np.abs(p64) @ np.abs(q))
+
+
+def test_matvec_full_size_sampled_rows(dcg):
+    # BASELINE size 16384 in the bench launch configuration; rows sampled so the
+    # float64 reference is cheap.
+    cfg = S.DENSE_16384
+    X, bs = S.draw_sequence(cfg, T=1)
+    X32 = X.astype(np.float32)
+    n = cfg.n
+    A = dcg.form_rbf_dense(dev(X32), cfg.lengthscale(19), 1.0, cfg.noise)
+    p = bs[0].astype(np.float32)
+    with dcg.DefCG(n, cfg.k, cfg.ell, cfg.tol) as s:
+        s.set_operator_dense(A)
+        q, pAp = s.matvec(dev(p))
+    rows = np.random.default_rng(1).choice(n, 96, replace=False)
+    Arows = A[torch.tensor(rows, device="cuda")].cpu().numpy().astype(np.float64)
+    ref = Arows @ p.astype(np.float64)
+    got = q.cpu().numpy()[rows].astype(np.float64)
+    bound = (n / 512 + 16) * 6e-8 * (np.abs(Arows) @ np.abs(p.astype(np.float64)))
+    assert np.all(np.abs(got - ref) <= bound)
+    qq = q.cpu().numpy().astype(np.float64)
+    assert abs(pAp - p.astype(np.float64) @ qq) <= 1e-12 * (np.abs(p) @ np.abs(qq))
+
+
+# ---------------------------------------------------------------------------
+# A2: multi-vector product Y = A V
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,c", [(5, 1), (1001, 7), (2048, 33), (3001, 65), (700, 129)])
+def test_apply_block_matches_oracle(dcg, n, c):
+    rng = np.random.default_rng(c)
+    lda = (n + 3) // 4 * 4
+    A32 = rng.standard_normal((n, n)).astype(np.float32)
+    V = rng.standard_normal((c, n)).astype(np.float32)    # row j = column j of V
+    with dcg.DefCG(n, 0, 0, 1e-6) as s:
+        s.set_operator_dense(dev(padded(A32, lda)), lda)
+        Y = s.apply_block(dev(V)).cpu().numpy().astype(np.float64)
+    ref = V.astype(np.float64) @ A32.astype(np.float64).T
+    bound = (n / 32 + 32) * 6e-8 * (np.abs(V.astype(np.float64)) @ np.abs(A32.astype(np.float64)).T)
+    assert np.all(np.abs(Y - ref) <= bound)
+
+
+# ---------------------------------------------------------------------------
+# A3-A8: solves
+# ---------------------------------------------------------------------------
+def _spd32(n, eigs_lo, eigs_hi, seed):
+    eigs = np.geomspace(eigs_lo, eigs_hi, n)
+    A, Q = S.spd_with_spectrum(eigs, seed=seed)
+    return A.astype(np.float32), Q, eigs
+
+
+@pytest.mark.parametrize("n,k", [(1001, 0), (1001, 8), (2050, 16)])
+def test_solve_well_conditioned_matches_oracle(dcg, n, k):
+    # kappa = 10: |x - x*| / |x*| <= kappa * relres, so relres <= 1e-6 on both
+    # sides bounds the solution difference by ~2e-5; tol = 1e-7 gives margin
+    # for the 1e-5 solution-error target.
+    A32, _, _ = _spd32(n, 1.0, 10.0, seed=n + k)
+    A64 = A32.astype(np.float64)
+    rng = np.random.default_rng(k)
+    b = rng.standard_normal(n).astype(np.float32)
+    W = rng.standard_normal((k, n)).astype(np.float32)
+    lda = (n + 3) // 4 * 4
+    tol = 1e-6
+    with dcg.DefCG(n, max(k, 1), 16, tol, record_history=True) as s:
+        s.set_operator_dense(dev(padded(A32, lda)), lda)
+        if k:
+            s.set_subspace(dev(W))
+        x, info = s.solve(dev(b))
+        hist = s.history()
+    x = x.cpu().numpy().astype(np.float64)
+    ref = O.defcg(A64, b.astype(np.float64), W=W.T.astype(np.float64) if k else None, tol=tol)
+    assert info["status"] == 0
+    relres = np.linalg.norm(b - A64 @ x) / np.linalg.norm(b)
+    assert relres <= tol * 1.001
+    assert abs(info["relres_true"] - relres) <= 1e-3 * relres + 1e-12
+    assert abs(info["iters"] - ref.iters) <= 2
+    assert np.linalg.norm(x - ref.x) <= 1e-5 * np.linalg.norm(ref.x)
+    assert info["matvecs_setup"] == k
+    # the recursive residual history follows the oracle's while rounding is small
+    m = min(len(hist), len(ref.history), 8)
+    np.testing.assert_allclose(hist[:m], ref.history[:m], rtol=1e-4)
+
+
+def test_exact_eigenvectors_deflate(dcg):
+    # W = exact eigenvectors of the 8 largest eigenvalues: the iteration count is
+    # that of CG on the remaining spectrum (pinned in the oracle), within 2.
+    n = 1500
+    eigs = np.concatenate([np.linspace(1.0, 5.0, n - 8), np.geomspace(100.0, 1000.0, 8)])
+    A, Q = S.spd_with_spectrum(eigs, seed=4)
+    A32 = A.astype(np.float32)
+    b = np.random.default_rng(3).standard_normal(n).astype(np.float32)
+    W = Q[:, -8:].T.astype(np.float32)
+    with dcg.DefCG(n, 8, 0, 1e-6) as s:
+        s.set_operator_dense(dev(A32))
+        s.set_subspace(dev(W))
+        x, info = s.solve(dev(b))
+    ref = O.defcg(A32.astype(np.float64), b.astype(np.float64), W=W.T.astype(np.float64), tol=1e-6)
+    plain = O.cg(A32.astype(np.float64), b.astype(np.float64), tol=1e-6)
+    assert abs(info["iters"] - ref.iters) <= 2
+    assert info["iters"] < plain.iters
+
+
+def test_zero_rhs(dcg):
+    n = 300
+    A32, _, _ = _spd32(n, 1, 10, 1)
+    with dcg.DefCG(n, 4, 8, 1e-6, warm_start=True) as s:
+        s.set_operator_dense(dev(A32))
+        x0 = torch.ones(n, device="cuda")
+        x, info = s.solve(torch.zeros(n, device="cuda"), x0)
+    assert info["status"] == 0 and info["iters"] == 0
+    assert torch.count_nonzero(x).item() == 0
+
+
+def test_breakdown_on_indefinite(dcg):
+    n = 64
+    eigs = np.concatenate([[-1.0], np.linspace(1, 3, n - 1)])
+    A, Q = S.spd_with_spectrum(eigs, seed=2)
+    with dcg.DefCG(n, 0, 0, 1e-8) as s:
+        s.set_operator_dense(dev(A.astype(np.float32)))
+        x, info = s.solve(dev(Q[:, 0]), raise_on_error=False)
+    assert info["status"] == 4
+
+
+def test_maxiter_reports_true_residual(dcg):
+    n = 800
+    A32, _, _ = _spd32(n, 1e-3, 10, 5)
+    b = np.random.default_rng(0).standard_normal(n).astype(np.float32)
+    with dcg.DefCG(n, 0, 0, 1e-10, max_iter=5) as s:
+        s.set_operator_dense(dev(A32))
+        x, info = s.solve(dev(b), raise_on_error=False)
+    assert info["status"] == 6 and info["iters"] == 5
+    x = x.cpu().numpy().astype(np.float64)
+    rr = np.linalg.norm(b - A32.astype(np.float64) @ x) / np.linalg.norm(b)
+    assert abs(info["relres_true"] - rr) <= 1e-4 * rr
+
+
+def test_warm_start_matches_oracle(dcg):
+    n = 1200
+    A32, _, _ = _spd32(n, 1, 10, 9)
+    rng = np.random.default_rng(9)
+    b = rng.standard_normal(n).astype(np.float32)
+    x0 = rng.standard_normal(n).astype(np.float32)
+    W = rng.standard_normal((4, n)).astype(np.float32)
+    with dcg.DefCG(n, 4, 0, 1e-6, warm_start=True) as s:
+        s.set_operator_dense(dev(A32))
+        s.set_subspace(dev(W))
+        x, info = s.solve(dev(b), dev(x0))
+    ref = O.defcg(A32.astype(np.float64), b.astype(np.float64), x_init=x0.astype(np.float64),
+                  W=W.T.astype(np.float64), tol=1e-6)
+    assert info["matvecs_setup"] == 5
+    assert abs(info["iters"] - ref.iters) <= 2
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-5 * np.linalg.norm(ref.x)
+
+
+def test_refinement_every_m(dcg):
+    n = 1000
+    A32, _, _ = _spd32(n, 1e-2, 10, 11)
+    b = np.random.default_rng(2).standard_normal(n).astype(np.float32)
+    rng = np.random.default_rng(5)
+    W = rng.standard_normal((6, n)).astype(np.float32)
+    with dcg.DefCG(n, 6, 0, 1e-6, refine_every=10) as s:
+        s.set_operator_dense(dev(A32))
+        s.set_subspace(dev(W))
+        x, info = s.solve(dev(b))
+    ref = O.defcg(A32.astype(np.float64), b.astype(np.float64), W=W.T.astype(np.float64), tol=1e-6,
+                  refine_every=10)
+    assert info["status"] == 0
+    assert info["matvecs_check"] >= info["iters"] // 10
+    assert abs(info["iters"] - ref.iters) <= 2
+    xx = x.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(b - A32.astype(np.float64) @ xx) / np.linalg.norm(b) <= 1e-6
+
+
+# ---------------------------------------------------------------------------
+# A9: harmonic Ritz extraction
+# ---------------------------------------------------------------------------
+def test_ritz_keeps_exact_invariant_subspace(dcg):
+    # W spans the top-6 eigenvectors; the extraction from Z = [W, P] must return
+    # those eigenvalues as the largest harmonic Ritz values (Eq. 7 is exact on
+    # an invariant subspace) and the same span.
+    n = 1024
+    eigs = np.concatenate([np.linspace(1.0, 4.0, n - 6), np.geomspace(50.0, 500.0, 6)])
+    A, Q = S.spd_with_spectrum(eigs, seed=8)
+    A32 = A.astype(np.float32)
+    b = np.random.default_rng(1).standard_normal(n).astype(np.float32)
+    R = np.random.default_rng(2).standard_normal((6, 6))
+    W = (Q[:, -6:] @ R).T.astype(np.float32)
+    with dcg.DefCG(n, 6, 12, 1e-6) as s:
+        s.set_operator_dense(dev(A32))
+        s.set_subspace(dev(W))
+        s.solve(dev(b))
+        k_new = s.update_subspace()
+        theta = s.ritz_values()
+        Wn = s.get_subspace().cpu().numpy().astype(np.float64)
+    assert k_new == 6
+    np.testing.assert_allclose(theta[:6], np.sort(eigs[-6:])[::-1], rtol=2e-5)
+    # span check: the principal angles between span(W_new) and span(Q_S)
+    qn, _ = np.linalg.qr(Wn.T)
+    s_vals = np.linalg.svd(Q[:, -6:].T @ qn, compute_uv=False)
+    assert s_vals.min() > 1 - 1e-6
+    np.testing.assert_allclose(np.linalg.norm(Wn, axis=1), 1.0, rtol=1e-5)
+    piv = np.argmax(np.abs(Wn), axis=1)
+    assert np.all(Wn[np.arange(6), piv] > 0)
+
+
+def test_ritz_first_window_matches_oracle(dcg):
+    # First system (plain CG) with window FIRST: the first ell directions span
+    # a Krylov space on which float32 and float64 agree closely.
+    n = 2000
+    A32, _, eigs = _spd32(n, 0.5, 200.0, 13)
+    b = np.random.default_rng(4).standard_normal(n).astype(np.float32)
+    with dcg.DefCG(n, 4, 10, 1e-6, window="first") as s:
+        s.set_operator_dense(dev(A32))
+        s.solve(dev(b))
+        s.update_subspace()
+        theta = s.ritz_values()
+    ref = O.defcg(A32.astype(np.float64), b.astype(np.float64), tol=1e-6, ell=10, window="first")
+    rr = O.harmonic_ritz(None, None, ref.P, ref.Q, 4)
+    np.testing.assert_allclose(theta, rr.theta, rtol=1e-3)
+
+
+def _sequence_gpu(dcg, cfg, T, tol, deflate=True, refine_every=0):
+    X, bs = S.draw_sequence(cfg, T=T)
+    Xd = dev(X.astype(np.float32))
+    n = cfg.n
+    out = []
+    with dcg.DefCG(n, cfg.k if deflate else 0, cfg.ell if deflate else 0, tol, refine_every=refine_every) as s:
+        A = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        for t in range(T):
+            dcg.form_rbf_dense(Xd, cfg.lengthscale(t), cfg.signal_var, cfg.noise, out=A)
+            s.set_operator_dense(A)
+            x, info = s.solve(dev(bs[t]))
+            if deflate:
+                s.update_subspace()
+                info["theta"] = s.ritz_values()[:8]
+            info["x"] = x.cpu().numpy()
+            out.append(info)
+    return out
+
+
+def test_sequence_small_matches_oracle_golden(dcg):
+    # n = 1024 sequence (5 systems), tol 1e-6, k = 8, ell = 32, window last.
+    g = json.load(open(os.path.join(HERE, "golden", "small_1024_tol1e-6_oracle.json")))
+    cfg = S.RBFSequence(**{**S.SMALL_1024.__dict__, "tol": 1e-6})
+    got = _sequence_gpu(dcg, cfg, cfg.T, 1e-6)
+    for info, ref in zip(got, g["systems"]):
+        assert info["status"] == 0
+        assert info["relres_true"] <= 1e-6
+        # float32 loses conjugacy earlier than float64 on these kappa ~ 1e3
+        # systems; iteration counts agree within 5 % (+2)
+        assert abs(info["iters"] - ref["defcg_iters"]) <= 2 + 0.05 * ref["defcg_iters"], (info["iters"], ref)
+        np.testing.assert_allclose(info["theta"][0], ref["theta_top"][0], rtol=1e-3)
+    plain = _sequence_gpu(dcg, cfg, cfg.T, 1e-6, deflate=False)
+    for t in range(1, cfg.T):
+        assert got[t]["iters"] < plain[t]["iters"]
