@@ -234,7 +234,7 @@ def gpu_arm(args):
     # pinned host memory, x_t back to pinned host memory, inside the timing
     Xh = torch.tensor(X32).pin_memory()
     bh = [torch.tensor(b).pin_memory() for b in b32]
-    xh = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(T)]
+    xh = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(T)]
     solver.set_subspace(torch.zeros((0, n), device="cuda"))
     torch.cuda.synchronize()
     w0 = time.perf_counter()
@@ -303,7 +303,7 @@ def gpu_arm(args):
         "e2e": {
             "value": e2e_s, "unit": "s/sequence",
             "h2d_bytes_per_step": int(X32.nbytes + T * n * 4),
-            "d2h_bytes_per_step": int(T * n * 4),
+            "d2h_bytes_per_step": int(T * n * 8),
         },
         "gpu_launches": launches_of(infos, True) * args.steps,
         "clocks": clk.summary(),

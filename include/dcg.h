@@ -91,7 +91,7 @@ typedef struct dcg_solve_info {
   int32_t stored;          /* directions stored for the next extraction           */
   int32_t reserved;
   double relres_recursive; /* |r_j| / |b| of the recursion at exit                */
-  double relres_true;      /* |b - A x| / |b| with float64 accumulation           */
+  double relres_true;      /* |b - A x| / |b|, compensated accumulation (see dcg_solve) */
   double ms_total;         /* device time of the whole solve (CUDA events)        */
   double ms_setup;         /* start-of-solve product, E and its factor, x_0, p_0  */
 } dcg_solve_info;
@@ -171,20 +171,25 @@ dcg_status dcg_form_rbf_dense(const float* X, int64_t n, int32_t d, double lengt
 
 /* dcg_solve: runs Deflated-CG(k, ell)(A, b, x_{-1}, W, AW, tol).
  *   b    device, n floats (read).
- *   x    device, n floats; in: x_{-1} if cfg.warm_start, else ignored;
- *        out: the solution (or the last iterate on error).
+ *   x    device, n doubles; in: x_{-1} if cfg.warm_start, else ignored;
+ *        out: the solution (or the last iterate on error). The iterate is
+ *        accumulated in float64 (x_{j+1} = x_j + alpha_j p_j with float32 p_j):
+ *        a float32 iterate cannot represent a solution below the residual floor
+ *        ~ eps32 |A| |x| / |b|, which exceeds 1e-6 on ill-conditioned systems.
  *   info host, may be NULL.
  * Steps (all on the device, one host synchronisation at the end):
- *   A [x_{-1} | W] in one pass; E = W^T (AW) in float64 and its Cholesky
- *   factor; x_0 = x_{-1} + W E^{-1} W^T r_{-1} (line 3); p_0 = r_0 - W mu_0
- *   (line 4); then the loop of lines 5-14 as a CUDA graph with a device-side
- *   while node. Stops when |r_j| <= tol |b|, confirmed by a true residual
- *   b - A x with float64 accumulation (replaced and continued if above tol).
+ *   A W in one pass; r_{-1} = b - A x_{-1} (warm start only); E = W^T (AW) in
+ *   float64 and its Cholesky factor; x_0 = x_{-1} + W E^{-1} W^T r_{-1}
+ *   (line 3); p_0 = r_0 - W mu_0 (line 4); then the loop of lines 5-14 as a
+ *   CUDA graph with a device-side while node. Stops when |r_j| <= tol |b|,
+ *   confirmed by a true residual b - A x evaluated with compensated (twice
+ *   float32 precision, Ogita-Rump-Oishi Dot2) accumulation and summed in
+ *   float64; if it is above tol |b| it replaces r and the loop continues.
  *   The last ell (or first ell) directions p_j and A p_j are kept for
  *   dcg_update_subspace.
  * Returns the solve status (also in info->status): OK, MAXITER, BREAKDOWN,
- * SUBSPACE_SINGULAR, STATE (no operator), INVALID_ARG, CUDA. */
-dcg_status dcg_solve(dcg_ctx* ctx, const float* b, float* x, dcg_solve_info* info);
+ * SUBSPACE_SINGULAR, TIMEOUT, STATE (no operator), INVALID_ARG, CUDA. */
+dcg_status dcg_solve(dcg_ctx* ctx, const float* b, double* x, dcg_solve_info* info);
 
 /* dcg_update_subspace: harmonic-Ritz extraction (Sec. 2.3, Eq. 7) from the
  * last solve: Z = [W, P], AZ = [AW, AP], F = Z^T AZ (symmetrised),

@@ -37,7 +37,7 @@ struct dcg_ctx {
   double* gramE_part = nullptr;
 
   // harmonic Ritz buffers
-  double *F = nullptr, *G = nullptr, *Vd = nullptr, *theta = nullptr, *ritz_part = nullptr, *colscale = nullptr;
+  double *F = nullptr, *G = nullptr, *Vd = nullptr, *Vd2 = nullptr, *theta = nullptr, *ritz_part = nullptr, *colscale = nullptr;
   float *Vj = nullptr, *U = nullptr, *Wout = nullptr;
   int *k_out = nullptr, *ritz_status = nullptr;
   int k_active = 0;
@@ -50,6 +50,9 @@ struct dcg_ctx {
   const float* A = nullptr;
   int64_t lda = 0;
   CUtensorMap tmap;
+
+  // split-K partials of the block product
+  float* block_scratch = nullptr;
 
   // standalone matvec scratch
   double* mv_partials = nullptr;
@@ -208,6 +211,9 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   w.tol = g.tol;
   CKC(dalloc(c, &w.XW, size_t(n) * (1 + kmax)));
   CKC(dalloc(c, &w.Y, size_t(n) * (1 + kmax)));
+  CKC(dalloc(c, &w.xd, size_t(n)));
+  CKC(dalloc(c, &w.xh, size_t(n)));
+  CKC(dalloc(c, &w.xl, size_t(n)));
   CKC(dalloc(c, &w.r, size_t(n)));
   CKC(dalloc(c, &w.p, size_t(n)));
   CKC(dalloc(c, &w.q, size_t(n)));
@@ -217,6 +223,10 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   const int kk = std::max(kmax, 1);
   CKC(dalloc(c, &w.E, size_t(kk) * kk));
   CKC(dalloc(c, &w.Linv, size_t(kk) * kk));
+  CKC(dalloc(c, &w.GW, size_t(kk) * kk));
+  CKC(dalloc(c, &w.Einv, size_t(kk) * kk));
+  CKC(dalloc(c, &w.N, size_t(kk) * kk));
+  CKC(dalloc(c, &w.M, size_t(kk) * kk));
   CKC(dalloc(c, &w.h, size_t(kk)));
   CKC(dalloc(c, &w.hp, size_t(kk)));
   CKC(dalloc(c, &w.mu, size_t(kk)));
@@ -234,15 +244,20 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   CKC(dalloc(c, &c->F, size_t(mm) * mm));
   CKC(dalloc(c, &c->G, size_t(mm) * mm));
   CKC(dalloc(c, &c->Vd, size_t(mm) * mm));
-  CKC(dalloc(c, &c->Vj, size_t(mm) * mm));
+  CKC(dalloc(c, &c->Vd2, size_t(mm) * mm));
+  CKC(dalloc(c, &c->Vj, size_t(mm) * (mm + 1)));
   CKC(dalloc(c, &c->theta, size_t(mm)));
   CKC(dalloc(c, &c->U, size_t(mm) * kk));
   CKC(dalloc(c, &c->Wout, size_t(n) * kk));
   CKC(dalloc(c, &c->colscale, size_t(kk)));
-  CKC(dalloc(c, &c->k_out, 1));
+  CKC(dalloc(c, &c->k_out, 2));
   CKC(dalloc(c, &c->ritz_status, 1));
   CKC(dalloc(c, &c->ritz_part, gram_partials_doubles(n, mm, c->num_sms)));
   CKC(dalloc(c, &c->mv_partials, size_t(c->grid_rows) + 1));
+  {
+    const size_t bs = apply_block_scratch_floats(n, kMaxBlockCols, c->num_sms);
+    if (bs) CKC(dalloc(c, &c->block_scratch, bs));
+  }
   CKC(dalloc(c, &c->mv_result, 1));
   CKC(dalloc(c, &c->mv_ticket, 1));
   CKC(cudaMallocHost(&c->h_st, sizeof(DevState)));
@@ -316,8 +331,11 @@ static cudaError_t op_matvec(dcg_ctx* c, const float* p, float* q, double* resul
 }
 
 static cudaError_t op_resid(dcg_ctx* c, int mode, int skip_if_done, cudaStream_t s) {
+  cudaError_t e = launch_split_x(c->w, c->grid_iter, skip_if_done, s);
+  if (e != cudaSuccess) return e;
   RowOpArgs a{};
-  a.v = c->w.XW;
+  a.xh = c->w.xh;
+  a.xl = c->w.xl;
   a.out = c->w.r;
   a.b = c->w.b;
   a.n = c->w.n;
@@ -340,7 +358,7 @@ static cudaError_t op_block(dcg_ctx* c, const float* V, int ncols, float* Y, Dev
   a.c = ncols;
   a.st = st;
   a.skip_if_done = st ? 1 : 0;
-  return launch_apply_block(a, st ? c->w.kmax + 1 : ncols, s);
+  return launch_apply_block(a, st ? c->w.kmax : ncols, c->block_scratch, c->num_sms, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -390,11 +408,14 @@ static dcg_status build_graph(dcg_ctx* c) {
   auto run = [&](cudaError_t r) {
     if (e == cudaSuccess) e = r;
   };
-  // Start of solve: A [x_{-1} | W], r_{-1}, E and its factor, x_0, p_0.
+  // Start of solve: AW, r_{-1} (warm start), E and its factor, x_0, p_0.
   run(op_block(c, w.XW, 0, w.Y, c->st, s0));
+  run(op_resid(c, 0, 1, s0));
   run(launch_setup_r(w, c->grid_iter, s0));
   run(launch_gram_E(w, c->gramE_part, c->num_sms, s0));
+  run(launch_gram_GW(w, c->gramE_part, c->num_sms, s0));
   run(launch_chol_E(w, s0));
+  run(launch_small_prods(w, s0));
   run(launch_check_dots(w, c->grid_iter, s0));
   run(launch_check_update(w, c->grid_iter, 0, 1, h, s0));
   run(launch_phase2_setup(w, c->grid_iter, s0));
@@ -448,7 +469,7 @@ static dcg_status build_graph(dcg_ctx* c) {
 // ---------------------------------------------------------------------------
 // Solve
 // ---------------------------------------------------------------------------
-extern "C" dcg_status dcg_solve(dcg_ctx* c, const float* b, float* x, dcg_solve_info* info) {
+extern "C" dcg_status dcg_solve(dcg_ctx* c, const float* b, double* x, dcg_solve_info* info) {
   if (!c) return DCG_ERR_INVALID_ARG;
   if (!b || !x) return fail(c, DCG_ERR_INVALID_ARG, "b and x must not be NULL");
   if (c->op == OP_NONE) return fail(c, DCG_ERR_STATE, "no operator set");
@@ -473,13 +494,13 @@ extern "C" dcg_status dcg_solve(dcg_ctx* c, const float* b, float* x, dcg_solve_
   CK(cudaMemcpyAsync(c->st, hs, sizeof(DevState), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->w.b, b, size_t(n) * 4, cudaMemcpyDeviceToDevice, s));
   if (c->cfg.warm_start)
-    CK(cudaMemcpyAsync(c->w.XW, x, size_t(n) * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->w.xd, x, size_t(n) * 8, cudaMemcpyDeviceToDevice, s));
   else
-    CK(cudaMemsetAsync(c->w.XW, 0, size_t(n) * 4, s));
+    CK(cudaMemsetAsync(c->w.xd, 0, size_t(n) * 8, s));
   CK(cudaEventRecord(c->ev0, s));
   CK(cudaGraphLaunch(c->exec, s));
   CK(cudaEventRecord(c->ev1, s));
-  CK(cudaMemcpyAsync(x, c->w.XW, size_t(n) * 4, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(x, c->w.xd, size_t(n) * 8, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(hs, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   float ms = 0.f;
@@ -536,6 +557,7 @@ extern "C" dcg_status dcg_update_subspace(dcg_ctx* c, int32_t* k_new) {
   a.part = c->ritz_part;
   a.Vj = c->Vj;
   a.Vd = c->Vd;
+  a.Vd2 = c->Vd2;
   a.theta = c->theta;
   a.U = c->U;
   a.Wout = c->Wout;
@@ -544,14 +566,17 @@ extern "C" dcg_status dcg_update_subspace(dcg_ctx* c, int32_t* k_new) {
   a.colscale = c->colscale;
   cudaStream_t s = c->stream;
   CK(launch_ritz(a, c->num_sms, c->w.XW + c->w.n, s));
-  CK(cudaMemcpyAsync(c->h_small, c->k_out, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(c->h_small + 1, c->ritz_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->h_small, c->k_out, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->h_small + 2, c->ritz_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   c->have_solve = false;
-  if (c->h_small[1] != DCG_OK) return fail(c, dcg_status(c->h_small[1]), "harmonic Ritz: F not positive definite");
+  if (c->h_small[2] != DCG_OK) {
+    c->m_last = 0;
+    return fail(c, dcg_status(c->h_small[2]), "harmonic Ritz: F not positive definite");
+  }
   knew = c->h_small[0];
   c->k_active = knew;
-  c->m_last = m;
+  c->m_last = c->h_small[1];
   if (k_new) *k_new = knew;
   return DCG_OK;
 }

@@ -7,15 +7,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/dcg.h"
+#include "dcg.h"  // include/ is on the include path
 
 namespace dcg {
 
-constexpr int kMaxK = 128;        // deflation vectors (columns of W)
+constexpr int kMaxK = 96;         // deflation vectors (columns of W)
 constexpr int kMaxEll = 128;      // stored directions
-constexpr int kMaxM = kMaxK + kMaxEll;
+constexpr int kMaxM = kMaxK + kMaxEll;  // 224: the float32 Jacobi matrix fits in 200 KB of shared memory
 constexpr int kMaxBlockCols = 129;  // columns of one multi-vector product
-constexpr int kReduceSlots = 2 * kMaxK + 8;  // per-CTA partial sums of one reduction
+constexpr int kReduceSlots = 3 * kMaxK + 8;  // per-CTA partial sums of one reduction
 constexpr long long kSpinLimit = 1ll << 22;  // bounded waits: polls before giving up
 
 // Ticket counters for the "last CTA finishes the reduction" pattern, one per

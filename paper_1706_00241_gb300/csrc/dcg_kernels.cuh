@@ -19,7 +19,10 @@ struct Ws {
   int n;
   int kmax;
   int ellmax;
-  float* XW;       // n x (1 + kmax)
+  float* XW;       // n x (1 + kmax); column 0 unused, W from column 1
+  double* xd;      // the iterate x, float64
+  float* xh;       // x split for the compensated residual: x = xh + xl
+  float* xl;
   float* Y;        // n x (1 + kmax)
   float* r;
   float* p;
@@ -29,6 +32,10 @@ struct Ws {
   float* Q;        // n x ellmax stored A p
   double* E;       // kmax x kmax, W^T A W
   double* Linv;    // kmax x kmax, inverse Cholesky factor of E (row-major, lower)
+  double* GW;      // kmax x kmax, (AW)^T (AW)
+  double* Einv;    // kmax x kmax, E^{-1}
+  double* N;       // kmax x kmax, G_W E^{-1}
+  double* M;       // kmax x kmax, E^{-1} G_W E^{-1}
   double* h;       // kmax: (AW)^T r
   double* hp;      // kmax: (AW)^T p
   double* mu;      // kmax
@@ -50,7 +57,9 @@ struct Handles {
 };
 
 struct RowOpArgs {
-  const float* v;        // p (matvec) or x (residual)
+  const float* v;        // p (matvec)
+  const float* xh;       // x (residual), high float32 part
+  const float* xl;       // x (residual), low float32 part
   float* out;            // q (matvec) or r (residual)
   const float* b;        // residual only
   int n;
@@ -59,7 +68,7 @@ struct RowOpArgs {
   double* result;        // matvec: p^T q; residual without state: |r|^2
   DevState* st;          // residual: updates rho_true etc.; may be null
   int skip_if_done;
-  int resid_mode;        // 1 check, 2 refinement, 3 final, -1: read st->mode
+  int resid_mode;        // 0 warm-start setup, 1 check, 2 refinement, 3 final, -1: read st->mode
 };
 
 struct ApplyBlockArgs {
@@ -69,7 +78,7 @@ struct ApplyBlockArgs {
   float* Y;
   int n;
   int c;
-  DevState* st;          // if set: c = k + warm_start, columns start at x or W
+  DevState* st;          // if set: c = st->k, V and Y point at column 0 (W starts at column 1)
   int skip_if_done;
 };
 
@@ -79,14 +88,17 @@ cudaError_t rowop_configure();
 int rowop_grid(int n, int num_sms);
 bool make_rowop_tmap(CUtensorMap* map, const float* A, int64_t n, int64_t lda, EncodeTiledFn encode);
 cudaError_t launch_rowop(const CUtensorMap* tmap, const RowOpArgs& a, bool resid, int grid, cudaStream_t s);
-cudaError_t launch_apply_block(const ApplyBlockArgs& a, int cmax, cudaStream_t s);
+cudaError_t launch_apply_block(const ApplyBlockArgs& a, int cmax, float* scratch, int num_sms, cudaStream_t s);
+size_t apply_block_scratch_floats(int n, int cmax, int num_sms);
 cudaError_t launch_form_rbf(const float* X, int n, int d, double l, double s2, double noise, float* A, int64_t lda,
                             cudaStream_t s);
 
 // ---- iteration kernels (k_iter.cu)
 cudaError_t launch_setup_r(const Ws& w, int grid, cudaStream_t s);
 cudaError_t launch_gram_E(const Ws& w, double* part, int num_sms, cudaStream_t s);
+cudaError_t launch_gram_GW(const Ws& w, double* part, int num_sms, cudaStream_t s);
 cudaError_t launch_chol_E(const Ws& w, cudaStream_t s);
+cudaError_t launch_small_prods(const Ws& w, cudaStream_t s);
 cudaError_t launch_check_dots(const Ws& w, int grid, cudaStream_t s);
 cudaError_t launch_check_update(const Ws& w, int grid, int pre_loop, int setup, Handles h, cudaStream_t s);
 cudaError_t launch_phase1(const Ws& w, int grid, Handles h, cudaStream_t s);
@@ -95,6 +107,7 @@ cudaError_t launch_phase2_setup(const Ws& w, int grid, cudaStream_t s);
 cudaError_t launch_loop_gate(const Ws& w, Handles h, cudaStream_t s);
 cudaError_t launch_final_gate(const Ws& w, Handles h, cudaStream_t s);
 cudaError_t launch_finalize(const Ws& w, int grid, cudaStream_t s);
+cudaError_t launch_split_x(const Ws& w, int grid, int skip_if_done, cudaStream_t s);
 
 // ---- harmonic Ritz (k_ritz.cu)
 struct RitzArgs {
@@ -112,6 +125,7 @@ struct RitzArgs {
   double* part;     // gram partials
   float* Vj;        // m x m Jacobi eigenvectors (float32)
   double* Vd;       // m x m float64 scratch
+  double* Vd2;      // m x m float64 scratch
   double* theta;    // m, descending
   float* U;         // m x k_want (column-major, leading dimension m)
   float* Wout;      // n x k_want

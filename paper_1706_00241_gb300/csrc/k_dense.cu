@@ -1,12 +1,15 @@
 // Stored-operator kernels (dense row-major float32 A):
 //   * k_rowop_tma: q = A p with the fused p^T q of Algorithm 1 line 6, or the
-//     true residual r = b - A x with float64 accumulation (the stopping test of
-//     the Sec. 3 experiments and the residual replacement). A streams through a
+//     true residual r = b - A x for the float64 iterate x with compensated
+//     (Dot2) accumulation (the stopping test of the Sec. 3 experiments and the
+//     residual replacement). A streams through a
 //     shared-memory ring filled by 2-D TMA tiles (cp.async.bulk.tensor) and
 //     completed on mbarriers; one CTA per SM owns a contiguous band of rows.
 //   * k_apply_block: Y = A V for up to 129 columns in one pass (the start-of-
-//     solve product A [x_{-1} | W] of Algorithm 1 line 3).
+//     solve product AW of Algorithm 1 line 3).
 //   * k_form_rbf: A = K + noise I for the Sec. 3 RBF kernel.
+#include <algorithm>
+
 #include "dcg_kernels.cuh"
 
 namespace dcg {
@@ -33,19 +36,48 @@ __device__ __forceinline__ void record_timeout(DevState* st, int site) {
   }
 }
 
+// Compensated dot-product step (Ogita, Rump & Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26, 2005, algorithm Dot2): the product
+// a * xh is split exactly into p + e with one FMA, (s, p) is summed exactly
+// into s + t (Knuth's TwoSum), and the rounding terms collect in c. The low
+// part xl of the float64 iterate (x = xh + xl) is added into c directly: its
+// contribution is ~eps32 of the total, so float32 accuracy suffices for it.
+// Explicit _rn intrinsics keep the compiler from contracting the splits.
+__device__ __forceinline__ void dot2_step(float& s, float& c, float a, float xh, float xl) {
+  const float p = __fmul_rn(a, xh);
+  const float e = __fmaf_rn(a, xh, -p);
+  const float s2 = __fadd_rn(s, p);
+  const float z = __fsub_rn(s2, s);
+  const float t = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, z)), __fsub_rn(p, z));
+  s = s2;
+  c = __fadd_rn(c, __fadd_rn(t, e));
+  c = __fmaf_rn(a, xl, c);
+}
+
+// (s1, c1) += (s2, c2) for compensated partial sums.
+__device__ __forceinline__ void dot2_merge(float& s1, float& c1, float s2, float c2) {
+  const float s = __fadd_rn(s1, s2);
+  const float z = __fsub_rn(s, s1);
+  const float t = __fadd_rn(__fsub_rn(s1, __fsub_rn(s, z)), __fsub_rn(s2, z));
+  s1 = s;
+  c1 = __fadd_rn(c1, __fadd_rn(c2, t));
+}
+
 // One CTA streams rows [RB_ROWS*g_lo, RB_ROWS*g_hi) of A. Warp w of the
 // consumers owns box w of every stage (256 columns); lane l owns float4 slots
-// l and l + 32 of each box row, so each thread keeps RB_ROWS accumulators.
-template <bool RESID>
+// l and l + 32 of each box row, so each thread keeps RB_ROWS accumulators
+// (RB_ROWS compensated pairs for the residual).
+template <bool RESID, bool COMPQ>
 __global__ void __launch_bounds__(RB_THREADS, 1)
     k_rowop_tma(const __grid_constant__ CUtensorMap tmap, RowOpArgs a) {
-  using Acc = typename std::conditional<RESID, double, float>::type;
+  constexpr bool COMP = RESID || COMPQ;  // compensated (Dot2) accumulation
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float* tiles = reinterpret_cast<float*>(smem);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(RB_STAGES) * RB_STAGE_BYTES);
   uint64_t* empty = full + RB_STAGES;
-  __shared__ Acc red[RB_CONSUMER_WARPS][RB_ROWS];
+  __shared__ float red[RB_CONSUMER_WARPS][RB_ROWS];
+  __shared__ float redc[RB_CONSUMER_WARPS][RB_ROWS];
   __shared__ int s_abort;
   __shared__ int s_issued;
   __shared__ int s_consumed[RB_CONSUMER_WARPS];
@@ -53,6 +85,7 @@ __global__ void __launch_bounds__(RB_THREADS, 1)
 
   DevState* st = a.st;
   if (st && a.skip_if_done && st->done) return;
+  if (RESID && st && a.resid_mode == 0 && !st->warm_start) return;  // setup: cold start needs no A x
 
   const int n = a.n;
   const int ngroups = (n + RB_ROWS - 1) / RB_ROWS;
@@ -99,9 +132,9 @@ __global__ void __launch_bounds__(RB_THREADS, 1)
     }
   } else {
     // ---------------- consumers ---------------------------------------------
-    Acc acc[RB_ROWS];
+    float acc[RB_ROWS], cmp[RB_ROWS];
 #pragma unroll
-    for (int r = 0; r < RB_ROWS; ++r) acc[r] = Acc(0);
+    for (int r = 0; r < RB_ROWS; ++r) acc[r] = cmp[r] = 0.f;
     int it = 0;
     for (; it < total; ++it) {
       const int s = it % RB_STAGES;
@@ -117,28 +150,52 @@ __global__ void __launch_bounds__(RB_THREADS, 1)
         for (int h = 0; h < 2; ++h) {
           const int slot = lane + 32 * h;
           const int j = col0 + 4 * slot;
-          float4 v;
-          if (j + 3 < n) {
-            v = __ldg(reinterpret_cast<const float4*>(a.v + j));
-          } else {
-            v.x = j < n ? __ldg(a.v + j) : 0.f;
-            v.y = j + 1 < n ? __ldg(a.v + j + 1) : 0.f;
-            v.z = j + 2 < n ? __ldg(a.v + j + 2) : 0.f;
-            v.w = 0.f;
-          }
-#pragma unroll
-          for (int r = 0; r < RB_ROWS; ++r) {
-            const float4 av = reinterpret_cast<const float4*>(box + r * RB_BOXW)[slot];
-            if constexpr (RESID) {
-              acc[r] = fma(double(av.x), double(v.x), acc[r]);
-              acc[r] = fma(double(av.y), double(v.y), acc[r]);
-              acc[r] = fma(double(av.z), double(v.z), acc[r]);
-              acc[r] = fma(double(av.w), double(v.w), acc[r]);
+          if constexpr (RESID) {
+            float xh[4], xl[4];
+            if (j + 3 < n) {
+              const float4 u = __ldg(reinterpret_cast<const float4*>(a.xh + j));
+              const float4 l = __ldg(reinterpret_cast<const float4*>(a.xl + j));
+              xh[0] = u.x; xh[1] = u.y; xh[2] = u.z; xh[3] = u.w;
+              xl[0] = l.x; xl[1] = l.y; xl[2] = l.z; xl[3] = l.w;
             } else {
-              acc[r] = fmaf(av.x, v.x, acc[r]);
-              acc[r] = fmaf(av.y, v.y, acc[r]);
-              acc[r] = fmaf(av.z, v.z, acc[r]);
-              acc[r] = fmaf(av.w, v.w, acc[r]);
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                xh[e] = j + e < n ? __ldg(a.xh + j + e) : 0.f;
+                xl[e] = j + e < n ? __ldg(a.xl + j + e) : 0.f;
+              }
+            }
+#pragma unroll
+            for (int r = 0; r < RB_ROWS; ++r) {
+              const float4 av = reinterpret_cast<const float4*>(box + r * RB_BOXW)[slot];
+              dot2_step(acc[r], cmp[r], av.x, xh[0], xl[0]);
+              dot2_step(acc[r], cmp[r], av.y, xh[1], xl[1]);
+              dot2_step(acc[r], cmp[r], av.z, xh[2], xl[2]);
+              dot2_step(acc[r], cmp[r], av.w, xh[3], xl[3]);
+            }
+          } else {
+            float4 v;
+            if (j + 3 < n) {
+              v = __ldg(reinterpret_cast<const float4*>(a.v + j));
+            } else {
+              v.x = j < n ? __ldg(a.v + j) : 0.f;
+              v.y = j + 1 < n ? __ldg(a.v + j + 1) : 0.f;
+              v.z = j + 2 < n ? __ldg(a.v + j + 2) : 0.f;
+              v.w = 0.f;
+            }
+#pragma unroll
+            for (int r = 0; r < RB_ROWS; ++r) {
+              const float4 av = reinterpret_cast<const float4*>(box + r * RB_BOXW)[slot];
+              if constexpr (COMPQ) {
+                dot2_step(acc[r], cmp[r], av.x, v.x, 0.f);
+                dot2_step(acc[r], cmp[r], av.y, v.y, 0.f);
+                dot2_step(acc[r], cmp[r], av.z, v.z, 0.f);
+                dot2_step(acc[r], cmp[r], av.w, v.w, 0.f);
+              } else {
+                acc[r] = fmaf(av.x, v.x, acc[r]);
+                acc[r] = fmaf(av.y, v.y, acc[r]);
+                acc[r] = fmaf(av.z, v.z, acc[r]);
+                acc[r] = fmaf(av.w, v.w, acc[r]);
+              }
             }
           }
         }
@@ -149,24 +206,50 @@ __global__ void __launch_bounds__(RB_THREADS, 1)
         // end of a row group: reduce the RB_ROWS accumulators over the CTA
 #pragma unroll
         for (int r = 0; r < RB_ROWS; ++r) {
-          Acc v = warp_sum(acc[r]);
-          if (lane == 0) red[warp][r] = v;
-          acc[r] = Acc(0);
+          if constexpr (COMP) {
+            float sv = acc[r], cv = cmp[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              const float s2 = __shfl_xor_sync(0xffffffffu, sv, o);
+              const float c2 = __shfl_xor_sync(0xffffffffu, cv, o);
+              dot2_merge(sv, cv, s2, c2);
+            }
+            if (lane == 0) {
+              red[warp][r] = sv;
+              redc[warp][r] = cv;
+            }
+          } else {
+            const float v = warp_sum(acc[r]);
+            if (lane == 0) red[warp][r] = v;
+          }
+          acc[r] = cmp[r] = 0.f;
         }
         asm volatile("bar.sync 1, %0;" ::"r"(RB_CONSUMER_WARPS * 32));
         if (threadIdx.x < RB_ROWS) {
           const int row = g * RB_ROWS + threadIdx.x;
-          Acc s = Acc(0);
-#pragma unroll
-          for (int w = 0; w < RB_CONSUMER_WARPS; ++w) s += red[w][threadIdx.x];
           if (row < n) {
             if constexpr (RESID) {
-              const double rr = double(a.b[row]) - double(s);
+              double tot = 0.0;
+#pragma unroll
+              for (int w = 0; w < RB_CONSUMER_WARPS; ++w)
+                tot += double(red[w][threadIdx.x]) + double(redc[w][threadIdx.x]);
+              const double rr = double(a.b[row]) - tot;
               a.out[row] = float(rr);
               my_part += rr * rr;
+            } else if constexpr (COMPQ) {
+              double tot = 0.0;
+#pragma unroll
+              for (int w = 0; w < RB_CONSUMER_WARPS; ++w)
+                tot += double(red[w][threadIdx.x]) + double(redc[w][threadIdx.x]);
+              const float qv = float(tot);
+              a.out[row] = qv;
+              my_part += double(a.v[row]) * double(qv);
             } else {
-              a.out[row] = float(s);
-              my_part += double(a.v[row]) * double(float(s));
+              float sum = 0.f;
+#pragma unroll
+              for (int w = 0; w < RB_CONSUMER_WARPS; ++w) sum += red[w][threadIdx.x];
+              a.out[row] = sum;
+              my_part += double(a.v[row]) * double(sum);
             }
           }
         }
@@ -203,9 +286,9 @@ __global__ void __launch_bounds__(RB_THREADS, 1)
     for (int i = lane; i < G; i += 32) s += a.partials[i];
     s = warp_sum(s);
     if (lane == 0) {
-      if (!RESID) {
-        *a.result = s;
-      } else if (st) {
+      if (!RESID || !st) {
+        if (a.result) *a.result = s;
+      } else if (a.resid_mode != 0) {
         st->rho_true = s;
         st->matvecs_check += 1;
         st->relres_true = st->bnorm2 > 0.0 ? sqrt(s / st->bnorm2) : sqrt(s);
@@ -214,26 +297,33 @@ __global__ void __launch_bounds__(RB_THREADS, 1)
         if (mode == 1 && s <= st->thresh2 && st->status == DCG_OK) {
           st->done = 1;
         }
-      } else {
-        *a.result = s;
       }
     }
   }
 }
 
+// Compensated accumulation for q = A p as well (COMPQ) was measured on GB300:
+// the 11-instruction Dot2 step per element makes the kernel issue-bound
+// (243 us instead of 174 us at n = 16384, 64 % of HBM) while cutting CG
+// iterations by only 2 % (float32 vector rounding, not the matvec sum,
+// separates float32 from float64 CG here). The plain float32 sum is used.
+constexpr bool kCompensatedMatvec = false;
+
 cudaError_t launch_rowop(const CUtensorMap* tmap, const RowOpArgs& a, bool resid, int grid, cudaStream_t s) {
   if (resid) {
-    k_rowop_tma<true><<<grid, RB_THREADS, RB_SMEM, s>>>(*tmap, a);
+    k_rowop_tma<true, false><<<grid, RB_THREADS, RB_SMEM, s>>>(*tmap, a);
   } else {
-    k_rowop_tma<false><<<grid, RB_THREADS, RB_SMEM, s>>>(*tmap, a);
+    k_rowop_tma<false, kCompensatedMatvec><<<grid, RB_THREADS, RB_SMEM, s>>>(*tmap, a);
   }
   return cudaGetLastError();
 }
 
 cudaError_t rowop_configure() {
-  cudaError_t e = cudaFuncSetAttribute(k_rowop_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(RB_SMEM));
+  cudaError_t e = cudaFuncSetAttribute(k_rowop_tma<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(RB_SMEM));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_rowop_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(RB_SMEM));
+  return cudaFuncSetAttribute(k_rowop_tma<false, kCompensatedMatvec>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(RB_SMEM));
 }
 
 int rowop_grid(int n, int num_sms) {
@@ -255,53 +345,59 @@ bool make_rowop_tmap(CUtensorMap* map, const float* A, int64_t n, int64_t lda, E
 }
 
 // ---------------------------------------------------------------------------
-// Y = A V, V and Y column-major n x c (leading dimension n). CUDA-core tiles of
-// 64 rows x BN columns, K-steps of 32; each thread owns a 4 x (BN/16) block.
-// The column count is read from the device state when cstate is set (graph
-// launches with a per-solve k), otherwise from the argument.
+// Y = A V, V and Y column-major n x c (leading dimension n), c <= 129.
+// One row of Y per thread, all AB_CB = 32 columns of a column block in
+// registers; per K-step of 32 the CTA stages A[256 rows x 32] transposed in
+// shared memory (so a thread reads its row with conflict-free scalar loads)
+// and V[32 x 32] (each row read as a float4 broadcast). The K range is split
+// over blockIdx.y so that ~3 CTAs run per SM; the split partials are summed
+// in a fixed order by k_block_reduce (no atomics, deterministic).
+// In a solve (st set) the columns are the k active columns of W.
 // ---------------------------------------------------------------------------
-template <int BN>
-__global__ void __launch_bounds__(256) k_apply_block(ApplyBlockArgs a) {
-  constexpr int BM = 64, BK = 32, TN = BN / 16;
-  __shared__ float As[BK][BM + 4];
-  __shared__ float Vs[BK][BN + 4];
+constexpr int AB_ROWS = 256;
+constexpr int AB_K = 32;
+constexpr int AB_CB = 32;
+
+__global__ void __launch_bounds__(AB_ROWS) k_apply_block(ApplyBlockArgs a, int kchunk, float* part) {
+  __shared__ float As[AB_K][AB_ROWS + 1];
+  __shared__ __align__(16) float Vs[AB_K][AB_CB + 4];
   int c = a.c;
   const float* V = a.V;
   float* Y = a.Y;
   if (a.st) {
     if (a.skip_if_done && a.st->done) return;
-    const int warm = a.st->warm_start;
-    c = a.st->k + warm;
-    if (!warm) {
-      V += a.n;
-      Y += a.n;
-    }
+    c = a.st->k;
+    V += a.n;
+    Y += a.n;
   }
   const int n = a.n;
-  const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;
+  const int col0 = blockIdx.z * AB_CB;
   if (col0 >= c) return;
-  const int t = threadIdx.x, ty = t / 16, tx = t % 16;
-  float acc[4][TN];
+  const int cw = min(AB_CB, c - col0);
+  const int row0 = blockIdx.x * AB_ROWS;
+  const int k_lo = blockIdx.y * kchunk, k_hi = min(n, k_lo + kchunk);
+  const int t = threadIdx.x;
+  const bool vec_ok = (a.lda % 4) == 0 && (reinterpret_cast<uintptr_t>(a.A) & 15) == 0;
+  float acc[AB_CB];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int j = 0; j < AB_CB; ++j) acc[j] = 0.f;
+  for (int k0 = k_lo; k0 < k_hi; k0 += AB_K) {
+    // A tile: 256 rows x 32 columns, 8 float4 per thread, stored transposed
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
-  const bool vec_ok = (a.lda % 4) == 0;
-  for (int k0 = 0; k0 < n; k0 += BK) {
-    // A tile: 64 rows x 32 cols, stored transposed As[kk][row]
-    for (int idx = t; idx < BM * (BK / 4); idx += 256) {
-      const int r = idx / (BK / 4), c4 = idx % (BK / 4);
+    for (int q = 0; q < (AB_ROWS * AB_K / 4) / AB_ROWS; ++q) {
+      const int idx = q * AB_ROWS + t;
+      const int r = idx / (AB_K / 4), c4 = idx % (AB_K / 4);
       const int gr = row0 + r, gk = k0 + 4 * c4;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (gr < n) {
         const float* src = a.A + int64_t(gr) * a.lda + gk;
-        if (vec_ok && gk + 3 < n) {
+        if (vec_ok && gk + 3 < k_hi) {
           v = __ldg(reinterpret_cast<const float4*>(src));
         } else {
-          v.x = gk < n ? __ldg(src) : 0.f;
-          v.y = gk + 1 < n ? __ldg(src + 1) : 0.f;
-          v.z = gk + 2 < n ? __ldg(src + 2) : 0.f;
-          v.w = gk + 3 < n ? __ldg(src + 3) : 0.f;
+          v.x = gk < k_hi ? __ldg(src) : 0.f;
+          v.y = gk + 1 < k_hi ? __ldg(src + 1) : 0.f;
+          v.z = gk + 2 < k_hi ? __ldg(src + 2) : 0.f;
+          v.w = gk + 3 < k_hi ? __ldg(src + 3) : 0.f;
         }
       }
       As[4 * c4 + 0][r] = v.x;
@@ -309,50 +405,96 @@ __global__ void __launch_bounds__(256) k_apply_block(ApplyBlockArgs a) {
       As[4 * c4 + 2][r] = v.z;
       As[4 * c4 + 3][r] = v.w;
     }
-    // V tile: 32 rows (k) x BN cols, Vs[kk][col]
-    for (int idx = t; idx < BK * BN; idx += 256) {
-      const int j = idx / BK, kk = idx % BK;
-      const int gj = col0 + j, gk = k0 + kk;
-      Vs[kk][j] = (gj < c && gk < n) ? __ldg(V + int64_t(gj) * n + gk) : 0.f;
+    // V tile: 32 k-rows x 32 columns (coalesced along k)
+#pragma unroll
+    for (int q = 0; q < (AB_K * AB_CB) / AB_ROWS; ++q) {
+      const int idx = q * AB_ROWS + t;
+      const int j = idx / AB_K, kk = idx % AB_K;
+      const int gk = k0 + kk;
+      Vs[kk][j] = (j < cw && gk < k_hi) ? __ldg(V + int64_t(col0 + j) * n + gk) : 0.f;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < BK; ++kk) {
-      const float4 av = *reinterpret_cast<const float4*>(&As[kk][4 * ty]);
-      float vv[TN];
+#pragma unroll 4
+    for (int kk = 0; kk < AB_K; ++kk) {
+      const float av = As[kk][t];
+      const float4* vr = reinterpret_cast<const float4*>(&Vs[kk][0]);
 #pragma unroll
-      for (int j = 0; j < TN; ++j) vv[j] = Vs[kk][tx + 16 * j];
-#pragma unroll
-      for (int j = 0; j < TN; ++j) {
-        acc[0][j] = fmaf(av.x, vv[j], acc[0][j]);
-        acc[1][j] = fmaf(av.y, vv[j], acc[1][j]);
-        acc[2][j] = fmaf(av.z, vv[j], acc[2][j]);
-        acc[3][j] = fmaf(av.w, vv[j], acc[3][j]);
+      for (int j4 = 0; j4 < AB_CB / 4; ++j4) {
+        const float4 v = vr[j4];
+        acc[4 * j4 + 0] = fmaf(av, v.x, acc[4 * j4 + 0]);
+        acc[4 * j4 + 1] = fmaf(av, v.y, acc[4 * j4 + 1]);
+        acc[4 * j4 + 2] = fmaf(av, v.z, acc[4 * j4 + 2]);
+        acc[4 * j4 + 3] = fmaf(av, v.w, acc[4 * j4 + 3]);
       }
     }
     __syncthreads();
   }
+  const int gr = row0 + t;
+  if (gr >= n) return;
+  if (gridDim.y == 1) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int gr = row0 + 4 * ty + i;
-    if (gr >= n) continue;
+    for (int j = 0; j < AB_CB; ++j)
+      if (j < cw) Y[int64_t(col0 + j) * n + gr] = acc[j];
+  } else {
+    float* dst = part + int64_t(blockIdx.y) * (int64_t(gridDim.z) * AB_CB) * n;
 #pragma unroll
-    for (int j = 0; j < TN; ++j) {
-      const int gj = col0 + tx + 16 * j;
-      if (gj < c) Y[int64_t(gj) * n + gr] = acc[i][j];
-    }
+    for (int j = 0; j < AB_CB; ++j)
+      if (j < cw) dst[int64_t(col0 + j) * n + gr] = acc[j];
   }
 }
 
-cudaError_t launch_apply_block(const ApplyBlockArgs& a, int cmax, cudaStream_t s) {
-  if (cmax <= 0) return cudaSuccess;
-  if (cmax <= 32) {
-    dim3 grid((a.n + 63) / 64, 1);
-    k_apply_block<32><<<grid, 256, 0, s>>>(a);
-  } else {
-    dim3 grid((a.n + 63) / 64, (cmax + 63) / 64);
-    k_apply_block<64><<<grid, 256, 0, s>>>(a);
+// Y[:, j] = sum over the K splits of the partials (fixed order).
+__global__ void __launch_bounds__(256) k_block_reduce(ApplyBlockArgs a, int splits, int colblocks, const float* part) {
+  int c = a.c;
+  float* Y = a.Y;
+  if (a.st) {
+    if (a.skip_if_done && a.st->done) return;
+    c = a.st->k;
+    Y += a.n;
   }
+  const int64_t total = int64_t(c) * a.n;
+  const int64_t sstride = int64_t(colblocks) * AB_CB * a.n;
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    float s = 0.f;
+    for (int sp = 0; sp < splits; ++sp) s += part[sp * sstride + idx];
+    Y[idx] = s;
+  }
+}
+
+int apply_block_splits(int n, int cmax, int num_sms) {
+  const int rowblocks = (n + AB_ROWS - 1) / AB_ROWS;
+  const int colblocks = (cmax + AB_CB - 1) / AB_CB;
+  int splits = (3 * num_sms) / (rowblocks * colblocks);
+  const int kmax_splits = (n + AB_K * 8 - 1) / (AB_K * 8);  // at least 8 K-steps per split
+  if (splits > kmax_splits) splits = kmax_splits;
+  if (splits > 16) splits = 16;
+  return splits < 1 ? 1 : splits;
+}
+
+// Largest split-K partial buffer any column count up to cmax can need.
+size_t apply_block_scratch_floats(int n, int cmax, int num_sms) {
+  size_t best = 0;
+  for (int cb = 1; cb <= (cmax + AB_CB - 1) / AB_CB; ++cb) {
+    const int splits = apply_block_splits(n, cb * AB_CB, num_sms);
+    if (splits > 1) best = std::max(best, size_t(splits) * cb * AB_CB * size_t(n));
+  }
+  return best;
+}
+
+cudaError_t launch_apply_block(const ApplyBlockArgs& a, int cmax, float* scratch, int num_sms, cudaStream_t s) {
+  if (cmax <= 0) return cudaSuccess;
+  const int n = a.n;
+  const int splits = scratch ? apply_block_splits(n, cmax, num_sms) : 1;
+  int kchunk = (n + splits - 1) / splits;
+  kchunk = (kchunk + AB_K - 1) / AB_K * AB_K;
+  const int used = (n + kchunk - 1) / kchunk;
+  const int colblocks = (cmax + AB_CB - 1) / AB_CB;
+  dim3 grid((n + AB_ROWS - 1) / AB_ROWS, used, colblocks);
+  k_apply_block<<<grid, AB_ROWS, 0, s>>>(a, kchunk, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || used == 1) return e;
+  k_block_reduce<<<2 * num_sms, 256, 0, s>>>(a, used, colblocks, scratch);
   return cudaGetLastError();
 }
 

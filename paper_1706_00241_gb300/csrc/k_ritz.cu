@@ -101,6 +101,7 @@ __global__ void k_gram_reduce(const double* part, int splits, int ma, int mb, do
 
 static int gram_splits(int n, int tiles, int num_sms) {
   int splits = (2 * num_sms + tiles - 1) / max(tiles, 1);
+  if (splits > 64) splits = 64;
   const int max_splits = (n + GR_T - 1) / GR_T;
   if (splits > max_splits) splits = max_splits;
   return splits < 1 ? 1 : splits;
@@ -137,6 +138,18 @@ cudaError_t launch_gram_E(const Ws& w, double* part, int num_sms, cudaStream_t s
   g.st = w.st;
   if (w.kmax == 0) return cudaSuccess;
   return launch_gram(g, w.kmax, w.kmax, num_sms, w.E, w.st, s);
+}
+
+// G_W = (AW)^T (AW): used to re-deflate the residual every iteration.
+cudaError_t launch_gram_GW(const Ws& w, double* part, int num_sms, cudaStream_t s) {
+  GramArgs g{};
+  g.n = w.n;
+  g.a1 = w.Y + w.n;
+  g.b1 = w.Y + w.n;
+  g.part = part;
+  g.st = w.st;
+  if (w.kmax == 0) return cudaSuccess;
+  return launch_gram(g, w.kmax, w.kmax, num_sms, w.GW, w.st, s);
 }
 
 // --------------------------------------------------------------------------
@@ -217,6 +230,7 @@ cudaError_t chol_configure(int kmax) {
 // --------------------------------------------------------------------------
 constexpr int EIG_THREADS = 1024;
 constexpr int EIG_MAX_SWEEPS = 30;
+constexpr int EIG_SMEM_MAX = 200 * 1024;  // dynamic shared memory of the eigen kernel
 
 __device__ void jacobi_pair(int m2, int r, int i, int& p, int& q) {
   // circle method: s_0 = 0, s_j = 1 + ((j - 1 + r) mod (m2 - 1))
@@ -225,96 +239,186 @@ __device__ void jacobi_pair(int m2, int r, int i, int& p, int& q) {
   q = pos(m2 - 1 - i);
 }
 
+// Cholesky factorisation in place (lower triangle of L, leading dimension ld)
+// with column dropping: a pivot below drop_tol marks the column dropped (its
+// entries are zeroed, so later columns ignore it). Returns the kept count.
+__device__ int chol_drop(float* L, int m, int ld, float drop_tol, int* kept) {
+  __shared__ int s_cnt;
+  const int t = threadIdx.x;
+  if (t == 0) s_cnt = 0;
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    if (t < 32) {  // pivot: one warp sums the row
+      float s = 0.f;
+      for (int p = t; p < j; p += 32) s = fmaf(L[j * ld + p], L[j * ld + p], s);
+      s = warp_sum(s);
+      if (t == 0) {
+        const float piv = L[j * ld + j] - s;
+        const int ok = (piv > drop_tol) && isfinite(piv);
+        kept[j] = ok;
+        L[j * ld + j] = ok ? sqrtf(piv) : 1.f;
+        s_cnt += ok;
+      }
+    }
+    __syncthreads();
+    const float ljj = L[j * ld + j];
+    const int ok = kept[j];
+    // column j below the diagonal: one warp per row, lanes over p
+    const int warp = t / 32, lane = t % 32, nw = blockDim.x / 32;
+    for (int i = j + 1 + warp; i < m; i += nw) {
+      if (!ok) {
+        if (lane == 0) L[i * ld + j] = 0.f;
+        continue;
+      }
+      float s = 0.f;
+      for (int p = lane; p < j; p += 32) s = fmaf(L[i * ld + p], L[j * ld + p], s);
+      s = warp_sum(s);
+      if (lane == 0) L[i * ld + j] = (L[i * ld + j] - s) / ljj;
+    }
+    if (!ok)
+      for (int p = t; p < j; p += blockDim.x) L[j * ld + p] = 0.f;
+    __syncthreads();
+  }
+  return s_cnt;
+}
+
+// Row-parallel forward substitution L Y = B for m right-hand sides (columns
+// of B, leading dimension m, overwritten with Y): for each row i the m
+// columns are split over the threads and the dot product over j < i is
+// accumulated sequentially per column.
+__device__ void trsm_lower(const float* L, float* B, int m) {
+  for (int i = 0; i < m; ++i) {
+    const float lii = L[i * m + i];
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      float s = B[i * m + c];
+      for (int j = 0; j < i; ++j) s = fmaf(-L[i * m + j], B[j * m + c], s);
+      B[i * m + c] = s / lii;
+    }
+    __syncthreads();
+  }
+}
+
+// Harmonic Ritz eigen-solve of Eq. 7 (one CTA of 1024 threads).
+// F, G: m x m float64 (row-major) from the Gram kernels. The pencil is scaled
+// to unit diagonal F' = S F S (S = diag(F_jj^{-1/2})); in that scaling the
+// columns of Z are nearly A-conjugate, so F' is close to the identity and the
+// reduction runs in float32: F' = L L^T, C = L^{-1} G' L^{-T}, cyclic Jacobi on
+// C, u = S L^{-T} v. (Float64 on this part has a ~57x lower throughput and long
+// dependent-chain latency on GB300; the float32 eigenvectors only set the
+// deflation basis, whose accuracy is that of the float32 directions anyway.)
 __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, int k_new) {
-  extern __shared__ float C[];  // m x m
+  extern __shared__ float C[];  // m x (m + 1), then V^T when it fits
   __shared__ float cs_c[kMaxM / 2 + 1], cs_s[kMaxM / 2 + 1];
   __shared__ int pp[kMaxM / 2 + 1], qq[kMaxM / 2 + 1];
-  __shared__ double scale[kMaxM];
-  __shared__ int s_fail, s_changed;
+  __shared__ float scale[kMaxM];
+  __shared__ int kept[kMaxM], pos[kMaxM], orig[kMaxM];
+  __shared__ int s_changed;
   __shared__ float th[kMaxM];
   __shared__ int rank_of[kMaxM];
-  double* F = a.F;
-  double* G = a.G;
   const int t = threadIdx.x;
-  if (t == 0) s_fail = 0;
-  // 1. diagonal scaling S = diag(F_jj^{-1/2}) and symmetrisation (in place)
+  // float32 work arrays in the float64 scratch buffers
+  float* Ff = reinterpret_cast<float*>(a.Vd);       // F' (m x m), then L
+  float* Fc = Ff + m * m;                           // copy of F' for a refactorisation
+  float* Gf = reinterpret_cast<float*>(a.Vd2);      // G', then Y = L^{-1} G'
+  float* Xc = Gf + m * m;                           // C columns
+  // 1. diagonal scaling and symmetrisation (float64 sums -> float32)
   for (int j = t; j < m; j += blockDim.x) {
-    const double f = F[j * m + j];
-    scale[j] = f > 0.0 ? 1.0 / sqrt(f) : 0.0;
+    const double f = a.F[j * m + j];
+    scale[j] = f > 0.0 ? float(1.0 / sqrt(f)) : 0.f;
   }
   __syncthreads();
   for (int idx = t; idx < m * m; idx += blockDim.x) {
     const int i = idx / m, j = idx % m;
-    if (i < j) continue;
-    const double sij = scale[i] * scale[j];
-    const double f = 0.5 * (F[i * m + j] + F[j * m + i]) * sij;
-    const double g = 0.5 * (G[i * m + j] + G[j * m + i]) * sij;
-    F[i * m + j] = f;
-    F[j * m + i] = f;
-    G[i * m + j] = g;
-    G[j * m + i] = g;
+    const double sij = double(scale[i]) * double(scale[j]);
+    const float f = float(0.5 * (a.F[i * m + j] + a.F[j * m + i]) * sij);
+    Ff[idx] = f;
+    Fc[idx] = f;
+    Gf[idx] = float(0.5 * (a.G[i * m + j] + a.G[j * m + i]) * sij);
   }
   __syncthreads();
-  // 2. Cholesky F' = L L^T (lower part of F)
-  for (int j = 0; j < m; ++j) {
-    if (t == 0) {
-      double s = F[j * m + j];
-      for (int p = 0; p < j; ++p) s -= F[j * m + p] * F[j * m + p];
-      if (!(s > 1e-14) || !isfinite(s)) {
-        s_fail = 1;
-        s = 1.0;
+  // 2. Cholesky F' = L L^T; a direction whose pivot falls below 1e-6 (unit
+  //    diagonal, so relative; float32 rounding of F' is ~1e-7) is numerically
+  //    dependent on the earlier ones and is dropped (rank-deficient Z, reading
+  //    R6); the rest is compacted and refactorised.
+  const int mk = chol_drop(Ff, m, m, 1e-6f, kept);
+  if (t == 0) {
+    int c = 0;
+    for (int j = 0; j < m; ++j) {
+      pos[j] = kept[j] ? c : -1;
+      if (kept[j]) orig[c++] = j;
+    }
+  }
+  __syncthreads();
+  float* L = Ff;
+  float* G = Gf;
+  if (mk < m) {
+    if (mk == 0) {
+      if (t == 0) {
+        *a.status = DCG_ERR_SUBSPACE_SINGULAR;
+        a.k_out[0] = 0;
+        a.k_out[1] = 0;
       }
-      F[j * m + j] = sqrt(s);
+      return;
+    }
+    // compact F' (from the copy) into Ff and G' into Xc, then move G' back
+    for (int idx = t; idx < mk * mk; idx += blockDim.x) {
+      const int i = orig[idx / mk], j = orig[idx % mk];
+      Ff[idx] = Fc[i * m + j];
+      Xc[idx] = Gf[i * m + j];
     }
     __syncthreads();
-    const double ljj = F[j * m + j];
-    for (int i = j + 1 + t; i < m; i += blockDim.x) {
-      double s = F[i * m + j];
-      for (int p = 0; p < j; ++p) s -= F[i * m + p] * F[j * m + p];
-      F[i * m + j] = s / ljj;
+    for (int idx = t; idx < mk * mk; idx += blockDim.x) Gf[idx] = Xc[idx];
+    __shared__ int kept2[kMaxM];
+    const int mk2 = chol_drop(Ff, mk, mk, 1e-12f, kept2);
+    if (mk2 < mk) {
+      if (t == 0) {
+        *a.status = DCG_ERR_SUBSPACE_SINGULAR;
+        a.k_out[0] = 0;
+        a.k_out[1] = 0;
+      }
+      return;
     }
-    __syncthreads();
   }
-  if (s_fail) {
-    if (t == 0) {
-      *a.status = DCG_ERR_SUBSPACE_SINGULAR;
-      *a.k_out = 0;
-    }
-    return;
-  }
-  // 3. Y = L^{-1} G' (forward substitution, one column of G' per thread)
-  for (int c = t; c < m; c += blockDim.x) {
-    for (int i = 0; i < m; ++i) {
-      double s = G[i * m + c];
-      for (int j = 0; j < i; ++j) s -= F[i * m + j] * G[j * m + c];
-      G[i * m + c] = s / F[i * m + i];
-    }
+  const int mm = mk;  // size of the reduced pencil
+  if (k_new > mm) k_new = mm;
+  // 3. Y = L^{-1} G'
+  trsm_lower(L, G, mm);
+  // 4. C = L^{-1} Y^T = L^{-1} G' L^{-T}: transpose Y into Xc and solve again
+  for (int idx = t; idx < mm * mm; idx += blockDim.x) {
+    const int i = idx / mm, j = idx % mm;
+    Xc[idx] = G[j * mm + i];
   }
   __syncthreads();
-  // 4. C = L^{-1} Y^T (Y^T = G' L^{-T}, so C = L^{-1} G' L^{-T}); row c of Y
-  //    is solved per thread; C written to shared memory in float32.
-  //    Column c of C solves L x = (row c of Y)^T.
-  double* Xc = a.Vd;  // m x m scratch (column-major by c)
-  for (int c = t; c < m; c += blockDim.x) {
-    for (int i = 0; i < m; ++i) {
-      double s = G[c * m + i];
-      for (int j = 0; j < i; ++j) s -= F[i * m + j] * Xc[int64_t(c) * m + j];
-      Xc[int64_t(c) * m + i] = s / F[i * m + i];
+  trsm_lower(L, Xc, mm);
+  m = mm;
+  // C (float32, leading dimension ldc = m + 1 so that column sweeps are free of
+  // bank conflicts) and V^T (row p holds column p of V) in shared memory when
+  // both fit, V^T in global memory otherwise.
+  const int ldc = m + 1;
+  float* Vt = (2 * m * ldc * int(sizeof(float)) <= EIG_SMEM_MAX) ? C + m * ldc : a.Vj;
+  for (int i = t / 32; i < m; i += blockDim.x / 32)
+    for (int j = t % 32; j < m; j += 32) {
+      C[i * ldc + j] = 0.5f * (Xc[i * m + j] + Xc[j * m + i]);
+      Vt[i * ldc + j] = (i == j) ? 1.f : 0.f;
     }
+  __shared__ float s_cmax;
+  __syncthreads();
+  if (t == 0) {
+    float cm = 0.f;
+    for (int i = 0; i < m; ++i) cm = fmaxf(cm, fabsf(C[i * ldc + i]));
+    s_cmax = cm;
   }
   __syncthreads();
-  for (int idx = t; idx < m * m; idx += blockDim.x) {
-    const int i = idx / m, j = idx % m;
-    C[i * m + j] = float(0.5 * (Xc[int64_t(j) * m + i] + Xc[int64_t(i) * m + j]));
-  }
-  // V = I
-  float* V = a.Vj;
-  for (int idx = t; idx < m * m; idx += blockDim.x) V[idx] = (idx / m == idx % m) ? 1.f : 0.f;
-  __syncthreads();
+  const float abs_tol = 1e-6f * s_cmax;
 
-  // 5. cyclic Jacobi (circle-method ordering; rotations of disjoint pairs applied together)
+  // 5. cyclic Jacobi (circle-method ordering; rotations of disjoint pairs
+  //    applied together). A pair is rotated while its off-diagonal entry is
+  //    above both 2e-6 sqrt(|c_pp c_qq|) and 1e-6 max|c_ii|: in float32 the
+  //    off-diagonal entries settle at rounding noise ~eps32 |C|, which a
+  //    purely relative test would chase forever.
   const int m2 = (m + 1) & ~1;
   const int half = m2 / 2;
+  const int warp = t / 32, lane = t % 32, nwarps = blockDim.x / 32;
   for (int sweep = 0; sweep < EIG_MAX_SWEEPS; ++sweep) {
     if (t == 0) s_changed = 0;
     __syncthreads();
@@ -327,54 +431,59 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
           p = q;
           q = tmp;
         }
-        float c = 1.f, s = 0.f;
+        float c = 1.f, sn = 0.f;
         if (q < m) {
-          const float apq = C[p * m + q];
-          const float app = C[p * m + p], aqq = C[q * m + q];
-          if (fabsf(apq) > 4e-7f * sqrtf(fabsf(app * aqq)) && apq != 0.f) {
+          const float apq = C[p * ldc + q];
+          const float app = C[p * ldc + p], aqq = C[q * ldc + q];
+          const float aa = fabsf(apq);
+          if (aa > 2e-6f * sqrtf(fabsf(app * aqq)) && aa > abs_tol) {
             const float tau = (aqq - app) / (2.f * apq);
             const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
             c = rsqrtf(1.f + tt * tt);
-            s = tt * c;
+            sn = tt * c;
             s_changed = 1;
           }
         }
         pp[t] = p;
         qq[t] = q;
         cs_c[t] = c;
-        cs_s[t] = s;
+        cs_s[t] = sn;
       }
       __syncthreads();
-      // rows p, q of C  <- J^T C
-      for (int idx = t; idx < half * m; idx += blockDim.x) {
-        const int pr = idx / m, j = idx % m;
+      // rows p, q of C <- J^T C; rows p, q of V^T <- (V J)^T
+      for (int pr = warp; pr < half; pr += nwarps) {
+        const float sn = cs_s[pr];
+        if (sn == 0.f) continue;
         const int p = pp[pr], q = qq[pr];
-        if (q >= m || cs_s[pr] == 0.f) continue;
-        const float c = cs_c[pr], s = cs_s[pr];
-        const float a_p = C[p * m + j], a_q = C[q * m + j];
-        C[p * m + j] = c * a_p - s * a_q;
-        C[q * m + j] = s * a_p + c * a_q;
+        const float c = cs_c[pr];
+        for (int j = lane; j < m; j += 32) {
+          const float a_p = C[p * ldc + j], a_q = C[q * ldc + j];
+          C[p * ldc + j] = c * a_p - sn * a_q;
+          C[q * ldc + j] = sn * a_p + c * a_q;
+          const float v_p = Vt[p * ldc + j], v_q = Vt[q * ldc + j];
+          Vt[p * ldc + j] = c * v_p - sn * v_q;
+          Vt[q * ldc + j] = sn * v_p + c * v_q;
+        }
       }
       __syncthreads();
-      // columns p, q of C and V  <- C J, V J
-      for (int idx = t; idx < half * m; idx += blockDim.x) {
-        const int pr = idx / m, i = idx % m;
+      // columns p, q of C <- C J
+      for (int pr = warp; pr < half; pr += nwarps) {
+        const float sn = cs_s[pr];
+        if (sn == 0.f) continue;
         const int p = pp[pr], q = qq[pr];
-        if (q >= m || cs_s[pr] == 0.f) continue;
-        const float c = cs_c[pr], s = cs_s[pr];
-        const float a_p = C[i * m + p], a_q = C[i * m + q];
-        C[i * m + p] = c * a_p - s * a_q;
-        C[i * m + q] = s * a_p + c * a_q;
-        const float v_p = V[i * m + p], v_q = V[i * m + q];
-        V[i * m + p] = c * v_p - s * v_q;
-        V[i * m + q] = s * v_p + c * v_q;
+        const float c = cs_c[pr];
+        for (int i = lane; i < m; i += 32) {
+          const float a_p = C[i * ldc + p], a_q = C[i * ldc + q];
+          C[i * ldc + p] = c * a_p - sn * a_q;
+          C[i * ldc + q] = sn * a_p + c * a_q;
+        }
       }
       __syncthreads();
     }
     if (!s_changed) break;
   }
   // 6. order the values (descending, ties by lower index) and select
-  for (int i = t; i < m; i += blockDim.x) th[i] = C[i * m + i];
+  for (int i = t; i < m; i += blockDim.x) th[i] = C[i * ldc + i];
   __syncthreads();
   for (int i = t; i < m; i += blockDim.x) {
     int rk = 0;
@@ -383,23 +492,36 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
     a.theta[rk] = double(th[i]);
   }
   __syncthreads();
-  // 7. U[:, c] = S L^{-T} v_sel(c): back substitution L^T y = v, then scale
-  for (int c = t; c < k_new; c += blockDim.x) {
-    int sel = -1;
-    const int want = (a.select == DCG_SELECT_SMALLEST) ? (m - 1 - c) : c;
-    for (int i = 0; i < m; ++i)
-      if (rank_of[i] == want) sel = i;
-    double* y = Xc + int64_t(c) * m;
-    for (int i = m - 1; i >= 0; --i) {
-      double s = double(V[i * m + sel]);
-      for (int j = i + 1; j < m; ++j) s -= F[j * m + i] * y[j];
-      y[i] = s / F[i * m + i];
+  // 7. U[:, c] = S L^{-T} v_sel(c) on the kept rows (dropped rows are zero):
+  //    back substitution L^T y = v (one warp per vector), then scale
+  const int m_orig = a.k_act + a.nstored;
+  {
+    const int warp = t / 32, lane = t % 32, nw = blockDim.x / 32;
+    for (int c = warp; c < k_new; c += nw) {
+      const int want = (a.select == DCG_SELECT_SMALLEST) ? (m - 1 - c) : c;
+      int sel = -1;
+      for (int i = lane; i < m; i += 32)
+        if (rank_of[i] == want) sel = i;
+      for (int o = 16; o > 0; o >>= 1) sel = max(sel, __shfl_xor_sync(0xffffffffu, sel, o));
+      float* y = Xc + int64_t(c) * m;
+      for (int i = m - 1; i >= 0; --i) {
+        float s = 0.f;
+        for (int j = i + 1 + lane; j < m; j += 32) s = fmaf(L[j * m + i], y[j], s);
+        s = warp_sum(s);
+        if (lane == 0) y[i] = (Vt[sel * ldc + i] - s) / L[i * m + i];
+        __syncwarp();
+      }
+      for (int i = lane; i < m_orig; i += 32) {
+        const int ci = pos[i];
+        a.U[int64_t(c) * m_orig + i] = ci >= 0 ? scale[i] * y[ci] : 0.f;
+      }
     }
-    for (int i = 0; i < m; ++i) a.U[int64_t(c) * m + i] = float(scale[i] * y[i]);
   }
+  __syncthreads();
   if (t == 0) {
     *a.status = DCG_OK;
-    *a.k_out = k_new;
+    a.k_out[0] = k_new;
+    a.k_out[1] = m;
   }
 }
 
@@ -408,6 +530,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
 __global__ void __launch_bounds__(256) k_zu(RitzArgs a, int m, int k_new) {
   extern __shared__ float Us[];  // m x 32
   if (*a.status != DCG_OK) return;
+  k_new = min(k_new, a.k_out[0]);
   const int n = a.n;
   for (int c0 = 0; c0 < k_new; c0 += 32) {
     const int cw = min(32, k_new - c0);
@@ -433,7 +556,7 @@ __global__ void __launch_bounds__(256) k_zu(RitzArgs a, int m, int k_new) {
 
 // Column norm and sign pivot (largest magnitude, lowest index) of W_out[:, c].
 __global__ void __launch_bounds__(256) k_colnorm(RitzArgs a) {
-  if (*a.status != DCG_OK) return;
+  if (*a.status != DCG_OK || int(blockIdx.x) >= a.k_out[0]) return;
   const int c = blockIdx.x, n = a.n;
   const float* col = a.Wout + int64_t(c) * n;
   double ss = 0.0;
@@ -477,6 +600,7 @@ __global__ void __launch_bounds__(256) k_colnorm(RitzArgs a) {
 // W (columns 1.. of XW) <- W_out * colscale
 __global__ void __launch_bounds__(256) k_colscale(RitzArgs a, float* dstW, int k_new) {
   if (*a.status != DCG_OK) return;
+  k_new = min(k_new, a.k_out[0]);
   const int n = a.n;
   const int64_t total = int64_t(n) * k_new;
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
@@ -487,7 +611,7 @@ __global__ void __launch_bounds__(256) k_colscale(RitzArgs a, float* dstW, int k
 }
 
 cudaError_t ritz_configure() {
-  const int smem = kMaxM * kMaxM * sizeof(float);
+  const int smem = EIG_SMEM_MAX;
   cudaError_t e = cudaFuncSetAttribute(k_ritz_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_zu, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxM * 32 * 4);
@@ -509,9 +633,9 @@ cudaError_t launch_ritz(const RitzArgs& a, int num_sms, float* dstW, cudaStream_
   g.a1 = a.AW; g.ka1 = a.k_act; g.a2 = a.Q; g.ka2 = a.nstored;
   e = launch_gram(g, m, m, num_sms, a.G, nullptr, s);
   if (e != cudaSuccess) return e;
-  k_ritz_eig<<<1, EIG_THREADS, size_t(m) * m * sizeof(float), s>>>(a, m, k_new);
+  k_ritz_eig<<<1, EIG_THREADS, EIG_SMEM_MAX, s>>>(a, m, k_new);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_zu<<<num_sms, 256, size_t(m) * 32 * sizeof(float), s>>>(a, m, k_new);
+  k_zu<<<num_sms, 256, size_t(m) * 32 * sizeof(float), s>>>(a, m, k_new);  // k_new is an upper bound; k_zu reads k_out
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_colnorm<<<k_new, 256, 0, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -37,12 +37,14 @@ class DefCG:
     Parameters follow ``dcg_config`` in include/dcg.h: ``window`` is "last" or
     "first" (Algorithm 1 line 13), ``select`` "largest" or "smallest"
     (Sec. 2.3), ``refine_every`` the residual-replacement period (0 = only the
-    final true-residual confirmation).
+    final true-residual confirmation). ``reproject`` (default on) takes mu from
+    (AW)^T (beta p + r), equal to (AW)^T r in exact arithmetic, which keeps the
+    float32 directions A-conjugate to W.
     """
 
     def __init__(self, n: int, k: int, ell: int, tol: float, max_iter: int | None = None,
                  window: str = "last", select: str = "largest", refine_every: int = 0,
-                 warm_start: bool = False, reproject: bool = False,
+                 warm_start: bool = False, reproject: bool = True,
                  record_history: bool = False, stream=None):
         self.lib = _lib.load()
         self.n, self.k, self.ell = int(n), int(k), int(ell)
@@ -98,11 +100,13 @@ class DefCG:
 
     # -- solve --------------------------------------------------------------
     def solve(self, b: torch.Tensor, x: torch.Tensor | None = None, raise_on_error: bool = True):
-        """Runs Algorithm 1 on (A, b); returns (x, info dict)."""
+        """Runs Algorithm 1 on (A, b); returns (x, info dict). b is float32,
+        x float64 (the iterate accumulates in float64; see dcg_solve)."""
         _dev_f32(b, "b")
         if x is None:
-            x = torch.zeros_like(b)
-        _dev_f32(x, "x")
+            x = torch.zeros(b.shape, dtype=torch.float64, device=b.device)
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+            raise TypeError("x must be a contiguous float64 CUDA tensor")
         info = _lib.DcgSolveInfo()
         st = self.lib.dcg_solve(self._ctx, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
                                 ctypes.byref(info))
