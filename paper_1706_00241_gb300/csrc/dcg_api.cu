@@ -50,6 +50,17 @@ struct dcg_ctx {
   const float* A = nullptr;
   int64_t lda = 0;
   CUtensorMap tmap;
+  // matrix-free RBF operator (owned copies of the points)
+  int n_pad = 0;             // n rounded up to the 128-row tile
+  int rbf_d = 0, rbf_xformat = 0;
+  float* Xr = nullptr;       // n x 64 capacity, rounded points
+  void* Xt = nullptr;        // n_pad x 128 bytes tensor-core tiles
+  float* nsq = nullptr;      // n_pad
+  float* vcol = nullptr;     // n_pad
+  RbfParams* prm = nullptr;
+  float* pmv = nullptr;      // n_pad: padded copy of a caller's p (single-step matvec)
+  CUtensorMap rbf_tmap;
+  int rbf_grid = 1;
 
   // split-K partials of the block product
   float* block_scratch = nullptr;
@@ -198,6 +209,7 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   CKC(cudaEventCreate(&c->ev1));
   CKC(cudaEventCreate(&c->ev2));
   CKC(rowop_configure());
+  CKC(rbf_mv_configure());
   CKC(chol_configure(96));
   CKC(ritz_configure());
 
@@ -215,7 +227,8 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   CKC(dalloc(c, &w.xh, size_t(n)));
   CKC(dalloc(c, &w.xl, size_t(n)));
   CKC(dalloc(c, &w.r, size_t(n)));
-  CKC(dalloc(c, &w.p, size_t(n)));
+  c->n_pad = (n + 127) / 128 * 128;
+  CKC(dalloc(c, &w.p, size_t(c->n_pad)));  // zero tail: the matrix-free kernel reads whole 128-row tiles
   CKC(dalloc(c, &w.q, size_t(n)));
   CKC(dalloc(c, &w.b, size_t(n)));
   CKC(dalloc(c, &w.P, size_t(n) * std::max(ellmax, 1)));
@@ -253,7 +266,8 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   CKC(dalloc(c, &c->k_out, 2));
   CKC(dalloc(c, &c->ritz_status, 1));
   CKC(dalloc(c, &c->ritz_part, gram_partials_doubles(n, mm, c->num_sms)));
-  CKC(dalloc(c, &c->mv_partials, size_t(c->grid_rows) + 1));
+  CKC(dalloc(c, &c->mv_partials,
+              2 * size_t(std::max(std::max(c->grid_rows, 2 * c->num_sms), rbf_exact_grid(n))) + 2));
   {
     const size_t bs = apply_block_scratch_floats(n, kMaxBlockCols, c->num_sms);
     if (bs) CKC(dalloc(c, &c->block_scratch, bs));
@@ -295,14 +309,43 @@ extern "C" dcg_status dcg_set_operator_dense(dcg_ctx* c, const float* A, int64_t
 extern "C" dcg_status dcg_set_operator_rbf(dcg_ctx* c, const float* X, int32_t d, int32_t xformat, double l,
                                            double s2, double noise) {
   if (!c) return DCG_ERR_INVALID_ARG;
-  (void)X; (void)d; (void)xformat; (void)l; (void)s2; (void)noise;
-  return fail(c, DCG_ERR_UNSUPPORTED, "matrix-free RBF operator not available in this build");
+  if (!X) return fail(c, DCG_ERR_INVALID_ARG, "X is NULL");
+  if (!(l > 0.0) || !(s2 > 0.0) || !(noise >= 0.0)) return fail(c, DCG_ERR_INVALID_ARG, "bad RBF parameters");
+  if (xformat != DCG_X_BF16 && xformat != DCG_X_TF32)
+    return fail(c, DCG_ERR_UNSUPPORTED, "matrix-free operator: xformat BF16 or TF32 in this build");
+  if (d < 1 || d > (xformat == DCG_X_BF16 ? 64 : 32))
+    return fail(c, DCG_ERR_UNSUPPORTED, "matrix-free operator: d <= 64 (BF16) or d <= 32 (TF32)");
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return fail(c, DCG_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  const int n = c->w.n, n_pad = c->n_pad;
+  if (!c->Xr) {
+    CK(dalloc(c, &c->Xr, size_t(n) * 64));
+    CK(dalloc(c, reinterpret_cast<unsigned char**>(&c->Xt), size_t(n_pad) * 128));
+    CK(dalloc(c, &c->nsq, size_t(n_pad)));
+    CK(dalloc(c, &c->vcol, size_t(n_pad)));
+    CK(dalloc(c, &c->prm, 1));
+    CK(dalloc(c, &c->pmv, size_t(n_pad)));
+  }
+  CK(launch_rbf_prep(X, n, n_pad, d, xformat, c->Xr, c->Xt, c->nsq, c->stream));
+  CK(launch_rbf_params(c->nsq, n, n_pad, l, s2, noise, c->vcol, c->prm, c->stream));
+  CUtensorMap m;
+  if (!make_rbf_tmap(&m, c->Xt, n_pad, xformat, enc)) return fail(c, DCG_ERR_INVALID_ARG, "tensor map encode failed");
+  c->rbf_tmap = m;
+  c->rbf_d = d;
+  c->rbf_xformat = xformat;
+  c->rbf_grid = rbf_mv_grid(n_pad / 128, c->num_sms);
+  c->op = OP_RBF;
+  c->A = nullptr;
+  destroy_graph(c);
+  return DCG_OK;
 }
 
 extern "C" dcg_status dcg_set_rbf_params(dcg_ctx* c, double l, double s2, double noise) {
   if (!c) return DCG_ERR_INVALID_ARG;
-  (void)l; (void)s2; (void)noise;
-  return fail(c, DCG_ERR_STATE, "no matrix-free operator set");
+  if (c->op != OP_RBF) return fail(c, DCG_ERR_STATE, "no matrix-free operator set");
+  if (!(l > 0.0) || !(s2 > 0.0) || !(noise >= 0.0)) return fail(c, DCG_ERR_INVALID_ARG, "bad RBF parameters");
+  CK(launch_rbf_params(c->nsq, c->w.n, c->n_pad, l, s2, noise, c->vcol, c->prm, c->stream));
+  return DCG_OK;
 }
 
 extern "C" dcg_status dcg_form_rbf_dense(const float* X, int64_t n, int32_t d, double l, double s2, double noise,
@@ -318,6 +361,24 @@ extern "C" dcg_status dcg_form_rbf_dense(const float* X, int64_t n, int32_t d, d
 // ---------------------------------------------------------------------------
 static cudaError_t op_matvec(dcg_ctx* c, const float* p, float* q, double* result, double* partials,
                              unsigned int* ticket, DevState* st, cudaStream_t s) {
+  if (c->op == OP_RBF) {
+    RbfMvArgs a{};
+    a.p = p;  // n_pad floats with a zero tail
+    a.vcol = c->vcol;
+    a.q = q;
+    a.n = c->w.n;
+    a.n_tiles = c->n_pad / 128;
+    a.d = c->rbf_d;
+    a.xformat = c->rbf_xformat;
+    a.prm = c->prm;
+    a.partials = partials;
+    a.ticket = ticket;
+    a.result = result;
+    a.st = st;
+    a.skip_if_done = st ? 1 : 0;
+    a.col_idx = -1;
+    return launch_rbf_mv(&c->rbf_tmap, a, c->rbf_grid, s);
+  }
   RowOpArgs a{};
   a.v = p;
   a.out = q;
@@ -330,9 +391,28 @@ static cudaError_t op_matvec(dcg_ctx* c, const float* p, float* q, double* resul
   return launch_rowop(&c->tmap, a, false, c->grid_rows, s);
 }
 
+// r = b - A x for the float64 iterate (compensated sums), with the state's
+// check / refinement bookkeeping; mode as in RowOpArgs::resid_mode.
 static cudaError_t op_resid(dcg_ctx* c, int mode, int skip_if_done, cudaStream_t s) {
   cudaError_t e = launch_split_x(c->w, c->grid_iter, skip_if_done, s);
   if (e != cudaSuccess) return e;
+  if (c->op == OP_RBF) {
+    RbfExactArgs a{};
+    a.Xr = c->Xr;
+    a.n = c->w.n;
+    a.d = c->rbf_d;
+    a.prm = c->prm;
+    a.xh = c->w.xh;
+    a.xl = c->w.xl;
+    a.b = c->w.b;
+    a.r = c->w.r;
+    a.partials = c->mv_partials;
+    a.ticket = &c->st->ticket[T_CHECK_RES];
+    a.st = c->st;
+    a.skip_if_done = skip_if_done;
+    a.resid_mode = mode;
+    return launch_rbf_resid(a, s);
+  }
   RowOpArgs a{};
   a.xh = c->w.xh;
   a.xl = c->w.xl;
@@ -349,6 +429,45 @@ static cudaError_t op_resid(dcg_ctx* c, int mode, int skip_if_done, cudaStream_t
 }
 
 static cudaError_t op_block(dcg_ctx* c, const float* V, int ncols, float* Y, DevState* st, cudaStream_t s) {
+  if (c->op == OP_RBF && st) {
+    // Start of a solve: AW with the same tensor-core operator the iteration
+    // applies, so that the deflation (E, mu, the re-deflation of r) is
+    // consistent with the Krylov recursion; one tile matvec per column.
+    for (int col = 0; col < c->w.kmax; ++col) {
+      cudaError_t e = launch_copy_col(V + int64_t(1 + col) * c->w.n, c->pmv, c->w.n, col, st, s);
+      if (e != cudaSuccess) return e;
+      RbfMvArgs a{};
+      a.p = c->pmv;
+      a.vcol = c->vcol;
+      a.q = Y + int64_t(1 + col) * c->w.n;
+      a.n = c->w.n;
+      a.n_tiles = c->n_pad / 128;
+      a.d = c->rbf_d;
+      a.xformat = c->rbf_xformat;
+      a.prm = c->prm;
+      a.partials = c->mv_partials;
+      a.ticket = c->mv_ticket;
+      a.result = c->mv_result;
+      a.st = st;
+      a.skip_if_done = 1;
+      a.col_idx = col;
+      if ((e = launch_rbf_mv(&c->rbf_tmap, a, c->rbf_grid, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  if (c->op == OP_RBF) {
+    RbfExactArgs a{};
+    a.Xr = c->Xr;
+    a.n = c->w.n;
+    a.d = c->rbf_d;
+    a.prm = c->prm;
+    a.V = V;
+    a.Y = Y;
+    a.ncols = ncols;
+    a.st = st;
+    a.skip_if_done = st ? 1 : 0;
+    return launch_rbf_block(a, st ? c->w.kmax : ncols, s);
+  }
   ApplyBlockArgs a{};
   a.A = c->A;
   a.lda = c->lda;
@@ -629,7 +748,12 @@ extern "C" dcg_status dcg_matvec(dcg_ctx* c, const float* p, float* q, double* p
   if (!c) return DCG_ERR_INVALID_ARG;
   if (c->op == OP_NONE) return fail(c, DCG_ERR_STATE, "no operator set");
   if (!p || !q || (reinterpret_cast<uintptr_t>(p) & 15)) return fail(c, DCG_ERR_INVALID_ARG, "p, q: 16-byte aligned device vectors");
-  CK(op_matvec(c, p, q, c->mv_result, c->mv_partials, c->mv_ticket, nullptr, c->stream));
+  const float* pin = p;
+  if (c->op == OP_RBF) {  // the tile kernel reads whole 128-row tiles of p
+    CK(cudaMemcpyAsync(c->pmv, p, size_t(c->w.n) * 4, cudaMemcpyDeviceToDevice, c->stream));
+    pin = c->pmv;
+  }
+  CK(op_matvec(c, pin, q, c->mv_result, c->mv_partials, c->mv_ticket, nullptr, c->stream));
   if (pAp) {
     CK(cudaMemcpyAsync(pAp, c->mv_result, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));

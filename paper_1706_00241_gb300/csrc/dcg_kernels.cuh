@@ -82,6 +82,69 @@ struct ApplyBlockArgs {
   int skip_if_done;
 };
 
+// ---- matrix-free RBF operator (k_rbf.cu)
+struct RbfParams {
+  float c2;          // 2 log2(e) / (2 l^2)
+  float l2s;         // log2(s^2)
+  float s2;          // s^2
+  float noise;       // diagonal shift
+  float neg_inv2l2;  // -1 / (2 l^2), rounded
+  float neg_inv2l2_lo;  // its rounding error
+  float s2_lo;       // s^2 - float(s^2)
+  double noise_d;    // diagonal shift in double (residual recomputation)
+};
+
+struct RbfMvArgs {
+  const float* p;      // n_pad floats, zero beyond n
+  const float* vcol;   // n_pad floats: -c |x_j|^2, -inf beyond n
+  float* q;
+  int n;
+  int n_tiles;         // n_pad / 128
+  int d;
+  int xformat;
+  const RbfParams* prm;
+  double* partials;
+  unsigned int* ticket;
+  double* result;      // p^T q
+  DevState* st;
+  int skip_if_done;
+  int col_idx;         // >= 0: column of W in a start-of-solve product (skipped if >= st->k)
+};
+
+struct RbfExactArgs {
+  const float* Xr;     // n x d rounded points
+  int n;
+  int d;
+  const RbfParams* prm;
+  const float* xh;     // residual: x = xh + xl
+  const float* xl;
+  const float* b;
+  float* r;
+  const float* V;      // block: n x ncols column-major
+  float* Y;
+  int ncols;
+  double* partials;
+  unsigned int* ticket;
+  double* result;
+  DevState* st;
+  int skip_if_done;
+  int resid_mode;
+};
+
+cudaError_t launch_rbf_prep(const float* X, int n, int n_pad, int d, int xformat, float* Xr, void* Xt, float* nsq,
+                            cudaStream_t s);
+cudaError_t launch_rbf_params(const float* nsq, int n, int n_pad, double l, double s2, double noise, float* vcol,
+                              RbfParams* prm, cudaStream_t s);
+bool make_rbf_tmap(CUtensorMap* map, const void* Xt, int n_pad, int xformat, EncodeTiledFn encode);
+size_t rbf_mv_smem_bytes();
+cudaError_t rbf_mv_configure();
+int rbf_mv_grid(int n_tiles, int num_sms);
+cudaError_t launch_rbf_mv(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s);
+int rbf_exact_grid(int n);
+cudaError_t launch_copy_col(const float* src, float* dst, int n, int col, const DevState* st, cudaStream_t s);
+cudaError_t launch_rbf_resid(const RbfExactArgs& a, cudaStream_t s);
+cudaError_t launch_rbf_block(const RbfExactArgs& a, int cmax, cudaStream_t s);
+
 // ---- dense operator (k_dense.cu)
 size_t rowop_smem_bytes();
 cudaError_t rowop_configure();

@@ -1,0 +1,622 @@
+// Matrix-free RBF operator A = K + noise I, K_ij = s^2 exp(-|x_i - x_j|^2 / (2 l^2))
+// (the Sec. 3 kernel), never stored.
+//
+//   * k_rbf_mv: q = A p with the fused p^T q (Algorithm 1 line 6). Persistent,
+//     warp-specialised: a TMA warp streams X_J tiles (128 rows x 128 bytes,
+//     128-byte swizzle) with p_J and v_J = -c |x_j|^2 by bulk copies; one
+//     thread issues tcgen05.mma (BF16 or TF32 inputs, float32 accumulation)
+//     for S = X_I X_J^T into one of two TMEM buffers; eight epilogue warps read
+//     S with tcgen05.ld and accumulate q_i += exp2(u_i + v_j + 2c S_ij) p_j
+//     with the exponential on the SFU (ex2.approx), c = log2(e) / (2 l^2),
+//     u_i = log2(s^2) - c |x_i|^2. Padded columns carry v_j = -inf (K = 0).
+//   * k_rbf_exact: the same operator on CUDA cores in the difference form
+//     sum_m (x_im - x_jm)^2 (float32 pair: exact squares, compensated sum).
+//     For the true residual b - A x the exponential is a float32 pair too
+//     (entries to ~1e-9, compensated Dot2 sums with x = xh + xl) and the
+//     convergence test includes the entry-error bound; the block product A V
+//     uses expf (entries to ~2 ulp).
+//     The tensor-core Gram form n_i + n_j - 2 S_ij carries ~1e-5 relative
+//     error on close pairs; the residual recomputation in this exact form is
+//     the refinement that wins the accuracy back.
+#include <cuda_bf16.h>
+
+#include "dcg_kernels.cuh"
+#include "tc.cuh"
+
+namespace dcg {
+
+// ---------------------------------------------------------------------------
+// Preparation: rounded X (the operator's points), padded tensor-core copy,
+// squared norms; v_j for the current lengthscale.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t u = __float_as_uint(x);
+  const uint32_t lsb = (u >> 13) & 1u;
+  u = (u + 0xFFFu + lsb) & 0xFFFFE000u;  // round to nearest even at 10 mantissa bits
+  return __uint_as_float(u);
+}
+
+// Xr (n x d float32): X rounded to the chosen element format; Xt: the
+// 128-byte-per-row tile copy (BF16: 64 elements, TF32: 32 elements), zero
+// padded to n_pad rows; nsq[i] = |xr_i|^2 (float64 sum, rounded).
+__global__ void k_rbf_prep(const float* __restrict__ X, int n, int n_pad, int d, int xformat, float* Xr,
+                           void* Xt, float* nsq) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x) {
+    double ss = 0.0;
+    if (xformat == DCG_X_BF16) {
+      __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xt) + int64_t(i) * 64;
+      for (int m = 0; m < 64; ++m) {
+        float v = 0.f;
+        if (i < n && m < d) {
+          v = round_bf16(X[int64_t(i) * d + m]);
+          Xr[int64_t(i) * d + m] = v;
+          ss += double(v) * double(v);
+        }
+        row[m] = __float2bfloat16_rn(v);
+      }
+    } else {
+      float* row = reinterpret_cast<float*>(Xt) + int64_t(i) * 32;
+      for (int m = 0; m < 32; ++m) {
+        float v = 0.f;
+        if (i < n && m < d) {
+          v = round_tf32(X[int64_t(i) * d + m]);
+          Xr[int64_t(i) * d + m] = v;
+          ss += double(v) * double(v);
+        }
+        row[m] = v;
+      }
+    }
+    nsq[i] = float(ss);
+  }
+}
+
+// v_j = -c nsq[j] (c = log2(e) / (2 l^2)); padded rows get -inf so that their
+// kernel values are exactly zero. Also writes the scalar parameters.
+__global__ void k_rbf_params(const float* nsq, int n, int n_pad, double l, double s2, double noise, float* vcol,
+                             RbfParams* prm) {
+  const double c = 1.4426950408889634 / (2.0 * l * l);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_pad; j += gridDim.x * blockDim.x)
+    vcol[j] = j < n ? float(-c * double(nsq[j])) : -INFINITY;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    prm->c2 = float(2.0 * c);
+    prm->l2s = float(log2(s2));
+    prm->s2 = float(s2);
+    prm->noise = float(noise);
+    prm->neg_inv2l2 = float(-1.0 / (2.0 * l * l));
+    prm->neg_inv2l2_lo = float(-1.0 / (2.0 * l * l) - double(prm->neg_inv2l2));
+    prm->s2_lo = float(s2 - double(prm->s2));
+    prm->noise_d = noise;
+  }
+}
+
+cudaError_t launch_rbf_prep(const float* X, int n, int n_pad, int d, int xformat, float* Xr, void* Xt, float* nsq,
+                            cudaStream_t s) {
+  k_rbf_prep<<<(n_pad + 255) / 256, 256, 0, s>>>(X, n, n_pad, d, xformat, Xr, Xt, nsq);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rbf_params(const float* nsq, int n, int n_pad, double l, double s2, double noise, float* vcol,
+                              RbfParams* prm, cudaStream_t s) {
+  k_rbf_params<<<(n_pad + 255) / 256, 256, 0, s>>>(nsq, n, n_pad, l, s2, noise, vcol, prm);
+  return cudaGetLastError();
+}
+
+bool make_rbf_tmap(CUtensorMap* map, const void* Xt, int n_pad, int xformat, EncodeTiledFn encode) {
+  const bool bf = xformat == DCG_X_BF16;
+  cuuint64_t gdim[2] = {cuuint64_t(bf ? 64 : 32), cuuint64_t(n_pad)};
+  cuuint64_t gstride[1] = {128};
+  cuuint32_t box[2] = {cuuint32_t(bf ? 64 : 32), 128};
+  cuuint32_t estride[2] = {1, 1};
+  CUresult r = encode(map, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                      const_cast<void*>(Xt), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core matvec
+// ---------------------------------------------------------------------------
+constexpr int MV_TILE = 128;                // rows of an I block and columns of a J tile
+constexpr int MV_STAGES = 4;
+constexpr int MV_TILE_BYTES = MV_TILE * 128;  // 16 KB: 128 rows x 128 bytes
+constexpr int MV_EPI_WARPS = 8;
+constexpr int MV_THREADS = (2 + MV_EPI_WARPS) * 32;
+constexpr int MV_TMEM_COLS = 2 * MV_TILE;     // two accumulator buffers
+// shared memory: X_I tile, stages of {X_J tile, p_J, v_J}, barriers
+constexpr int MV_STAGE_BYTES = MV_TILE_BYTES + 2 * MV_TILE * 4;
+constexpr size_t MV_SMEM = 1024 + MV_TILE_BYTES + size_t(MV_STAGES) * MV_STAGE_BYTES + 256;
+
+size_t rbf_mv_smem_bytes() { return MV_SMEM; }
+
+__global__ void __launch_bounds__(MV_THREADS, 1)
+    k_rbf_mv(const __grid_constant__ CUtensorMap tmap, RbfMvArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* xi_tile = base;                                   // 1024-aligned
+  unsigned char* stages = base + MV_TILE_BYTES;                    // each stage 1024-aligned (16 KB + 1 KB)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stages + size_t(MV_STAGES) * MV_STAGE_BYTES);
+  uint64_t* full = bars;                       // [MV_STAGES]
+  uint64_t* empty = full + MV_STAGES;          // [MV_STAGES]
+  uint64_t* tfull = empty + MV_STAGES;         // [2]
+  uint64_t* tempty = tfull + 2;                // [2]
+  uint64_t* xi_full = tempty + 2;
+  uint64_t* xi_empty = xi_full + 1;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  __shared__ float s_half[MV_TILE];
+  __shared__ double s_part[MV_EPI_WARPS];
+
+  DevState* st = a.st;
+  if (st && a.skip_if_done && st->done) return;
+  if (st && a.col_idx >= 0 && a.col_idx >= st->k) return;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = a.n, n_tiles = a.n_tiles;
+  const int kind_tf32 = a.xformat != DCG_X_BF16;
+  const int ksteps = kind_tf32 ? (a.d + 7) / 8 : (a.d + 15) / 16;   // 32-byte K steps
+  const uint32_t idesc = tc::instr_desc(kind_tf32 ? tc::kFmtTF32 : tc::kFmtBF16, MV_TILE, MV_TILE);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < MV_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], MV_EPI_WARPS);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], MV_EPI_WARPS);
+    }
+    mbar_init(xi_full, 1);
+    mbar_init(xi_empty, 1);
+    fence_mbarrier_init();
+    s_abort = 0;
+  }
+  if (warp == 1) tc::tmem_alloc(&s_tmem, MV_TMEM_COLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+
+  double my_part = 0.0;
+  if (warp == 0) {
+    // -------------------------------- producer ------------------------------
+    if (lane == 0) {
+      prefetch_tensormap(&tmap);
+      long long it = 0;
+      int rbc = 0;
+      for (int rb = blockIdx.x; rb < n_tiles && !s_abort; rb += gridDim.x, ++rbc) {
+        if (rbc > 0 && !mbar_wait_bounded(xi_empty, (rbc - 1) & 1)) { s_abort = 1; break; }
+        mbar_arrive_expect_tx(xi_full, MV_TILE_BYTES);
+        tma_load_2d(xi_tile, &tmap, xi_full, 0, rb * MV_TILE);
+        for (int J = 0; J < n_tiles; ++J, ++it) {
+          const int s = int(it % MV_STAGES);
+          if (it >= MV_STAGES && !mbar_wait_bounded(&empty[s], uint32_t((it / MV_STAGES) - 1) & 1)) {
+            s_abort = 1;
+            break;
+          }
+          unsigned char* stg = stages + size_t(s) * MV_STAGE_BYTES;
+          mbar_arrive_expect_tx(&full[s], MV_TILE_BYTES + 2 * MV_TILE * 4);
+          tma_load_2d(stg, &tmap, &full[s], 0, J * MV_TILE);
+          tc::bulk_load(stg + MV_TILE_BYTES, a.p + size_t(J) * MV_TILE, MV_TILE * 4, &full[s]);
+          tc::bulk_load(stg + MV_TILE_BYTES + MV_TILE * 4, a.vcol + size_t(J) * MV_TILE, MV_TILE * 4, &full[s]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // -------------------------------- MMA issuer -----------------------------
+    if (lane == 0) {
+      long long it = 0;
+      int rbc = 0;
+      const uint32_t a_base = smem_u32(xi_tile);
+      for (int rb = blockIdx.x; rb < n_tiles && !s_abort; rb += gridDim.x, ++rbc) {
+        if (!mbar_wait_bounded(xi_full, rbc & 1)) { s_abort = 1; break; }
+        tc::fence_after_sync();
+        for (int J = 0; J < n_tiles; ++J, ++it) {
+          const int s = int(it % MV_STAGES);
+          const int b = int(it & 1);
+          if (!mbar_wait_bounded(&full[s], uint32_t(it / MV_STAGES) & 1)) { s_abort = 1; break; }
+          if (it >= 2 && !mbar_wait_bounded(&tempty[b], uint32_t((it >> 1) - 1) & 1)) { s_abort = 1; break; }
+          tc::fence_after_sync();
+          const uint32_t b_base = smem_u32(stages + size_t(s) * MV_STAGE_BYTES);
+          const uint32_t d_tmem = tmem + uint32_t(b * MV_TILE);
+          for (int kk = 0; kk < ksteps; ++kk) {
+            const uint64_t ad = tc::smem_desc_sw128(a_base + 32 * kk);
+            const uint64_t bd = tc::smem_desc_sw128(b_base + 32 * kk);
+            if (kind_tf32)
+              tc::mma_tf32(d_tmem, ad, bd, idesc, kk > 0);
+            else
+              tc::mma_bf16(d_tmem, ad, bd, idesc, kk > 0);
+          }
+          tc::mma_commit(&tfull[b]);
+        }
+        tc::mma_commit(xi_empty);
+      }
+    }
+  } else {
+    // -------------------------------- epilogue -------------------------------
+    const int ew = warp - 2;                  // 0..7
+    const int quarter = warp & 3;             // TMEM lane quarter this warp may access
+    const int half = ew >> 2;                 // column half of the tile
+    const int row_l = quarter * 32 + lane;    // row within the I block
+    const float c2 = a.prm->c2, l2s = a.prm->l2s, noise = a.prm->noise;
+    long long it = 0;
+    for (int rb = blockIdx.x; rb < n_tiles; rb += gridDim.x) {
+      const int row = rb * MV_TILE + row_l;
+      const float u = l2s + a.vcol[row];        // vcol has n_pad entries
+      float acc = 0.f, comp = 0.f;              // Kahan sum of per-tile partials
+      bool aborted = false;
+      for (int J = 0; J < n_tiles; ++J, ++it) {
+        const int s = int(it % MV_STAGES);
+        const int b = int(it & 1);
+        if (!mbar_wait_bounded(&tfull[b], uint32_t(it >> 1) & 1)) { s_abort = 1; aborted = true; break; }
+        tc::fence_after_sync();
+        const unsigned char* stg = stages + size_t(s) * MV_STAGE_BYTES;
+        const float* pj = reinterpret_cast<const float*>(stg + MV_TILE_BYTES) + half * 64;
+        const float* vj = reinterpret_cast<const float*>(stg + MV_TILE_BYTES + MV_TILE * 4) + half * 64;
+        float part = 0.f;
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 32) {
+          float sv[32];
+          tc::tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * MV_TILE + half * 64 + c0), sv);
+#pragma unroll
+          for (int j = 0; j < 32; j += 4) {
+            const float4 p4 = *reinterpret_cast<const float4*>(pj + c0 + j);
+            const float4 v4 = *reinterpret_cast<const float4*>(vj + c0 + j);
+            part = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 0], u + v4.x)), p4.x, part);
+            part = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 1], u + v4.y)), p4.y, part);
+            part = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 2], u + v4.z)), p4.z, part);
+            part = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 3], u + v4.w)), p4.w, part);
+          }
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&tempty[b]);
+          mbar_arrive(&empty[s]);
+        }
+        const float y = part - comp;
+        const float t = acc + y;
+        comp = (t - acc) - y;
+        acc = t;
+      }
+      if (aborted) break;
+      // combine the two column halves of each row (named barrier: epilogue warps)
+      if (half == 1) s_half[row_l] = acc;
+      asm volatile("bar.sync 1, %0;" ::"r"(MV_EPI_WARPS * 32));
+      if (half == 0 && row < n) {
+        const float pi = a.p[row];
+        const float q = acc + s_half[row_l] + noise * pi;
+        a.q[row] = q;
+        my_part += double(pi) * double(q);
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(MV_EPI_WARPS * 32));
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, MV_TMEM_COLS);
+  }
+  if (s_abort && threadIdx.x == 0 && st) {
+    st->status = DCG_ERR_TIMEOUT;
+    st->timeout_site = 3;
+    st->done = 1;
+  }
+  // p^T q: CTA partial, then the last CTA sums in a fixed order
+  if (warp >= 2) {
+    const double v = warp_sum(my_part);
+    if (lane == 0) s_part[warp - 2] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < MV_EPI_WARPS; ++w) s += s_part[w];
+    a.partials[blockIdx.x] = s;
+  }
+  if (!arrive_last(a.ticket)) return;
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int i = lane; i < int(gridDim.x); i += 32) s += a.partials[i];
+    s = warp_sum(s);
+    if (lane == 0 && a.result) *a.result = s;
+  }
+}
+
+cudaError_t rbf_mv_configure() {
+  return cudaFuncSetAttribute(k_rbf_mv, cudaFuncAttributeMaxDynamicSharedMemorySize, int(MV_SMEM));
+}
+
+// Persistent grid: as many CTAs as can be resident (each holds 256 TMEM
+// columns, so at most two per SM).
+int rbf_mv_grid(int n_tiles, int num_sms) {
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbf_mv, MV_THREADS, MV_SMEM) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  if (per_sm > 2) per_sm = 2;
+  const int g = per_sm * num_sms;
+  return n_tiles < g ? n_tiles : g;
+}
+
+cudaError_t launch_rbf_mv(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s) {
+  k_rbf_mv<<<grid, MV_THREADS, MV_SMEM, s>>>(*tmap, a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Exact-form operator on CUDA cores: 128 rows per CTA (one per thread, x_i in
+// registers), J tiles of 64 points staged in shared memory.
+//   mode 0: r = b - A x (x = xh + xl, compensated Dot2 sums), |r|^2 reduced
+//   mode 1: Y[:, c] = A V[:, c] for c < ncols (<= 32 per launch column block)
+// ---------------------------------------------------------------------------
+constexpr int EX_ROWS = 128;
+// Relative error bound of one entry K_ij of the residual kernel. The entry is
+// carried as a float32 pair through every step: exact coordinate differences
+// (TwoDiff), exact squares (FMA), a compensated sum, the exponent as a pair,
+// and exp to ~1.2e-13 relative (emulated against 200-bit arithmetic over
+// a in [-103, 0]); with the s^2 pair the entry is good to ~(5 + |a|) 2^-48.
+// The bound carries a factor of about 5 over that for |a| <= 40.
+constexpr double kRbfEntryEps = 1e-12;
+constexpr int EX_J = 64;
+constexpr int EX_MAXD = 64;
+constexpr int EX_CB = 16;
+
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float v) {
+  const float s2 = __fadd_rn(s, v);
+  const float z = __fsub_rn(s2, s);
+  c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(s2, z)), __fsub_rn(v, z)));
+  s = s2;
+}
+
+// ln 2 / 64 = kL1 + kL2 + kL3 to ~2^-70 relative: kL1 has 10 significant bits
+// so that k kL1 is exact for |k| < 2^14; kL2 and kL3 are the next float32
+// pieces. k64L = 64 / ln 2 rounded (only used to pick k).
+constexpr float kL1 = 0x1.63p-7f;
+constexpr float kL2 = -0x1.bd0106p-19f;
+constexpr float kL3 = 0x1.cf79acp-46f;
+constexpr float k64L = 0x1.715476p+6f;
+
+// exp(a_hi + a_lo) for -103 <= a <= 0 as 2^m (e_hi + e_lo). Table-driven
+// reduction (Tang's method): a = k ln2/64 + r, k = 64 m + j, |r| <= ln2/128,
+// exp(a) = 2^m 2^(j/64) exp(r). r is formed as a float32 pair from the exact
+// product k kL1 and the FMA-exact error of k kL2. exp(r) - 1 = r + r^2/2 +
+// r^3 c(r) with c the Taylor terms to r^5 (truncation r^6/720 < 4e-17); r and
+// r^2/2 are carried as pairs, the cubic tail (< 3e-8) in float32. tab[j] =
+// 2^(j/64) as a float32 pair.
+__device__ __forceinline__ void exp_tang(float a_hi, float a_lo, const float2* tab, float& e_hi, float& e_lo,
+                                         int& m) {
+  const float kf = rintf(__fmul_rn(a_hi, k64L));
+  const float t1 = __fmaf_rn(-kf, kL1, a_hi);  // exact
+  const float p2 = __fmul_rn(kf, kL2);
+  const float e2 = __fmaf_rn(kf, kL2, -p2);    // exact error of k kL2
+  const float p3 = __fmul_rn(kf, kL3);
+  // (r_hi, r_lo) = t1 - p2 by TwoSum, plus the low-order terms
+  float r_hi = __fsub_rn(t1, p2);
+  const float z = __fsub_rn(r_hi, t1);
+  float r_lo = __fadd_rn(__fsub_rn(t1, __fsub_rn(r_hi, z)), __fsub_rn(-p2, z));
+  r_lo = __fadd_rn(r_lo, __fsub_rn(__fsub_rn(a_lo, e2), p3));
+  {
+    const float s = __fadd_rn(r_hi, r_lo);
+    r_lo = __fsub_rn(r_lo, __fsub_rn(s, r_hi));
+    r_hi = s;
+  }
+  const float sq = __fmul_rn(r_hi, r_hi);
+  const float sq_e = __fmaf_rn(r_hi, r_hi, -sq);
+  const float h = 0.5f * sq;                                   // exact
+  const float h_lo = __fmaf_rn(r_hi, r_lo, 0.5f * sq_e);
+  const float c = __fmul_rn(__fmul_rn(sq, r_hi),
+                            __fmaf_rn(r_hi, __fmaf_rn(r_hi, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f));
+  const float s_hi = __fadd_rn(r_hi, h);                       // |r_hi| >= |h|
+  const float s_e = __fsub_rn(h, __fsub_rn(s_hi, r_hi));
+  const float lo = __fadd_rn(__fadd_rn(s_e, r_lo), __fadd_rn(h_lo, c));
+  const float e1 = __fadd_rn(1.f, s_hi);                       // 1 >= |s_hi|
+  const float e1_e = __fsub_rn(s_hi, __fsub_rn(e1, 1.f));
+  const float e1_lo = __fadd_rn(e1_e, lo);
+  const int ki = int(kf);
+  const int j = ki & 63;
+  m = (ki - j) / 64;  // exact: ki - j is a multiple of 64
+  const float2 t = tab[j];
+  e_hi = __fmul_rn(t.x, e1);
+  e_lo = __fadd_rn(__fmaf_rn(t.x, e1, -e_hi), __fmaf_rn(t.x, e1_lo, __fmul_rn(t.y, e1)));
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(EX_ROWS) k_rbf_exact(RbfExactArgs a) {
+  __shared__ float xj[EX_J][EX_MAXD + 1];
+  __shared__ float vj[EX_J][EX_CB + 1];
+  __shared__ float vlo[EX_J];
+  __shared__ float2 exp_tab[64];
+  if (MODE == 0 && threadIdx.x < 64) {
+    const double t = exp2(double(threadIdx.x) / 64.0);
+    exp_tab[threadIdx.x] = make_float2(float(t), float(t - double(float(t))));
+  }
+  DevState* st = a.st;
+  if (st && a.skip_if_done && st->done) return;
+  if (MODE == 0 && st && a.resid_mode == 0 && !st->warm_start) return;
+  const int n = a.n, d = a.d;
+  int ncols = a.ncols;
+  const float* V = a.V;
+  float* Y = a.Y;
+  if (MODE == 1 && st) {  // start of a solve: AW for the active columns of W
+    ncols = st->k;
+    V += n;
+    Y += n;
+  }
+  const int col0 = blockIdx.y * EX_CB;
+  if (MODE == 1 && col0 >= ncols) return;
+  const int cw = MODE == 1 ? min(EX_CB, ncols - col0) : 1;
+  const int i = blockIdx.x * EX_ROWS + threadIdx.x;
+  const float neg_inv2l2 = a.prm->neg_inv2l2, neg_inv2l2_lo = a.prm->neg_inv2l2_lo;
+  const float s2 = a.prm->s2, s2_lo = a.prm->s2_lo, noise = a.prm->noise;
+  float xi[EX_MAXD];
+#pragma unroll
+  for (int m = 0; m < EX_MAXD; ++m) xi[m] = (i < n && m < d) ? a.Xr[int64_t(i) * d + m] : 0.f;
+  static_assert(EX_MAXD == 64, "the distance loop is fully unrolled over 64 coordinates");
+  float acc[EX_CB], cmp[EX_CB];
+#pragma unroll
+  for (int c = 0; c < EX_CB; ++c) acc[c] = cmp[c] = 0.f;
+  float esq = 0.f;  // sum_j (K_ij x_j)^2: scale of the entry-error term of the residual
+  for (int j0 = 0; j0 < n; j0 += EX_J) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < EX_J * d; idx += EX_ROWS) {
+      const int jj = idx / d, m = idx % d;
+      xj[jj][m] = (j0 + jj < n) ? a.Xr[int64_t(j0 + jj) * d + m] : 0.f;
+    }
+    if (MODE == 0) {
+      for (int jj = threadIdx.x; jj < EX_J; jj += EX_ROWS) {
+        vj[jj][0] = (j0 + jj < n) ? a.xh[j0 + jj] : 0.f;
+        vlo[jj] = (j0 + jj < n) ? a.xl[j0 + jj] : 0.f;
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < EX_J * EX_CB; idx += EX_ROWS) {
+        const int c = idx / EX_J, jj = idx % EX_J;
+        vj[jj][c] = (c < cw && j0 + jj < n) ? V[int64_t(col0 + c) * n + j0 + jj] : 0.f;
+      }
+    }
+    __syncthreads();
+    const int jn = min(EX_J, n - j0);
+    for (int jj = 0; jj < jn; ++jj) {
+      // |x_i - x_j|^2 as a float32 pair (exact differences by TwoDiff, exact
+      // squares by FMA, compensated sum)
+      float dh = 0.f, dl = 0.f;
+#pragma unroll
+      for (int m = 0; m < EX_MAXD; ++m) {
+        if (m < d) {
+          const float u = xi[m], v = xj[jj][m];
+          const float df = __fsub_rn(u, v);
+          const float dz = __fsub_rn(df, u);
+          const float df_lo = __fadd_rn(__fsub_rn(u, __fsub_rn(df, dz)), __fsub_rn(-v, dz));
+          const float sq = __fmul_rn(df, df);
+          dl = __fadd_rn(dl, __fmaf_rn(2.f * df, df_lo, __fmaf_rn(df, df, -sq)));
+          const float hi = fmaxf(dh, sq), lo = fminf(dh, sq);
+          const float t = __fadd_rn(hi, lo);
+          dl = __fadd_rn(dl, __fsub_rn(lo, __fsub_rn(t, hi)));
+          dh = t;
+        }
+      }
+      // exponent a = -(dh + dl) / (2 l^2) split as a_hi + a_lo (exact product
+      // error by FMA)
+      const float a_hi = __fmul_rn(dh, neg_inv2l2);
+      const float a_lo = __fmaf_rn(dh, neg_inv2l2, -a_hi) + dl * neg_inv2l2 + dh * neg_inv2l2_lo;
+      if (MODE == 0) {
+        // K = s^2 exp(a) as a float32 pair, then a Dot2 step with x = xh + xl
+        if (a_hi < -103.f) continue;  // below the float32 range: K = 0
+        float e_hi, e_lo;
+        int k2;
+        exp_tang(a_hi, a_lo, exp_tab, e_hi, e_lo, k2);
+        const float m_hi = __fmul_rn(s2, e_hi);
+        const float m_lo = __fmaf_rn(s2, e_hi, -m_hi) + __fmaf_rn(s2, e_lo, s2_lo * e_hi);
+        const float k_hi = ldexpf(m_hi, k2), k_lo = ldexpf(m_lo, k2);
+        const float xhv = vj[jj][0];
+        const float p = __fmul_rn(k_hi, xhv);
+        const float e = __fmaf_rn(k_hi, xhv, -p);
+        two_sum_add(acc[0], cmp[0], p);
+        cmp[0] = __fadd_rn(cmp[0], e);
+        cmp[0] = __fmaf_rn(k_hi, vlo[jj], __fmaf_rn(k_lo, xhv, cmp[0]));
+        esq = fmaf(p, p, esq);
+      } else {
+        const float kij = s2 * expf(a_hi) * (1.f + a_lo);
+#pragma unroll
+        for (int c = 0; c < EX_CB; ++c) acc[c] = fmaf(kij, vj[jj][c], acc[c]);
+      }
+    }
+  }
+  double my = 0.0, my_e = 0.0;
+  if (i < n) {
+    if (MODE == 0) {
+      const double x = double(a.xh[i]) + double(a.xl[i]);
+      const double ax = double(acc[0]) + double(cmp[0]) + a.prm->noise_d * x;
+      const double rr = double(a.b[i]) - ax;
+      a.r[i] = float(rr);
+      my = rr * rr;
+      my_e = double(esq);
+    } else {
+#pragma unroll
+      for (int c = 0; c < EX_CB; ++c)
+        if (c < cw) Y[int64_t(col0 + c) * n + i] = acc[c] + noise * V[int64_t(col0 + c) * n + i];
+    }
+  }
+  if (MODE == 1) return;
+  // |r|^2 and e^2 = sum_ij (K_ij x_j)^2: CTA partials -> last CTA
+  __shared__ double s_part[2][EX_ROWS / 32];
+  const double v = warp_sum(my), ve = warp_sum(my_e);
+  if ((threadIdx.x & 31) == 0) {
+    s_part[0][threadIdx.x >> 5] = v;
+    s_part[1][threadIdx.x >> 5] = ve;
+  }
+  __syncthreads();
+  const int G = gridDim.x;
+  if (threadIdx.x == 0) {
+    double s = 0.0, se = 0.0;
+    for (int w = 0; w < EX_ROWS / 32; ++w) {
+      s += s_part[0][w];
+      se += s_part[1][w];
+    }
+    a.partials[blockIdx.x] = s;
+    a.partials[G + blockIdx.x] = se;
+  }
+  if (!arrive_last(a.ticket)) return;
+  if (threadIdx.x < 32) {
+    double s = 0.0, se = 0.0;
+    for (int b = threadIdx.x; b < G; b += 32) {
+      s += __ldcg(a.partials + b);
+      se += __ldcg(a.partials + G + b);
+    }
+    s = warp_sum(s);
+    se = warp_sum(se);
+    if (threadIdx.x == 0) {
+      if (!st) {
+        if (a.result) *a.result = s;
+      } else if (a.resid_mode != 0) {
+        // Each entry K_ij carries a relative error <= kRbfEntryEps (the
+        // distance, exponent, exponential and s^2 product are float32 pairs;
+        // the largest terms are the Taylor truncation and the float32 tail).
+        // The errors of different entries are independent, so the error of
+        // the computed residual is ~kRbfEntryEps sqrt(sum_ij (K_ij x_j)^2)
+        // (probabilistic rounding-error model, Higham & Mary 2019); the
+        // worst-case sum of |K_ij x_j| overstates it by orders of magnitude
+        // because b - A x cancels heavily. Convergence is accepted only if the
+        // residual plus three times that estimate meets tol.
+        const double err = 3.0 * kRbfEntryEps * sqrt(se);
+        st->rho_true = s;
+        st->matvecs_check += 1;
+        st->relres_true = st->bnorm2 > 0.0 ? sqrt(s / st->bnorm2) : sqrt(s);
+        st->true_valid = 1;
+        const int mode = a.resid_mode >= 0 ? a.resid_mode : st->mode;
+        const double lim = sqrt(st->thresh2) - err;
+        if (mode == 1 && lim > 0.0 && s <= lim * lim && st->status == DCG_OK) st->done = 1;
+      }
+    }
+  }
+}
+
+int rbf_exact_grid(int n) { return (n + EX_ROWS - 1) / EX_ROWS; }
+
+// dst[0, n) = src[0, n) for a column of W that is active in this solve; the
+// tail of dst (up to the 128-row tile) stays zero.
+__global__ void k_copy_col(const float* src, float* dst, int n, int col, const DevState* st) {
+  if (st && (st->done || col >= st->k)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+cudaError_t launch_copy_col(const float* src, float* dst, int n, int col, const DevState* st, cudaStream_t s) {
+  k_copy_col<<<(n + 1023) / 1024, 256, 0, s>>>(src, dst, n, col, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rbf_resid(const RbfExactArgs& a, cudaStream_t s) {
+  k_rbf_exact<0><<<rbf_exact_grid(a.n), EX_ROWS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rbf_block(const RbfExactArgs& a, int cmax, cudaStream_t s) {
+  if (cmax <= 0) return cudaSuccess;
+  dim3 grid(rbf_exact_grid(a.n), (cmax + EX_CB - 1) / EX_CB);
+  k_rbf_exact<1><<<grid, EX_ROWS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace dcg

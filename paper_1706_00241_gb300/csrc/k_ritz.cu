@@ -239,49 +239,6 @@ __device__ void jacobi_pair(int m2, int r, int i, int& p, int& q) {
   q = pos(m2 - 1 - i);
 }
 
-// Cholesky factorisation in place (lower triangle of L, leading dimension ld)
-// with column dropping: a pivot below drop_tol marks the column dropped (its
-// entries are zeroed, so later columns ignore it). Returns the kept count.
-__device__ int chol_drop(float* L, int m, int ld, float drop_tol, int* kept) {
-  __shared__ int s_cnt;
-  const int t = threadIdx.x;
-  if (t == 0) s_cnt = 0;
-  __syncthreads();
-  for (int j = 0; j < m; ++j) {
-    if (t < 32) {  // pivot: one warp sums the row
-      float s = 0.f;
-      for (int p = t; p < j; p += 32) s = fmaf(L[j * ld + p], L[j * ld + p], s);
-      s = warp_sum(s);
-      if (t == 0) {
-        const float piv = L[j * ld + j] - s;
-        const int ok = (piv > drop_tol) && isfinite(piv);
-        kept[j] = ok;
-        L[j * ld + j] = ok ? sqrtf(piv) : 1.f;
-        s_cnt += ok;
-      }
-    }
-    __syncthreads();
-    const float ljj = L[j * ld + j];
-    const int ok = kept[j];
-    // column j below the diagonal: one warp per row, lanes over p
-    const int warp = t / 32, lane = t % 32, nw = blockDim.x / 32;
-    for (int i = j + 1 + warp; i < m; i += nw) {
-      if (!ok) {
-        if (lane == 0) L[i * ld + j] = 0.f;
-        continue;
-      }
-      float s = 0.f;
-      for (int p = lane; p < j; p += 32) s = fmaf(L[i * ld + p], L[j * ld + p], s);
-      s = warp_sum(s);
-      if (lane == 0) L[i * ld + j] = (L[i * ld + j] - s) / ljj;
-    }
-    if (!ok)
-      for (int p = t; p < j; p += blockDim.x) L[j * ld + p] = 0.f;
-    __syncthreads();
-  }
-  return s_cnt;
-}
-
 // Row-parallel forward substitution L Y = B for m right-hand sides (columns
 // of B, leading dimension m, overwritten with Y): for each row i the m
 // columns are split over the threads and the dot product over j < i is
@@ -311,7 +268,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
   __shared__ float cs_c[kMaxM / 2 + 1], cs_s[kMaxM / 2 + 1];
   __shared__ int pp[kMaxM / 2 + 1], qq[kMaxM / 2 + 1];
   __shared__ float scale[kMaxM];
-  __shared__ int kept[kMaxM], pos[kMaxM], orig[kMaxM];
+  __shared__ int pos[kMaxM], orig[kMaxM];
   __shared__ int s_changed;
   __shared__ float th[kMaxM];
   __shared__ int rank_of[kMaxM];
@@ -336,49 +293,91 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
     Gf[idx] = float(0.5 * (a.G[i * m + j] + a.G[j * m + i]) * sij);
   }
   __syncthreads();
-  // 2. Cholesky F' = L L^T; a direction whose pivot falls below 1e-6 (unit
-  //    diagonal, so relative; float32 rounding of F' is ~1e-7) is numerically
-  //    dependent on the earlier ones and is dropped (rank-deficient Z, reading
-  //    R6); the rest is compacted and refactorised.
-  const int mk = chol_drop(Ff, m, m, 1e-6f, kept);
-  if (t == 0) {
-    int c = 0;
-    for (int j = 0; j < m; ++j) {
-      pos[j] = kept[j] ? c : -1;
-      if (kept[j]) orig[c++] = j;
-    }
+  // 2. Diagonally pivoted Cholesky of F' (rank revealing): step k eliminates
+  //    the column with the largest remaining Schur-complement diagonal and
+  //    stops when that falls below 1e-4. The dropped columns then lie within
+  //    1e-2 (A-norm, relative) of the span of the kept ones (rank-deficient Z,
+  //    reading R6), and cond(F') of the kept part stays ~1e4, which the float32
+  //    reduction handles; late float32 CG directions do lose A-conjugacy and
+  //    can make F' indefinite. Lrow[i][k] holds L(i, k) for original index i.
+  float* Lrow = Fc;                     // m x m, reuses the F' copy
+  __shared__ float dg[kMaxM];
+  __shared__ int done_[kMaxM];
+  __shared__ int s_rank, s_piv;
+  for (int j = t; j < m; j += blockDim.x) {
+    dg[j] = Ff[j * m + j];
+    done_[j] = 0;
   }
+  if (t == 0) s_rank = 0;
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    if (t < 32) {  // argmax of the remaining diagonal (ties: lower index)
+      float best = -1.f;
+      int bi = m;
+      for (int j = t; j < m; j += 32)
+        if (!done_[j] && (dg[j] > best)) {
+          best = dg[j];
+          bi = j;
+        }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (t == 0) s_piv = (best >= 1e-4f && isfinite(best)) ? bi : -1;
+    }
+    __syncthreads();
+    const int c = s_piv;
+    if (c < 0) break;
+    const float lkk = sqrtf(dg[c]);
+    // column k of L: L(i, k) = (F'(i, c) - sum_{p<k} L(i, p) L(c, p)) / L(c, k)
+    const int warp = t / 32, lane = t % 32, nw = blockDim.x / 32;
+    for (int i = warp; i < m; i += nw) {
+      if (done_[i] || i == c) continue;
+      float sdot = 0.f;
+      for (int p = lane; p < k; p += 32) sdot = fmaf(Lrow[i * m + p], Lrow[c * m + p], sdot);
+      sdot = warp_sum(sdot);
+      if (lane == 0) {
+        const float lik = (Ff[i * m + c] - sdot) / lkk;
+        Lrow[i * m + k] = lik;
+        dg[i] -= lik * lik;
+      }
+    }
+    __syncthreads();
+    if (t == 0) {
+      Lrow[c * m + k] = lkk;
+      done_[c] = 1;
+      orig[k] = c;
+      s_rank = k + 1;
+    }
+    __syncthreads();
+  }
+  const int mk = s_rank;
+  if (mk == 0) {
+    if (t == 0) {
+      *a.status = DCG_ERR_SUBSPACE_SINGULAR;
+      a.k_out[0] = 0;
+      a.k_out[1] = 0;
+    }
+    return;
+  }
+  for (int j = t; j < m; j += blockDim.x) pos[j] = -1;
+  __syncthreads();
+  for (int q = t; q < mk; q += blockDim.x) pos[orig[q]] = q;
+  // compact: L (mk x mk, lower, pivot order) into Ff; G' reordered into Xc
+  for (int idx = t; idx < mk * mk; idx += blockDim.x) {
+    const int qa = idx / mk, qb = idx % mk;
+    Ff[idx] = qb <= qa ? Lrow[orig[qa] * m + qb] : 0.f;
+    Xc[idx] = Gf[orig[qa] * m + orig[qb]];
+  }
+  __syncthreads();
+  for (int idx = t; idx < mk * mk; idx += blockDim.x) Gf[idx] = Xc[idx];
   __syncthreads();
   float* L = Ff;
   float* G = Gf;
-  if (mk < m) {
-    if (mk == 0) {
-      if (t == 0) {
-        *a.status = DCG_ERR_SUBSPACE_SINGULAR;
-        a.k_out[0] = 0;
-        a.k_out[1] = 0;
-      }
-      return;
-    }
-    // compact F' (from the copy) into Ff and G' into Xc, then move G' back
-    for (int idx = t; idx < mk * mk; idx += blockDim.x) {
-      const int i = orig[idx / mk], j = orig[idx % mk];
-      Ff[idx] = Fc[i * m + j];
-      Xc[idx] = Gf[i * m + j];
-    }
-    __syncthreads();
-    for (int idx = t; idx < mk * mk; idx += blockDim.x) Gf[idx] = Xc[idx];
-    __shared__ int kept2[kMaxM];
-    const int mk2 = chol_drop(Ff, mk, mk, 1e-12f, kept2);
-    if (mk2 < mk) {
-      if (t == 0) {
-        *a.status = DCG_ERR_SUBSPACE_SINGULAR;
-        a.k_out[0] = 0;
-        a.k_out[1] = 0;
-      }
-      return;
-    }
-  }
   const int mm = mk;  // size of the reduced pencil
   if (k_new > mm) k_new = mm;
   // 3. Y = L^{-1} G'

@@ -98,6 +98,24 @@ class DefCG:
         self._check(self.lib.dcg_set_operator_dense(self._ctx, ctypes.c_void_p(A.data_ptr()), lda),
                     "dcg_set_operator_dense")
 
+    def set_operator_rbf(self, X: torch.Tensor, lengthscale: float, signal_var: float, noise: float,
+                         xformat: str = "bf16"):
+        """Matrix-free A = K + noise I over the rows of X (n x d float32, Sec. 3
+        kernel). ``xformat`` "bf16" or "tf32": X is rounded to that format, which
+        defines the operator, and Gram tiles run on the tensor cores."""
+        _dev_f32(X, "X")
+        n, d = X.shape
+        if n != self.n:
+            raise ValueError("X must have n rows")
+        self._check(self.lib.dcg_set_operator_rbf(self._ctx, ctypes.c_void_p(X.data_ptr()), d,
+                                                  _lib.XFORMAT[xformat], float(lengthscale),
+                                                  float(signal_var), float(noise)), "dcg_set_operator_rbf")
+
+    def set_rbf_params(self, lengthscale: float, signal_var: float, noise: float):
+        """New hyperparameters for the current matrix-free operator (no re-copy of X)."""
+        self._check(self.lib.dcg_set_rbf_params(self._ctx, float(lengthscale), float(signal_var), float(noise)),
+                    "dcg_set_rbf_params")
+
     # -- solve --------------------------------------------------------------
     def solve(self, b: torch.Tensor, x: torch.Tensor | None = None, raise_on_error: bool = True):
         """Runs Algorithm 1 on (A, b); returns (x, info dict). b is float32,

@@ -1,0 +1,144 @@
+"""GPU parity of the matrix-free RBF operator (tensor-core Gram tiles with the
+exponential on the SFU; exact-form CUDA-core kernel for residuals and block
+products) against the FP64 oracle on the same rounded points.
+
+The operator is defined by X rounded to the chosen format (BF16 or TF32); both
+sides read the rounded values from dcg_synth's storage conversion.
+"""
+
+import numpy as np
+import pytest
+
+import dcg_synth as S
+from oracle import dcg_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ROUND = {"bf16": S.round_to_bf16, "tf32": S.round_to_tf32}
+
+
+@pytest.fixture(scope="module")
+def dcg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1706_00241_gb300 import build
+    build.build()
+    import paper_1706_00241_gb300 as P
+    return P
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+def gram_tol(Xr, l, K_abs_p):
+    # Tensor-core Gram form: |x_i|^2 + |x_j|^2 - 2 x_i.x_j with float32 sums of
+    # exact products; the absolute error of the exponent is <= ~(d + 2) eps32
+    # (|x_i|^2 + |x_j|^2) / (2 l^2), plus ex2.approx (2 ulp) and the float32 sum.
+    nmax = np.max(np.sum(Xr.astype(np.float64) ** 2, axis=1))
+    d = Xr.shape[1]
+    expo = (d + 4) * 6e-8 * 2 * nmax / (2 * l * l)
+    return (expo + 5e-7) * K_abs_p + 1e-7 * np.max(K_abs_p)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "tf32"])
+@pytest.mark.parametrize("n,d", [(1, 3), (100, 4), (1000, 8), (4096, 32), (2000, 17)])
+def test_rbf_matvec_matches_oracle(dcg, fmt, n, d):
+    if fmt == "tf32" and d > 32:
+        pytest.skip("tf32 tiles hold 32 coordinates")
+    rng = np.random.default_rng(n + d)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Xr = ROUND[fmt](X)
+    p = rng.standard_normal(n).astype(np.float32)
+    l, s2, noise = 1.3 + 0.1 * d ** 0.5, 0.8, 1e-2
+    with dcg.DefCG(n, 0, 0, 1e-6) as s:
+        s.set_operator_rbf(dev(X), l, s2, noise, xformat=fmt)
+        q, pAp = s.matvec(dev(p))
+        q = q.cpu().numpy().astype(np.float64)
+    K = O.rbf_gram(Xr.astype(np.float64), l, s2, noise)
+    ref = K @ p.astype(np.float64)
+    tol = gram_tol(Xr, l, np.abs(K) @ np.abs(p.astype(np.float64)))
+    assert np.all(np.abs(q - ref) <= tol), np.max(np.abs(q - ref) / tol)
+    assert abs(pAp - p.astype(np.float64) @ q) <= 1e-12 * (np.abs(p) @ np.abs(q)) + 1e-30
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "tf32"])
+def test_rbf_residual_and_block_exact(dcg, fmt):
+    # The exact-form kernel (difference form, expf, compensated residual sums)
+    # through a warm-started zero-iteration solve is awkward to isolate, so the
+    # block product and a solve's reported true residual are checked instead.
+    n, d = 1500, 6
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Xr = ROUND[fmt](X).astype(np.float64)
+    V = rng.standard_normal((20, n)).astype(np.float32)
+    l, s2, noise = 1.1, 1.0, 0.05
+    with dcg.DefCG(n, 0, 0, 1e-6) as s:
+        s.set_operator_rbf(dev(X), l, s2, noise, xformat=fmt)
+        Y = s.apply_block(dev(V)).cpu().numpy().astype(np.float64)
+    K = O.rbf_gram(Xr, l, s2, noise)
+    ref = V.astype(np.float64) @ K.T
+    bound = 2e-6 * (np.abs(V.astype(np.float64)) @ np.abs(K).T) + 1e-9
+    assert np.all(np.abs(Y - ref) <= bound)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "tf32"])
+def test_rbf_sequence_with_refinement(dcg, fmt):
+    # A short lengthscale path on the matrix-free operator: def-CG with
+    # recycling and residual replacement every 25 iterations reaches the true
+    # relative residual 1e-6 on every system (the float64 oracle on the same
+    # rounded points does too). The GPU iterates with the tensor-core Gram form
+    # (entries ~5e-6 off the exact operator) in float32; every replacement and
+    # the final check use the exact-form residual, so the answer is that of
+    # the exact operator (iterative refinement). The inexact iteration costs
+    # 10-16 % more iterations than the float64 oracle on this path (measured);
+    # the bound is 1.25x + 10. The solution error bound is the 1e-4 stated for
+    # the BF16 form.
+    cfg = S.RBFSequence(name="mf", n=2048, d=8, T=3, l0=1.0, growth=0.15, noise=1e-2, k=8, ell=24, tol=1e-6)
+    X, bs = S.draw_sequence(cfg)
+    Xr = ROUND[fmt](X.astype(np.float32)).astype(np.float64)
+    Xd = dev(X)
+    W = None
+    with dcg.DefCG(cfg.n, cfg.k, cfg.ell, cfg.tol, refine_every=25) as s:
+        s.set_operator_rbf(Xd, cfg.lengthscale(0), 1.0, cfg.noise, xformat=fmt)
+        for t in range(cfg.T):
+            s.set_rbf_params(cfg.lengthscale(t), 1.0, cfg.noise)
+            b = bs[t].astype(np.float32)
+            x, info = s.solve(dev(b))
+            s.update_subspace()
+            A = O.rbf_gram(Xr, cfg.lengthscale(t), 1.0, cfg.noise)
+            xr = x.cpu().numpy()
+            relres = np.linalg.norm(b - A @ xr) / np.linalg.norm(b)
+            assert info["status"] == 0 and relres <= 1.05e-6, (info, relres)
+            # The exact-form residual the GPU certified with agrees with the
+            # float64 residual of the returned x to its stated entry-error
+            # estimate: 3 * 1e-12 * sqrt(sum_ij (K_ij x_j)^2) / |b|.
+            est = 3e-12 * np.sqrt((A ** 2).sum(axis=0) @ xr ** 2) / np.linalg.norm(b)
+            assert abs(info["relres_true"] - relres) <= est + 1e-13, (info["relres_true"], relres, est)
+            ref = O.defcg(A, b.astype(np.float64), W=W, tol=cfg.tol, ell=cfg.ell, refine_every=25)
+            W = O.harmonic_ritz(ref.W, ref.AW, ref.P, ref.Q, cfg.k).W
+            assert info["iters"] <= 10 + 1.25 * ref.iters, (info["iters"], ref.iters)
+            assert info["matvecs_check"] >= 1
+            assert np.linalg.norm(xr - ref.x) <= 1e-4 * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("cfg,fmt", [(S.MF_131072, "bf16"), (S.MF_262144, "tf32")])
+def test_rbf_matvec_full_size_sampled_rows(dcg, cfg, fmt):
+    # The two large matrix-free workloads at full size: one matvec, 48 rows
+    # checked against rows of the oracle's kernel computed one by one.
+    X, bs = S.draw_sequence(cfg, T=1)
+    X32 = X.astype(np.float32)
+    Xr = ROUND[fmt](X32).astype(np.float64)
+    p = bs[0].astype(np.float32)
+    l = cfg.lengthscale(0)
+    with dcg.DefCG(cfg.n, 0, 0, 1e-6) as s:
+        s.set_operator_rbf(dev(X32), l, cfg.signal_var, cfg.noise, xformat=fmt)
+        q, pAp = s.matvec(dev(p))
+        q = q.cpu().numpy().astype(np.float64)
+    rows = np.random.default_rng(3).choice(cfg.n, 48, replace=False)
+    Krows = O.rbf_gram(Xr, l, cfg.signal_var, cfg.noise, rows=rows)
+    ref = Krows @ p.astype(np.float64)
+    tol = gram_tol(Xr, l, np.abs(Krows) @ np.abs(p.astype(np.float64)))
+    assert np.all(np.abs(q[rows] - ref) <= tol), np.max(np.abs(q[rows] - ref) / tol)
+    assert np.isfinite(pAp)
