@@ -106,8 +106,9 @@ typedef struct dcg_ctx dcg_ctx;
 const char* dcg_status_string(dcg_status s);
 
 /* Last error message of a context (empty string if none); ctx may be NULL,
- * in which case the message of the last failed dcg_create is returned. The
- * pointer stays valid until the next call on the context. */
+ * in which case the message of the last failed call made without a context
+ * (dcg_create, dcg_matvec_dense_noalloc) is returned. The pointer stays valid
+ * until the next call on the context. */
 const char* dcg_last_error(const dcg_ctx* ctx);
 
 /* ------------------------------------------------------------------------ */
@@ -233,6 +234,41 @@ dcg_status dcg_apply_block(dcg_ctx* ctx, const float* V, int32_t c, float* Y);
 
 /* Synchronises the context's stream. */
 dcg_status dcg_sync(dcg_ctx* ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Context-free matvec on fixed scratch (no device allocation)               */
+/* ------------------------------------------------------------------------ */
+
+/* q = A p and p^T q for a dense stored operator, without a context and
+ * without allocating device memory: the same kernel as dcg_matvec (the q = A p
+ * of Algorithm 1 line 6 with its fused p^T q), with the reduction scratch in
+ * a fixed array inside the library. The paper has no counterpart: there the
+ * matvec only runs inside a solve. It serves callers that hold no dcg context
+ * and may not allocate at the point of the call: code working inside another
+ * framework's device-memory budget (its caching allocator owns the free
+ * memory, so a cudaMalloc here could fail or fragment it), and loops that
+ * cannot afford the device-wide synchronisation that cudaMalloc and cudaFree
+ * may imply.
+ *   A      device, row-major float32 n x n with leading dimension lda
+ *          (lda >= n, lda % 4 == 0), 16-byte aligned. Read only.
+ *   n      1 <= n <= 2^30.
+ *   p      device, n floats, 16-byte aligned. Read only.
+ *   q      device, n floats. Written.
+ *   pAp    device, one double receiving p^T q, or NULL.
+ *   stream cudaStream_t as void*; everything runs on it, nothing synchronises.
+ * Scratch: a 4352-byte array in the library, per device: an arrival counter
+ * (cleared to zero on `stream` before every launch) and one double partial
+ * per CTA for at most 512 CTAs. The grid is min(ceil(n / 4), number of SMs);
+ * a device that would need more than 512 CTAs is rejected with UNSUPPORTED.
+ * The scratch address is looked up once per device (cudaGetSymbolAddress with
+ * that device current); make the first call on each device before any stream
+ * capture begins. All calls on a device share the scratch: calls that overlap
+ * in time (different streams, or host threads without ordering between them)
+ * race on it and give wrong results, so order them, e.g. on one stream.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA; the message is kept for
+ * dcg_last_error(NULL). */
+dcg_status dcg_matvec_dense_noalloc(const float* A, int64_t n, int64_t lda, const float* p, float* q,
+                                    double* pAp, void* stream);
 
 #ifdef __cplusplus
 }

@@ -9,4 +9,4 @@ Python binding (torch supplies device memory and streams).
 """
 
 from ._lib import DcgError, load  # noqa: F401
-from .solver import DefCG, form_rbf_dense  # noqa: F401
+from .solver import DefCG, form_rbf_dense, matvec_dense_noalloc  # noqa: F401

@@ -83,6 +83,7 @@ SIGNATURES = {
     "dcg_get_subspace": (_I32, [_P, _P, _PI32]),
     "dcg_get_history": (_I32, [_P, _PD, _I32, _PI32]),
     "dcg_matvec": (_I32, [_P, _P, _P, _PD]),
+    "dcg_matvec_dense_noalloc": (_I32, [_P, _I64, _I64, _P, _P, _P, _P]),
     "dcg_apply_block": (_I32, [_P, _P, _I32, _P]),
     "dcg_sync": (_I32, [_P]),
 }

@@ -356,6 +356,37 @@ extern "C" dcg_status dcg_form_rbf_dense(const float* X, int64_t n, int32_t d, d
   return e == cudaSuccess ? DCG_OK : DCG_ERR_CUDA;
 }
 
+// q = A p and p^T q for a dense operator with no context: the matvec kernel
+// of dcg_matvec on the library's fixed scratch instead of context buffers.
+extern "C" dcg_status dcg_matvec_dense_noalloc(const float* A, int64_t n, int64_t lda, const float* p, float* q,
+                                               double* pAp, void* stream) {
+  if (!A || !p || !q) return fail(nullptr, DCG_ERR_INVALID_ARG, "dcg_matvec_dense_noalloc: A, p and q are required");
+  if (n < 1 || n > (int64_t(1) << 30))
+    return fail(nullptr, DCG_ERR_INVALID_ARG, "dcg_matvec_dense_noalloc: n out of range [1, 2^30]");
+  if (lda < n || (lda % 4) != 0)
+    return fail(nullptr, DCG_ERR_INVALID_ARG, "dcg_matvec_dense_noalloc: lda must be >= n and a multiple of 4");
+  if ((reinterpret_cast<uintptr_t>(A) & 15) != 0 || (reinterpret_cast<uintptr_t>(p) & 15) != 0)
+    return fail(nullptr, DCG_ERR_INVALID_ARG, "dcg_matvec_dense_noalloc: A and p must be 16-byte aligned");
+  dcg_ctx* c = nullptr;  // errors below are reported without a context
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = rowop_grid(int(n), sms);
+  if (grid > noalloc_max_ctas())
+    return fail(nullptr, DCG_ERR_UNSUPPORTED,
+                "dcg_matvec_dense_noalloc: this device needs " + std::to_string(grid) +
+                    " reduction slots; the fixed scratch holds " + std::to_string(noalloc_max_ctas()));
+  void* scratch = nullptr;
+  CK(noalloc_scratch(&scratch));
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return fail(nullptr, DCG_ERR_CUDA, "dcg_matvec_dense_noalloc: cuTensorMapEncodeTiled unavailable");
+  CUtensorMap m;
+  if (!make_rowop_tmap(&m, A, n, lda, enc))
+    return fail(nullptr, DCG_ERR_INVALID_ARG, "dcg_matvec_dense_noalloc: tensor map encode failed");
+  CK(launch_matvec_noalloc(&m, p, q, int(n), pAp, grid, scratch, static_cast<cudaStream_t>(stream)));
+  return DCG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Operator launches (one place per operator kind)
 // ---------------------------------------------------------------------------

@@ -151,6 +151,11 @@ cudaError_t rowop_configure();
 int rowop_grid(int n, int num_sms);
 bool make_rowop_tmap(CUtensorMap* map, const float* A, int64_t n, int64_t lda, EncodeTiledFn encode);
 cudaError_t launch_rowop(const CUtensorMap* tmap, const RowOpArgs& a, bool resid, int grid, cudaStream_t s);
+// Context-free q = A p on the library's fixed scratch (no allocation).
+int noalloc_max_ctas();
+cudaError_t noalloc_scratch(void** base);
+cudaError_t launch_matvec_noalloc(const CUtensorMap* tmap, const float* p, float* q, int n, double* pAp, int grid,
+                                  void* scratch, cudaStream_t s);
 cudaError_t launch_apply_block(const ApplyBlockArgs& a, int cmax, float* scratch, int num_sms, cudaStream_t s);
 size_t apply_block_scratch_floats(int n, int cmax, int num_sms);
 cudaError_t launch_form_rbf(const float* X, int n, int d, double l, double s2, double noise, float* A, int64_t lda,

@@ -9,6 +9,7 @@
 //     solve product AW of Algorithm 1 line 3).
 //   * k_form_rbf: A = K + noise I for the Sec. 3 RBF kernel.
 #include <algorithm>
+#include <mutex>
 
 #include "dcg_kernels.cuh"
 
@@ -329,6 +330,58 @@ cudaError_t rowop_configure() {
 int rowop_grid(int n, int num_sms) {
   const int ngroups = (n + RB_ROWS - 1) / RB_ROWS;
   return ngroups < num_sms ? ngroups : num_sms;
+}
+
+// ---------------------------------------------------------------------------
+// Fixed scratch of the context-free matvec (dcg_matvec_dense_noalloc), which
+// allocates no device memory: the arrival counter of the last-CTA reduction
+// at byte 0 (it must be zero when a launch starts; the launcher clears it on
+// the stream before every launch) and one double partial per CTA from byte
+// 256. The grid is min(ceil(n / RB_ROWS), SMs), so kNoallocMaxCtas slots
+// cover every device with up to 512 SMs (GB300: 152).
+// ---------------------------------------------------------------------------
+constexpr int kNoallocMaxCtas = 512;
+constexpr size_t kNoallocScratchBytes = 256 + sizeof(double) * kNoallocMaxCtas;  // 4352 bytes
+constexpr int kNoallocMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+int noalloc_max_ctas() { return kNoallocMaxCtas; }
+
+// Device address of the scratch for the current device, looked up with
+// cudaGetSymbolAddress once per device (with that device current) and cached;
+// the first lookup also sets the matvec kernel's shared-memory attribute.
+cudaError_t noalloc_scratch(void** base) {
+  static std::mutex mu;
+  static void* addr[kNoallocMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* a = nullptr;
+    if ((e = cudaGetSymbolAddress(&a, g_noalloc_scratch)) != cudaSuccess) return e;
+    if ((e = rowop_configure()) != cudaSuccess) return e;
+    addr[dev] = a;
+  }
+  *base = addr[dev];
+  return cudaSuccess;
+}
+
+cudaError_t launch_matvec_noalloc(const CUtensorMap* tmap, const float* p, float* q, int n, double* pAp, int grid,
+                                  void* scratch, cudaStream_t s) {
+  if (grid < 1 || grid > kNoallocMaxCtas) return cudaErrorInvalidValue;
+  unsigned int* counter = static_cast<unsigned int*>(scratch);
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  RowOpArgs a{};
+  a.v = p;
+  a.out = q;
+  a.n = n;
+  a.partials = reinterpret_cast<double*>(static_cast<unsigned char*>(scratch) + 256);
+  a.ticket = counter;
+  a.result = pAp;
+  return launch_rowop(tmap, a, false, grid, s);
 }
 
 // Tensor map over row-major A (n x n, leading dimension lda floats): box of

@@ -212,3 +212,23 @@ def form_rbf_dense(X: torch.Tensor, lengthscale: float, signal_var: float, noise
                                 ctypes.c_void_p(_stream_handle(stream)))
     _lib.check(st, None, "dcg_form_rbf_dense")
     return out
+
+
+def matvec_dense_noalloc(A: torch.Tensor, p: torch.Tensor, q: torch.Tensor, pAp: torch.Tensor | None = None,
+                         lda: int | None = None, stream=None) -> None:
+    """q = A p (and p^T q into the one-element float64 device tensor pAp) with
+    no context and no device allocation: q and pAp are caller-owned. Calls on
+    one device must not overlap in time (they share the library's scratch)."""
+    lib = _lib.load()
+    _dev_f32(A, "A")
+    _dev_f32(p, "p")
+    _dev_f32(q, "q")
+    if pAp is not None and (not pAp.is_cuda or pAp.dtype != torch.float64 or pAp.numel() < 1):
+        raise ValueError("pAp must be a float64 CUDA tensor with one element")
+    n = p.shape[0]
+    lda = A.shape[1] if lda is None else lda
+    st = lib.dcg_matvec_dense_noalloc(ctypes.c_void_p(A.data_ptr()), n, lda, ctypes.c_void_p(p.data_ptr()),
+                                      ctypes.c_void_p(q.data_ptr()),
+                                      ctypes.c_void_p(pAp.data_ptr()) if pAp is not None else None,
+                                      ctypes.c_void_p(_stream_handle(stream)))
+    _lib.check(st, None, "dcg_matvec_dense_noalloc")
