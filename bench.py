@@ -167,7 +167,7 @@ def gpu_arm(args):
 
     def make(deflate):
         return P.DefCG(n, CFG.k if deflate else 0, CFG.ell if deflate else 0, CFG.tol,
-                       max_iter=20000, window="last", select="largest")
+                       max_iter=20000, window="last", select="largest", host_loop=args.host_loop)
 
     # warm-up (builds the graph, first-touch of buffers)
     solver = make(True)
@@ -281,6 +281,7 @@ def gpu_arm(args):
             "workload": CFG.name, "n": n, "d": CFG.d, "systems": T, "k": CFG.k, "ell": CFG.ell,
             "window": "last", "tol": CFG.tol, "operator": "stored dense fp32 (1 GiB > L2)",
             "l2": "inputs larger than L2 (A is 1 GiB per system)", "parallelism": f"replicas x{world}",
+            "launch": "host loop (profiling mode)" if args.host_loop else "one CUDA graph per solve",
         },
         "defcg": {
             "s_per_sequence": seq_s, "iters": loop_mv, "check_matvecs": check_mv,
@@ -314,6 +315,80 @@ def gpu_arm(args):
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+# Kernel-only mode: one hot kernel on its own (for ncu captures of a small case)
+# ---------------------------------------------------------------------------
+def kernel_arm(args):
+    import torch
+
+    import paper_1706_00241_gb300 as P
+    from paper_1706_00241_gb300 import build as B
+
+    torch.cuda.set_device(0)
+    B.build()
+    stream = torch.cuda.current_stream()
+    if args.kernel == "gemv":
+        n = args.n or CFG.n
+        X, bs = S.draw_sequence(CFG.scaled(n, T=1) if n != CFG.n else CFG, T=1)
+        Xd = torch.tensor(X.astype(np.float32), device="cuda")
+        A = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        P.form_rbf_dense(Xd, CFG.lengthscale(0), CFG.signal_var, CFG.noise, out=A)
+        solver = P.DefCG(n, 0, 0, CFG.tol)
+        solver.set_operator_dense(A)
+        algo = 4.0 * n * n + 8.0 * n
+        name = "k_rowop_tma<false> (q = A p, fused p^T q)"
+        unit, bound = "GB/s", "hbm"
+        peak, kind = peaks()
+        workload = f"stored dense fp32 n={n}"
+    else:
+        cfg = S.MF_131072 if args.xformat == "bf16" else S.MF_262144
+        n = args.n or cfg.n
+        rng = np.random.default_rng(0)
+        X = rng.standard_normal((n, cfg.d)).astype(np.float32)
+        Xd = torch.tensor(X, device="cuda")
+        solver = P.DefCG(n, 0, 0, cfg.tol)
+        solver.set_operator_rbf(Xd, cfg.lengthscale(0), cfg.signal_var, cfg.noise, xformat=args.xformat)
+        dpad = (cfg.d + 15) // 16 * 16 if args.xformat == "bf16" else (cfg.d + 7) // 8 * 8
+        algo = 2.0 * n * n * dpad                      # Gram tile FLOPs on the tensor cores
+        name = "k_rbf_mv (tcgen05 Gram tiles, fused exp and contraction)"
+        unit, bound = "TFLOP/s", "tensor"
+        peak, kind = tensor_peak(args.xformat)
+        workload = f"matrix-free rbf n={n} d={cfg.d} {args.xformat}"
+    p = torch.tensor(np.random.default_rng(1).standard_normal(n).astype(np.float32), device="cuda")
+    q = torch.empty_like(p)
+    for _ in range(args.warmup):
+        solver.matvec(p, q, want_pAp=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        solver.matvec(p, q, want_pAp=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    scale = 1e9 if unit == "GB/s" else 1e12
+    achieved = algo / (ms * 1e-3) / scale
+    solver.close()
+    print(json.dumps({"kernel": name, "workload": workload, "launch_ms": ms, "launches": args.steps,
+                      "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                                   "frac": achieved / peak, "peak_kind": kind,
+                                   "algorithmic_per_launch": algo}}))
+
+
+def tensor_peak(xformat):
+    """Dense tensor peak for the operand type: the measured bf16 figure; TF32
+    at the nominal tf32/bf16 ratio (1.1 / 2.25) of it."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        bf16 = float(json.load(open(p))["bf16_tflops"])
+        kind = "measured"
+    else:
+        bf16, kind = 1900.0, "fallback"
+    if xformat == "bf16":
+        return bf16, kind
+    return bf16 * 1.1 / 2.25, kind + " (bf16 x nominal tf32/bf16)"
 
 
 # ---------------------------------------------------------------------------
@@ -366,19 +441,23 @@ def extrapolate(solve_s, mv, sampled):
     return solve_s * CFG.T / sampled, "extrapolated by system count (no golden)"
 
 
-def cpu_baseline(samples=2):
+def cpu_baseline(samples=2, min_seconds=10.0):
     """Oracle def-CG + harmonic Ritz on systems 0 .. samples-1 of the sequence,
-    timed and extrapolated to the whole sequence."""
+    repeated until at least min_seconds of oracle work is timed, extrapolated
+    to the whole sequence by matvec count."""
     smp = OracleSample(samples)
-    solve_s, mv = 0.0, 0
-    for t in range(samples):
-        dt, m = smp.time_system(t)
-        solve_s += dt
-        mv += m
-    est, how = extrapolate(solve_s, mv, samples)
+    solve_s, mv, reps = 0.0, 0, 0
+    while solve_s < min_seconds:
+        for t in range(samples):
+            dt, m = smp.time_system(t)
+            solve_s += dt
+            mv += m
+        reps += 1
+    est, how = extrapolate(solve_s, mv, samples * reps)
     return {"value": est, "unit": "s/sequence", "cores": _cores(), "kind": "oracle",
             "sample": f"systems 0..{samples - 1} of the n=16384 sequence, FP64 numpy def-CG + harmonic "
-                      f"Ritz ({solve_s:.2f} s, {mv} matvecs), {how}; formation of A_t excluded as on the GPU"}
+                      f"Ritz, repeated {reps}x ({solve_s:.2f} s, {mv} matvecs), {how}; formation of A_t "
+                      f"excluded as on the GPU"}
 
 
 def reference_arm(args):
@@ -413,11 +492,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="launch the solve's kernels from the host instead of one CUDA graph "
+                         "(profiling mode: ncu cannot list kernels inside conditional graphs)")
+    ap.add_argument("--kernel", choices=["gemv", "rbf_mv"], default=None,
+                    help="time one hot kernel alone (q = A p) instead of the sequence")
+    ap.add_argument("--n", type=int, default=0, help="system size for --kernel (default: the workload's)")
+    ap.add_argument("--xformat", choices=["bf16", "tf32"], default="bf16", help="X format for --kernel rbf_mv")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         reference_arm(args)
+    elif args.kernel:
+        kernel_arm(args)
     else:
         gpu_arm(args)
 

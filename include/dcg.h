@@ -77,7 +77,12 @@ typedef struct dcg_config {
   int32_t warm_start;   /* 0: x_{-1} = 0 and the input x is ignored; 1: x is x_{-1} */
   int32_t reproject;    /* 1: take mu from (AW)^T (beta p + r) every iteration   */
   int32_t record_history; /* 1: keep |r_j| / |b| per iteration (dcg_get_history) */
-  int32_t reserved[7];  /* must be zero                                          */
+  int32_t host_loop;    /* 0: the solve runs as one CUDA graph with conditional
+                           nodes (default). 1: the same kernels in the same order,
+                           launched from the host with one state read per
+                           iteration (slower; for profilers that cannot see
+                           kernels inside conditional graphs, and for debugging) */
+  int32_t reserved[6];  /* must be zero                                          */
   double tol;           /* relative residual target |b - A x| <= tol |b|         */
 } dcg_config;
 

@@ -34,7 +34,8 @@ class DcgConfig(ctypes.Structure):
         ("warm_start", ctypes.c_int32),
         ("reproject", ctypes.c_int32),
         ("record_history", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("host_loop", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
         ("tol", ctypes.c_double),
     ]
 

@@ -174,8 +174,9 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   if (!cfg || !out) return fail(nullptr, DCG_ERR_INVALID_ARG, "cfg and out must not be NULL");
   *out = nullptr;
   const dcg_config& g = *cfg;
-  for (int i = 0; i < 7; ++i)
+  for (int i = 0; i < 6; ++i)
     if (g.reserved[i]) return fail(nullptr, DCG_ERR_INVALID_ARG, "reserved fields must be zero");
+  if (g.host_loop != 0 && g.host_loop != 1) return fail(nullptr, DCG_ERR_INVALID_ARG, "host_loop must be 0 or 1");
   if (g.n < 1 || g.n > (int64_t(1) << 30)) return fail(nullptr, DCG_ERR_INVALID_ARG, "n out of range");
   if (g.k < 0 || g.ell < 0 || g.k > g.n || g.ell > g.n) return fail(nullptr, DCG_ERR_INVALID_ARG, "k, ell out of range");
   if (g.max_iter < 1) return fail(nullptr, DCG_ERR_INVALID_ARG, "max_iter must be >= 1");
@@ -616,6 +617,53 @@ static dcg_status build_graph(dcg_ctx* c) {
   return DCG_OK;
 }
 
+// The solve graph's kernels in the same order, launched from the host. Each
+// conditional node becomes a host decision on the state the kernels wrote:
+// the pre-loop check when |r_0| met tol (mode 1 after setup), the loop while
+// not done, the in-loop check branch when phase 1 chose a check (mode != 0),
+// the final residual when the last iterate has none.
+static dcg_status run_host_loop(dcg_ctx* c, cudaStream_t s) {
+  Handles h0{};  // no graph: the kernels set no conditionals
+  Ws& w = c->w;
+  DevState* hs = c->h_st;
+  auto read_state = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(hs, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+    return e != cudaSuccess ? e : cudaStreamSynchronize(s);
+  };
+  CK(op_block(c, w.XW, 0, w.Y, c->st, s));
+  CK(op_resid(c, 0, 1, s));
+  CK(launch_setup_r(w, c->grid_iter, s));
+  CK(launch_gram_E(w, c->gramE_part, c->num_sms, s));
+  CK(launch_gram_GW(w, c->gramE_part, c->num_sms, s));
+  CK(launch_chol_E(w, s));
+  CK(launch_small_prods(w, s));
+  CK(launch_check_dots(w, c->grid_iter, s));
+  CK(launch_check_update(w, c->grid_iter, 0, 1, h0, s));
+  CK(launch_phase2_setup(w, c->grid_iter, s));
+  CK(read_state());
+  if (hs->mode == 1) {
+    CK(op_resid(c, -1, 1, s));
+    CK(launch_check_dots(w, c->grid_iter, s));
+    CK(launch_check_update(w, c->grid_iter, 1, 0, h0, s));
+    CK(read_state());
+  }
+  while (!hs->done) {
+    CK(op_matvec(c, w.p, w.q, &c->st->d, c->mv_partials, &c->st->ticket[T_MATVEC], c->st, s));
+    CK(launch_phase1(w, c->grid_iter, h0, s));
+    CK(read_state());
+    if (hs->mode != 0 && hs->status != DCG_ERR_BREAKDOWN) {
+      CK(op_resid(c, -1, 1, s));
+      CK(launch_check_dots(w, c->grid_iter, s));
+      CK(launch_check_update(w, c->grid_iter, 0, 0, h0, s));
+    }
+    CK(launch_phase2(w, c->grid_iter, h0, s));
+    CK(read_state());
+  }
+  if (!hs->true_valid && !hs->zero_rhs) CK(op_resid(c, 3, 0, s));
+  CK(launch_finalize(w, c->grid_iter, s));
+  return DCG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Solve
 // ---------------------------------------------------------------------------
@@ -623,7 +671,7 @@ extern "C" dcg_status dcg_solve(dcg_ctx* c, const float* b, double* x, dcg_solve
   if (!c) return DCG_ERR_INVALID_ARG;
   if (!b || !x) return fail(c, DCG_ERR_INVALID_ARG, "b and x must not be NULL");
   if (c->op == OP_NONE) return fail(c, DCG_ERR_STATE, "no operator set");
-  if (!c->graph_valid) {
+  if (!c->cfg.host_loop && !c->graph_valid) {
     dcg_status s = build_graph(c);
     if (s != DCG_OK) return s;
   }
@@ -648,7 +696,12 @@ extern "C" dcg_status dcg_solve(dcg_ctx* c, const float* b, double* x, dcg_solve
   else
     CK(cudaMemsetAsync(c->w.xd, 0, size_t(n) * 8, s));
   CK(cudaEventRecord(c->ev0, s));
-  CK(cudaGraphLaunch(c->exec, s));
+  if (c->cfg.host_loop) {
+    dcg_status hst = run_host_loop(c, s);
+    if (hst != DCG_OK) return hst;
+  } else {
+    CK(cudaGraphLaunch(c->exec, s));
+  }
   CK(cudaEventRecord(c->ev1, s));
   CK(cudaMemcpyAsync(x, c->w.xd, size_t(n) * 8, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(hs, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));

@@ -45,7 +45,7 @@ class DefCG:
     def __init__(self, n: int, k: int, ell: int, tol: float, max_iter: int | None = None,
                  window: str = "last", select: str = "largest", refine_every: int = 0,
                  warm_start: bool = False, reproject: bool = True,
-                 record_history: bool = False, stream=None):
+                 record_history: bool = False, host_loop: bool = False, stream=None):
         self.lib = _lib.load()
         self.n, self.k, self.ell = int(n), int(k), int(ell)
         cfg = _lib.DcgConfig()
@@ -59,6 +59,7 @@ class DefCG:
         cfg.warm_start = int(bool(warm_start))
         cfg.reproject = int(bool(reproject))
         cfg.record_history = int(bool(record_history))
+        cfg.host_loop = int(bool(host_loop))
         cfg.tol = float(tol)
         self.cfg = cfg
         self.stream = stream if stream is not None else torch.cuda.current_stream()

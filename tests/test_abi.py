@@ -49,7 +49,7 @@ def test_binding_covers_header(lib_path):
 
 def test_config_struct_layout():
     from paper_1706_00241_gb300 import _lib
-    # int64 n, nine int32 fields, int32 reserved[7], then a double: 8 + 64 + 8
+    # int64 n, ten int32 fields, int32 reserved[6], then a double: 8 + 64 + 8
     assert ctypes.sizeof(_lib.DcgConfig) == 80
     assert _lib.DcgConfig.tol.offset == 72
     assert ctypes.sizeof(_lib.DcgSolveInfo) == 64

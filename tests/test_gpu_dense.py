@@ -311,12 +311,13 @@ def test_ritz_first_window_matches_oracle(dcg):
     np.testing.assert_allclose(theta, rr.theta, rtol=1e-3)
 
 
-def _sequence_gpu(dcg, cfg, T, tol, deflate=True, refine_every=0):
+def _sequence_gpu(dcg, cfg, T, tol, deflate=True, refine_every=0, host_loop=False):
     X, bs = S.draw_sequence(cfg, T=T)
     Xd = dev(X.astype(np.float32))
     n = cfg.n
     out = []
-    with dcg.DefCG(n, cfg.k if deflate else 0, cfg.ell if deflate else 0, tol, refine_every=refine_every) as s:
+    with dcg.DefCG(n, cfg.k if deflate else 0, cfg.ell if deflate else 0, tol, refine_every=refine_every,
+                   host_loop=host_loop) as s:
         A = torch.empty((n, n), dtype=torch.float32, device="cuda")
         for t in range(T):
             dcg.form_rbf_dense(Xd, cfg.lengthscale(t), cfg.signal_var, cfg.noise, out=A)
@@ -363,3 +364,18 @@ def test_sequence_dense_16384_full_size(dcg):
     for info, ref in zip(got, g["systems"]):
         assert info["status"] == 0 and info["relres_true"] <= 1e-6
         assert abs(info["iters"] - ref["defcg_iters"]) <= 2 + 0.06 * ref["defcg_iters"], (info["iters"], ref)
+
+
+@pytest.mark.parametrize("refine_every", [0, 7])
+def test_host_loop_matches_graph(dcg, refine_every):
+    # The host-driven loop launches the graph's kernels in the same order with
+    # the same arguments; every reduction has a fixed order, so iterates,
+    # counts and Ritz values are bit-identical.
+    cfg = S.SMALL_1024
+    g = _sequence_gpu(dcg, cfg, 3, 1e-6, refine_every=refine_every)
+    h = _sequence_gpu(dcg, cfg, 3, 1e-6, refine_every=refine_every, host_loop=True)
+    for a, b in zip(g, h):
+        assert a["iters"] == b["iters"] and a["matvecs_check"] == b["matvecs_check"]
+        assert a["status"] == b["status"] == 0
+        assert np.array_equal(a["x"], b["x"])
+        assert np.array_equal(a["theta"], b["theta"])
