@@ -60,7 +60,9 @@ typedef enum dcg_select {         /* which harmonic Ritz values are kept (Sec. 2
 } dcg_select;
 
 typedef enum dcg_xformat {        /* element format of X for the matrix-free operator */
-  DCG_X_FP32 = 0,                 /* Gram tiles in split TF32 (three products)     */
+  DCG_X_FP32 = 0,                 /* X kept in float32: not supported by the
+                                     matrix-free operator (UNSUPPORTED); use the
+                                     stored operator for float32 X               */
   DCG_X_BF16 = 1,                 /* X rounded to bfloat16; exact BF16 products    */
   DCG_X_TF32 = 2                  /* X rounded to TF32; one TF32 product           */
 } dcg_xformat;
