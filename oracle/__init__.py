@@ -20,7 +20,14 @@ Parity status per function (what pins it; tests in ``tests/test_oracle_*.py``):
                          the reduced spectrum
   harmonic_ritz          pinned: invariant subspace gives exact eigenvalues and
                          eigenvectors; generalized-eigen residual
-  nll_and_grad           pinned: central finite differences in log space
+  gp_oracle.gp_nll, gp_nll_grad
+                         pinned: central finite differences in log space, the
+                         closed form for a vanishing lengthscale
+  gp_oracle.dtheta_forms pinned: finite differences of the operator
+  gp_oracle.hutchinson, logdet_grad_probes, gp_nll_grad_probes
+                         pinned: exact on diagonal matrices, unbiased over
+                         20000 probes (5 standard errors)
+  gp_oracle.adam_path    pinned: closed-form steps under a constant gradient
 """
 
 from .dcg_oracle import (  # noqa: F401
