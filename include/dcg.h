@@ -46,7 +46,11 @@ typedef enum dcg_status {
   DCG_ERR_MAXITER = 6,           /* max_iter reached before tol               */
   DCG_ERR_TIMEOUT = 7,           /* a bounded device-side wait gave up        */
   DCG_ERR_STATE = 8,             /* call out of order (e.g. no operator set)  */
-  DCG_ERR_UNSUPPORTED = 9        /* configuration this build does not handle  */
+  DCG_ERR_UNSUPPORTED = 9,       /* configuration this build does not handle  */
+  DCG_ERR_STAGNATION = 10        /* the true residual stopped decreasing above
+                                    tol (tol below the attainable accuracy);
+                                    x is the last iterate, relres_true its
+                                    residual                                   */
 } dcg_status;
 
 typedef enum dcg_window {         /* which directions feed the next W (Alg. 1 l.13) */
@@ -163,6 +167,25 @@ dcg_status dcg_set_operator_rbf(dcg_ctx* ctx, const float* X, int32_t d, int32_t
 /* Change only the RBF hyperparameters of the current matrix-free operator
  * (the lengthscale path of a sequence). Marks A W stale. Errors: STATE. */
 dcg_status dcg_set_rbf_params(dcg_ctx* ctx, double lengthscale, double signal_var, double noise);
+
+/* Hyperparameter derivative forms of the current matrix-free operator, for
+ * the gradient of a Gaussian-process objective whose solves run through
+ * dcg_solve. The paper does not differentiate; the kernel is the Sec. 3 RBF
+ * kernel K_ij = s2 exp(-D_ij / (2 l^2)), D_ij = |x_i - x_j|^2 (x as rounded
+ * by dcg_set_operator_rbf), and A = K + noise I, so
+ *   dA/dl = K .* D / l^3,  dA/ds2 = K / s2,  dA/dnoise = I.
+ * For each column pair (u_p, v_p):
+ *   out[3p]     = u_p^T (dA/dl) v_p
+ *   out[3p + 1] = u_p^T (dA/ds2) v_p
+ *   out[3p + 2] = u_p^T (dA/dnoise) v_p = u_p^T v_p
+ * computed in one pass over the n^2 kernel entries (float32 entries, float64
+ * accumulation across tiles and rows).
+ *   U, V    device, column-major n x npairs float32 (leading dimension n).
+ *   npairs  1 <= npairs <= 64.
+ *   out     host, 3 * npairs doubles.
+ * Synchronises the context's stream. Errors: STATE (no matrix-free operator),
+ * INVALID_ARG, NOMEM (first call allocates its reduction scratch), CUDA. */
+dcg_status dcg_rbf_dtheta(dcg_ctx* ctx, const float* U, const float* V, int32_t npairs, double* out);
 
 /* Forms a stored RBF operator (A1): A[i*lda + j] = signal_var *
  * exp(-|x_i - x_j|^2 / (2 l^2)) + noise * [i == j], float32, computed from X

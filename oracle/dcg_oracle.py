@@ -28,6 +28,8 @@ design notes of the repository):
   R13 residual replacement every m iterations: r <- b - A x, re-deflate
      (x += W g, r -= AW g, g = E^{-1} W^T r), and take mu from
      (AW)^T (beta p_j + r_{j+1}) so that p_{j+1} is re-projected against W.
+     beta keeps the recursion's value |r_{j+1}|^2 / |r_j|^2 (before the
+     replacement); rho is recomputed from the replaced residual.
 """
 
 from __future__ import annotations
@@ -323,6 +325,7 @@ def defcg(A, b, x_init=None, W=None, AW=None, tol=1e-6, max_iter=None, ell=0,
         rho_new = r @ r
         j += 1
         res.history.append(np.sqrt(rho_new) / bnorm)
+        rho_rec = rho_new                    # the recursion's own |r_{j+1}|^2
         replaced = False
         if np.sqrt(rho_new) <= thresh:       # R2
             r_true = b - _mv(A, x)
@@ -337,7 +340,7 @@ def defcg(A, b, x_init=None, W=None, AW=None, tol=1e-6, max_iter=None, ell=0,
             res.matvecs_check += 1
             rho_new = r @ r
             replaced = True
-        beta = rho_new / rho                 # line 10
+        beta = rho_rec / rho                 # line 10 (R13: beta from the recursion)
         if k:                                # line 11 (R1; R13 after a replacement)
             h = AW.T @ r
             if replaced:

@@ -16,6 +16,7 @@ DCG_OK = 0
 STATUS_NAMES = {
     0: "OK", 1: "INVALID_ARG", 2: "NOMEM", 3: "CUDA", 4: "BREAKDOWN",
     5: "SUBSPACE_SINGULAR", 6: "MAXITER", 7: "TIMEOUT", 8: "STATE", 9: "UNSUPPORTED",
+    10: "STAGNATION",
 }
 WINDOW = {"first": 0, "last": 1}
 SELECT = {"largest": 0, "smallest": 1}
@@ -84,6 +85,7 @@ SIGNATURES = {
     "dcg_get_subspace": (_I32, [_P, _P, _PI32]),
     "dcg_get_history": (_I32, [_P, _PD, _I32, _PI32]),
     "dcg_matvec": (_I32, [_P, _P, _P, _PD]),
+    "dcg_rbf_dtheta": (_I32, [_P, _P, _P, _I32, _PD]),
     "dcg_matvec_dense_noalloc": (_I32, [_P, _I64, _I64, _P, _P, _P, _P]),
     "dcg_apply_block": (_I32, [_P, _P, _I32, _P]),
     "dcg_sync": (_I32, [_P]),

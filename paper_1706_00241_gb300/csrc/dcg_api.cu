@@ -59,6 +59,10 @@ struct dcg_ctx {
   float* vcol = nullptr;     // n_pad
   RbfParams* prm = nullptr;
   float* pmv = nullptr;      // n_pad: padded copy of a caller's p (single-step matvec)
+  double rbf_l = 0.0, rbf_s2 = 0.0, rbf_noise = 0.0;  // current hyperparameters (host copy)
+  double* dth_partials = nullptr;  // derivative forms: 3 * kMaxDthetaPairs per CTA
+  double* dth_out = nullptr;       // 3 * kMaxDthetaPairs
+  unsigned int* dth_ticket = nullptr;
   CUtensorMap rbf_tmap;
   int rbf_grid = 1;
 
@@ -138,6 +142,7 @@ extern "C" const char* dcg_status_string(dcg_status s) {
     case DCG_ERR_TIMEOUT: return "device-side wait timed out";
     case DCG_ERR_STATE: return "call out of order";
     case DCG_ERR_UNSUPPORTED: return "unsupported configuration";
+    case DCG_ERR_STAGNATION: return "stagnation: the true residual stopped decreasing above tol";
   }
   return "unknown status";
 }
@@ -225,6 +230,7 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   CKC(dalloc(c, &w.XW, size_t(n) * (1 + kmax)));
   CKC(dalloc(c, &w.Y, size_t(n) * (1 + kmax)));
   CKC(dalloc(c, &w.xd, size_t(n)));
+  CKC(dalloc(c, &w.xbest, size_t(n)));
   CKC(dalloc(c, &w.xh, size_t(n)));
   CKC(dalloc(c, &w.xl, size_t(n)));
   CKC(dalloc(c, &w.r, size_t(n)));
@@ -334,6 +340,9 @@ extern "C" dcg_status dcg_set_operator_rbf(dcg_ctx* c, const float* X, int32_t d
   c->rbf_tmap = m;
   c->rbf_d = d;
   c->rbf_xformat = xformat;
+  c->rbf_l = l;
+  c->rbf_s2 = s2;
+  c->rbf_noise = noise;
   c->rbf_grid = rbf_mv_grid(n_pad / 128, c->num_sms);
   c->op = OP_RBF;
   c->A = nullptr;
@@ -346,6 +355,48 @@ extern "C" dcg_status dcg_set_rbf_params(dcg_ctx* c, double l, double s2, double
   if (c->op != OP_RBF) return fail(c, DCG_ERR_STATE, "no matrix-free operator set");
   if (!(l > 0.0) || !(s2 > 0.0) || !(noise >= 0.0)) return fail(c, DCG_ERR_INVALID_ARG, "bad RBF parameters");
   CK(launch_rbf_params(c->nsq, c->w.n, c->n_pad, l, s2, noise, c->vcol, c->prm, c->stream));
+  c->rbf_l = l;
+  c->rbf_s2 = s2;
+  c->rbf_noise = noise;
+  return DCG_OK;
+}
+
+// u_p^T (dA/dtheta) v_p for theta = (l, s^2, noise) of the current matrix-free
+// operator, from the kernel's SD, SE, SI forms: dA/dl = s^2 E .* D / l^3,
+// dA/ds^2 = E, dA/dnoise = I.
+extern "C" dcg_status dcg_rbf_dtheta(dcg_ctx* c, const float* U, const float* V, int32_t npairs, double* out) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  if (c->op != OP_RBF) return fail(c, DCG_ERR_STATE, "no matrix-free operator set");
+  if (!U || !V || !out) return fail(c, DCG_ERR_INVALID_ARG, "U, V and out are required");
+  if (npairs < 1 || npairs > kMaxDthetaPairs)
+    return fail(c, DCG_ERR_INVALID_ARG, "npairs must be in [1, " + std::to_string(kMaxDthetaPairs) + "]");
+  const int n = c->w.n;
+  if (!c->dth_partials) {
+    CK(dalloc(c, &c->dth_partials, size_t(3) * kMaxDthetaPairs * rbf_dtheta_grid(n)));
+    CK(dalloc(c, &c->dth_out, size_t(3) * kMaxDthetaPairs));
+    CK(dalloc(c, &c->dth_ticket, 1));
+  }
+  RbfDthetaArgs a{};
+  a.Xr = c->Xr;
+  a.n = n;
+  a.d = c->rbf_d;
+  a.prm = c->prm;
+  a.U = U;
+  a.V = V;
+  a.npairs = npairs;
+  a.partials = c->dth_partials;
+  a.ticket = c->dth_ticket;
+  a.out = c->dth_out;
+  CK(launch_rbf_dtheta(a, c->stream));
+  std::vector<double> raw(size_t(3) * npairs);
+  CK(cudaMemcpyAsync(raw.data(), c->dth_out, raw.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const double l = c->rbf_l, s2 = c->rbf_s2;
+  for (int p = 0; p < npairs; ++p) {
+    out[3 * p] = s2 * raw[3 * p] / (l * l * l);
+    out[3 * p + 1] = raw[3 * p + 1];
+    out[3 * p + 2] = raw[3 * p + 2];
+  }
   return DCG_OK;
 }
 

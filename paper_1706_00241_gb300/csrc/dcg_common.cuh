@@ -56,6 +56,10 @@ struct DevState {
   int warm_start;
   int zero_rhs;
   int timeout_site;  // nonzero: which bounded wait gave up
+  int stall;         // consecutive true-residual checks without progress
+  int save_best;     // 1: the check-update kernel copies x to the best iterate
+  double rho_best;   // smallest true |r|^2 seen by a check (0: none yet)
+  double rho_prev_chk;  // true |r|^2 of the previous check
   unsigned int ticket[T_COUNT];
 };
 
@@ -90,6 +94,34 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
   __syncthreads();
   if (s_last) __threadfence();
   return s_last != 0;
+}
+
+// Progress of the true residual over the checks of a solve (mode 1: the
+// recursive residual met tol but the true one did not; mode 2: periodic
+// replacement). The iterate with the smallest true residual is kept
+// (save_best asks the check-update kernel to copy x). A check is a stall if it
+// does not halve the best true residual and either is a failed convergence
+// check or shows a true residual that rose since the previous check.
+// kStallChecks consecutive stalls end the solve with DCG_ERR_STAGNATION (tol
+// lies below the accuracy the iteration reaches, and iterating on lets the
+// iterate drift); the solve then returns the best iterate.
+constexpr int kStallChecks = 8;
+__device__ __forceinline__ void note_check(DevState* st, double rho_true, int mode) {
+  const bool first = st->rho_best == 0.0;
+  const bool halved = first || rho_true < 0.25 * st->rho_best;
+  if (first || rho_true < st->rho_best) {
+    st->rho_best = rho_true;
+    st->save_best = 1;
+  }
+  if (halved) {
+    st->stall = 0;
+  } else if (mode == 1 || rho_true > st->rho_prev_chk) {
+    if (++st->stall >= kStallChecks) {
+      st->status = DCG_ERR_STAGNATION;
+      st->done = 1;
+    }
+  }
+  st->rho_prev_chk = rho_true;
 }
 
 // --------------------------------------------------------------------------

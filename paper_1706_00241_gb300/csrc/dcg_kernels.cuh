@@ -21,6 +21,7 @@ struct Ws {
   int ellmax;
   float* XW;       // n x (1 + kmax); column 0 unused, W from column 1
   double* xd;      // the iterate x, float64
+  double* xbest;   // the iterate with the smallest true residual seen by a check
   float* xh;       // x split for the compensated residual: x = xh + xl
   float* xl;
   float* Y;        // n x (1 + kmax)
@@ -130,6 +131,25 @@ struct RbfExactArgs {
   int skip_if_done;
   int resid_mode;
 };
+
+// Hyperparameter derivative forms of the matrix-free operator for column pairs
+// (u_p, v_p): out[3p] = sum_ij u_pi E_ij D_ij v_pj, out[3p+1] = sum_ij u_pi
+// E_ij v_pj, out[3p+2] = sum_i u_pi v_pi, E_ij = exp(-D_ij / (2 l^2)).
+struct RbfDthetaArgs {
+  const float* Xr;     // n x d rounded points
+  int n;
+  int d;
+  const RbfParams* prm;
+  const float* U;      // n x npairs column-major
+  const float* V;      // n x npairs column-major
+  int npairs;
+  double* partials;    // >= 3 * npairs * grid doubles
+  unsigned int* ticket;
+  double* out;         // 3 * npairs doubles
+};
+constexpr int kMaxDthetaPairs = 64;
+int rbf_dtheta_grid(int n);
+cudaError_t launch_rbf_dtheta(const RbfDthetaArgs& a, cudaStream_t s);
 
 cudaError_t launch_rbf_prep(const float* X, int n, int n_pad, int d, int xformat, float* Xr, void* Xt, float* nsq,
                             cudaStream_t s);

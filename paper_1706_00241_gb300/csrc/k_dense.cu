@@ -295,8 +295,13 @@ __global__ void __launch_bounds__(RB_THREADS, 1)
         st->relres_true = st->bnorm2 > 0.0 ? sqrt(s / st->bnorm2) : sqrt(s);
         st->true_valid = 1;
         const int mode = a.resid_mode >= 0 ? a.resid_mode : st->mode;
-        if (mode == 1 && s <= st->thresh2 && st->status == DCG_OK) {
-          st->done = 1;
+        if (mode == 1 && st->status == DCG_OK) {
+          if (s <= st->thresh2)
+            st->done = 1;
+          else
+            note_check(st, s, 1);
+        } else if (mode == 2 && st->status == DCG_OK) {
+          note_check(st, s, 2);
         }
       }
     }

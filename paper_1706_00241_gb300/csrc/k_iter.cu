@@ -151,8 +151,13 @@ cudaError_t launch_check_dots(const Ws& w, int grid, cudaStream_t s) {
 //   setup:    mu_0 = E^{-1} h (line 4), beta = 0, arms the pre-loop check if
 //             |r_0| <= tol |b|;
 //   pre_loop: after a failed initial check only rho is refreshed;
-//   in loop:  beta = rho_new / rho and mu = E^{-1}(h + beta hp), which
-//             re-projects p_{j+1} against W after the replacement (R13).
+//   in loop:  beta = rho_rec / rho from the recursion's own |r_{j+1}|^2
+//             (st->rho_new, written by phase 1), rho = |r_true|^2 after the
+//             replacement, and mu = E^{-1}(h + beta hp), which re-projects
+//             p_{j+1} against W (R13: keep beta, recompute rho). Where the
+//             true residual sits far above the recursive one (an inexact
+//             iteration operator at its accuracy floor) beta stays <= 1 and
+//             the step acts as a restart instead of amplifying p.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_check_update(Ws w, int pre_loop, int setup, Handles hd) {
   DevState* st = w.st;
@@ -167,9 +172,11 @@ __global__ void __launch_bounds__(256) k_check_update(Ws w, int pre_loop, int se
   __shared__ float gsh[kMaxK];
   for (int c = threadIdx.x; c < k; c += blockDim.x) gsh[c] = w.gamma_f[c];
   __syncthreads();
+  const bool save_best = st->save_best != 0;  // this check found the best iterate so far
   float acc = 0.f;
   for (int i = threadIdx.x; i < len; i += blockDim.x) {
     const int gi = i0 + i;
+    if (save_best) w.xbest[gi] = w.xd[gi];
     float dx = 0.f, ri = w.r[gi];
     for (int c = 0; c < k; ++c) {
       const float g = gsh[c];
@@ -200,7 +207,7 @@ __global__ void __launch_bounds__(256) k_check_update(Ws w, int pre_loop, int se
     if (setup) {
       s_beta = 0.0;
     } else {
-      s_beta = st->rho > 0.0 ? rho_new / st->rho : 0.0;
+      s_beta = st->rho > 0.0 ? st->rho_new / st->rho : 0.0;
     }
   }
   __syncthreads();
@@ -221,6 +228,7 @@ __global__ void __launch_bounds__(256) k_check_update(Ws w, int pre_loop, int se
     w.gamma_f[c] = 0.f;
   }
   if (threadIdx.x == 0) {
+    st->save_best = 0;
     st->rho = rho_new;
     st->rho_new = rho_new;
     if (k) st->true_valid = 0;
@@ -561,7 +569,9 @@ __global__ void __launch_bounds__(256) k_phase2(Ws w, Handles hd, int set_loop) 
       w.xd[gi] += double(dx);
       w.r[gi] = ri;
     }
-    w.p[gi] = fmaf(beta, w.p[gi], ri) - wm;
+    // beta = 0 starts a fresh direction without reading the old p (a
+    // non-finite p left by an earlier failed solve must not leak in)
+    w.p[gi] = (beta != 0.f ? fmaf(beta, w.p[gi], ri) : ri) - wm;
   }
 }
 
@@ -595,9 +605,18 @@ cudaError_t launch_final_gate(const Ws& w, Handles h, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// b = 0 returns x = 0; a stagnated solve returns the iterate with the
+// smallest true residual seen, with that residual.
 __global__ void __launch_bounds__(256) k_finalize(Ws w) {
-  if (!w.st->zero_rhs) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += gridDim.x * blockDim.x) w.xd[i] = 0.0;
+  DevState* st = w.st;
+  const bool restore = !st->zero_rhs && st->status == DCG_ERR_STAGNATION && st->rho_best > 0.0;
+  if (!st->zero_rhs && !restore) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += gridDim.x * blockDim.x)
+    w.xd[i] = restore ? w.xbest[i] : 0.0;
+  if (restore && blockIdx.x == 0 && threadIdx.x == 0) {
+    st->rho_true = st->rho_best;
+    st->relres_true = st->bnorm2 > 0.0 ? sqrt(st->rho_best / st->bnorm2) : sqrt(st->rho_best);
+  }
 }
 
 // x = xh + xl with xh = fl32(x), xl = fl32(x - xh): the float32 pair the

@@ -353,13 +353,16 @@ cudaError_t launch_rbf_mv(const CUtensorMap* tmap, const RbfMvArgs& a, int grid,
 //   mode 1: Y[:, c] = A V[:, c] for c < ncols (<= 32 per launch column block)
 // ---------------------------------------------------------------------------
 constexpr int EX_ROWS = 128;
-// Relative error bound of one entry K_ij of the residual kernel. The entry is
-// carried as a float32 pair through every step: exact coordinate differences
-// (TwoDiff), exact squares (FMA), a compensated sum, the exponent as a pair,
-// and exp to ~1.2e-13 relative (emulated against 200-bit arithmetic over
-// a in [-103, 0]); with the s^2 pair the entry is good to ~(5 + |a|) 2^-48.
-// The bound carries a factor of about 5 over that for |a| <= 40.
-constexpr double kRbfEntryEps = 1e-12;
+// Error model of one entry K_ij of the residual kernel, in units of
+// u^2 = 2^-48 (the float32-pair precision). The entry is carried as a float32
+// pair through every step: exact coordinate differences (TwoDiff), exact
+// squares (FMA), a compensated sum of d squares (relative error <= d u^2),
+// the exponent a = -D / (2 l^2) as a pair (2 u^2 |a|), exp after Tang
+// (emulated against 200-bit arithmetic over a in [-103, 0]: <= 2 u^2 + |a| u^2
+// from the exponent's own representation), then the s^2 pair and one Dot2
+// step (~4 u^2). Relative error of the entry: <= (8 + (d + 3) |a|) u^2.
+constexpr double kU2 = 3.552713678800501e-15;  // 2^-48
+constexpr float kEntryErrC0 = 8.f;
 constexpr int EX_J = 64;
 constexpr int EX_MAXD = 64;
 constexpr int EX_CB = 16;
@@ -458,7 +461,8 @@ __global__ void __launch_bounds__(EX_ROWS) k_rbf_exact(RbfExactArgs a) {
   float acc[EX_CB], cmp[EX_CB];
 #pragma unroll
   for (int c = 0; c < EX_CB; ++c) acc[c] = cmp[c] = 0.f;
-  float esq = 0.f;  // sum_j (K_ij x_j)^2: scale of the entry-error term of the residual
+  float esq = 0.f;  // sum_j (e_ij K_ij x_j)^2, e_ij the entry's relative error in units of u^2
+  const float err_da = float(d + 3);
   for (int j0 = 0; j0 < n; j0 += EX_J) {
     __syncthreads();
     for (int idx = threadIdx.x; idx < EX_J * d; idx += EX_ROWS) {
@@ -516,7 +520,8 @@ __global__ void __launch_bounds__(EX_ROWS) k_rbf_exact(RbfExactArgs a) {
         two_sum_add(acc[0], cmp[0], p);
         cmp[0] = __fadd_rn(cmp[0], e);
         cmp[0] = __fmaf_rn(k_hi, vlo[jj], __fmaf_rn(k_lo, xhv, cmp[0]));
-        esq = fmaf(p, p, esq);
+        const float e_ij = fmaf(err_da, fabsf(a_hi), kEntryErrC0) * p;
+        esq = fmaf(e_ij, e_ij, esq);
       } else {
         const float kij = s2 * expf(a_hi) * (1.f + a_lo);
 #pragma unroll
@@ -571,26 +576,152 @@ __global__ void __launch_bounds__(EX_ROWS) k_rbf_exact(RbfExactArgs a) {
       if (!st) {
         if (a.result) *a.result = s;
       } else if (a.resid_mode != 0) {
-        // Each entry K_ij carries a relative error <= kRbfEntryEps (the
-        // distance, exponent, exponential and s^2 product are float32 pairs;
-        // the largest terms are the Taylor truncation and the float32 tail).
+        // Entry K_ij carries a relative error <= e_ij u^2 (the model above).
         // The errors of different entries are independent, so the error of
-        // the computed residual is ~kRbfEntryEps sqrt(sum_ij (K_ij x_j)^2)
+        // the computed residual is ~u^2 sqrt(sum_ij (e_ij K_ij x_j)^2)
         // (probabilistic rounding-error model, Higham & Mary 2019); the
         // worst-case sum of |K_ij x_j| overstates it by orders of magnitude
         // because b - A x cancels heavily. Convergence is accepted only if the
         // residual plus three times that estimate meets tol.
-        const double err = 3.0 * kRbfEntryEps * sqrt(se);
+        const double err = 3.0 * kU2 * sqrt(se);
         st->rho_true = s;
         st->matvecs_check += 1;
         st->relres_true = st->bnorm2 > 0.0 ? sqrt(s / st->bnorm2) : sqrt(s);
         st->true_valid = 1;
         const int mode = a.resid_mode >= 0 ? a.resid_mode : st->mode;
         const double lim = sqrt(st->thresh2) - err;
-        if (mode == 1 && lim > 0.0 && s <= lim * lim && st->status == DCG_OK) st->done = 1;
+        if (mode == 1 && st->status == DCG_OK) {
+          if (lim > 0.0 && s <= lim * lim)
+            st->done = 1;
+          else
+            note_check(st, s, 1);
+        } else if (mode == 2 && st->status == DCG_OK) {
+          note_check(st, s, 2);
+        }
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Derivative forms for the hyperparameter gradient (RBF kernel of Sec. 3):
+// for pairs (u_p, v_p), in one pass over the n^2 entries,
+//   SD_p = sum_ij u_pi E_ij D_ij v_pj,  SE_p = sum_ij u_pi E_ij v_pj,
+//   SI_p = sum_i u_pi v_pi,  E_ij = exp(-D_ij / (2 l^2)), D_ij = |x_i - x_j|^2,
+// so that u^T (dA/dl) v = s^2 SD / l^3, u^T (dA/ds^2) v = SE and
+// u^T (dA/dnoise) v = SI. 128 rows per CTA (one per thread), PB pairs per
+// blockIdx.y, 64-point column tiles in shared memory; float32 sums over a
+// tile, float64 across tiles and rows; the last CTA reduces the per-CTA
+// partials in a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int DT_ROWS = 128;
+constexpr int DT_J = 64;
+
+template <int DMAX, int PB>
+__global__ void __launch_bounds__(DT_ROWS) k_rbf_dtheta(RbfDthetaArgs a) {
+  __shared__ float xj[DT_J][DMAX + 1];
+  __shared__ float vj[DT_J][PB + 1];
+  __shared__ double s_part[DT_ROWS / 32][3 * PB];
+  const int n = a.n, d = a.d;
+  const int p0 = blockIdx.y * PB;
+  const int pw = min(PB, a.npairs - p0);
+  const int i = blockIdx.x * DT_ROWS + threadIdx.x;
+  const float cexp = -0.5f * a.prm->c2;  // exp(-D / (2 l^2)) = exp2(cexp D)
+  float xi[DMAX];
+#pragma unroll
+  for (int m = 0; m < DMAX; ++m) xi[m] = (i < n && m < d) ? a.Xr[int64_t(i) * d + m] : 0.f;
+  double accE[PB], accD[PB];
+#pragma unroll
+  for (int c = 0; c < PB; ++c) accE[c] = accD[c] = 0.0;
+  for (int j0 = 0; j0 < n; j0 += DT_J) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < DT_J * d; idx += DT_ROWS) {
+      const int jj = idx / d, m = idx % d;
+      xj[jj][m] = (j0 + jj < n) ? a.Xr[int64_t(j0 + jj) * d + m] : 0.f;
+    }
+    for (int idx = threadIdx.x; idx < DT_J * PB; idx += DT_ROWS) {
+      const int c = idx / DT_J, jj = idx % DT_J;
+      vj[jj][c] = (c < pw && j0 + jj < n) ? a.V[int64_t(p0 + c) * n + j0 + jj] : 0.f;
+    }
+    __syncthreads();
+    const int jn = min(DT_J, n - j0);
+    float tE[PB], tD[PB];
+#pragma unroll
+    for (int c = 0; c < PB; ++c) tE[c] = tD[c] = 0.f;
+    for (int jj = 0; jj < jn; ++jj) {
+      float D = 0.f;
+#pragma unroll
+      for (int m = 0; m < DMAX; ++m) {
+        if (m < d) {
+          const float df = xi[m] - xj[jj][m];
+          D = fmaf(df, df, D);
+        }
+      }
+      const float E = tc::ex2_approx(cexp * D);
+      const float ED = E * D;
+#pragma unroll
+      for (int c = 0; c < PB; ++c) {
+        tE[c] = fmaf(E, vj[jj][c], tE[c]);
+        tD[c] = fmaf(ED, vj[jj][c], tD[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < PB; ++c) {
+      accE[c] += double(tE[c]);
+      accD[c] += double(tD[c]);
+    }
+  }
+  // row i's contributions, reduced over the CTA
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < PB; ++c) {
+    double ui = 0.0, vi = 0.0;
+    if (i < n && c < pw) {
+      ui = double(a.U[int64_t(p0 + c) * n + i]);
+      vi = double(a.V[int64_t(p0 + c) * n + i]);
+    }
+    const double sd = warp_sum(ui * accD[c]);
+    const double se = warp_sum(ui * accE[c]);
+    const double si = warp_sum(ui * vi);
+    if (lane == 0) {
+      s_part[warp][3 * c] = sd;
+      s_part[warp][3 * c + 1] = se;
+      s_part[warp][3 * c + 2] = si;
+    }
+  }
+  __syncthreads();
+  const int G = gridDim.x;
+  for (int v = threadIdx.x; v < 3 * pw; v += DT_ROWS) {
+    double s = 0.0;
+    for (int w = 0; w < DT_ROWS / 32; ++w) s += s_part[w][v];
+    a.partials[int64_t(3 * p0 + v) * G + blockIdx.x] = s;
+  }
+  if (!arrive_last(a.ticket)) return;
+  for (int v = threadIdx.x; v < 3 * a.npairs; v += DT_ROWS) {
+    double s = 0.0;
+    for (int b = 0; b < G; ++b) s += __ldcg(a.partials + int64_t(v) * G + b);
+    a.out[v] = s;
+  }
+}
+
+int rbf_dtheta_grid(int n) { return (n + DT_ROWS - 1) / DT_ROWS; }
+
+cudaError_t launch_rbf_dtheta(const RbfDthetaArgs& a, cudaStream_t s) {
+  if (a.npairs < 1 || a.npairs > kMaxDthetaPairs || a.d < 1 || a.d > EX_MAXD) return cudaErrorInvalidValue;
+  const int gx = rbf_dtheta_grid(a.n);
+  if (a.npairs == 1) {
+    if (a.d <= 16)
+      k_rbf_dtheta<16, 1><<<dim3(gx, 1), DT_ROWS, 0, s>>>(a);
+    else
+      k_rbf_dtheta<EX_MAXD, 1><<<dim3(gx, 1), DT_ROWS, 0, s>>>(a);
+  } else {
+    const dim3 grid(gx, (a.npairs + 15) / 16);
+    if (a.d <= 16)
+      k_rbf_dtheta<16, 16><<<grid, DT_ROWS, 0, s>>>(a);
+    else
+      k_rbf_dtheta<EX_MAXD, 16><<<grid, DT_ROWS, 0, s>>>(a);
+  }
+  return cudaGetLastError();
 }
 
 int rbf_exact_grid(int n) { return (n + EX_ROWS - 1) / EX_ROWS; }

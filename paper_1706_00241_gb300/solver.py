@@ -187,6 +187,22 @@ class DefCG:
                                         ctypes.byref(d) if want_pAp else None), "dcg_matvec")
         return q, (d.value if want_pAp else None)
 
+    def rbf_dtheta(self, U: torch.Tensor, V: torch.Tensor) -> np.ndarray:
+        """u_p^T (dA/dtheta) v_p for theta = (lengthscale, signal_var, noise) of
+        the matrix-free operator; U, V are (P, n) float32 tensors (row p is the
+        pair's vector). Returns a (P, 3) float64 array."""
+        _dev_f32(U, "U")
+        _dev_f32(V, "V")
+        if U.dim() == 1:
+            U, V = U[None], V[None]
+        if U.shape != V.shape or U.shape[1] != self.n:
+            raise ValueError("U and V must both be (P, n)")
+        P = U.shape[0]
+        out = (ctypes.c_double * (3 * P))()
+        self._check(self.lib.dcg_rbf_dtheta(self._ctx, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                                            P, out), "dcg_rbf_dtheta")
+        return np.array(out[:], dtype=np.float64).reshape(P, 3)
+
     def apply_block(self, V: torch.Tensor, Y: torch.Tensor | None = None) -> torch.Tensor:
         """Y = A V for a (c, n) tensor V (row j is column j), in one pass over A."""
         _dev_f32(V, "V")

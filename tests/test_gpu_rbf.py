@@ -142,3 +142,29 @@ def test_rbf_matvec_full_size_sampled_rows(dcg, cfg, fmt):
     tol = gram_tol(Xr, l, np.abs(Krows) @ np.abs(p.astype(np.float64)))
     assert np.all(np.abs(q[rows] - ref) <= tol), np.max(np.abs(q[rows] - ref) / tol)
     assert np.isfinite(pAp)
+
+
+def test_rbf_unreachable_tol_stagnates_then_context_recovers(dcg):
+    # tol 1e-13 lies below what the exact-form residual can certify for this
+    # operator: the solve must stop on the stagnation guard (not iterate on
+    # at the floor until it drifts or hits max_iter), report the residual it
+    # reached, and leave the context usable for the next solve.
+    n = 1024
+    rng = np.random.default_rng(21)
+    X = rng.random((n, 8)).astype(np.float32)
+    Xr = S.round_to_bf16(X).astype(np.float64)
+    A = O.rbf_gram(Xr, 0.5, 1.0, 0.1)
+    z = np.where(rng.random(n) < 0.5, -1.0, 1.0).astype(np.float32)
+    with dcg.DefCG(n, 0, 0, 1e-13, refine_every=25, max_iter=5000) as s:
+        s.set_operator_rbf(dev(X), 0.5, 1.0, 0.1, xformat="bf16")
+        x, info = s.solve(dev(z), raise_on_error=False)
+        assert info["status"] == 10, info                 # DCG_ERR_STAGNATION
+        assert info["iters"] < 1000
+        relres = np.linalg.norm(z - A @ x.cpu().numpy()) / np.linalg.norm(z)
+        assert relres <= 1e-9 and abs(relres - info["relres_true"]) <= 1e-11, (relres, info["relres_true"])
+        # same context, a fresh right-hand side: the solve starts clean
+        b = rng.standard_normal(n).astype(np.float32)
+        x2, info2 = s.solve(dev(b), raise_on_error=False)
+        assert info2["iters"] >= 1 and info2["status"] in (0, 10), info2
+        r2 = np.linalg.norm(b - A @ x2.cpu().numpy()) / np.linalg.norm(b)
+        assert r2 <= 1e-9 and np.isfinite(x2.cpu().numpy()).all()
