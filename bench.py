@@ -151,8 +151,8 @@ def gpu_arm(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     B.build()
-    n, T = CFG.n, CFG.T
-    X, bs = S.draw_sequence(CFG)
+    n, T = CFG.n, (args.systems if args.systems else CFG.T)
+    X, bs = S.draw_sequence(CFG, T=T)
     X32 = X.astype(np.float32)
     b32 = [b.astype(np.float32) for b in bs]
     Xd = torch.tensor(X32, device="cuda")
@@ -282,6 +282,7 @@ def gpu_arm(args):
             "window": "last", "tol": CFG.tol, "operator": "stored dense fp32 (1 GiB > L2)",
             "l2": "inputs larger than L2 (A is 1 GiB per system)", "parallelism": f"replicas x{world}",
             "launch": "host loop (profiling mode)" if args.host_loop else "one CUDA graph per solve",
+            **({"systems_override": T} if args.systems else {}),
         },
         "defcg": {
             "s_per_sequence": seq_s, "iters": loop_mv, "check_matvecs": check_mv,
@@ -498,6 +499,9 @@ def main():
     ap.add_argument("--kernel", choices=["gemv", "rbf_mv"], default=None,
                     help="time one hot kernel alone (q = A p) instead of the sequence")
     ap.add_argument("--n", type=int, default=0, help="system size for --kernel (default: the workload's)")
+    ap.add_argument("--systems", type=int, default=0,
+                    help="solve only the first T systems of the sequence (small profiling captures; "
+                         "not a benchmark line)")
     ap.add_argument("--xformat", choices=["bf16", "tf32"], default="bf16", help="X format for --kernel rbf_mv")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -183,6 +183,14 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
     if (g.reserved[i]) return fail(nullptr, DCG_ERR_INVALID_ARG, "reserved fields must be zero");
   if (g.host_loop != 0 && g.host_loop != 1) return fail(nullptr, DCG_ERR_INVALID_ARG, "host_loop must be 0 or 1");
   if (g.n < 1 || g.n > (int64_t(1) << 30)) return fail(nullptr, DCG_ERR_INVALID_ARG, "n out of range");
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0 &&
+        g.n > iter_max_n(sms))
+      return fail(nullptr, DCG_ERR_UNSUPPORTED,
+                  "n above " + std::to_string(iter_max_n(sms)) + " (one co-resident CTA per SM, 16 rows per thread)");
+  }
   if (g.k < 0 || g.ell < 0 || g.k > g.n || g.ell > g.n) return fail(nullptr, DCG_ERR_INVALID_ARG, "k, ell out of range");
   if (g.max_iter < 1) return fail(nullptr, DCG_ERR_INVALID_ARG, "max_iter must be >= 1");
   if (!(g.tol > 0.0)) return fail(nullptr, DCG_ERR_INVALID_ARG, "tol must be > 0");
@@ -215,6 +223,7 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   CKC(cudaEventCreate(&c->ev1));
   CKC(cudaEventCreate(&c->ev2));
   CKC(rowop_configure());
+  CKC(iter_configure());
   CKC(rbf_mv_configure());
   CKC(chol_configure(96));
   CKC(ritz_configure());
@@ -246,6 +255,8 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   CKC(dalloc(c, &w.GW, size_t(kk) * kk));
   CKC(dalloc(c, &w.Einv, size_t(kk) * kk));
   CKC(dalloc(c, &w.N, size_t(kk) * kk));
+  CKC(dalloc(c, &w.NT, size_t(kk) * kk));
+  CKC(dalloc(c, &w.mats2, size_t(3) * kk * kk));
   CKC(dalloc(c, &w.M, size_t(kk) * kk));
   CKC(dalloc(c, &w.h, size_t(kk)));
   CKC(dalloc(c, &w.hp, size_t(kk)));
@@ -636,16 +647,18 @@ static dcg_status build_graph(dcg_ctx* c) {
   if (e == cudaSuccess) {
     run(cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     run(op_matvec(c, w.p, w.q, &c->st->d, c->mv_partials, &c->st->ticket[T_MATVEC], c->st, s1));
-    run(launch_phase1(w, c->grid_iter, h, s1));
+    run(launch_iter_fused(w, c->num_sms, h, s1));
+    // IF a convergence check or a replacement is due: the true residual, the
+    // replacement and line 12 (which the fused kernel then skipped)
     cudaGraph_t inner = nullptr;
     run(add_conditional(s1, h.chk, cudaGraphCondTypeIf, &inner));
     if (e == cudaSuccess) {
       run(cudaStreamBeginCaptureToGraph(s2, inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
       run(capture_check_branch(c, s2, 0));
+      run(launch_phase2(w, c->grid_iter, h, s2));
       cudaGraph_t tmp;
       run(cudaStreamEndCapture(s2, &tmp));
     }
-    run(launch_phase2(w, c->grid_iter, h, s1));
     cudaGraph_t tmp;
     run(cudaStreamEndCapture(s1, &tmp));
   }
@@ -671,8 +684,9 @@ static dcg_status build_graph(dcg_ctx* c) {
 // The solve graph's kernels in the same order, launched from the host. Each
 // conditional node becomes a host decision on the state the kernels wrote:
 // the pre-loop check when |r_0| met tol (mode 1 after setup), the loop while
-// not done, the in-loop check branch when phase 1 chose a check (mode != 0),
-// the final residual when the last iterate has none.
+// not done, the in-loop check branch (true residual, replacement, line 12)
+// when the fused iteration kernel chose a check (mode != 0), the final
+// residual when the last iterate has none.
 static dcg_status run_host_loop(dcg_ctx* c, cudaStream_t s) {
   Handles h0{};  // no graph: the kernels set no conditionals
   Ws& w = c->w;
@@ -700,15 +714,15 @@ static dcg_status run_host_loop(dcg_ctx* c, cudaStream_t s) {
   }
   while (!hs->done) {
     CK(op_matvec(c, w.p, w.q, &c->st->d, c->mv_partials, &c->st->ticket[T_MATVEC], c->st, s));
-    CK(launch_phase1(w, c->grid_iter, h0, s));
+    CK(launch_iter_fused(w, c->num_sms, h0, s));
     CK(read_state());
-    if (hs->mode != 0 && hs->status != DCG_ERR_BREAKDOWN) {
+    if (hs->mode != 0 && !hs->done) {
       CK(op_resid(c, -1, 1, s));
       CK(launch_check_dots(w, c->grid_iter, s));
       CK(launch_check_update(w, c->grid_iter, 0, 0, h0, s));
+      CK(launch_phase2(w, c->grid_iter, h0, s));
+      CK(read_state());
     }
-    CK(launch_phase2(w, c->grid_iter, h0, s));
-    CK(read_state());
   }
   if (!hs->true_valid && !hs->zero_rhs) CK(op_resid(c, 3, 0, s));
   CK(launch_finalize(w, c->grid_iter, s));

@@ -61,6 +61,8 @@ struct DevState {
   double rho_best;   // smallest true |r|^2 seen by a check (0: none yet)
   double rho_prev_chk;  // true |r|^2 of the previous check
   unsigned int ticket[T_COUNT];
+  unsigned int bar_count;  // grid barrier of the fused iteration kernel: arrivals
+  unsigned int bar_gen;    // and generation
 };
 
 // --------------------------------------------------------------------------
@@ -169,6 +171,26 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase)
   for (long long i = 0; i < kSpinLimit; ++i)
     if (mbar_try_wait(bar, phase)) return true;
   return false;
+}
+
+// L2 cache policy for data read once per launch (the stored operator): its
+// lines are evicted first, so streaming a 1 GiB matrix through the 129 MB L2
+// does not displace the few MB the iteration kernels reuse (x, r, p, q, W, AW,
+// the k x k matrices).
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+// As tma_load_2d, with an L2 cache policy (l2_policy_evict_first).
+__device__ __forceinline__ void tma_load_2d_hint(void* smem_dst, const CUtensorMap* map, uint64_t* bar, int x0,
+                                                 int y0, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cta.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%3, "
+      "%4}], [%2], %5;" ::"r"(smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x0), "r"(y0), "l"(pol)
+      : "memory");
 }
 
 // 2-D tiled TMA load of box {x, y} at coordinates (x0, y0) into shared memory,

@@ -36,7 +36,9 @@ struct Ws {
   double* GW;      // kmax x kmax, (AW)^T (AW)
   double* Einv;    // kmax x kmax, E^{-1}
   double* N;       // kmax x kmax, G_W E^{-1}
+  double* NT;      // its transpose E^{-1} G_W
   double* M;       // kmax x kmax, E^{-1} G_W E^{-1}
+  float2* mats2;   // [E^{-1} | M | N^T] as float pairs (hi, lo), k x k each, contiguous
   double* h;       // kmax: (AW)^T r
   double* hp;      // kmax: (AW)^T p
   double* mu;      // kmax
@@ -189,7 +191,9 @@ cudaError_t launch_chol_E(const Ws& w, cudaStream_t s);
 cudaError_t launch_small_prods(const Ws& w, cudaStream_t s);
 cudaError_t launch_check_dots(const Ws& w, int grid, cudaStream_t s);
 cudaError_t launch_check_update(const Ws& w, int grid, int pre_loop, int setup, Handles h, cudaStream_t s);
-cudaError_t launch_phase1(const Ws& w, int grid, Handles h, cudaStream_t s);
+cudaError_t launch_iter_fused(const Ws& w, int grid, Handles h, cudaStream_t s);
+int64_t iter_max_n(int num_sms);
+cudaError_t iter_configure();
 cudaError_t launch_phase2(const Ws& w, int grid, Handles h, cudaStream_t s);
 cudaError_t launch_phase2_setup(const Ws& w, int grid, cudaStream_t s);
 cudaError_t launch_loop_gate(const Ws& w, Handles h, cudaStream_t s);

@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(RB_THREADS, 1)
     // ---------------- producer: one elected lane issues the TMA tiles -------
     if (lane == 0) {
       prefetch_tensormap(&tmap);
+      const uint64_t pol = l2_policy_evict_first();  // A is read once per launch
       int it = 0;
       for (; it < total; ++it) {
         const int s = it % RB_STAGES;
@@ -126,8 +127,8 @@ __global__ void __launch_bounds__(RB_THREADS, 1)
         const int nb = min(RB_BOXES, (n - c * RB_CHUNK + RB_BOXW - 1) / RB_BOXW);
         mbar_arrive_expect_tx(&full[s], uint32_t(nb) * RB_ROWS * RB_BOXW * 4);
         for (int bx = 0; bx < nb; ++bx)
-          tma_load_2d(tiles + size_t(s) * RB_STAGE_FLOATS + bx * RB_ROWS * RB_BOXW, &tmap, &full[s],
-                      c * RB_CHUNK + bx * RB_BOXW, g * RB_ROWS);
+          tma_load_2d_hint(tiles + size_t(s) * RB_STAGE_FLOATS + bx * RB_ROWS * RB_BOXW, &tmap, &full[s],
+                           c * RB_CHUNK + bx * RB_BOXW, g * RB_ROWS, pol);
       }
       s_issued = it;
     }

@@ -6,6 +6,7 @@
 // does the small float64 work that needs the full sums (alpha, beta, the k x k
 // solve for mu or gamma) and the control decisions of the solve graph.
 #include "dcg_kernels.cuh"
+#include "tc.cuh"
 
 namespace dcg {
 
@@ -256,239 +257,425 @@ cudaError_t launch_check_update(const Ws& w, int grid, int pre_loop, int setup, 
 }
 
 // ---------------------------------------------------------------------------
-// Phase 1 of an iteration (lines 6-10 and 13-14 of Algorithm 1), after q = A p
-// and d = p^T q have been formed by the operator kernel:
-//   alpha = rho / d, x += alpha p, r -= alpha q, store (p, q) in the window,
-//   rho' = r^T r, h = (AW)^T r, g = W^T r [, hp = (AW)^T p];
-// last CTA: the convergence / refinement decision and the IF-node value for
-// the check branch; otherwise beta and mu (line 11, reading R1) for phase 2.
-//
 // Float32 re-deflation: in exact arithmetic W^T r_j = 0 for all j (Eq. 5), so
 // gamma = E^{-1} W^T r is zero. In float32 the rounding of mu leaves p slightly
 // A-non-conjugate to W, and r then drifts along W by ~eps32 * lambda(W) per
-// step; CG never removes that drift and the recursive residual stalls. Phase 2
-// therefore applies x += W gamma, r -= AW gamma every iteration (a no-op in
-// exact arithmetic). With r~ = r - AW gamma:
+// step; CG never removes that drift and the recursive residual stalls. Every
+// iteration therefore applies x += W gamma, r -= AW gamma (a no-op in exact
+// arithmetic). With r~ = r - AW gamma:
 //   |r~|^2 = rho' - 2 gamma^T h + gamma^T G_W gamma,   G_W = (AW)^T AW,
 //   mu = E^{-1} ((AW)^T r~ + beta hp) = E^{-1} h - M g + beta E^{-1} hp,
-// with E^{-1}, N = G_W E^{-1} and M = E^{-1} N formed once per solve, so the
-// last CTA only does k x k float64 matrix-vector products in parallel.
-//
-// Layout: one row per thread (the grid covers n with 256-row CTAs, rows
-// strided when n > 256 * grid); dot products are accumulated per thread for
-// 32 columns at a time and reduced through shared memory.
+// with E^{-1}, N = G_W E^{-1} and M = E^{-1} N formed once per solve.
 // ---------------------------------------------------------------------------
-constexpr int P1_THREADS = 256;
-constexpr int P1_CHUNK = 32;
 
-// Block reduction of P1_CHUNK per-thread values; column c of the result goes
-// to out[c * gridDim.x] (cw columns valid).
-__device__ void chunk_reduce(const float* acc, int cw, float (*red)[P1_CHUNK + 1], double* out) {
-  const int G = gridDim.x, t = threadIdx.x;
-  __shared__ float part8[P1_THREADS / P1_CHUNK][P1_CHUNK];
-#pragma unroll
-  for (int c = 0; c < P1_CHUNK; ++c) red[t][c] = acc[c];
+// Grid barrier for a cooperative launch (all CTAs co-resident): sense by
+// generation. Thread 0 of each CTA arrives; the last one resets the count and
+// advances the generation; the others poll it with a bounded wait. Returns
+// false if the wait gave up (the kernel then records a timeout).
+__device__ bool grid_barrier(DevState* st) {
+  __shared__ int s_ok;
   __syncthreads();
-  {
-    const int c = t % P1_CHUNK, q = t / P1_CHUNK;
-    float s = 0.f;
-    for (int i = q * 32; i < q * 32 + 32; ++i) s += red[i][c];
-    part8[q][c] = s;
-  }
-  __syncthreads();
-  if (t < cw) {
-    float s = 0.f;
-    for (int q = 0; q < P1_THREADS / P1_CHUNK; ++q) s += part8[q][t];
-    out[int64_t(t) * G] = double(s);
-  }
-  __syncthreads();
-}
-
-// Per-CTA partial dot products h = (AW)^T r, g = W^T r and (optionally)
-// hp = (AW)^T p over the thread's rows, in one pass over AW and W per block of
-// P1_CHUNK columns. Slots: h at out_h[c * G], g at out_g[c * G], hp at out_hp[c * G].
-__device__ void phase1_dots(const float* __restrict__ AW, const float* __restrict__ W, int k, int n,
-                            const int* rows, int nrows, const float* rv, const float* pv, bool do_hp,
-                            float (*red)[P1_CHUNK + 1], double* out_h, double* out_g, double* out_hp) {
-  const int G = gridDim.x;
-  for (int c0 = 0; c0 < k; c0 += P1_CHUNK) {
-    const int cw = min(P1_CHUNK, k - c0);
-    float ah[P1_CHUNK], ag[P1_CHUNK], ap[P1_CHUNK];
-#pragma unroll
-    for (int c = 0; c < P1_CHUNK; ++c) ah[c] = ag[c] = ap[c] = 0.f;
-    for (int j = 0; j < nrows; ++j) {
-      const float* aw = AW + int64_t(c0) * n + rows[j];
-      const float* ww = W + int64_t(c0) * n + rows[j];
-      const float r = rv[j], p = pv[j];
-#pragma unroll
-      for (int c = 0; c < P1_CHUNK; ++c) {
-        if (c < cw) {
-          const float a = __ldg(aw + int64_t(c) * n);
-          const float wv = __ldg(ww + int64_t(c) * n);
-          ah[c] = fmaf(a, r, ah[c]);
-          ap[c] = fmaf(a, p, ap[c]);
-          ag[c] = fmaf(wv, r, ag[c]);
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = &st->bar_gen;
+    const unsigned int my_gen = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+      st->bar_count = 0;
+      __threadfence();
+      atomicAdd(&st->bar_gen, 1u);
+    } else {
+      long long i = 0;
+      while (*gen == my_gen) {
+        __nanosleep(32);
+        if (++i >= kSpinLimit) {
+          ok = 0;
+          break;
         }
       }
     }
-    chunk_reduce(ah, cw, red, out_h + int64_t(c0) * G);
-    chunk_reduce(ag, cw, red, out_g + int64_t(c0) * G);
-    if (do_hp) chunk_reduce(ap, cw, red, out_hp + int64_t(c0) * G);
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Column sums of 32 per-lane values across a warp (reduce-scatter by
+// halving): afterwards lane l holds in v[0] the warp's sum of column l.
+__device__ __forceinline__ void warp_transpose_sum(float (&v)[32], int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const float send = up ? v[i] : v[i + s];
+      const float keep = up ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
   }
 }
 
-constexpr int P1_MAX_ROWS = 8;  // rows per thread (n <= 8 * 256 * grid)
+constexpr int IT_THREADS = 256;
+constexpr int IT_WARPS = IT_THREADS / 32;
+constexpr int IT_MAX_ROWS = 16;  // rows per thread (n <= 16 * 256 * grid)
 
-__global__ void __launch_bounds__(P1_THREADS) k_phase1(Ws w, Handles hd) {
+// One iteration after q = A p (Algorithm 1 lines 6-12, 13-14), as one
+// cooperative launch with one CTA per SM:
+//   A. rows (thread t of CTA b: b * 256 + t + j * 256 * grid):
+//      alpha = rho / d, x += alpha p, r -= alpha q, store (p, q) in the
+//      window; per-CTA partials of rho' = r^T r, h = (AW)^T r, g = W^T r
+//      [, hp = (AW)^T p] (warp transpose sums, one block barrier);
+//   grid barrier;
+//   B. every CTA reduces all partials in the same fixed order and forms, one
+//      thread per output, gamma = E^{-1} g, a = E^{-1} h - M g,
+//      b = E^{-1} hp and u = N g (E^{-1} and M symmetric, N read through its
+//      transpose, so every read is coalesced); then the re-deflated rho', the
+//      mode (convergence check, periodic replacement, or neither) and beta.
+//      CTA 0 alone writes the solver state and the IF-node value of the check
+//      branch;
+//   C. if no check follows, every CTA applies line 12 to its rows:
+//      x += W gamma, r -= AW gamma, p = beta p + r - W mu, mu = a + beta b.
+// Every CTA reads the state it needs before the barrier, so CTA 0's writes
+// after it cannot race with them. Float32 re-deflation (gamma): see the
+// note above.
+// Double-float arithmetic on float32 pairs (hi, lo), |lo| <= ulp(hi) / 2, for
+// the per-iteration reductions and k x k products: float64 on GB300 issues at
+// ~1/64 of the float32 rate, so a warp-wide float64 instruction occupies the
+// pipe ~17 cycles; the pairs keep ~44 bits on the float32 pipe. TwoSum and the
+// FMA-exact product are the standard error-free transformations (Knuth;
+// Dekker; Ogita, Rump & Oishi 2005).
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df df_add(df a, df b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float v = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+// acc + x * y
+__device__ __forceinline__ df df_fma(df acc, float2 x, df y) {
+  const float p = __fmul_rn(x.x, y.hi);
+  float pe = __fmaf_rn(x.x, y.hi, -p);
+  pe = __fmaf_rn(x.x, y.lo, pe);
+  pe = __fmaf_rn(x.y, y.hi, pe);
+  return df_add(acc, df{p, pe});
+}
+__device__ __forceinline__ df df_shfl_xor(df a, int m) {
+  return {__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
+}
+__device__ __forceinline__ double df_to_double(df a) { return double(a.hi) + double(a.lo); }
+
+constexpr int IT_MAX_GRID = 160;   // the unrolled partial reduction covers <= 160 CTAs
+constexpr int IT_STAGE_KMAX = 64;  // E^{-1}, M, N^T staged in shared memory up to this k
+
+__host__ __device__ constexpr uint32_t it_mat_bytes(int k) { return uint32_t((3 * k * k * 8 + 15) & ~15); }
+
+__global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int stage) {
   DevState* st = w.st;
-  if (st->done) return;
-  __shared__ float red[P1_THREADS][P1_CHUNK + 1];
+  if (st->done) {
+    if (hd.loop && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hd.loop, 0);
+    return;
+  }
   const int n = w.n, k = st->k;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const double d = st->d;
   const bool ok = (d > 0.0) && isfinite(d);
-  const double alpha_d = ok ? st->rho / d : 0.0;
+  const double rho_old = st->rho;
+  const double alpha_d = ok ? rho_old / d : 0.0;
   const float alpha = float(alpha_d);
-  int slot = -1;
-  if (st->ell > 0) {
-    if (st->window == DCG_WINDOW_FIRST) {
-      if (st->iter < st->ell) slot = st->iter;
-    } else {
-      slot = st->head;
-    }
-  }
+  const int iter = st->iter + 1;
+  const int ell = st->ell, window = st->window, head = st->head, nstored = st->nstored;
+  const double thresh2 = st->thresh2, bnorm2 = st->bnorm2;
+  const int refine_every = st->refine_every, max_iter = st->max_iter;
+  const int hist_on = st->hist_on, hist_cap = st->hist_cap;
   const int reproj = st->reproject;
-  int rows[P1_MAX_ROWS];
-  float rv[P1_MAX_ROWS], pv[P1_MAX_ROWS];
-  int nrows = 0;
-  float acc = 0.f;
-  const int stride = gridDim.x * P1_THREADS;
-  for (int gi = blockIdx.x * P1_THREADS + threadIdx.x; gi < n && nrows < P1_MAX_ROWS; gi += stride) {
-    const float pi = w.p[gi], qi = w.q[gi];
-    float ri = w.r[gi];
-    if (ok) {
-      w.xd[gi] += alpha_d * double(pi);
-      ri = fmaf(-alpha, qi, ri);
-      w.r[gi] = ri;
-      if (slot >= 0) {
-        w.P[int64_t(slot) * n + gi] = pi;
-        w.Q[int64_t(slot) * n + gi] = qi;
-      }
+  int slot = -1;
+  if (ell > 0) {
+    if (window == DCG_WINDOW_FIRST) {
+      if (iter - 1 < ell) slot = iter - 1;
+    } else {
+      slot = head;
     }
-    rows[nrows] = gi;
-    rv[nrows] = ri;
-    pv[nrows] = pi;
-    ++nrows;
-    acc = fmaf(ri, ri, acc);
   }
-  const float rho_part = block_sum(acc);
-  const int G = gridDim.x;
-  double* part = my_slots(w.partials);
-  if (threadIdx.x == 0) part[0] = double(rho_part);
-  if (ok && k > 0)
-    phase1_dots(w.Y + n, w.XW + n, k, n, rows, nrows, rv, pv, reproj != 0, red, part + G,
-                part + int64_t(1 + k) * G, part + int64_t(1 + 2 * k) * G);
-  if (!arrive_last(&st->ticket[T_PHASE1])) return;
-
-  __shared__ double sred[1 + 3 * kMaxK], gam[kMaxK], av[kMaxK], bv[kMaxK], uv[kMaxK];
-  __shared__ int s_mode;
-  __shared__ double s_beta;
-  if (!ok) {
-    if (threadIdx.x == 0) {
+  if (!ok) {  // breakdown: every CTA sees the same d
+    if (blockIdx.x == 0 && t == 0) {
       st->status = DCG_ERR_BREAKDOWN;
       st->done = 1;
       if (hd.chk) cudaGraphSetConditional(hd.chk, 0);
+      if (hd.loop) cudaGraphSetConditional(hd.loop, 0);
     }
     return;
   }
-  reduce_partials(w.partials, 1 + (reproj ? 3 : 2) * k, sred);
-  const double* h = sred + 1;
-  const double* g = sred + 1 + k;
-  const double* hp = sred + 1 + 2 * k;
-  // gamma = E^{-1} g, a = E^{-1} h - M g, b = E^{-1} hp, u = N g = G_W gamma
-  for (int o = threadIdx.x; o < 4 * k; o += blockDim.x) {
-    const int which = o / k, c = o % k;
-    double s = 0.0;
-    const double* Ei = w.Einv + c * k;
+  // E^{-1}, M and N^T (read by phase B) arrive in shared memory by bulk copies
+  // while phase A runs
+  extern __shared__ __align__(16) float2 smat[];
+  __shared__ __align__(8) uint64_t mat_bar;
+  const bool staged = stage && k > 0 && k <= IT_STAGE_KMAX;
+  const uint32_t mbytes = it_mat_bytes(k);
+  if (staged && t == 0) {
+    mbar_init(&mat_bar, 1);
+    fence_mbarrier_init();
+    mbar_arrive_expect_tx(&mat_bar, mbytes);
+    tc::bulk_load(smat, w.mats2, mbytes, &mat_bar);
+  }
+  const int G = gridDim.x;
+  const int stride = G * IT_THREADS;
+  const int row0 = blockIdx.x * IT_THREADS + t;
+
+  // ---- A. x, r update, window store, rho' ----
+  float acc = 0.f;
+  for (int gi = row0; gi < n; gi += stride) {
+    const float pi = w.p[gi], qi = w.q[gi];
+    w.xd[gi] += alpha_d * double(pi);
+    const float ri = fmaf(-alpha, qi, w.r[gi]);
+    w.r[gi] = ri;
+    if (slot >= 0) {
+      w.P[int64_t(slot) * n + gi] = pi;
+      w.Q[int64_t(slot) * n + gi] = qi;
+    }
+    acc = fmaf(ri, ri, acc);
+  }
+  // per-warp column sums of the dots, 32 columns at a time
+  __shared__ float wsum[IT_WARPS][1 + 3 * kMaxK];
+  {
+    const float rs = warp_sum(acc);
+    if (lane == 0) wsum[warp][0] = rs;
+  }
+  const int nd = reproj ? 3 : 2;  // h, g [, hp]
+  for (int c0 = 0; c0 < k; c0 += 32) {
+    const int cw = min(32, k - c0);
+    float vh[32], vg[32], vp[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) vh[c] = vg[c] = vp[c] = 0.f;
+    for (int gi = row0; gi < n; gi += stride) {
+      const float ri = w.r[gi], pi = w.p[gi];
+      const float* aw = w.Y + int64_t(1 + c0) * n + gi;
+      const float* ww = w.XW + int64_t(1 + c0) * n + gi;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c < cw) {
+          const float a = __ldg(aw + int64_t(c) * n);
+          const float wv = __ldg(ww + int64_t(c) * n);
+          vh[c] = fmaf(a, ri, vh[c]);
+          vp[c] = fmaf(a, pi, vp[c]);
+          vg[c] = fmaf(wv, ri, vg[c]);
+        }
+      }
+    }
+    warp_transpose_sum(vh, lane);
+    warp_transpose_sum(vg, lane);
+    if (reproj) warp_transpose_sum(vp, lane);
+    if (lane < cw) {
+      wsum[warp][1 + c0 + lane] = vh[0];
+      wsum[warp][1 + k + c0 + lane] = vg[0];
+      if (reproj) wsum[warp][1 + 2 * k + c0 + lane] = vp[0];
+    }
+  }
+  __syncthreads();
+  const int count = 1 + nd * k;
+  float* partf = reinterpret_cast<float*>(w.partials);  // float slots [v * G + b]
+  for (int v = t; v < count; v += IT_THREADS) {
+    float sum = 0.f;
+#pragma unroll
+    for (int q = 0; q < IT_WARPS; ++q) sum += wsum[q][v];
+    partf[int64_t(v) * G + blockIdx.x] = sum;
+  }
+  if (!grid_barrier(st)) {
+    if (t == 0) {
+      st->status = DCG_ERR_TIMEOUT;
+      st->timeout_site = 4;
+      st->done = 1;
+      if (hd.chk) cudaGraphSetConditional(hd.chk, 0);
+      if (hd.loop) cudaGraphSetConditional(hd.loop, 0);
+    }
+    return;
+  }
+
+  // ---- B. the same reduction and k x k products in every CTA ----
+  __shared__ df sred[1 + 3 * kMaxK];
+  __shared__ double gam[kMaxK], av[kMaxK], bv[kMaxK], uv[kMaxK];
+  __shared__ int s_mode, s_done;
+  __shared__ double s_beta;
+  for (int v0 = warp * 4; v0 < count; v0 += IT_WARPS * 4) {
+    df sv[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+    for (int i = 0; i < IT_MAX_GRID / 32; ++i) {  // all loads of the round in flight
+      const int b = lane + 32 * i;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (b < G && v0 + u < count) sv[u] = df_add(sv[u], df{__ldcg(partf + int64_t(v0 + u) * G + b), 0.f});
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int m = 16; m >= 1; m >>= 1) sv[u] = df_add(sv[u], df_shfl_xor(sv[u], m));
+      if (lane == 0 && v0 + u < count) sred[v0 + u] = sv[u];
+    }
+  }
+  __syncthreads();
+  const df* h = sred + 1;
+  const df* g = sred + 1 + k;
+  const df* hp = sred + 1 + 2 * k;
+  const float2* Ei = w.mats2;
+  if (staged) {
+    __shared__ int s_mat_ok;
+    if (t == 0) s_mat_ok = mbar_wait_bounded(&mat_bar, 0) ? 1 : 0;
+    __syncthreads();
+    if (s_mat_ok) {
+      Ei = smat;
+    } else if (t == 0) {
+      st->status = DCG_ERR_TIMEOUT;   // the copy never landed: read from global, end the solve
+      st->timeout_site = 5;
+      st->done = 1;
+    }
+  }
+  const float2* Mm = Ei + k * k;
+  const float2* Nt = Ei + 2 * k * k;
+  for (int o = t; o < 4 * k; o += IT_THREADS) {
+    const int which = o / k, c = o - which * k;
+    df s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
     if (which == 0) {
-      for (int j = 0; j < k; ++j) s = fma(Ei[j], g[j], s);
-      gam[c] = s;
+      for (int j = 0; j < k; ++j) s0 = df_fma(s0, Ei[j * k + c], g[j]);
+      gam[c] = df_to_double(s0);
     } else if (which == 1) {
-      const double* Mi = w.M + c * k;
-      for (int j = 0; j < k; ++j) s = fma(Ei[j], h[j], fma(-Mi[j], g[j], s));
-      av[c] = s;
+      for (int j = 0; j < k; ++j) {
+        s0 = df_fma(s0, Ei[j * k + c], h[j]);
+        s1 = df_fma(s1, Mm[j * k + c], g[j]);
+      }
+      av[c] = df_to_double(s0) - df_to_double(s1);
     } else if (which == 2) {
       if (reproj)
-        for (int j = 0; j < k; ++j) s = fma(Ei[j], hp[j], s);
-      bv[c] = s;
+        for (int j = 0; j < k; ++j) s0 = df_fma(s0, Ei[j * k + c], hp[j]);
+      bv[c] = df_to_double(s0);
     } else {
-      const double* Ni = w.N + c * k;
-      for (int j = 0; j < k; ++j) s = fma(Ni[j], g[j], s);
-      uv[c] = s;
+      for (int j = 0; j < k; ++j) s0 = df_fma(s0, Nt[j * k + c], g[j]);
+      uv[c] = df_to_double(s0);
     }
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
+  if (warp == 0) {
     double corr = 0.0;
-    for (int c = threadIdx.x; c < k; c += 32) corr += gam[c] * (uv[c] - 2.0 * h[c]);
+    for (int c = lane; c < k; c += 32) corr += gam[c] * (uv[c] - 2.0 * df_to_double(h[c]));
     corr = warp_sum(corr);
-    if (threadIdx.x == 0) {
-      double rho_new = sred[0] + corr;
-      if (!(rho_new > 0.0)) rho_new = sred[0];
-      const int iter = st->iter + 1;
-      st->iter = iter;
-      st->alpha = alpha_d;
-      if (st->ell > 0) {
-        if (st->window == DCG_WINDOW_FIRST) {
-          st->nstored = min(iter, st->ell);
-        } else {
-          st->head = (st->head + 1) % st->ell;
-          st->nstored = min(st->nstored + 1, st->ell);
-        }
-      }
-      if (st->hist_on && iter < st->hist_cap) w.hist[iter] = sqrt(rho_new / st->bnorm2);
-      st->rho_new = rho_new;
-      st->true_valid = 0;
+    if (lane == 0) {
+      const double rho_raw = df_to_double(sred[0]);
+      double rho_new = rho_raw + corr;
+      if (!(rho_new > 0.0)) rho_new = rho_raw;
       int mode = 0;
-      if (rho_new <= st->thresh2)
+      if (rho_new <= thresh2)
         mode = 1;
-      else if (st->refine_every > 0 && iter % st->refine_every == 0)
+      else if (refine_every > 0 && iter % refine_every == 0)
         mode = 2;
-      st->mode = mode;
+      const int done = (mode == 0 && iter >= max_iter) ? 1 : 0;
       s_mode = mode;
-      s_beta = rho_new / st->rho;
-      if (mode == 0) {
-        st->beta = s_beta;
-        st->rho = rho_new;
-        if (iter >= st->max_iter) {
-          st->status = DCG_ERR_MAXITER;
-          st->done = 1;
+      s_done = done;
+      s_beta = rho_new / rho_old;
+      if (blockIdx.x == 0) {
+        st->iter = iter;
+        st->alpha = alpha_d;
+        if (ell > 0) {
+          if (window == DCG_WINDOW_FIRST) {
+            st->nstored = min(iter, ell);
+          } else {
+            st->head = (head + 1) % ell;
+            st->nstored = min(nstored + 1, ell);
+          }
         }
+        if (hist_on && iter < hist_cap) w.hist[iter] = sqrt(rho_new / bnorm2);
+        st->rho_new = rho_new;
+        st->true_valid = 0;
+        st->mode = mode;
+        if (mode == 0) {
+          st->beta = s_beta;
+          st->rho = rho_new;
+          if (done) {
+            st->status = DCG_ERR_MAXITER;
+            st->done = 1;
+          }
+        }
+        if (hd.chk) cudaGraphSetConditional(hd.chk, mode != 0 ? 1 : 0);
+        if (done && hd.loop) cudaGraphSetConditional(hd.loop, 0);
       }
-      if (hd.chk) cudaGraphSetConditional(hd.chk, mode != 0 ? 1 : 0);
     }
   }
   __syncthreads();
-  if (s_mode != 0) return;  // the check branch recomputes gamma, beta and mu
-  const double beta = s_beta;
-  for (int c = threadIdx.x; c < k; c += blockDim.x) {
-    const double mu = av[c] + beta * bv[c];
-    w.mu[c] = mu;
-    w.mu_f[c] = float(mu);
-    w.gamma[c] = gam[c];
-    w.gamma_f[c] = float(gam[c]);
+  if (s_mode != 0 || s_done) return;  // the check branch recomputes gamma, beta and mu
+
+  // ---- C. line 12 on this CTA's rows ----
+  __shared__ float msh[kMaxK], gsh[kMaxK];
+  const double beta_d = s_beta;
+  for (int c = t; c < k; c += IT_THREADS) {
+    msh[c] = float(av[c] + beta_d * bv[c]);
+    gsh[c] = float(gam[c]);
+  }
+  __syncthreads();
+  const float beta = float(beta_d);
+  for (int gi = row0; gi < n; gi += stride) {
+    float ri = w.r[gi], dx = 0.f, wm = 0.f;
+    const float pi = w.p[gi];
+    for (int c0 = 0; c0 < k; c0 += 16) {
+      float wc[16], ac[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        wc[c] = c0 + c < k ? __ldg(w.XW + int64_t(c0 + c + 1) * n + gi) : 0.f;
+        ac[c] = c0 + c < k ? __ldg(w.Y + int64_t(c0 + c + 1) * n + gi) : 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        if (c0 + c < k) {
+          dx = fmaf(wc[c], gsh[c0 + c], dx);
+          wm = fmaf(wc[c], msh[c0 + c], wm);
+          ri = fmaf(-ac[c], gsh[c0 + c], ri);
+        }
+      }
+    }
+    if (k) {
+      w.xd[gi] += double(dx);
+      w.r[gi] = ri;
+    }
+    w.p[gi] = (beta != 0.f ? fmaf(beta, pi, ri) : ri) - wm;
   }
 }
 
-int phase1_grid(int n, int num_sms) {
-  int g = (n + P1_THREADS - 1) / P1_THREADS;
-  if (g > num_sms) g = num_sms;
-  while (int64_t(g) * P1_THREADS * P1_MAX_ROWS < n) ++g;
-  return g < 1 ? 1 : g;
+// Largest n the fused iteration kernel covers with one co-resident CTA per SM.
+int64_t iter_max_n(int num_sms) {
+  return int64_t(num_sms < IT_MAX_GRID ? num_sms : IT_MAX_GRID) * IT_THREADS * IT_MAX_ROWS;
 }
 
-cudaError_t launch_phase1(const Ws& w, int grid, Handles h, cudaStream_t s) {
-  k_phase1<<<phase1_grid(w.n, grid), P1_THREADS, 0, s>>>(w, h);
-  return cudaGetLastError();
+
+// Cooperative launch: the grid barrier needs every CTA resident at once (the
+// grid is at most one CTA per SM for the sizes this library accepts).
+static size_t iter_dyn_smem(int kmax) { return kmax <= IT_STAGE_KMAX ? size_t(it_mat_bytes(kmax)) : 0; }
+
+// The attribute is per device, not per context: always allow the largest
+// staging size, so contexts with different k never lower it for each other.
+cudaError_t iter_configure() {
+  return cudaFuncSetAttribute(k_iter_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(iter_dyn_smem(IT_STAGE_KMAX)));
+}
+
+cudaError_t launch_iter_fused(const Ws& w, int num_sms, Handles h, cudaStream_t s) {
+  int grid = (w.n + IT_THREADS - 1) / IT_THREADS;
+  if (grid > num_sms) grid = num_sms;
+  if (grid > IT_MAX_GRID) grid = IT_MAX_GRID;
+  if (grid < 1) grid = 1;
+  if (int64_t(grid) * IT_THREADS * IT_MAX_ROWS < w.n) return cudaErrorInvalidValue;
+  const size_t dyn = iter_dyn_smem(w.kmax);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(IT_THREADS);
+  cfg.dynamicSmemBytes = dyn;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_iter_fused, w, h, dyn > 0 ? 1 : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -506,19 +693,28 @@ __global__ void k_small_prods(Ws w, int which) {
     if (which == 0) {         // Einv[i][j] = sum_l Linv[l][i] Linv[l][j], l >= max(i, j)
       for (int l = max(i, j); l < k; ++l) s = fma(w.Linv[l * k + i], w.Linv[l * k + j], s);
       w.Einv[i * k + j] = s;
-    } else if (which == 1) {  // N = G_W Einv
+    } else if (which == 1) {  // N = G_W Einv (and its transpose, read by columns)
       for (int l = 0; l < k; ++l) s = fma(w.GW[i * k + l], w.Einv[l * k + j], s);
       w.N[i * k + j] = s;
-    } else {                  // M = Einv N
+      w.NT[j * k + i] = s;
+    } else if (which == 2) {  // M = Einv N
       for (int l = 0; l < k; ++l) s = fma(w.Einv[i * k + l], w.N[l * k + j], s);
       w.M[i * k + j] = s;
+    } else {                  // float pairs of Einv, M, N^T for the fused iteration kernel
+      const int kk = k * k, ij = i * k + j;
+      const double src[3] = {w.Einv[ij], w.M[ij], w.NT[ij]};
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const float hi = float(src[m]);
+        w.mats2[m * kk + ij] = make_float2(hi, float(src[m] - double(hi)));
+      }
     }
   }
 }
 
 cudaError_t launch_small_prods(const Ws& w, cudaStream_t s) {
   if (w.kmax == 0) return cudaSuccess;
-  for (int which = 0; which < 3; ++which) {
+  for (int which = 0; which < 4; ++which) {
     k_small_prods<<<w.kmax, 128, 0, s>>>(w, which);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
