@@ -347,7 +347,7 @@ extern "C" dcg_status dcg_set_operator_rbf(dcg_ctx* c, const float* X, int32_t d
   CK(launch_rbf_prep(X, n, n_pad, d, xformat, c->Xr, c->Xt, c->nsq, c->stream));
   CK(launch_rbf_params(c->nsq, n, n_pad, l, s2, noise, c->vcol, c->prm, c->stream));
   CUtensorMap m;
-  if (!make_rbf_tmap(&m, c->Xt, n_pad, xformat, enc)) return fail(c, DCG_ERR_INVALID_ARG, "tensor map encode failed");
+  if (!make_rbf_tmap(&m, c->Xt, n_pad, xformat, d, enc)) return fail(c, DCG_ERR_INVALID_ARG, "tensor map encode failed");
   c->rbf_tmap = m;
   c->rbf_d = d;
   c->rbf_xformat = xformat;

@@ -157,7 +157,8 @@ cudaError_t launch_rbf_prep(const float* X, int n, int n_pad, int d, int xformat
                             cudaStream_t s);
 cudaError_t launch_rbf_params(const float* nsq, int n, int n_pad, double l, double s2, double noise, float* vcol,
                               RbfParams* prm, cudaStream_t s);
-bool make_rbf_tmap(CUtensorMap* map, const void* Xt, int n_pad, int xformat, EncodeTiledFn encode);
+bool make_rbf_tmap(CUtensorMap* map, const void* Xt, int n_pad, int xformat, int d, EncodeTiledFn encode);
+__host__ __device__ int rbf_row_bytes(int xformat, int d);
 size_t rbf_mv_smem_bytes();
 cudaError_t rbf_mv_configure();
 int rbf_mv_grid(int n_tiles, int num_sms);

@@ -103,16 +103,29 @@ cudaError_t launch_rbf_params(const float* nsq, int n, int n_pad, double l, doub
   return cudaGetLastError();
 }
 
-bool make_rbf_tmap(CUtensorMap* map, const void* Xt, int n_pad, int xformat, EncodeTiledFn encode) {
+// Bytes of one X row the MMA reads: the d coordinates rounded up to a 32, 64
+// or 128 byte swizzle row. Loading only these (not the full 128-byte packed
+// row) cuts the L2 -> shared traffic, which bounds this kernel: every J tile is
+// fetched once per I block.
+__host__ __device__ int rbf_row_bytes(int xformat, int d) {
+  const int bytes = d * (xformat == DCG_X_BF16 ? 2 : 4);
+  return bytes <= 32 ? 32 : (bytes <= 64 ? 64 : 128);
+}
+
+bool make_rbf_tmap(CUtensorMap* map, const void* Xt, int n_pad, int xformat, int d, EncodeTiledFn encode) {
   const bool bf = xformat == DCG_X_BF16;
+  const int row_bytes = rbf_row_bytes(xformat, d);
+  const int esize = bf ? 2 : 4;
   cuuint64_t gdim[2] = {cuuint64_t(bf ? 64 : 32), cuuint64_t(n_pad)};
   cuuint64_t gstride[1] = {128};
-  cuuint32_t box[2] = {cuuint32_t(bf ? 64 : 32), 128};
+  cuuint32_t box[2] = {cuuint32_t(row_bytes / esize), 128};
   cuuint32_t estride[2] = {1, 1};
+  const CUtensorMapSwizzle swz = row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                 : row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                   : CU_TENSOR_MAP_SWIZZLE_32B;
   CUresult r = encode(map, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                      const_cast<void*>(Xt), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                      const_cast<void*>(Xt), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
@@ -120,11 +133,12 @@ bool make_rbf_tmap(CUtensorMap* map, const void* Xt, int n_pad, int xformat, Enc
 // Tensor-core matvec
 // ---------------------------------------------------------------------------
 constexpr int MV_TILE = 128;                // rows of an I block and columns of a J tile
-constexpr int MV_STAGES = 4;
+constexpr int MV_STAGES = 6;
 constexpr int MV_TILE_BYTES = MV_TILE * 128;  // 16 KB: 128 rows x 128 bytes
-constexpr int MV_EPI_WARPS = 8;
+constexpr int MV_EPI_WARPS = 16;            // four per SMSP: latency hiding for the exp chains
 constexpr int MV_THREADS = (2 + MV_EPI_WARPS) * 32;
-constexpr int MV_TMEM_COLS = 2 * MV_TILE;     // two accumulator buffers
+constexpr int MV_TBUF = 4;                    // TMEM accumulator buffers (tiles in flight)
+constexpr int MV_TMEM_COLS = MV_TBUF * MV_TILE;  // all 512 columns: one CTA per SM
 // shared memory: X_I tile, stages of {X_J tile, p_J, v_J}, barriers
 constexpr int MV_STAGE_BYTES = MV_TILE_BYTES + 2 * MV_TILE * 4;
 constexpr size_t MV_SMEM = 1024 + MV_TILE_BYTES + size_t(MV_STAGES) * MV_STAGE_BYTES + 256;
@@ -140,13 +154,13 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(stages + size_t(MV_STAGES) * MV_STAGE_BYTES);
   uint64_t* full = bars;                       // [MV_STAGES]
   uint64_t* empty = full + MV_STAGES;          // [MV_STAGES]
-  uint64_t* tfull = empty + MV_STAGES;         // [2]
-  uint64_t* tempty = tfull + 2;                // [2]
-  uint64_t* xi_full = tempty + 2;
+  uint64_t* tfull = empty + MV_STAGES;         // [MV_TBUF]
+  uint64_t* tempty = tfull + MV_TBUF;          // [MV_TBUF]
+  uint64_t* xi_full = tempty + MV_TBUF;
   uint64_t* xi_empty = xi_full + 1;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
-  __shared__ float s_half[MV_TILE];
+  __shared__ float s_slice[3][MV_TILE];
   __shared__ double s_part[MV_EPI_WARPS];
 
   DevState* st = a.st;
@@ -157,6 +171,8 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
   const int n = a.n, n_tiles = a.n_tiles;
   const int kind_tf32 = a.xformat != DCG_X_BF16;
   const int ksteps = kind_tf32 ? (a.d + 7) / 8 : (a.d + 15) / 16;   // 32-byte K steps
+  const uint32_t row_bytes = uint32_t(rbf_row_bytes(a.xformat, a.d));
+  const uint32_t tile_bytes = MV_TILE * row_bytes;                  // bytes of one X tile in use
   const uint32_t idesc = tc::instr_desc(kind_tf32 ? tc::kFmtTF32 : tc::kFmtBF16, MV_TILE, MV_TILE);
 
   if (threadIdx.x == 0) {
@@ -164,7 +180,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], MV_EPI_WARPS);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < MV_TBUF; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], MV_EPI_WARPS);
     }
@@ -188,7 +204,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
       int rbc = 0;
       for (int rb = blockIdx.x; rb < n_tiles && !s_abort; rb += gridDim.x, ++rbc) {
         if (rbc > 0 && !mbar_wait_bounded(xi_empty, (rbc - 1) & 1)) { s_abort = 1; break; }
-        mbar_arrive_expect_tx(xi_full, MV_TILE_BYTES);
+        mbar_arrive_expect_tx(xi_full, tile_bytes);
         tma_load_2d(xi_tile, &tmap, xi_full, 0, rb * MV_TILE);
         for (int J = 0; J < n_tiles; ++J, ++it) {
           const int s = int(it % MV_STAGES);
@@ -197,7 +213,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
             break;
           }
           unsigned char* stg = stages + size_t(s) * MV_STAGE_BYTES;
-          mbar_arrive_expect_tx(&full[s], MV_TILE_BYTES + 2 * MV_TILE * 4);
+          mbar_arrive_expect_tx(&full[s], tile_bytes + 2 * MV_TILE * 4);
           tma_load_2d(stg, &tmap, &full[s], 0, J * MV_TILE);
           tc::bulk_load(stg + MV_TILE_BYTES, a.p + size_t(J) * MV_TILE, MV_TILE * 4, &full[s]);
           tc::bulk_load(stg + MV_TILE_BYTES + MV_TILE * 4, a.vcol + size_t(J) * MV_TILE, MV_TILE * 4, &full[s]);
@@ -215,15 +231,18 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
         tc::fence_after_sync();
         for (int J = 0; J < n_tiles; ++J, ++it) {
           const int s = int(it % MV_STAGES);
-          const int b = int(it & 1);
+          const int b = int(it % MV_TBUF);
           if (!mbar_wait_bounded(&full[s], uint32_t(it / MV_STAGES) & 1)) { s_abort = 1; break; }
-          if (it >= 2 && !mbar_wait_bounded(&tempty[b], uint32_t((it >> 1) - 1) & 1)) { s_abort = 1; break; }
+          if (it >= MV_TBUF && !mbar_wait_bounded(&tempty[b], uint32_t((it / MV_TBUF) - 1) & 1)) {
+            s_abort = 1;
+            break;
+          }
           tc::fence_after_sync();
           const uint32_t b_base = smem_u32(stages + size_t(s) * MV_STAGE_BYTES);
           const uint32_t d_tmem = tmem + uint32_t(b * MV_TILE);
           for (int kk = 0; kk < ksteps; ++kk) {
-            const uint64_t ad = tc::smem_desc_sw128(a_base + 32 * kk);
-            const uint64_t bd = tc::smem_desc_sw128(b_base + 32 * kk);
+            const uint64_t ad = tc::smem_desc_kmajor(a_base + 32 * kk, row_bytes);
+            const uint64_t bd = tc::smem_desc_kmajor(b_base + 32 * kk, row_bytes);
             if (kind_tf32)
               tc::mma_tf32(d_tmem, ad, bd, idesc, kk > 0);
             else
@@ -236,9 +255,9 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
     }
   } else {
     // -------------------------------- epilogue -------------------------------
-    const int ew = warp - 2;                  // 0..7
+    const int ew = warp - 2;                  // 0..15
     const int quarter = warp & 3;             // TMEM lane quarter this warp may access
-    const int half = ew >> 2;                 // column half of the tile
+    const int slice = ew >> 2;                // 32-column slice of the tile
     const int row_l = quarter * 32 + lane;    // row within the I block
     const float c2 = a.prm->c2, l2s = a.prm->l2s, noise = a.prm->noise;
     long long it = 0;
@@ -249,45 +268,44 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
       bool aborted = false;
       for (int J = 0; J < n_tiles; ++J, ++it) {
         const int s = int(it % MV_STAGES);
-        const int b = int(it & 1);
-        if (!mbar_wait_bounded(&tfull[b], uint32_t(it >> 1) & 1)) { s_abort = 1; aborted = true; break; }
+        const int b = int(it % MV_TBUF);
+        if (!mbar_wait_bounded(&tfull[b], uint32_t(it / MV_TBUF) & 1)) { s_abort = 1; aborted = true; break; }
         tc::fence_after_sync();
         const unsigned char* stg = stages + size_t(s) * MV_STAGE_BYTES;
-        const float* pj = reinterpret_cast<const float*>(stg + MV_TILE_BYTES) + half * 64;
-        const float* vj = reinterpret_cast<const float*>(stg + MV_TILE_BYTES + MV_TILE * 4) + half * 64;
-        float part = 0.f;
-#pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 32) {
-          float sv[32];
-          tc::tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * MV_TILE + half * 64 + c0), sv);
-#pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            const float4 p4 = *reinterpret_cast<const float4*>(pj + c0 + j);
-            const float4 v4 = *reinterpret_cast<const float4*>(vj + c0 + j);
-            part = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 0], u + v4.x)), p4.x, part);
-            part = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 1], u + v4.y)), p4.y, part);
-            part = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 2], u + v4.z)), p4.z, part);
-            part = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 3], u + v4.w)), p4.w, part);
-          }
-        }
+        const float* pj = reinterpret_cast<const float*>(stg + MV_TILE_BYTES) + slice * 32;
+        const float* vj = reinterpret_cast<const float*>(stg + MV_TILE_BYTES + MV_TILE * 4) + slice * 32;
+        float sv[32];
+        tc::tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * MV_TILE + slice * 32), sv);
+        // the values are in registers: hand the accumulator back to the MMA
+        // warp before the math (the stage with p and v is released after it)
         tc::fence_before_sync();
         __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&tempty[b]);
-          mbar_arrive(&empty[s]);
+        if (lane == 0) mbar_arrive(&tempty[b]);
+        float pa = 0.f, pb = 0.f, pc = 0.f, pd = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          const float4 p4 = *reinterpret_cast<const float4*>(pj + j);
+          const float4 v4 = *reinterpret_cast<const float4*>(vj + j);
+          pa = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 0], u + v4.x)), p4.x, pa);
+          pb = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 1], u + v4.y)), p4.y, pb);
+          pc = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 2], u + v4.z)), p4.z, pc);
+          pd = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 3], u + v4.w)), p4.w, pd);
         }
+        const float part = (pa + pb) + (pc + pd);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
         const float y = part - comp;
         const float t = acc + y;
         comp = (t - acc) - y;
         acc = t;
       }
       if (aborted) break;
-      // combine the two column halves of each row (named barrier: epilogue warps)
-      if (half == 1) s_half[row_l] = acc;
+      // combine the four column slices of each row (named barrier: epilogue warps)
+      if (slice > 0) s_slice[slice - 1][row_l] = acc;
       asm volatile("bar.sync 1, %0;" ::"r"(MV_EPI_WARPS * 32));
-      if (half == 0 && row < n) {
+      if (slice == 0 && row < n) {
         const float pi = a.p[row];
-        const float q = acc + s_half[row_l] + noise * pi;
+        const float q = acc + ((s_slice[0][row_l] + s_slice[1][row_l]) + s_slice[2][row_l]) + noise * pi;
         a.q[row] = q;
         my_part += double(pi) * double(q);
       }
@@ -329,17 +347,9 @@ cudaError_t rbf_mv_configure() {
   return cudaFuncSetAttribute(k_rbf_mv, cudaFuncAttributeMaxDynamicSharedMemorySize, int(MV_SMEM));
 }
 
-// Persistent grid: as many CTAs as can be resident (each holds 256 TMEM
-// columns, so at most two per SM).
-int rbf_mv_grid(int n_tiles, int num_sms) {
-  int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbf_mv, MV_THREADS, MV_SMEM) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  if (per_sm > 2) per_sm = 2;
-  const int g = per_sm * num_sms;
-  return n_tiles < g ? n_tiles : g;
-}
+// Persistent grid, one CTA per SM: each CTA holds all 512 TMEM columns (four
+// accumulator buffers), and its register use keeps a second CTA off the SM.
+int rbf_mv_grid(int n_tiles, int num_sms) { return n_tiles < num_sms ? n_tiles : num_sms; }
 
 cudaError_t launch_rbf_mv(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s) {
   k_rbf_mv<<<grid, MV_THREADS, MV_SMEM, s>>>(*tmap, a);

@@ -24,6 +24,20 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t smem_addr) {
   return d;
 }
 
+// As smem_desc_sw128 for a K-major tile with rows of row_bytes = 32, 64 or 128
+// bytes under the matching swizzle (32B, 64B, 128B): SBO is the 8-row group
+// stride 8 * row_bytes; layout type 6, 4 or 2 in [61,64).
+__device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t smem_addr, uint32_t row_bytes) {
+  uint64_t d = 0;
+  d |= uint64_t((smem_addr >> 4) & 0x3FFF);
+  d |= uint64_t(1) << 16;
+  d |= uint64_t((8 * row_bytes) >> 4) << 32;
+  d |= uint64_t(1) << 46;
+  const uint64_t mode = row_bytes == 128 ? 2 : (row_bytes == 64 ? 4 : 6);
+  d |= mode << 61;
+  return d;
+}
+
 // Instruction descriptor for kind::f16 / kind::tf32 with float32 accumulation,
 // both operands K-major: D format F32 (bits [4,6) = 1), A and B formats in
 // [7,10) and [10,13) (BF16 = 1, TF32 = 2), N >> 3 in [17,23), M >> 4 in [24,29).
@@ -93,6 +107,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Two 32-column loads (columns [col, col + 64)) issued back to back before a
+// single wait, so their latencies overlap.
+__device__ __forceinline__ void tmem_ld32x2(uint32_t taddr, float* v) {
+  uint32_t r[64];
+#define DCG_TMEM_LD32(base, off)                                                                                  \
+  asm volatile(                                                                                                   \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, " \
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"              \
+      : "=r"(base[0]), "=r"(base[1]), "=r"(base[2]), "=r"(base[3]), "=r"(base[4]), "=r"(base[5]), "=r"(base[6]),  \
+        "=r"(base[7]), "=r"(base[8]), "=r"(base[9]), "=r"(base[10]), "=r"(base[11]), "=r"(base[12]),             \
+        "=r"(base[13]), "=r"(base[14]), "=r"(base[15]), "=r"(base[16]), "=r"(base[17]), "=r"(base[18]),          \
+        "=r"(base[19]), "=r"(base[20]), "=r"(base[21]), "=r"(base[22]), "=r"(base[23]), "=r"(base[24]),          \
+        "=r"(base[25]), "=r"(base[26]), "=r"(base[27]), "=r"(base[28]), "=r"(base[29]), "=r"(base[30]),          \
+        "=r"(base[31])                                                                                           \
+      : "r"(off))
+  DCG_TMEM_LD32(r, taddr);
+  DCG_TMEM_LD32((r + 32), taddr + 32u);
+#undef DCG_TMEM_LD32
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // 1-D bulk copy global -> shared completing on an mbarrier (16-byte aligned
