@@ -4,7 +4,8 @@
 //     products summed in float32 over short row runs and in float64 across them.
 //   * Cholesky factor of E and its inverse (float64, one CTA).
 //   * Harmonic Ritz extraction (Sec. 2.3, Eq. 7): diagonal scaling, Cholesky
-//     reduction C = L^{-1} G L^{-T} in float64, cyclic Jacobi eigen-solve of C,
+//     reduction C = L^{-1} G L^{-T}, symmetric eigen-solve of C (Householder
+//     tridiagonalisation, bisection, inverse iteration),
 //     selection of k values (reading R4), U = S L^{-T} V, W = Z U with unit
 //     columns whose largest-magnitude entry is positive (reading R5).
 #include "dcg_kernels.cuh"
@@ -229,15 +230,8 @@ cudaError_t chol_configure(int kmax) {
 // Y = L^{-1} G'; C (float32, shared memory) = L^{-1} G' L^{-T}.
 // --------------------------------------------------------------------------
 constexpr int EIG_THREADS = 1024;
-constexpr int EIG_MAX_SWEEPS = 30;
 constexpr int EIG_SMEM_MAX = 200 * 1024;  // dynamic shared memory of the eigen kernel
 
-__device__ void jacobi_pair(int m2, int r, int i, int& p, int& q) {
-  // circle method: s_0 = 0, s_j = 1 + ((j - 1 + r) mod (m2 - 1))
-  auto pos = [&](int j) { return j == 0 ? 0 : 1 + ((j - 1 + r) % (m2 - 1)); };
-  p = pos(i);
-  q = pos(m2 - 1 - i);
-}
 
 // Row-parallel forward substitution L Y = B for m right-hand sides (columns
 // of B, leading dimension m, overwritten with Y): for each row i the m
@@ -259,17 +253,14 @@ __device__ void trsm_lower(const float* L, float* B, int m) {
 // F, G: m x m float64 (row-major) from the Gram kernels. The pencil is scaled
 // to unit diagonal F' = S F S (S = diag(F_jj^{-1/2})); in that scaling the
 // columns of Z are nearly A-conjugate, so F' is close to the identity and the
-// reduction runs in float32: F' = L L^T, C = L^{-1} G' L^{-T}, cyclic Jacobi on
-// C, u = S L^{-T} v. (Float64 on this part has a ~57x lower throughput and long
+// reduction runs in float32: F' = L L^T, C = L^{-1} G' L^{-T}, symmetric
+// eigen-solve of C, u = S L^{-T} v. (Float64 on this part has a ~57x lower throughput and long
 // dependent-chain latency on GB300; the float32 eigenvectors only set the
 // deflation basis, whose accuracy is that of the float32 directions anyway.)
 __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, int k_new) {
   extern __shared__ float C[];  // m x (m + 1), then V^T when it fits
-  __shared__ float cs_c[kMaxM / 2 + 1], cs_s[kMaxM / 2 + 1];
-  __shared__ int pp[kMaxM / 2 + 1], qq[kMaxM / 2 + 1];
   __shared__ float scale[kMaxM];
   __shared__ int pos[kMaxM], orig[kMaxM];
-  __shared__ int s_changed;
   __shared__ float th[kMaxM];
   __shared__ int rank_of[kMaxM];
   const int t = threadIdx.x;
@@ -400,95 +391,256 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
       C[i * ldc + j] = 0.5f * (Xc[i * m + j] + Xc[j * m + i]);
       Vt[i * ldc + j] = (i == j) ? 1.f : 0.f;
     }
-  __shared__ float s_cmax;
   __syncthreads();
-  if (t == 0) {
-    float cm = 0.f;
-    for (int i = 0; i < m; ++i) cm = fmaxf(cm, fabsf(C[i * ldc + i]));
-    s_cmax = cm;
-  }
-  __syncthreads();
-  const float abs_tol = 1e-6f * s_cmax;
 
-  // 5. cyclic Jacobi (circle-method ordering; rotations of disjoint pairs
-  //    applied together). A pair is rotated while its off-diagonal entry is
-  //    above both 2e-6 sqrt(|c_pp c_qq|) and 1e-6 max|c_ii|: in float32 the
-  //    off-diagonal entries settle at rounding noise ~eps32 |C|, which a
-  //    purely relative test would chase forever.
-  const int m2 = (m + 1) & ~1;
-  const int half = m2 / 2;
+  // 5. Symmetric eigen-solve of C in three stages (one CTA):
+  //    a. Householder tridiagonalisation C = Q T Q^T, Q = H_0 ... H_{m-3},
+  //       H_j = I - tau_j v_j v_j^T with v_j(j+1) = 1; v_j is kept below the
+  //       subdiagonal of column j for the back-transformation;
+  //    b. all m eigenvalues of T by multisection on Sturm counts (a group of
+  //       threads per eigenvalue evaluates the count at evenly spaced points);
+  //    c. the selected eigenvectors of T by inverse iteration (thread per
+  //       vector), made orthonormal by modified Gram-Schmidt (near-equal
+  //       values), then z = Q y by applying the reflectors (warp per vector).
+  __shared__ float dT[kMaxM], eT[kMaxM], e2[kMaxM], tauH[kMaxM], hv[kMaxM], hw[kMaxM];
+  __shared__ float s_red[32];
+  __shared__ float s_tau, s_scal, s_K;
   const int warp = t / 32, lane = t % 32, nwarps = blockDim.x / 32;
-  for (int sweep = 0; sweep < EIG_MAX_SWEEPS; ++sweep) {
-    if (t == 0) s_changed = 0;
+  auto block_sum_f = [&](float v) -> float {
+    v = warp_sum(v);
+    if (lane == 0) s_red[warp] = v;
     __syncthreads();
-    for (int r = 0; r < m2 - 1; ++r) {
-      if (t < half) {
-        int p, q;
-        jacobi_pair(m2, r, t, p, q);
-        if (p > q) {
-          const int tmp = p;
-          p = q;
-          q = tmp;
-        }
-        float c = 1.f, sn = 0.f;
-        if (q < m) {
-          const float apq = C[p * ldc + q];
-          const float app = C[p * ldc + p], aqq = C[q * ldc + q];
-          const float aa = fabsf(apq);
-          if (aa > 2e-6f * sqrtf(fabsf(app * aqq)) && aa > abs_tol) {
-            const float tau = (aqq - app) / (2.f * apq);
-            const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            c = rsqrtf(1.f + tt * tt);
-            sn = tt * c;
-            s_changed = 1;
-          }
-        }
-        pp[t] = p;
-        qq[t] = q;
-        cs_c[t] = c;
-        cs_s[t] = sn;
-      }
-      __syncthreads();
-      // rows p, q of C <- J^T C; rows p, q of V^T <- (V J)^T
-      for (int pr = warp; pr < half; pr += nwarps) {
-        const float sn = cs_s[pr];
-        if (sn == 0.f) continue;
-        const int p = pp[pr], q = qq[pr];
-        const float c = cs_c[pr];
-        for (int j = lane; j < m; j += 32) {
-          const float a_p = C[p * ldc + j], a_q = C[q * ldc + j];
-          C[p * ldc + j] = c * a_p - sn * a_q;
-          C[q * ldc + j] = sn * a_p + c * a_q;
-          const float v_p = Vt[p * ldc + j], v_q = Vt[q * ldc + j];
-          Vt[p * ldc + j] = c * v_p - sn * v_q;
-          Vt[q * ldc + j] = sn * v_p + c * v_q;
-        }
-      }
-      __syncthreads();
-      // columns p, q of C <- C J
-      for (int pr = warp; pr < half; pr += nwarps) {
-        const float sn = cs_s[pr];
-        if (sn == 0.f) continue;
-        const int p = pp[pr], q = qq[pr];
-        const float c = cs_c[pr];
-        for (int i = lane; i < m; i += 32) {
-          const float a_p = C[i * ldc + p], a_q = C[i * ldc + q];
-          C[i * ldc + p] = c * a_p - sn * a_q;
-          C[i * ldc + q] = sn * a_p + c * a_q;
-        }
-      }
-      __syncthreads();
+    float r = 0.f;
+    if (warp == 0) {
+      r = lane < nwarps ? s_red[lane] : 0.f;
+      r = warp_sum(r);
     }
-    if (!s_changed) break;
+    __syncthreads();
+    if (t == 0) s_red[0] = r;
+    __syncthreads();
+    r = s_red[0];
+    __syncthreads();
+    return r;
+  };
+  // a. tridiagonalisation
+  for (int j = 0; j + 2 < m; ++j) {
+    const int Lh = m - j - 1;  // rows j+1 .. m-1
+    float part = 0.f;
+    for (int i = t + 1; i < Lh; i += blockDim.x) {
+      const float x = C[(j + 1 + i) * ldc + j];
+      part = fmaf(x, x, part);
+    }
+    const float sigma = block_sum_f(part);
+    if (t == 0) {
+      const float x0 = C[(j + 1) * ldc + j];
+      dT[j] = C[j * ldc + j];
+      if (sigma == 0.f) {
+        s_tau = 0.f;
+        s_scal = 0.f;
+        eT[j] = x0;
+      } else {
+        const float mu = sqrtf(fmaf(x0, x0, sigma));
+        const float beta = x0 <= 0.f ? mu : -mu;
+        s_tau = (beta - x0) / beta;
+        s_scal = 1.f / (x0 - beta);
+        eT[j] = beta;
+      }
+      tauH[j] = s_tau;
+    }
+    __syncthreads();
+    const float tau = s_tau, scal = s_scal;
+    for (int i = t; i < Lh; i += blockDim.x) {
+      const float v = i == 0 ? 1.f : C[(j + 1 + i) * ldc + j] * scal;
+      hv[i] = v;
+      if (i > 0) C[(j + 1 + i) * ldc + j] = v;
+    }
+    __syncthreads();
+    if (tau == 0.f) continue;
+    // p = tau A' v (A' = C[j+1.., j+1..]), one warp per row
+    for (int i = warp; i < Lh; i += nwarps) {
+      const float* row = C + (j + 1 + i) * ldc + (j + 1);
+      float sdot = 0.f;
+      for (int k = lane; k < Lh; k += 32) sdot = fmaf(row[k], hv[k], sdot);
+      sdot = warp_sum(sdot);
+      if (lane == 0) hw[i] = tau * sdot;
+    }
+    __syncthreads();
+    float pv = 0.f;
+    for (int i = t; i < Lh; i += blockDim.x) pv = fmaf(hw[i], hv[i], pv);
+    pv = block_sum_f(pv);
+    const float K = 0.5f * tau * pv;
+    for (int i = t; i < Lh; i += blockDim.x) hw[i] = fmaf(-K, hv[i], hw[i]);  // w = p - K v
+    __syncthreads();
+    // A' -= v w^T + w v^T
+    for (int idx = t; idx < Lh * Lh; idx += blockDim.x) {
+      const int i = idx / Lh, k = idx - i * Lh;
+      float* cij = C + (j + 1 + i) * ldc + (j + 1 + k);
+      *cij = fmaf(-hv[i], hw[k], fmaf(-hw[i], hv[k], *cij));
+    }
+    __syncthreads();
   }
-  // 6. order the values (descending, ties by lower index) and select
-  for (int i = t; i < m; i += blockDim.x) th[i] = C[i * ldc + i];
+  if (t == 0) {
+    if (m >= 2) {
+      dT[m - 2] = C[(m - 2) * ldc + (m - 2)];
+      eT[m - 2] = C[(m - 1) * ldc + (m - 2)];
+    }
+    dT[m - 1] = C[(m - 1) * ldc + (m - 1)];
+  }
   __syncthreads();
+  for (int i = t; i + 1 < m; i += blockDim.x) e2[i] = eT[i] * eT[i];
+  __shared__ float s_lo, s_hi;
+  if (warp == 0) {  // Gershgorin bounds
+    float lo = 3.4e38f, hi = -3.4e38f;
+    for (int i = lane; i < m; i += 32) {
+      const float r = (i > 0 ? fabsf(eT[i - 1]) : 0.f) + (i + 1 < m ? fabsf(eT[i]) : 0.f);
+      lo = fminf(lo, dT[i] - r);
+      hi = fmaxf(hi, dT[i] + r);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      const float pad = 1e-6f * fmaxf(fabsf(lo), fabsf(hi)) + 1e-30f;
+      s_lo = lo - pad;
+      s_hi = hi + pad;
+    }
+  }
+  __syncthreads();
+  // b. eigenvalue r (ascending) in [elo[r], ehi[r]]: count(x) = #{lambda < x}
+  __shared__ float elo[kMaxM], ehi[kMaxM];
+  __shared__ unsigned char cnt_le[EIG_THREADS];
+  const int grp = max(1, int(blockDim.x) / m);  // threads per eigenvalue
+  for (int r = t; r < m; r += blockDim.x) {
+    elo[r] = s_lo;
+    ehi[r] = s_hi;
+  }
+  __syncthreads();
+  const float tiny = 1e-30f;
+  auto sturm = [&](float x) -> int {
+    float q = dT[0] - x;
+    int c = q < 0.f;
+    for (int i = 1; i < m; ++i) {
+      const float qq = fabsf(q) < tiny ? -tiny : q;
+      q = (dT[i] - x) - __fdividef(e2[i - 1], qq);
+      c += q < 0.f;
+    }
+    return c;
+  };
+  const int my_r = t / grp, my_s = t - my_r * grp;
+  for (int round = 0; round < 64; ++round) {
+    if (my_r < m) {
+      const float lo = elo[my_r], hi = ehi[my_r];
+      const float x = lo + (hi - lo) * float(my_s + 1) / float(grp + 1);
+      cnt_le[t] = sturm(x) <= my_r ? 1 : 0;  // lambda_r >= x
+    }
+    __syncthreads();
+    __shared__ int s_more;
+    if (t == 0) s_more = 0;
+    __syncthreads();
+    if (my_r < m && my_s == 0) {
+      const float lo = elo[my_r], hi = ehi[my_r];
+      float nlo = lo, nhi = hi;
+      for (int q = 0; q < grp; ++q) {
+        const float x = lo + (hi - lo) * float(q + 1) / float(grp + 1);
+        if (cnt_le[my_r * grp + q]) {
+          nlo = x;
+        } else {
+          nhi = x;
+          break;
+        }
+      }
+      elo[my_r] = nlo;
+      ehi[my_r] = nhi;
+      if (nhi - nlo > 1e-7f * (fabsf(nlo) + fabsf(nhi)) + 2e-7f * fmaxf(fabsf(s_lo), fabsf(s_hi))) s_more = 1;
+    }
+    __syncthreads();
+    if (!s_more) break;
+  }
   for (int i = t; i < m; i += blockDim.x) {
-    int rk = 0;
-    for (int j = 0; j < m; ++j) rk += (th[j] > th[i]) || (th[j] == th[i] && j < i);
-    rank_of[i] = rk;
-    a.theta[rk] = double(th[i]);
+    th[i] = 0.5f * (elo[i] + ehi[i]);
+    rank_of[i] = m - 1 - i;  // descending rank; ascending index order
+    a.theta[m - 1 - i] = double(th[i]);
+  }
+  __syncthreads();
+  // c. eigenvectors of T for the selected indices (rows of Vt), then z = Q y
+  const bool smallest = a.select == DCG_SELECT_SMALLEST;
+  float* ytmp = Xc;  // per-vector work rows (m floats each)
+  const float piv_tiny = 1e-7f * fmaxf(fabsf(s_lo), fabsf(s_hi)) + 1e-30f;  // eps |T|
+  for (int c = t; c < k_new; c += blockDim.x) {
+    const int r = smallest ? c : (m - 1 - c);
+    const float lam = th[r];
+    float* y = Vt + r * ldc;
+    float* u = ytmp + int64_t(c) * m;  // U diagonal of the LU of T - lam I
+    for (int i = 0; i < m; ++i) y[i] = 1.f + 0.0137f * float((i * 7 + c * 3) % 11);
+    for (int itn = 0; itn < 3; ++itn) {
+      // LU of T - lam I without pivoting (tiny pivots perturbed), forward and
+      // back substitution on y; then normalise
+      float ui = dT[0] - lam;
+      if (fabsf(ui) < piv_tiny) ui = piv_tiny;
+      u[0] = ui;
+      for (int i = 1; i < m; ++i) {
+        const float l = eT[i - 1] / u[i - 1];
+        y[i] = fmaf(-l, y[i - 1], y[i]);
+        ui = fmaf(-l, eT[i - 1], dT[i] - lam);
+        if (fabsf(ui) < piv_tiny) ui = piv_tiny;
+        u[i] = ui;
+      }
+      y[m - 1] = y[m - 1] / u[m - 1];
+      for (int i = m - 2; i >= 0; --i) y[i] = fmaf(-eT[i], y[i + 1], y[i]) / u[i];
+      float nrm = 0.f;
+      for (int i = 0; i < m; ++i) nrm = fmaf(y[i], y[i], nrm);
+      const float inv = nrm > 0.f && isfinite(nrm) ? rsqrtf(nrm) : 0.f;
+      for (int i = 0; i < m; ++i) y[i] *= inv;
+    }
+  }
+  __syncthreads();
+  // modified Gram-Schmidt over the selected vectors (in selection order)
+  for (int c = 1; c < k_new; ++c) {
+    const int r = smallest ? c : (m - 1 - c);
+    float* y = Vt + r * ldc;
+    __shared__ float s_dot[kMaxM];
+    for (int c2 = warp; c2 < c; c2 += nwarps) {
+      const int r2 = smallest ? c2 : (m - 1 - c2);
+      const float* y2 = Vt + r2 * ldc;
+      float sdot = 0.f;
+      for (int i = lane; i < m; i += 32) sdot = fmaf(y[i], y2[i], sdot);
+      sdot = warp_sum(sdot);
+      if (lane == 0) s_dot[c2] = sdot;
+    }
+    __syncthreads();
+    for (int i = t; i < m; i += blockDim.x) {
+      float v = y[i];
+      for (int c2 = 0; c2 < c; ++c2) v = fmaf(-s_dot[c2], Vt[(smallest ? c2 : (m - 1 - c2)) * ldc + i], v);
+      y[i] = v;
+    }
+    __syncthreads();
+    float nn = 0.f;
+    for (int i = t; i < m; i += blockDim.x) nn = fmaf(y[i], y[i], nn);
+    nn = block_sum_f(nn);
+    const float inv = nn > 0.f ? rsqrtf(nn) : 0.f;
+    for (int i = t; i < m; i += blockDim.x) y[i] *= inv;
+    __syncthreads();
+  }
+  // z = H_0 H_1 ... H_{m-3} y: apply H_{m-3} first; one warp per vector
+  for (int c = warp; c < k_new; c += nwarps) {
+    float* y = Vt + (smallest ? c : (m - 1 - c)) * ldc;
+    for (int j = m - 3; j >= 0; --j) {
+      const float tau = tauH[j];
+      if (tau == 0.f) continue;
+      const int Lh = m - j - 1;
+      float sdot = 0.f;
+      for (int i = lane; i < Lh; i += 32) {
+        const float v = i == 0 ? 1.f : C[(j + 1 + i) * ldc + j];
+        sdot = fmaf(v, y[j + 1 + i], sdot);
+      }
+      sdot = warp_sum(sdot) * tau;
+      for (int i = lane; i < Lh; i += 32) {
+        const float v = i == 0 ? 1.f : C[(j + 1 + i) * ldc + j];
+        y[j + 1 + i] = fmaf(-sdot, v, y[j + 1 + i]);
+      }
+      __syncwarp();
+    }
   }
   __syncthreads();
   // 7. U[:, c] = S L^{-T} v_sel(c) on the kept rows (dropped rows are zero):
