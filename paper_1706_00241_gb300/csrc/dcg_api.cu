@@ -223,6 +223,7 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   CKC(cudaEventCreate(&c->ev1));
   CKC(cudaEventCreate(&c->ev2));
   CKC(rowop_configure());
+  CKC(apply_block_configure());
   CKC(iter_configure());
   CKC(rbf_mv_configure());
   CKC(chol_configure(96));

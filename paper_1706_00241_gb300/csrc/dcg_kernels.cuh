@@ -181,6 +181,7 @@ cudaError_t launch_matvec_noalloc(const CUtensorMap* tmap, const float* p, float
                                   void* scratch, cudaStream_t s);
 cudaError_t launch_apply_block(const ApplyBlockArgs& a, int cmax, float* scratch, int num_sms, cudaStream_t s);
 size_t apply_block_scratch_floats(int n, int cmax, int num_sms);
+cudaError_t apply_block_configure();
 cudaError_t launch_form_rbf(const float* X, int n, int d, double l, double s2, double noise, float* A, int64_t lda,
                             cudaStream_t s);
 

@@ -416,10 +416,15 @@ bool make_rowop_tmap(CUtensorMap* map, const float* A, int64_t n, int64_t lda, E
 constexpr int AB_ROWS = 256;
 constexpr int AB_K = 32;
 constexpr int AB_CB = 32;
+constexpr int AB_LDS = AB_ROWS + 4;   // row stride of the transposed A tile (16-byte aligned)
+constexpr size_t AB_SMEM = size_t(2) * (AB_K * AB_LDS + AB_K * (AB_CB + 4)) * sizeof(float);
 
-__global__ void __launch_bounds__(AB_ROWS) k_apply_block(ApplyBlockArgs a, int kchunk, float* part) {
-  __shared__ float As[AB_K][AB_ROWS + 1];
-  __shared__ __align__(16) float Vs[AB_K][AB_CB + 4];
+// Thread t computes rows 4 (t % 64) .. + 3 and columns 8 (t / 64) .. + 7 of
+// the CTA's 256 x 32 output tile (one float4 of A and two broadcast float4 of
+// V per K, 32 FMAs). The next K-step's tiles are loaded into registers while
+// the current one is computed, then stored into the other shared-memory half.
+__global__ void __launch_bounds__(AB_ROWS, 2) k_apply_block(ApplyBlockArgs a, int kchunk, float* part) {
+  extern __shared__ __align__(16) float ab_smem[];
   int c = a.c;
   const float* V = a.V;
   float* Y = a.Y;
@@ -436,12 +441,15 @@ __global__ void __launch_bounds__(AB_ROWS) k_apply_block(ApplyBlockArgs a, int k
   const int row0 = blockIdx.x * AB_ROWS;
   const int k_lo = blockIdx.y * kchunk, k_hi = min(n, k_lo + kchunk);
   const int t = threadIdx.x;
+  const int rg = t & 63, cg = t >> 6;
   const bool vec_ok = (a.lda % 4) == 0 && (reinterpret_cast<uintptr_t>(a.A) & 15) == 0;
-  float acc[AB_CB];
-#pragma unroll
-  for (int j = 0; j < AB_CB; ++j) acc[j] = 0.f;
-  for (int k0 = k_lo; k0 < k_hi; k0 += AB_K) {
-    // A tile: 256 rows x 32 columns, 8 float4 per thread, stored transposed
+  // buffer b: A tile at ab_smem + b * AB_K * AB_LDS, V tile after both A tiles
+  auto a_buf = [&](int b) { return ab_smem + b * (AB_K * AB_LDS); };
+  auto v_buf = [&](int b) { return ab_smem + 2 * (AB_K * AB_LDS) + b * (AB_K * (AB_CB + 4)); };
+
+  float4 pa[(AB_ROWS * AB_K / 4) / AB_ROWS];
+  float pv[(AB_K * AB_CB) / AB_ROWS];
+  auto load_tile = [&](int k0) {
 #pragma unroll
     for (int q = 0; q < (AB_ROWS * AB_K / 4) / AB_ROWS; ++q) {
       const int idx = q * AB_ROWS + t;
@@ -459,47 +467,85 @@ __global__ void __launch_bounds__(AB_ROWS) k_apply_block(ApplyBlockArgs a, int k
           v.w = gk + 3 < k_hi ? __ldg(src + 3) : 0.f;
         }
       }
-      As[4 * c4 + 0][r] = v.x;
-      As[4 * c4 + 1][r] = v.y;
-      As[4 * c4 + 2][r] = v.z;
-      As[4 * c4 + 3][r] = v.w;
+      pa[q] = v;
     }
-    // V tile: 32 k-rows x 32 columns (coalesced along k)
 #pragma unroll
     for (int q = 0; q < (AB_K * AB_CB) / AB_ROWS; ++q) {
       const int idx = q * AB_ROWS + t;
       const int j = idx / AB_K, kk = idx % AB_K;
       const int gk = k0 + kk;
-      Vs[kk][j] = (j < cw && gk < k_hi) ? __ldg(V + int64_t(col0 + j) * n + gk) : 0.f;
+      pv[q] = (j < cw && gk < k_hi) ? __ldg(V + int64_t(col0 + j) * n + gk) : 0.f;
     }
-    __syncthreads();
-#pragma unroll 4
+  };
+  auto store_tile = [&](int b) {
+    float* as = a_buf(b);
+#pragma unroll
+    for (int q = 0; q < (AB_ROWS * AB_K / 4) / AB_ROWS; ++q) {
+      const int idx = q * AB_ROWS + t;
+      const int r = idx / (AB_K / 4), c4 = idx % (AB_K / 4);
+      as[(4 * c4 + 0) * AB_LDS + r] = pa[q].x;
+      as[(4 * c4 + 1) * AB_LDS + r] = pa[q].y;
+      as[(4 * c4 + 2) * AB_LDS + r] = pa[q].z;
+      as[(4 * c4 + 3) * AB_LDS + r] = pa[q].w;
+    }
+    float* vs = v_buf(b);
+#pragma unroll
+    for (int q = 0; q < (AB_K * AB_CB) / AB_ROWS; ++q) {
+      const int idx = q * AB_ROWS + t;
+      const int j = idx / AB_K, kk = idx % AB_K;
+      vs[kk * (AB_CB + 4) + j] = pv[q];
+    }
+  };
+
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  int cur = 0;
+  if (k_lo < k_hi) {
+    load_tile(k_lo);
+    store_tile(0);
+  }
+  __syncthreads();
+  for (int k0 = k_lo; k0 < k_hi; k0 += AB_K) {
+    const bool more = k0 + AB_K < k_hi;
+    if (more) load_tile(k0 + AB_K);  // in flight during the compute below
+    const float* as = a_buf(cur);
+    const float* vs = v_buf(cur);
+#pragma unroll 8
     for (int kk = 0; kk < AB_K; ++kk) {
-      const float av = As[kk][t];
-      const float4* vr = reinterpret_cast<const float4*>(&Vs[kk][0]);
+      const float4 av = *reinterpret_cast<const float4*>(as + kk * AB_LDS + 4 * rg);
+      const float4 v0 = *reinterpret_cast<const float4*>(vs + kk * (AB_CB + 4) + 8 * cg);
+      const float4 v1 = *reinterpret_cast<const float4*>(vs + kk * (AB_CB + 4) + 8 * cg + 4);
+      const float ar[4] = {av.x, av.y, av.z, av.w};
+      const float vr[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-      for (int j4 = 0; j4 < AB_CB / 4; ++j4) {
-        const float4 v = vr[j4];
-        acc[4 * j4 + 0] = fmaf(av, v.x, acc[4 * j4 + 0]);
-        acc[4 * j4 + 1] = fmaf(av, v.y, acc[4 * j4 + 1]);
-        acc[4 * j4 + 2] = fmaf(av, v.z, acc[4 * j4 + 2]);
-        acc[4 * j4 + 3] = fmaf(av, v.w, acc[4 * j4 + 3]);
-      }
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(ar[i], vr[j], acc[i][j]);
     }
+    if (more) store_tile(cur ^ 1);
     __syncthreads();
+    cur ^= 1;
   }
-  const int gr = row0 + t;
-  if (gr >= n) return;
-  if (gridDim.y == 1) {
+  float* dst = Y;
+  if (gridDim.y > 1) dst = part + int64_t(blockIdx.y) * (int64_t(gridDim.z) * AB_CB) * n;
 #pragma unroll
-    for (int j = 0; j < AB_CB; ++j)
-      if (j < cw) Y[int64_t(col0 + j) * n + gr] = acc[j];
-  } else {
-    float* dst = part + int64_t(blockIdx.y) * (int64_t(gridDim.z) * AB_CB) * n;
+  for (int j = 0; j < 8; ++j) {
+    const int cj = 8 * cg + j;
+    if (cj >= cw) continue;
+    float* colp = dst + int64_t(col0 + cj) * n;
 #pragma unroll
-    for (int j = 0; j < AB_CB; ++j)
-      if (j < cw) dst[int64_t(col0 + j) * n + gr] = acc[j];
+    for (int i = 0; i < 4; ++i) {
+      const int gr = row0 + 4 * rg + i;
+      if (gr < n) colp[gr] = acc[i][j];
+    }
   }
+}
+
+cudaError_t apply_block_configure() {
+  return cudaFuncSetAttribute(k_apply_block, cudaFuncAttributeMaxDynamicSharedMemorySize, int(AB_SMEM));
 }
 
 // Y[:, j] = sum over the K splits of the partials (fixed order).
@@ -550,7 +596,7 @@ cudaError_t launch_apply_block(const ApplyBlockArgs& a, int cmax, float* scratch
   const int used = (n + kchunk - 1) / kchunk;
   const int colblocks = (cmax + AB_CB - 1) / AB_CB;
   dim3 grid((n + AB_ROWS - 1) / AB_ROWS, used, colblocks);
-  k_apply_block<<<grid, AB_ROWS, 0, s>>>(a, kchunk, scratch);
+  k_apply_block<<<grid, AB_ROWS, AB_SMEM, s>>>(a, kchunk, scratch);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || used == 1) return e;
   k_block_reduce<<<2 * num_sms, 256, 0, s>>>(a, used, colblocks, scratch);
