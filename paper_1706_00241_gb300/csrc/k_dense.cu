@@ -605,68 +605,108 @@ cudaError_t launch_apply_block(const ApplyBlockArgs& a, int cmax, float* scratch
 
 // ---------------------------------------------------------------------------
 // A = s^2 exp(-|x_i - x_j|^2 / (2 l^2)) + noise [i == j]  (Sec. 3 RBF kernel)
-// 64 x 64 output tiles; X rows of the tile staged in shared memory; float32
-// difference-form squared distances.
+// 128 x 128 output tiles, 256 threads, 8 x 8 entries per thread (rows
+// 8 ty .. 8 ty + 7, columns 4 tx .. 4 tx + 3 and 64 + 4 tx .. 64 + 4 tx + 3, so
+// that each store instruction writes 256 contiguous bytes of two rows). The X
+// rows of the tile are staged transposed in shared memory, 16 dimensions per
+// pass. Squared distances in float32 difference form, two entries per packed
+// f32x2 subtract and fused multiply-add; exp(z) = 2^(z log2 e) on the
+// hardware ex2 (about 2 ulp), evaluated on the float32 argument as expf would be.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_form_rbf(const float* __restrict__ X, int n, int d, float neg_inv2l2,
-                                                  float s2, float noise, float* __restrict__ A, int64_t lda) {
-  extern __shared__ float xs[];  // [2][64][d]
-  float* xi = xs;
-  float* xj = xs + 64 * d;
-  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
-  for (int idx = threadIdx.x; idx < 64 * d; idx += 256) {
-    const int r = idx / d, m = idx % d;
-    xi[idx] = (i0 + r < n) ? X[int64_t(i0 + r) * d + m] : 0.f;
-    xj[idx] = (j0 + r < n) ? X[int64_t(j0 + r) * d + m] : 0.f;
-  }
-  __syncthreads();
-  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  float sq[4][4];
+constexpr int FR_T = 128;          // output tile edge
+constexpr int FR_DC = 16;          // dimensions per pass
+constexpr int FR_LD = FR_T + 4;    // padded row of the transposed X tiles
+
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+  return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long v) {
+  return make_float2(__uint_as_float(unsigned(v)), __uint_as_float(unsigned(v >> 32)));
+}
+// acc += (u - v) * (u - v), lane-wise on float pairs
+__device__ __forceinline__ void f2_sqdiff_acc(unsigned long long& acc, unsigned long long u, unsigned long long v) {
+  unsigned long long df;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(df) : "l"(u), "l"(v));
+  asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(acc) : "l"(df));
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__global__ void __launch_bounds__(256, 2) k_form_rbf(const float* __restrict__ X, int n, int d, float c_exp2,
+                                                     float s2, float noise, float* __restrict__ A, int64_t lda) {
+  __shared__ __align__(16) float xiT[FR_DC][FR_LD];
+  __shared__ __align__(16) float xjT[FR_DC][FR_LD];
+  const int t = threadIdx.x, ty = t / 16, tx = t % 16;
+  const int i0 = blockIdx.y * FR_T, j0 = blockIdx.x * FR_T;
+  unsigned long long sq[8][4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) sq[a][c] = 0.f;
-  for (int m = 0; m < d; ++m) {
-    float u[4], v[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) u[a] = xi[(4 * ty + a) * d + m];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) v[c] = xj[(4 * tx + c) * d + m];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float df = u[a] - v[c];
-        sq[a][c] = fmaf(df, df, sq[a][c]);
-      }
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int i = i0 + 4 * ty + a;
-    if (i >= n) continue;
-    float out[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int j = j0 + 4 * tx + c;
-      out[c] = s2 * expf(sq[a][c] * neg_inv2l2) + (i == j ? noise : 0.f);
+    for (int p = 0; p < 4; ++p) sq[a][p] = 0ull;
+  for (int m0 = 0; m0 < d; m0 += FR_DC) {
+    const int dc = min(FR_DC, d - m0);
+    if (m0 > 0) __syncthreads();
+    for (int idx = t; idx < FR_T * FR_DC; idx += 256) {
+      const int r = idx / FR_DC, mm = idx % FR_DC;
+      const bool okm = mm < dc;
+      xiT[mm][r] = (okm && i0 + r < n) ? X[int64_t(i0 + r) * d + m0 + mm] : 0.f;
+      xjT[mm][r] = (okm && j0 + r < n) ? X[int64_t(j0 + r) * d + m0 + mm] : 0.f;
     }
-    const int j = j0 + 4 * tx;
-    float* dst = A + int64_t(i) * lda + j;
-    if (j + 3 < n && (lda % 4) == 0) {
-      *reinterpret_cast<float4*>(dst) = make_float4(out[0], out[1], out[2], out[3]);
-    } else {
-      for (int c = 0; c < 4; ++c)
-        if (j + c < n) dst[c] = out[c];
+    __syncthreads();
+    for (int mm = 0; mm < dc; ++mm) {
+      const float4 ua = *reinterpret_cast<const float4*>(&xiT[mm][8 * ty]);
+      const float4 ub = *reinterpret_cast<const float4*>(&xiT[mm][8 * ty + 4]);
+      const float4 va = *reinterpret_cast<const float4*>(&xjT[mm][4 * tx]);
+      const float4 vb = *reinterpret_cast<const float4*>(&xjT[mm][64 + 4 * tx]);
+      const unsigned long long v2[4] = {f2_pack(va.x, va.y), f2_pack(va.z, va.w), f2_pack(vb.x, vb.y),
+                                        f2_pack(vb.z, vb.w)};
+      const float u[8] = {ua.x, ua.y, ua.z, ua.w, ub.x, ub.y, ub.z, ub.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const unsigned long long uu = f2_pack(u[a], u[a]);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) f2_sqdiff_acc(sq[a][p], uu, v2[p]);
+      }
+    }
+  }
+  const bool diag_tile = blockIdx.x == blockIdx.y;
+  const bool vec_ok = (lda % 4) == 0 && (reinterpret_cast<uintptr_t>(A) % 16) == 0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int i = i0 + 8 * ty + a;
+    if (i >= n) continue;
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int j = j0 + 64 * g + 4 * tx;
+      const float2 q0 = f2_unpack(sq[a][2 * g]), q1 = f2_unpack(sq[a][2 * g + 1]);
+      float out[4] = {s2 * ex2_approx(q0.x * c_exp2), s2 * ex2_approx(q0.y * c_exp2),
+                      s2 * ex2_approx(q1.x * c_exp2), s2 * ex2_approx(q1.y * c_exp2)};
+      if (diag_tile) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (i == j + c) out[c] += noise;
+      }
+      float* dst = A + int64_t(i) * lda + j;
+      if (vec_ok && j + 3 < n) {
+        *reinterpret_cast<float4*>(dst) = make_float4(out[0], out[1], out[2], out[3]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (j + c < n) dst[c] = out[c];
+      }
     }
   }
 }
 
 cudaError_t launch_form_rbf(const float* X, int n, int d, double l, double s2, double noise, float* A, int64_t lda,
                             cudaStream_t s) {
-  dim3 grid((n + 63) / 64, (n + 63) / 64);
-  const size_t smem = size_t(2) * 64 * d * sizeof(float);
-  const float neg_inv2l2 = float(-1.0 / (2.0 * l * l));
-  k_form_rbf<<<grid, 256, smem, s>>>(X, n, d, neg_inv2l2, float(s2), float(noise), A, lda);
+  dim3 grid((n + FR_T - 1) / FR_T, (n + FR_T - 1) / FR_T);
+  // exp(-sq / (2 l^2)) = 2^(sq * c), c = -log2(e) / (2 l^2)
+  const float c_exp2 = float(-1.4426950408889634 / (2.0 * l * l));
+  k_form_rbf<<<grid, 256, 0, s>>>(X, n, d, c_exp2, float(s2), float(noise), A, lda);
   return cudaGetLastError();
 }
 

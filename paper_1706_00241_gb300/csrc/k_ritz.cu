@@ -225,64 +225,159 @@ cudaError_t chol_configure(int kmax) {
 
 // --------------------------------------------------------------------------
 // Harmonic Ritz eigen-solve (one CTA of 1024 threads).
-// F, G: m x m float64 (row-major) from the Gram kernels. Work arrays in the
-// same buffers: F becomes its Cholesky factor L, G the scaled G' and then
-// Y = L^{-1} G'; C (float32, shared memory) = L^{-1} G' L^{-T}.
+// F, G: m x m float64 (row-major) from the Gram kernels. Float32 work arrays
+// in the float64 scratch buffers: F' (then the compacted Cholesky factor L)
+// and G'. Shared memory holds the pivoted Cholesky rows, then G' reduced in
+// place to C = L^{-1} G' L^{-T}, then the Householder vectors of C.
 // --------------------------------------------------------------------------
 constexpr int EIG_THREADS = 1024;
 constexpr int EIG_SMEM_MAX = 200 * 1024;  // dynamic shared memory of the eigen kernel
+constexpr int TS_P = 32;                  // panel rows of the blocked triangular solves
+constexpr int TS_CW = (kMaxM + 31) / 32;  // columns per lane in a panel update
 
+// Forward substitution L X = B in place. L: n x n lower triangular (global,
+// leading dimension ldl); B: n x ncols (shared, leading dimension ldb, odd).
+// Panels of 32 rows: a panel is first reduced by the rows solved before it
+// (one warp per panel row, lanes over columns), then solved by one warp per
+// column with lanes over the panel's rows and the panel's diagonal block
+// (reciprocal diagonal) in shared memory. Two barriers per panel.
+__device__ void trsm_lower_panels(const float* L, int ldl, float* B, int ldb, int n, int ncols,
+                                  float (*Ld)[TS_P + 1]) {
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, nw = blockDim.x >> 5;
+  for (int i0 = 0; i0 < n; i0 += TS_P) {
+    const int pr = min(TS_P, n - i0);
+    for (int idx = t; idx < TS_P * TS_P; idx += blockDim.x) {
+      const int r = idx / TS_P, q = idx % TS_P;
+      float v = 0.f;
+      if (r < pr && q <= r) {
+        v = L[(i0 + r) * ldl + i0 + q];
+        if (q == r) v = 1.f / v;
+      }
+      Ld[r][q] = v;
+    }
+    if (i0 > 0) {
+      for (int rr = warp; rr < pr; rr += nw) {
+        const float* lrow = L + (i0 + rr) * ldl;
+        float acc[TS_CW];
+#pragma unroll
+        for (int q = 0; q < TS_CW; ++q) acc[q] = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < i0; ++j) {
+          const float l = lrow[j];
+          const float* bj = B + j * ldb + lane;
+#pragma unroll
+          for (int q = 0; q < TS_CW; ++q)
+            if (lane + 32 * q < ncols) acc[q] = fmaf(l, bj[32 * q], acc[q]);
+        }
+        float* brow = B + (i0 + rr) * ldb + lane;
+#pragma unroll
+        for (int q = 0; q < TS_CW; ++q)
+          if (lane + 32 * q < ncols) brow[32 * q] -= acc[q];
+      }
+    }
+    __syncthreads();
+    for (int c = warp; c < ncols; c += nw) {
+      float x = lane < pr ? B[(i0 + lane) * ldb + c] : 0.f;
+      for (int jj = 0; jj < pr; ++jj) {
+        const float y = __shfl_sync(0xffffffffu, x, jj) * Ld[jj][jj];
+        if (lane == jj) x = y;
+        else if (lane > jj) x = fmaf(-Ld[lane][jj], y, x);
+      }
+      if (lane < pr) B[(i0 + lane) * ldb + c] = x;
+    }
+    __syncthreads();
+  }
+}
 
-// Row-parallel forward substitution L Y = B for m right-hand sides (columns
-// of B, leading dimension m, overwritten with Y): for each row i the m
-// columns are split over the threads and the dot product over j < i is
-// accumulated sequentially per column.
-__device__ void trsm_lower(const float* L, float* B, int m) {
-  for (int i = 0; i < m; ++i) {
-    const float lii = L[i * m + i];
-    for (int c = threadIdx.x; c < m; c += blockDim.x) {
-      float s = B[i * m + c];
-      for (int j = 0; j < i; ++j) s = fmaf(-L[i * m + j], B[j * m + c], s);
-      B[i * m + c] = s / lii;
+// Back substitution L^T X = B in place (same layouts as trsm_lower_panels),
+// panels from the bottom.
+__device__ void trsm_lower_t_panels(const float* L, int ldl, float* B, int ldb, int n, int ncols,
+                                    float (*Ld)[TS_P + 1]) {
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, nw = blockDim.x >> 5;
+  for (int i1 = n; i1 > 0; i1 -= TS_P) {
+    const int i0 = max(0, i1 - TS_P), pr = i1 - i0;
+    // Ld[r][q] = L^T(i0 + r, i0 + q) = L(i0 + q, i0 + r), q >= r
+    for (int idx = t; idx < TS_P * TS_P; idx += blockDim.x) {
+      const int r = idx / TS_P, q = idx % TS_P;
+      float v = 0.f;
+      if (q < pr && r <= q) {
+        v = L[(i0 + q) * ldl + i0 + r];
+        if (q == r) v = 1.f / v;
+      }
+      Ld[r][q] = v;
+    }
+    if (i1 < n) {
+      for (int rr = warp; rr < pr; rr += nw) {
+        const int i = i0 + rr;
+        float acc[TS_CW];
+#pragma unroll
+        for (int q = 0; q < TS_CW; ++q) acc[q] = 0.f;
+#pragma unroll 4
+        for (int j = i1; j < n; ++j) {
+          const float l = L[j * ldl + i];
+          const float* bj = B + j * ldb + lane;
+#pragma unroll
+          for (int q = 0; q < TS_CW; ++q)
+            if (lane + 32 * q < ncols) acc[q] = fmaf(l, bj[32 * q], acc[q]);
+        }
+        float* brow = B + i * ldb + lane;
+#pragma unroll
+        for (int q = 0; q < TS_CW; ++q)
+          if (lane + 32 * q < ncols) brow[32 * q] -= acc[q];
+      }
+    }
+    __syncthreads();
+    for (int c = warp; c < ncols; c += nw) {
+      float x = lane < pr ? B[(i0 + lane) * ldb + c] : 0.f;
+      for (int jj = pr - 1; jj >= 0; --jj) {
+        const float y = __shfl_sync(0xffffffffu, x, jj) * Ld[jj][jj];
+        if (lane == jj) x = y;
+        else if (lane < jj) x = fmaf(-Ld[lane][jj], y, x);
+      }
+      if (lane < pr) B[(i0 + lane) * ldb + c] = x;
     }
     __syncthreads();
   }
 }
 
 // Harmonic Ritz eigen-solve of Eq. 7 (one CTA of 1024 threads).
-// F, G: m x m float64 (row-major) from the Gram kernels. The pencil is scaled
-// to unit diagonal F' = S F S (S = diag(F_jj^{-1/2})); in that scaling the
-// columns of Z are nearly A-conjugate, so F' is close to the identity and the
-// reduction runs in float32: F' = L L^T, C = L^{-1} G' L^{-T}, symmetric
-// eigen-solve of C, u = S L^{-T} v. (Float64 on this part has a ~57x lower throughput and long
-// dependent-chain latency on GB300; the float32 eigenvectors only set the
-// deflation basis, whose accuracy is that of the float32 directions anyway.)
+// The pencil is scaled to unit diagonal F' = S F S (S = diag(F_jj^{-1/2})); in
+// that scaling the columns of Z are nearly A-conjugate, so F' is close to the
+// identity and the reduction runs in float32: F' = L L^T, C = L^{-1} G' L^{-T},
+// symmetric eigen-solve of C, u = S L^{-T} v. (Float64 on this part has a
+// ~57x lower throughput and long dependent-chain latency on GB300; the float32
+// eigenvectors only set the deflation basis, whose accuracy is that of the
+// float32 directions anyway.)
 __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, int k_new) {
-  extern __shared__ float C[];  // m x (m + 1), then V^T when it fits
+  extern __shared__ float C[];  // Cholesky rows; then C (m x ldc); then V^T when it fits
   __shared__ float scale[kMaxM];
   __shared__ int pos[kMaxM], orig[kMaxM];
   __shared__ float th[kMaxM];
-  __shared__ int rank_of[kMaxM];
+  __shared__ float Ld[TS_P][TS_P + 1];
   const int t = threadIdx.x;
+  const int warp = t / 32, lane = t % 32, nw = blockDim.x / 32;
   // float32 work arrays in the float64 scratch buffers
-  float* Ff = reinterpret_cast<float*>(a.Vd);       // F' (m x m), then L
-  float* Fc = Ff + m * m;                           // copy of F' for a refactorisation
-  float* Gf = reinterpret_cast<float*>(a.Vd2);      // G', then Y = L^{-1} G'
-  float* Xc = Gf + m * m;                           // C columns
-  // 1. diagonal scaling and symmetrisation (float64 sums -> float32)
+  float* Ff = reinterpret_cast<float*>(a.Vd);   // the compacted Cholesky factor L
+  float* Gf = reinterpret_cast<float*>(a.Vd2);  // G' (m x m)
+  float* Xc = Gf + m * m;                       // inverse-iteration pivots
+  // 1. diagonal scaling and symmetrisation (float64 sums rounded to float32
+  //    once, the rest in float32): F' (lower triangle) into shared memory as
+  //    S (leading dimension lds, odd), G' into global memory
+  const int lds = m | 1;
+  float* S = C;
   for (int j = t; j < m; j += blockDim.x) {
     const double f = a.F[j * m + j];
     scale[j] = f > 0.0 ? float(1.0 / sqrt(f)) : 0.f;
   }
   __syncthreads();
-  for (int idx = t; idx < m * m; idx += blockDim.x) {
-    const int i = idx / m, j = idx % m;
-    const double sij = double(scale[i]) * double(scale[j]);
-    const float f = float(0.5 * (a.F[i * m + j] + a.F[j * m + i]) * sij);
-    Ff[idx] = f;
-    Fc[idx] = f;
-    Gf[idx] = float(0.5 * (a.G[i * m + j] + a.G[j * m + i]) * sij);
-  }
+  for (int i = warp; i < m; i += nw)
+    for (int j = lane; j <= i; j += 32) {
+      const float sij = scale[i] * scale[j];
+      S[i * lds + j] = 0.5f * (float(a.F[i * m + j]) + float(a.F[j * m + i])) * sij;
+      const float g = 0.5f * (float(a.G[i * m + j]) + float(a.G[j * m + i])) * sij;
+      Gf[i * m + j] = g;
+      Gf[j * m + i] = g;
+    }
   __syncthreads();
   // 2. Diagonally pivoted Cholesky of F' (rank revealing): step k eliminates
   //    the column with the largest remaining Schur-complement diagonal and
@@ -290,63 +385,60 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
   //    1e-2 (A-norm, relative) of the span of the kept ones (rank-deficient Z,
   //    reading R6), and cond(F') of the kept part stays ~1e4, which the float32
   //    reduction handles; late float32 CG directions do lose A-conjugacy and
-  //    can make F' indefinite. Lrow[i][k] holds L(i, k) for original index i.
-  float* Lrow = Fc;                     // m x m, reuses the F' copy
-  __shared__ float dg[kMaxM];
-  __shared__ int done_[kMaxM];
-  __shared__ int s_rank, s_piv;
-  for (int j = t; j < m; j += blockDim.x) {
-    dg[j] = Ff[j * m + j];
-    done_[j] = 0;
-  }
-  if (t == 0) s_rank = 0;
+  //    can make F' indefinite. Right-looking on the lower triangle of S: step k
+  //    with pivot c subtracts S(i, c) S(j, c) / S(c, c) from the remaining
+  //    entries and leaves column c as it is, so that afterwards
+  //    L(q_a, q_b) = S(orig[q_a], orig[q_b]) / L(q_b, q_b) (pivot order).
+  //    Every warp takes the pivot itself (same data, same order), and the
+  //    remaining diagonal alternates between two arrays (eliminated columns
+  //    hold -inf), so a step needs one barrier.
+  __shared__ float dgb[2][kMaxM], lkk[kMaxM];
+  for (int j = t; j < m; j += blockDim.x) dgb[0][j] = S[j * lds + j];
   __syncthreads();
+  int mk = 0;
   for (int k = 0; k < m; ++k) {
-    if (t < 32) {  // argmax of the remaining diagonal (ties: lower index)
-      float best = -1.f;
-      int bi = m;
-      for (int j = t; j < m; j += 32)
-        if (!done_[j] && (dg[j] > best)) {
-          best = dg[j];
-          bi = j;
-        }
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) {
-          best = ob;
-          bi = oi;
-        }
+    const float* dgc = dgb[k & 1];
+    float* dgn = dgb[(k + 1) & 1];
+    float best = -1.f;  // argmax of the remaining diagonal (ties: lower index)
+    int bi = m;
+    for (int j = lane; j < m; j += 32)
+      if (dgc[j] > best) {
+        best = dgc[j];
+        bi = j;
       }
-      if (t == 0) s_piv = (best >= 1e-4f && isfinite(best)) ? bi : -1;
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
     }
-    __syncthreads();
-    const int c = s_piv;
-    if (c < 0) break;
-    const float lkk = sqrtf(dg[c]);
-    // column k of L: L(i, k) = (F'(i, c) - sum_{p<k} L(i, p) L(c, p)) / L(c, k)
-    const int warp = t / 32, lane = t % 32, nw = blockDim.x / 32;
+    if (!(best >= 1e-4f && isfinite(best))) break;
+    const int c = bi;
+    const float rb = 1.f / best;
     for (int i = warp; i < m; i += nw) {
-      if (done_[i] || i == c) continue;
-      float sdot = 0.f;
-      for (int p = lane; p < k; p += 32) sdot = fmaf(Lrow[i * m + p], Lrow[c * m + p], sdot);
-      sdot = warp_sum(sdot);
-      if (lane == 0) {
-        const float lik = (Ff[i * m + c] - sdot) / lkk;
-        Lrow[i * m + k] = lik;
-        dg[i] -= lik * lik;
+      const float di = dgc[i];
+      if (i == c || di == -INFINITY) {
+        if (lane == 0) dgn[i] = -INFINITY;
+        continue;
+      }
+      const float sic = (i > c ? S[i * lds + c] : S[c * lds + i]) * rb;
+      float* srow = S + i * lds;
+      for (int j = lane; j <= i; j += 32) {
+        if (j == c || dgc[j] == -INFINITY) continue;
+        const float v = fmaf(-sic, j > c ? S[j * lds + c] : S[c * lds + j], srow[j]);
+        srow[j] = v;
+        if (j == i) dgn[i] = v;
       }
     }
-    __syncthreads();
     if (t == 0) {
-      Lrow[c * m + k] = lkk;
-      done_[c] = 1;
       orig[k] = c;
-      s_rank = k + 1;
+      lkk[k] = sqrtf(best);
     }
+    mk = k + 1;
     __syncthreads();
   }
-  const int mk = s_rank;
   if (mk == 0) {
     if (t == 0) {
       *a.status = DCG_ERR_SUBSPACE_SINGULAR;
@@ -358,38 +450,46 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
   for (int j = t; j < m; j += blockDim.x) pos[j] = -1;
   __syncthreads();
   for (int q = t; q < mk; q += blockDim.x) pos[orig[q]] = q;
-  // compact: L (mk x mk, lower, pivot order) into Ff; G' reordered into Xc
+  // compact L (mk x mk, lower, pivot order) into Ff
   for (int idx = t; idx < mk * mk; idx += blockDim.x) {
     const int qa = idx / mk, qb = idx % mk;
-    Ff[idx] = qb <= qa ? Lrow[orig[qa] * m + qb] : 0.f;
-    Xc[idx] = Gf[orig[qa] * m + orig[qb]];
+    float v = 0.f;
+    if (qb == qa) {
+      v = lkk[qa];
+    } else if (qb < qa) {
+      const int ia = orig[qa], ib = orig[qb];
+      v = (ia > ib ? S[ia * lds + ib] : S[ib * lds + ia]) / lkk[qb];
+    }
+    Ff[idx] = v;
   }
-  __syncthreads();
-  for (int idx = t; idx < mk * mk; idx += blockDim.x) Gf[idx] = Xc[idx];
-  __syncthreads();
-  float* L = Ff;
-  float* G = Gf;
-  const int mm = mk;  // size of the reduced pencil
-  if (k_new > mm) k_new = mm;
-  // 3. Y = L^{-1} G'
-  trsm_lower(L, G, mm);
-  // 4. C = L^{-1} Y^T = L^{-1} G' L^{-T}: transpose Y into Xc and solve again
-  for (int idx = t; idx < mm * mm; idx += blockDim.x) {
-    const int i = idx / mm, j = idx % mm;
-    Xc[idx] = G[j * mm + i];
-  }
-  __syncthreads();
-  trsm_lower(L, Xc, mm);
-  m = mm;
-  // C (float32, leading dimension ldc = m + 1 so that column sweeps are free of
+  const int m_full = m;
+  m = mk;  // size of the reduced pencil
+  if (k_new > m) k_new = m;
+  // C (float32, odd leading dimension ldc so that column sweeps are free of
   // bank conflicts) and V^T (row p holds column p of V) in shared memory when
   // both fit, V^T in global memory otherwise.
-  const int ldc = m + 1;
+  const int ldc = m | 1;
   float* Vt = (2 * m * ldc * int(sizeof(float)) <= EIG_SMEM_MAX) ? C + m * ldc : a.Vj;
-  for (int i = t / 32; i < m; i += blockDim.x / 32)
-    for (int j = t % 32; j < m; j += 32) {
-      C[i * ldc + j] = 0.5f * (Xc[i * m + j] + Xc[j * m + i]);
-      Vt[i * ldc + j] = (i == j) ? 1.f : 0.f;
+  __syncthreads();
+  // G' in pivot order into shared memory
+  for (int i = warp; i < m; i += nw)
+    for (int j = lane; j < m; j += 32) C[i * ldc + j] = Gf[orig[i] * m_full + orig[j]];
+  __syncthreads();
+  // 3. Y = L^{-1} G'; 4. C = L^{-1} Y^T = L^{-1} G' L^{-T}, symmetrised
+  trsm_lower_panels(Ff, m, C, ldc, m, m, Ld);
+  for (int i = warp; i < m; i += nw)
+    for (int j = i + 1 + lane; j < m; j += 32) {
+      const float u = C[i * ldc + j];
+      C[i * ldc + j] = C[j * ldc + i];
+      C[j * ldc + i] = u;
+    }
+  __syncthreads();
+  trsm_lower_panels(Ff, m, C, ldc, m, m, Ld);
+  for (int i = warp; i < m; i += nw)
+    for (int j = i + 1 + lane; j < m; j += 32) {
+      const float s = 0.5f * (C[i * ldc + j] + C[j * ldc + i]);
+      C[i * ldc + j] = s;
+      C[j * ldc + i] = s;
     }
   __syncthreads();
 
@@ -400,84 +500,103 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
   //    b. all m eigenvalues of T by multisection on Sturm counts (a group of
   //       threads per eigenvalue evaluates the count at evenly spaced points);
   //    c. the selected eigenvectors of T by inverse iteration (thread per
-  //       vector), made orthonormal by modified Gram-Schmidt (near-equal
-  //       values), then z = Q y by applying the reflectors (warp per vector).
-  __shared__ float dT[kMaxM], eT[kMaxM], e2[kMaxM], tauH[kMaxM], hv[kMaxM], hw[kMaxM];
-  __shared__ float s_red[32];
-  __shared__ float s_tau, s_scal, s_K;
-  const int warp = t / 32, lane = t % 32, nwarps = blockDim.x / 32;
-  auto block_sum_f = [&](float v) -> float {
-    v = warp_sum(v);
-    if (lane == 0) s_red[warp] = v;
-    __syncthreads();
-    float r = 0.f;
-    if (warp == 0) {
-      r = lane < nwarps ? s_red[lane] : 0.f;
-      r = warp_sum(r);
-    }
-    __syncthreads();
-    if (t == 0) s_red[0] = r;
-    __syncthreads();
-    r = s_red[0];
-    __syncthreads();
-    return r;
-  };
-  // a. tridiagonalisation
+  //       vector), made orthonormal by Gram-Schmidt in selection order
+  //       (near-equal values), then z = Q y by applying the reflectors.
+  __shared__ float dT[kMaxM], eT[kMaxM], e2[kMaxM], tauH[kMaxM], hw[kMaxM];
+  // a. tridiagonalisation; per step every warp forms the reflector of column
+  //    j itself (v_k for k = lane + 32 q in registers), then one warp per row
+  //    forms p = tau A' v; after a barrier every warp forms K = tau/2 p^T v
+  //    and updates its rows of A' -= v w^T + w v^T with w = p - K v. Column j
+  //    is not read after step j; warp 0 stores the scaled v_j into it during
+  //    step j + 1.
+  static_assert(EIG_THREADS == 1024, "tridiagonalisation assumes 32 warps");
+  constexpr int RQ = (kMaxM + 31) / 32;  // rows per warp and entries per lane
+  float scal_prev = 0.f;
   for (int j = 0; j + 2 < m; ++j) {
     const int Lh = m - j - 1;  // rows j+1 .. m-1
+    if (warp == 0 && j > 0) {
+      const int jp = j - 1, Lp = Lh + 1;
+      for (int i = lane + 1; i < Lp; i += 32) C[(jp + 1 + i) * ldc + jp] *= scal_prev;
+    }
+    float x[RQ];
     float part = 0.f;
-    for (int i = t + 1; i < Lh; i += blockDim.x) {
-      const float x = C[(j + 1 + i) * ldc + j];
-      part = fmaf(x, x, part);
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+      const int i = lane + 32 * q;
+      x[q] = i < Lh ? C[(j + 1 + i) * ldc + j] : 0.f;
+      if (i > 0) part = fmaf(x[q], x[q], part);
     }
-    const float sigma = block_sum_f(part);
+    const float sigma = warp_sum(part);
+    const float x0 = __shfl_sync(0xffffffffu, x[0], 0);
+    float tau = 0.f, scal = 0.f, beta = x0;
+    if (sigma != 0.f) {
+      const float mu = sqrtf(fmaf(x0, x0, sigma));
+      beta = x0 <= 0.f ? mu : -mu;
+      tau = (beta - x0) / beta;
+      scal = 1.f / (x0 - beta);
+    }
     if (t == 0) {
-      const float x0 = C[(j + 1) * ldc + j];
       dT[j] = C[j * ldc + j];
-      if (sigma == 0.f) {
-        s_tau = 0.f;
-        s_scal = 0.f;
-        eT[j] = x0;
-      } else {
-        const float mu = sqrtf(fmaf(x0, x0, sigma));
-        const float beta = x0 <= 0.f ? mu : -mu;
-        s_tau = (beta - x0) / beta;
-        s_scal = 1.f / (x0 - beta);
-        eT[j] = beta;
+      eT[j] = beta;
+      tauH[j] = tau;
+    }
+    scal_prev = scal;
+    float v[RQ];
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) v[q] = (lane + 32 * q == 0) ? 1.f : x[q] * scal;
+    if (tau == 0.f) {  // uniform: every warp computed the same tau
+      __syncthreads();  // column j is read by every warp before warp 0 scales it
+      continue;
+    }
+    float dd[RQ];
+#pragma unroll
+    for (int r = 0; r < RQ; ++r) {
+      const int i = warp + 32 * r;
+      dd[r] = 0.f;
+      if (i < Lh) {
+        const float* row = C + (j + 1 + i) * ldc + (j + 1);
+#pragma unroll
+        for (int q = 0; q < RQ; ++q)
+          if (lane + 32 * q < Lh) dd[r] = fmaf(row[lane + 32 * q], v[q], dd[r]);
       }
-      tauH[j] = s_tau;
+    }
+#pragma unroll
+    for (int r = 0; r < RQ; ++r)
+      if (warp + 32 * r < Lh) {
+        const float s_ = warp_sum(dd[r]);
+        if (lane == 0) hw[warp + 32 * r] = tau * s_;
+      }
+    __syncthreads();
+    float pv = 0.f, w[RQ];
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+      const int k = lane + 32 * q;
+      w[q] = k < Lh ? hw[k] : 0.f;
+      pv = fmaf(w[q], v[q], pv);
+    }
+    const float K = 0.5f * tau * warp_sum(pv);
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) w[q] = fmaf(-K, v[q], w[q]);
+#pragma unroll
+    for (int r = 0; r < RQ; ++r) {
+      const int i = warp + 32 * r;
+      if (i < Lh) {
+        const float vi = i == 0 ? 1.f : C[(j + 1 + i) * ldc + j] * scal;
+        const float wi = fmaf(-K, vi, hw[i]);
+        float* crow = C + (j + 1 + i) * ldc + (j + 1);
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+          const int k = lane + 32 * q;
+          if (k < Lh) crow[k] = fmaf(-vi, w[q], fmaf(-wi, v[q], crow[k]));
+        }
+      }
     }
     __syncthreads();
-    const float tau = s_tau, scal = s_scal;
-    for (int i = t; i < Lh; i += blockDim.x) {
-      const float v = i == 0 ? 1.f : C[(j + 1 + i) * ldc + j] * scal;
-      hv[i] = v;
-      if (i > 0) C[(j + 1 + i) * ldc + j] = v;
-    }
-    __syncthreads();
-    if (tau == 0.f) continue;
-    // p = tau A' v (A' = C[j+1.., j+1..]), one warp per row
-    for (int i = warp; i < Lh; i += nwarps) {
-      const float* row = C + (j + 1 + i) * ldc + (j + 1);
-      float sdot = 0.f;
-      for (int k = lane; k < Lh; k += 32) sdot = fmaf(row[k], hv[k], sdot);
-      sdot = warp_sum(sdot);
-      if (lane == 0) hw[i] = tau * sdot;
-    }
-    __syncthreads();
-    float pv = 0.f;
-    for (int i = t; i < Lh; i += blockDim.x) pv = fmaf(hw[i], hv[i], pv);
-    pv = block_sum_f(pv);
-    const float K = 0.5f * tau * pv;
-    for (int i = t; i < Lh; i += blockDim.x) hw[i] = fmaf(-K, hv[i], hw[i]);  // w = p - K v
-    __syncthreads();
-    // A' -= v w^T + w v^T
-    for (int idx = t; idx < Lh * Lh; idx += blockDim.x) {
-      const int i = idx / Lh, k = idx - i * Lh;
-      float* cij = C + (j + 1 + i) * ldc + (j + 1 + k);
-      *cij = fmaf(-hv[i], hw[k], fmaf(-hw[i], hv[k], *cij));
-    }
-    __syncthreads();
+  }
+  __syncthreads();
+  if (warp == 0 && m >= 3) {  // scaled v of the last reflector
+    const int jp = m - 3, Lp = 2;
+    for (int i = lane + 1; i < Lp; i += 32) C[(jp + 1 + i) * ldc + jp] *= scal_prev;
   }
   if (t == 0) {
     if (m >= 2) {
@@ -559,72 +678,93 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
   }
   for (int i = t; i < m; i += blockDim.x) {
     th[i] = 0.5f * (elo[i] + ehi[i]);
-    rank_of[i] = m - 1 - i;  // descending rank; ascending index order
-    a.theta[m - 1 - i] = double(th[i]);
+    a.theta[m - 1 - i] = double(th[i]);  // descending
   }
   __syncthreads();
-  // c. eigenvectors of T for the selected indices (rows of Vt), then z = Q y
+  // c. eigenvectors of T for the selected indices (rows of Vt): the c-th
+  //    selected vector is the eigenvalue of ascending index c (smallest) or
+  //    m-1-c (largest).
   const bool smallest = a.select == DCG_SELECT_SMALLEST;
-  float* ytmp = Xc;  // per-vector work rows (m floats each)
+  auto vrow = [&](int c) -> float* { return Vt + (smallest ? c : (m - 1 - c)) * ldc; };
   const float piv_tiny = 1e-7f * fmaxf(fabsf(s_lo), fabsf(s_hi)) + 1e-30f;  // eps |T|
   for (int c = t; c < k_new; c += blockDim.x) {
-    const int r = smallest ? c : (m - 1 - c);
-    const float lam = th[r];
-    float* y = Vt + r * ldc;
-    float* u = ytmp + int64_t(c) * m;  // U diagonal of the LU of T - lam I
-    for (int i = 0; i < m; ++i) y[i] = 1.f + 0.0137f * float((i * 7 + c * 3) % 11);
-    for (int itn = 0; itn < 3; ++itn) {
-      // LU of T - lam I without pivoting (tiny pivots perturbed), forward and
-      // back substitution on y; then normalise
-      float ui = dT[0] - lam;
+    const float lam = th[smallest ? c : (m - 1 - c)];
+    float* __restrict__ y = vrow(c);
+    float* __restrict__ ru = Xc + c * m;  // reciprocal pivots of T - lam I
+    // LU of T - lam I without pivoting (tiny pivots perturbed), computed once;
+    // l_i = e_{i-1} / u_{i-1}
+    float ui = dT[0] - lam;
+    if (fabsf(ui) < piv_tiny) ui = piv_tiny;
+    float rprev = 1.f / ui;
+    ru[0] = rprev;
+    for (int i = 1; i < m; ++i) {
+      const float l = eT[i - 1] * rprev;
+      ui = fmaf(-l, eT[i - 1], dT[i] - lam);
       if (fabsf(ui) < piv_tiny) ui = piv_tiny;
-      u[0] = ui;
+      rprev = 1.f / ui;
+      ru[i] = rprev;
+    }
+    for (int i = 0; i < m; ++i) y[i] = 1.f + 0.0137f * float((i * 7 + c * 3) % 11);
+    for (int itn = 0; itn < 3; ++itn) {  // forward and back substitution, normalise
+      float yp = y[0];
       for (int i = 1; i < m; ++i) {
-        const float l = eT[i - 1] / u[i - 1];
-        y[i] = fmaf(-l, y[i - 1], y[i]);
-        ui = fmaf(-l, eT[i - 1], dT[i] - lam);
-        if (fabsf(ui) < piv_tiny) ui = piv_tiny;
-        u[i] = ui;
+        yp = fmaf(-eT[i - 1] * ru[i - 1], yp, y[i]);
+        y[i] = yp;
       }
-      y[m - 1] = y[m - 1] / u[m - 1];
-      for (int i = m - 2; i >= 0; --i) y[i] = fmaf(-eT[i], y[i + 1], y[i]) / u[i];
-      float nrm = 0.f;
-      for (int i = 0; i < m; ++i) nrm = fmaf(y[i], y[i], nrm);
+      float yn = y[m - 1] * ru[m - 1];
+      y[m - 1] = yn;
+      float nrm = yn * yn;
+      for (int i = m - 2; i >= 0; --i) {
+        yn = fmaf(-eT[i], yn, y[i]) * ru[i];
+        y[i] = yn;
+        nrm = fmaf(yn, yn, nrm);
+      }
       const float inv = nrm > 0.f && isfinite(nrm) ? rsqrtf(nrm) : 0.f;
       for (int i = 0; i < m; ++i) y[i] *= inv;
     }
   }
   __syncthreads();
-  // modified Gram-Schmidt over the selected vectors (in selection order)
+  // Gram-Schmidt over the selected vectors in selection order, normalisation
+  // deferred: step c takes the dot products of y_c with every earlier vector
+  // (and |y_{c-1}|^2), then subtracts (y_c . y_c2) / |y_c2|^2 y_c2; two
+  // barriers per step.
+  __shared__ float s_dot[kMaxM], s_inv2[kMaxM];
   for (int c = 1; c < k_new; ++c) {
-    const int r = smallest ? c : (m - 1 - c);
-    float* y = Vt + r * ldc;
-    __shared__ float s_dot[kMaxM];
-    for (int c2 = warp; c2 < c; c2 += nwarps) {
-      const int r2 = smallest ? c2 : (m - 1 - c2);
-      const float* y2 = Vt + r2 * ldc;
+    float* y = vrow(c);
+    for (int c2 = warp; c2 < c; c2 += nw) {
+      const float* y2 = vrow(c2);
       float sdot = 0.f;
       for (int i = lane; i < m; i += 32) sdot = fmaf(y[i], y2[i], sdot);
       sdot = warp_sum(sdot);
       if (lane == 0) s_dot[c2] = sdot;
     }
+    if (warp == nw - 1) {
+      const float* y1 = vrow(c - 1);
+      float nn = 0.f;
+      for (int i = lane; i < m; i += 32) nn = fmaf(y1[i], y1[i], nn);
+      nn = warp_sum(nn);
+      if (lane == 0) s_inv2[c - 1] = nn > 0.f ? 1.f / nn : 0.f;
+    }
     __syncthreads();
     for (int i = t; i < m; i += blockDim.x) {
       float v = y[i];
-      for (int c2 = 0; c2 < c; ++c2) v = fmaf(-s_dot[c2], Vt[(smallest ? c2 : (m - 1 - c2)) * ldc + i], v);
+      for (int c2 = 0; c2 < c; ++c2) v = fmaf(-s_dot[c2] * s_inv2[c2], vrow(c2)[i], v);
       y[i] = v;
     }
     __syncthreads();
-    float nn = 0.f;
-    for (int i = t; i < m; i += blockDim.x) nn = fmaf(y[i], y[i], nn);
-    nn = block_sum_f(nn);
-    const float inv = nn > 0.f ? rsqrtf(nn) : 0.f;
-    for (int i = t; i < m; i += blockDim.x) y[i] *= inv;
-    __syncthreads();
   }
+  for (int c = warp; c < k_new; c += nw) {
+    float* y = vrow(c);
+    float nn = 0.f;
+    for (int i = lane; i < m; i += 32) nn = fmaf(y[i], y[i], nn);
+    nn = warp_sum(nn);
+    const float inv = nn > 0.f ? rsqrtf(nn) : 0.f;
+    for (int i = lane; i < m; i += 32) y[i] *= inv;
+  }
+  __syncthreads();
   // z = H_0 H_1 ... H_{m-3} y: apply H_{m-3} first; one warp per vector
-  for (int c = warp; c < k_new; c += nwarps) {
-    float* y = Vt + (smallest ? c : (m - 1 - c)) * ldc;
+  for (int c = warp; c < k_new; c += nw) {
+    float* y = vrow(c);
     for (int j = m - 3; j >= 0; --j) {
       const float tau = tauH[j];
       if (tau == 0.f) continue;
@@ -644,30 +784,20 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
   }
   __syncthreads();
   // 7. U[:, c] = S L^{-T} v_sel(c) on the kept rows (dropped rows are zero):
-  //    back substitution L^T y = v (one warp per vector), then scale
+  //    back substitution L^T Y = [v_sel(0) ...] with Y (m x k_new, odd leading
+  //    dimension) in the shared memory that held C, then scale
   const int m_orig = a.k_act + a.nstored;
-  {
-    const int warp = t / 32, lane = t % 32, nw = blockDim.x / 32;
-    for (int c = warp; c < k_new; c += nw) {
-      const int want = (a.select == DCG_SELECT_SMALLEST) ? (m - 1 - c) : c;
-      int sel = -1;
-      for (int i = lane; i < m; i += 32)
-        if (rank_of[i] == want) sel = i;
-      for (int o = 16; o > 0; o >>= 1) sel = max(sel, __shfl_xor_sync(0xffffffffu, sel, o));
-      float* y = Xc + int64_t(c) * m;
-      for (int i = m - 1; i >= 0; --i) {
-        float s = 0.f;
-        for (int j = i + 1 + lane; j < m; j += 32) s = fmaf(L[j * m + i], y[j], s);
-        s = warp_sum(s);
-        if (lane == 0) y[i] = (Vt[sel * ldc + i] - s) / L[i * m + i];
-        __syncwarp();
-      }
-      for (int i = lane; i < m_orig; i += 32) {
-        const int ci = pos[i];
-        a.U[int64_t(c) * m_orig + i] = ci >= 0 ? scale[i] * y[ci] : 0.f;
-      }
+  const int ldb = k_new | 1;
+  float* Y = C;
+  for (int i = warp; i < m; i += nw)
+    for (int c = lane; c < k_new; c += 32) Y[i * ldb + c] = vrow(c)[i];
+  __syncthreads();
+  trsm_lower_t_panels(Ff, m, Y, ldb, m, k_new, Ld);
+  for (int c = warp; c < k_new; c += nw)
+    for (int i = lane; i < m_orig; i += 32) {
+      const int ci = pos[i];
+      a.U[int64_t(c) * m_orig + i] = ci >= 0 ? scale[i] * Y[ci * ldb + c] : 0.f;
     }
-  }
   __syncthreads();
   if (t == 0) {
     *a.status = DCG_OK;
