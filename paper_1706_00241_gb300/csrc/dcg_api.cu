@@ -189,7 +189,7 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0 &&
         g.n > iter_max_n(sms))
       return fail(nullptr, DCG_ERR_UNSUPPORTED,
-                  "n above " + std::to_string(iter_max_n(sms)) + " (one co-resident CTA per SM, 16 rows per thread)");
+                  "n above " + std::to_string(iter_max_n(sms)) + " (one co-resident CTA per SM, at most 32 passes of 128 rows each)");
   }
   if (g.k < 0 || g.ell < 0 || g.k > g.n || g.ell > g.n) return fail(nullptr, DCG_ERR_INVALID_ARG, "k, ell out of range");
   if (g.max_iter < 1) return fail(nullptr, DCG_ERR_INVALID_ARG, "max_iter must be >= 1");

@@ -61,8 +61,7 @@ struct DevState {
   double rho_best;   // smallest true |r|^2 seen by a check (0: none yet)
   double rho_prev_chk;  // true |r|^2 of the previous check
   unsigned int ticket[T_COUNT];
-  unsigned int bar_count;  // grid barrier of the fused iteration kernel: arrivals
-  unsigned int bar_gen;    // and generation
+  unsigned long long bar_count;  // grid barrier of the fused iteration kernel: arrivals in this solve
 };
 
 // --------------------------------------------------------------------------

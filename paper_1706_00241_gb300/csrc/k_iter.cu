@@ -268,33 +268,33 @@ cudaError_t launch_check_update(const Ws& w, int grid, int pre_loop, int setup, 
 // with E^{-1}, N = G_W E^{-1} and M = E^{-1} N formed once per solve.
 // ---------------------------------------------------------------------------
 
-// Grid barrier for a cooperative launch (all CTAs co-resident): sense by
-// generation. Thread 0 of each CTA arrives; the last one resets the count and
-// advances the generation; the others poll it with a bounded wait. Returns
-// false if the wait gave up (the kernel then records a timeout).
+// Grid barrier for a cooperative launch (all CTAs co-resident): one 64-bit
+// arrival counter that only grows within a solve (the solver state is zeroed
+// at the start of every solve). After the block barrier, thread 0 of each CTA
+// adds 1 with release semantics; its barrier completes when the counter
+// reaches the next multiple of gridDim.x above its ticket, which it polls with
+// acquire loads (bounded wait). Returns false if the wait gave up (the kernel
+// then records a timeout).
 __device__ bool grid_barrier(DevState* st) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* gen = &st->bar_gen;
-    const unsigned int my_gen = *gen;
-    __threadfence();
+    unsigned long long* cnt = &st->bar_count;
+    unsigned long long ticket;
+    asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(ticket) : "l"(cnt) : "memory");
+    const unsigned long long target = (ticket / gridDim.x + 1) * gridDim.x;
     int ok = 1;
-    if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
-      st->bar_count = 0;
-      __threadfence();
-      atomicAdd(&st->bar_gen, 1u);
-    } else {
-      long long i = 0;
-      while (*gen == my_gen) {
-        __nanosleep(32);
-        if (++i >= kSpinLimit) {
-          ok = 0;
-          break;
-        }
+    long long i = 0;
+    for (;;) {
+      unsigned long long v;
+      asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(cnt) : "memory");
+      if (v >= target) break;
+      __nanosleep(32);
+      if (++i >= kSpinLimit) {
+        ok = 0;
+        break;
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
@@ -318,24 +318,29 @@ __device__ __forceinline__ void warp_transpose_sum(float (&v)[32], int lane) {
 
 constexpr int IT_THREADS = 256;
 constexpr int IT_WARPS = IT_THREADS / 32;
-constexpr int IT_MAX_ROWS = 16;  // rows per thread (n <= 16 * 256 * grid)
+constexpr int IT_ROWS = IT_THREADS / 2;  // rows per CTA pass: the two halves of a CTA split the columns
+constexpr int IT_MAX_PASSES = 32;         // row passes per CTA (n <= 32 * 128 * grid)
+constexpr int IT_RED_U = 13;              // partial sums each warp reduces per round
 
 // One iteration after q = A p (Algorithm 1 lines 6-12, 13-14), as one
-// cooperative launch with one CTA per SM:
-//   A. rows (thread t of CTA b: b * 256 + t + j * 256 * grid):
-//      alpha = rho / d, x += alpha p, r -= alpha q, store (p, q) in the
-//      window; per-CTA partials of rho' = r^T r, h = (AW)^T r, g = W^T r
-//      [, hp = (AW)^T p] (warp transpose sums, one block barrier);
+// cooperative launch with one CTA per SM. A CTA owns rows
+// b * 128 + i + j * 128 * grid (i < 128); threads t and t + 128 share row i and
+// split every 32-column block of W and AW into halves of 16 columns:
+//   A. x += alpha p, r -= alpha q, store (p, q) in the window, rho' = r^T r
+//      (first half); then per-CTA partials of h = (AW)^T r, g = W^T r
+//      [, hp = (AW)^T p] (each half its 16 columns, warp transpose sums);
 //   grid barrier;
-//   B. every CTA reduces all partials in the same fixed order and forms, one
-//      thread per output, gamma = E^{-1} g, a = E^{-1} h - M g,
-//      b = E^{-1} hp and u = N g (E^{-1} and M symmetric, N read through its
-//      transpose, so every read is coalesced); then the re-deflated rho', the
-//      mode (convergence check, periodic replacement, or neither) and beta.
-//      CTA 0 alone writes the solver state and the IF-node value of the check
-//      branch;
+//   B. every CTA reduces all partials in the same fixed order and forms
+//      gamma = E^{-1} g, a = E^{-1} h - M g, b = E^{-1} hp and u = N g (E^{-1}
+//      and M symmetric, N read through its transpose, so every read is
+//      coalesced; two threads per output, half of the sum each); then the
+//      re-deflated rho', the mode (convergence check, periodic replacement, or
+//      neither) and beta. CTA 0 alone writes the solver state and the IF-node
+//      value of the check branch;
 //   C. if no check follows, every CTA applies line 12 to its rows:
-//      x += W gamma, r -= AW gamma, p = beta p + r - W mu, mu = a + beta b.
+//      x += W gamma, r -= AW gamma, p = beta p + r - W mu, mu = a + beta b
+//      (each half sums its columns; the second half hands its sums to the
+//      first through shared memory).
 // Every CTA reads the state it needs before the barrier, so CTA 0's writes
 // after it cannot race with them. Float32 re-deflation (gamma): see the
 // note above.
@@ -374,6 +379,22 @@ constexpr int IT_STAGE_KMAX = 64;  // E^{-1}, M, N^T staged in shared memory up 
 
 __host__ __device__ constexpr uint32_t it_mat_bytes(int k) { return uint32_t((3 * k * k * 8 + 15) & ~15); }
 
+// Column sums of 16 per-lane values across a warp: afterwards lanes l and
+// l + 16 hold in v[0] the warp's sum of column l (l < 16).
+__device__ __forceinline__ void warp_transpose_sum16(float (&v)[16], int lane) {
+#pragma unroll
+  for (int s = 8; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const float send = up ? v[i] : v[i + s];
+      const float keep = up ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
 __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int stage) {
   DevState* st = w.st;
   if (st->done) {
@@ -382,11 +403,14 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
   }
   const int n = w.n, k = st->k;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int half = t / IT_ROWS, rt = t % IT_ROWS;  // column half, row slot
   const double d = st->d;
   const bool ok = (d > 0.0) && isfinite(d);
   const double rho_old = st->rho;
   const double alpha_d = ok ? rho_old / d : 0.0;
   const float alpha = float(alpha_d);
+  // 1 / rho_old for beta, formed early by the one thread that needs it
+  const double inv_rho_old = t == 0 ? 1.0 / rho_old : 0.0;
   const int iter = st->iter + 1;
   const int ell = st->ell, window = st->window, head = st->head, nstored = st->nstored;
   const double thresh2 = st->thresh2, bnorm2 = st->bnorm2;
@@ -423,65 +447,73 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
     tc::bulk_load(smat, w.mats2, mbytes, &mat_bar);
   }
   const int G = gridDim.x;
-  const int stride = G * IT_THREADS;
-  const int row0 = blockIdx.x * IT_THREADS + t;
+  const int stride = G * IT_ROWS;
+  const int row0 = blockIdx.x * IT_ROWS + rt;
 
   // ---- A. x, r update, window store, rho' ----
   float acc = 0.f;
-  for (int gi = row0; gi < n; gi += stride) {
-    const float pi = w.p[gi], qi = w.q[gi];
-    w.xd[gi] += alpha_d * double(pi);
-    const float ri = fmaf(-alpha, qi, w.r[gi]);
-    w.r[gi] = ri;
-    if (slot >= 0) {
-      w.P[int64_t(slot) * n + gi] = pi;
-      w.Q[int64_t(slot) * n + gi] = qi;
+  if (half == 0) {
+    for (int gi = row0; gi < n; gi += stride) {
+      const float pi = w.p[gi], qi = w.q[gi];
+      w.xd[gi] += alpha_d * double(pi);
+      const float ri = fmaf(-alpha, qi, w.r[gi]);
+      w.r[gi] = ri;
+      if (slot >= 0) {
+        w.P[int64_t(slot) * n + gi] = pi;
+        w.Q[int64_t(slot) * n + gi] = qi;
+      }
+      acc = fmaf(ri, ri, acc);
     }
-    acc = fmaf(ri, ri, acc);
   }
-  // per-warp column sums of the dots, 32 columns at a time
-  __shared__ float wsum[IT_WARPS][1 + 3 * kMaxK];
-  {
+  // per-warp column sums of the dots; warp 4 h + j (half h) writes slot j
+  __shared__ float wsum[IT_WARPS / 2][1 + 3 * kMaxK];
+  const int wj = warp % (IT_WARPS / 2);
+  if (half == 0) {
     const float rs = warp_sum(acc);
-    if (lane == 0) wsum[warp][0] = rs;
+    if (lane == 0) wsum[wj][0] = rs;
   }
-  const int nd = reproj ? 3 : 2;  // h, g [, hp]
+  __syncthreads();  // r' of this CTA's rows, written by the first half, read by both
   for (int c0 = 0; c0 < k; c0 += 32) {
-    const int cw = min(32, k - c0);
-    float vh[32], vg[32], vp[32];
+    const int cb = c0 + 16 * half;
+    const int cw = min(16, k - cb);  // warp-uniform
+    if (cw <= 0) continue;
+    float vh[16], vg[16], vp[16];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) vh[c] = vg[c] = vp[c] = 0.f;
+    for (int c = 0; c < 16; ++c) vh[c] = vg[c] = vp[c] = 0.f;
     for (int gi = row0; gi < n; gi += stride) {
       const float ri = w.r[gi], pi = w.p[gi];
-      const float* aw = w.Y + int64_t(1 + c0) * n + gi;
-      const float* ww = w.XW + int64_t(1 + c0) * n + gi;
+      const float* aw = w.Y + int64_t(1 + cb) * n + gi;
+      const float* ww = w.XW + int64_t(1 + cb) * n + gi;
+      float av_[16], wv_[16];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        if (c < cw) {
-          const float a = __ldg(aw + int64_t(c) * n);
-          const float wv = __ldg(ww + int64_t(c) * n);
-          vh[c] = fmaf(a, ri, vh[c]);
-          vp[c] = fmaf(a, pi, vp[c]);
-          vg[c] = fmaf(wv, ri, vg[c]);
-        }
+      for (int c = 0; c < 16; ++c) {
+        av_[c] = c < cw ? __ldg(aw + int64_t(c) * n) : 0.f;
+        wv_[c] = c < cw ? __ldg(ww + int64_t(c) * n) : 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        vh[c] = fmaf(av_[c], ri, vh[c]);
+        vp[c] = fmaf(av_[c], pi, vp[c]);
+        vg[c] = fmaf(wv_[c], ri, vg[c]);
       }
     }
-    warp_transpose_sum(vh, lane);
-    warp_transpose_sum(vg, lane);
-    if (reproj) warp_transpose_sum(vp, lane);
+    warp_transpose_sum16(vh, lane);
+    warp_transpose_sum16(vg, lane);
+    if (reproj) warp_transpose_sum16(vp, lane);
     if (lane < cw) {
-      wsum[warp][1 + c0 + lane] = vh[0];
-      wsum[warp][1 + k + c0 + lane] = vg[0];
-      if (reproj) wsum[warp][1 + 2 * k + c0 + lane] = vp[0];
+      wsum[wj][1 + cb + lane] = vh[0];
+      wsum[wj][1 + k + cb + lane] = vg[0];
+      if (reproj) wsum[wj][1 + 2 * k + cb + lane] = vp[0];
     }
   }
   __syncthreads();
+  const int nd = reproj ? 3 : 2;  // h, g [, hp]
   const int count = 1 + nd * k;
   float* partf = reinterpret_cast<float*>(w.partials);  // float slots [v * G + b]
   for (int v = t; v < count; v += IT_THREADS) {
     float sum = 0.f;
 #pragma unroll
-    for (int q = 0; q < IT_WARPS; ++q) sum += wsum[q][v];
+    for (int q = 0; q < IT_WARPS / 2; ++q) sum += wsum[q][v];
     partf[int64_t(v) * G + blockIdx.x] = sum;
   }
   if (!grid_barrier(st)) {
@@ -496,24 +528,29 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
   }
 
   // ---- B. the same reduction and k x k products in every CTA ----
+  // warp w reduces values w * 13 .. w * 13 + 12 of each round of 104, all
+  // their loads in flight at once
   __shared__ df sred[1 + 3 * kMaxK];
   __shared__ double gam[kMaxK], av[kMaxK], bv[kMaxK], uv[kMaxK];
   __shared__ int s_mode, s_done;
   __shared__ double s_beta;
-  for (int v0 = warp * 4; v0 < count; v0 += IT_WARPS * 4) {
-    df sv[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  for (int v0 = warp * IT_RED_U; v0 < count; v0 += IT_WARPS * IT_RED_U) {
+    float ld[IT_RED_U][IT_MAX_GRID / 32];
 #pragma unroll
-    for (int i = 0; i < IT_MAX_GRID / 32; ++i) {  // all loads of the round in flight
-      const int b = lane + 32 * i;
+    for (int u = 0; u < IT_RED_U; ++u)
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (b < G && v0 + u < count) sv[u] = df_add(sv[u], df{__ldcg(partf + int64_t(v0 + u) * G + b), 0.f});
-    }
+      for (int i = 0; i < IT_MAX_GRID / 32; ++i) {
+        const int b = lane + 32 * i;
+        ld[u][i] = (b < G && v0 + u < count) ? __ldcg(partf + int64_t(v0 + u) * G + b) : 0.f;
+      }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < IT_RED_U; ++u) {
+      df sv = {0.f, 0.f};
 #pragma unroll
-      for (int m = 16; m >= 1; m >>= 1) sv[u] = df_add(sv[u], df_shfl_xor(sv[u], m));
-      if (lane == 0 && v0 + u < count) sred[v0 + u] = sv[u];
+      for (int i = 0; i < IT_MAX_GRID / 32; ++i) sv = df_add(sv, df{ld[u][i], 0.f});
+#pragma unroll
+      for (int m = 16; m >= 1; m >>= 1) sv = df_add(sv, df_shfl_xor(sv, m));
+      if (lane == 0 && v0 + u < count) sred[v0 + u] = sv;
     }
   }
   __syncthreads();
@@ -535,25 +572,34 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
   }
   const float2* Mm = Ei + k * k;
   const float2* Nt = Ei + 2 * k * k;
-  for (int o = t; o < 4 * k; o += IT_THREADS) {
-    const int which = o / k, c = o - which * k;
+  // output o = which * k + c; lanes 2 e and 2 e + 1 take j even and j odd
+  // (warp-uniform trip count: every lane reaches the pair shuffles)
+  for (int ob = t - lane; ob < 8 * k; ob += IT_THREADS) {
+    const int o2 = ob + lane;
+    const bool act = o2 < 8 * k;
+    const int o = o2 >> 1, par = o2 & 1;
+    const int which = act ? o / k : 4, c = act ? o - which * k : 0;
     df s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
     if (which == 0) {
-      for (int j = 0; j < k; ++j) s0 = df_fma(s0, Ei[j * k + c], g[j]);
-      gam[c] = df_to_double(s0);
+      for (int j = par; j < k; j += 2) s0 = df_fma(s0, Ei[j * k + c], g[j]);
     } else if (which == 1) {
-      for (int j = 0; j < k; ++j) {
+      for (int j = par; j < k; j += 2) {
         s0 = df_fma(s0, Ei[j * k + c], h[j]);
         s1 = df_fma(s1, Mm[j * k + c], g[j]);
       }
-      av[c] = df_to_double(s0) - df_to_double(s1);
     } else if (which == 2) {
       if (reproj)
-        for (int j = 0; j < k; ++j) s0 = df_fma(s0, Ei[j * k + c], hp[j]);
-      bv[c] = df_to_double(s0);
-    } else {
-      for (int j = 0; j < k; ++j) s0 = df_fma(s0, Nt[j * k + c], g[j]);
-      uv[c] = df_to_double(s0);
+        for (int j = par; j < k; j += 2) s0 = df_fma(s0, Ei[j * k + c], hp[j]);
+    } else if (which == 3) {
+      for (int j = par; j < k; j += 2) s0 = df_fma(s0, Nt[j * k + c], g[j]);
+    }
+    s0 = df_add(s0, df_shfl_xor(s0, 1));
+    s1 = df_add(s1, df_shfl_xor(s1, 1));
+    if (act && par == 0) {
+      if (which == 0) gam[c] = df_to_double(s0);
+      else if (which == 1) av[c] = df_to_double(s0) - df_to_double(s1);
+      else if (which == 2) bv[c] = df_to_double(s0);
+      else uv[c] = df_to_double(s0);
     }
   }
   __syncthreads();
@@ -573,7 +619,7 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
       const int done = (mode == 0 && iter >= max_iter) ? 1 : 0;
       s_mode = mode;
       s_done = done;
-      s_beta = rho_new / rho_old;
+      s_beta = rho_new * inv_rho_old;
       if (blockIdx.x == 0) {
         st->iter = iter;
         st->alpha = alpha_d;
@@ -607,6 +653,7 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
 
   // ---- C. line 12 on this CTA's rows ----
   __shared__ float msh[kMaxK], gsh[kMaxK];
+  __shared__ float xch[3][IT_ROWS];  // second half's sums: W gamma, AW gamma, W mu
   const double beta_d = s_beta;
   for (int c = t; c < k; c += IT_THREADS) {
     msh[c] = float(av[c] + beta_d * bv[c]);
@@ -614,36 +661,55 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
   }
   __syncthreads();
   const float beta = float(beta_d);
-  for (int gi = row0; gi < n; gi += stride) {
-    float ri = w.r[gi], dx = 0.f, wm = 0.f;
-    const float pi = w.p[gi];
-    for (int c0 = 0; c0 < k; c0 += 16) {
-      float wc[16], ac[16];
+  const int npass = (n - blockIdx.x * IT_ROWS + stride - 1) / stride;  // CTA-uniform
+  for (int pass = 0; pass < npass; ++pass) {
+    const int gi = row0 + pass * stride;
+    const bool live = gi < n;
+    float dx = 0.f, wm = 0.f, ra = 0.f;
+    if (live) {
+      for (int c0 = 16 * half; c0 < k; c0 += 32) {
+        const int cw = min(16, k - c0);
+        float wc[16], ac[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        wc[c] = c0 + c < k ? __ldg(w.XW + int64_t(c0 + c + 1) * n + gi) : 0.f;
-        ac[c] = c0 + c < k ? __ldg(w.Y + int64_t(c0 + c + 1) * n + gi) : 0.f;
-      }
+        for (int c = 0; c < 16; ++c) {
+          wc[c] = c < cw ? __ldg(w.XW + int64_t(c0 + c + 1) * n + gi) : 0.f;
+          ac[c] = c < cw ? __ldg(w.Y + int64_t(c0 + c + 1) * n + gi) : 0.f;
+        }
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        if (c0 + c < k) {
-          dx = fmaf(wc[c], gsh[c0 + c], dx);
-          wm = fmaf(wc[c], msh[c0 + c], wm);
-          ri = fmaf(-ac[c], gsh[c0 + c], ri);
+        for (int c = 0; c < 16; ++c) {
+          if (c < cw) {
+            dx = fmaf(wc[c], gsh[c0 + c], dx);
+            wm = fmaf(wc[c], msh[c0 + c], wm);
+            ra = fmaf(ac[c], gsh[c0 + c], ra);
+          }
         }
       }
     }
-    if (k) {
-      w.xd[gi] += double(dx);
-      w.r[gi] = ri;
+    if (half == 1) {
+      xch[0][rt] = dx;
+      xch[1][rt] = ra;
+      xch[2][rt] = wm;
     }
-    w.p[gi] = (beta != 0.f ? fmaf(beta, pi, ri) : ri) - wm;
+    __syncthreads();
+    if (half == 0 && live) {
+      dx += xch[0][rt];
+      ra += xch[1][rt];
+      wm += xch[2][rt];
+      const float ri = w.r[gi] - ra;
+      if (k) {
+        w.xd[gi] += double(dx);
+        w.r[gi] = ri;
+      }
+      const float pi = w.p[gi];
+      w.p[gi] = (beta != 0.f ? fmaf(beta, pi, ri) : ri) - wm;
+    }
+    __syncthreads();
   }
 }
 
 // Largest n the fused iteration kernel covers with one co-resident CTA per SM.
 int64_t iter_max_n(int num_sms) {
-  return int64_t(num_sms < IT_MAX_GRID ? num_sms : IT_MAX_GRID) * IT_THREADS * IT_MAX_ROWS;
+  return int64_t(num_sms < IT_MAX_GRID ? num_sms : IT_MAX_GRID) * IT_ROWS * IT_MAX_PASSES;
 }
 
 
@@ -659,11 +725,11 @@ cudaError_t iter_configure() {
 }
 
 cudaError_t launch_iter_fused(const Ws& w, int num_sms, Handles h, cudaStream_t s) {
-  int grid = (w.n + IT_THREADS - 1) / IT_THREADS;
+  int grid = (w.n + IT_ROWS - 1) / IT_ROWS;
   if (grid > num_sms) grid = num_sms;
   if (grid > IT_MAX_GRID) grid = IT_MAX_GRID;
   if (grid < 1) grid = 1;
-  if (int64_t(grid) * IT_THREADS * IT_MAX_ROWS < w.n) return cudaErrorInvalidValue;
+  if (int64_t(grid) * IT_ROWS * IT_MAX_PASSES < w.n) return cudaErrorInvalidValue;
   const size_t dyn = iter_dyn_smem(w.kmax);
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(grid);

@@ -8,6 +8,8 @@
 //     tridiagonalisation, bisection, inverse iteration),
 //     selection of k values (reading R4), U = S L^{-T} V, W = Z U with unit
 //     columns whose largest-magnitude entry is positive (reading R5).
+#include <algorithm>
+
 #include "dcg_kernels.cuh"
 
 namespace dcg {
@@ -86,23 +88,29 @@ __global__ void __launch_bounds__(256) k_gram(GramArgs g) {
   }
 }
 
-// out[i*mb + j] = sum over splits (fixed order); E mode reads the size from st.
+// out[i*mb + j] = sum over splits (fixed order: lane l adds splits l, l + 32,
+// ..., then a shuffle tree); one warp per output; E mode reads the size from st.
 __global__ void k_gram_reduce(const double* part, int splits, int ma, int mb, double* out, const DevState* st) {
   if (st) {
     if (st->done) return;
     ma = mb = st->k;
   }
   const int total = ma * mb;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int wstride = (gridDim.x * blockDim.x) >> 5;
+  for (int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < total; idx += wstride) {
     double s = 0.0;
-    for (int sp = 0; sp < splits; ++sp) s += part[int64_t(sp) * total + idx];
-    out[idx] = s;
+    for (int sp = lane; sp < splits; sp += 32) s += part[int64_t(sp) * total + idx];
+    s = warp_sum(s);
+    if (lane == 0) out[idx] = s;
   }
 }
 
+// Row splits of a Gram product: about eight CTAs per SM in total (each split
+// then covers a few 32-row blocks), at most 256 splits.
 static int gram_splits(int n, int tiles, int num_sms) {
-  int splits = (2 * num_sms + tiles - 1) / max(tiles, 1);
-  if (splits > 64) splits = 64;
+  int splits = (8 * num_sms + tiles - 1) / max(tiles, 1);
+  if (splits > 256) splits = 256;
   const int max_splits = (n + GR_T - 1) / GR_T;
   if (splits > max_splits) splits = max_splits;
   return splits < 1 ? 1 : splits;
@@ -125,7 +133,8 @@ static cudaError_t launch_gram(const GramArgs& g0, int ma_max, int mb_max, int n
   k_gram<<<dim3(tiles, used), 256, 0, s>>>(g);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_gram_reduce<<<64, 256, 0, s>>>(g.part, used, ma_max, mb_max, out, st);
+  const int red_blocks = std::min(1024, (ma_max * mb_max + 7) / 8);  // 8 warps per block, warp per output
+  k_gram_reduce<<<std::max(red_blocks, 1), 256, 0, s>>>(g.part, used, ma_max, mb_max, out, st);
   return cudaGetLastError();
 }
 
@@ -155,7 +164,21 @@ cudaError_t launch_gram_GW(const Ws& w, double* part, int num_sms, cudaStream_t 
 
 // --------------------------------------------------------------------------
 // Cholesky E = L L^T (symmetrised) and Linv = L^{-1}; float64, one CTA.
+// Right-looking: step j subtracts E(i, j) E(l, j) / d_j from the trailing lower
+// triangle (j < l <= i) and leaves column j unscaled, so a step needs one
+// barrier; column j is scaled by 1 / sqrt(d_j) at the end. 1 / sqrt(d_j) is a
+// float estimate refined by two Newton steps y <- y (3 - d y^2) / 2 (relative
+// error ~2^-22 -> ~2^-43 -> float64 rounding). Linv row by row, eight lanes per
+// entry sharing its dot product.
 // --------------------------------------------------------------------------
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  const float fd = float(d);
+  double y = (fd > 1e-30f && fd < 1e30f) ? double(rsqrtf(fd)) : 1.0 / sqrt(d);
+  y = y * fma(-0.5 * d * y, y, 1.5);
+  y = y * fma(-0.5 * d * y, y, 1.5);
+  return y;
+}
+
 __global__ void __launch_bounds__(256) k_chol_E(Ws w) {
   DevState* st = w.st;
   if (st->done) return;
@@ -164,51 +187,61 @@ __global__ void __launch_bounds__(256) k_chol_E(Ws w) {
   extern __shared__ double shd[];
   double* L = shd;          // k x k
   double* X = shd + k * k;  // k x k, inverse
+  __shared__ double rsd[kMaxK];  // 1 / L(j, j)
   __shared__ int s_fail;
-  if (threadIdx.x == 0) s_fail = 0;
-  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+  const int t = threadIdx.x;
+  if (t == 0) s_fail = 0;
+  for (int idx = t; idx < k * k; idx += blockDim.x) {
     const int i = idx / k, j = idx % k;
     L[idx] = 0.5 * (w.E[i * k + j] + w.E[j * k + i]);
+    X[idx] = 0.0;
   }
   __syncthreads();
   for (int j = 0; j < k; ++j) {
-    if (threadIdx.x == 0) {
-      double s = L[j * k + j];
-      for (int p = 0; p < j; ++p) s -= L[j * k + p] * L[j * k + p];
-      if (!(s > 0.0) || !isfinite(s)) {
-        s_fail = 1;
-        s = 1.0;
-      }
-      L[j * k + j] = sqrt(s);
+    const double dj = L[j * k + j];
+    const bool bad = !(dj > 0.0) || !isfinite(dj);
+    const double y = rsqrt_newton(bad ? 1.0 : dj);
+    if (t == 0) {
+      rsd[j] = y;
+      if (bad) s_fail = 1;
     }
-    __syncthreads();
-    const double ljj = L[j * k + j];
-    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) {
-      double s = L[i * k + j];
-      for (int p = 0; p < j; ++p) s -= L[i * k + p] * L[j * k + p];
-      L[i * k + j] = s / ljj;
+    const double inv_d = y * y;
+    const int m = k - j - 1;
+    for (int idx = t; idx < m * m; idx += blockDim.x) {
+      const int i = j + 1 + idx / m, l = j + 1 + idx % m;
+      if (l <= i) L[i * k + l] = fma(-L[i * k + j] * inv_d, L[l * k + j], L[i * k + l]);
     }
     __syncthreads();
   }
   if (s_fail) {
-    if (threadIdx.x == 0) {
+    if (t == 0) {
       st->status = DCG_ERR_SUBSPACE_SINGULAR;
       st->done = 1;
     }
     return;
   }
-  // column-parallel forward substitution L X = I
-  for (int c = threadIdx.x; c < k; c += blockDim.x) {
-    for (int i = 0; i < c; ++i) X[i * k + c] = 0.0;
-    X[c * k + c] = 1.0 / L[c * k + c];
-    for (int i = c + 1; i < k; ++i) {
-      double s = 0.0;
-      for (int j = c; j < i; ++j) s += L[i * k + j] * X[j * k + c];
-      X[i * k + c] = -s / L[i * k + i];
-    }
+  for (int idx = t; idx < k * k; idx += blockDim.x) {
+    const int i = idx / k, j = idx % k;
+    if (j < i) L[idx] *= rsd[j];
+    else if (j == i) L[idx] *= rsd[j];  // d_j / sqrt(d_j)
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) w.Linv[idx] = X[idx];
+  // X(i, c) = -(1 / L(i, i)) sum_{c <= j < i} L(i, j) X(j, c), X(i, i) = 1 / L(i, i)
+  const int grp = t >> 3, sub = t & 7;
+  for (int i = 0; i < k; ++i) {
+    for (int cb = 0; cb <= i; cb += 32) {  // trip count uniform across the CTA
+      const int c = cb + grp;
+      double sacc = 0.0;
+      if (c < i)
+        for (int j = c + sub; j < i; j += 8) sacc = fma(L[i * k + j], X[j * k + c], sacc);
+      sacc += __shfl_xor_sync(0xffffffffu, sacc, 4);
+      sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
+      sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+      if (sub == 0 && c <= i) X[i * k + c] = (c == i) ? rsd[i] : -sacc * rsd[i];
+    }
+    __syncthreads();
+  }
+  for (int idx = t; idx < k * k; idx += blockDim.x) w.Linv[idx] = X[idx];
 }
 
 cudaError_t launch_chol_E(const Ws& w, cudaStream_t s) {
