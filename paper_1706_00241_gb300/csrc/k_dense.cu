@@ -405,24 +405,37 @@ bool make_rowop_tmap(CUtensorMap* map, const float* A, int64_t n, int64_t lda, E
 
 // ---------------------------------------------------------------------------
 // Y = A V, V and Y column-major n x c (leading dimension n), c <= 129.
-// One row of Y per thread, all AB_CB = 32 columns of a column block in
-// registers; per K-step of 32 the CTA stages A[256 rows x 32] transposed in
-// shared memory (so a thread reads its row with conflict-free scalar loads)
-// and V[32 x 32] (each row read as a float4 broadcast). The K range is split
-// over blockIdx.y so that ~3 CTAs run per SM; the split partials are summed
-// in a fixed order by k_block_reduce (no atomics, deterministic).
+// A CTA computes 256 rows x 32 columns of Y over a K range (blockIdx.y; the
+// split partials are summed in a fixed order by k_block_reduce: no atomics,
+// deterministic). Per K-step of 32, the A tile (256 rows x 32, row-major, row
+// stride 36 floats) and the V tile (32 columns x 32, stride 36) arrive in
+// shared memory by asynchronous copies (cp.async, 16 bytes for A, 4 bytes for
+// V, whose columns need not be 16-byte aligned), two stages in flight.
+// Thread t computes rows rg, rg + 64, rg + 128, rg + 192 (rg = t % 64; at a row
+// stride of 36 floats, 8 consecutive lanes read 8 different 16-byte bank
+// groups) and columns 8 cg .. 8 cg + 7 (cg = t / 64, a broadcast within the
+// warp): per 4 K-values, 4 float4 loads of A and 8 of V feed 128 FMAs.
 // In a solve (st set) the columns are the k active columns of W.
 // ---------------------------------------------------------------------------
 constexpr int AB_ROWS = 256;
 constexpr int AB_K = 32;
 constexpr int AB_CB = 32;
-constexpr int AB_LDS = AB_ROWS + 4;   // row stride of the transposed A tile (16-byte aligned)
-constexpr size_t AB_SMEM = size_t(2) * (AB_K * AB_LDS + AB_K * (AB_CB + 4)) * sizeof(float);
+constexpr int AB_LD = AB_K + 4;  // row stride of both tiles (floats)
+constexpr int AB_STAGE_FLOATS = AB_ROWS * AB_LD + AB_CB * AB_LD;
+constexpr size_t AB_SMEM = size_t(2) * AB_STAGE_FLOATS * sizeof(float);
 
-// Thread t computes rows 4 (t % 64) .. + 3 and columns 8 (t / 64) .. + 7 of
-// the CTA's 256 x 32 output tile (one float4 of A and two broadcast float4 of
-// V per K, 32 FMAs). The next K-step's tiles are loaded into registers while
-// the current one is computed, then stored into the other shared-memory half.
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, int src_bytes) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, int src_bytes) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __global__ void __launch_bounds__(AB_ROWS, 2) k_apply_block(ApplyBlockArgs a, int kchunk, float* part) {
   extern __shared__ __align__(16) float ab_smem[];
   int c = a.c;
@@ -442,59 +455,31 @@ __global__ void __launch_bounds__(AB_ROWS, 2) k_apply_block(ApplyBlockArgs a, in
   const int k_lo = blockIdx.y * kchunk, k_hi = min(n, k_lo + kchunk);
   const int t = threadIdx.x;
   const int rg = t & 63, cg = t >> 6;
-  const bool vec_ok = (a.lda % 4) == 0 && (reinterpret_cast<uintptr_t>(a.A) & 15) == 0;
-  // buffer b: A tile at ab_smem + b * AB_K * AB_LDS, V tile after both A tiles
-  auto a_buf = [&](int b) { return ab_smem + b * (AB_K * AB_LDS); };
-  auto v_buf = [&](int b) { return ab_smem + 2 * (AB_K * AB_LDS) + b * (AB_K * (AB_CB + 4)); };
-
-  float4 pa[(AB_ROWS * AB_K / 4) / AB_ROWS];
-  float pv[(AB_K * AB_CB) / AB_ROWS];
-  auto load_tile = [&](int k0) {
+  const int64_t lda = a.lda;
+  // copies of one K-step into stage b: A chunk idx = q * 256 + t is row idx / 8,
+  // 16-byte column chunk idx % 8; V element idx = q * 256 + t is column idx / 32,
+  // K offset idx % 32. Out-of-range parts are zero-filled (source size 0 .. 16).
+  auto issue = [&](int b, int k0) {
+    float* as = ab_smem + b * AB_STAGE_FLOATS;
+    float* vs = as + AB_ROWS * AB_LD;
 #pragma unroll
     for (int q = 0; q < (AB_ROWS * AB_K / 4) / AB_ROWS; ++q) {
       const int idx = q * AB_ROWS + t;
-      const int r = idx / (AB_K / 4), c4 = idx % (AB_K / 4);
+      const int r = idx >> 3, c4 = idx & 7;
       const int gr = row0 + r, gk = k0 + 4 * c4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gr < n) {
-        const float* src = a.A + int64_t(gr) * a.lda + gk;
-        if (vec_ok && gk + 3 < k_hi) {
-          v = __ldg(reinterpret_cast<const float4*>(src));
-        } else {
-          v.x = gk < k_hi ? __ldg(src) : 0.f;
-          v.y = gk + 1 < k_hi ? __ldg(src + 1) : 0.f;
-          v.z = gk + 2 < k_hi ? __ldg(src + 2) : 0.f;
-          v.w = gk + 3 < k_hi ? __ldg(src + 3) : 0.f;
-        }
-      }
-      pa[q] = v;
+      const int nb = (gr < n) ? 4 * max(0, min(4, k_hi - gk)) : 0;
+      const float* src = nb > 0 ? a.A + int64_t(gr) * lda + gk : a.A;
+      cp_async16(as + r * AB_LD + 4 * c4, src, nb);
     }
 #pragma unroll
-    for (int q = 0; q < (AB_K * AB_CB) / AB_ROWS; ++q) {
+    for (int q = 0; q < (AB_CB * AB_K) / AB_ROWS; ++q) {
       const int idx = q * AB_ROWS + t;
-      const int j = idx / AB_K, kk = idx % AB_K;
+      const int j = idx >> 5, kk = idx & 31;
       const int gk = k0 + kk;
-      pv[q] = (j < cw && gk < k_hi) ? __ldg(V + int64_t(col0 + j) * n + gk) : 0.f;
+      const bool ok = j < cw && gk < k_hi;
+      cp_async4(vs + j * AB_LD + kk, ok ? V + int64_t(col0 + j) * n + gk : V, ok ? 4 : 0);
     }
-  };
-  auto store_tile = [&](int b) {
-    float* as = a_buf(b);
-#pragma unroll
-    for (int q = 0; q < (AB_ROWS * AB_K / 4) / AB_ROWS; ++q) {
-      const int idx = q * AB_ROWS + t;
-      const int r = idx / (AB_K / 4), c4 = idx % (AB_K / 4);
-      as[(4 * c4 + 0) * AB_LDS + r] = pa[q].x;
-      as[(4 * c4 + 1) * AB_LDS + r] = pa[q].y;
-      as[(4 * c4 + 2) * AB_LDS + r] = pa[q].z;
-      as[(4 * c4 + 3) * AB_LDS + r] = pa[q].w;
-    }
-    float* vs = v_buf(b);
-#pragma unroll
-    for (int q = 0; q < (AB_K * AB_CB) / AB_ROWS; ++q) {
-      const int idx = q * AB_ROWS + t;
-      const int j = idx / AB_K, kk = idx % AB_K;
-      vs[kk * (AB_CB + 4) + j] = pv[q];
-    }
+    cp_async_commit();
   };
 
   float acc[4][8];
@@ -502,32 +487,36 @@ __global__ void __launch_bounds__(AB_ROWS, 2) k_apply_block(ApplyBlockArgs a, in
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-  int cur = 0;
-  if (k_lo < k_hi) {
-    load_tile(k_lo);
-    store_tile(0);
-  }
-  __syncthreads();
-  for (int k0 = k_lo; k0 < k_hi; k0 += AB_K) {
-    const bool more = k0 + AB_K < k_hi;
-    if (more) load_tile(k0 + AB_K);  // in flight during the compute below
-    const float* as = a_buf(cur);
-    const float* vs = v_buf(cur);
-#pragma unroll 8
-    for (int kk = 0; kk < AB_K; ++kk) {
-      const float4 av = *reinterpret_cast<const float4*>(as + kk * AB_LDS + 4 * rg);
-      const float4 v0 = *reinterpret_cast<const float4*>(vs + kk * (AB_CB + 4) + 8 * cg);
-      const float4 v1 = *reinterpret_cast<const float4*>(vs + kk * (AB_CB + 4) + 8 * cg + 4);
-      const float ar[4] = {av.x, av.y, av.z, av.w};
-      const float vr[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+  const int nsteps = k_lo < k_hi ? (k_hi - k_lo + AB_K - 1) / AB_K : 0;
+  if (nsteps > 0) issue(0, k_lo);
+  for (int s = 0; s < nsteps; ++s) {
+    if (s + 1 < nsteps) {
+      issue((s + 1) & 1, k_lo + (s + 1) * AB_K);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // every thread's copies of step s have landed
+    const float* as = ab_smem + (s & 1) * AB_STAGE_FLOATS;
+    const float* vs = as + AB_ROWS * AB_LD;
+#pragma unroll 2
+    for (int kq = 0; kq < AB_K; kq += 4) {
+      float4 a4[4], v4[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a4[i] = *reinterpret_cast<const float4*>(as + (rg + 64 * i) * AB_LD + kq);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v4[j] = *reinterpret_cast<const float4*>(vs + (8 * cg + j) * AB_LD + kq);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(ar[i], vr[j], acc[i][j]);
+        for (int j = 0; j < 8; ++j) {
+          acc[i][j] = fmaf(a4[i].x, v4[j].x, acc[i][j]);
+          acc[i][j] = fmaf(a4[i].y, v4[j].y, acc[i][j]);
+          acc[i][j] = fmaf(a4[i].z, v4[j].z, acc[i][j]);
+          acc[i][j] = fmaf(a4[i].w, v4[j].w, acc[i][j]);
+        }
     }
-    if (more) store_tile(cur ^ 1);
-    __syncthreads();
-    cur ^= 1;
+    __syncthreads();  // stage s & 1 is refilled by the issue of step s + 2
   }
   float* dst = Y;
   if (gridDim.y > 1) dst = part + int64_t(blockIdx.y) * (int64_t(gridDim.z) * AB_CB) * n;
@@ -538,7 +527,7 @@ __global__ void __launch_bounds__(AB_ROWS, 2) k_apply_block(ApplyBlockArgs a, in
     float* colp = dst + int64_t(col0 + cj) * n;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int gr = row0 + 4 * rg + i;
+      const int gr = row0 + rg + 64 * i;
       if (gr < n) colp[gr] = acc[i][j];
     }
   }
@@ -567,14 +556,28 @@ __global__ void __launch_bounds__(256) k_block_reduce(ApplyBlockArgs a, int spli
   }
 }
 
+// K splits: the CTA count (row blocks x column blocks x splits) is chosen to
+// fill whole waves of two CTAs per SM (the smallest split count within 2% of
+// the best wave efficiency), with at least 8 K-steps per split, at most 16.
 int apply_block_splits(int n, int cmax, int num_sms) {
   const int rowblocks = (n + AB_ROWS - 1) / AB_ROWS;
   const int colblocks = (cmax + AB_CB - 1) / AB_CB;
-  int splits = (3 * num_sms) / (rowblocks * colblocks);
-  const int kmax_splits = (n + AB_K * 8 - 1) / (AB_K * 8);  // at least 8 K-steps per split
-  if (splits > kmax_splits) splits = kmax_splits;
-  if (splits > 16) splits = 16;
-  return splits < 1 ? 1 : splits;
+  const int base = rowblocks * colblocks;
+  const int slots = 2 * num_sms;
+  int kmax_splits = (n + AB_K * 8 - 1) / (AB_K * 8);
+  if (kmax_splits > 16) kmax_splits = 16;
+  if (kmax_splits < 1) kmax_splits = 1;
+  double eff[17] = {0.0};
+  double best = 0.0;
+  for (int sp = 1; sp <= kmax_splits; ++sp) {
+    const long long ctas = (long long)base * sp;
+    const long long waves = (ctas + slots - 1) / slots;
+    eff[sp] = double(ctas) / double(waves * slots);
+    best = std::max(best, eff[sp]);
+  }
+  for (int sp = 1; sp <= kmax_splits; ++sp)
+    if (eff[sp] >= best - 0.02) return sp;
+  return 1;
 }
 
 // Largest split-K partial buffer any column count up to cmax can need.

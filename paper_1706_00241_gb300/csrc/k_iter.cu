@@ -369,6 +369,15 @@ __device__ __forceinline__ df df_fma(df acc, float2 x, df y) {
   pe = __fmaf_rn(x.y, y.hi, pe);
   return df_add(acc, df{p, pe});
 }
+// a * b (FMA-exact product of the high parts, cross terms in float32)
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float hh = __fadd_rn(p, e);
+  return {hh, __fsub_rn(e, __fsub_rn(hh, p))};
+}
 __device__ __forceinline__ df df_shfl_xor(df a, int m) {
   return {__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
 }
@@ -531,7 +540,7 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
   // warp w reduces values w * 13 .. w * 13 + 12 of each round of 104, all
   // their loads in flight at once
   __shared__ df sred[1 + 3 * kMaxK];
-  __shared__ double gam[kMaxK], av[kMaxK], bv[kMaxK], uv[kMaxK];
+  __shared__ double gam[kMaxK], av[kMaxK], bv[kMaxK];
   __shared__ int s_mode, s_done;
   __shared__ double s_beta;
   for (int v0 = warp * IT_RED_U; v0 < count; v0 += IT_WARPS * IT_RED_U) {
@@ -572,44 +581,66 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
   }
   const float2* Mm = Ei + k * k;
   const float2* Nt = Ei + 2 * k * k;
-  // output o = which * k + c; lanes 2 e and 2 e + 1 take j even and j odd
-  // (warp-uniform trip count: every lane reaches the pair shuffles)
-  for (int ob = t - lane; ob < 8 * k; ob += IT_THREADS) {
+  // output o = which * k + c: 0 gamma_c and u_c = (N g)_c, hence the
+  // correction term gamma_c (u_c - 2 h_c); 1 a_c; 2 b_c. Lanes 2 e and 2 e + 1
+  // take j even and j odd, each in two interleaved sums (warp-uniform trip
+  // count: every lane reaches the pair shuffles).
+  __shared__ df sterm[kMaxK];
+  for (int ob = t - lane; ob < 6 * k; ob += IT_THREADS) {
     const int o2 = ob + lane;
-    const bool act = o2 < 8 * k;
+    const bool act = o2 < 6 * k;
     const int o = o2 >> 1, par = o2 & 1;
-    const int which = act ? o / k : 4, c = act ? o - which * k : 0;
-    df s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+    const int which = act ? o / k : 3, c = act ? o - which * k : 0;
+    df s0 = {0.f, 0.f}, s1 = {0.f, 0.f}, s2 = {0.f, 0.f}, s3 = {0.f, 0.f};
     if (which == 0) {
-      for (int j = par; j < k; j += 2) s0 = df_fma(s0, Ei[j * k + c], g[j]);
+      for (int j = par; j < k; j += 4) {
+        s0 = df_fma(s0, Ei[j * k + c], g[j]);
+        s1 = df_fma(s1, Nt[j * k + c], g[j]);
+        if (j + 2 < k) {
+          s2 = df_fma(s2, Ei[(j + 2) * k + c], g[j + 2]);
+          s3 = df_fma(s3, Nt[(j + 2) * k + c], g[j + 2]);
+        }
+      }
     } else if (which == 1) {
-      for (int j = par; j < k; j += 2) {
+      for (int j = par; j < k; j += 4) {
         s0 = df_fma(s0, Ei[j * k + c], h[j]);
         s1 = df_fma(s1, Mm[j * k + c], g[j]);
+        if (j + 2 < k) {
+          s2 = df_fma(s2, Ei[(j + 2) * k + c], h[j + 2]);
+          s3 = df_fma(s3, Mm[(j + 2) * k + c], g[j + 2]);
+        }
       }
-    } else if (which == 2) {
-      if (reproj)
-        for (int j = par; j < k; j += 2) s0 = df_fma(s0, Ei[j * k + c], hp[j]);
-    } else if (which == 3) {
-      for (int j = par; j < k; j += 2) s0 = df_fma(s0, Nt[j * k + c], g[j]);
+    } else if (which == 2 && reproj) {
+      for (int j = par; j < k; j += 4) {
+        s0 = df_fma(s0, Ei[j * k + c], hp[j]);
+        if (j + 2 < k) s2 = df_fma(s2, Ei[(j + 2) * k + c], hp[j + 2]);
+      }
     }
+    s0 = df_add(s0, s2);
+    s1 = df_add(s1, s3);
     s0 = df_add(s0, df_shfl_xor(s0, 1));
     s1 = df_add(s1, df_shfl_xor(s1, 1));
     if (act && par == 0) {
-      if (which == 0) gam[c] = df_to_double(s0);
-      else if (which == 1) av[c] = df_to_double(s0) - df_to_double(s1);
-      else if (which == 2) bv[c] = df_to_double(s0);
-      else uv[c] = df_to_double(s0);
+      if (which == 0) {
+        gam[c] = df_to_double(s0);
+        const df hm2 = {-2.f * h[c].hi, -2.f * h[c].lo};  // exact scaling
+        sterm[c] = df_mul(s0, df_add(s1, hm2));
+      } else if (which == 1) {
+        av[c] = df_to_double(s0) - df_to_double(s1);
+      } else {
+        bv[c] = df_to_double(s0);
+      }
     }
   }
   __syncthreads();
   if (warp == 0) {
-    double corr = 0.0;
-    for (int c = lane; c < k; c += 32) corr += gam[c] * (uv[c] - 2.0 * df_to_double(h[c]));
-    corr = warp_sum(corr);
+    df corr = {0.f, 0.f};
+    for (int c = lane; c < k; c += 32) corr = df_add(corr, sterm[c]);
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) corr = df_add(corr, df_shfl_xor(corr, m));
     if (lane == 0) {
       const double rho_raw = df_to_double(sred[0]);
-      double rho_new = rho_raw + corr;
+      double rho_new = df_to_double(df_add(sred[0], corr));
       if (!(rho_new > 0.0)) rho_new = rho_raw;
       int mode = 0;
       if (rho_new <= thresh2)
