@@ -16,13 +16,13 @@
 namespace dcg {
 
 // Tile geometry of the TMA row-band kernel.
-constexpr int RB_ROWS = 4;                      // rows per stage (box height)
+constexpr int RB_ROWS = 8;                      // rows per stage (box height): 8 KB TMA boxes
 constexpr int RB_BOXW = 256;                    // floats per box row (1 KB)
 constexpr int RB_BOXES = 8;                     // boxes per stage
 constexpr int RB_CHUNK = RB_BOXW * RB_BOXES;    // 2048 columns per stage
-constexpr int RB_STAGES = 6;
+constexpr int RB_STAGES = 3;
 constexpr int RB_STAGE_FLOATS = RB_ROWS * RB_CHUNK;
-constexpr int RB_STAGE_BYTES = RB_STAGE_FLOATS * 4;  // 32 KB
+constexpr int RB_STAGE_BYTES = RB_STAGE_FLOATS * 4;  // 64 KB
 constexpr int RB_CONSUMER_WARPS = 8;            // one warp per box
 constexpr int RB_THREADS = (RB_CONSUMER_WARPS + 1) * 32;
 constexpr size_t RB_SMEM = size_t(RB_STAGES) * RB_STAGE_BYTES + 2 * RB_STAGES * sizeof(uint64_t) + 1024;
