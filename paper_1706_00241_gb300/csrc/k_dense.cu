@@ -643,6 +643,7 @@ __global__ void __launch_bounds__(256, 2) k_form_rbf(const float* __restrict__ X
   __shared__ __align__(16) float xiT[FR_DC][FR_LD];
   __shared__ __align__(16) float xjT[FR_DC][FR_LD];
   const int t = threadIdx.x, ty = t / 16, tx = t % 16;
+  if (blockIdx.x < blockIdx.y) return;  // A is symmetric: the tile above the diagonal writes both
   const int i0 = blockIdx.y * FR_T, j0 = blockIdx.x * FR_T;
   unsigned long long sq[8][4];
 #pragma unroll
@@ -677,6 +678,24 @@ __global__ void __launch_bounds__(256, 2) k_form_rbf(const float* __restrict__ X
   }
   const bool diag_tile = blockIdx.x == blockIdx.y;
   const bool vec_ok = (lda % 4) == 0 && (reinterpret_cast<uintptr_t>(A) % 16) == 0;
+  // entry values, val[a][cc] for row 8 ty + a and column 64 (cc / 4) + 4 tx + cc % 4
+  float val[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int pp = 0; pp < 4; ++pp) {
+      const float2 q = f2_unpack(sq[a][pp]);
+      val[a][2 * pp] = s2 * ex2_approx(q.x * c_exp2);
+      val[a][2 * pp + 1] = s2 * ex2_approx(q.y * c_exp2);
+    }
+  if (diag_tile) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc)
+        if (8 * ty + a == 64 * (cc / 4) + 4 * tx + cc % 4) val[a][cc] += noise;
+  }
+  // the tile (rows i0.., columns j0..)
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     const int i = i0 + 8 * ty + a;
@@ -684,22 +703,32 @@ __global__ void __launch_bounds__(256, 2) k_form_rbf(const float* __restrict__ X
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
       const int j = j0 + 64 * g + 4 * tx;
-      const float2 q0 = f2_unpack(sq[a][2 * g]), q1 = f2_unpack(sq[a][2 * g + 1]);
-      float out[4] = {s2 * ex2_approx(q0.x * c_exp2), s2 * ex2_approx(q0.y * c_exp2),
-                      s2 * ex2_approx(q1.x * c_exp2), s2 * ex2_approx(q1.y * c_exp2)};
-      if (diag_tile) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (i == j + c) out[c] += noise;
-      }
       float* dst = A + int64_t(i) * lda + j;
       if (vec_ok && j + 3 < n) {
-        *reinterpret_cast<float4*>(dst) = make_float4(out[0], out[1], out[2], out[3]);
+        *reinterpret_cast<float4*>(dst) = make_float4(val[a][4 * g], val[a][4 * g + 1], val[a][4 * g + 2], val[a][4 * g + 3]);
       } else {
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-          if (j + c < n) dst[c] = out[c];
+          if (j + c < n) dst[c] = val[a][4 * g + c];
       }
+    }
+  }
+  if (diag_tile) return;
+  // its mirror (rows j0.., columns i0..): each lane writes 8 consecutive
+  // floats (one 32-byte run) of a row
+  const int ic = i0 + 8 * ty;
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) {
+    const int jr = j0 + 64 * (cc / 4) + 4 * tx + cc % 4;
+    if (jr >= n) continue;
+    float* dst = A + int64_t(jr) * lda + ic;
+    if (vec_ok && ic + 7 < n) {
+      *reinterpret_cast<float4*>(dst) = make_float4(val[0][cc], val[1][cc], val[2][cc], val[3][cc]);
+      *reinterpret_cast<float4*>(dst + 4) = make_float4(val[4][cc], val[5][cc], val[6][cc], val[7][cc]);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+        if (ic + a < n) dst[a] = val[a][cc];
     }
   }
 }

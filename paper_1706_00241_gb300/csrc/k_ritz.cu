@@ -266,7 +266,7 @@ cudaError_t chol_configure(int kmax) {
 constexpr int EIG_THREADS = 1024;
 constexpr int EIG_SMEM_MAX = 200 * 1024;  // dynamic shared memory of the eigen kernel
 constexpr int TS_P = 32;                  // panel rows of the blocked triangular solves
-constexpr int TS_CW = (kMaxM + 31) / 32;  // columns per lane in a panel update
+constexpr int TS_CWMAX = (kMaxM + 31) / 32;  // 32-column blocks of a panel update, at most
 
 // Forward substitution L X = B in place. L: n x n lower triangular (global,
 // leading dimension ldl); B: n x ncols (shared, leading dimension ldb, odd).
@@ -274,6 +274,7 @@ constexpr int TS_CW = (kMaxM + 31) / 32;  // columns per lane in a panel update
 // (one warp per panel row, lanes over columns), then solved by one warp per
 // column with lanes over the panel's rows and the panel's diagonal block
 // (reciprocal diagonal) in shared memory. Two barriers per panel.
+template <int CW>  // live 32-column blocks (ncols <= 32 CW)
 __device__ void trsm_lower_panels(const float* L, int ldl, float* B, int ldb, int n, int ncols,
                                   float (*Ld)[TS_P + 1]) {
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31, nw = blockDim.x >> 5;
@@ -291,20 +292,20 @@ __device__ void trsm_lower_panels(const float* L, int ldl, float* B, int ldb, in
     if (i0 > 0) {
       for (int rr = warp; rr < pr; rr += nw) {
         const float* lrow = L + (i0 + rr) * ldl;
-        float acc[TS_CW];
+        float acc[CW];
 #pragma unroll
-        for (int q = 0; q < TS_CW; ++q) acc[q] = 0.f;
+        for (int q = 0; q < CW; ++q) acc[q] = 0.f;
 #pragma unroll 4
         for (int j = 0; j < i0; ++j) {
           const float l = lrow[j];
           const float* bj = B + j * ldb + lane;
 #pragma unroll
-          for (int q = 0; q < TS_CW; ++q)
+          for (int q = 0; q < CW; ++q)
             if (lane + 32 * q < ncols) acc[q] = fmaf(l, bj[32 * q], acc[q]);
         }
         float* brow = B + (i0 + rr) * ldb + lane;
 #pragma unroll
-        for (int q = 0; q < TS_CW; ++q)
+        for (int q = 0; q < CW; ++q)
           if (lane + 32 * q < ncols) brow[32 * q] -= acc[q];
       }
     }
@@ -324,6 +325,7 @@ __device__ void trsm_lower_panels(const float* L, int ldl, float* B, int ldb, in
 
 // Back substitution L^T X = B in place (same layouts as trsm_lower_panels),
 // panels from the bottom.
+template <int CW>  // live 32-column blocks (ncols <= 32 CW)
 __device__ void trsm_lower_t_panels(const float* L, int ldl, float* B, int ldb, int n, int ncols,
                                     float (*Ld)[TS_P + 1]) {
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31, nw = blockDim.x >> 5;
@@ -342,20 +344,20 @@ __device__ void trsm_lower_t_panels(const float* L, int ldl, float* B, int ldb, 
     if (i1 < n) {
       for (int rr = warp; rr < pr; rr += nw) {
         const int i = i0 + rr;
-        float acc[TS_CW];
+        float acc[CW];
 #pragma unroll
-        for (int q = 0; q < TS_CW; ++q) acc[q] = 0.f;
+        for (int q = 0; q < CW; ++q) acc[q] = 0.f;
 #pragma unroll 4
         for (int j = i1; j < n; ++j) {
           const float l = L[j * ldl + i];
           const float* bj = B + j * ldb + lane;
 #pragma unroll
-          for (int q = 0; q < TS_CW; ++q)
+          for (int q = 0; q < CW; ++q)
             if (lane + 32 * q < ncols) acc[q] = fmaf(l, bj[32 * q], acc[q]);
         }
         float* brow = B + i * ldb + lane;
 #pragma unroll
-        for (int q = 0; q < TS_CW; ++q)
+        for (int q = 0; q < CW; ++q)
           if (lane + 32 * q < ncols) brow[32 * q] -= acc[q];
       }
     }
@@ -371,6 +373,118 @@ __device__ void trsm_lower_t_panels(const float* L, int ldl, float* B, int ldb, 
     }
     __syncthreads();
   }
+}
+
+// Dispatch on the number of live 32-column blocks (CTA-uniform).
+__device__ void trsm_lower(const float* L, int ldl, float* B, int ldb, int n, int ncols, float (*Ld)[TS_P + 1]) {
+  switch ((ncols + 31) / 32) {
+    case 1: trsm_lower_panels<1>(L, ldl, B, ldb, n, ncols, Ld); break;
+    case 2: trsm_lower_panels<2>(L, ldl, B, ldb, n, ncols, Ld); break;
+    case 3: trsm_lower_panels<3>(L, ldl, B, ldb, n, ncols, Ld); break;
+    case 4: trsm_lower_panels<4>(L, ldl, B, ldb, n, ncols, Ld); break;
+    case 5: trsm_lower_panels<5>(L, ldl, B, ldb, n, ncols, Ld); break;
+    case 6: trsm_lower_panels<6>(L, ldl, B, ldb, n, ncols, Ld); break;
+    default: trsm_lower_panels<TS_CWMAX>(L, ldl, B, ldb, n, ncols, Ld); break;
+  }
+}
+__device__ void trsm_lower_t(const float* L, int ldl, float* B, int ldb, int n, int ncols, float (*Ld)[TS_P + 1]) {
+  switch ((ncols + 31) / 32) {
+    case 1: trsm_lower_t_panels<1>(L, ldl, B, ldb, n, ncols, Ld); break;
+    case 2: trsm_lower_t_panels<2>(L, ldl, B, ldb, n, ncols, Ld); break;
+    case 3: trsm_lower_t_panels<3>(L, ldl, B, ldb, n, ncols, Ld); break;
+    case 4: trsm_lower_t_panels<4>(L, ldl, B, ldb, n, ncols, Ld); break;
+    case 5: trsm_lower_t_panels<5>(L, ldl, B, ldb, n, ncols, Ld); break;
+    case 6: trsm_lower_t_panels<6>(L, ldl, B, ldb, n, ncols, Ld); break;
+    default: trsm_lower_t_panels<TS_CWMAX>(L, ldl, B, ldb, n, ncols, Ld); break;
+  }
+}
+
+// One Householder step of the tridiagonalisation (column j, rows j+1 ..
+// j+Lh of C, Lh <= 32 NQ): every warp forms the reflector of column j itself
+// (v_k for k = lane + 32 q in registers), then one warp per row forms
+// p = tau A' v; after a barrier every warp forms K = tau/2 p^T v and updates
+// its rows of A' -= v w^T + w v^T with w = p - K v. Column j is not read after
+// step j; warp 0 stores the scaled v_j into it at the start of step j + 1.
+// NQ is the number of live 32-blocks, so no iteration is issued for entries
+// beyond the active part (32 warps; the caller dispatches on NQ).
+template <int NQ>
+__device__ __forceinline__ void tridiag_step(float* C, int ldc, int j, int Lh, float* dT, float* eT, float* tauH,
+                                             float* hw, float& scal_prev) {
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  float x[NQ];
+  float part = 0.f;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int i = lane + 32 * q;
+    x[q] = i < Lh ? C[(j + 1 + i) * ldc + j] : 0.f;
+    if (i > 0) part = fmaf(x[q], x[q], part);
+  }
+  const float sigma = warp_sum(part);
+  const float x0 = __shfl_sync(0xffffffffu, x[0], 0);
+  float tau = 0.f, scal = 0.f, beta = x0;
+  if (sigma != 0.f) {
+    const float mu = sqrtf(fmaf(x0, x0, sigma));
+    beta = x0 <= 0.f ? mu : -mu;
+    tau = (beta - x0) / beta;
+    scal = 1.f / (x0 - beta);
+  }
+  if (t == 0) {
+    dT[j] = C[j * ldc + j];
+    eT[j] = beta;
+    tauH[j] = tau;
+  }
+  scal_prev = scal;
+  float v[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) v[q] = (lane + 32 * q == 0) ? 1.f : x[q] * scal;
+  if (tau == 0.f) {   // uniform: every warp computed the same tau
+    __syncthreads();  // column j is read by every warp before warp 0 scales it
+    return;
+  }
+  float dd[NQ];
+#pragma unroll
+  for (int r = 0; r < NQ; ++r) {
+    const int i = warp + 32 * r;
+    dd[r] = 0.f;
+    if (i < Lh) {
+      const float* row = C + (j + 1 + i) * ldc + (j + 1);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        if (lane + 32 * q < Lh) dd[r] = fmaf(row[lane + 32 * q], v[q], dd[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NQ; ++r)
+    if (warp + 32 * r < Lh) {
+      const float s_ = warp_sum(dd[r]);
+      if (lane == 0) hw[warp + 32 * r] = tau * s_;
+    }
+  __syncthreads();
+  float pv = 0.f, w[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int k = lane + 32 * q;
+    w[q] = k < Lh ? hw[k] : 0.f;
+    pv = fmaf(w[q], v[q], pv);
+  }
+  const float K = 0.5f * tau * warp_sum(pv);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) w[q] = fmaf(-K, v[q], w[q]);
+#pragma unroll
+  for (int r = 0; r < NQ; ++r) {
+    const int i = warp + 32 * r;
+    if (i < Lh) {
+      const float vi = i == 0 ? 1.f : C[(j + 1 + i) * ldc + j] * scal;
+      const float wi = fmaf(-K, vi, hw[i]);
+      float* crow = C + (j + 1 + i) * ldc + (j + 1);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int k = lane + 32 * q;
+        if (k < Lh) crow[k] = fmaf(-vi, w[q], fmaf(-wi, v[q], crow[k]));
+      }
+    }
+  }
+  __syncthreads();
 }
 
 // Harmonic Ritz eigen-solve of Eq. 7 (one CTA of 1024 threads).
@@ -509,7 +623,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
     for (int j = lane; j < m; j += 32) C[i * ldc + j] = Gf[orig[i] * m_full + orig[j]];
   __syncthreads();
   // 3. Y = L^{-1} G'; 4. C = L^{-1} Y^T = L^{-1} G' L^{-T}, symmetrised
-  trsm_lower_panels(Ff, m, C, ldc, m, m, Ld);
+  trsm_lower(Ff, m, C, ldc, m, m, Ld);
   for (int i = warp; i < m; i += nw)
     for (int j = i + 1 + lane; j < m; j += 32) {
       const float u = C[i * ldc + j];
@@ -517,7 +631,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
       C[j * ldc + i] = u;
     }
   __syncthreads();
-  trsm_lower_panels(Ff, m, C, ldc, m, m, Ld);
+  trsm_lower(Ff, m, C, ldc, m, m, Ld);
   for (int i = warp; i < m; i += nw)
     for (int j = i + 1 + lane; j < m; j += 32) {
       const float s = 0.5f * (C[i * ldc + j] + C[j * ldc + i]);
@@ -536,14 +650,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
   //       vector), made orthonormal by Gram-Schmidt in selection order
   //       (near-equal values), then z = Q y by applying the reflectors.
   __shared__ float dT[kMaxM], eT[kMaxM], e2[kMaxM], tauH[kMaxM], hw[kMaxM];
-  // a. tridiagonalisation; per step every warp forms the reflector of column
-  //    j itself (v_k for k = lane + 32 q in registers), then one warp per row
-  //    forms p = tau A' v; after a barrier every warp forms K = tau/2 p^T v
-  //    and updates its rows of A' -= v w^T + w v^T with w = p - K v. Column j
-  //    is not read after step j; warp 0 stores the scaled v_j into it during
-  //    step j + 1.
+  // a. tridiagonalisation, one tridiag_step per column
   static_assert(EIG_THREADS == 1024, "tridiagonalisation assumes 32 warps");
-  constexpr int RQ = (kMaxM + 31) / 32;  // rows per warp and entries per lane
   float scal_prev = 0.f;
   for (int j = 0; j + 2 < m; ++j) {
     const int Lh = m - j - 1;  // rows j+1 .. m-1
@@ -551,80 +659,15 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
       const int jp = j - 1, Lp = Lh + 1;
       for (int i = lane + 1; i < Lp; i += 32) C[(jp + 1 + i) * ldc + jp] *= scal_prev;
     }
-    float x[RQ];
-    float part = 0.f;
-#pragma unroll
-    for (int q = 0; q < RQ; ++q) {
-      const int i = lane + 32 * q;
-      x[q] = i < Lh ? C[(j + 1 + i) * ldc + j] : 0.f;
-      if (i > 0) part = fmaf(x[q], x[q], part);
+    switch ((Lh + 31) / 32) {  // CTA-uniform: the step unrolled for the live 32-blocks only
+      case 1: tridiag_step<1>(C, ldc, j, Lh, dT, eT, tauH, hw, scal_prev); break;
+      case 2: tridiag_step<2>(C, ldc, j, Lh, dT, eT, tauH, hw, scal_prev); break;
+      case 3: tridiag_step<3>(C, ldc, j, Lh, dT, eT, tauH, hw, scal_prev); break;
+      case 4: tridiag_step<4>(C, ldc, j, Lh, dT, eT, tauH, hw, scal_prev); break;
+      case 5: tridiag_step<5>(C, ldc, j, Lh, dT, eT, tauH, hw, scal_prev); break;
+      case 6: tridiag_step<6>(C, ldc, j, Lh, dT, eT, tauH, hw, scal_prev); break;
+      default: tridiag_step<7>(C, ldc, j, Lh, dT, eT, tauH, hw, scal_prev); break;
     }
-    const float sigma = warp_sum(part);
-    const float x0 = __shfl_sync(0xffffffffu, x[0], 0);
-    float tau = 0.f, scal = 0.f, beta = x0;
-    if (sigma != 0.f) {
-      const float mu = sqrtf(fmaf(x0, x0, sigma));
-      beta = x0 <= 0.f ? mu : -mu;
-      tau = (beta - x0) / beta;
-      scal = 1.f / (x0 - beta);
-    }
-    if (t == 0) {
-      dT[j] = C[j * ldc + j];
-      eT[j] = beta;
-      tauH[j] = tau;
-    }
-    scal_prev = scal;
-    float v[RQ];
-#pragma unroll
-    for (int q = 0; q < RQ; ++q) v[q] = (lane + 32 * q == 0) ? 1.f : x[q] * scal;
-    if (tau == 0.f) {  // uniform: every warp computed the same tau
-      __syncthreads();  // column j is read by every warp before warp 0 scales it
-      continue;
-    }
-    float dd[RQ];
-#pragma unroll
-    for (int r = 0; r < RQ; ++r) {
-      const int i = warp + 32 * r;
-      dd[r] = 0.f;
-      if (i < Lh) {
-        const float* row = C + (j + 1 + i) * ldc + (j + 1);
-#pragma unroll
-        for (int q = 0; q < RQ; ++q)
-          if (lane + 32 * q < Lh) dd[r] = fmaf(row[lane + 32 * q], v[q], dd[r]);
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < RQ; ++r)
-      if (warp + 32 * r < Lh) {
-        const float s_ = warp_sum(dd[r]);
-        if (lane == 0) hw[warp + 32 * r] = tau * s_;
-      }
-    __syncthreads();
-    float pv = 0.f, w[RQ];
-#pragma unroll
-    for (int q = 0; q < RQ; ++q) {
-      const int k = lane + 32 * q;
-      w[q] = k < Lh ? hw[k] : 0.f;
-      pv = fmaf(w[q], v[q], pv);
-    }
-    const float K = 0.5f * tau * warp_sum(pv);
-#pragma unroll
-    for (int q = 0; q < RQ; ++q) w[q] = fmaf(-K, v[q], w[q]);
-#pragma unroll
-    for (int r = 0; r < RQ; ++r) {
-      const int i = warp + 32 * r;
-      if (i < Lh) {
-        const float vi = i == 0 ? 1.f : C[(j + 1 + i) * ldc + j] * scal;
-        const float wi = fmaf(-K, vi, hw[i]);
-        float* crow = C + (j + 1 + i) * ldc + (j + 1);
-#pragma unroll
-        for (int q = 0; q < RQ; ++q) {
-          const int k = lane + 32 * q;
-          if (k < Lh) crow[k] = fmaf(-vi, w[q], fmaf(-wi, v[q], crow[k]));
-        }
-      }
-    }
-    __syncthreads();
   }
   __syncthreads();
   if (warp == 0 && m >= 3) {  // scaled v of the last reflector
@@ -720,10 +763,15 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
   const bool smallest = a.select == DCG_SELECT_SMALLEST;
   auto vrow = [&](int c) -> float* { return Vt + (smallest ? c : (m - 1 - c)) * ldc; };
   const float piv_tiny = 1e-7f * fmaxf(fabsf(s_lo), fabsf(s_hi)) + 1e-30f;  // eps |T|
+  // reciprocal pivots of T - lam I, interleaved (entry i of vector c at
+  // i * k_new + c, so the threads of a warp touch consecutive words): in
+  // shared memory after C and V^T when they fit, in global memory otherwise
+  const int used_f = (Vt == a.Vj ? 1 : 2) * m * ldc;
+  float* rub = (used_f + k_new * m) * int(sizeof(float)) <= EIG_SMEM_MAX ? C + used_f : Xc;
   for (int c = t; c < k_new; c += blockDim.x) {
     const float lam = th[smallest ? c : (m - 1 - c)];
     float* __restrict__ y = vrow(c);
-    float* __restrict__ ru = Xc + c * m;  // reciprocal pivots of T - lam I
+    float* __restrict__ ru = rub + c;  // ru[i * k_new]
     // LU of T - lam I without pivoting (tiny pivots perturbed), computed once;
     // l_i = e_{i-1} / u_{i-1}
     float ui = dT[0] - lam;
@@ -735,20 +783,20 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
       ui = fmaf(-l, eT[i - 1], dT[i] - lam);
       if (fabsf(ui) < piv_tiny) ui = piv_tiny;
       rprev = 1.f / ui;
-      ru[i] = rprev;
+      ru[i * k_new] = rprev;
     }
     for (int i = 0; i < m; ++i) y[i] = 1.f + 0.0137f * float((i * 7 + c * 3) % 11);
     for (int itn = 0; itn < 3; ++itn) {  // forward and back substitution, normalise
       float yp = y[0];
       for (int i = 1; i < m; ++i) {
-        yp = fmaf(-eT[i - 1] * ru[i - 1], yp, y[i]);
+        yp = fmaf(-eT[i - 1] * ru[(i - 1) * k_new], yp, y[i]);
         y[i] = yp;
       }
-      float yn = y[m - 1] * ru[m - 1];
+      float yn = y[m - 1] * ru[(m - 1) * k_new];
       y[m - 1] = yn;
       float nrm = yn * yn;
       for (int i = m - 2; i >= 0; --i) {
-        yn = fmaf(-eT[i], yn, y[i]) * ru[i];
+        yn = fmaf(-eT[i], yn, y[i]) * ru[i * k_new];
         y[i] = yn;
         nrm = fmaf(yn, yn, nrm);
       }
@@ -825,7 +873,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
   for (int i = warp; i < m; i += nw)
     for (int c = lane; c < k_new; c += 32) Y[i * ldb + c] = vrow(c)[i];
   __syncthreads();
-  trsm_lower_t_panels(Ff, m, Y, ldb, m, k_new, Ld);
+  trsm_lower_t(Ff, m, Y, ldb, m, k_new, Ld);
   for (int c = warp; c < k_new; c += nw)
     for (int i = lane; i < m_orig; i += 32) {
       const int ci = pos[i];
