@@ -101,27 +101,47 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def run_sequence(P, torch, solver, Xd, bs_dev, A, T, deflate, ev_pool):
-    """One sequence; returns per-system infos and device-timed (form, solve) ms."""
+def run_sequence(P, torch, solver, Xd, bs_dev, A, T, deflate, ev_pool, side=None):
+    """One sequence; returns per-system infos and device-timed (form, solve) ms.
+
+    With a side stream and deflation, A_{t+1} is formed on the side stream
+    while the harmonic-Ritz update of system t runs on the solver's stream
+    (dcg_update_subspace_async: the update reads W, AW and the stored
+    directions, never A; the next solve waits for both). The solve times then
+    include the update, and the form times overlap them."""
     infos = []
-    form_ms = 0.0
-    solve_ms = 0.0
     stream = torch.cuda.current_stream()
+    fs, fe, ss, se = (ev_pool[i * T:(i + 1) * T] for i in range(4))
+    overlap = side is not None and deflate
+    fs[0].record(stream)
+    P.form_rbf_dense(Xd, CFG.lengthscale(0), CFG.signal_var, CFG.noise, out=A)
+    fe[0].record(stream)
     for t in range(T):
-        e0, e1, e2 = ev_pool[3 * t], ev_pool[3 * t + 1], ev_pool[3 * t + 2]
-        e0.record(stream)
-        P.form_rbf_dense(Xd, CFG.lengthscale(t), CFG.signal_var, CFG.noise, out=A)
-        e1.record(stream)
         solver.set_operator_dense(A)
+        ss[t].record(stream)
         x, info = solver.solve(bs_dev[t])
-        if deflate:
-            solver.update_subspace()
-        e2.record(stream)
         infos.append(info)
+        if overlap:
+            side.wait_stream(stream)      # the solve is complete (A free); the update is not waited for
+            solver.update_subspace(wait=False)
+            se[t].record(stream)
+            if t + 1 < T:
+                fs[t + 1].record(side)
+                P.form_rbf_dense(Xd, CFG.lengthscale(t + 1), CFG.signal_var, CFG.noise, out=A, stream=side)
+                fe[t + 1].record(side)
+                stream.wait_stream(side)
+        else:
+            if deflate:
+                solver.update_subspace()
+            se[t].record(stream)
+            if t + 1 < T:
+                fs[t + 1].record(stream)
+                P.form_rbf_dense(Xd, CFG.lengthscale(t + 1), CFG.signal_var, CFG.noise, out=A)
+                fe[t + 1].record(stream)
+    solver.sync()                          # a pending update of the last system
     torch.cuda.synchronize()
-    for t in range(T):
-        form_ms += ev_pool[3 * t].elapsed_time(ev_pool[3 * t + 1])
-        solve_ms += ev_pool[3 * t + 1].elapsed_time(ev_pool[3 * t + 2])
+    form_ms = sum(fs[t].elapsed_time(fe[t]) for t in range(T))
+    solve_ms = sum(ss[t].elapsed_time(se[t]) for t in range(T))
     return infos, form_ms, solve_ms
 
 
@@ -147,6 +167,12 @@ def gpu_arm(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    # solver stream at high priority, so that the one-CTA eigen-solve of an
+    # overlapped update gets an SM ahead of the next operator's formation,
+    # which runs on the (default-priority) side stream
+    main = torch.cuda.Stream(priority=-1)
+    torch.cuda.set_stream(main)
+    side = torch.cuda.Stream()
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -158,7 +184,7 @@ def gpu_arm(args):
     Xd = torch.tensor(X32, device="cuda")
     bs_dev = [torch.tensor(b, device="cuda") for b in b32]
     A = torch.empty((n, n), dtype=torch.float32, device="cuda")
-    ev_pool = [torch.cuda.Event(enable_timing=True) for _ in range(3 * T)]
+    ev_pool = [torch.cuda.Event(enable_timing=True) for _ in range(4 * T)]
 
     def barrier():
         if world > 1:
@@ -173,7 +199,7 @@ def gpu_arm(args):
     solver = make(True)
     for _ in range(args.warmup):
         solver.set_subspace(torch.zeros((0, n), device="cuda"))
-        run_sequence(P, torch, solver, Xd, bs_dev, A, T, True, ev_pool)
+        run_sequence(P, torch, solver, Xd, bs_dev, A, T, True, ev_pool, side)
 
     # timed region: K whole sequences
     seq_solve_ms, seq_form_ms, all_infos = [], [], []
@@ -184,7 +210,7 @@ def gpu_arm(args):
         t_start.record()
         for _ in range(args.steps):
             solver.set_subspace(torch.zeros((0, n), device="cuda"))
-            infos, fm, sm = run_sequence(P, torch, solver, Xd, bs_dev, A, T, True, ev_pool)
+            infos, fm, sm = run_sequence(P, torch, solver, Xd, bs_dev, A, T, True, ev_pool, side)
             seq_solve_ms.append(sm)
             seq_form_ms.append(fm)
             all_infos.append(infos)
@@ -245,14 +271,20 @@ def gpu_arm(args):
     w0 = time.perf_counter()
     Xd2 = Xh.to("cuda", non_blocking=True)
     e2e_infos = []
+    cur = torch.cuda.current_stream()
+    P.form_rbf_dense(Xd2, CFG.lengthscale(0), CFG.signal_var, CFG.noise, out=A)
     for t in range(T):
-        P.form_rbf_dense(Xd2, CFG.lengthscale(t), CFG.signal_var, CFG.noise, out=A)
         solver.set_operator_dense(A)
         bd = bh[t].to("cuda", non_blocking=True)
         x, info = solver.solve(bd)
-        solver.update_subspace()
         xh[t].copy_(x, non_blocking=True)
+        side.wait_stream(cur)
+        solver.update_subspace(wait=False)
+        if t + 1 < T:
+            P.form_rbf_dense(Xd2, CFG.lengthscale(t + 1), CFG.signal_var, CFG.noise, out=A, stream=side)
+            cur.wait_stream(side)
         e2e_infos.append(info)
+    solver.sync()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - w0
     solver.close()

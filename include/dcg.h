@@ -224,13 +224,26 @@ dcg_status dcg_solve(dcg_ctx* ctx, const float* b, double* x, dcg_solve_info* in
 
 /* dcg_update_subspace: harmonic-Ritz extraction (Sec. 2.3, Eq. 7) from the
  * last solve: Z = [W, P], AZ = [AW, AP], F = Z^T AZ (symmetrised),
- * G = AZ^T AZ, G u = theta F u in float64, keep min(k, cols(Z)) values
- * (largest or smallest per cfg.select), W <- Z U with unit columns whose
- * largest-magnitude entry is positive.
+ * G = AZ^T AZ (float64 sums), G u = theta F u solved in float32 after scaling
+ * the pencil to unit diagonal (pivoted Cholesky of F, directions dependent at
+ * float32 dropped), keep min(k, cols(Z)) values (largest or smallest per
+ * cfg.select), W <- Z U with unit columns whose largest-magnitude entry is
+ * positive. Waits for the result on the host.
  *   k_new host, may be NULL; receives the new number of columns of W.
  * Errors: STATE (no completed solve since the last update), SUBSPACE_SINGULAR
  * (F not positive definite even after dropping directions), CUDA. */
 dcg_status dcg_update_subspace(dcg_ctx* ctx, int32_t* k_new);
+
+/* dcg_update_subspace_async: the same extraction, enqueued on the context's
+ * stream without waiting, so that the caller can overlap it with other work
+ * (for example forming the next operator on another stream: the update reads
+ * W, AW and the stored directions, not A). The update is then pending: the
+ * next call of dcg_solve, dcg_update_subspace(_async), dcg_get_subspace,
+ * dcg_set_subspace, dcg_get_ritz_values or dcg_sync waits for it first and,
+ * if it failed, returns its error (SUBSPACE_SINGULAR or CUDA) instead of doing
+ * its own work; W is then unchanged. Errors here: STATE (no completed solve
+ * since the last update), CUDA (enqueueing failed). */
+dcg_status dcg_update_subspace_async(dcg_ctx* ctx);
 
 /* Harmonic Ritz values of the last update, descending (float64, host).
  *   theta host, capacity cap; m host: number of values (cols(Z)). */
@@ -288,7 +301,7 @@ dcg_status dcg_sync(dcg_ctx* ctx);
  *   stream cudaStream_t as void*; everything runs on it, nothing synchronises.
  * Scratch: a 4352-byte array in the library, per device: an arrival counter
  * (cleared to zero on `stream` before every launch) and one double partial
- * per CTA for at most 512 CTAs. The grid is min(ceil(n / 4), number of SMs);
+ * per CTA for at most 512 CTAs. The grid is min(ceil(n / 8), number of SMs);
  * a device that would need more than 512 CTAs is rejected with UNSUPPORTED.
  * The scratch address is looked up once per device (cudaGetSymbolAddress with
  * that device current); make the first call on each device before any stream

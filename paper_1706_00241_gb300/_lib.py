@@ -80,6 +80,7 @@ SIGNATURES = {
     "dcg_form_rbf_dense": (_I32, [_P, _I64, _I32, _D, _D, _D, _P, _I64, _P]),
     "dcg_solve": (_I32, [_P, _P, _P, ctypes.POINTER(DcgSolveInfo)]),
     "dcg_update_subspace": (_I32, [_P, _PI32]),
+    "dcg_update_subspace_async": (_I32, [_P]),
     "dcg_get_ritz_values": (_I32, [_P, _PD, _I32, _PI32]),
     "dcg_set_subspace": (_I32, [_P, _P, _I32]),
     "dcg_get_subspace": (_I32, [_P, _P, _PI32]),

@@ -43,6 +43,7 @@ struct dcg_ctx {
   int k_active = 0;
   int m_last = 0;        // number of harmonic Ritz values of the last update
   bool have_solve = false;
+  bool ritz_pending = false;  // an update was enqueued and its result not yet read
   int last_iters = 0;
 
   // operator
@@ -94,6 +95,8 @@ static dcg_status fail(dcg_ctx* c, dcg_status s, const std::string& msg) {
     g_create_err = msg;
   return s;
 }
+
+static dcg_status finish_update(dcg_ctx* c);  // waits for a pending asynchronous update
 
 static dcg_status cuda_fail(dcg_ctx* c, cudaError_t e, const char* where) {
   std::string m = std::string(where) + ": " + cudaGetErrorString(e);
@@ -735,6 +738,7 @@ static dcg_status run_host_loop(dcg_ctx* c, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 extern "C" dcg_status dcg_solve(dcg_ctx* c, const float* b, double* x, dcg_solve_info* info) {
   if (!c) return DCG_ERR_INVALID_ARG;
+  { const dcg_status pend = finish_update(c); if (pend != DCG_OK) return pend; }
   if (!b || !x) return fail(c, DCG_ERR_INVALID_ARG, "b and x must not be NULL");
   if (c->op == OP_NONE) return fail(c, DCG_ERR_STATE, "no operator set");
   if (!c->cfg.host_loop && !c->graph_valid) {
@@ -799,18 +803,9 @@ extern "C" dcg_status dcg_solve(dcg_ctx* c, const float* b, double* x, dcg_solve
   return dcg_status(hs->status);
 }
 
-extern "C" dcg_status dcg_update_subspace(dcg_ctx* c, int32_t* k_new) {
-  if (!c) return DCG_ERR_INVALID_ARG;
-  if (!c->have_solve) return fail(c, DCG_ERR_STATE, "no completed solve since the last update");
+// Enqueues the harmonic-Ritz update on the context's stream (no host wait).
+static dcg_status enqueue_update(dcg_ctx* c) {
   const int kk = c->k_active, ns = c->h_st->nstored;
-  const int m = kk + ns;
-  int knew = std::min(c->cfg.k, m);
-  if (c->cfg.k == 0 || m == 0) {
-    c->have_solve = false;
-    c->m_last = 0;
-    if (k_new) *k_new = c->k_active;
-    return DCG_OK;
-  }
   RitzArgs a{};
   a.n = c->w.n;
   a.k_act = kk;
@@ -837,21 +832,66 @@ extern "C" dcg_status dcg_update_subspace(dcg_ctx* c, int32_t* k_new) {
   CK(launch_ritz(a, c->num_sms, c->w.XW + c->w.n, s));
   CK(cudaMemcpyAsync(c->h_small, c->k_out, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(c->h_small + 2, c->ritz_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
   c->have_solve = false;
+  c->ritz_pending = true;
+  return DCG_OK;
+}
+
+// Waits for an enqueued update and applies its result (new k, Ritz count);
+// returns the update's status.
+static dcg_status finish_update(dcg_ctx* c) {
+  if (!c->ritz_pending) return DCG_OK;
+  c->ritz_pending = false;
+  CK(cudaStreamSynchronize(c->stream));
   if (c->h_small[2] != DCG_OK) {
     c->m_last = 0;
     return fail(c, dcg_status(c->h_small[2]), "harmonic Ritz: F not positive definite");
   }
-  knew = c->h_small[0];
-  c->k_active = knew;
+  c->k_active = c->h_small[0];
   c->m_last = c->h_small[1];
-  if (k_new) *k_new = knew;
   return DCG_OK;
+}
+
+// Common checks of both update calls; *skip is set when there is nothing to
+// extract (k = 0 or no columns in Z).
+static dcg_status begin_update(dcg_ctx* c, bool* skip) {
+  *skip = false;
+  dcg_status st = finish_update(c);
+  if (st != DCG_OK) return st;
+  if (!c->have_solve) return fail(c, DCG_ERR_STATE, "no completed solve since the last update");
+  const int m = c->k_active + c->h_st->nstored;
+  if (c->cfg.k == 0 || m == 0) {
+    c->have_solve = false;
+    c->m_last = 0;
+    *skip = true;
+  }
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_update_subspace(dcg_ctx* c, int32_t* k_new) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  bool skip = false;
+  dcg_status st = begin_update(c, &skip);
+  if (st != DCG_OK) return st;
+  if (!skip) {
+    if ((st = enqueue_update(c)) != DCG_OK) return st;
+    if ((st = finish_update(c)) != DCG_OK) return st;
+  }
+  if (k_new) *k_new = c->k_active;
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_update_subspace_async(dcg_ctx* c) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  bool skip = false;
+  dcg_status st = begin_update(c, &skip);
+  if (st != DCG_OK || skip) return st;
+  return enqueue_update(c);
 }
 
 extern "C" dcg_status dcg_get_ritz_values(dcg_ctx* c, double* theta, int32_t cap, int32_t* m) {
   if (!c) return DCG_ERR_INVALID_ARG;
+  { const dcg_status pend = finish_update(c); if (pend != DCG_OK) return pend; }
   if (m) *m = c->m_last;
   if (!theta || cap <= 0 || c->m_last == 0) return DCG_OK;
   const int cnt = std::min(cap, c->m_last);
@@ -862,6 +902,7 @@ extern "C" dcg_status dcg_get_ritz_values(dcg_ctx* c, double* theta, int32_t cap
 
 extern "C" dcg_status dcg_set_subspace(dcg_ctx* c, const float* W, int32_t k) {
   if (!c) return DCG_ERR_INVALID_ARG;
+  { const dcg_status pend = finish_update(c); if (pend != DCG_OK) return pend; }
   if (k < 0 || k > c->cfg.k) return fail(c, DCG_ERR_INVALID_ARG, "k must be in [0, cfg.k]");
   if (k > 0 && !W) return fail(c, DCG_ERR_INVALID_ARG, "W is NULL");
   if (k > 0)
@@ -873,6 +914,7 @@ extern "C" dcg_status dcg_set_subspace(dcg_ctx* c, const float* W, int32_t k) {
 
 extern "C" dcg_status dcg_get_subspace(dcg_ctx* c, float* W, int32_t* k) {
   if (!c) return DCG_ERR_INVALID_ARG;
+  { const dcg_status pend = finish_update(c); if (pend != DCG_OK) return pend; }
   if (k) *k = c->k_active;
   if (W && c->k_active > 0) {
     CK(cudaMemcpyAsync(W, c->w.XW + c->w.n, size_t(c->w.n) * c->k_active * 4, cudaMemcpyDeviceToDevice,
@@ -921,6 +963,7 @@ extern "C" dcg_status dcg_apply_block(dcg_ctx* c, const float* V, int32_t ncols,
 
 extern "C" dcg_status dcg_sync(dcg_ctx* c) {
   if (!c) return DCG_ERR_INVALID_ARG;
+  { const dcg_status pend = finish_update(c); if (pend != DCG_OK) return pend; }
   CK(cudaStreamSynchronize(c->stream));
   return DCG_OK;
 }

@@ -135,8 +135,16 @@ class DefCG:
             self._check(st, "dcg_solve")
         return x, d
 
-    def update_subspace(self) -> int:
-        """Harmonic-Ritz extraction of the next W (Sec. 2.3); returns its width."""
+    def update_subspace(self, wait: bool = True) -> int | None:
+        """Harmonic-Ritz extraction of the next W (Sec. 2.3); returns its width.
+
+        With ``wait=False`` the extraction is only enqueued on the solver's
+        stream and None is returned; the next solve (or subspace query) waits
+        for it and raises its error, if any. Work on other streams, such as
+        forming the next operator, then overlaps it."""
+        if not wait:
+            self._check(self.lib.dcg_update_subspace_async(self._ctx), "dcg_update_subspace_async")
+            return None
         k = ctypes.c_int32(0)
         self._check(self.lib.dcg_update_subspace(self._ctx, ctypes.byref(k)), "dcg_update_subspace")
         return k.value

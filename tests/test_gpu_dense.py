@@ -379,3 +379,47 @@ def test_host_loop_matches_graph(dcg, refine_every):
         assert a["status"] == b["status"] == 0
         assert np.array_equal(a["x"], b["x"])
         assert np.array_equal(a["theta"], b["theta"])
+
+
+def test_async_update_overlapped_with_forming_matches_sync(dcg):
+    # dcg_update_subspace_async, with the next operator formed on a second
+    # stream while the extraction runs, gives bit-identical solves to the
+    # synchronous update: the extraction reads W, AW and the stored
+    # directions, never A, and the next solve waits for both.
+    cfg = S.DENSE_16384.scaled(3000, T=5)
+    X, bs = S.draw_sequence(cfg, T=cfg.T)
+    Xd = dev(X.astype(np.float32))
+    n = cfg.n
+    lda = (n + 3) // 4 * 4
+    runs = []
+    for overlap in (False, True):
+        side = torch.cuda.Stream()
+        A = torch.empty((n, lda), dtype=torch.float32, device="cuda")
+        xs, its = [], []
+        with dcg.DefCG(n, cfg.k, cfg.ell, 1e-6) as s:
+            main = s.stream
+            dcg.form_rbf_dense(Xd, cfg.lengthscale(0), cfg.signal_var, cfg.noise, out=A)
+            for t in range(cfg.T):
+                s.set_operator_dense(A, lda)
+                x, info = s.solve(dev(bs[t]))
+                assert info["status"] == 0 and info["relres_true"] <= 1e-6
+                xs.append(x.cpu().numpy())
+                its.append(info["iters"])
+                if not overlap:
+                    s.update_subspace()
+                    if t + 1 < cfg.T:
+                        dcg.form_rbf_dense(Xd, cfg.lengthscale(t + 1), cfg.signal_var, cfg.noise, out=A)
+                else:
+                    side.wait_stream(main)  # the solve is complete; the update below is not waited for
+                    assert s.update_subspace(wait=False) is None
+                    if t + 1 < cfg.T:
+                        dcg.form_rbf_dense(Xd, cfg.lengthscale(t + 1), cfg.signal_var, cfg.noise, out=A,
+                                           stream=side)
+                        main.wait_stream(side)
+            s.sync()
+            k_final = s.get_subspace().shape[0]
+        runs.append((xs, its, k_final))
+    (xs0, it0, k0), (xs1, it1, k1) = runs
+    assert it0 == it1 and k0 == k1 == cfg.k
+    for a, b in zip(xs0, xs1):
+        assert np.array_equal(a, b)
