@@ -137,9 +137,45 @@ __global__ void __launch_bounds__(RB_THREADS, 1)
     float acc[RB_ROWS], cmp[RB_ROWS];
 #pragma unroll
     for (int r = 0; r < RB_ROWS; ++r) acc[r] = cmp[r] = 0.f;
+    // The vector slice of a stage (v, or the split x = xh + xl) does not depend
+    // on the tile: the slice of stage it + 1 is loaded before the wait for tile
+    // it, so its L2 latency overlaps the current stage.
+    constexpr int VW = RESID ? 8 : 4;  // floats per slot: xh[4] xl[4], or v[4]
+    auto load_vec = [&](int itv, float (&dstv)[2][VW]) {
+      const int cv = itv % nchunks;
+      const int c0 = cv * RB_CHUNK + warp * RB_BOXW;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = c0 + 4 * (lane + 32 * h);
+        if (j + 3 < n) {
+          if constexpr (RESID) {
+            const float4 u = __ldg(reinterpret_cast<const float4*>(a.xh + j));
+            const float4 l = __ldg(reinterpret_cast<const float4*>(a.xl + j));
+            dstv[h][0] = u.x; dstv[h][1] = u.y; dstv[h][2] = u.z; dstv[h][3] = u.w;
+            dstv[h][4] = l.x; dstv[h][5] = l.y; dstv[h][6] = l.z; dstv[h][7] = l.w;
+          } else {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(a.v + j));
+            dstv[h][0] = v.x; dstv[h][1] = v.y; dstv[h][2] = v.z; dstv[h][3] = v.w;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if constexpr (RESID) {
+              dstv[h][e] = j + e < n ? __ldg(a.xh + j + e) : 0.f;
+              dstv[h][4 + e] = j + e < n ? __ldg(a.xl + j + e) : 0.f;
+            } else {
+              dstv[h][e] = j + e < n ? __ldg(a.v + j + e) : 0.f;
+            }
+          }
+        }
+      }
+    };
+    float vcur[2][VW], vnxt[2][VW];
+    if (total > 0) load_vec(0, vcur);
     int it = 0;
     for (; it < total; ++it) {
       const int s = it % RB_STAGES;
+      if (it + 1 < total) load_vec(it + 1, vnxt);
       if (!mbar_wait_bounded(&full[s], (it / RB_STAGES) & 1)) {
         s_abort = 1;
         break;
@@ -151,57 +187,38 @@ __global__ void __launch_bounds__(RB_THREADS, 1)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int slot = lane + 32 * h;
-          const int j = col0 + 4 * slot;
           if constexpr (RESID) {
-            float xh[4], xl[4];
-            if (j + 3 < n) {
-              const float4 u = __ldg(reinterpret_cast<const float4*>(a.xh + j));
-              const float4 l = __ldg(reinterpret_cast<const float4*>(a.xl + j));
-              xh[0] = u.x; xh[1] = u.y; xh[2] = u.z; xh[3] = u.w;
-              xl[0] = l.x; xl[1] = l.y; xl[2] = l.z; xl[3] = l.w;
-            } else {
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                xh[e] = j + e < n ? __ldg(a.xh + j + e) : 0.f;
-                xl[e] = j + e < n ? __ldg(a.xl + j + e) : 0.f;
-              }
-            }
 #pragma unroll
             for (int r = 0; r < RB_ROWS; ++r) {
               const float4 av = reinterpret_cast<const float4*>(box + r * RB_BOXW)[slot];
-              dot2_step(acc[r], cmp[r], av.x, xh[0], xl[0]);
-              dot2_step(acc[r], cmp[r], av.y, xh[1], xl[1]);
-              dot2_step(acc[r], cmp[r], av.z, xh[2], xl[2]);
-              dot2_step(acc[r], cmp[r], av.w, xh[3], xl[3]);
+              dot2_step(acc[r], cmp[r], av.x, vcur[h][0], vcur[h][4]);
+              dot2_step(acc[r], cmp[r], av.y, vcur[h][1], vcur[h][5]);
+              dot2_step(acc[r], cmp[r], av.z, vcur[h][2], vcur[h][6]);
+              dot2_step(acc[r], cmp[r], av.w, vcur[h][3], vcur[h][7]);
             }
           } else {
-            float4 v;
-            if (j + 3 < n) {
-              v = __ldg(reinterpret_cast<const float4*>(a.v + j));
-            } else {
-              v.x = j < n ? __ldg(a.v + j) : 0.f;
-              v.y = j + 1 < n ? __ldg(a.v + j + 1) : 0.f;
-              v.z = j + 2 < n ? __ldg(a.v + j + 2) : 0.f;
-              v.w = 0.f;
-            }
 #pragma unroll
             for (int r = 0; r < RB_ROWS; ++r) {
               const float4 av = reinterpret_cast<const float4*>(box + r * RB_BOXW)[slot];
               if constexpr (COMPQ) {
-                dot2_step(acc[r], cmp[r], av.x, v.x, 0.f);
-                dot2_step(acc[r], cmp[r], av.y, v.y, 0.f);
-                dot2_step(acc[r], cmp[r], av.z, v.z, 0.f);
-                dot2_step(acc[r], cmp[r], av.w, v.w, 0.f);
+                dot2_step(acc[r], cmp[r], av.x, vcur[h][0], 0.f);
+                dot2_step(acc[r], cmp[r], av.y, vcur[h][1], 0.f);
+                dot2_step(acc[r], cmp[r], av.z, vcur[h][2], 0.f);
+                dot2_step(acc[r], cmp[r], av.w, vcur[h][3], 0.f);
               } else {
-                acc[r] = fmaf(av.x, v.x, acc[r]);
-                acc[r] = fmaf(av.y, v.y, acc[r]);
-                acc[r] = fmaf(av.z, v.z, acc[r]);
-                acc[r] = fmaf(av.w, v.w, acc[r]);
+                acc[r] = fmaf(av.x, vcur[h][0], acc[r]);
+                acc[r] = fmaf(av.y, vcur[h][1], acc[r]);
+                acc[r] = fmaf(av.z, vcur[h][2], acc[r]);
+                acc[r] = fmaf(av.w, vcur[h][3], acc[r]);
               }
             }
           }
         }
       }
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) vcur[h][e] = vnxt[h][e];
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
       if (c == nchunks - 1) {
