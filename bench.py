@@ -383,6 +383,8 @@ def kernel_arm(args):
         unit, bound = "GB/s", "hbm"
         peak, kind = peaks()
         workload = f"stored dense fp32 n={n}"
+    elif args.kernel in ("apply_block", "form", "iter"):
+        return kernel_arm_dense(args, P, torch, stream)
     else:
         cfg = S.MF_131072 if args.xformat == "bf16" else S.MF_262144
         n = args.n or cfg.n
@@ -416,6 +418,68 @@ def kernel_arm(args):
                       "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                                    "frac": achieved / peak, "peak_kind": kind,
                                    "algorithmic_per_launch": algo}}))
+
+
+def kernel_arm_dense(args, P, torch, stream):
+    """Single-kernel timing on the stored workload, for profiling:
+    apply_block: Y = A W with 32 columns (k_apply_block); form: A = K + sigma^2 I
+    (k_form_rbf); iter: system 1 of the sequence solved in host-loop mode
+    after system 0 and its update (its k_iter_fused launches are the ones a
+    profiler captures; the line reports the solve)."""
+    n = args.n or CFG.n
+    X, bs = S.draw_sequence(CFG.scaled(n, T=2) if n != CFG.n else CFG, T=2)
+    Xd = torch.tensor(X.astype(np.float32), device="cuda")
+    A = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    P.form_rbf_dense(Xd, CFG.lengthscale(0), CFG.signal_var, CFG.noise, out=A)
+    hz = 2.07e9
+    if args.kernel == "iter":
+        solver = P.DefCG(n, CFG.k, CFG.ell, CFG.tol, window="last", select="largest", host_loop=True)
+        solver.set_operator_dense(A)
+        solver.solve(torch.tensor(bs[0].astype(np.float32), device="cuda"))
+        solver.update_subspace()
+        P.form_rbf_dense(Xd, CFG.lengthscale(1), CFG.signal_var, CFG.noise, out=A)
+        solver.set_operator_dense(A)
+        b1 = torch.tensor(bs[1].astype(np.float32), device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, info = solver.solve(b1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        solver.close()
+        print(json.dumps({"kernel": "k_iter_fused (inside a host-loop solve)", "workload": f"stored dense fp32 n={n}, "
+                          f"system 1, k={CFG.k}", "solve_ms": e0.elapsed_time(e1), "iters": info["iters"],
+                          "status": info["status"]}))
+        return
+    if args.kernel == "apply_block":
+        solver = P.DefCG(n, 0, 0, CFG.tol)
+        solver.set_operator_dense(A)
+        V = torch.tensor(np.random.default_rng(1).standard_normal((CFG.k, n)).astype(np.float32), device="cuda")
+        fn = lambda: solver.apply_block(V)
+        algo, unit, bound = 2.0 * n * n * CFG.k, "TFLOP/s", "alu"
+        peak, kind = 152 * 128 * 2 * hz / 1e12, "nominal FP32 FMA (152 SMs x 128 lanes x 2070 MHz)"
+        name = f"k_apply_block (Y = A W, {CFG.k} columns)"
+    else:
+        solver = None
+        fn = lambda: P.form_rbf_dense(Xd, CFG.lengthscale(0), CFG.signal_var, CFG.noise, out=A)
+        algo, unit, bound = 4.0 * n * n, "GB/s", "hbm"
+        peak, kind = peaks()
+        name = "k_form_rbf (A = K + sigma^2 I, written once)"
+    for _ in range(args.warmup):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    achieved = algo / (ms * 1e-3) / (1e9 if unit == "GB/s" else 1e12)
+    if solver is not None:
+        solver.close()
+    print(json.dumps({"kernel": name, "workload": f"stored dense fp32 n={n}", "launch_ms": ms, "launches": args.steps,
+                      "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                                   "frac": achieved / peak, "peak_kind": kind, "algorithmic_per_launch": algo}}))
 
 
 def tensor_peak(xformat):
@@ -544,7 +608,7 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the solve's kernels from the host instead of one CUDA graph "
                          "(profiling mode: ncu cannot list kernels inside conditional graphs)")
-    ap.add_argument("--kernel", choices=["gemv", "rbf_mv"], default=None,
+    ap.add_argument("--kernel", choices=["gemv", "rbf_mv", "apply_block", "form", "iter"], default=None,
                     help="time one hot kernel alone (q = A p) instead of the sequence")
     ap.add_argument("--n", type=int, default=0, help="system size for --kernel (default: the workload's)")
     ap.add_argument("--systems", type=int, default=0,
