@@ -581,61 +581,29 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
   }
   const float2* Mm = Ei + k * k;
   const float2* Nt = Ei + 2 * k * k;
-  // output o = which * k + c: 0 gamma_c and u_c = (N g)_c, hence the
-  // correction term gamma_c (u_c - 2 h_c); 1 a_c; 2 b_c. Lanes 2 e and 2 e + 1
-  // take j even and j odd, each in two interleaved sums (warp-uniform trip
-  // count: every lane reaches the pair shuffles).
-  __shared__ df sterm[kMaxK];
-  for (int ob = t - lane; ob < 6 * k; ob += IT_THREADS) {
-    const int o2 = ob + lane;
-    const bool act = o2 < 6 * k;
-    const int o = o2 >> 1, par = o2 & 1;
-    const int which = act ? o / k : 3, c = act ? o - which * k : 0;
-    df s0 = {0.f, 0.f}, s1 = {0.f, 0.f}, s2 = {0.f, 0.f}, s3 = {0.f, 0.f};
-    if (which == 0) {
-      for (int j = par; j < k; j += 4) {
-        s0 = df_fma(s0, Ei[j * k + c], g[j]);
-        s1 = df_fma(s1, Nt[j * k + c], g[j]);
-        if (j + 2 < k) {
-          s2 = df_fma(s2, Ei[(j + 2) * k + c], g[j + 2]);
-          s3 = df_fma(s3, Nt[(j + 2) * k + c], g[j + 2]);
-        }
-      }
-    } else if (which == 1) {
-      for (int j = par; j < k; j += 4) {
-        s0 = df_fma(s0, Ei[j * k + c], h[j]);
-        s1 = df_fma(s1, Mm[j * k + c], g[j]);
-        if (j + 2 < k) {
-          s2 = df_fma(s2, Ei[(j + 2) * k + c], h[j + 2]);
-          s3 = df_fma(s3, Mm[(j + 2) * k + c], g[j + 2]);
-        }
-      }
-    } else if (which == 2 && reproj) {
-      for (int j = par; j < k; j += 4) {
-        s0 = df_fma(s0, Ei[j * k + c], hp[j]);
-        if (j + 2 < k) s2 = df_fma(s2, Ei[(j + 2) * k + c], hp[j + 2]);
-      }
-    }
-    s0 = df_add(s0, s2);
-    s1 = df_add(s1, s3);
-    s0 = df_add(s0, df_shfl_xor(s0, 1));
-    s1 = df_add(s1, df_shfl_xor(s1, 1));
-    if (act && par == 0) {
-      if (which == 0) {
-        gam[c] = df_to_double(s0);
-        const df hm2 = {-2.f * h[c].hi, -2.f * h[c].lo};  // exact scaling
-        sterm[c] = df_mul(s0, df_add(s1, hm2));
-      } else if (which == 1) {
-        av[c] = df_to_double(s0) - df_to_double(s1);
-      } else {
-        bv[c] = df_to_double(s0);
-      }
-    }
-  }
-  __syncthreads();
+  // Warp 0: gamma_c = (E^{-1} g)_c, u_c = (N g)_c and the correction
+  // gamma^T (u - 2 h) to rho', one lane per output (even and odd j in
+  // separate sums), then straight on to the scalar tail. Warps 1..: a_c and
+  // b_c, two lanes per output (warp-uniform trip count for the pair
+  // shuffles). One block barrier afterwards.
   if (warp == 0) {
     df corr = {0.f, 0.f};
-    for (int c = lane; c < k; c += 32) corr = df_add(corr, sterm[c]);
+    for (int c = lane; c < k; c += 32) {
+      df s0 = {0.f, 0.f}, s1 = {0.f, 0.f}, s2 = {0.f, 0.f}, s3 = {0.f, 0.f};
+      for (int j = 0; j < k; j += 2) {
+        s0 = df_fma(s0, Ei[j * k + c], g[j]);
+        s1 = df_fma(s1, Nt[j * k + c], g[j]);
+        if (j + 1 < k) {
+          s2 = df_fma(s2, Ei[(j + 1) * k + c], g[j + 1]);
+          s3 = df_fma(s3, Nt[(j + 1) * k + c], g[j + 1]);
+        }
+      }
+      s0 = df_add(s0, s2);
+      s1 = df_add(s1, s3);
+      gam[c] = df_to_double(s0);
+      const df hm2 = {-2.f * h[c].hi, -2.f * h[c].lo};  // exact scaling
+      corr = df_add(corr, df_mul(s0, df_add(s1, hm2)));
+    }
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) corr = df_add(corr, df_shfl_xor(corr, m));
     if (lane == 0) {
@@ -676,6 +644,37 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
         }
         if (hd.chk) cudaGraphSetConditional(hd.chk, mode != 0 ? 1 : 0);
         if (done && hd.loop) cudaGraphSetConditional(hd.loop, 0);
+      }
+    }
+  } else {
+    for (int ob = (warp - 1) * 32; ob < 4 * k; ob += (IT_WARPS - 1) * 32) {
+      const int o2 = ob + lane;
+      const bool act = o2 < 4 * k;
+      const int o = o2 >> 1, par = o2 & 1;
+      const int which = act ? o / k : 2, c = act ? o - which * k : 0;
+      df s0 = {0.f, 0.f}, s1 = {0.f, 0.f}, s2 = {0.f, 0.f}, s3 = {0.f, 0.f};
+      if (which == 0) {
+        for (int j = par; j < k; j += 4) {
+          s0 = df_fma(s0, Ei[j * k + c], h[j]);
+          s1 = df_fma(s1, Mm[j * k + c], g[j]);
+          if (j + 2 < k) {
+            s2 = df_fma(s2, Ei[(j + 2) * k + c], h[j + 2]);
+            s3 = df_fma(s3, Mm[(j + 2) * k + c], g[j + 2]);
+          }
+        }
+      } else if (which == 1 && reproj) {
+        for (int j = par; j < k; j += 4) {
+          s0 = df_fma(s0, Ei[j * k + c], hp[j]);
+          if (j + 2 < k) s2 = df_fma(s2, Ei[(j + 2) * k + c], hp[j + 2]);
+        }
+      }
+      s0 = df_add(s0, s2);
+      s1 = df_add(s1, s3);
+      s0 = df_add(s0, df_shfl_xor(s0, 1));
+      s1 = df_add(s1, df_shfl_xor(s1, 1));
+      if (act && par == 0) {
+        if (which == 0) av[c] = df_to_double(s0) - df_to_double(s1);
+        else bv[c] = df_to_double(s0);
       }
     }
   }
