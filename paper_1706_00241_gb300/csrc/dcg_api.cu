@@ -2,9 +2,9 @@
 //
 // A context owns its device workspace and a CUDA graph of one whole solve of
 // Algorithm 1: the start-of-solve product and E = W^T A W, lines 3-4, then a
-// device-side WHILE node over the iteration (operator, phase 1, an IF node for
-// the true-residual check / refinement, phase 2), an IF node for the final true
-// residual, and the finishing kernel. The graph is built once per operator and
+// device-side WHILE node over the iteration (operator, the fused iteration
+// kernel, an IF node for the true-residual check / refinement and line 12), an
+// IF node for the final true residual, and the finishing kernel. The graph is built once per operator and
 // replayed for every solve; kernels read the per-solve values (k, warm start,
 // tolerances) from the device state, so nothing is re-captured between solves.
 #include <algorithm>

@@ -13,7 +13,7 @@ namespace dcg {
 
 constexpr int kMaxK = 96;         // deflation vectors (columns of W)
 constexpr int kMaxEll = 128;      // stored directions
-constexpr int kMaxM = kMaxK + kMaxEll;  // 224: the float32 Jacobi matrix fits in 200 KB of shared memory
+constexpr int kMaxM = kMaxK + kMaxEll;  // 224: the float32 m x m reduced pencil fits in 200 KB of shared memory
 constexpr int kMaxBlockCols = 129;  // columns of one multi-vector product
 constexpr int kReduceSlots = 3 * kMaxK + 8;  // per-CTA partial sums of one reduction
 constexpr long long kSpinLimit = 1ll << 22;  // bounded waits: polls before giving up

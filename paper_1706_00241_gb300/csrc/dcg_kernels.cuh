@@ -217,7 +217,7 @@ struct RitzArgs {
   double* F;        // m x m
   double* G;
   double* part;     // gram partials
-  float* Vj;        // m x m Jacobi eigenvectors (float32)
+  float* Vj;        // m x m eigenvector rows (float32) when they do not fit in shared memory
   double* Vd;       // m x m float64 scratch
   double* Vd2;      // m x m float64 scratch
   double* theta;    // m, descending

@@ -153,7 +153,7 @@ cudaError_t launch_check_dots(const Ws& w, int grid, cudaStream_t s) {
 //             |r_0| <= tol |b|;
 //   pre_loop: after a failed initial check only rho is refreshed;
 //   in loop:  beta = rho_rec / rho from the recursion's own |r_{j+1}|^2
-//             (st->rho_new, written by phase 1), rho = |r_true|^2 after the
+//             (st->rho_new, written by the fused iteration kernel), rho = |r_true|^2 after the
 //             replacement, and mu = E^{-1}(h + beta hp), which re-projects
 //             p_{j+1} against W (R13: keep beta, recompute rho). Where the
 //             true residual sits far above the recursive one (an inexact
@@ -776,7 +776,8 @@ cudaError_t launch_iter_fused(const Ws& w, int num_sms, Handles h, cudaStream_t 
 
 // ---------------------------------------------------------------------------
 // E^{-1} = Linv^T Linv, N = G_W E^{-1}, M = E^{-1} N (float64, k x k, once
-// per solve): the small matrices phase 1 applies every iteration. One CTA per
+// per solve): the small matrices the fused iteration kernel applies every
+// iteration (as float pairs, staged in its shared memory). One CTA per
 // output row, one thread per column.
 // ---------------------------------------------------------------------------
 __global__ void k_small_prods(Ws w, int which) {
