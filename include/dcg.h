@@ -135,7 +135,9 @@ const char* dcg_last_error(const dcg_ctx* ctx);
  * (k_active = 0), so the first solve is plain CG (Fig. 1 caption).
  * Errors: INVALID_ARG (n < 1, k < 0, ell < 0, k > n, ell > n, max_iter < 1,
  * tol <= 0, k > 0 with ell + k < k, reserved nonzero), NOMEM, CUDA,
- * UNSUPPORTED (k > 128 or ell > 256: limits of the small dense kernels). */
+ * UNSUPPORTED (k > 96 or ell > 128: limits of the small dense kernels; or n
+ * above what the fused iteration kernel covers with one CTA per SM, 32 passes
+ * of 128 rows per CTA: 622592 on a 152-SM GB300). */
 dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** out);
 
 /* Frees everything the context owns. NULL is allowed. Synchronizes its stream. */

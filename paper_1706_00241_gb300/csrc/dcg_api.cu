@@ -202,7 +202,7 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   if (g.select != DCG_SELECT_LARGEST && g.select != DCG_SELECT_SMALLEST)
     return fail(nullptr, DCG_ERR_INVALID_ARG, "bad select");
   if (g.refine_every < 0) return fail(nullptr, DCG_ERR_INVALID_ARG, "refine_every must be >= 0");
-  if (g.k > 96 || g.ell > kMaxEll)
+  if (g.k > kMaxK || g.ell > kMaxEll)
     return fail(nullptr, DCG_ERR_UNSUPPORTED, "k <= 96 and ell <= 128 in this build");
 
   dcg_ctx* c = new dcg_ctx();
