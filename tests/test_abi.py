@@ -72,3 +72,24 @@ def test_create_rejects_bad_config_without_gpu(lib_path):
     cfg.tol = 1e-6
     cfg.k = 200
     assert lib.dcg_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) in (1, 9)
+
+
+def test_create_reports_build_limits_without_gpu(lib_path):
+    # k <= 96 and ell <= 128 in this build (UNSUPPORTED = 9), checked before
+    # any allocation; k > n stays an argument error (INVALID_ARG = 1)
+    from paper_1706_00241_gb300 import _lib
+    lib = _lib.load()
+    cfg = _lib.DcgConfig()
+    cfg.n = 1000
+    cfg.max_iter = 10
+    cfg.tol = 1e-6
+    cfg.window = 1
+    ctx = ctypes.c_void_p()
+    cfg.k, cfg.ell = 97, 32
+    assert lib.dcg_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) == 9
+    assert b"k <= 96" in lib.dcg_last_error(None)
+    cfg.k, cfg.ell = 32, 129
+    assert lib.dcg_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) == 9
+    cfg.n, cfg.k, cfg.ell = 20, 21, 4
+    assert lib.dcg_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) == 1
+    assert not ctx.value
