@@ -60,6 +60,7 @@ struct dcg_ctx {
   float* vcol = nullptr;     // n_pad
   RbfParams* prm = nullptr;
   float* pmv = nullptr;      // n_pad: padded copy of a caller's p (single-step matvec)
+  float* pmvb = nullptr;     // rbf_block_nc() x n_pad: padded W columns of one multi-column pass
   double rbf_l = 0.0, rbf_s2 = 0.0, rbf_noise = 0.0;  // current hyperparameters (host copy)
   double* dth_partials = nullptr;  // derivative forms: 3 * kMaxDthetaPairs per CTA
   double* dth_out = nullptr;       // 3 * kMaxDthetaPairs
@@ -347,6 +348,7 @@ extern "C" dcg_status dcg_set_operator_rbf(dcg_ctx* c, const float* X, int32_t d
     CK(dalloc(c, &c->vcol, size_t(n_pad)));
     CK(dalloc(c, &c->prm, 1));
     CK(dalloc(c, &c->pmv, size_t(n_pad)));
+    CK(dalloc(c, &c->pmvb, size_t(rbf_block_nc()) * n_pad));
   }
   CK(launch_rbf_prep(X, n, n_pad, d, xformat, c->Xr, c->Xt, c->nsq, c->stream));
   CK(launch_rbf_params(c->nsq, n, n_pad, l, s2, noise, c->vcol, c->prm, c->stream));
@@ -530,26 +532,28 @@ static cudaError_t op_block(dcg_ctx* c, const float* V, int ncols, float* Y, Dev
   if (c->op == OP_RBF && st) {
     // Start of a solve: AW with the same tensor-core operator the iteration
     // applies, so that the deflation (E, mu, the re-deflation of r) is
-    // consistent with the Krylov recursion; one tile matvec per column.
-    for (int col = 0; col < c->w.kmax; ++col) {
-      cudaError_t e = launch_copy_col(V + int64_t(1 + col) * c->w.n, c->pmv, c->w.n, col, st, s);
+    // consistent with the Krylov recursion; passes of rbf_block_nc() columns,
+    // each entry's exponential formed once per pass.
+    const int nc = rbf_block_nc();
+    for (int col0 = 0; col0 < c->w.kmax; col0 += nc) {
+      cudaError_t e = launch_copy_cols(V + int64_t(1 + col0) * c->w.n, c->pmvb, c->w.n, c->n_pad, col0, nc, st, s);
       if (e != cudaSuccess) return e;
       RbfMvArgs a{};
-      a.p = c->pmv;
+      a.p = c->pmvb;
+      a.ldp = c->n_pad;
       a.vcol = c->vcol;
-      a.q = Y + int64_t(1 + col) * c->w.n;
+      a.q = Y + int64_t(1 + col0) * c->w.n;
+      a.ldq = c->w.n;
+      a.ncols = nc;
       a.n = c->w.n;
       a.n_tiles = c->n_pad / 128;
       a.d = c->rbf_d;
       a.xformat = c->rbf_xformat;
       a.prm = c->prm;
-      a.partials = c->mv_partials;
-      a.ticket = c->mv_ticket;
-      a.result = c->mv_result;
       a.st = st;
       a.skip_if_done = 1;
-      a.col_idx = col;
-      if ((e = launch_rbf_mv(&c->rbf_tmap, a, c->rbf_grid, s)) != cudaSuccess) return e;
+      a.col_idx = col0;
+      if ((e = launch_rbf_mv_block(&c->rbf_tmap, a, c->rbf_grid, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
   }

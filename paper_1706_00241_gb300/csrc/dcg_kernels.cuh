@@ -112,6 +112,9 @@ struct RbfMvArgs {
   DevState* st;
   int skip_if_done;
   int col_idx;         // >= 0: column of W in a start-of-solve product (skipped if >= st->k)
+  int64_t ldp;         // multi-column product: leading dimension of the padded columns in p
+  int64_t ldq;         // multi-column product: leading dimension of q
+  int ncols;           // multi-column product: columns to write
 };
 
 struct RbfExactArgs {
@@ -165,6 +168,10 @@ int rbf_mv_grid(int n_tiles, int num_sms);
 cudaError_t launch_rbf_mv(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s);
 int rbf_exact_grid(int n);
 cudaError_t launch_copy_col(const float* src, float* dst, int n, int col, const DevState* st, cudaStream_t s);
+cudaError_t launch_copy_cols(const float* src, float* dst, int n, int64_t ldd, int col0, int nc, const DevState* st,
+                             cudaStream_t s);
+cudaError_t launch_rbf_mv_block(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s);
+int rbf_block_nc();
 cudaError_t launch_rbf_resid(const RbfExactArgs& a, cudaStream_t s);
 cudaError_t launch_rbf_block(const RbfExactArgs& a, int cmax, cudaStream_t s);
 

@@ -139,14 +139,28 @@ constexpr int MV_EPI_WARPS = 16;            // four per SMSP: latency hiding for
 constexpr int MV_THREADS = (2 + MV_EPI_WARPS) * 32;
 constexpr int MV_TBUF = 4;                    // TMEM accumulator buffers (tiles in flight)
 constexpr int MV_TMEM_COLS = MV_TBUF * MV_TILE;  // all 512 columns: one CTA per SM
-// shared memory: X_I tile, stages of {X_J tile, p_J, v_J}, barriers
-constexpr int MV_STAGE_BYTES = MV_TILE_BYTES + 2 * MV_TILE * 4;
-constexpr size_t MV_SMEM = 1024 + MV_TILE_BYTES + size_t(MV_STAGES) * MV_STAGE_BYTES + 256;
+// shared memory: X_I tile, stages of {X_J tile, the NC vector columns p_J
+// (column-major, 128 floats each), v_J}, barriers; stages 1024-aligned for
+// the swizzled X tiles
+constexpr int MV_BLOCK_NC = 8;  // columns per pass of the multi-column product
+__host__ __device__ constexpr int mv_stage_bytes(int nc) {
+  return (MV_TILE_BYTES + (nc + 1) * MV_TILE * 4 + 1023) / 1024 * 1024;
+}
+__host__ __device__ constexpr size_t mv_smem(int nc) {
+  return 1024 + MV_TILE_BYTES + size_t(MV_STAGES) * mv_stage_bytes(nc) + 256;
+}
+constexpr size_t MV_SMEM = mv_smem(1);
 
 size_t rbf_mv_smem_bytes() { return MV_SMEM; }
 
+// NC = 1: q = A p with the fused p^T q. NC > 1 (the start-of-solve product):
+// Y[:, col0 + c] = A V[:, col0 + c] for the NC columns of a group, each
+// entry's exponential formed once and contracted with all NC columns
+// (columns at or beyond k are read but not written).
+template <int NC>
 __global__ void __launch_bounds__(MV_THREADS, 1)
     k_rbf_mv(const __grid_constant__ CUtensorMap tmap, RbfMvArgs a) {
+  constexpr int MV_STAGE_BYTES = mv_stage_bytes(NC);
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* xi_tile = base;                                   // 1024-aligned
@@ -166,6 +180,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
   DevState* st = a.st;
   if (st && a.skip_if_done && st->done) return;
   if (st && a.col_idx >= 0 && a.col_idx >= st->k) return;
+  const int ncw = (st && a.col_idx >= 0) ? min(NC, st->k - a.col_idx) : a.ncols;  // columns written
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = a.n, n_tiles = a.n_tiles;
@@ -213,10 +228,14 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
             break;
           }
           unsigned char* stg = stages + size_t(s) * MV_STAGE_BYTES;
-          mbar_arrive_expect_tx(&full[s], tile_bytes + 2 * MV_TILE * 4);
+          mbar_arrive_expect_tx(&full[s], tile_bytes + (NC + 1) * MV_TILE * 4);
           tma_load_2d(stg, &tmap, &full[s], 0, J * MV_TILE);
-          tc::bulk_load(stg + MV_TILE_BYTES, a.p + size_t(J) * MV_TILE, MV_TILE * 4, &full[s]);
-          tc::bulk_load(stg + MV_TILE_BYTES + MV_TILE * 4, a.vcol + size_t(J) * MV_TILE, MV_TILE * 4, &full[s]);
+#pragma unroll 1
+          for (int c = 0; c < NC; ++c)
+            tc::bulk_load(stg + MV_TILE_BYTES + c * MV_TILE * 4, a.p + size_t(c) * a.ldp + size_t(J) * MV_TILE,
+                          MV_TILE * 4, &full[s]);
+          tc::bulk_load(stg + MV_TILE_BYTES + NC * MV_TILE * 4, a.vcol + size_t(J) * MV_TILE, MV_TILE * 4,
+                        &full[s]);
         }
       }
     }
@@ -264,7 +283,9 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
     for (int rb = blockIdx.x; rb < n_tiles; rb += gridDim.x) {
       const int row = rb * MV_TILE + row_l;
       const float u = l2s + a.vcol[row];        // vcol has n_pad entries
-      float acc = 0.f, comp = 0.f;              // Kahan sum of per-tile partials
+      float acc[NC], comp[NC];                  // Kahan sums of per-tile partials
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] = comp[c] = 0.f;
       bool aborted = false;
       for (int J = 0; J < n_tiles; ++J, ++it) {
         const int s = int(it % MV_STAGES);
@@ -273,7 +294,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
         tc::fence_after_sync();
         const unsigned char* stg = stages + size_t(s) * MV_STAGE_BYTES;
         const float* pj = reinterpret_cast<const float*>(stg + MV_TILE_BYTES) + slice * 32;
-        const float* vj = reinterpret_cast<const float*>(stg + MV_TILE_BYTES + MV_TILE * 4) + slice * 32;
+        const float* vj = reinterpret_cast<const float*>(stg + MV_TILE_BYTES + NC * MV_TILE * 4) + slice * 32;
         float sv[32];
         tc::tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * MV_TILE + slice * 32), sv);
         // the values are in registers: hand the accumulator back to the MMA
@@ -281,35 +302,76 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
         tc::fence_before_sync();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[b]);
-        float pa = 0.f, pb = 0.f, pc = 0.f, pd = 0.f;
+        if constexpr (NC == 1) {
+          float pa = 0.f, pb = 0.f, pc = 0.f, pd = 0.f;
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-          const float4 p4 = *reinterpret_cast<const float4*>(pj + j);
-          const float4 v4 = *reinterpret_cast<const float4*>(vj + j);
-          pa = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 0], u + v4.x)), p4.x, pa);
-          pb = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 1], u + v4.y)), p4.y, pb);
-          pc = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 2], u + v4.z)), p4.z, pc);
-          pd = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 3], u + v4.w)), p4.w, pd);
+          for (int j = 0; j < 32; j += 4) {
+            const float4 p4 = *reinterpret_cast<const float4*>(pj + j);
+            const float4 v4 = *reinterpret_cast<const float4*>(vj + j);
+            pa = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 0], u + v4.x)), p4.x, pa);
+            pb = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 1], u + v4.y)), p4.y, pb);
+            pc = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 2], u + v4.z)), p4.z, pc);
+            pd = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 3], u + v4.w)), p4.w, pd);
+          }
+          const float part = (pa + pb) + (pc + pd);
+          const float y = part - comp[0];
+          const float t = acc[0] + y;
+          comp[0] = (t - acc[0]) - y;
+          acc[0] = t;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; j += 4) {  // the entries, once
+            const float4 v4 = *reinterpret_cast<const float4*>(vj + j);
+            sv[j + 0] = tc::ex2_approx(fmaf(c2, sv[j + 0], u + v4.x));
+            sv[j + 1] = tc::ex2_approx(fmaf(c2, sv[j + 1], u + v4.y));
+            sv[j + 2] = tc::ex2_approx(fmaf(c2, sv[j + 2], u + v4.z));
+            sv[j + 3] = tc::ex2_approx(fmaf(c2, sv[j + 3], u + v4.w));
+          }
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {  // contracted with every column
+            const float* pc = pj + c * MV_TILE;
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+              const float4 pa4 = *reinterpret_cast<const float4*>(pc + j);
+              const float4 pb4 = *reinterpret_cast<const float4*>(pc + j + 4);
+              s0 = fmaf(sv[j + 0], pa4.x, s0);
+              s1 = fmaf(sv[j + 1], pa4.y, s1);
+              s0 = fmaf(sv[j + 2], pa4.z, s0);
+              s1 = fmaf(sv[j + 3], pa4.w, s1);
+              s0 = fmaf(sv[j + 4], pb4.x, s0);
+              s1 = fmaf(sv[j + 5], pb4.y, s1);
+              s0 = fmaf(sv[j + 6], pb4.z, s0);
+              s1 = fmaf(sv[j + 7], pb4.w, s1);
+            }
+            const float y = (s0 + s1) - comp[c];
+            const float t = acc[c] + y;
+            comp[c] = (t - acc[c]) - y;
+            acc[c] = t;
+          }
         }
-        const float part = (pa + pb) + (pc + pd);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
-        const float y = part - comp;
-        const float t = acc + y;
-        comp = (t - acc) - y;
-        acc = t;
       }
       if (aborted) break;
       // combine the four column slices of each row (named barrier: epilogue warps)
-      if (slice > 0) s_slice[slice - 1][row_l] = acc;
-      asm volatile("bar.sync 1, %0;" ::"r"(MV_EPI_WARPS * 32));
-      if (slice == 0 && row < n) {
-        const float pi = a.p[row];
-        const float q = acc + ((s_slice[0][row_l] + s_slice[1][row_l]) + s_slice[2][row_l]) + noise * pi;
-        a.q[row] = q;
-        my_part += double(pi) * double(q);
+#pragma unroll 1
+      for (int c = 0; c < NC; ++c) {
+        if (slice > 0) s_slice[slice - 1][row_l] = acc[c];
+        asm volatile("bar.sync 1, %0;" ::"r"(MV_EPI_WARPS * 32));
+        if (slice == 0 && row < n) {
+          const float tot = acc[c] + ((s_slice[0][row_l] + s_slice[1][row_l]) + s_slice[2][row_l]);
+          if constexpr (NC == 1) {
+            const float pi = a.p[row];
+            const float q = tot + noise * pi;
+            a.q[row] = q;
+            my_part += double(pi) * double(q);
+          } else {
+            if (c < ncw) a.q[int64_t(c) * a.ldq + row] = tot + noise * a.p[int64_t(c) * a.ldp + row];
+          }
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(MV_EPI_WARPS * 32));
       }
-      asm volatile("bar.sync 1, %0;" ::"r"(MV_EPI_WARPS * 32));
     }
   }
   tc::fence_before_sync();
@@ -323,6 +385,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
     st->timeout_site = 3;
     st->done = 1;
   }
+  if constexpr (NC > 1) return;
   // p^T q: CTA partial, then the last CTA sums in a fixed order
   if (warp >= 2) {
     const double v = warp_sum(my_part);
@@ -344,7 +407,10 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
 }
 
 cudaError_t rbf_mv_configure() {
-  return cudaFuncSetAttribute(k_rbf_mv, cudaFuncAttributeMaxDynamicSharedMemorySize, int(MV_SMEM));
+  cudaError_t e = cudaFuncSetAttribute(k_rbf_mv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(MV_SMEM));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_rbf_mv<MV_BLOCK_NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(mv_smem(MV_BLOCK_NC)));
 }
 
 // Persistent grid, one CTA per SM: each CTA holds all 512 TMEM columns (four
@@ -352,7 +418,42 @@ cudaError_t rbf_mv_configure() {
 int rbf_mv_grid(int n_tiles, int num_sms) { return n_tiles < num_sms ? n_tiles : num_sms; }
 
 cudaError_t launch_rbf_mv(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s) {
-  k_rbf_mv<<<grid, MV_THREADS, MV_SMEM, s>>>(*tmap, a);
+  k_rbf_mv<1><<<grid, MV_THREADS, MV_SMEM, s>>>(*tmap, a);
+  return cudaGetLastError();
+}
+
+int rbf_block_nc() { return MV_BLOCK_NC; }
+
+// One pass of the multi-column product over columns col0 .. col0 + NC - 1:
+// a.p = NC padded columns (leading dimension a.ldp = n_pad, zero beyond n),
+// a.q = the first output column (leading dimension a.ldq), a.ncols = columns
+// to write (a.col_idx = col0 with a solver state: the pass is skipped when
+// col0 >= k, and columns at or beyond k are not written).
+cudaError_t launch_rbf_mv_block(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s) {
+  k_rbf_mv<MV_BLOCK_NC><<<grid, MV_THREADS, mv_smem(MV_BLOCK_NC), s>>>(*tmap, a);
+  return cudaGetLastError();
+}
+
+// dst[c * ldd + i] = src[c * n + i] for i < n and the columns col0 + c < k
+// (all NC columns without a solver state); the tails beyond n are left as
+// they are (zero in the caller's padded buffer).
+__global__ void k_copy_cols(const float* src, float* dst, int n, int64_t ldd, int col0, int nc, const DevState* st) {
+  int kv = nc;
+  if (st) {
+    if (st->done) return;
+    kv = min(nc, st->k - col0);
+  }
+  const int64_t total = int64_t(kv) * n;
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(idx / n), i = int(idx - int64_t(c) * n);
+    dst[c * ldd + i] = src[int64_t(c) * n + i];
+  }
+}
+
+cudaError_t launch_copy_cols(const float* src, float* dst, int n, int64_t ldd, int col0, int nc, const DevState* st,
+                             cudaStream_t s) {
+  k_copy_cols<<<256, 256, 0, s>>>(src, dst, n, ldd, col0, nc, st);
   return cudaGetLastError();
 }
 
