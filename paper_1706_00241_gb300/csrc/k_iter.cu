@@ -552,15 +552,22 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
         const int b = lane + 32 * i;
         ld[u][i] = (b < G && v0 + u < count) ? __ldcg(partf + int64_t(v0 + u) * G + b) : 0.f;
       }
+    // the values' sums advance level by level together (independent chains
+    // interleave instead of running one value after another)
+    df sv[IT_RED_U];
 #pragma unroll
-    for (int u = 0; u < IT_RED_U; ++u) {
-      df sv = {0.f, 0.f};
+    for (int u = 0; u < IT_RED_U; ++u) sv[u] = df{ld[u][0], 0.f};
 #pragma unroll
-      for (int i = 0; i < IT_MAX_GRID / 32; ++i) sv = df_add(sv, df{ld[u][i], 0.f});
+    for (int i = 1; i < IT_MAX_GRID / 32; ++i)
 #pragma unroll
-      for (int m = 16; m >= 1; m >>= 1) sv = df_add(sv, df_shfl_xor(sv, m));
-      if (lane == 0 && v0 + u < count) sred[v0 + u] = sv;
-    }
+      for (int u = 0; u < IT_RED_U; ++u) sv[u] = df_add(sv[u], df{ld[u][i], 0.f});
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1)
+#pragma unroll
+      for (int u = 0; u < IT_RED_U; ++u) sv[u] = df_add(sv[u], df_shfl_xor(sv[u], m));
+#pragma unroll
+    for (int u = 0; u < IT_RED_U; ++u)
+      if (lane == 0 && v0 + u < count) sred[v0 + u] = sv[u];
   }
   __syncthreads();
   const df* h = sred + 1;
