@@ -162,12 +162,10 @@ cudaError_t launch_rbf_params(const float* nsq, int n, int n_pad, double l, doub
                               RbfParams* prm, cudaStream_t s);
 bool make_rbf_tmap(CUtensorMap* map, const void* Xt, int n_pad, int xformat, int d, EncodeTiledFn encode);
 __host__ __device__ int rbf_row_bytes(int xformat, int d);
-size_t rbf_mv_smem_bytes();
 cudaError_t rbf_mv_configure();
 int rbf_mv_grid(int n_tiles, int num_sms);
 cudaError_t launch_rbf_mv(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s);
 int rbf_exact_grid(int n);
-cudaError_t launch_copy_col(const float* src, float* dst, int n, int col, const DevState* st, cudaStream_t s);
 cudaError_t launch_copy_cols(const float* src, float* dst, int n, int64_t ldd, int col0, int nc, const DevState* st,
                              cudaStream_t s);
 cudaError_t launch_rbf_mv_block(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s);
@@ -176,7 +174,6 @@ cudaError_t launch_rbf_resid(const RbfExactArgs& a, cudaStream_t s);
 cudaError_t launch_rbf_block(const RbfExactArgs& a, int cmax, cudaStream_t s);
 
 // ---- dense operator (k_dense.cu)
-size_t rowop_smem_bytes();
 cudaError_t rowop_configure();
 int rowop_grid(int n, int num_sms);
 bool make_rowop_tmap(CUtensorMap* map, const float* A, int64_t n, int64_t lda, EncodeTiledFn encode);

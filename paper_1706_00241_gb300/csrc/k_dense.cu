@@ -27,8 +27,6 @@ constexpr int RB_CONSUMER_WARPS = 8;            // one warp per box
 constexpr int RB_THREADS = (RB_CONSUMER_WARPS + 1) * 32;
 constexpr size_t RB_SMEM = size_t(RB_STAGES) * RB_STAGE_BYTES + 2 * RB_STAGES * sizeof(uint64_t) + 1024;
 
-size_t rowop_smem_bytes() { return RB_SMEM; }
-
 __device__ __forceinline__ void record_timeout(DevState* st, int site) {
   if (st) {
     st->status = DCG_ERR_TIMEOUT;

@@ -151,8 +151,6 @@ __host__ __device__ constexpr size_t mv_smem(int nc) {
 }
 constexpr size_t MV_SMEM = mv_smem(1);
 
-size_t rbf_mv_smem_bytes() { return MV_SMEM; }
-
 // NC = 1: q = A p with the fused p^T q. NC > 1 (the start-of-solve product):
 // Y[:, col0 + c] = A V[:, col0 + c] for the NC columns of a group, each
 // entry's exponential formed once and contracted with all NC columns
@@ -839,16 +837,6 @@ int rbf_exact_grid(int n) { return (n + EX_ROWS - 1) / EX_ROWS; }
 
 // dst[0, n) = src[0, n) for a column of W that is active in this solve; the
 // tail of dst (up to the 128-row tile) stays zero.
-__global__ void k_copy_col(const float* src, float* dst, int n, int col, const DevState* st) {
-  if (st && (st->done || col >= st->k)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
-}
-
-cudaError_t launch_copy_col(const float* src, float* dst, int n, int col, const DevState* st, cudaStream_t s) {
-  k_copy_col<<<(n + 1023) / 1024, 256, 0, s>>>(src, dst, n, col, st);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_rbf_resid(const RbfExactArgs& a, cudaStream_t s) {
   k_rbf_exact<0><<<rbf_exact_grid(a.n), EX_ROWS, 0, s>>>(a);
   return cudaGetLastError();
