@@ -93,7 +93,7 @@ def test_matvec_matches_oracle(dcg, n):
 
 
 def test_matvec_full_size_sampled_rows(dcg):
-    # BASELINE size 16384 in the bench launch configuration; rows sampled so the
+    # The stored workload at n = 16384 in the bench launch configuration; rows sampled so the
     # float64 reference is cheap.
     cfg = S.DENSE_16384
     X, bs = S.draw_sequence(cfg, T=1)
