@@ -211,7 +211,10 @@ dcg_status dcg_form_rbf_dense(const float* X, int64_t n, int32_t d, double lengt
  *        ~ eps32 |A| |x| / |b|, which exceeds 1e-6 on ill-conditioned systems.
  *   info host, may be NULL.
  * Steps (all on the device, one host synchronisation at the end):
- *   A W in one pass; r_{-1} = b - A x_{-1} (warm start only); E = W^T (AW) in
+ *   A W (stored operator: one pass over A; matrix-free: one pass per 8
+ *   columns of W, with the tensor-core entries of the loop's matvec, so that
+ *   the deflation matches the iteration's operator); r_{-1} = b - A x_{-1}
+ *   (warm start only); E = W^T (AW) in
  *   float64 and its Cholesky factor; x_0 = x_{-1} + W E^{-1} W^T r_{-1}
  *   (line 3); p_0 = r_0 - W mu_0 (line 4); then the loop of lines 5-14 as a
  *   CUDA graph with a device-side while node. Stops when |r_j| <= tol |b|,
@@ -272,8 +275,9 @@ dcg_status dcg_get_history(dcg_ctx* ctx, double* relres, int32_t cap, int32_t* c
  * Errors: STATE (no operator), INVALID_ARG, CUDA. */
 dcg_status dcg_matvec(dcg_ctx* ctx, const float* p, float* q, double* pAp);
 
-/* Multi-vector product Y = A V in one pass over the operator (the start-of-
- * solve product of Algorithm 1 line 3 with AW).
+/* Multi-vector product Y = A V (the start-of-solve product of Algorithm 1
+ * line 3 with AW): one pass over a stored A; for the matrix-free operator the
+ * exact-form entries (as in its true residual), one pass per 16 columns.
  *   V device, column-major n x c; Y device, column-major n x c; 1 <= c <= 129. */
 dcg_status dcg_apply_block(dcg_ctx* ctx, const float* V, int32_t c, float* Y);
 
