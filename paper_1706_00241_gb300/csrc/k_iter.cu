@@ -330,13 +330,15 @@ constexpr int IT_RED_U = 13;              // partial sums each warp reduces per 
 //      (first half); then per-CTA partials of h = (AW)^T r, g = W^T r
 //      [, hp = (AW)^T p] (each half its 16 columns, warp transpose sums);
 //   grid barrier;
-//   B. every CTA reduces all partials in the same fixed order and forms
+//   B. every CTA reduces all partials in the same fixed order (the values of
+//      a warp step through the shuffle tree together) and forms
 //      gamma = E^{-1} g, a = E^{-1} h - M g, b = E^{-1} hp and u = N g (E^{-1}
 //      and M symmetric, N read through its transpose, so every read is
-//      coalesced; two threads per output, half of the sum each); then the
-//      re-deflated rho', the mode (convergence check, periodic replacement, or
-//      neither) and beta. CTA 0 alone writes the solver state and the IF-node
-//      value of the check branch;
+//      coalesced): warp 0 takes gamma, u and the correction gamma^T (u - 2 h)
+//      to rho', one lane per output, then the mode (convergence check,
+//      periodic replacement, or neither) and beta, while the other warps form
+//      a and b with two lanes per output. CTA 0 alone writes the solver state
+//      and the IF-node value of the check branch;
 //   C. if no check follows, every CTA applies line 12 to its rows:
 //      x += W gamma, r -= AW gamma, p = beta p + r - W mu, mu = a + beta b
 //      (each half sums its columns; the second half hands its sums to the
