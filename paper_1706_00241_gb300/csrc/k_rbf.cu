@@ -1,20 +1,23 @@
 // Matrix-free RBF operator A = K + noise I, K_ij = s^2 exp(-|x_i - x_j|^2 / (2 l^2))
 // (the Sec. 3 kernel), never stored.
 //
-//   * k_rbf_mv: q = A p with the fused p^T q (Algorithm 1 line 6). Persistent,
-//     warp-specialised: a TMA warp streams X_J tiles (128 rows x 128 bytes,
-//     128-byte swizzle) with p_J and v_J = -c |x_j|^2 by bulk copies; one
-//     thread issues tcgen05.mma (BF16 or TF32 inputs, float32 accumulation)
-//     for S = X_I X_J^T into one of two TMEM buffers; eight epilogue warps read
+//   * k_rbf_mv<1>: q = A p with the fused p^T q (Algorithm 1 line 6).
+//     Persistent, warp-specialised: a TMA warp streams X_J tiles (128 rows,
+//     swizzled) with p_J and v_J = -c |x_j|^2 by bulk copies; one thread
+//     issues tcgen05.mma (BF16 or TF32 inputs, float32 accumulation) for
+//     S = X_I X_J^T into one of four TMEM buffers; sixteen epilogue warps read
 //     S with tcgen05.ld and accumulate q_i += exp2(u_i + v_j + 2c S_ij) p_j
 //     with the exponential on the SFU (ex2.approx), c = log2(e) / (2 l^2),
 //     u_i = log2(s^2) - c |x_i|^2. Padded columns carry v_j = -inf (K = 0).
+//   * k_rbf_mv<8>: the start-of-solve product A W, eight columns of W per
+//     pass, each entry's exponential formed once and contracted with all
+//     eight (the same entries as the loop's matvec).
 //   * k_rbf_exact: the same operator on CUDA cores in the difference form
 //     sum_m (x_im - x_jm)^2 (float32 pair: exact squares, compensated sum).
 //     For the true residual b - A x the exponential is a float32 pair too
-//     (entries to ~1e-9, compensated Dot2 sums with x = xh + xl) and the
-//     convergence test includes the entry-error bound; the block product A V
-//     uses expf (entries to ~2 ulp).
+//     (entries to ~1e-12 relative; error model below; compensated Dot2 sums
+//     with x = xh + xl) and the convergence test includes the entry-error
+//     bound; the block product A V uses expf (entries to ~2 ulp).
 //     The tensor-core Gram form n_i + n_j - 2 S_ij carries ~1e-5 relative
 //     error on close pairs; the residual recomputation in this exact form is
 //     the refinement that wins the accuracy back.
