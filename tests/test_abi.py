@@ -93,3 +93,38 @@ def test_create_reports_build_limits_without_gpu(lib_path):
     cfg.n, cfg.k, cfg.ell = 20, 21, 4
     assert lib.dcg_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) == 1
     assert not ctx.value
+
+
+def test_header_is_plain_c_and_links(lib_path, tmp_path):
+    # the boundary is a C ABI: a C99 translation unit that includes the header
+    # and references the core calls compiles with gcc and links against the
+    # library (it is not run: no GPU is needed)
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not available")
+    src = tmp_path / "use_dcg.c"
+    src.write_text(
+        '#include "dcg.h"\n'
+        "#include <stddef.h>\n"
+        "int main(void) {\n"
+        "  dcg_config cfg = {0};\n"
+        "  dcg_ctx* ctx = NULL;\n"
+        "  cfg.n = 16; cfg.k = 2; cfg.ell = 4; cfg.max_iter = 10; cfg.tol = 1e-6;\n"
+        "  dcg_status s = dcg_create(&cfg, NULL, &ctx);\n"
+        "  if (s == DCG_OK) {\n"
+        "    dcg_solve_info info;\n"
+        "    (void)dcg_solve(ctx, NULL, NULL, &info);\n"
+        "    (void)dcg_update_subspace(ctx, NULL);\n"
+        "    (void)dcg_destroy(ctx);\n"
+        "  }\n"
+        "  return (int)s;\n"
+        "}\n")
+    exe = tmp_path / "use_dcg"
+    libdir = os.path.dirname(lib_path)
+    libname = os.path.basename(lib_path)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-o", str(exe), os.path.join(libdir, libname), f"-Wl,-rpath,{libdir}"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
