@@ -295,6 +295,38 @@ def test_ritz_keeps_exact_invariant_subspace(dcg):
     assert np.all(Wn[np.arange(6), piv] > 0)
 
 
+def test_ritz_smallest_keeps_exact_invariant_subspace(dcg):
+    # select="smallest" (Sec. 2.3): W spans the 6 smallest eigenvectors, well
+    # separated from a bulk in [1, 4]. Eq. 7 is exact on an invariant subspace
+    # and the directions of P are A-conjugate to it, so the 6 smallest harmonic
+    # Ritz values are those eigenvalues and the new W spans the same space.
+    n = 1024
+    small = np.linspace(0.1, 0.35, 6)
+    eigs = np.concatenate([small, np.linspace(1.0, 4.0, n - 6)])
+    A, Q = S.spd_with_spectrum(eigs, seed=9)
+    A32 = A.astype(np.float32)
+    b = np.random.default_rng(3).standard_normal(n).astype(np.float32)
+    R = np.random.default_rng(4).standard_normal((6, 6))
+    W = (Q[:, :6] @ R).T.astype(np.float32)
+    with dcg.DefCG(n, 6, 12, 1e-6, select="smallest") as s:
+        s.set_operator_dense(dev(A32))
+        s.set_subspace(dev(W))
+        s.solve(dev(b))
+        k_new = s.update_subspace()
+        theta = s.ritz_values()
+        Wn = s.get_subspace().cpu().numpy().astype(np.float64)
+    assert k_new == 6
+    # the values come back descending over all of Z; the selected ones are last
+    np.testing.assert_allclose(np.sort(theta)[:6], small, rtol=1e-4)
+    assert np.sort(theta)[6] > 0.9
+    qn, _ = np.linalg.qr(Wn.T)
+    s_vals = np.linalg.svd(Q[:, :6].T @ qn, compute_uv=False)
+    assert s_vals.min() > 1 - 1e-6
+    np.testing.assert_allclose(np.linalg.norm(Wn, axis=1), 1.0, rtol=1e-5)
+    piv = np.argmax(np.abs(Wn), axis=1)
+    assert np.all(Wn[np.arange(6), piv] > 0)
+
+
 def test_ritz_first_window_matches_oracle(dcg):
     # First system (plain CG) with window FIRST: the first ell directions span
     # a Krylov space on which float32 and float64 agree closely.
