@@ -516,10 +516,16 @@ def tensor_peak(xformat):
 # CPU oracle (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
 def _golden_total_matvecs():
-    g = os.path.join(ROOT, "tests", "golden", "dense_16384_oracle.json")
-    if os.path.exists(g):
-        d = json.load(open(g))
-        return d["total_defcg_matvecs"], "tests/golden/dense_16384_oracle.json"
+    """The oracle's matvec total over the whole sequence, when a stored oracle
+    run of this exact workload exists (written by tests/golden/make_golden.py)."""
+    gdir = os.path.join(ROOT, "tests", "golden")
+    for name in sorted(os.listdir(gdir)) if os.path.isdir(gdir) else []:
+        if not name.endswith("_oracle.json"):
+            continue
+        d = json.load(open(os.path.join(gdir, name)))
+        if (d.get("workload") == CFG.name and d.get("tol") == CFG.tol
+                and "total_defcg_matvecs" in d):
+            return d["total_defcg_matvecs"], f"tests/golden/{name}"
     return None, None
 
 
@@ -583,7 +589,7 @@ def cpu_baseline(samples=2, min_seconds=10.0):
     est, how = extrapolate(solve_s, mv, samples * reps)
     est += CFG.T * smp.form_s
     return {"value": est, "unit": "s/sequence", "cores": _cores(), "kind": "oracle",
-            "sample": f"systems 0..{samples - 1} of the n=16384 sequence, FP64 numpy def-CG + harmonic "
+            "sample": f"systems 0..{samples - 1} of the n={CFG.n} sequence, FP64 numpy def-CG + harmonic "
                       f"Ritz, repeated {reps}x ({solve_s:.2f} s, {mv} matvecs), {how}; plus {CFG.T} x the "
                       f"oracle's formation of one A_t ({smp.form_s:.2f} s)"}
 
@@ -606,7 +612,7 @@ def reference_arm(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": CFG.name, "n": CFG.n, "systems": CFG.T, "k": CFG.k, "ell": CFG.ell},
         "cpu_baseline": {"value": value, "unit": "s/sequence", "cores": _cores(), "kind": "oracle",
-                         "sample": "per step: FP64 numpy def-CG + harmonic Ritz on system 1 of the n=16384 "
+                         "sample": f"per step: FP64 numpy def-CG + harmonic Ritz on system 1 of the n={CFG.n} "
                                    "sequence (W recycled from system 0), " + how
                                    + f"; plus {CFG.T} x the oracle's formation of one A_t ({smp.form_s:.2f} s)"},
         "e2e": {"value": value, "unit": "s/sequence", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
