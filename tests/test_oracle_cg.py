@@ -2,8 +2,8 @@
 
 Each check compares the oracle with something other than itself: a dense
 factorisation, a hand-derived exact run, a property CG must have in exact
-arithmetic (finite termination, W^T r_j = 0, A-conjugacy), or CG on the
-reduced spectrum.
+arithmetic (finite termination, W^T r_j = 0, A-conjugacy, A-norm optimality of
+each iterate over its search space), or CG on the reduced spectrum.
 """
 
 import numpy as np
@@ -113,6 +113,66 @@ def test_defcg_residuals_orthogonal_to_W_and_directions_conjugate():
     for j in range(min(len(P) - 1, 12)):
         c = P[j] @ (A @ P[j + 1])
         assert abs(c) <= 1e-9 * np.sqrt((P[j] @ A @ P[j]) * (P[j + 1] @ A @ P[j + 1]))
+
+
+def _a_norm_minimiser(A, b, x0, B):
+    """argmin over x in x0 + span(B) of |x - A^{-1} b|_A, by least squares in
+    the metric of the Cholesky factor (A = L L^T): min |L^T (x0 + B c - x*)|."""
+    L = np.linalg.cholesky(A)
+    xs = sla.cho_solve((L, True), b)
+    c, *_ = np.linalg.lstsq(L.T @ B, L.T @ (xs - x0), rcond=None)
+    return x0 + B @ c
+
+
+@pytest.mark.parametrize("k,warm", [(0, False), (4, False), (4, True)])
+def test_defcg_iterates_minimise_the_a_norm_error(k, warm):
+    # Optimality of deflated CG (Saad, Yeung, Erhel and Guyomarc'h, SIAM J.
+    # Sci. Comput. 21, 2000): the j-th iterate minimises |x - x*|_A over
+    # x_{-1} + span(W) + K_j(H A, H r_0), H = I - W (W^T A W)^{-1} (AW)^T, with
+    # r_0 the residual of the A-norm-best point of x_{-1} + span(W) (Sec. 2.2,
+    # Eq. 5-6). k = 0 is the plain CG statement. The minimiser is computed here
+    # by least squares on an orthonormal basis, not by a recursion.
+    n = 60
+    A, _ = _spd(n, seed=33, hi=30.0)
+    rng = np.random.default_rng(12)
+    b = rng.standard_normal(n)
+    W = rng.standard_normal((n, k)) if k else None
+    x_init = rng.standard_normal(n) if warm else None
+    res = O.defcg(A, b, x_init=x_init, W=W, tol=1e-11, keep_iterates=True)
+    xm1 = np.zeros(n) if x_init is None else x_init
+    if k:
+        x0 = _a_norm_minimiser(A, b, xm1, W)
+        H = np.eye(n) - W @ np.linalg.solve(W.T @ A @ W, (A @ W).T)
+    else:
+        x0 = xm1
+        H = np.eye(n)
+    np.testing.assert_allclose(res.x_history[0], x0, rtol=0, atol=1e-11 * np.linalg.norm(x0))
+    v = H @ (b - A @ x0)
+    kry = []
+    for j in range(1, min(9, len(res.x_history))):
+        kry.append(v / np.linalg.norm(v))
+        v = H @ (A @ kry[-1])
+        Bj, _ = np.linalg.qr(np.column_stack(([W] if k else []) + kry))
+        want = _a_norm_minimiser(A, b, xm1, Bj)
+        got = res.x_history[j]
+        assert np.linalg.norm(got - want) <= 1e-9 * np.linalg.norm(want), j
+
+
+def test_defcg_error_bounded_by_residual_in_the_a_norm():
+    # |x - x*|_A^2 = r^T A^{-1} r <= |r|^2 / lambda_min, and |x*|_A^2 = b^T A^{-1} b
+    # >= |b|^2 / lambda_max, so the relative A-norm error of the returned x is at
+    # most sqrt(kappa) times its relative true residual; the residual meets tol.
+    n, k = 200, 6
+    eigs = np.geomspace(1e-2, 10.0, n)
+    A, Q = S.spd_with_spectrum(eigs, seed=5)
+    b = np.random.default_rng(6).standard_normal(n)
+    res = O.defcg(A, b, W=Q[:, :k], tol=1e-8)
+    xs = np.linalg.solve(A, b)
+    e = res.x - xs
+    rel_a = np.sqrt(e @ A @ e) / np.sqrt(xs @ A @ xs)
+    relres = np.linalg.norm(b - A @ res.x) / np.linalg.norm(b)
+    assert relres <= 1e-8
+    assert rel_a <= np.sqrt(eigs[-1] / eigs[0]) * relres * (1 + 1e-8)
 
 
 def test_defcg_k0_reproduces_cg_bitwise():
