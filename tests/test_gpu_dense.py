@@ -343,7 +343,7 @@ def test_ritz_first_window_matches_oracle(dcg):
     np.testing.assert_allclose(theta, rr.theta, rtol=1e-3)
 
 
-def _sequence_gpu(dcg, cfg, T, tol, deflate=True, refine_every=0, host_loop=False):
+def _sequence_gpu(dcg, cfg, T, tol, deflate=True, refine_every=0, host_loop=False, keep_A=False):
     X, bs = S.draw_sequence(cfg, T=T)
     Xd = dev(X.astype(np.float32))
     n = cfg.n
@@ -359,6 +359,8 @@ def _sequence_gpu(dcg, cfg, T, tol, deflate=True, refine_every=0, host_loop=Fals
                 s.update_subspace()
                 info["theta"] = s.ritz_values()[:8]
             info["x"] = x.cpu().numpy()
+            if keep_A:
+                info["A"] = A.cpu().numpy()
             out.append(info)
     return out
 
@@ -384,6 +386,31 @@ def test_sequence_small_matches_oracle_golden(dcg):
     plain = _sequence_gpu(dcg, cfg, cfg.T, 1e-6, deflate=False)
     for t in range(1, cfg.T):
         assert got[t]["iters"] < plain[t]["iters"]
+
+
+def test_sequence_small_error_against_cholesky(dcg):
+    # Besides following the oracle, each solution of the n = 1024 sequence is
+    # compared with the exact solution x* of the float32 operator the GPU formed
+    # (float64 Cholesky here). The relative residual, formed here in float64,
+    # meets tol and agrees with the library's compensated true residual; the
+    # relative A-norm error is at most sqrt(kappa) times it, since
+    # |e|_A^2 = r^T A^{-1} r <= |r|^2 / lambda_min and |x*|_A^2 >= |b|^2 / lambda_max.
+    import scipy.linalg as sla
+    cfg = S.RBFSequence(**{**S.SMALL_1024.__dict__, "tol": 1e-6})
+    got = _sequence_gpu(dcg, cfg, cfg.T, 1e-6, keep_A=True)
+    _, bs = S.draw_sequence(cfg, T=cfg.T)
+    for t, info in enumerate(got):
+        A = info["A"].astype(np.float64)
+        b = bs[t].astype(np.float32).astype(np.float64)
+        x = np.asarray(info["x"], dtype=np.float64)
+        relres = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+        assert info["status"] == 0 and relres <= 1e-6 * (1 + 1e-6), (t, relres)
+        np.testing.assert_allclose(info["relres_true"], relres, rtol=1e-6)
+        lam = np.linalg.eigvalsh(A)
+        xs = sla.cho_solve(sla.cho_factor(A), b)
+        e = x - xs
+        rel_a = np.sqrt(e @ A @ e) / np.sqrt(xs @ A @ xs)
+        assert rel_a <= np.sqrt(lam[-1] / lam[0]) * relres * (1 + 1e-6), (t, rel_a, lam[-1] / lam[0])
 
 
 def test_sequence_dense_16384_full_size(dcg):
