@@ -9,6 +9,8 @@ Paper: de Roos & Hennig, arXiv 1706.00241.
   * Sec. 2.2, Algorithm 1: Deflated-CG(k, ell)(A, b, x_{-1}, W, (AW), tol).
   * Sec. 2.3, Eq. 7: harmonic projection G u = theta F u with F = (AZ)^T Z,
     G = (AZ)^T (AZ), Z = [W, P_ell]; the next W is Z U for k chosen u.
+  * Sec. 2.3, the equation before Eq. 7: orthogonal (Rayleigh-Ritz) projection
+    Z^T A Z u = theta Z^T Z u, offered as the alternative extraction.
   * Sec. 3: the RBF kernel k(x_i, x_j) = theta^2 exp(-|x_i - x_j|^2 / (2 lambda^2)).
 
 Readings where the paper is silent or ambiguous (each one is also listed in the
@@ -426,16 +428,60 @@ def harmonic_ritz(W, AW, P, Q, k, select="largest"):
                       theta_selected=theta[sel])
 
 
+def rayleigh_ritz(W, AW, P, Q, k, select="largest"):
+    """k Ritz vectors by orthogonal projection onto Z = [W, P_ell] (Sec. 2.3).
+
+    The Galerkin condition Z^T (A - theta I) Z u = 0 gives the pencil
+    Z^T A Z u = theta Z^T Z u (the equation before Eq. 7). Z^T A Z is formed as
+    Z^T [AW, A P_ell] and symmetrised; the pencil is reduced with a factor T of
+    (Z^T Z)^{-1} (T^T Z^T Z T = I, R6 when Z is rank deficient): C = T^T (Z^T A Z) T,
+    C v = theta v, u = T v. Keeps k values per R4 and returns W = Z U scaled
+    per R5. The returned F and G are Z^T Z and Z^T A Z.
+    """
+    cols = [np.asarray(W, dtype=F64)] if W is not None and W.shape[1] else []
+    acols = [np.asarray(AW, dtype=F64)] if AW is not None and AW.shape[1] else []
+    if len(P):
+        cols.append(np.column_stack(P).astype(F64))
+        acols.append(np.column_stack(Q).astype(F64))
+    Z = np.hstack(cols)
+    AZ = np.hstack(acols)
+    M = Z.T @ Z
+    M = 0.5 * (M + M.T)
+    K = Z.T @ AZ
+    K = 0.5 * (K + K.T)
+    T = _whitener(M)
+    C = T.T @ K @ T
+    C = 0.5 * (C + C.T)
+    theta, V = np.linalg.eigh(C)            # ascending
+    U_all = T @ V
+    if select == "largest":
+        order = np.argsort(-theta, kind="stable")
+    elif select == "smallest":
+        order = np.argsort(theta, kind="stable")
+    else:
+        raise ValueError(select)
+    kk = min(k, theta.size)
+    sel = order[:kk]
+    U = U_all[:, sel]
+    Wn = Z @ U
+    Wn = Wn / np.linalg.norm(Wn, axis=0)
+    piv = np.argmax(np.abs(Wn), axis=0)
+    Wn = Wn * np.sign(Wn[piv, np.arange(kk)])
+    return RitzResult(theta=np.sort(theta)[::-1], W=Wn, U=U, F=M, G=K,
+                      theta_selected=theta[sel])
+
+
 # ----------------------------------------------------------------------------
 # A sequence of systems (Eq. 1) with recycling between them (Fig. 1)
 # ----------------------------------------------------------------------------
 
 def run_sequence(operators, rhs, k, ell, tol, window="last", select="largest",
-                 refine_every=0, max_iter=None, deflate=True, W0=None):
+                 refine_every=0, max_iter=None, deflate=True, W0=None, extraction="harmonic"):
     """Solve A_t x_t = b_t in order, carrying W from one system to the next.
 
     The first system runs as plain CG unless ``W0`` is given (Fig. 1 caption);
-    after each solve k new vectors are extracted by ``harmonic_ritz``.
+    after each solve k new vectors are extracted by ``harmonic_ritz`` (Eq. 7),
+    or by ``rayleigh_ritz`` with ``extraction="ritz"``.
     ``deflate=False`` runs plain CG on every system (the Sec. 3 comparison).
     Returns a list of per-system dicts.
     """
@@ -445,7 +491,8 @@ def run_sequence(operators, rhs, k, ell, tol, window="last", select="largest",
         if deflate:
             res = defcg(A, b, W=W, tol=tol, max_iter=max_iter, ell=ell, window=window,
                         refine_every=refine_every)
-            rr = harmonic_ritz(res.W, res.AW, res.P, res.Q, k, select=select)
+            extract = {"harmonic": harmonic_ritz, "ritz": rayleigh_ritz}[extraction]
+            rr = extract(res.W, res.AW, res.P, res.Q, k, select=select)
             W = rr.W
             out.append({"result": res, "ritz": rr})
         else:

@@ -137,3 +137,81 @@ def test_sequence_recycling_saves_iterations():
     for t in range(1, cfg.T):
         assert d[t]["result"].iters < c[t]["result"].iters
         assert d[t]["result"].relres_true <= cfg.tol
+
+
+# ---------------------------------------------------------------------------
+# Orthogonal (Rayleigh-Ritz) extraction: the equation before Eq. 7
+# ---------------------------------------------------------------------------
+
+def test_rayleigh_ritz_galerkin_condition_and_orthonormal_basis():
+    # The definition: every returned pair (theta, v = Z u) leaves a residual
+    # A v - theta v orthogonal to span(Z). And the values are those of the
+    # standard symmetric problem Q^T A Q on an orthonormal basis Q of span(Z).
+    n, k = 90, 4
+    A, _ = S.spd_with_spectrum(np.geomspace(0.5, 80.0, 90), seed=17)
+    Z = np.random.default_rng(5).standard_normal((n, 11))
+    W, AW, P, AP = _split(Z, A, k)
+    rr = O.rayleigh_ritz(W, AW, P, AP, k=6, select="largest")
+    for j in range(6):
+        v = Z @ rr.U[:, j]
+        res = A @ v - rr.theta_selected[j] * v
+        assert np.linalg.norm(Z.T @ res) <= 1e-10 * np.linalg.norm(Z) * np.linalg.norm(A @ v)
+    Qz, _ = np.linalg.qr(Z)
+    ref = np.sort(np.linalg.eigvalsh(Qz.T @ A @ Qz))[::-1]
+    np.testing.assert_allclose(rr.theta, ref, rtol=1e-11)
+    np.testing.assert_allclose(rr.theta_selected, ref[:6], rtol=1e-11)
+    small = O.rayleigh_ritz(W, AW, P, AP, k=3, select="smallest")
+    np.testing.assert_allclose(small.theta_selected, ref[::-1][:3], rtol=1e-11)
+    # Cauchy interlacing: the i-th largest Ritz value lies between the i-th
+    # largest and the (n - m + i)-th largest eigenvalue of A
+    lam = np.sort(np.linalg.eigvalsh(A))[::-1]
+    m = Z.shape[1]
+    for i in range(m):
+        assert lam[n - m + i] * (1 - 1e-12) <= rr.theta[i] <= lam[i] * (1 + 1e-12)
+    for j in range(6):
+        assert abs(np.linalg.norm(rr.W[:, j]) - 1) < 1e-12
+        piv = np.argmax(np.abs(rr.W[:, j]))
+        assert rr.W[piv, j] > 0
+
+
+def test_rayleigh_ritz_on_cg_directions_is_the_lanczos_tridiagonal():
+    # Plain CG from x = 0: p_0 .. p_{j-1} span K_j(A, b), so the Ritz values on
+    # them are the eigenvalues of the Lanczos matrix that CG's own scalars
+    # define (Saad, Iterative Methods for Sparse Linear Systems, Sec. 6.7):
+    # T_ii = 1/alpha_i + beta_{i-1}/alpha_{i-1}, T_{i,i+1} = sqrt(beta_i)/alpha_i.
+    n, j = 120, 9
+    A, _ = S.spd_with_spectrum(np.geomspace(1.0, 40.0, n), seed=23)
+    b = np.random.default_rng(8).standard_normal(n)
+    res = O.defcg(A, b, tol=1e-12, ell=j, window="first")
+    assert len(res.P) == j and res.iters > j
+    al, be = res.alpha[:j], res.beta[:j]
+    T = np.zeros((j, j))
+    for i in range(j):
+        T[i, i] = 1.0 / al[i] + (be[i - 1] / al[i - 1] if i else 0.0)
+        if i + 1 < j:
+            T[i, i + 1] = T[i + 1, i] = math.sqrt(be[i]) / al[i]
+    ref = np.sort(np.linalg.eigvalsh(T))[::-1]
+    rr = O.rayleigh_ritz(None, None, res.P, res.Q, k=3)
+    np.testing.assert_allclose(rr.theta, ref, rtol=1e-9)
+
+
+def test_rayleigh_ritz_invariant_subspace_and_sequence():
+    # On an invariant span(Z) the Ritz values are eigenvalues of A; a recycled
+    # sequence with extraction="ritz" converges on every system.
+    n = 60
+    eigs = np.linspace(1.0, 30.0, n)
+    A, Q = S.spd_with_spectrum(eigs, seed=4)
+    idx = np.array([2, 9, 30, 50, 57, 59])
+    Z = Q[:, idx] @ np.random.default_rng(3).standard_normal((idx.size, idx.size))
+    W, AW, P, AP = _split(Z, A, 2)
+    rr = O.rayleigh_ritz(W, AW, P, AP, k=3)
+    np.testing.assert_allclose(rr.theta, np.sort(eigs[idx])[::-1], rtol=1e-10)
+    for j in range(3):
+        w = rr.W[:, j]
+        assert np.linalg.norm(A @ w - rr.theta_selected[j] * w) <= 1e-9
+    cfg = S.SMALL_1024.scaled(256, T=3)
+    X, bs = S.draw_sequence(cfg, T=3)
+    ops = [O.rbf_gram(X.astype(np.float64), cfg.lengthscale(t), cfg.signal_var, cfg.noise) for t in range(3)]
+    out = O.run_sequence(ops, bs, cfg.k, cfg.ell, 1e-8, extraction="ritz")
+    for o in out:
+        assert o["result"].status == O.STATUS_OK and o["result"].relres_true <= 1e-8
