@@ -58,10 +58,17 @@ typedef enum dcg_window {         /* which directions feed the next W (Alg. 1 l.
   DCG_WINDOW_LAST = 1             /* the final ell directions of the solve        */
 } dcg_window;
 
-typedef enum dcg_select {         /* which harmonic Ritz values are kept (Sec. 2.3) */
+typedef enum dcg_select {         /* which (harmonic) Ritz values are kept (Sec. 2.3) */
   DCG_SELECT_LARGEST = 0,
   DCG_SELECT_SMALLEST = 1
 } dcg_select;
+
+typedef enum dcg_extraction {     /* how the next W is drawn from Z = [W, P] (Sec. 2.3) */
+  DCG_EXTRACT_HARMONIC = 0,       /* harmonic projection, G u = theta F u (Eq. 7)    */
+  DCG_EXTRACT_RITZ = 1            /* orthogonal projection,
+                                     Z^T A Z u = theta Z^T Z u (the equation before
+                                     Eq. 7)                                          */
+} dcg_extraction;
 
 typedef enum dcg_xformat {        /* element format of X for the matrix-free operator */
   DCG_X_FP32 = 0,                 /* X kept in float32: not supported by the
@@ -88,7 +95,8 @@ typedef struct dcg_config {
                            launched from the host with one state read per
                            iteration (slower; for profilers that cannot see
                            kernels inside conditional graphs, and for debugging) */
-  int32_t reserved[6];  /* must be zero                                          */
+  int32_t extraction;   /* dcg_extraction (0 = harmonic, the paper's choice)     */
+  int32_t reserved[5];  /* must be zero                                          */
   double tol;           /* relative residual target |b - A x| <= tol |b|         */
 } dcg_config;
 
@@ -233,7 +241,9 @@ dcg_status dcg_solve(dcg_ctx* ctx, const float* b, double* x, dcg_solve_info* in
  * the pencil to unit diagonal (pivoted Cholesky of F, directions dependent at
  * float32 dropped), keep min(k, cols(Z)) values (largest or smallest per
  * cfg.select), W <- Z U with unit columns whose largest-magnitude entry is
- * positive. Waits for the result on the host.
+ * positive. With cfg.extraction = DCG_EXTRACT_RITZ the pencil is the
+ * orthogonal projection instead: F = Z^T Z, G = Z^T AZ (symmetrised), the
+ * rest unchanged. Waits for the result on the host.
  *   k_new host, may be NULL; receives the new number of columns of W.
  * Errors: STATE (no completed solve since the last update), SUBSPACE_SINGULAR
  * (F not positive definite even after dropping directions), CUDA. */
@@ -250,7 +260,7 @@ dcg_status dcg_update_subspace(dcg_ctx* ctx, int32_t* k_new);
  * since the last update), CUDA (enqueueing failed). */
 dcg_status dcg_update_subspace_async(dcg_ctx* ctx);
 
-/* Harmonic Ritz values of the last update, descending (float64, host).
+/* (Harmonic) Ritz values of the last update, descending (float64, host).
  *   theta host, capacity cap; m host: number of values (cols(Z)). */
 dcg_status dcg_get_ritz_values(dcg_ctx* ctx, double* theta, int32_t cap, int32_t* m);
 

@@ -20,6 +20,7 @@ STATUS_NAMES = {
 }
 WINDOW = {"first": 0, "last": 1}
 SELECT = {"largest": 0, "smallest": 1}
+EXTRACTION = {"harmonic": 0, "ritz": 1}
 XFORMAT = {"fp32": 0, "bf16": 1, "tf32": 2}
 
 
@@ -36,7 +37,8 @@ class DcgConfig(ctypes.Structure):
         ("reproject", ctypes.c_int32),
         ("record_history", ctypes.c_int32),
         ("host_loop", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 6),
+        ("extraction", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
         ("tol", ctypes.c_double),
     ]
 

@@ -183,7 +183,7 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   if (!cfg || !out) return fail(nullptr, DCG_ERR_INVALID_ARG, "cfg and out must not be NULL");
   *out = nullptr;
   const dcg_config& g = *cfg;
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 5; ++i)
     if (g.reserved[i]) return fail(nullptr, DCG_ERR_INVALID_ARG, "reserved fields must be zero");
   if (g.host_loop != 0 && g.host_loop != 1) return fail(nullptr, DCG_ERR_INVALID_ARG, "host_loop must be 0 or 1");
   if (g.n < 1 || g.n > (int64_t(1) << 30)) return fail(nullptr, DCG_ERR_INVALID_ARG, "n out of range");
@@ -202,6 +202,8 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
     return fail(nullptr, DCG_ERR_INVALID_ARG, "bad window");
   if (g.select != DCG_SELECT_LARGEST && g.select != DCG_SELECT_SMALLEST)
     return fail(nullptr, DCG_ERR_INVALID_ARG, "bad select");
+  if (g.extraction != DCG_EXTRACT_HARMONIC && g.extraction != DCG_EXTRACT_RITZ)
+    return fail(nullptr, DCG_ERR_INVALID_ARG, "bad extraction");
   if (g.refine_every < 0) return fail(nullptr, DCG_ERR_INVALID_ARG, "refine_every must be >= 0");
   if (g.k > kMaxK || g.ell > kMaxEll)
     return fail(nullptr, DCG_ERR_UNSUPPORTED, "k <= 96 and ell <= 128 in this build");
@@ -816,6 +818,7 @@ static dcg_status enqueue_update(dcg_ctx* c) {
   a.nstored = ns;
   a.k_want = c->cfg.k;
   a.select = c->cfg.select;
+  a.extraction = c->cfg.extraction;
   a.W = c->w.XW + c->w.n;
   a.AW = c->w.Y + c->w.n;
   a.P = c->w.P;
@@ -849,7 +852,7 @@ static dcg_status finish_update(dcg_ctx* c) {
   CK(cudaStreamSynchronize(c->stream));
   if (c->h_small[2] != DCG_OK) {
     c->m_last = 0;
-    return fail(c, dcg_status(c->h_small[2]), "harmonic Ritz: F not positive definite");
+    return fail(c, dcg_status(c->h_small[2]), "Ritz extraction: F not positive definite");
   }
   c->k_active = c->h_small[0];
   c->m_last = c->h_small[1];

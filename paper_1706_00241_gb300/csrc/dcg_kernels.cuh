@@ -214,12 +214,13 @@ struct RitzArgs {
   int nstored;      // columns of P in Z
   int k_want;
   int select;       // dcg_select
+  int extraction;   // dcg_extraction: which pencil F, G hold
   const float* W;   // n x k_act
   const float* AW;
   const float* P;   // n x nstored
   const float* Q;
-  double* F;        // m x m
-  double* G;
+  double* F;        // m x m: Z^T AZ (harmonic) or Z^T Z (Ritz)
+  double* G;        // m x m: AZ^T AZ (harmonic) or Z^T AZ (Ritz)
   double* part;     // gram partials
   float* Vj;        // m x m eigenvector rows (float32) when they do not fit in shared memory
   double* Vd;       // m x m float64 scratch

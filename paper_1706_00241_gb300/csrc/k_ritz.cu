@@ -1,9 +1,12 @@
 // Small dense kernels:
 //   * Gram products C = A^T B of tall column blocks (E = W^T (AW) for line 3 of
-//     Algorithm 1; F = Z^T (AZ) and G = (AZ)^T (AZ) for Eq. 7), float32
+//     Algorithm 1; F = Z^T (AZ) and G = (AZ)^T (AZ) for Eq. 7, or Z^T Z and
+//     Z^T (AZ) for the orthogonal projection), float32
 //     products summed in float32 over short row runs and in float64 across them.
 //   * Cholesky factor of E and its inverse (float64, one CTA).
-//   * Harmonic Ritz extraction (Sec. 2.3, Eq. 7): diagonal scaling, Cholesky
+//   * Harmonic Ritz extraction (Sec. 2.3, Eq. 7), or the orthogonal
+//     projection Z^T A Z u = theta Z^T Z u (the same pencil solver with
+//     F = Z^T Z, G = Z^T AZ): diagonal scaling, Cholesky
 //     reduction C = L^{-1} G L^{-T}, symmetric eigen-solve of C (Householder
 //     tridiagonalisation, bisection, inverse iteration),
 //     selection of k values (reading R4), U = S L^{-T} V, W = Z U with unit
@@ -985,16 +988,27 @@ cudaError_t launch_ritz(const RitzArgs& a, int num_sms, float* dstW, cudaStream_
   if (m == 0 || k_new == 0) return cudaSuccess;
   GramArgs g{};
   g.n = a.n;
-  // F = Z^T (AZ)
-  g.a1 = a.W; g.ka1 = a.k_act; g.a2 = a.P; g.ka2 = a.nstored;
-  g.b1 = a.AW; g.kb1 = a.k_act; g.b2 = a.Q; g.kb2 = a.nstored;
   g.part = a.part;
-  cudaError_t e = launch_gram(g, m, m, num_sms, a.F, nullptr, s);
-  if (e != cudaSuccess) return e;
-  // G = (AZ)^T (AZ)
-  g.a1 = a.AW; g.ka1 = a.k_act; g.a2 = a.Q; g.ka2 = a.nstored;
-  e = launch_gram(g, m, m, num_sms, a.G, nullptr, s);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if (a.extraction == DCG_EXTRACT_RITZ) {
+    // orthogonal projection: F = Z^T Z, G = Z^T (AZ)
+    g.a1 = a.W; g.ka1 = a.k_act; g.a2 = a.P; g.ka2 = a.nstored;
+    g.b1 = a.W; g.kb1 = a.k_act; g.b2 = a.P; g.kb2 = a.nstored;
+    e = launch_gram(g, m, m, num_sms, a.F, nullptr, s);
+    if (e != cudaSuccess) return e;
+    g.b1 = a.AW; g.b2 = a.Q;
+    e = launch_gram(g, m, m, num_sms, a.G, nullptr, s);
+    if (e != cudaSuccess) return e;
+  } else {
+    // harmonic projection (Eq. 7): F = Z^T (AZ), G = (AZ)^T (AZ)
+    g.a1 = a.W; g.ka1 = a.k_act; g.a2 = a.P; g.ka2 = a.nstored;
+    g.b1 = a.AW; g.kb1 = a.k_act; g.b2 = a.Q; g.kb2 = a.nstored;
+    e = launch_gram(g, m, m, num_sms, a.F, nullptr, s);
+    if (e != cudaSuccess) return e;
+    g.a1 = a.AW; g.a2 = a.Q;
+    e = launch_gram(g, m, m, num_sms, a.G, nullptr, s);
+    if (e != cudaSuccess) return e;
+  }
   k_ritz_eig<<<1, EIG_THREADS, EIG_SMEM_MAX, s>>>(a, m, k_new);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_zu<<<num_sms, 256, size_t(m) * 32 * sizeof(float), s>>>(a, m, k_new);  // k_new is an upper bound; k_zu reads k_out

@@ -36,7 +36,8 @@ class DefCG:
 
     Parameters follow ``dcg_config`` in include/dcg.h: ``window`` is "last" or
     "first" (Algorithm 1 line 13), ``select`` "largest" or "smallest"
-    (Sec. 2.3), ``refine_every`` the residual-replacement period (0 = only the
+    (Sec. 2.3), ``extraction`` "harmonic" (Eq. 7) or "ritz" (the orthogonal
+    projection of Sec. 2.3), ``refine_every`` the residual-replacement period (0 = only the
     final true-residual confirmation). ``reproject`` (default on) takes mu from
     (AW)^T (beta p + r), equal to (AW)^T r in exact arithmetic, which keeps the
     float32 directions A-conjugate to W.
@@ -44,6 +45,7 @@ class DefCG:
 
     def __init__(self, n: int, k: int, ell: int, tol: float, max_iter: int | None = None,
                  window: str = "last", select: str = "largest", refine_every: int = 0,
+                 extraction: str = "harmonic",
                  warm_start: bool = False, reproject: bool = True,
                  record_history: bool = False, host_loop: bool = False, stream=None):
         self.lib = _lib.load()
@@ -54,6 +56,7 @@ class DefCG:
         cfg.ell = self.ell
         cfg.window = _lib.WINDOW[window]
         cfg.select = _lib.SELECT[select]
+        cfg.extraction = _lib.EXTRACTION[extraction]
         cfg.refine_every = int(refine_every)
         cfg.max_iter = int(max_iter if max_iter is not None else 10 * self.n)
         cfg.warm_start = int(bool(warm_start))

@@ -49,8 +49,9 @@ def test_binding_covers_header(lib_path):
 
 def test_config_struct_layout():
     from paper_1706_00241_gb300 import _lib
-    # int64 n, ten int32 fields, int32 reserved[6], then a double: 8 + 64 + 8
+    # int64 n, eleven int32 fields, int32 reserved[5], then a double: 8 + 64 + 8
     assert ctypes.sizeof(_lib.DcgConfig) == 80
+    assert _lib.DcgConfig.extraction.offset == 48
     assert _lib.DcgConfig.tol.offset == 72
     assert ctypes.sizeof(_lib.DcgSolveInfo) == 64
 
@@ -95,6 +96,22 @@ def test_create_reports_build_limits_without_gpu(lib_path):
     assert not ctx.value
 
 
+def test_create_rejects_unknown_extraction_without_gpu(lib_path):
+    from paper_1706_00241_gb300 import _lib
+    lib = _lib.load()
+    cfg = _lib.DcgConfig()
+    cfg.n, cfg.k, cfg.ell, cfg.max_iter, cfg.tol = 100, 4, 8, 10, 1e-6
+    ctx = ctypes.c_void_p()
+    cfg.extraction = 2
+    assert lib.dcg_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) == 1
+    assert b"bad extraction" in lib.dcg_last_error(None)
+    cfg.extraction = 0
+    cfg.reserved[4] = 1
+    assert lib.dcg_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) == 1
+    assert b"reserved" in lib.dcg_last_error(None)
+    assert not ctx.value
+
+
 def test_header_is_plain_c_and_links(lib_path, tmp_path):
     # the boundary is a C ABI: a C99 translation unit that includes the header
     # and references the core calls compiles with gcc and links against the
@@ -108,6 +125,10 @@ def test_header_is_plain_c_and_links(lib_path, tmp_path):
     src.write_text(
         '#include "dcg.h"\n'
         "#include <stddef.h>\n"
+        "/* the ctypes binding's offsets, checked at compile time */\n"
+        "typedef char extraction_at_48[offsetof(dcg_config, extraction) == 48 ? 1 : -1];\n"
+        "typedef char tol_at_72[offsetof(dcg_config, tol) == 72 ? 1 : -1];\n"
+        "typedef char config_is_80[sizeof(dcg_config) == 80 ? 1 : -1];\n"
         "int main(void) {\n"
         "  dcg_config cfg = {0};\n"
         "  dcg_ctx* ctx = NULL;\n"

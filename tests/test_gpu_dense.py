@@ -343,13 +343,98 @@ def test_ritz_first_window_matches_oracle(dcg):
     np.testing.assert_allclose(theta, rr.theta, rtol=1e-3)
 
 
-def _sequence_gpu(dcg, cfg, T, tol, deflate=True, refine_every=0, host_loop=False, keep_A=False):
+def test_rayleigh_ritz_first_window_matches_oracle(dcg):
+    # extraction="ritz" (the orthogonal projection of Sec. 2.3) on the first
+    # ell CG directions: the same float32 Krylov space as the harmonic test
+    # above, so the Ritz values agree with the oracle's to the same 1e-3.
+    n = 2000
+    A32, _, eigs = _spd32(n, 0.5, 200.0, 13)
+    b = np.random.default_rng(4).standard_normal(n).astype(np.float32)
+    with dcg.DefCG(n, 4, 10, 1e-6, window="first", extraction="ritz") as s:
+        s.set_operator_dense(dev(A32))
+        s.solve(dev(b))
+        k_new = s.update_subspace()
+        theta = s.ritz_values()
+        Wn = s.get_subspace().cpu().numpy().astype(np.float64)
+    ref = O.defcg(A32.astype(np.float64), b.astype(np.float64), tol=1e-6, ell=10, window="first")
+    rr = O.rayleigh_ritz(None, None, ref.P, ref.Q, 4)
+    assert k_new == 4
+    np.testing.assert_allclose(theta, rr.theta, rtol=1e-3)
+    # the Ritz vectors are unit and agree with the oracle's up to float32
+    # rounding of the directions (largest values: well separated)
+    np.testing.assert_allclose(np.linalg.norm(Wn, axis=1), 1.0, rtol=1e-5)
+    for j in range(2):
+        assert np.abs(Wn @ rr.W[:, j]).max() > 1 - 1e-3
+
+
+def test_rayleigh_ritz_keeps_exact_invariant_subspace(dcg):
+    # W spans the top-6 eigenvectors. W^T A P = 0 then forces W^T P = 0, so the
+    # orthogonal projection is exact on span(W) and its 6 largest Ritz values
+    # are those eigenvalues; the new W spans the same space.
+    n = 1024
+    eigs = np.concatenate([np.linspace(1.0, 4.0, n - 6), np.geomspace(50.0, 500.0, 6)])
+    A, Q = S.spd_with_spectrum(eigs, seed=8)
+    A32 = A.astype(np.float32)
+    b = np.random.default_rng(1).standard_normal(n).astype(np.float32)
+    R = np.random.default_rng(2).standard_normal((6, 6))
+    W = (Q[:, -6:] @ R).T.astype(np.float32)
+    with dcg.DefCG(n, 6, 12, 1e-6, extraction="ritz") as s:
+        s.set_operator_dense(dev(A32))
+        s.set_subspace(dev(W))
+        s.solve(dev(b))
+        k_new = s.update_subspace()
+        theta = s.ritz_values()
+        Wn = s.get_subspace().cpu().numpy().astype(np.float64)
+    assert k_new == 6
+    np.testing.assert_allclose(theta[:6], np.sort(eigs[-6:])[::-1], rtol=2e-5)
+    assert theta[6] < 4.0 * (1 + 1e-4)
+    qn, _ = np.linalg.qr(Wn.T)
+    s_vals = np.linalg.svd(Q[:, -6:].T @ qn, compute_uv=False)
+    assert s_vals.min() > 1 - 1e-6
+
+
+def test_rayleigh_ritz_sequence_small_matches_oracle(dcg):
+    # The n = 1024 sequence with extraction="ritz" against the float64 oracle
+    # running the same extraction: every solve meets tol, the recycled solves
+    # take fewer iterations than plain CG on the GPU, and the counts follow
+    # the oracle's within the float32 excess measured for the harmonic pencil
+    # on this sequence (8 % .. 26 %): 35 % + 2 per system, 25 % in total.
+    # The top Ritz value is a lower bound on lambda_max (Cauchy interlacing);
+    # from t = 1 on the oracle's sits 0.3 % .. 1.4 % below it, on a window of
+    # directions that the float32 solve does not reproduce, so the GPU's value
+    # is checked against that bound and its distance to lambda_max against
+    # the oracle's (at most twice it, plus 1e-3).
+    cfg = S.RBFSequence(**{**S.SMALL_1024.__dict__, "tol": 1e-6})
+    got = _sequence_gpu(dcg, cfg, cfg.T, 1e-6, extraction="ritz")
+    X, bs = S.draw_sequence(cfg, T=cfg.T)
+    X64 = X.astype(np.float32).astype(np.float64)
+    ops = [O.rbf_gram(X64, cfg.lengthscale(t), cfg.signal_var, cfg.noise) for t in range(cfg.T)]
+    ref = O.run_sequence(ops, [b.astype(np.float64) for b in bs], cfg.k, cfg.ell, 1e-6, extraction="ritz")
+    counts = [(info["iters"], r["result"].iters) for info, r in zip(got, ref)]
+    for (gi, oi), info, r in zip(counts, got, ref):
+        assert info["status"] == 0 and info["relres_true"] <= 1e-6
+        assert abs(gi - oi) <= 2 + 0.35 * oi, counts
+    for t, (info, r) in enumerate(zip(got, ref)):
+        lam_max = np.linalg.eigvalsh(ops[t])[-1]
+        gap_o = (lam_max - r["ritz"].theta[0]) / lam_max
+        th = info["theta"][0]
+        assert th <= lam_max * (1 + 1e-5), (t, th, lam_max)
+        assert (lam_max - th) / lam_max <= 2 * gap_o + 1e-3, (t, th, r["ritz"].theta[0], lam_max)
+    tot_g, tot_o = sum(c[0] for c in counts), sum(c[1] for c in counts)
+    assert abs(tot_g - tot_o) <= 0.25 * tot_o, counts
+    plain = _sequence_gpu(dcg, cfg, cfg.T, 1e-6, deflate=False)
+    for t in range(1, cfg.T):
+        assert got[t]["iters"] < plain[t]["iters"], (t, got[t]["iters"], plain[t]["iters"])
+
+
+def _sequence_gpu(dcg, cfg, T, tol, deflate=True, refine_every=0, host_loop=False, keep_A=False,
+                  extraction="harmonic"):
     X, bs = S.draw_sequence(cfg, T=T)
     Xd = dev(X.astype(np.float32))
     n = cfg.n
     out = []
     with dcg.DefCG(n, cfg.k if deflate else 0, cfg.ell if deflate else 0, tol, refine_every=refine_every,
-                   host_loop=host_loop) as s:
+                   host_loop=host_loop, extraction=extraction) as s:
         A = torch.empty((n, n), dtype=torch.float32, device="cuda")
         for t in range(T):
             dcg.form_rbf_dense(Xd, cfg.lengthscale(t), cfg.signal_var, cfg.noise, out=A)
