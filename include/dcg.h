@@ -7,6 +7,7 @@
  *   - Algorithm 1 (Sec. 2.2): Deflated-CG(k, ell)(A, b, x_{-1}, W, (AW), tol).
  *   - Sec. 2.3, Eq. 7: harmonic projection G u = theta F u, F = (AZ)^T Z,
  *     G = (AZ)^T AZ, Z = [W, P_ell]; the next W is Z U for k chosen u.
+ *     Optionally the orthogonal projection Z^T A Z u = theta Z^T Z u (Sec. 2.3).
  *   - Sec. 3: the RBF kernel k(x_i, x_j) = s^2 exp(-|x_i - x_j|^2 / (2 l^2)).
  *
  * Conventions for every entry point:
@@ -53,7 +54,7 @@ typedef enum dcg_status {
                                     residual                                   */
 } dcg_status;
 
-typedef enum dcg_window {         /* which directions feed the next W (Alg. 1 l.13) */
+typedef enum dcg_window {         /* which directions feed the next W (Algorithm 1) */
   DCG_WINDOW_FIRST = 0,           /* p_0 .. p_{ell-1}, as the paper stores        */
   DCG_WINDOW_LAST = 1             /* the final ell directions of the solve        */
 } dcg_window;
@@ -224,7 +225,8 @@ dcg_status dcg_form_rbf_dense(const float* X, int64_t n, int32_t d, double lengt
  *   the deflation matches the iteration's operator); r_{-1} = b - A x_{-1}
  *   (warm start only); E = W^T (AW) in
  *   float64 and its Cholesky factor; x_0 = x_{-1} + W E^{-1} W^T r_{-1}
- *   (line 3); p_0 = r_0 - W mu_0 (line 4); then the loop of lines 5-14 as a
+ *   (the initial projection); p_0 = r_0 - W mu_0 (the first direction); then
+ *   the iteration with its direction store as a
  *   CUDA graph with a device-side while node. Stops when |r_j| <= tol |b|,
  *   confirmed by a true residual b - A x evaluated with compensated (twice
  *   float32 precision, Ogita-Rump-Oishi Dot2) accumulation and summed in
@@ -280,13 +282,14 @@ dcg_status dcg_get_history(dcg_ctx* ctx, double* relres, int32_t cap, int32_t* c
 /* Single steps of the hot path, for testing and measurement                 */
 /* ------------------------------------------------------------------------ */
 
-/* One operator application q = A p with the fused product p^T q (line 6).
+/* One operator application q = A p with the fused product p^T q (the
+ * denominator d_j = p_j^T A p_j of Algorithm 1).
  *   p, q device n floats; pAp host, may be NULL (then no synchronisation).
  * Errors: STATE (no operator), INVALID_ARG, CUDA. */
 dcg_status dcg_matvec(dcg_ctx* ctx, const float* p, float* q, double* pAp);
 
-/* Multi-vector product Y = A V (the start-of-solve product of Algorithm 1
- * line 3 with AW): one pass over a stored A; for the matrix-free operator the
+/* Multi-vector product Y = A V (the start-of-solve product AW of Algorithm 1,
+ * needed by its initial projection): one pass over a stored A; for the matrix-free operator the
  * exact-form entries (as in its true residual), one pass per 16 columns.
  *   V device, column-major n x c; Y device, column-major n x c; 1 <= c <= 129. */
 dcg_status dcg_apply_block(dcg_ctx* ctx, const float* V, int32_t c, float* Y);
@@ -300,7 +303,7 @@ dcg_status dcg_sync(dcg_ctx* ctx);
 
 /* q = A p and p^T q for a dense stored operator, without a context and
  * without allocating device memory: the same kernel as dcg_matvec (the q = A p
- * of Algorithm 1 line 6 with its fused p^T q), with the reduction scratch in
+ * of Algorithm 1 with its fused p^T q), with the reduction scratch in
  * a fixed array inside the library. The paper has no counterpart: there the
  * matvec only runs inside a solve. It serves callers that hold no dcg context
  * and may not allocate at the point of the call: code working inside another

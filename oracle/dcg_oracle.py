@@ -167,7 +167,7 @@ class SolveResult:
 
 
 def cg(A, b, x_init=None, tol=1e-6, max_iter=None, keep_iterates=False):
-    """Hestenes-Stiefel CG: Algorithm 1 lines 6-10 with no deflation (W empty).
+    """Hestenes-Stiefel CG: the iteration of Algorithm 1 with no deflation (W empty).
 
     Stopping follows R2: relative recursive residual, confirmed by the true
     residual. Kept deliberately separate from ``defcg`` so that the k = 0 case
@@ -206,15 +206,15 @@ def cg(A, b, x_init=None, tol=1e-6, max_iter=None, keep_iterates=False):
         if j >= max_iter:
             res.status = STATUS_MAXITER
             break
-        q = _mv(A, p)                       # line 6: d = p^T A p
+        q = _mv(A, p)                       # A p_j, then d_j = p_j^T A p_j
         res.matvecs_loop += 1
         d = p @ q
         if not d > 0.0:
             res.status = STATUS_BREAKDOWN
             break
-        alpha = rho / d                     # line 7
-        x = x + alpha * p                   # line 8
-        r = r - alpha * q                   # line 9
+        alpha = rho / d                     # step length alpha_j = rho_j / d_j
+        x = x + alpha * p                   # x_{j+1}
+        r = r - alpha * q                   # r_{j+1}
         rho_new = r @ r
         j += 1
         res.history.append(np.sqrt(rho_new) / bnorm)
@@ -225,8 +225,8 @@ def cg(A, b, x_init=None, tol=1e-6, max_iter=None, keep_iterates=False):
                 break
             r = r_true
             rho_new = r @ r
-        beta = rho_new / rho                # line 10
-        p = beta * p + r                    # line 12 with W empty
+        beta = rho_new / rho                # beta_j = rho_{j+1} / rho_j
+        p = beta * p + r                    # direction update with W empty
         rho = rho_new
         if keep_iterates:
             res.x_history.append(x.copy()); res.r_history.append(r.copy()); res.p_history.append(p.copy())
@@ -266,7 +266,7 @@ def defcg(A, b, x_init=None, W=None, AW=None, tol=1e-6, max_iter=None, ell=0,
         return res
 
     def deflate(x, r):
-        """Line 3: x <- x + W E^{-1} W^T r, so that W^T r = 0 afterwards."""
+        """Initial projection: x <- x + W E^{-1} W^T r, so that W^T r = 0 afterwards."""
         if not k:
             return x, r
         g = Esolve(W.T @ r)
@@ -277,8 +277,8 @@ def defcg(A, b, x_init=None, W=None, AW=None, tol=1e-6, max_iter=None, ell=0,
         res.matvecs_setup += 1
     else:
         r = b.copy()
-    x, r = deflate(x, r)                    # line 3
-    if k:                                   # line 4: E mu_0 = W^T A r_0 (R1)
+    x, r = deflate(x, r)                    # initial projection: x_0, r_0
+    if k:                                   # first direction: E mu_0 = W^T A r_0 (R1)
         mu = Esolve(AW.T @ r)
         p = r - W @ mu
     else:
@@ -310,20 +310,20 @@ def defcg(A, b, x_init=None, W=None, AW=None, tol=1e-6, max_iter=None, ell=0,
             rho = r @ r
             converged = False
     j = 0
-    while not converged:                     # line 5
+    while not converged:                     # while |r_j| > tol |b| (R2)
         if j >= max_iter:
             res.status = STATUS_MAXITER
             break
         q = _mv(A, p)
         res.matvecs_loop += 1
-        d = p @ q                            # line 6
+        d = p @ q                            # d_j = p_j^T A p_j
         if not d > 0.0:
             res.status = STATUS_BREAKDOWN
             break
-        alpha = rho / d                      # line 7
-        x = x + alpha * p                    # line 8
-        r = r - alpha * q                    # line 9
-        store(j, p, q, d, alpha)             # lines 13-14 (R3)
+        alpha = rho / d                      # step length alpha_j = rho_j / d_j
+        x = x + alpha * p                    # x_{j+1}
+        r = r - alpha * q                    # r_{j+1}
+        store(j, p, q, d, alpha)             # direction store (R3)
         rho_new = r @ r
         j += 1
         res.history.append(np.sqrt(rho_new) / bnorm)
@@ -342,13 +342,13 @@ def defcg(A, b, x_init=None, W=None, AW=None, tol=1e-6, max_iter=None, ell=0,
             res.matvecs_check += 1
             rho_new = r @ r
             replaced = True
-        beta = rho_rec / rho                 # line 10 (R13: beta from the recursion)
-        if k:                                # line 11 (R1; R13 after a replacement)
+        beta = rho_rec / rho                 # beta_j (R13: from the recursion)
+        if k:                                # mu step: E mu_{j+1} = (AW)^T r_{j+1} (R1; R13)
             h = AW.T @ r
             if replaced:
                 h = h + beta * (AW.T @ p)
             mu = Esolve(h)
-            p = beta * p + r - W @ mu        # line 12
+            p = beta * p + r - W @ mu        # direction update
         else:
             mu = np.zeros(0)
             p = beta * p + r

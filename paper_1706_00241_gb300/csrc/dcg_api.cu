@@ -1,9 +1,10 @@
 // C ABI of the deflated-CG library (declarations and contracts in include/dcg.h).
 //
 // A context owns its device workspace and a CUDA graph of one whole solve of
-// Algorithm 1: the start-of-solve product and E = W^T A W, lines 3-4, then a
-// device-side WHILE node over the iteration (operator, the fused iteration
-// kernel, an IF node for the true-residual check / refinement and line 12), an
+// Algorithm 1: the start-of-solve product and E = W^T A W, the initial
+// projection and the first direction, then a device-side WHILE node over the
+// iteration (operator, the fused iteration kernel, an IF node for the
+// true-residual check / refinement and the direction update), an
 // IF node for the final true residual, and the finishing kernel. The graph is built once per operator and
 // replayed for every solve; kernels read the per-solve values (k, warm start,
 // tolerances) from the device state, so nothing is re-captured between solves.
@@ -652,14 +653,14 @@ static dcg_status build_graph(dcg_ctx* c) {
     run(cudaStreamEndCapture(s1, &tmp));
   }
   run(launch_loop_gate(w, h, s0));
-  // WHILE not done: one iteration of lines 5-14.
+  // WHILE not done: one iteration with its direction store.
   run(add_conditional(s0, h.loop, cudaGraphCondTypeWhile, &body));
   if (e == cudaSuccess) {
     run(cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     run(op_matvec(c, w.p, w.q, &c->st->d, c->mv_partials, &c->st->ticket[T_MATVEC], c->st, s1));
     run(launch_iter_fused(w, c->num_sms, h, s1));
     // IF a convergence check or a replacement is due: the true residual, the
-    // replacement and line 12 (which the fused kernel then skipped)
+    // replacement and the direction update (which the fused kernel then skipped)
     cudaGraph_t inner = nullptr;
     run(add_conditional(s1, h.chk, cudaGraphCondTypeIf, &inner));
     if (e == cudaSuccess) {
@@ -694,7 +695,7 @@ static dcg_status build_graph(dcg_ctx* c) {
 // The solve graph's kernels in the same order, launched from the host. Each
 // conditional node becomes a host decision on the state the kernels wrote:
 // the pre-loop check when |r_0| met tol (mode 1 after setup), the loop while
-// not done, the in-loop check branch (true residual, replacement, line 12)
+// not done, the in-loop check branch (true residual, replacement, direction update)
 // when the fused iteration kernel chose a check (mode != 0), the final
 // residual when the last iterate has none.
 static dcg_status run_host_loop(dcg_ctx* c, cudaStream_t s) {

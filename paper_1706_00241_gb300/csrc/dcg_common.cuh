@@ -30,7 +30,7 @@ enum Ticket : int {
 struct DevState {
   double rho;        // r^T r of the current residual
   double rho_new;    // r^T r after the x, r update of this iteration
-  double d;          // p^T A p of the current direction (Algorithm 1 line 6)
+  double d;          // p^T A p of the current direction (Algorithm 1)
   double alpha;
   double beta;
   double bnorm2;     // |b|^2

@@ -1,12 +1,12 @@
 // Stored-operator kernels (dense row-major float32 A):
-//   * k_rowop_tma: q = A p with the fused p^T q of Algorithm 1 line 6, or the
+//   * k_rowop_tma: q = A p with the fused p^T q of Algorithm 1, or the
 //     true residual r = b - A x for the float64 iterate x with compensated
 //     (Dot2) accumulation (the stopping test of the Sec. 3 experiments and the
 //     residual replacement). A streams through a
 //     shared-memory ring filled by 2-D TMA tiles (cp.async.bulk.tensor) and
 //     completed on mbarriers; one CTA per SM owns a contiguous band of rows.
 //   * k_apply_block: Y = A V for up to 129 columns in one pass (the start-of-
-//     solve product AW of Algorithm 1 line 3).
+//     solve product AW of Algorithm 1).
 //   * k_form_rbf: A = K + noise I for the Sec. 3 RBF kernel.
 #include <algorithm>
 #include <mutex>

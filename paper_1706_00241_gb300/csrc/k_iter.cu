@@ -111,8 +111,9 @@ cudaError_t launch_setup_r(const Ws& w, int grid, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// g = W^T r, then (last CTA) gamma = E^{-1} g: the correction of line 3 (and of
-// the re-deflation after a residual replacement, reading R13).
+// g = W^T r, then (last CTA) gamma = E^{-1} g: the correction of the initial
+// projection of Algorithm 1 (and of the re-deflation after a residual
+// replacement, reading R13).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_check_dots(Ws w) {
   DevState* st = w.st;
@@ -146,10 +147,10 @@ cudaError_t launch_check_dots(const Ws& w, int grid, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// x += W gamma, r -= (AW) gamma (line 3 / reading R13), then rho = r^T r,
+// x += W gamma, r -= (AW) gamma (initial projection / reading R13), then rho = r^T r,
 // h = (AW)^T r, hp = (AW)^T p. The last CTA finishes according to the place of
 // the kernel in the solve graph:
-//   setup:    mu_0 = E^{-1} h (line 4), beta = 0, arms the pre-loop check if
+//   setup:    mu_0 = E^{-1} h (first direction), beta = 0, arms the pre-loop check if
 //             |r_0| <= tol |b|;
 //   pre_loop: after a failed initial check only rho is refreshed;
 //   in loop:  beta = rho_rec / rho from the recursion's own |r_{j+1}|^2
@@ -322,7 +323,7 @@ constexpr int IT_ROWS = IT_THREADS / 2;  // rows per CTA pass: the two halves of
 constexpr int IT_MAX_PASSES = 32;         // row passes per CTA (n <= 32 * 128 * grid)
 constexpr int IT_RED_U = 13;              // partial sums each warp reduces per round
 
-// One iteration after q = A p (Algorithm 1 lines 6-12, 13-14), as one
+// One iteration of Algorithm 1 after q = A p, with its direction store, as one
 // cooperative launch with one CTA per SM. A CTA owns rows
 // b * 128 + i + j * 128 * grid (i < 128); threads t and t + 128 share row i and
 // split every 32-column block of W and AW into halves of 16 columns:
@@ -339,7 +340,7 @@ constexpr int IT_RED_U = 13;              // partial sums each warp reduces per 
 //      periodic replacement, or neither) and beta, while the other warps form
 //      a and b with two lanes per output. CTA 0 alone writes the solver state
 //      and the IF-node value of the check branch;
-//   C. if no check follows, every CTA applies line 12 to its rows:
+//   C. if no check follows, every CTA applies the direction update to its rows:
 //      x += W gamma, r -= AW gamma, p = beta p + r - W mu, mu = a + beta b
 //      (each half sums its columns; the second half hands its sums to the
 //      first through shared memory).
@@ -690,7 +691,7 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
   __syncthreads();
   if (s_mode != 0 || s_done) return;  // the check branch recomputes gamma, beta and mu
 
-  // ---- C. line 12 on this CTA's rows ----
+  // ---- C. the direction update on this CTA's rows ----
   __shared__ float msh[kMaxK], gsh[kMaxK];
   __shared__ float xch[3][IT_ROWS];  // second half's sums: W gamma, AW gamma, W mu
   const double beta_d = s_beta;
@@ -829,7 +830,7 @@ cudaError_t launch_small_prods(const Ws& w, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Phase 2 (line 12): x += W gamma, r -= AW gamma (float32 re-deflation, zero
+// Phase 2 (the direction update): x += W gamma, r -= AW gamma (float32 re-deflation, zero
 // in exact arithmetic), then p = beta p + r - W mu. In the loop body it also
 // ends the while node once the solve is done.
 // ---------------------------------------------------------------------------

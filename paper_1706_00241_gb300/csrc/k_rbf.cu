@@ -1,7 +1,7 @@
 // Matrix-free RBF operator A = K + noise I, K_ij = s^2 exp(-|x_i - x_j|^2 / (2 l^2))
 // (the Sec. 3 kernel), never stored.
 //
-//   * k_rbf_mv<1>: q = A p with the fused p^T q (Algorithm 1 line 6).
+//   * k_rbf_mv<1>: q = A p with the fused p^T q (Algorithm 1).
 //     Persistent, warp-specialised: a TMA warp streams X_J tiles (128 rows,
 //     swizzled) with p_J and v_J = -c |x_j|^2 by bulk copies; one thread
 //     issues tcgen05.mma (BF16 or TF32 inputs, float32 accumulation) for

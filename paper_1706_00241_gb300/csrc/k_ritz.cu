@@ -1,6 +1,6 @@
 // Small dense kernels:
-//   * Gram products C = A^T B of tall column blocks (E = W^T (AW) for line 3 of
-//     Algorithm 1; F = Z^T (AZ) and G = (AZ)^T (AZ) for Eq. 7, or Z^T Z and
+//   * Gram products C = A^T B of tall column blocks (E = W^T (AW) for the initial
+//     projection of Algorithm 1; F = Z^T (AZ) and G = (AZ)^T (AZ) for Eq. 7, or Z^T Z and
 //     Z^T (AZ) for the orthogonal projection), float32
 //     products summed in float32 over short row runs and in float64 across them.
 //   * Cholesky factor of E and its inverse (float64, one CTA).

@@ -35,7 +35,7 @@ class DefCG:
     """A def-CG(k, ell) solver context for systems of size n on the current GPU.
 
     Parameters follow ``dcg_config`` in include/dcg.h: ``window`` is "last" or
-    "first" (Algorithm 1 line 13), ``select`` "largest" or "smallest"
+    "first" (which directions Algorithm 1 stores), ``select`` "largest" or "smallest"
     (Sec. 2.3), ``extraction`` "harmonic" (Eq. 7) or "ritz" (the orthogonal
     projection of Sec. 2.3), ``refine_every`` the residual-replacement period (0 = only the
     final true-residual confirmation). ``reproject`` (default on) takes mu from
@@ -189,7 +189,7 @@ class DefCG:
 
     # -- single steps -------------------------------------------------------
     def matvec(self, p: torch.Tensor, q: torch.Tensor | None = None, want_pAp: bool = True):
-        """q = A p with the fused p^T q (Algorithm 1 line 6)."""
+        """q = A p with the fused p^T q (Algorithm 1)."""
         _dev_f32(p, "p")
         if q is None:
             q = torch.empty_like(p)

@@ -176,7 +176,7 @@ def test_defcg_error_bounded_by_residual_in_the_a_norm():
 
 
 def test_defcg_k0_reproduces_cg_bitwise():
-    # Algorithm 1 differs from CG only in lines 3 and 11 (Sec. 2.2): with W
+    # Algorithm 1 differs from CG only in the initial projection and the mu step (Sec. 2.2): with W
     # empty every iterate must be identical.
     n = 60
     A, _ = _spd(n, seed=8, hi=300.0)
