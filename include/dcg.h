@@ -126,9 +126,10 @@ typedef struct dcg_ctx dcg_ctx;
 const char* dcg_status_string(dcg_status s);
 
 /* Last error message of a context (empty string if none); ctx may be NULL,
- * in which case the message of the last failed call made without a context
- * (dcg_create, dcg_matvec_dense_noalloc) is returned. The pointer stays valid
- * until the next call on the context. */
+ * in which case the message of the calling host thread's last failed call
+ * made without a context (dcg_create, dcg_form_rbf_dense,
+ * dcg_matvec_dense_noalloc) is returned. The pointer stays valid until the
+ * next call on the context (or, for NULL, the thread's next such call). */
 const char* dcg_last_error(const dcg_ctx* ctx);
 
 /* ------------------------------------------------------------------------ */
@@ -202,7 +203,9 @@ dcg_status dcg_rbf_dtheta(dcg_ctx* ctx, const float* U, const float* V, int32_t 
  * exp(-|x_i - x_j|^2 / (2 l^2)) + noise * [i == j], float32, computed from X
  * (device, row-major float32 n x d) with float32 difference-form distances.
  * A: device, n x lda. No context needed; runs on `stream`.
- * Errors: INVALID_ARG, CUDA. */
+ * Errors: INVALID_ARG (X or A NULL, n outside [1, 2^30], lda < n, d outside
+ * [1, 256], lengthscale <= 0, a non-finite parameter), CUDA. The message is
+ * kept for dcg_last_error(NULL). */
 dcg_status dcg_form_rbf_dense(const float* X, int64_t n, int32_t d, double lengthscale,
                               double signal_var, double noise, float* A, int64_t lda,
                               void* stream);

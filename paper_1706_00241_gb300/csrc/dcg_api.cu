@@ -86,7 +86,9 @@ struct dcg_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
 };
 
-static std::string g_create_err;
+// Message of the last failed call made without a context, per host thread
+// (calls on different threads do not overwrite each other's message).
+static thread_local std::string g_create_err;
 static std::mutex g_mu;
 static EncodeTiledFn g_encode = nullptr;
 
@@ -422,10 +424,15 @@ extern "C" dcg_status dcg_rbf_dtheta(dcg_ctx* c, const float* U, const float* V,
 
 extern "C" dcg_status dcg_form_rbf_dense(const float* X, int64_t n, int32_t d, double l, double s2, double noise,
                                          float* A, int64_t lda, void* stream) {
-  if (!X || !A || n < 1 || d < 1 || d > 256 || lda < n || !(l > 0.0)) return DCG_ERR_INVALID_ARG;
-  if (n > (int64_t(1) << 30)) return DCG_ERR_INVALID_ARG;
+  if (!X || !A) return fail(nullptr, DCG_ERR_INVALID_ARG, "dcg_form_rbf_dense: X and A are required");
+  if (n < 1 || n > (int64_t(1) << 30) || lda < n)
+    return fail(nullptr, DCG_ERR_INVALID_ARG, "dcg_form_rbf_dense: need 1 <= n <= 2^30 and lda >= n");
+  if (d < 1 || d > 256) return fail(nullptr, DCG_ERR_INVALID_ARG, "dcg_form_rbf_dense: d must be in [1, 256]");
+  if (!(l > 0.0) || !std::isfinite(l) || !std::isfinite(s2) || !std::isfinite(noise))
+    return fail(nullptr, DCG_ERR_INVALID_ARG, "dcg_form_rbf_dense: lengthscale > 0 and finite parameters");
   cudaError_t e = launch_form_rbf(X, int(n), d, l, s2, noise, A, lda, static_cast<cudaStream_t>(stream));
-  return e == cudaSuccess ? DCG_OK : DCG_ERR_CUDA;
+  if (e != cudaSuccess) return fail(nullptr, DCG_ERR_CUDA, std::string("dcg_form_rbf_dense: ") + cudaGetErrorString(e));
+  return DCG_OK;
 }
 
 // q = A p and p^T q for a dense operator with no context: the matvec kernel

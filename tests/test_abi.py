@@ -112,6 +112,51 @@ def test_create_rejects_unknown_extraction_without_gpu(lib_path):
     assert not ctx.value
 
 
+def test_form_rbf_dense_rejects_bad_arguments_with_a_message(lib_path):
+    # every case fails the argument checks, which run before any CUDA call, so
+    # the placeholder addresses are never dereferenced
+    from paper_1706_00241_gb300 import _lib
+    lib = _lib.load()
+    P = ctypes.c_void_p
+    fake = P(0x1000)
+    cases = [
+        ((None, 16, 4, 1.0, 1.0, 0.1, fake, 16, None), b"X and A are required"),
+        ((fake, 0, 4, 1.0, 1.0, 0.1, fake, 16, None), b"lda >= n"),
+        ((fake, 16, 4, 1.0, 1.0, 0.1, fake, 8, None), b"lda >= n"),
+        ((fake, 16, 0, 1.0, 1.0, 0.1, fake, 16, None), b"d must be in [1, 256]"),
+        ((fake, 16, 4, -1.0, 1.0, 0.1, fake, 16, None), b"lengthscale > 0"),
+        ((fake, 16, 4, 1.0, float("nan"), 0.1, fake, 16, None), b"finite"),
+    ]
+    for args, msg in cases:
+        assert lib.dcg_form_rbf_dense(*args) == 1, args
+        assert msg in lib.dcg_last_error(None), (args, lib.dcg_last_error(None))
+
+
+def test_context_free_error_message_is_per_thread(lib_path):
+    # a failing dcg_create on another host thread leaves this thread's message
+    import threading
+    from paper_1706_00241_gb300 import _lib
+    lib = _lib.load()
+    cfg = _lib.DcgConfig()
+    cfg.n, cfg.max_iter, cfg.tol = 10, 10, 0.0
+    ctx = ctypes.c_void_p()
+    assert lib.dcg_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) == 1
+    assert b"tol must be > 0" in lib.dcg_last_error(None)
+    other = []
+
+    def worker():
+        c2 = _lib.DcgConfig()
+        c2.n, c2.max_iter, c2.tol = 0, 10, 1e-6
+        lib.dcg_create(ctypes.byref(c2), None, ctypes.byref(ctypes.c_void_p()))
+        other.append(lib.dcg_last_error(None))
+
+    t = threading.Thread(target=worker)
+    t.start()
+    t.join()
+    assert b"n out of range" in other[0]
+    assert b"tol must be > 0" in lib.dcg_last_error(None)
+
+
 def test_header_is_plain_c_and_links(lib_path, tmp_path):
     # the boundary is a C ABI: a C99 translation unit that includes the header
     # and references the core calls compiles with gcc and links against the
