@@ -31,6 +31,26 @@ def _dev_f32(t: torch.Tensor, name: str) -> torch.Tensor:
     return t
 
 
+def _need_len(t: torch.Tensor, n: int, name: str) -> None:
+    """The library reads or writes exactly n elements behind the pointer."""
+    if t.numel() != n:
+        raise ValueError(f"{name} must hold n = {n} elements, got {t.numel()}")
+
+
+def _need_rows(t: torch.Tensor, rows: int, name: str, lda: int | None = None, min_cols: int = 0) -> int:
+    """A row-major (rows, lda) matrix behind the pointer: t must be 2-D with
+    that many rows and a row length equal to lda; returns lda."""
+    if t.dim() != 2 or t.shape[0] != rows:
+        raise ValueError(f"{name} must be a 2-D tensor with {rows} rows, got shape {tuple(t.shape)}")
+    row = t.shape[1]
+    lda = row if lda is None else int(lda)
+    if lda != row:
+        raise ValueError(f"lda = {lda} must equal the row length of {name} ({row})")
+    if row < min_cols:
+        raise ValueError(f"{name} needs at least {min_cols} columns, got {row}")
+    return lda
+
+
 class DefCG:
     """A def-CG(k, ell) solver context for systems of size n on the current GPU.
 
@@ -97,7 +117,7 @@ class DefCG:
     def set_operator_dense(self, A: torch.Tensor, lda: int | None = None):
         """Borrow a stored row-major float32 operator (n x n, or n x lda)."""
         _dev_f32(A, "A")
-        lda = A.shape[1] if lda is None else lda
+        lda = _need_rows(A, self.n, "A", lda, min_cols=self.n)
         self._op_ref = A
         self._check(self.lib.dcg_set_operator_dense(self._ctx, ctypes.c_void_p(A.data_ptr()), lda),
                     "dcg_set_operator_dense")
@@ -125,10 +145,12 @@ class DefCG:
         """Runs Algorithm 1 on (A, b); returns (x, info dict). b is float32,
         x float64 (the iterate accumulates in float64; see dcg_solve)."""
         _dev_f32(b, "b")
+        _need_len(b, self.n, "b")
         if x is None:
             x = torch.zeros(b.shape, dtype=torch.float64, device=b.device)
         if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
             raise TypeError("x must be a contiguous float64 CUDA tensor")
+        _need_len(x, self.n, "x")
         info = _lib.DcgSolveInfo()
         st = self.lib.dcg_solve(self._ctx, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
                                 ctypes.byref(info))
@@ -175,7 +197,12 @@ class DefCG:
     def set_subspace(self, W: torch.Tensor):
         """Sets W from a (k, n) tensor (row j is column j of W)."""
         _dev_f32(W, "W")
-        k = W.shape[0] if W.dim() == 2 else 0
+        if W.numel() == 0:
+            k = 0
+        elif W.dim() != 2 or W.shape[1] != self.n:
+            raise ValueError(f"W must be (k, n) with n = {self.n}, got shape {tuple(W.shape)}")
+        else:
+            k = W.shape[0]
         self._check(self.lib.dcg_set_subspace(self._ctx, ctypes.c_void_p(W.data_ptr() if k else 0), k),
                     "dcg_set_subspace")
 
@@ -191,8 +218,11 @@ class DefCG:
     def matvec(self, p: torch.Tensor, q: torch.Tensor | None = None, want_pAp: bool = True):
         """q = A p with the fused p^T q (Algorithm 1)."""
         _dev_f32(p, "p")
+        _need_len(p, self.n, "p")
         if q is None:
             q = torch.empty_like(p)
+        _dev_f32(q, "q")
+        _need_len(q, self.n, "q")
         d = ctypes.c_double(0.0)
         self._check(self.lib.dcg_matvec(self._ctx, ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(q.data_ptr()),
                                         ctypes.byref(d) if want_pAp else None), "dcg_matvec")
@@ -217,8 +247,13 @@ class DefCG:
     def apply_block(self, V: torch.Tensor, Y: torch.Tensor | None = None) -> torch.Tensor:
         """Y = A V for a (c, n) tensor V (row j is column j), in one pass over A."""
         _dev_f32(V, "V")
+        if V.dim() != 2 or V.shape[1] != self.n:
+            raise ValueError(f"V must be (c, n) with n = {self.n}, got shape {tuple(V.shape)}")
         if Y is None:
             Y = torch.empty_like(V)
+        _dev_f32(Y, "Y")
+        if Y.shape != V.shape:
+            raise ValueError(f"Y must have V's shape {tuple(V.shape)}, got {tuple(Y.shape)}")
         self._check(self.lib.dcg_apply_block(self._ctx, ctypes.c_void_p(V.data_ptr()), V.shape[0],
                                              ctypes.c_void_p(Y.data_ptr())), "dcg_apply_block")
         return Y
@@ -232,9 +267,13 @@ def form_rbf_dense(X: torch.Tensor, lengthscale: float, signal_var: float, noise
     """A = s^2 exp(-|x_i - x_j|^2 / (2 l^2)) + noise I as a dense float32 matrix (Sec. 3)."""
     lib = _lib.load()
     _dev_f32(X, "X")
+    if X.dim() != 2:
+        raise ValueError(f"X must be (n, d), got shape {tuple(X.shape)}")
     n, d = X.shape
     if out is None:
         out = torch.empty((n, n), dtype=torch.float32, device=X.device)
+    _dev_f32(out, "out")
+    _need_rows(out, n, "out", min_cols=n)
     st = lib.dcg_form_rbf_dense(ctypes.c_void_p(X.data_ptr()), n, d, float(lengthscale), float(signal_var),
                                 float(noise), ctypes.c_void_p(out.data_ptr()), out.shape[1],
                                 ctypes.c_void_p(_stream_handle(stream)))
@@ -253,8 +292,9 @@ def matvec_dense_noalloc(A: torch.Tensor, p: torch.Tensor, q: torch.Tensor, pAp:
     _dev_f32(q, "q")
     if pAp is not None and (not pAp.is_cuda or pAp.dtype != torch.float64 or pAp.numel() < 1):
         raise ValueError("pAp must be a float64 CUDA tensor with one element")
-    n = p.shape[0]
-    lda = A.shape[1] if lda is None else lda
+    n = p.numel()
+    _need_len(q, n, "q")
+    lda = _need_rows(A, n, "A", lda, min_cols=n)
     st = lib.dcg_matvec_dense_noalloc(ctypes.c_void_p(A.data_ptr()), n, lda, ctypes.c_void_p(p.data_ptr()),
                                       ctypes.c_void_p(q.data_ptr()),
                                       ctypes.c_void_p(pAp.data_ptr()) if pAp is not None else None,
