@@ -387,25 +387,11 @@ def _whitener(F):
         return Qf[:, keep] / np.sqrt(lam[keep])
 
 
-def harmonic_ritz(W, AW, P, Q, k, select="largest"):
-    """k harmonic Ritz vectors from Z = [W, P_ell] and AZ = [AW, A P_ell] (Sec. 2.3).
-
-    Forms F = (AZ)^T Z (symmetrised; it equals Z^T A Z for symmetric A) and
-    G = (AZ)^T (AZ), solves G u = theta F u (Eq. 7) by reducing with a
-    factor T of F^{-1} (T^T F T = I): C = T^T G T, C v = theta v, u = T v.
-    Keeps k values per R4 and returns W = Z U scaled per R5.
-    """
-    cols = [np.asarray(W, dtype=F64)] if W is not None and W.shape[1] else []
-    acols = [np.asarray(AW, dtype=F64)] if AW is not None and AW.shape[1] else []
-    if len(P):
-        cols.append(np.column_stack(P).astype(F64))
-        acols.append(np.column_stack(Q).astype(F64))
-    Z = np.hstack(cols)
-    AZ = np.hstack(acols)
-    F = AZ.T @ Z
-    F = 0.5 * (F + F.T)
-    G = AZ.T @ AZ
-    G = 0.5 * (G + G.T)
+def _pencil_extract(Z, F, G, k, select):
+    """Solves G u = theta F u (F symmetric positive definite on span(Z)) by
+    reducing with a factor T of F^{-1} (T^T F T = I, R6 when F is singular):
+    C = T^T G T, C v = theta v, u = T v. Keeps k values per R4 and returns
+    W = Z U scaled per R5, with the pencil's F and G."""
     T = _whitener(F)
     C = T.T @ G @ T
     C = 0.5 * (C + C.T)
@@ -426,6 +412,28 @@ def harmonic_ritz(W, AW, P, Q, k, select="largest"):
     Wn = Wn * np.sign(Wn[piv, np.arange(kk)])
     return RitzResult(theta=np.sort(theta)[::-1], W=Wn, U=U, F=F, G=G,
                       theta_selected=theta[sel])
+
+
+def harmonic_ritz(W, AW, P, Q, k, select="largest"):
+    """k harmonic Ritz vectors from Z = [W, P_ell] and AZ = [AW, A P_ell] (Sec. 2.3).
+
+    Forms F = (AZ)^T Z (symmetrised; it equals Z^T A Z for symmetric A) and
+    G = (AZ)^T (AZ), solves G u = theta F u (Eq. 7) by reducing with a
+    factor T of F^{-1} (T^T F T = I): C = T^T G T, C v = theta v, u = T v.
+    Keeps k values per R4 and returns W = Z U scaled per R5.
+    """
+    cols = [np.asarray(W, dtype=F64)] if W is not None and W.shape[1] else []
+    acols = [np.asarray(AW, dtype=F64)] if AW is not None and AW.shape[1] else []
+    if len(P):
+        cols.append(np.column_stack(P).astype(F64))
+        acols.append(np.column_stack(Q).astype(F64))
+    Z = np.hstack(cols)
+    AZ = np.hstack(acols)
+    F = AZ.T @ Z
+    F = 0.5 * (F + F.T)
+    G = AZ.T @ AZ
+    G = 0.5 * (G + G.T)
+    return _pencil_extract(Z, F, G, k, select)
 
 
 def rayleigh_ritz(W, AW, P, Q, k, select="largest"):
@@ -449,26 +457,58 @@ def rayleigh_ritz(W, AW, P, Q, k, select="largest"):
     M = 0.5 * (M + M.T)
     K = Z.T @ AZ
     K = 0.5 * (K + K.T)
-    T = _whitener(M)
-    C = T.T @ K @ T
-    C = 0.5 * (C + C.T)
-    theta, V = np.linalg.eigh(C)            # ascending
-    U_all = T @ V
-    if select == "largest":
-        order = np.argsort(-theta, kind="stable")
-    elif select == "smallest":
-        order = np.argsort(theta, kind="stable")
-    else:
-        raise ValueError(select)
-    kk = min(k, theta.size)
-    sel = order[:kk]
-    U = U_all[:, sel]
-    Wn = Z @ U
-    Wn = Wn / np.linalg.norm(Wn, axis=0)
-    piv = np.argmax(np.abs(Wn), axis=0)
-    Wn = Wn * np.sign(Wn[piv, np.arange(kk)])
-    return RitzResult(theta=np.sort(theta)[::-1], W=Wn, U=U, F=M, G=K,
-                      theta_selected=theta[sel])
+    return _pencil_extract(Z, M, K, k, select)
+
+
+def sparse_FG(E, GW, d, alpha, rho, h):
+    """F and G of Eq. 7 from the scalars of a def-CG run, without Z or AZ: the
+    explicit sparse forms of Saad et al. that Sec. 2.3 mentions.
+
+    For ell consecutive stored directions p_s .. p_{s+ell-1} with no residual
+    replacement between r_s and r_{s+ell}:
+      * A-conjugacy and (AW)^T p_j = 0 (Sec. 2.2) make F = (AZ)^T Z
+        block diagonal: E = W^T A W, then diag(d_j), d_j = p_j^T A p_j;
+      * A p_j = (r_j - r_{j+1}) / alpha_j with mutually orthogonal residuals
+        makes (AP)^T (AP) tridiagonal: (rho_j + rho_{j+1}) / alpha_j^2 on the
+        diagonal, -rho_{j+1} / (alpha_j alpha_{j+1}) beside it;
+      * the same identity gives the coupling (AW)^T A p_j = (h_j - h_{j+1}) / alpha_j
+        with h_j = (AW)^T r_j; the W block is G_W = (AW)^T (AW).
+
+    E, GW: k x k. d, alpha: ell values. rho: ell + 1 values |r_j|^2,
+    j = s .. s + ell. h: k x (ell + 1), columns (AW)^T r_j for the same j.
+    """
+    E = np.asarray(E, dtype=F64)
+    k, ell = E.shape[0], len(d)
+    d, alpha, rho = (np.asarray(v, dtype=F64) for v in (d, alpha, rho))
+    m = k + ell
+    F = np.zeros((m, m))
+    G = np.zeros((m, m))
+    if k:
+        F[:k, :k] = 0.5 * (E + E.T)
+        GW = np.asarray(GW, dtype=F64)
+        G[:k, :k] = 0.5 * (GW + GW.T)
+    for j in range(ell):
+        F[k + j, k + j] = d[j]
+        G[k + j, k + j] = (rho[j] + rho[j + 1]) / alpha[j] ** 2
+        if j + 1 < ell:
+            G[k + j, k + j + 1] = G[k + j + 1, k + j] = -rho[j + 1] / (alpha[j] * alpha[j + 1])
+        if k:
+            col = (np.asarray(h[:, j], dtype=F64) - np.asarray(h[:, j + 1], dtype=F64)) / alpha[j]
+            G[:k, k + j] = col
+            G[k + j, :k] = col
+    return F, G
+
+
+def harmonic_ritz_sparse(W, P, E, GW, d, alpha, rho, h, k, select="largest"):
+    """Eq. 7 with F and G from ``sparse_FG`` (no pass over AZ); the rest as in
+    ``harmonic_ritz``: the same pencil reduction, selection and W = Z U."""
+    kw = W.shape[1] if W is not None else 0
+    cols = [np.asarray(W, dtype=F64)] if kw else []
+    if len(P):
+        cols.append(np.column_stack(P).astype(F64))
+    Z = np.hstack(cols)
+    F, G = sparse_FG(E if kw else np.zeros((0, 0)), GW, d, alpha, rho, h)
+    return _pencil_extract(Z, F, G, k, select)
 
 
 # ----------------------------------------------------------------------------

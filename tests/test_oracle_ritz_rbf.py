@@ -215,3 +215,49 @@ def test_rayleigh_ritz_invariant_subspace_and_sequence():
     out = O.run_sequence(ops, bs, cfg.k, cfg.ell, 1e-8, extraction="ritz")
     for o in out:
         assert o["result"].status == O.STATUS_OK and o["result"].relres_true <= 1e-8
+
+
+# ---------------------------------------------------------------------------
+# Sparse F and G from the scalars of the run (Saad et al., mentioned in Sec. 2.3)
+# ---------------------------------------------------------------------------
+
+def _sparse_inputs(res, s, ell):
+    R = res.r_history
+    W, AW = res.W, res.AW
+    k = 0 if W is None else W.shape[1]
+    E = W.T @ AW if k else np.zeros((0, 0))
+    GW = AW.T @ AW if k else np.zeros((0, 0))
+    rho = [R[j] @ R[j] for j in range(s, s + ell + 1)]
+    h = np.column_stack([AW.T @ R[j] for j in range(s, s + ell + 1)]) if k else np.zeros((0, ell + 1))
+    return E, GW, res.d, res.alpha, rho, h
+
+
+@pytest.mark.parametrize("k,window", [(0, "first"), (4, "first"), (4, "last")])
+def test_sparse_FG_equal_the_dense_products(k, window):
+    # F = (AZ)^T Z and G = (AZ)^T (AZ) formed from Z and AZ must equal the
+    # forms built only from E, G_W, d_j, alpha_j, |r_j|^2 and (AW)^T r_j; the
+    # harmonic Ritz values and vectors then agree as well.
+    n, ell = 150, 8
+    A, _ = S.spd_with_spectrum(np.geomspace(1.0, 60.0, n), seed=31)
+    rng = np.random.default_rng(9)
+    b = rng.standard_normal(n)
+    W = rng.standard_normal((n, k)) if k else None
+    if window == "first":
+        res = O.defcg(A, b, W=W, tol=1e-12, ell=ell, window="first", keep_iterates=True)
+        s = 0
+    else:
+        # stop by max_iter so that the residual after the last stored direction
+        # is in the kept history
+        res = O.defcg(A, b, W=W, tol=1e-14, max_iter=20, ell=ell, window="last", keep_iterates=True)
+        assert res.status == O.STATUS_MAXITER and res.iters == 20
+        s = res.iters - ell
+    assert len(res.P) == ell and res.iters > ell
+    dense = O.harmonic_ritz(res.W if k else None, res.AW if k else None, res.P, res.Q, 5)
+    E, GW, d, alpha, rho, h = _sparse_inputs(res, s, ell)
+    F, G = O.sparse_FG(E, GW, d, alpha, rho, h)
+    np.testing.assert_allclose(F, dense.F, rtol=0, atol=1e-10 * np.abs(dense.F).max())
+    np.testing.assert_allclose(G, dense.G, rtol=0, atol=1e-10 * np.abs(dense.G).max())
+    sp = O.harmonic_ritz_sparse(res.W if k else None, res.P, E, GW, d, alpha, rho, h, 5)
+    np.testing.assert_allclose(sp.theta, dense.theta, rtol=1e-9)
+    for j in range(5):
+        assert abs(sp.W[:, j] @ dense.W[:, j]) > 1 - 1e-9
