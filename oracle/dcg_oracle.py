@@ -11,6 +11,9 @@ Paper: de Roos & Hennig, arXiv 1706.00241.
     G = (AZ)^T (AZ), Z = [W, P_ell]; the next W is Z U for k chosen u.
   * Sec. 2.3, the equation before Eq. 7: orthogonal (Rayleigh-Ritz) projection
     Z^T A Z u = theta Z^T Z u, offered as the alternative extraction.
+  * Sec. 2.3 (Saad et al.'s explicit forms): F and G of Eq. 7 built from the
+    scalars of the run (E, G_W, d_j, alpha_j, |r_j|^2, (AW)^T r_j) instead of
+    products over Z and AZ.
   * Sec. 3: the RBF kernel k(x_i, x_j) = theta^2 exp(-|x_i - x_j|^2 / (2 lambda^2)).
 
 Readings where the paper is silent or ambiguous (each one is also listed in the
