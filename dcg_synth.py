@@ -150,3 +150,18 @@ def gp_targets(X: np.ndarray, seed: int = 0) -> np.ndarray:
     """Regression targets ``y = sin(6 x_0) + 0.1 eps`` for the gradient workload."""
     rng = np.random.default_rng(seed + 1)
     return np.sin(6.0 * X[:, 0]) + 0.1 * rng.standard_normal(X.shape[0])
+
+
+def classification_data(n: int, d: int, seed: int = 0, spread: float = 0.15):
+    """Binary classification inputs in the shape of the Sec. 3 experiment
+    (images of two digits, pixel values in [0, 1], labels +-1): two classes
+    around seeded centres in [0.3, 0.7]^d with Gaussian spread, clipped to
+    [0, 1], labels alternating +1, -1. A synthetic stand-in for the infinite
+    MNIST threes and fives, which are not available here.
+    Returns X (n, d) float64 and y (n,) float64."""
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(0.3, 0.7, size=(2, d))
+    y = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    cls = (y < 0).astype(int)
+    X = np.clip(centres[cls] + spread * rng.standard_normal((n, d)), 0.0, 1.0)
+    return X, y

@@ -20,6 +20,13 @@ Parity status per function (what pins it; tests in ``tests/test_oracle_*.py``):
                          the reduced spectrum
   harmonic_ritz          pinned: invariant subspace gives exact eigenvalues and
                          eigenvectors; generalized-eigen residual
+  rayleigh_ritz          pinned: Galerkin condition, orthonormal-basis eigenvalues,
+                         the CG-Lanczos tridiagonal, Cauchy interlacing
+  sparse_FG, harmonic_ritz_sparse
+                         pinned: equal to the products over Z and AZ
+  laplace_oracle         pinned: finite differences of the likelihood, the plain
+                         Newton step, the mode's fixed-point equation, the
+                         system's spectrum bound, a generic optimiser
   gp_oracle.gp_nll, gp_nll_grad
                          pinned: central finite differences in log space, the
                          closed form for a vanishing lengthscale
