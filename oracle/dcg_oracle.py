@@ -34,7 +34,10 @@ design notes of the repository):
      (x += W g, r -= AW g, g = E^{-1} W^T r), and take mu from
      (AW)^T (beta p_j + r_{j+1}) so that p_{j+1} is re-projected against W.
      beta keeps the recursion's value |r_{j+1}|^2 / |r_j|^2 (before the
-     replacement); rho is recomputed from the replaced residual.
+     replacement); rho is recomputed from the replaced residual. The two steps
+     are the functions project_out and next_direction; defcg's A_true names
+     the operator whose residual the replacements and checks form (iterative
+     refinement when the loop operator only approximates it).
 """
 
 from __future__ import annotations
@@ -238,8 +241,30 @@ def cg(A, b, x_init=None, tol=1e-6, max_iter=None, keep_iterates=False):
     return res
 
 
+def project_out(x, r, W, AW, Esolve):
+    """Deflation of an iterate (the initial projection of Algorithm 1, reused
+    by R13 after a replacement): g = E^{-1} W^T r, x <- x + W g, r <- r - AW g.
+    Afterwards W^T r = W^T r_in - (W^T AW) E^{-1} W^T r_in = 0, and x and r
+    move together: x_out - x_in = W g and r_in - r_out = AW g."""
+    g = Esolve(W.T @ r)
+    return x + W @ g, r - AW @ g
+
+
+def next_direction(r, p, beta, W, AW, Esolve, reproject):
+    """Direction update of Algorithm 1: p <- beta p + r - W mu with
+    E mu = (AW)^T r (R1). With ``reproject`` (R13, after a replacement) mu is
+    taken from (AW)^T (beta p + r), so that (AW)^T p_out = 0 even when the
+    incoming p is not A-conjugate to W; in exact arithmetic (AW)^T p = 0 and
+    the two forms agree. Returns (mu, p_out)."""
+    h = AW.T @ r
+    if reproject:
+        h = h + beta * (AW.T @ p)
+    mu = Esolve(h)
+    return mu, beta * p + r - W @ mu
+
+
 def defcg(A, b, x_init=None, W=None, AW=None, tol=1e-6, max_iter=None, ell=0,
-          window="last", refine_every=0, keep_iterates=False):
+          window="last", refine_every=0, keep_iterates=False, A_true=None):
     """Deflated-CG(k, ell)(A, b, x_{-1}, W, (AW), tol): Algorithm 1, Sec. 2.2.
 
     ``A`` is a dense matrix or a callable v -> A v. ``W`` is n x k (k may be 0
@@ -247,6 +272,14 @@ def defcg(A, b, x_init=None, W=None, AW=None, tol=1e-6, max_iter=None, ell=0,
     it optionally); otherwise it is formed with k products. Returns a
     ``SolveResult`` holding x, the iteration count, the recursive residual
     history and the stored directions p_j with A p_j (reading R3).
+
+    ``A_true`` (default: ``A``) is the operator whose residual b - A_true x is
+    formed by the true-residual steps (the warm-start r_{-1}, the R2
+    confirmation, the R13 replacements and the reported residual), while the
+    recursion, A W and the stored A p_j use ``A``. With an ``A`` that only
+    approximates ``A_true`` this is iterative refinement: the GPU's
+    mixed-precision operators iterate with rounded kernel entries and certify
+    with accurate ones.
     """
     b = np.asarray(b, dtype=F64)
     n = b.size
@@ -268,15 +301,16 @@ def defcg(A, b, x_init=None, W=None, AW=None, tol=1e-6, max_iter=None, ell=0,
         res.x = np.zeros(n)
         return res
 
+    A_res = A if A_true is None else A_true
+
     def deflate(x, r):
         """Initial projection: x <- x + W E^{-1} W^T r, so that W^T r = 0 afterwards."""
         if not k:
             return x, r
-        g = Esolve(W.T @ r)
-        return x + W @ g, r - AW @ g
+        return project_out(x, r, W, AW, Esolve)
 
     if x_init is not None and np.any(x):
-        r = b - _mv(A, x)                   # r_{-1}
+        r = b - _mv(A_res, x)               # r_{-1}
         res.matvecs_setup += 1
     else:
         r = b.copy()
@@ -306,7 +340,7 @@ def defcg(A, b, x_init=None, W=None, AW=None, tol=1e-6, max_iter=None, ell=0,
 
     converged = np.sqrt(rho) <= thresh
     if converged:
-        r_true = b - _mv(A, x)
+        r_true = b - _mv(A_res, x)
         res.matvecs_check += 1
         if np.linalg.norm(r_true) > thresh:
             x, r = deflate(x, r_true)
@@ -333,7 +367,7 @@ def defcg(A, b, x_init=None, W=None, AW=None, tol=1e-6, max_iter=None, ell=0,
         rho_rec = rho_new                    # the recursion's own |r_{j+1}|^2
         replaced = False
         if np.sqrt(rho_new) <= thresh:       # R2
-            r_true = b - _mv(A, x)
+            r_true = b - _mv(A_res, x)
             res.matvecs_check += 1
             if np.linalg.norm(r_true) <= thresh:
                 break
@@ -341,17 +375,13 @@ def defcg(A, b, x_init=None, W=None, AW=None, tol=1e-6, max_iter=None, ell=0,
             rho_new = r @ r
             replaced = True
         elif refine_every and j % refine_every == 0:   # R13
-            x, r = deflate(x, b - _mv(A, x))
+            x, r = deflate(x, b - _mv(A_res, x))
             res.matvecs_check += 1
             rho_new = r @ r
             replaced = True
         beta = rho_rec / rho                 # beta_j (R13: from the recursion)
         if k:                                # mu step: E mu_{j+1} = (AW)^T r_{j+1} (R1; R13)
-            h = AW.T @ r
-            if replaced:
-                h = h + beta * (AW.T @ p)
-            mu = Esolve(h)
-            p = beta * p + r - W @ mu        # direction update
+            mu, p = next_direction(r, p, beta, W, AW, Esolve, replaced)
         else:
             mu = np.zeros(0)
             p = beta * p + r
@@ -361,7 +391,7 @@ def defcg(A, b, x_init=None, W=None, AW=None, tol=1e-6, max_iter=None, ell=0,
         if keep_iterates:
             res.x_history.append(x.copy()); res.r_history.append(r.copy()); res.p_history.append(p.copy())
     res.x, res.iters = x, j
-    res.relres_true = true_relres(A, b, x)
+    res.relres_true = true_relres(A_res, b, x)
     return res
 
 

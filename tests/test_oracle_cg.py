@@ -270,3 +270,147 @@ def test_breakdown_on_indefinite():
     _, Q = S.spd_with_spectrum(eigs, seed=0)
     res = O.defcg(A, Q[:, 0], tol=1e-10)
     assert res.status == O.STATUS_BREAKDOWN
+
+
+# ----------------------------------------------------------------------------
+# Residual replacement (reading R13: r <- b - A x every m iterations, re-deflate,
+# mu from (AW)^T (beta p + r), beta from the recursion; van der Vorst and Ye's
+# residual replacement). In exact arithmetic with one operator a replacement
+# changes nothing, so the branch is pinned three ways: its two steps as
+# functions on arbitrary inputs, the no-op property with one operator, and its
+# exact identities when the loop operator only approximates the certified one
+# (iterative refinement, the GPU's mixed-precision setting).
+# ----------------------------------------------------------------------------
+
+def _galerkin_parts(n, k, seed):
+    A, _ = _spd(n, seed=seed, hi=40.0)
+    rng = np.random.default_rng(seed + 100)
+    W = rng.standard_normal((n, k))
+    AW = A @ W
+    W, AW, Esolve = O._galerkin(W, AW)
+    return A, W, AW, Esolve, rng
+
+
+def test_project_out_deflates_and_moves_x_and_r_together():
+    n, k = 40, 5
+    A, W, AW, Esolve, rng = _galerkin_parts(n, k, seed=21)
+    x, r = rng.standard_normal(n), rng.standard_normal(n)
+    assert np.linalg.norm(W.T @ r) > 1.0          # the input is not deflated
+    x2, r2 = O.project_out(x, r, W, AW, Esolve)
+    # W^T r = 0 afterwards (the Galerkin condition of the initial projection)
+    assert np.linalg.norm(W.T @ r2) <= 1e-12 * np.linalg.norm(W) * np.linalg.norm(r)
+    # one coefficient vector g moves both: x2 - x = W g, r - r2 = AW g
+    g, *_ = np.linalg.lstsq(W, x2 - x, rcond=None)
+    np.testing.assert_allclose(W @ g, x2 - x, rtol=0, atol=1e-12 * np.linalg.norm(x2 - x))
+    np.testing.assert_allclose(AW @ g, r - r2, rtol=0, atol=1e-12 * np.linalg.norm(AW @ g))
+    # a residual consistent with x stays consistent: r = b - A x => r2 = b - A x2
+    b = r + A @ x
+    x3, r3 = O.project_out(x, b - A @ x, W, AW, Esolve)
+    np.testing.assert_allclose(r3, b - A @ x3, rtol=0, atol=1e-12 * np.linalg.norm(b))
+
+
+def test_next_direction_reprojects_an_arbitrary_direction():
+    n, k = 40, 5
+    A, W, AW, Esolve, rng = _galerkin_parts(n, k, seed=22)
+    r, p, beta = rng.standard_normal(n), rng.standard_normal(n), 0.37
+    assert np.linalg.norm(AW.T @ p) > 1.0         # p is not A-conjugate to W
+    mu, p2 = O.next_direction(r, p, beta, W, AW, Esolve, reproject=True)
+    # (AW)^T p2 = 0: the new direction is A-conjugate to W whatever p was
+    assert np.linalg.norm(AW.T @ p2) <= 1e-12 * np.linalg.norm(AW) * np.linalg.norm(p)
+    # p2 = beta p + r - W mu with mu solving E mu = (AW)^T (beta p + r)
+    np.testing.assert_allclose(p2, beta * p + r - W @ mu, rtol=0, atol=1e-13 * np.linalg.norm(p2))
+    E = W.T @ AW
+    np.testing.assert_allclose(E @ mu, AW.T @ (beta * p + r), rtol=0,
+                               atol=1e-11 * np.linalg.norm(AW.T @ (beta * p + r)))
+    # the plain form (Algorithm 1's mu from (AW)^T r) leaves beta (AW)^T p behind
+    _, p3 = O.next_direction(r, p, beta, W, AW, Esolve, reproject=False)
+    np.testing.assert_allclose(AW.T @ p3, beta * (AW.T @ p), rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("kappa,n,tol", [(10.0, 80, 1e-8), (20.0, 120, 1e-9)])
+def test_replacement_is_a_noop_with_one_operator(kappa, n, tol):
+    # Well-conditioned systems (kappa <= 20, measured: iterates of the two runs
+    # agree to 5e-16 and 2e-13 of |b|); on harder ones FP64 CG's loss of
+    # orthogonality makes the replaced and the recursive paths part visibly.
+    k = 4
+    A, _ = S.spd_with_spectrum(np.geomspace(1.0, kappa, n), seed=23)
+    rng = np.random.default_rng(24)
+    b, W = rng.standard_normal(n), rng.standard_normal((n, k))
+    ref = O.defcg(A, b, W=W, tol=tol, keep_iterates=True)
+    rep = O.defcg(A, b, W=W, tol=tol, refine_every=3, keep_iterates=True)
+    assert rep.iters == ref.iters
+    assert rep.matvecs_check >= ref.iters // 3
+    bn = np.linalg.norm(b)
+    for j in range(len(ref.x_history)):
+        for a, c in ((rep.x_history[j], ref.x_history[j]), (rep.p_history[j], ref.p_history[j]),
+                     (rep.r_history[j], ref.r_history[j])):
+            assert np.linalg.norm(a - c) <= 1e-11 * bn, j
+    np.testing.assert_allclose(rep.x, ref.x, rtol=0, atol=1e-11 * np.linalg.norm(ref.x))
+    np.testing.assert_allclose(rep.beta, ref.beta, rtol=1e-6)
+
+
+def _perturbed(A, rel, seed):
+    rng = np.random.default_rng(seed)
+    S_ = rng.standard_normal(A.shape)
+    S_ = 0.5 * (S_ + S_.T)
+    return A + rel * np.linalg.norm(A, 2) / np.linalg.norm(S_, 2) * S_
+
+
+def test_replacement_identities_with_an_approximate_loop_operator():
+    # The loop runs on A_loop = A + E (|E| = 1e-6 |A|), the replacements and
+    # the final check on A: iterative refinement. Every replacement must
+    # re-deflate (W^T r = 0 afterwards), keep p A_loop-conjugate to W, and take
+    # beta from the recursion's |r_{j+1}|^2 over the current rho (recomputed
+    # from the replaced residual); the solve must still certify tol on A.
+    n, k, m = 120, 6, 5
+    A, _ = _spd(n, seed=25, hi=200.0)
+    A_loop = _perturbed(A, 1e-6, seed=26)
+    rng = np.random.default_rng(27)
+    b, W = rng.standard_normal(n), rng.standard_normal((n, k))
+    tol = 1e-11
+    res = O.defcg(A_loop, b, W=W, tol=tol, refine_every=m, keep_iterates=True, A_true=A)
+    assert res.status == O.STATUS_OK
+    assert O.true_relres(A, b, res.x) <= tol
+    assert res.relres_true == O.true_relres(A, b, res.x)
+    Wk, AWk = res.W, res.AW
+    np.testing.assert_allclose(AWk, A_loop @ Wk, rtol=0, atol=1e-12 * np.linalg.norm(AWk))
+    bn = np.linalg.norm(b)
+    replaced_steps = [j for j in range(1, len(res.r_history)) if j % m == 0]
+    assert len(replaced_steps) >= 3
+    drift = 0.0
+    for j in replaced_steps:
+        r, p, x = res.r_history[j], res.p_history[j], res.x_history[j]
+        assert np.linalg.norm(Wk.T @ r) <= 1e-12 * np.linalg.norm(Wk) * np.linalg.norm(r), j
+        assert np.linalg.norm(AWk.T @ p) <= 1e-12 * np.linalg.norm(AWk) * np.linalg.norm(p), j
+        # the replaced residual is the true one up to the re-deflation's
+        # (A - A_loop) W g (|r - (b - A x)| <= 1.4e-11 |b| measured) and differs
+        # from the recursion's (otherwise this test could not tell the choices
+        # of beta apart)
+        assert np.linalg.norm(r - (b - A @ x)) <= 1e-10 * bn, j
+        drift = max(drift, abs(np.linalg.norm(r) - res.history[j] * bn) / np.linalg.norm(r))
+    assert drift > 1e-9
+    # beta_j = (recursion's |r_{j+1}|^2) / rho_j with rho_j = |r_j|^2 of the
+    # residual the loop carries (the replaced one after a replacement), at
+    # every step
+    assert len(res.beta) == len(res.r_history) - 1
+    for j in range(len(res.beta)):
+        r = res.r_history[j]
+        beta_expected = (res.history[j + 1] * bn) ** 2 / (r @ r)
+        assert abs(res.beta[j] - beta_expected) <= 1e-12 * beta_expected, j
+
+
+def test_refinement_reaches_the_certified_operator_solution():
+    # With the approximate loop operator and no replacement other than the
+    # final confirmation (R2), x still solves A x = b to tol: each failed
+    # confirmation replaces r by b - A x and the recursion continues.
+    n, k = 100, 4
+    A, _ = _spd(n, seed=28, hi=300.0)
+    A_loop = _perturbed(A, 1e-5, seed=29)
+    rng = np.random.default_rng(30)
+    b, W = rng.standard_normal(n), rng.standard_normal((n, k))
+    for m in (0, 7):
+        res = O.defcg(A_loop, b, W=W, tol=1e-11, refine_every=m, A_true=A)
+        x_ref = sla.cho_solve(sla.cho_factor(A), b)
+        assert O.true_relres(A, b, res.x) <= 1e-11
+        assert np.linalg.norm(res.x - x_ref) <= 300.0 * 1e-11 * np.linalg.norm(x_ref)
+        assert res.matvecs_check >= 2     # at least one failed confirmation
