@@ -17,7 +17,11 @@ Parity status per function (what pins it; tests in ``tests/test_oracle_*.py``):
                          (#distinct eigenvalues) steps, exact rational 2x2 run
   defcg                  pinned: dense solve, W^T r_j = 0, A-conjugacy, k = 0
                          reproduces cg bitwise, exact eigenvectors give CG on
-                         the reduced spectrum
+                         the reduced spectrum; the replacement branch (R13):
+                         project_out / next_direction identities on arbitrary
+                         inputs, no-op with one operator, W^T r = 0,
+                         (AW)^T p = 0 and the recursion's beta under an
+                         approximate loop operator (A_true)
   harmonic_ritz          pinned: invariant subspace gives exact eigenvalues and
                          eigenvectors; generalized-eigen residual
   rayleigh_ritz          pinned: Galerkin condition, orthonormal-basis eigenvalues,
