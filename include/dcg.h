@@ -300,15 +300,28 @@ dcg_status dcg_apply_block(dcg_ctx* ctx, const float* V, int32_t c, float* Y);
 /* Synchronises the context's stream. */
 dcg_status dcg_sync(dcg_ctx* ctx);
 
+/* Failure-handling test hook (no counterpart in the paper): arms the next
+ * dcg_solve of this context so that, in its first iteration, CTA 0 of the
+ * fused iteration kernel withholds its arrival at the grid barrier that
+ * separates the per-CTA partial sums from their reduction, and every CTA's
+ * bounded wait there gives up after `polls` polls (1 <= polls <= 2^22, about
+ * 32 ns or more each) instead of the normal limit. That solve then ends with
+ * DCG_ERR_TIMEOUT; dcg_last_error() names the wait that gave up, x holds the
+ * iterate as the kernels left it, and no GPU fault or hang is involved (the
+ * wait returns; no copy is left in flight). The hook is
+ * disarmed by that solve, and later solves on the context run normally.
+ * Errors: INVALID_ARG (polls out of range), STATE (no operator set). */
+dcg_status dcg_debug_arm_barrier_timeout(dcg_ctx* ctx, int32_t polls);
+
 /* ------------------------------------------------------------------------ */
 /* Context-free matvec on fixed scratch (no device allocation)               */
 /* ------------------------------------------------------------------------ */
 
 /* q = A p and p^T q for a dense stored operator, without a context and
- * without allocating device memory: the same kernel as dcg_matvec (the q = A p
- * of Algorithm 1 with its fused p^T q), with the reduction scratch in
- * a fixed array inside the library. The paper has no counterpart: there the
- * matvec only runs inside a solve. It serves callers that hold no dcg context
+ * without allocating device memory: the same kernel, grid and reduction order
+ * as dcg_matvec (results are bit-identical), with the reduction scratch in
+ * a fixed array inside the library. The paper has no counterpart. It serves
+ * callers that hold no dcg context
  * and may not allocate at the point of the call: code working inside another
  * framework's device-memory budget (its caching allocator owns the free
  * memory, so a cudaMalloc here could fail or fragment it), and loops that
@@ -322,14 +335,19 @@ dcg_status dcg_sync(dcg_ctx* ctx);
  *   pAp    device, one double receiving p^T q, or NULL.
  *   stream cudaStream_t as void*; everything runs on it, nothing synchronises.
  * Scratch: a 4352-byte array in the library, per device: an arrival counter
- * (cleared to zero on `stream` before every launch) and one double partial
- * per CTA for at most 512 CTAs. The grid is min(ceil(n / 8), number of SMs);
+ * and a timeout word (both cleared to zero on `stream` before every launch)
+ * and one double partial per CTA for at most 512 CTAs. The grid is min(ceil(n / 8), number of SMs);
  * a device that would need more than 512 CTAs is rejected with UNSUPPORTED.
  * The scratch address is looked up once per device (cudaGetSymbolAddress with
  * that device current); make the first call on each device before any stream
  * capture begins. All calls on a device share the scratch: calls that overlap
  * in time (different streams, or host threads without ordering between them)
  * race on it and give wrong results, so order them, e.g. on one stream.
+ * Bounded waits: every wait of the kernel gives up after a fixed number of
+ * polls instead of hanging. The call returns before the kernel runs, so such
+ * a failure cannot be returned as a status: the CTAs that gave up write NaN
+ * into their whole band of rows of q, and *pAp (when given) receives NaN. A
+ * finite *pAp means every row of q was computed; without pAp, check q.
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA; the message is kept for
  * dcg_last_error(NULL). */
 dcg_status dcg_matvec_dense_noalloc(const float* A, int64_t n, int64_t lda, const float* p, float* q,

@@ -47,6 +47,8 @@ struct dcg_ctx {
   bool ritz_pending = false;  // an update was enqueued and its result not yet read
   int last_iters = 0;
 
+  int test_barrier_polls = 0;  // > 0: the next solve withholds a grid-barrier arrival (test hook)
+
   // operator
   int op = OP_NONE;
   const float* A = nullptr;
@@ -747,6 +749,18 @@ static dcg_status run_host_loop(dcg_ctx* c, cudaStream_t s) {
   return DCG_OK;
 }
 
+// Which bounded device-side wait gave up (DevState::timeout_site).
+static const char* timeout_site_name(int site) {
+  switch (site) {
+    case 1: return "site 1, TMA tile wait of the stored-operator matvec";
+    case 2: return "site 2, TMA tile wait of the stored-operator true residual";
+    case 3: return "site 3, pipeline wait of the matrix-free matvec";
+    case 4: return "site 4, grid barrier of the fused iteration kernel";
+    case 5: return "site 5, staged k x k matrices of the fused iteration kernel";
+    default: return "unknown site";
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Solve
 // ---------------------------------------------------------------------------
@@ -772,6 +786,11 @@ extern "C" dcg_status dcg_solve(dcg_ctx* c, const float* b, double* x, dcg_solve
   hs->hist_cap = c->cfg.record_history ? c->cfg.max_iter + 2 : 0;
   hs->warm_start = c->cfg.warm_start;
   hs->status = DCG_OK;
+  if (c->test_barrier_polls > 0) {  // one-shot failure-handling test hook
+    hs->test_skip_arrival = 1;
+    hs->spin_limit = c->test_barrier_polls;
+    c->test_barrier_polls = 0;
+  }
   cudaStream_t s = c->stream;
   CK(cudaMemcpyAsync(c->st, hs, sizeof(DevState), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->w.b, b, size_t(n) * 4, cudaMemcpyDeviceToDevice, s));
@@ -808,10 +827,11 @@ extern "C" dcg_status dcg_solve(dcg_ctx* c, const float* b, double* x, dcg_solve
     info->ms_total = ms;
   }
   if (hs->status != DCG_OK) {
-    char buf[160];
+    char buf[256];
+    std::string where;
+    if (hs->status == DCG_ERR_TIMEOUT) where = std::string(" (bounded wait gave up: ") + timeout_site_name(hs->timeout_site) + ")";
     snprintf(buf, sizeof(buf), "solve ended with status %d (%s) after %d iterations%s", hs->status,
-             dcg_status_string(dcg_status(hs->status)), hs->iter,
-             hs->status == DCG_ERR_TIMEOUT ? " (bounded wait gave up)" : "");
+             dcg_status_string(dcg_status(hs->status)), hs->iter, where.c_str());
     c->err = buf;
   }
   return dcg_status(hs->status);
@@ -973,6 +993,14 @@ extern "C" dcg_status dcg_apply_block(dcg_ctx* c, const float* V, int32_t ncols,
   if (c->op == OP_NONE) return fail(c, DCG_ERR_STATE, "no operator set");
   if (!V || !Y || ncols < 1 || ncols > kMaxBlockCols) return fail(c, DCG_ERR_INVALID_ARG, "bad block arguments");
   CK(op_block(c, V, ncols, Y, nullptr, c->stream));
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_debug_arm_barrier_timeout(dcg_ctx* c, int32_t polls) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  if (polls < 1 || polls > (1 << 22)) return fail(c, DCG_ERR_INVALID_ARG, "polls must lie in [1, 2^22]");
+  if (c->op == OP_NONE) return fail(c, DCG_ERR_STATE, "no operator set");
+  c->test_barrier_polls = polls;
   return DCG_OK;
 }
 

@@ -62,6 +62,11 @@ struct DevState {
   double rho_prev_chk;  // true |r|^2 of the previous check
   unsigned int ticket[T_COUNT];
   unsigned long long bar_count;  // grid barrier of the fused iteration kernel: arrivals in this solve
+  // Failure-handling test hook (dcg_debug_arm_barrier_timeout), zero otherwise:
+  // CTA 0 withholds its arrival at the fused kernel's grid barrier and every
+  // CTA gives up after spin_limit polls.
+  int test_skip_arrival;
+  long long spin_limit;
 };
 
 // --------------------------------------------------------------------------

@@ -72,6 +72,9 @@ struct RowOpArgs {
   DevState* st;          // residual: updates rho_true etc.; may be null
   int skip_if_done;
   int resid_mode;        // 0 warm-start setup, 1 check, 2 refinement, 3 final, -1: read st->mode
+  int* abort_word;       // without a state (context-free matvec): set to the wait site
+                         // when a bounded wait gives up; the CTA's rows of out and
+                         // *result are then NaN. May be null.
 };
 
 struct ApplyBlockArgs {

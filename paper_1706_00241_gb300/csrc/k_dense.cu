@@ -284,6 +284,18 @@ __global__ void __launch_bounds__(RB_THREADS, 1)
     for (int w = 0; w < RB_CONSUMER_WARPS; ++w) lo = min(lo, s_consumed[w]);
     for (int it = lo; it < s_issued; ++it) mbar_wait_bounded(&full[it % RB_STAGES], (it / RB_STAGES) & 1);
     record_timeout(st, RESID ? 2 : 1);
+    if (a.abort_word) atomicExch(a.abort_word, RESID ? 2 : 1);
+  }
+  // Without a solver state nothing else records the timeout: the rows of this
+  // CTA's band are overwritten with NaN (some were never computed) and the
+  // last CTA reports a NaN sum.
+  if (a.abort_word) {
+    __syncthreads();
+    if (s_abort) {
+      const float qnan = __int_as_float(0x7fc00000);
+      for (int row = g_lo * RB_ROWS + int(threadIdx.x); row < min(g_hi * RB_ROWS, n); row += RB_THREADS)
+        a.out[row] = qnan;
+    }
   }
 
   // CTA partial -> last CTA sums all partials in float64 (fixed order).
@@ -303,6 +315,7 @@ __global__ void __launch_bounds__(RB_THREADS, 1)
     for (int i = lane; i < G; i += 32) s += a.partials[i];
     s = warp_sum(s);
     if (lane == 0) {
+      if (a.abort_word && *reinterpret_cast<volatile int*>(a.abort_word) != 0) s = __longlong_as_double(0x7ff8000000000000ll);
       if (!RESID || !st) {
         if (a.result) *a.result = s;
       } else if (a.resid_mode != 0) {
@@ -356,9 +369,9 @@ int rowop_grid(int n, int num_sms) {
 // ---------------------------------------------------------------------------
 // Fixed scratch of the context-free matvec (dcg_matvec_dense_noalloc), which
 // allocates no device memory: the arrival counter of the last-CTA reduction
-// at byte 0 (it must be zero when a launch starts; the launcher clears it on
-// the stream before every launch) and one double partial per CTA from byte
-// 256. The grid is min(ceil(n / RB_ROWS), SMs), so kNoallocMaxCtas slots
+// at byte 0 and the timeout word at byte 4 (both must be zero when a launch
+// starts; the launcher clears the two on the stream before every launch), and
+// one double partial per CTA from byte 256. The grid is min(ceil(n / RB_ROWS), SMs), so kNoallocMaxCtas slots
 // cover every device with up to 512 SMs (GB300: 152).
 // ---------------------------------------------------------------------------
 constexpr int kNoallocMaxCtas = 512;
@@ -393,7 +406,7 @@ cudaError_t launch_matvec_noalloc(const CUtensorMap* tmap, const float* p, float
                                   void* scratch, cudaStream_t s) {
   if (grid < 1 || grid > kNoallocMaxCtas) return cudaErrorInvalidValue;
   unsigned int* counter = static_cast<unsigned int*>(scratch);
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
+  cudaError_t e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned int), s);  // counter and timeout word
   if (e != cudaSuccess) return e;
   RowOpArgs a{};
   a.v = p;
@@ -401,6 +414,7 @@ cudaError_t launch_matvec_noalloc(const CUtensorMap* tmap, const float* p, float
   a.n = n;
   a.partials = reinterpret_cast<double*>(static_cast<unsigned char*>(scratch) + 256);
   a.ticket = counter;
+  a.abort_word = reinterpret_cast<int*>(counter + 1);
   a.result = pAp;
   return launch_rowop(tmap, a, false, grid, s);
 }

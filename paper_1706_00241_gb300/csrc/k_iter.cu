@@ -275,14 +275,21 @@ cudaError_t launch_check_update(const Ws& w, int grid, int pre_loop, int setup, 
 // adds 1 with release semantics; its barrier completes when the counter
 // reaches the next multiple of gridDim.x above its ticket, which it polls with
 // acquire loads (bounded wait). Returns false if the wait gave up (the kernel
-// then records a timeout).
+// then records a timeout). With the state's test hook armed, CTA 0 reads the
+// counter instead of adding to it, so that no CTA's wait can complete, and the
+// wait gives up after st->spin_limit polls.
 __device__ bool grid_barrier(DevState* st) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long* cnt = &st->bar_count;
     unsigned long long ticket;
-    asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(ticket) : "l"(cnt) : "memory");
+    const bool withhold = st->test_skip_arrival != 0 && blockIdx.x == 0;
+    const long long limit = st->spin_limit > 0 ? st->spin_limit : kSpinLimit;
+    if (withhold)
+      asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(ticket) : "l"(cnt) : "memory");
+    else
+      asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(ticket) : "l"(cnt) : "memory");
     const unsigned long long target = (ticket / gridDim.x + 1) * gridDim.x;
     int ok = 1;
     long long i = 0;
@@ -291,7 +298,7 @@ __device__ bool grid_barrier(DevState* st) {
       asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(cnt) : "memory");
       if (v >= target) break;
       __nanosleep(32);
-      if (++i >= kSpinLimit) {
+      if (++i >= limit) {
         ok = 0;
         break;
       }
@@ -530,6 +537,9 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
   }
   if (!grid_barrier(st)) {
     if (t == 0) {
+      // the bulk copy of the k x k matrices may still be landing in shared
+      // memory: wait for it (bounded) before the CTA leaves
+      if (staged) mbar_wait_bounded(&mat_bar, 0);
       st->status = DCG_ERR_TIMEOUT;
       st->timeout_site = 4;
       st->done = 1;

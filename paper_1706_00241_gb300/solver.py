@@ -261,6 +261,15 @@ class DefCG:
     def sync(self):
         self._check(self.lib.dcg_sync(self._ctx), "dcg_sync")
 
+    def debug_arm_barrier_timeout(self, polls: int = 64):
+        """Test hook: the next solve's grid barrier misses one arrival and its
+        bounded wait gives up after ``polls`` polls (DCG_ERR_TIMEOUT)."""
+        self._check(self.lib.dcg_debug_arm_barrier_timeout(self._ctx, int(polls)),
+                    "dcg_debug_arm_barrier_timeout")
+
+    def last_error(self) -> str:
+        return self.lib.dcg_last_error(self._ctx).decode()
+
 
 def form_rbf_dense(X: torch.Tensor, lengthscale: float, signal_var: float, noise: float,
                    out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
