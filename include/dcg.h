@@ -291,6 +291,23 @@ dcg_status dcg_get_history(dcg_ctx* ctx, double* relres, int32_t cap, int32_t* c
  * Errors: STATE (no operator), INVALID_ARG, CUDA. */
 dcg_status dcg_matvec(dcg_ctx* ctx, const float* p, float* q, double* pAp);
 
+/* True residual r = b - A x of the current operator: the quantity of the
+ * solve's stopping test (the relative |b - A x| / |b| of the Sec. 3
+ * experiments) and of its residual replacement. Stored operator: Dot2
+ * compensated sums over A with x split as a float32 pair. Matrix-free
+ * operator: exact-form entries (Gram-form distances summed onto a fixed grid,
+ * a table-driven float32-pair exponential) and Dot2 sums.
+ *   b device n floats; x device n doubles; r device n floats (written).
+ *   rnorm2 host, may be NULL: |r|^2 summed in float64.
+ *   err host, may be NULL: for the matrix-free operator the estimated error
+ *     of |r| from the entries' rounding (probabilistic model; the solve
+ *     accepts convergence only when |r| + err <= tol |b|); 0 for the stored
+ *     operator.
+ * Uses the context's iterate buffers (a later dcg_solve overwrites them
+ * anyway). Synchronises the context's stream.
+ * Errors: STATE (no operator), INVALID_ARG, CUDA. */
+dcg_status dcg_residual(dcg_ctx* ctx, const float* b, const double* x, float* r, double* rnorm2, double* err);
+
 /* Multi-vector product Y = A V (the start-of-solve product AW of Algorithm 1,
  * needed by its initial projection): one pass over a stored A; for the matrix-free operator the
  * exact-form entries (as in its true residual), one pass per 16 columns.

@@ -90,6 +90,7 @@ SIGNATURES = {
     "dcg_matvec": (_I32, [_P, _P, _P, _PD]),
     "dcg_rbf_dtheta": (_I32, [_P, _P, _P, _I32, _PD]),
     "dcg_matvec_dense_noalloc": (_I32, [_P, _I64, _I64, _P, _P, _P, _P]),
+    "dcg_residual": (_I32, [_P, _P, _P, _P, _PD, _PD]),
     "dcg_apply_block": (_I32, [_P, _P, _I32, _P]),
     "dcg_sync": (_I32, [_P]),
     "dcg_debug_arm_barrier_timeout": (_I32, [_P, _I32]),

@@ -62,6 +62,15 @@ struct dcg_ctx {
   float* nsq = nullptr;      // n_pad
   float* vcol = nullptr;     // n_pad
   RbfParams* prm = nullptr;
+  // exact-form residual: transposed points, |x_i|^2 split on the anchor grid,
+  // per-split partial sums
+  float* XrT = nullptr;      // 64 x n_pad
+  double* n64 = nullptr;     // n_pad
+  unsigned int* nmax = nullptr;
+  float* nh = nullptr;       // n_pad
+  float* nl = nullptr;       // n_pad
+  float* resid_part = nullptr;  // 3 x resid_splits x n
+  int resid_splits = 1;
   float* pmv = nullptr;      // n_pad: padded copy of a caller's p (single-step matvec)
   float* pmvb = nullptr;     // rbf_block_nc() x n_pad: padded W columns of one multi-column pass
   double rbf_l = 0.0, rbf_s2 = 0.0, rbf_noise = 0.0;  // current hyperparameters (host copy)
@@ -302,7 +311,7 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
     const size_t bs = apply_block_scratch_floats(n, kMaxBlockCols, c->num_sms);
     if (bs) CKC(dalloc(c, &c->block_scratch, bs));
   }
-  CKC(dalloc(c, &c->mv_result, 1));
+  CKC(dalloc(c, &c->mv_result, 2));
   CKC(dalloc(c, &c->mv_ticket, 1));
   CKC(cudaMallocHost(&c->h_st, sizeof(DevState)));
   CKC(cudaMallocHost(&c->h_small, 4 * sizeof(int)));
@@ -356,9 +365,17 @@ extern "C" dcg_status dcg_set_operator_rbf(dcg_ctx* c, const float* X, int32_t d
     CK(dalloc(c, &c->prm, 1));
     CK(dalloc(c, &c->pmv, size_t(n_pad)));
     CK(dalloc(c, &c->pmvb, size_t(rbf_block_nc()) * n_pad));
+    c->resid_splits = rbf_resid_splits(n, c->num_sms);
+    CK(dalloc(c, &c->XrT, size_t(64) * n_pad));
+    CK(dalloc(c, &c->n64, size_t(n_pad)));
+    CK(dalloc(c, &c->nmax, 1));
+    CK(dalloc(c, &c->nh, size_t(n_pad)));
+    CK(dalloc(c, &c->nl, size_t(n_pad)));
+    CK(dalloc(c, &c->resid_part, size_t(3) * c->resid_splits * n));
   }
   CK(launch_rbf_prep(X, n, n_pad, d, xformat, c->Xr, c->Xt, c->nsq, c->stream));
-  CK(launch_rbf_params(c->nsq, n, n_pad, l, s2, noise, c->vcol, c->prm, c->stream));
+  CK(launch_rbf_anchor(c->Xr, n, n_pad, d, c->n64, c->nmax, c->prm, c->nh, c->nl, c->XrT, c->stream));
+  CK(launch_rbf_params(c->nsq, n, n_pad, d, l, s2, noise, c->vcol, c->prm, c->stream));
   CUtensorMap m;
   if (!make_rbf_tmap(&m, c->Xt, n_pad, xformat, d, enc)) return fail(c, DCG_ERR_INVALID_ARG, "tensor map encode failed");
   c->rbf_tmap = m;
@@ -378,7 +395,7 @@ extern "C" dcg_status dcg_set_rbf_params(dcg_ctx* c, double l, double s2, double
   if (!c) return DCG_ERR_INVALID_ARG;
   if (c->op != OP_RBF) return fail(c, DCG_ERR_STATE, "no matrix-free operator set");
   if (!(l > 0.0) || !(s2 > 0.0) || !(noise >= 0.0)) return fail(c, DCG_ERR_INVALID_ARG, "bad RBF parameters");
-  CK(launch_rbf_params(c->nsq, c->w.n, c->n_pad, l, s2, noise, c->vcol, c->prm, c->stream));
+  CK(launch_rbf_params(c->nsq, c->w.n, c->n_pad, c->rbf_d, l, s2, noise, c->vcol, c->prm, c->stream));
   c->rbf_l = l;
   c->rbf_s2 = s2;
   c->rbf_noise = noise;
@@ -503,27 +520,39 @@ static cudaError_t op_matvec(dcg_ctx* c, const float* p, float* q, double* resul
   return launch_rowop(&c->tmap, a, false, c->grid_rows, s);
 }
 
+// Arguments of the matrix-free exact-form residual shared by the solve and
+// dcg_residual.
+static RbfExactArgs rbf_resid_args(dcg_ctx* c) {
+  RbfExactArgs a{};
+  a.Xr = c->Xr;
+  a.XrT = c->XrT;
+  a.nh = c->nh;
+  a.nl = c->nl;
+  a.n = c->w.n;
+  a.n_pad = c->n_pad;
+  a.d = c->rbf_d;
+  a.prm = c->prm;
+  a.partials_f = c->resid_part;
+  a.partials = c->mv_partials;
+  return a;
+}
+
 // r = b - A x for the float64 iterate (compensated sums), with the state's
 // check / refinement bookkeeping; mode as in RowOpArgs::resid_mode.
 static cudaError_t op_resid(dcg_ctx* c, int mode, int skip_if_done, cudaStream_t s) {
   cudaError_t e = launch_split_x(c->w, c->grid_iter, skip_if_done, s);
   if (e != cudaSuccess) return e;
   if (c->op == OP_RBF) {
-    RbfExactArgs a{};
-    a.Xr = c->Xr;
-    a.n = c->w.n;
-    a.d = c->rbf_d;
-    a.prm = c->prm;
+    RbfExactArgs a = rbf_resid_args(c);
     a.xh = c->w.xh;
     a.xl = c->w.xl;
     a.b = c->w.b;
     a.r = c->w.r;
-    a.partials = c->mv_partials;
     a.ticket = &c->st->ticket[T_CHECK_RES];
     a.st = c->st;
     a.skip_if_done = skip_if_done;
     a.resid_mode = mode;
-    return launch_rbf_resid(a, s);
+    return launch_rbf_resid(a, c->resid_splits, s);
   }
   RowOpArgs a{};
   a.xh = c->w.xh;
@@ -985,6 +1014,46 @@ extern "C" dcg_status dcg_matvec(dcg_ctx* c, const float* p, float* q, double* p
     CK(cudaMemcpyAsync(pAp, c->mv_result, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_residual(dcg_ctx* c, const float* b, const double* x, float* r, double* rnorm2,
+                                   double* err) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  if (c->op == OP_NONE) return fail(c, DCG_ERR_STATE, "no operator set");
+  if (!b || !x || !r) return fail(c, DCG_ERR_INVALID_ARG, "b, x and r are required");
+  cudaStream_t s = c->stream;
+  // x goes through the solver's iterate buffer and its float32 split
+  CK(cudaMemcpyAsync(c->w.xd, x, size_t(c->w.n) * 8, cudaMemcpyDeviceToDevice, s));
+  CK(launch_split_x(c->w, c->grid_iter, 0, s));
+  CK(cudaMemsetAsync(c->mv_result, 0, 2 * sizeof(double), s));
+  if (c->op == OP_RBF) {
+    RbfExactArgs a = rbf_resid_args(c);
+    a.xh = c->w.xh;
+    a.xl = c->w.xl;
+    a.b = b;
+    a.r = r;
+    a.ticket = c->mv_ticket;
+    a.result = c->mv_result;
+    a.result_err = c->mv_result + 1;
+    CK(launch_rbf_resid(a, c->resid_splits, s));
+  } else {
+    RowOpArgs a{};
+    a.xh = c->w.xh;
+    a.xl = c->w.xl;
+    a.out = r;
+    a.b = b;
+    a.n = c->w.n;
+    a.partials = c->mv_partials;
+    a.ticket = c->mv_ticket;
+    a.result = c->mv_result;
+    CK(launch_rowop(&c->tmap, a, true, c->grid_rows, s));
+  }
+  double h[2] = {0.0, 0.0};
+  CK(cudaMemcpyAsync(h, c->mv_result, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (rnorm2) *rnorm2 = h[0];
+  if (err) *err = h[1];
   return DCG_OK;
 }
 

@@ -98,6 +98,9 @@ struct RbfParams {
   float neg_inv2l2_lo;  // its rounding error
   float s2_lo;       // s^2 - float(s^2)
   double noise_d;    // diagonal shift in double (residual recomputation)
+  float g_anchor;    // grid of the residual's distance sums (see k_rbf.cu)
+  float sigma_anchor;  // 1.5 2^23 g
+  float err_dist;    // distance part of the residual entries' error model (units of u^2)
 };
 
 struct RbfMvArgs {
@@ -121,8 +124,12 @@ struct RbfMvArgs {
 };
 
 struct RbfExactArgs {
-  const float* Xr;     // n x d rounded points
+  const float* Xr;     // n x d points of the operator
+  const float* XrT;    // residual: the points transposed, d x n_pad (zero padded)
+  const float* nh;     // residual: |x_i|^2 = nh + nl, nh on the anchor grid (n_pad)
+  const float* nl;
   int n;
+  int n_pad;
   int d;
   const RbfParams* prm;
   const float* xh;     // residual: x = xh + xl
@@ -132,9 +139,11 @@ struct RbfExactArgs {
   const float* V;      // block: n x ncols column-major
   float* Y;
   int ncols;
-  double* partials;
+  float* partials_f;   // residual: 3 x splits x n per-split sums
+  double* partials;    // residual: 2 x rows / 128 CTA sums
   unsigned int* ticket;
-  double* result;
+  double* result;      // residual without a state: |r|^2
+  double* result_err;  // residual without a state: the entry-error estimate of |r|
   DevState* st;
   int skip_if_done;
   int resid_mode;
@@ -161,8 +170,11 @@ cudaError_t launch_rbf_dtheta(const RbfDthetaArgs& a, cudaStream_t s);
 
 cudaError_t launch_rbf_prep(const float* X, int n, int n_pad, int d, int xformat, float* Xr, void* Xt, float* nsq,
                             cudaStream_t s);
-cudaError_t launch_rbf_params(const float* nsq, int n, int n_pad, double l, double s2, double noise, float* vcol,
-                              RbfParams* prm, cudaStream_t s);
+cudaError_t launch_rbf_params(const float* nsq, int n, int n_pad, int d, double l, double s2, double noise,
+                              float* vcol, RbfParams* prm, cudaStream_t s);
+cudaError_t launch_rbf_anchor(const float* Xr, int n, int n_pad, int d, double* n64, unsigned int* maxbits,
+                              RbfParams* prm, float* nh, float* nl, float* XrT, cudaStream_t s);
+int rbf_resid_splits(int n, int num_sms);
 bool make_rbf_tmap(CUtensorMap* map, const void* Xt, int n_pad, int xformat, int d, EncodeTiledFn encode);
 __host__ __device__ int rbf_row_bytes(int xformat, int d);
 cudaError_t rbf_mv_configure();
@@ -173,7 +185,7 @@ cudaError_t launch_copy_cols(const float* src, float* dst, int n, int64_t ldd, i
                              cudaStream_t s);
 cudaError_t launch_rbf_mv_block(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s);
 int rbf_block_nc();
-cudaError_t launch_rbf_resid(const RbfExactArgs& a, cudaStream_t s);
+cudaError_t launch_rbf_resid(const RbfExactArgs& a, int splits, cudaStream_t s);
 cudaError_t launch_rbf_block(const RbfExactArgs& a, int cmax, cudaStream_t s);
 
 // ---- dense operator (k_dense.cu)

@@ -77,8 +77,8 @@ __global__ void k_rbf_prep(const float* __restrict__ X, int n, int n_pad, int d,
 
 // v_j = -c nsq[j] (c = log2(e) / (2 l^2)); padded rows get -inf so that their
 // kernel values are exactly zero. Also writes the scalar parameters.
-__global__ void k_rbf_params(const float* nsq, int n, int n_pad, double l, double s2, double noise, float* vcol,
-                             RbfParams* prm) {
+__global__ void k_rbf_params(const float* nsq, int n, int n_pad, int d, double l, double s2, double noise,
+                             float* vcol, RbfParams* prm) {
   const double c = 1.4426950408889634 / (2.0 * l * l);
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_pad; j += gridDim.x * blockDim.x)
     vcol[j] = j < n ? float(-c * double(nsq[j])) : -INFINITY;
@@ -91,6 +91,9 @@ __global__ void k_rbf_params(const float* nsq, int n, int n_pad, double l, doubl
     prm->neg_inv2l2_lo = float(-1.0 / (2.0 * l * l) - double(prm->neg_inv2l2));
     prm->s2_lo = float(s2 - double(prm->s2));
     prm->noise_d = noise;
+    // distance part of the residual entries' error model (units of u^2,
+    // u = 2^-24): (0.87 d + 1) g / (2 l^2) / u, g the anchor grid
+    prm->err_dist = float((0.87 * d + 1.0) * double(prm->g_anchor) / (2.0 * l * l) * 16777216.0);
   }
 }
 
@@ -100,9 +103,9 @@ cudaError_t launch_rbf_prep(const float* X, int n, int n_pad, int d, int xformat
   return cudaGetLastError();
 }
 
-cudaError_t launch_rbf_params(const float* nsq, int n, int n_pad, double l, double s2, double noise, float* vcol,
-                              RbfParams* prm, cudaStream_t s) {
-  k_rbf_params<<<(n_pad + 255) / 256, 256, 0, s>>>(nsq, n, n_pad, l, s2, noise, vcol, prm);
+cudaError_t launch_rbf_params(const float* nsq, int n, int n_pad, int d, double l, double s2, double noise,
+                              float* vcol, RbfParams* prm, cudaStream_t s) {
+  k_rbf_params<<<(n_pad + 255) / 256, 256, 0, s>>>(nsq, n, n_pad, d, l, s2, noise, vcol, prm);
   return cudaGetLastError();
 }
 
@@ -459,25 +462,106 @@ cudaError_t launch_copy_cols(const float* src, float* dst, int n, int64_t ldd, i
 }
 
 // ---------------------------------------------------------------------------
-// Exact-form operator on CUDA cores: 128 rows per CTA (one per thread, x_i in
-// registers), J tiles of 64 points staged in shared memory.
-//   mode 0: r = b - A x (x = xh + xl, compensated Dot2 sums), |r|^2 reduced
-//   mode 1: Y[:, c] = A V[:, c] for c < ncols (<= 32 per launch column block)
+// Exact-form operator on CUDA cores (128 rows per CTA, one per thread, x_i in
+// registers; J tiles of 64 points staged in shared memory):
+//   * k_rbf_resid + k_rbf_resid_fin: r = b - A x for the float64 iterate
+//     x = xh + xl, the true residual of the refinement. Entries are float32
+//     pairs, the sums compensated (Dot2); the J range is split over grid.y so
+//     that the grid fills whole waves, and the finishing kernel merges the
+//     per-split pairs in a fixed order.
+//   * k_rbf_block: Y[:, c] = A V[:, c] (dcg_apply_block), entries to ~2 ulp.
+//
+// Distances of the residual kernel, Gram form D_ij = n_i + n_j - 2 G_ij with
+// G_ij = sum_m x_im x_jm summed onto a fixed grid (the error-free extraction
+// onto a grid of Rump, Ogita and Oishi, "Accurate floating-point summation",
+// SIAM J. Sci. Comput. 31, 2008): T starts at the anchor sigma = 1.5 2^23 g,
+// whose float32 neighbours are spaced g apart, and every partial sum of G is
+// below 2^22 g in magnitude (g = 2^(E - 22) with max_i |x_i|^2 < 2^E). Each
+// step T' = fma(x_im, x_jm, T) rounds the product onto the grid; the step
+// T' - T is exact (both lie in [2^23 g, 2^24 g)), and so is what the rounding
+// dropped, e = fma(x_im, x_jm, -(T' - T)), |e| <= g / 2 (BF16 and TF32
+// products fit in float32; for float32 points e carries one rounding of
+// size u g / 2). Hence G = (T - sigma) + sum_m e_m: the first part exact on
+// the grid, the second summed in float32. With |x_i|^2 = nh_i + nl_i, nh_i on
+// the grid, D_hi = nh_i + nh_j - 2 (T - sigma) is exact in float32 (all terms
+// are multiples of g below 2^24 g) and D_lo = nl_i + nl_j - 2 sum e carries
+// the rest. Two entries go through each packed f32x2 instruction: four per
+// coordinate and pair.
+//
+// Error model of one residual entry K_ij in units of u^2 = 2^-48:
+//   * distance: the float32 sum of the d remainders (each <= g/2, rounding
+//     errors growing like sqrt(d) u |sum e| ~ d u g / sqrt(12), taken three
+//     times for a probabilistic bound) and nl's rounding: relative error of
+//     K_ij <= (0.87 d + 1) g c / u with c = 1 / (2 l^2);
+//   * the exponent a = -D c as a pair (2 |a|), exp after Tang (emulated
+//     against 200-bit arithmetic over a in [-103, 0]: <= 2 + |a| from the
+//     exponent's own representation), the s^2 pair and one Dot2 step (~4).
+//   Relative error of the entry: <= (8 + 3 |a| + (0.87 d + 1) g c / u) u^2.
 // ---------------------------------------------------------------------------
 constexpr int EX_ROWS = 128;
-// Error model of one entry K_ij of the residual kernel, in units of
-// u^2 = 2^-48 (the float32-pair precision). The entry is carried as a float32
-// pair through every step: exact coordinate differences (TwoDiff), exact
-// squares (FMA), a compensated sum of d squares (relative error <= d u^2),
-// the exponent a = -D / (2 l^2) as a pair (2 u^2 |a|), exp after Tang
-// (emulated against 200-bit arithmetic over a in [-103, 0]: <= 2 u^2 + |a| u^2
-// from the exponent's own representation), then the s^2 pair and one Dot2
-// step (~4 u^2). Relative error of the entry: <= (8 + (d + 3) |a|) u^2.
 constexpr double kU2 = 3.552713678800501e-15;  // 2^-48
 constexpr float kEntryErrC0 = 8.f;
 constexpr int EX_J = 64;
 constexpr int EX_MAXD = 64;
 constexpr int EX_CB = 16;
+constexpr int EX_MAX_SPLITS = 16;  // J-range splits of the residual kernel (grid.y)
+// Smallest exponent the residual kernel evaluates: below it exp(a) < 1.7e-38
+// (near the smallest normal float32) and the entry is dropped, which changes
+// a row's sum by less than n 1.7e-38 max|x|. From a >= -87 the binary
+// exponent of exp_tang is >= -126, so 2^m is a normal float32.
+constexpr float kExpMinArg = -87.0f;
+
+// |x_i|^2 in float64 (exact squares, float64 sums) and the largest of them as
+// float bits rounded up (positive floats order like their bit patterns).
+__global__ void k_rbf_norms(const float* __restrict__ Xr, int n, int d, double* n64, unsigned int* maxbits) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double ss = 0.0;
+    for (int m = 0; m < d; ++m) {
+      const double v = Xr[int64_t(i) * d + m];
+      ss = fma(v, v, ss);
+    }
+    n64[i] = ss;
+    atomicMax(maxbits, __float_as_uint(__double2float_ru(ss)));
+  }
+}
+
+// The grid of the distance sums: g = 2^(E - 22) with max |x_i|^2 < 2^E,
+// sigma = 1.5 2^23 g; nh_i = |x_i|^2 rounded to a multiple of g (below
+// 2^24 g, so exact in float32), nl_i = the rest, rounded. Rows beyond n get
+// zeros. XrT: the points transposed (d x n_pad, zero padded) for coalesced
+// staging of the J tiles.
+__global__ void k_rbf_anchor(const double* __restrict__ n64, const float* __restrict__ Xr, int n, int n_pad, int d,
+                             const unsigned int* maxbits, RbfParams* prm, float* nh, float* nl, float* XrT) {
+  const float mx = __uint_as_float(*maxbits);
+  int E = 0;
+  frexpf(mx > 0.f ? mx : 1.f, &E);  // mx < 2^E
+  const double g = ldexp(1.0, E - 22);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    prm->g_anchor = float(g);
+    prm->sigma_anchor = float(1.5 * ldexp(1.0, 23) * g);
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x) {
+    float h = 0.f, l = 0.f;
+    if (i < n) {
+      const double q = rint(n64[i] / g);
+      h = float(q * g);
+      l = float(n64[i] - q * g);
+    }
+    nh[i] = h;
+    nl[i] = l;
+    for (int m = 0; m < d; ++m) XrT[int64_t(m) * n_pad + i] = i < n ? Xr[int64_t(i) * d + m] : 0.f;
+  }
+}
+
+cudaError_t launch_rbf_anchor(const float* Xr, int n, int n_pad, int d, double* n64, unsigned int* maxbits,
+                              RbfParams* prm, float* nh, float* nl, float* XrT, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(maxbits, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  k_rbf_norms<<<(n + 255) / 256, 256, 0, s>>>(Xr, n, d, n64, maxbits);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_rbf_anchor<<<(n_pad + 255) / 256, 256, 0, s>>>(n64, Xr, n, n_pad, d, maxbits, prm, nh, nl, XrT);
+  return cudaGetLastError();
+}
 
 __device__ __forceinline__ void two_sum_add(float& s, float& c, float v) {
   const float s2 = __fadd_rn(s, v);
@@ -538,126 +622,154 @@ __device__ __forceinline__ void exp_tang(float a_hi, float a_lo, const float2* t
   e_lo = __fadd_rn(__fmaf_rn(t.x, e1, -e_hi), __fmaf_rn(t.x, e1_lo, __fmul_rn(t.y, e1)));
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(EX_ROWS) k_rbf_exact(RbfExactArgs a) {
-  __shared__ float xj[EX_J][EX_MAXD + 1];
-  __shared__ float vj[EX_J][EX_CB + 1];
-  __shared__ float vlo[EX_J];
+// One grid step for two entries at once: T' = fma(x, y, T), e = the part of
+// x y the rounding onto the grid dropped, L += e (packed f32x2).
+__device__ __forceinline__ void anchored_step2(unsigned long long& T, unsigned long long& L, unsigned long long x,
+                                               unsigned long long y) {
+  unsigned long long Tn, ndt, e;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(Tn) : "l"(x), "l"(y), "l"(T));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(ndt) : "l"(T), "l"(Tn));  // -(T' - T), exact
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(e) : "l"(x), "l"(y), "l"(ndt));
+  asm("add.rn.f32x2 %0, %0, %1;" : "+l"(L) : "l"(e));
+  T = Tn;
+}
+
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+  return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
+}
+
+// Partial residual sums of one row over the J tiles of split blockIdx.y:
+// part[(y * 3 + 0) * n + i] = s, [1] = c (the Dot2 pair of sum_j K_ij x_j),
+// [2] = sum_j (e_ij K_ij x_j)^2 (entry-error estimate, units of u^2).
+template <int DMAX>
+__global__ void __launch_bounds__(EX_ROWS) k_rbf_resid(RbfExactArgs a) {
+  __shared__ __align__(16) float xs[DMAX][EX_J];
+  __shared__ __align__(16) float sh_xh[EX_J], sh_xl[EX_J], sh_nh[EX_J], sh_nl[EX_J];
   __shared__ float2 exp_tab[64];
-  if (MODE == 0 && threadIdx.x < 64) {
+  if (threadIdx.x < 64) {
     const double t = exp2(double(threadIdx.x) / 64.0);
     exp_tab[threadIdx.x] = make_float2(float(t), float(t - double(float(t))));
   }
   DevState* st = a.st;
   if (st && a.skip_if_done && st->done) return;
-  if (MODE == 0 && st && a.resid_mode == 0 && !st->warm_start) return;
-  const int n = a.n, d = a.d;
-  int ncols = a.ncols;
-  const float* V = a.V;
-  float* Y = a.Y;
-  if (MODE == 1 && st) {  // start of a solve: AW for the active columns of W
-    ncols = st->k;
-    V += n;
-    Y += n;
-  }
-  const int col0 = blockIdx.y * EX_CB;
-  if (MODE == 1 && col0 >= ncols) return;
-  const int cw = MODE == 1 ? min(EX_CB, ncols - col0) : 1;
+  if (st && a.resid_mode == 0 && !st->warm_start) return;
+  const int n = a.n, d = a.d, n_pad = a.n_pad;
   const int i = blockIdx.x * EX_ROWS + threadIdx.x;
-  const float neg_inv2l2 = a.prm->neg_inv2l2, neg_inv2l2_lo = a.prm->neg_inv2l2_lo;
-  const float s2 = a.prm->s2, s2_lo = a.prm->s2_lo, noise = a.prm->noise;
-  float xi[EX_MAXD];
+  const float k_hi = a.prm->neg_inv2l2, k_lo = a.prm->neg_inv2l2_lo;
+  const float s2 = a.prm->s2, s2_lo = a.prm->s2_lo;
+  const float sigma = a.prm->sigma_anchor;
+  const float err0 = kEntryErrC0 + a.prm->err_dist;
+  float xi[DMAX];
 #pragma unroll
-  for (int m = 0; m < EX_MAXD; ++m) xi[m] = (i < n && m < d) ? a.Xr[int64_t(i) * d + m] : 0.f;
-  static_assert(EX_MAXD == 64, "the distance loop is fully unrolled over 64 coordinates");
-  float acc[EX_CB], cmp[EX_CB];
-#pragma unroll
-  for (int c = 0; c < EX_CB; ++c) acc[c] = cmp[c] = 0.f;
-  float esq = 0.f;  // sum_j (e_ij K_ij x_j)^2, e_ij the entry's relative error in units of u^2
-  const float err_da = float(d + 3);
-  for (int j0 = 0; j0 < n; j0 += EX_J) {
+  for (int m = 0; m < DMAX; ++m) xi[m] = (i < n && m < d) ? a.XrT[int64_t(m) * n_pad + i] : 0.f;
+  const float nh_i = a.nh[min(i, n_pad - 1)], nl_i = a.nl[min(i, n_pad - 1)];
+  float acc = 0.f, cmp = 0.f, esq = 0.f;
+  // tiles of this split: J tiles t with t % gridDim.y == blockIdx.y
+  const int ntiles = (n + EX_J - 1) / EX_J;
+  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+    const int j0 = tile * EX_J;
     __syncthreads();
-    for (int idx = threadIdx.x; idx < EX_J * d; idx += EX_ROWS) {
-      const int jj = idx / d, m = idx % d;
-      xj[jj][m] = (j0 + jj < n) ? a.Xr[int64_t(j0 + jj) * d + m] : 0.f;
+    for (int idx = threadIdx.x; idx < d * (EX_J / 4); idx += EX_ROWS) {
+      const int m = idx / (EX_J / 4), q = idx % (EX_J / 4);
+      *reinterpret_cast<float4*>(&xs[m][4 * q]) =
+          *reinterpret_cast<const float4*>(a.XrT + int64_t(m) * n_pad + j0 + 4 * q);
     }
-    if (MODE == 0) {
-      for (int jj = threadIdx.x; jj < EX_J; jj += EX_ROWS) {
-        vj[jj][0] = (j0 + jj < n) ? a.xh[j0 + jj] : 0.f;
-        vlo[jj] = (j0 + jj < n) ? a.xl[j0 + jj] : 0.f;
-      }
-    } else {
-      for (int idx = threadIdx.x; idx < EX_J * EX_CB; idx += EX_ROWS) {
-        const int c = idx / EX_J, jj = idx % EX_J;
-        vj[jj][c] = (c < cw && j0 + jj < n) ? V[int64_t(col0 + c) * n + j0 + jj] : 0.f;
-      }
+    if (threadIdx.x < EX_J) {
+      const int j = j0 + threadIdx.x;
+      const bool in = j < n;
+      sh_xh[threadIdx.x] = in ? a.xh[j] : 0.f;
+      sh_xl[threadIdx.x] = in ? a.xl[j] : 0.f;
+      sh_nh[threadIdx.x] = a.nh[j];  // j < n_pad: zero beyond n
+      sh_nl[threadIdx.x] = a.nl[j];
     }
     __syncthreads();
     const int jn = min(EX_J, n - j0);
-    for (int jj = 0; jj < jn; ++jj) {
-      // |x_i - x_j|^2 as a float32 pair (exact differences by TwoDiff, exact
-      // squares by FMA, compensated sum)
-      float dh = 0.f, dl = 0.f;
+    for (int jq = 0; jq < jn; jq += 4) {
+      unsigned long long T01 = pk2(sigma, sigma), T23 = T01, L01 = 0ull, L23 = 0ull;
 #pragma unroll
-      for (int m = 0; m < EX_MAXD; ++m) {
+      for (int m = 0; m < DMAX; ++m) {
         if (m < d) {
-          const float u = xi[m], v = xj[jj][m];
-          const float df = __fsub_rn(u, v);
-          const float dz = __fsub_rn(df, u);
-          const float df_lo = __fadd_rn(__fsub_rn(u, __fsub_rn(df, dz)), __fsub_rn(-v, dz));
-          const float sq = __fmul_rn(df, df);
-          dl = __fadd_rn(dl, __fmaf_rn(2.f * df, df_lo, __fmaf_rn(df, df, -sq)));
-          const float hi = fmaxf(dh, sq), lo = fminf(dh, sq);
-          const float t = __fadd_rn(hi, lo);
-          dl = __fadd_rn(dl, __fsub_rn(lo, __fsub_rn(t, hi)));
-          dh = t;
+          const float4 x4 = *reinterpret_cast<const float4*>(&xs[m][jq]);
+          const unsigned long long xx = pk2(xi[m], xi[m]);
+          anchored_step2(T01, L01, xx, pk2(x4.x, x4.y));
+          anchored_step2(T23, L23, xx, pk2(x4.z, x4.w));
         }
       }
-      // exponent a = -(dh + dl) / (2 l^2) split as a_hi + a_lo (exact product
-      // error by FMA)
-      const float a_hi = __fmul_rn(dh, neg_inv2l2);
-      const float a_lo = __fmaf_rn(dh, neg_inv2l2, -a_hi) + dl * neg_inv2l2 + dh * neg_inv2l2_lo;
-      if (MODE == 0) {
-        // K = s^2 exp(a) as a float32 pair, then a Dot2 step with x = xh + xl
-        if (a_hi < -103.f) continue;  // below the float32 range: K = 0
+      const float Tv[4] = {__uint_as_float(unsigned(T01)), __uint_as_float(unsigned(T01 >> 32)),
+                           __uint_as_float(unsigned(T23)), __uint_as_float(unsigned(T23 >> 32))};
+      const float Lv[4] = {__uint_as_float(unsigned(L01)), __uint_as_float(unsigned(L01 >> 32)),
+                           __uint_as_float(unsigned(L23)), __uint_as_float(unsigned(L23 >> 32))};
+#pragma unroll
+      for (int e4 = 0; e4 < 4; ++e4) {
+        const int jj = jq + e4;
+        if (jj >= jn) break;
+        const float ghi = __fsub_rn(Tv[e4], sigma);                            // exact
+        const float dh = __fmaf_rn(-2.f, ghi, __fadd_rn(nh_i, sh_nh[jj]));   // exact
+        const float dl = __fmaf_rn(-2.f, Lv[e4], __fadd_rn(nl_i, sh_nl[jj]));
+        // exponent a = -(dh + dl) / (2 l^2) as a_hi + a_lo (exact product error by FMA)
+        const float a_hi = __fmul_rn(dh, k_hi);
+        const float a_lo = __fmaf_rn(dh, k_hi, -a_hi) + dl * k_hi + dh * k_lo;
+        // exp(a) < 2^-126 (K below the smallest normal float32): K = 0. Above
+        // it the binary exponent m of exp_tang lies in [-126, 0], and 2^m is
+        // a normal float32 built from its bits.
+        if (a_hi < kExpMinArg) continue;
         float e_hi, e_lo;
         int k2;
         exp_tang(a_hi, a_lo, exp_tab, e_hi, e_lo, k2);
         const float m_hi = __fmul_rn(s2, e_hi);
         const float m_lo = __fmaf_rn(s2, e_hi, -m_hi) + __fmaf_rn(s2, e_lo, s2_lo * e_hi);
-        const float k_hi = ldexpf(m_hi, k2), k_lo = ldexpf(m_lo, k2);
-        const float xhv = vj[jj][0];
-        const float p = __fmul_rn(k_hi, xhv);
-        const float e = __fmaf_rn(k_hi, xhv, -p);
-        two_sum_add(acc[0], cmp[0], p);
-        cmp[0] = __fadd_rn(cmp[0], e);
-        cmp[0] = __fmaf_rn(k_hi, vlo[jj], __fmaf_rn(k_lo, xhv, cmp[0]));
-        const float e_ij = fmaf(err_da, fabsf(a_hi), kEntryErrC0) * p;
+        const float scale = __int_as_float((k2 + 127) << 23);
+        const float kv_hi = __fmul_rn(m_hi, scale), kv_lo = __fmul_rn(m_lo, scale);
+        const float xhv = sh_xh[jj];
+        const float p = __fmul_rn(kv_hi, xhv);
+        const float pe = __fmaf_rn(kv_hi, xhv, -p);
+        two_sum_add(acc, cmp, p);
+        cmp = __fadd_rn(cmp, pe);
+        cmp = __fmaf_rn(kv_hi, sh_xl[jj], __fmaf_rn(kv_lo, xhv, cmp));
+        const float e_ij = fmaf(3.f, fabsf(a_hi), err0) * p;
         esq = fmaf(e_ij, e_ij, esq);
-      } else {
-        const float kij = s2 * expf(a_hi) * (1.f + a_lo);
-#pragma unroll
-        for (int c = 0; c < EX_CB; ++c) acc[c] = fmaf(kij, vj[jj][c], acc[c]);
       }
     }
   }
+  if (i < n) {
+    float* part = a.partials_f + int64_t(blockIdx.y) * 3 * n;
+    part[i] = acc;
+    part[n + i] = cmp;
+    part[2 * n + i] = esq;
+  }
+}
+
+// r_i = b_i - (A x)_i from the per-split pairs (merged in split order, so the
+// result does not depend on scheduling), |r|^2 and the entry-error sum
+// reduced by the last CTA, and the true-residual bookkeeping of the solve.
+__global__ void __launch_bounds__(EX_ROWS) k_rbf_resid_fin(RbfExactArgs a, int splits) {
+  DevState* st = a.st;
+  if (st && a.skip_if_done && st->done) return;
+  if (st && a.resid_mode == 0 && !st->warm_start) return;
+  const int n = a.n;
+  const int i = blockIdx.x * EX_ROWS + threadIdx.x;
   double my = 0.0, my_e = 0.0;
   if (i < n) {
-    if (MODE == 0) {
-      const double x = double(a.xh[i]) + double(a.xl[i]);
-      const double ax = double(acc[0]) + double(cmp[0]) + a.prm->noise_d * x;
-      const double rr = double(a.b[i]) - ax;
-      a.r[i] = float(rr);
-      my = rr * rr;
-      my_e = double(esq);
-    } else {
-#pragma unroll
-      for (int c = 0; c < EX_CB; ++c)
-        if (c < cw) Y[int64_t(col0 + c) * n + i] = acc[c] + noise * V[int64_t(col0 + c) * n + i];
+    float s = 0.f, c = 0.f;
+    double se = 0.0;
+    for (int y = 0; y < splits; ++y) {
+      const float* part = a.partials_f + int64_t(y) * 3 * n;
+      const float ps = part[i], pc = part[n + i];
+      const float t = __fadd_rn(s, ps);
+      const float z = __fsub_rn(t, s);
+      const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(ps, z));
+      s = t;
+      c = __fadd_rn(c, __fadd_rn(pc, err));
+      se += double(part[2 * n + i]);
     }
+    const double x = double(a.xh[i]) + double(a.xl[i]);
+    const double ax = double(s) + double(c) + a.prm->noise_d * x;
+    const double rr = double(a.b[i]) - ax;
+    a.r[i] = float(rr);
+    my = rr * rr;
+    my_e = se;
   }
-  if (MODE == 1) return;
-  // |r|^2 and e^2 = sum_ij (K_ij x_j)^2: CTA partials -> last CTA
+  // |r|^2 and e^2 = sum_ij (e_ij K_ij x_j)^2: CTA partials -> last CTA
   __shared__ double s_part[2][EX_ROWS / 32];
   const double v = warp_sum(my), ve = warp_sum(my_e);
   if ((threadIdx.x & 31) == 0) {
@@ -687,6 +799,7 @@ __global__ void __launch_bounds__(EX_ROWS) k_rbf_exact(RbfExactArgs a) {
     if (threadIdx.x == 0) {
       if (!st) {
         if (a.result) *a.result = s;
+        if (a.result_err) *a.result_err = 3.0 * kU2 * sqrt(se);
       } else if (a.resid_mode != 0) {
         // Entry K_ij carries a relative error <= e_ij u^2 (the model above).
         // The errors of different entries are independent, so the error of
@@ -712,6 +825,79 @@ __global__ void __launch_bounds__(EX_ROWS) k_rbf_exact(RbfExactArgs a) {
         }
       }
     }
+  }
+}
+
+// Y[:, c] = A V[:, c] for c < ncols, EX_CB columns per blockIdx.y: distances
+// in the difference form as float32 pairs (exact differences by TwoDiff,
+// exact squares by FMA, compensated sum), entries s^2 expf(a_hi) (1 + a_lo)
+// (~2 ulp).
+__global__ void __launch_bounds__(EX_ROWS) k_rbf_block(RbfExactArgs a) {
+  __shared__ float xj[EX_J][EX_MAXD + 1];
+  __shared__ float vj[EX_J][EX_CB + 1];
+  DevState* st = a.st;
+  if (st && a.skip_if_done && st->done) return;
+  const int n = a.n, d = a.d;
+  int ncols = a.ncols;
+  const float* V = a.V;
+  float* Y = a.Y;
+  if (st) {  // start of a solve: AW for the active columns of W
+    ncols = st->k;
+    V += n;
+    Y += n;
+  }
+  const int col0 = blockIdx.y * EX_CB;
+  if (col0 >= ncols) return;
+  const int cw = min(EX_CB, ncols - col0);
+  const int i = blockIdx.x * EX_ROWS + threadIdx.x;
+  const float neg_inv2l2 = a.prm->neg_inv2l2, neg_inv2l2_lo = a.prm->neg_inv2l2_lo;
+  const float s2 = a.prm->s2, noise = a.prm->noise;
+  float xi[EX_MAXD];
+#pragma unroll
+  for (int m = 0; m < EX_MAXD; ++m) xi[m] = (i < n && m < d) ? a.Xr[int64_t(i) * d + m] : 0.f;
+  float acc[EX_CB];
+#pragma unroll
+  for (int c = 0; c < EX_CB; ++c) acc[c] = 0.f;
+  for (int j0 = 0; j0 < n; j0 += EX_J) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < EX_J * d; idx += EX_ROWS) {
+      const int jj = idx / d, m = idx % d;
+      xj[jj][m] = (j0 + jj < n) ? a.Xr[int64_t(j0 + jj) * d + m] : 0.f;
+    }
+    for (int idx = threadIdx.x; idx < EX_J * EX_CB; idx += EX_ROWS) {
+      const int c = idx / EX_J, jj = idx % EX_J;
+      vj[jj][c] = (c < cw && j0 + jj < n) ? V[int64_t(col0 + c) * n + j0 + jj] : 0.f;
+    }
+    __syncthreads();
+    const int jn = min(EX_J, n - j0);
+    for (int jj = 0; jj < jn; ++jj) {
+      float dh = 0.f, dl = 0.f;
+#pragma unroll
+      for (int m = 0; m < EX_MAXD; ++m) {
+        if (m < d) {
+          const float u = xi[m], v = xj[jj][m];
+          const float df = __fsub_rn(u, v);
+          const float dz = __fsub_rn(df, u);
+          const float df_lo = __fadd_rn(__fsub_rn(u, __fsub_rn(df, dz)), __fsub_rn(-v, dz));
+          const float sq = __fmul_rn(df, df);
+          dl = __fadd_rn(dl, __fmaf_rn(2.f * df, df_lo, __fmaf_rn(df, df, -sq)));
+          const float hi = fmaxf(dh, sq), lo = fminf(dh, sq);
+          const float t = __fadd_rn(hi, lo);
+          dl = __fadd_rn(dl, __fsub_rn(lo, __fsub_rn(t, hi)));
+          dh = t;
+        }
+      }
+      const float a_hi = __fmul_rn(dh, neg_inv2l2);
+      const float a_lo = __fmaf_rn(dh, neg_inv2l2, -a_hi) + dl * neg_inv2l2 + dh * neg_inv2l2_lo;
+      const float kij = s2 * expf(a_hi) * (1.f + a_lo);
+#pragma unroll
+      for (int c = 0; c < EX_CB; ++c) acc[c] = fmaf(kij, vj[jj][c], acc[c]);
+    }
+  }
+  if (i < n) {
+#pragma unroll
+    for (int c = 0; c < EX_CB; ++c)
+      if (c < cw) Y[int64_t(col0 + c) * n + i] = acc[c] + noise * V[int64_t(col0 + c) * n + i];
   }
 }
 
@@ -838,17 +1024,36 @@ cudaError_t launch_rbf_dtheta(const RbfDthetaArgs& a, cudaStream_t s) {
 
 int rbf_exact_grid(int n) { return (n + EX_ROWS - 1) / EX_ROWS; }
 
-// dst[0, n) = src[0, n) for a column of W that is active in this solve; the
-// tail of dst (up to the 128-row tile) stays zero.
-cudaError_t launch_rbf_resid(const RbfExactArgs& a, cudaStream_t s) {
-  k_rbf_exact<0><<<rbf_exact_grid(a.n), EX_ROWS, 0, s>>>(a);
+// J-range splits of the residual kernel (grid.y): enough CTAs for about four
+// waves at four resident CTAs per SM, at most one split per J tile.
+int rbf_resid_splits(int n, int num_sms) {
+  const int rows = rbf_exact_grid(n);
+  const int ntiles = (n + EX_J - 1) / EX_J;
+  const int want = (16 * num_sms + rows - 1) / rows;
+  return max(1, min(min(want, EX_MAX_SPLITS), ntiles));
+}
+
+cudaError_t launch_rbf_resid(const RbfExactArgs& a, int splits, cudaStream_t s) {
+  if (splits < 1 || splits > EX_MAX_SPLITS || a.d < 1 || a.d > EX_MAXD) return cudaErrorInvalidValue;
+  const dim3 grid(rbf_exact_grid(a.n), splits);
+  if (a.d <= 8)
+    k_rbf_resid<8><<<grid, EX_ROWS, 0, s>>>(a);
+  else if (a.d <= 16)
+    k_rbf_resid<16><<<grid, EX_ROWS, 0, s>>>(a);
+  else if (a.d <= 32)
+    k_rbf_resid<32><<<grid, EX_ROWS, 0, s>>>(a);
+  else
+    k_rbf_resid<64><<<grid, EX_ROWS, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_rbf_resid_fin<<<rbf_exact_grid(a.n), EX_ROWS, 0, s>>>(a, splits);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rbf_block(const RbfExactArgs& a, int cmax, cudaStream_t s) {
   if (cmax <= 0) return cudaSuccess;
   dim3 grid(rbf_exact_grid(a.n), (cmax + EX_CB - 1) / EX_CB);
-  k_rbf_exact<1><<<grid, EX_ROWS, 0, s>>>(a);
+  k_rbf_block<<<grid, EX_ROWS, 0, s>>>(a);
   return cudaGetLastError();
 }
 

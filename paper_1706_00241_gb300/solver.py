@@ -244,6 +244,24 @@ class DefCG:
                                             P, out), "dcg_rbf_dtheta")
         return np.array(out[:], dtype=np.float64).reshape(P, 3)
 
+    def residual(self, b: torch.Tensor, x: torch.Tensor, r: torch.Tensor | None = None):
+        """True residual r = b - A x (float32 r, float64 x); returns
+        (r, |r|^2, entry-error estimate of |r|)."""
+        _dev_f32(b, "b")
+        _need_len(b, self.n, "b")
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+            raise TypeError("x must be a contiguous float64 CUDA tensor")
+        _need_len(x, self.n, "x")
+        if r is None:
+            r = torch.empty_like(b)
+        _dev_f32(r, "r")
+        _need_len(r, self.n, "r")
+        rr, err = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.dcg_residual(self._ctx, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                          ctypes.c_void_p(r.data_ptr()), ctypes.byref(rr), ctypes.byref(err)),
+                    "dcg_residual")
+        return r, rr.value, err.value
+
     def apply_block(self, V: torch.Tensor, Y: torch.Tensor | None = None) -> torch.Tensor:
         """Y = A V for a (c, n) tensor V (row j is column j), in one pass over A."""
         _dev_f32(V, "V")
