@@ -386,16 +386,21 @@ def kernel_arm(args):
     torch.cuda.set_device(0)
     B.build()
     stream = torch.cuda.current_stream()
-    if args.kernel == "gemv":
+    if args.kernel in ("gemv", "symv"):
         n = args.n or CFG.n
         X, bs = S.draw_sequence(CFG.scaled(n, T=1) if n != CFG.n else CFG, T=1)
         Xd = torch.tensor(X.astype(np.float32), device="cuda")
         A = torch.empty((n, n), dtype=torch.float32, device="cuda")
         P.form_rbf_dense(Xd, CFG.lengthscale(0), CFG.signal_var, CFG.noise, out=A)
         solver = P.DefCG(n, 0, 0, CFG.tol)
-        solver.set_operator_dense(A)
-        algo = 4.0 * n * n + 8.0 * n
-        name = "k_rowop_tma<false> (q = A p, fused p^T q)"
+        sym = args.kernel == "symv"
+        solver.set_operator_dense(A, symmetric=sym)
+        if sym:   # the upper triangle with its diagonal, p read, q written
+            algo = 2.0 * n * (n + 1) + 8.0 * n
+            name = "k_symv_tma + k_symv_fin (q = A p from the upper triangle, fused p^T q)"
+        else:
+            algo = 4.0 * n * n + 8.0 * n
+            name = "k_rowop_tma<false> (q = A p, fused p^T q)"
         unit, bound = "GB/s", "hbm"
         peak, kind = peaks()
         workload = f"stored dense fp32 n={n}"
@@ -630,7 +635,7 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the solve's kernels from the host instead of one CUDA graph "
                          "(profiling mode: ncu cannot list kernels inside conditional graphs)")
-    ap.add_argument("--kernel", choices=["gemv", "rbf_mv", "apply_block", "form", "iter"], default=None,
+    ap.add_argument("--kernel", choices=["gemv", "symv", "rbf_mv", "apply_block", "form", "iter"], default=None,
                     help="time one hot kernel alone (q = A p) instead of the sequence")
     ap.add_argument("--n", type=int, default=0, help="system size for --kernel (default: the workload's)")
     ap.add_argument("--systems", type=int, default=0,

@@ -164,12 +164,29 @@ dcg_status dcg_destroy(dcg_ctx* ctx);
  * Errors: INVALID_ARG (NULL, misaligned, lda < n or lda % 4 != 0), CUDA. */
 dcg_status dcg_set_operator_dense(dcg_ctx* ctx, const float* A, int64_t lda);
 
+/* Symmetric stored operator given by its upper triangle: as
+ * dcg_set_operator_dense, but the operator is the symmetric matrix whose
+ * entries A[i*lda + j], j >= i, are read (the strictly lower triangle is never
+ * read by the matvec). The matvec of the solve then streams about half of the
+ * 4 n^2 bytes: tiles on or right of the diagonal, each contributing A_ij p_j
+ * to q_i and, right of the diagonal blocks, A_ij p_i to q_j (the stored
+ * operator of Eq. 1 is symmetric positive definite, as Algorithm 1 assumes).
+ * The true residual (convergence test and replacement) reads the full
+ * matrix, so A must be exactly symmetric (dcg_form_rbf_dense writes it so).
+ * Scratch: (8 ceil(n / 2048) + ceil(n / 128)) n floats of partial sums,
+ * allocated by the first call on a context (24 MB at n = 16384).
+ * Errors: INVALID_ARG (NULL, misaligned, lda < n or lda % 4 != 0), NOMEM, CUDA. */
+dcg_status dcg_set_operator_dense_sym(dcg_ctx* ctx, const float* A, int64_t lda);
+
 /* Matrix-free RBF operator A = K + noise I, K_ij = signal_var *
  * exp(-|x_i - x_j|^2 / (2 lengthscale^2)) (Sec. 3 kernel).
  *   X        device, row-major float32 n x d (row i is x_i); copied into the
  *            context's own padded buffer in the requested format, so X is
  *            not borrowed.
- *   d        1 <= d <= 64.
+ *   d        1 <= d <= 61 (BF16) or 1 <= d <= 29 (TF32): a tile row holds
+ *            the d coordinates and three pieces of -|x_j|^2 / 2 in 128 bytes,
+ *            so that the tensor-core product x_i . x_j - |x_j|^2 / 2 gives each
+ *            entry's exponent with one FMA.
  *   xformat  dcg_xformat; fixes how X_I X_J^T tiles are formed on the tensor
  *            cores (the operator is the one defined by the rounded X).
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */

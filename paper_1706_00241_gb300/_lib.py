@@ -77,6 +77,7 @@ SIGNATURES = {
     "dcg_create": (_I32, [ctypes.POINTER(DcgConfig), _P, ctypes.POINTER(_P)]),
     "dcg_destroy": (_I32, [_P]),
     "dcg_set_operator_dense": (_I32, [_P, _P, _I64]),
+    "dcg_set_operator_dense_sym": (_I32, [_P, _P, _I64]),
     "dcg_set_operator_rbf": (_I32, [_P, _P, _I32, _I32, _D, _D, _D]),
     "dcg_set_rbf_params": (_I32, [_P, _D, _D, _D]),
     "dcg_form_rbf_dense": (_I32, [_P, _I64, _I32, _D, _D, _D, _P, _I64, _P]),

@@ -68,7 +68,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
-        run([exe, *ARCH, "-shared", "-o", LIB, *objs])
+        # -z defs: every symbol must resolve at link time (a launcher missing
+        # from its translation unit fails the build, not the first call)
+        run([exe, *ARCH, "-shared", "-Xlinker", "-z,defs", "-o", LIB, *objs])
     return LIB
 
 

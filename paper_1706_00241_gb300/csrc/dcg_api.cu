@@ -48,6 +48,11 @@ struct dcg_ctx {
   int last_iters = 0;
 
   int test_barrier_polls = 0;  // > 0: the next solve withholds a grid-barrier arrival (test hook)
+  bool dense_sym = false;      // stored operator given as its upper triangle (symmetric matvec)
+  float* sym_rowpart = nullptr;
+  float* sym_colpart = nullptr;
+  int* sym_sched = nullptr;        // per-CTA item lists of the symmetric matvec: offsets, then items
+  int* sym_sched_items = nullptr;
 
   // operator
   int op = OP_NONE;
@@ -77,7 +82,7 @@ struct dcg_ctx {
   double* dth_partials = nullptr;  // derivative forms: 3 * kMaxDthetaPairs per CTA
   double* dth_out = nullptr;       // 3 * kMaxDthetaPairs
   unsigned int* dth_ticket = nullptr;
-  CUtensorMap rbf_tmap;
+  CUtensorMap rbf_tmap[2];   // tile copies of the points: I-tile rows, J-tile rows
   int rbf_grid = 1;
 
   // split-K partials of the block product
@@ -243,6 +248,7 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   CKC(cudaEventCreate(&c->ev1));
   CKC(cudaEventCreate(&c->ev2));
   CKC(rowop_configure());
+  CKC(symv_configure());
   CKC(apply_block_configure());
   CKC(iter_configure());
   CKC(rbf_mv_configure());
@@ -306,7 +312,8 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   CKC(dalloc(c, &c->ritz_status, 1));
   CKC(dalloc(c, &c->ritz_part, gram_partials_doubles(n, mm, c->num_sms)));
   CKC(dalloc(c, &c->mv_partials,
-              2 * size_t(std::max(std::max(c->grid_rows, 2 * c->num_sms), rbf_exact_grid(n))) + 2));
+              2 * size_t(std::max(std::max(c->grid_rows, 2 * c->num_sms),
+                                  std::max(rbf_exact_grid(n), symv_fin_grid(n, c->num_sms)))) + 2));
   {
     const size_t bs = apply_block_scratch_floats(n, kMaxBlockCols, c->num_sms);
     if (bs) CKC(dalloc(c, &c->block_scratch, bs));
@@ -325,14 +332,26 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
 // ---------------------------------------------------------------------------
 // Operators
 // ---------------------------------------------------------------------------
-extern "C" dcg_status dcg_set_operator_dense(dcg_ctx* c, const float* A, int64_t lda) {
+static dcg_status set_dense(dcg_ctx* c, const float* A, int64_t lda, bool sym) {
   if (!c) return DCG_ERR_INVALID_ARG;
   if (!A) return fail(c, DCG_ERR_INVALID_ARG, "A is NULL");
   if (lda < c->cfg.n || (lda % 4) != 0) return fail(c, DCG_ERR_INVALID_ARG, "lda must be >= n and a multiple of 4");
   if ((reinterpret_cast<uintptr_t>(A) & 15) != 0) return fail(c, DCG_ERR_INVALID_ARG, "A must be 16-byte aligned");
   EncodeTiledFn enc = get_encode();
   if (!enc) return fail(c, DCG_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-  const bool same = (c->op == OP_DENSE && c->A == A && c->lda == lda);
+  if (sym && !c->sym_rowpart) {
+    CK(dalloc(c, &c->sym_rowpart, symv_rowpart_floats(c->w.n)));
+    CK(dalloc(c, &c->sym_colpart, symv_colpart_floats(c->w.n)));
+    std::vector<int> off, items;
+    symv_schedule(c->w.n, c->num_sms, off, items);
+    CK(dalloc(c, &c->sym_sched, off.size() + items.size()));
+    CK(cudaMemcpyAsync(c->sym_sched, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->sym_sched + off.size(), items.data(), items.size() * sizeof(int),
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->sym_sched_items = c->sym_sched + off.size();
+  }
+  const bool same = (c->op == OP_DENSE && c->A == A && c->lda == lda && c->dense_sym == sym);
   if (!same) {
     CUtensorMap m;
     if (!make_rowop_tmap(&m, A, c->cfg.n, lda, enc)) return fail(c, DCG_ERR_INVALID_ARG, "tensor map encode failed");
@@ -340,9 +359,18 @@ extern "C" dcg_status dcg_set_operator_dense(dcg_ctx* c, const float* A, int64_t
     c->A = A;
     c->lda = lda;
     c->op = OP_DENSE;
+    c->dense_sym = sym;
     destroy_graph(c);
   }
   return DCG_OK;
+}
+
+extern "C" dcg_status dcg_set_operator_dense(dcg_ctx* c, const float* A, int64_t lda) {
+  return set_dense(c, A, lda, false);
+}
+
+extern "C" dcg_status dcg_set_operator_dense_sym(dcg_ctx* c, const float* A, int64_t lda) {
+  return set_dense(c, A, lda, true);
 }
 
 extern "C" dcg_status dcg_set_operator_rbf(dcg_ctx* c, const float* X, int32_t d, int32_t xformat, double l,
@@ -352,14 +380,15 @@ extern "C" dcg_status dcg_set_operator_rbf(dcg_ctx* c, const float* X, int32_t d
   if (!(l > 0.0) || !(s2 > 0.0) || !(noise >= 0.0)) return fail(c, DCG_ERR_INVALID_ARG, "bad RBF parameters");
   if (xformat != DCG_X_BF16 && xformat != DCG_X_TF32)
     return fail(c, DCG_ERR_UNSUPPORTED, "matrix-free operator: xformat BF16 or TF32 in this build");
-  if (d < 1 || d > (xformat == DCG_X_BF16 ? 64 : 32))
-    return fail(c, DCG_ERR_UNSUPPORTED, "matrix-free operator: d <= 64 (BF16) or d <= 32 (TF32)");
+  if (d < 1 || d > rbf_max_d(xformat))
+    return fail(c, DCG_ERR_UNSUPPORTED, "matrix-free operator: d <= " + std::to_string(rbf_max_d(DCG_X_BF16)) +
+                                            " (BF16) or d <= " + std::to_string(rbf_max_d(DCG_X_TF32)) + " (TF32)");
   EncodeTiledFn enc = get_encode();
   if (!enc) return fail(c, DCG_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   const int n = c->w.n, n_pad = c->n_pad;
   if (!c->Xr) {
     CK(dalloc(c, &c->Xr, size_t(n) * 64));
-    CK(dalloc(c, reinterpret_cast<unsigned char**>(&c->Xt), size_t(n_pad) * 128));
+    CK(dalloc(c, reinterpret_cast<unsigned char**>(&c->Xt), size_t(2) * n_pad * 128));
     CK(dalloc(c, &c->nsq, size_t(n_pad)));
     CK(dalloc(c, &c->vcol, size_t(n_pad)));
     CK(dalloc(c, &c->prm, 1));
@@ -376,9 +405,10 @@ extern "C" dcg_status dcg_set_operator_rbf(dcg_ctx* c, const float* X, int32_t d
   CK(launch_rbf_prep(X, n, n_pad, d, xformat, c->Xr, c->Xt, c->nsq, c->stream));
   CK(launch_rbf_anchor(c->Xr, n, n_pad, d, c->n64, c->nmax, c->prm, c->nh, c->nl, c->XrT, c->stream));
   CK(launch_rbf_params(c->nsq, n, n_pad, d, l, s2, noise, c->vcol, c->prm, c->stream));
-  CUtensorMap m;
-  if (!make_rbf_tmap(&m, c->Xt, n_pad, xformat, d, enc)) return fail(c, DCG_ERR_INVALID_ARG, "tensor map encode failed");
-  c->rbf_tmap = m;
+  CUtensorMap m[2];
+  if (!make_rbf_tmap(m, c->Xt, n_pad, xformat, d, enc)) return fail(c, DCG_ERR_INVALID_ARG, "tensor map encode failed");
+  c->rbf_tmap[0] = m[0];
+  c->rbf_tmap[1] = m[1];
   c->rbf_d = d;
   c->rbf_xformat = xformat;
   c->rbf_l = l;
@@ -506,7 +536,23 @@ static cudaError_t op_matvec(dcg_ctx* c, const float* p, float* q, double* resul
     a.st = st;
     a.skip_if_done = st ? 1 : 0;
     a.col_idx = -1;
-    return launch_rbf_mv(&c->rbf_tmap, a, c->rbf_grid, s);
+    return launch_rbf_mv(c->rbf_tmap, a, c->rbf_grid, s);
+  }
+  if (c->dense_sym) {
+    SymvArgs a{};
+    a.p = p;
+    a.q = q;
+    a.n = c->w.n;
+    a.rowpart = c->sym_rowpart;
+    a.colpart = c->sym_colpart;
+    a.sched_off = c->sym_sched;
+    a.sched_items = c->sym_sched_items;
+    a.partials = partials;
+    a.ticket = ticket;
+    a.result = result;
+    a.st = st;
+    a.skip_if_done = st ? 1 : 0;
+    return launch_symv(&c->tmap, a, c->num_sms, s);
   }
   RowOpArgs a{};
   a.v = p;
@@ -594,7 +640,7 @@ static cudaError_t op_block(dcg_ctx* c, const float* V, int ncols, float* Y, Dev
       a.st = st;
       a.skip_if_done = 1;
       a.col_idx = col0;
-      if ((e = launch_rbf_mv_block(&c->rbf_tmap, a, c->rbf_grid, s)) != cudaSuccess) return e;
+      if ((e = launch_rbf_mv_block(c->rbf_tmap, a, c->rbf_grid, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
   }

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <type_traits>
+#include <vector>
 
 #include "dcg_common.cuh"
 
@@ -75,6 +76,24 @@ struct RowOpArgs {
   int* abort_word;       // without a state (context-free matvec): set to the wait site
                          // when a bounded wait gives up; the CTA's rows of out and
                          // *result are then NaN. May be null.
+};
+
+// Symmetric stored matvec (upper triangle read once): see k_dense.cu.
+struct SymvArgs {
+  const float* p;
+  float* q;
+  int n;
+  int nbands;          // set by launch_symv
+  int nchunks;         // set by launch_symv
+  float* rowpart;      // symv_rowpart_floats(n)
+  float* colpart;      // symv_colpart_floats(n)
+  const int* sched_off;    // per-CTA item lists (symv_schedule), device
+  const int* sched_items;
+  double* partials;    // >= symv_fin_grid(n) doubles
+  unsigned int* ticket;
+  double* result;      // p^T q
+  DevState* st;
+  int skip_if_done;
 };
 
 struct ApplyBlockArgs {
@@ -175,11 +194,12 @@ cudaError_t launch_rbf_params(const float* nsq, int n, int n_pad, int d, double 
 cudaError_t launch_rbf_anchor(const float* Xr, int n, int n_pad, int d, double* n64, unsigned int* maxbits,
                               RbfParams* prm, float* nh, float* nl, float* XrT, cudaStream_t s);
 int rbf_resid_splits(int n, int num_sms);
-bool make_rbf_tmap(CUtensorMap* map, const void* Xt, int n_pad, int xformat, int d, EncodeTiledFn encode);
+bool make_rbf_tmap(CUtensorMap* map, const void* Xt, int n_pad, int xformat, int d, EncodeTiledFn encode);  // map[2]
+int rbf_max_d(int xformat);
 __host__ __device__ int rbf_row_bytes(int xformat, int d);
 cudaError_t rbf_mv_configure();
 int rbf_mv_grid(int n_tiles, int num_sms);
-cudaError_t launch_rbf_mv(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_rbf_mv(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s);  // tmap[2]
 int rbf_exact_grid(int n);
 cudaError_t launch_copy_cols(const float* src, float* dst, int n, int64_t ldd, int col0, int nc, const DevState* st,
                              cudaStream_t s);
@@ -193,6 +213,12 @@ cudaError_t rowop_configure();
 int rowop_grid(int n, int num_sms);
 bool make_rowop_tmap(CUtensorMap* map, const float* A, int64_t n, int64_t lda, EncodeTiledFn encode);
 cudaError_t launch_rowop(const CUtensorMap* tmap, const RowOpArgs& a, bool resid, int grid, cudaStream_t s);
+size_t symv_rowpart_floats(int n);
+size_t symv_colpart_floats(int n);
+int symv_fin_grid(int n, int num_sms);
+cudaError_t symv_configure();
+cudaError_t launch_symv(const CUtensorMap* tmap, SymvArgs a, int num_sms, cudaStream_t s);
+void symv_schedule(int n, int ctas, std::vector<int>& off, std::vector<int>& items);
 // Context-free q = A p on the library's fixed scratch (no allocation).
 int noalloc_max_ctas();
 cudaError_t noalloc_scratch(void** base);

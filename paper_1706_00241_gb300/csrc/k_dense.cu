@@ -10,6 +10,7 @@
 //   * k_form_rbf: A = K + noise I for the Sec. 3 RBF kernel.
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "dcg_kernels.cuh"
 
@@ -364,6 +365,345 @@ cudaError_t rowop_configure() {
 int rowop_grid(int n, int num_sms) {
   const int ngroups = (n + RB_ROWS - 1) / RB_ROWS;
   return ngroups < num_sms ? ngroups : num_sms;
+}
+
+// ---------------------------------------------------------------------------
+// Symmetric stored matvec q = A p reading the upper triangle only (entries
+// j >= i), about half of the 4 n^2 bytes of the full GEMV: the stored kernel
+// is HBM-bound, so the bytes are the time.
+//   Work item (b, c): rows [64 b, 64 b + 64) (a band) x the columns of chunk
+//   c ([2048 c, 2048 c + 2048)) at or right of column 64 b; only the TMA
+//   boxes (256 columns x 8 rows) that reach column 64 b are loaded. The items
+//   are unequal (those on the diagonal load fewer boxes) and every CTA gets a
+//   list built on the host by longest-processing-time assignment (within ~2 %
+//   of the mean at n = 16384; a plain round robin over the triangle left some
+//   CTAs twice the mean).
+//   Element (i, j), j >= 64 b: the row sum takes A_ij p_j when j >= i, and
+//   the transposed contribution A_ij p_i goes to q_j when j > i. The masks
+//   matter only in stages whose rows meet the thread's columns (the band's
+//   diagonal block); elsewhere either both apply or, left of the band start,
+//   neither (p_j is zero there).
+//   A thread owns 8 columns of the chunk: its transposed sums over the band's
+//   64 rows stay in registers and need no reduction (colpart[b n + j]). Each
+//   consumer warp reduces the row sums of its 256 columns over its lanes; the
+//   last warp to finish a stage (a shared counter per slot) adds the 8 warps'
+//   values (rowpart[c n + i]). No warp waits for another, so a bounded wait
+//   that gives up in one warp cannot leave the others waiting. k_symv_fin adds
+//   the partials in a fixed order (deterministic):
+//   q_i = sum_{c >= c0(b_i)} rowpart + sum_{b <= b_i} colpart, and p^T q.
+// ---------------------------------------------------------------------------
+constexpr int SY_H = 64;                   // rows per band: 8 row groups
+constexpr int SY_GROUPS = SY_H / RB_ROWS;
+
+__device__ __forceinline__ int symv_c_lo(int b) { return (b * SY_H) / RB_CHUNK; }
+
+// Row and column contributions of 4 consecutive columns j0 .. j0 + 3 of one
+// box row (row i): rows use p_j (zero left of the band), columns use p_i.
+// With MASK, only entries j >= i enter the row sum and j > i the columns.
+template <bool MASK>
+__device__ __forceinline__ void symv_quad(const float4 av, const float* pj, float pi, int i, int j0, float& racc,
+                                          float* colacc) {
+  const float a4[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (MASK) {
+      const int j = j0 + e;
+      racc = fmaf(j >= i ? a4[e] : 0.f, pj[e], racc);
+      colacc[e] = fmaf(j > i ? a4[e] : 0.f, pi, colacc[e]);
+    } else {
+      racc = fmaf(a4[e], pj[e], racc);
+      colacc[e] = fmaf(a4[e], pi, colacc[e]);
+    }
+  }
+}
+
+// Sums of 8 per-lane values over the warp (reduce-scatter by halving):
+// afterwards lanes with (lane & 3) == 0 hold in v[0] the warp's sum of value
+// (lane >> 2) & 7. Nine shuffles instead of 8 x 5.
+__device__ __forceinline__ float warp_sum8_scatter(float (&v)[8], int lane) {
+#pragma unroll
+  for (int m = 4, sft = 16; m >= 1; m >>= 1, sft >>= 1) {
+    const bool up = (lane & sft) != 0;
+#pragma unroll
+    for (int i = 0; i < m; ++i) {
+      const float send = up ? v[i] : v[i + m];
+      const float keep = up ? v[i + m] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
+    }
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  return v[0];
+}
+
+__global__ void __launch_bounds__(RB_THREADS, 1) k_symv_tma(const __grid_constant__ CUtensorMap tmap, SymvArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  float* tiles = reinterpret_cast<float*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(RB_STAGES) * RB_STAGE_BYTES);
+  uint64_t* empty = full + RB_STAGES;
+  // row sums of a stage: one value per warp and row, summed by the last warp
+  // to arrive (a counter per slot; no warp waits for another)
+  __shared__ float red[RB_STAGES][RB_CONSUMER_WARPS][RB_ROWS];
+  __shared__ unsigned int red_cnt[RB_STAGES];
+  __shared__ int s_abort;
+  __shared__ int s_issued;
+  __shared__ int s_consumed[RB_CONSUMER_WARPS];
+
+  DevState* st = a.st;
+  if (st && a.skip_if_done && st->done) return;
+  const int n = a.n, nc = a.nchunks;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < RB_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], RB_CONSUMER_WARPS);
+    }
+    fence_mbarrier_init();
+    s_abort = 0;
+    s_issued = 0;
+    for (int s = 0; s < RB_STAGES; ++s) red_cnt[s] = 0u;
+  }
+  __syncthreads();
+
+  if (warp == RB_CONSUMER_WARPS) {
+    // ---------------- producer: one elected lane issues the TMA boxes -------
+    if (lane == 0) {
+      prefetch_tensormap(&tmap);
+      const uint64_t pol = l2_policy_evict_first();
+      int it = 0;
+      bool stop = false;
+      for (int t = a.sched_off[blockIdx.x]; t < a.sched_off[blockIdx.x + 1] && !stop; ++t) {
+        const int b = a.sched_items[t] / nc, c = a.sched_items[t] % nc;
+        const int bx_lo = max(0, (b * SY_H - c * RB_CHUNK) / RB_BOXW);
+        const int bx_hi = min(RB_BOXES, (n - c * RB_CHUNK + RB_BOXW - 1) / RB_BOXW);
+        for (int g = 0; g < SY_GROUPS; ++g, ++it) {
+          if (b * SY_H + g * RB_ROWS >= n) break;  // row groups past n (last band)
+          const int s = it % RB_STAGES;
+          if (it >= RB_STAGES && !mbar_wait_bounded(&empty[s], ((it / RB_STAGES) - 1) & 1)) {
+            s_abort = 1;
+            stop = true;
+            break;
+          }
+          if (*(volatile int*)&s_abort) {
+            stop = true;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[s], uint32_t(bx_hi - bx_lo) * RB_ROWS * RB_BOXW * 4);
+          for (int bx = bx_lo; bx < bx_hi; ++bx)
+            tma_load_2d_hint(tiles + size_t(s) * RB_STAGE_FLOATS + bx * RB_ROWS * RB_BOXW, &tmap, &full[s],
+                             c * RB_CHUNK + bx * RB_BOXW, b * SY_H + g * RB_ROWS, pol);
+        }
+      }
+      s_issued = it;
+    }
+  } else {
+    // ---------------- consumers: warp w owns box w of every stage -----------
+    int it = 0;
+    bool stop = false;
+    for (int t = a.sched_off[blockIdx.x]; t < a.sched_off[blockIdx.x + 1] && !stop; ++t) {
+      const int b = a.sched_items[t] / nc, c = a.sched_items[t] % nc;
+      const int bx_lo = max(0, (b * SY_H - c * RB_CHUNK) / RB_BOXW);
+      const int bx_hi = min(RB_BOXES, (n - c * RB_CHUNK + RB_BOXW - 1) / RB_BOXW);
+      const bool active = warp >= bx_lo && warp < bx_hi;
+      const int row_lo = b * SY_H;
+      const int jbase = c * RB_CHUNK + warp * RB_BOXW + 4 * lane;  // columns jbase + 128 h + e
+      float pj[8];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int j = jbase + 128 * h + e;
+          pj[4 * h + e] = (j >= row_lo && j < n) ? __ldg(a.p + j) : 0.f;
+        }
+      float colacc[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) colacc[e] = 0.f;
+      for (int g = 0; g < SY_GROUPS; ++g, ++it) {
+        const int row0 = row_lo + g * RB_ROWS;
+        if (row0 >= n) break;  // row groups past n (last band): not loaded
+        const int s = it % RB_STAGES;
+        float prow[RB_ROWS];
+#pragma unroll
+        for (int r = 0; r < RB_ROWS; ++r) prow[r] = row0 + r < n ? __ldg(a.p + row0 + r) : 0.f;
+        if (!mbar_wait_bounded(&full[s], (it / RB_STAGES) & 1)) {
+          s_abort = 1;
+          stop = true;
+          break;
+        }
+        float racc[RB_ROWS];
+#pragma unroll
+        for (int r = 0; r < RB_ROWS; ++r) racc[r] = 0.f;
+        if (active) {
+          const float* box = tiles + size_t(s) * RB_STAGE_FLOATS + warp * RB_ROWS * RB_BOXW;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int j0 = jbase + 128 * h;
+            if (j0 > row0 + RB_ROWS - 1) {       // right of every row of the stage
+#pragma unroll
+              for (int r = 0; r < RB_ROWS; ++r)
+                symv_quad<false>(reinterpret_cast<const float4*>(box + r * RB_BOXW)[lane + 32 * h], pj + 4 * h,
+                                 prow[r], row0 + r, j0, racc[r], colacc + 4 * h);
+            } else if (j0 + 3 >= row0) {         // meets the stage's rows: masks
+#pragma unroll
+              for (int r = 0; r < RB_ROWS; ++r)
+                symv_quad<true>(reinterpret_cast<const float4*>(box + r * RB_BOXW)[lane + 32 * h], pj + 4 * h,
+                                prow[r], row0 + r, j0, racc[r], colacc + 4 * h);
+            }                                    // else: left of every row, nothing
+          }
+        }
+        // row sums of this warp's 256 columns for the stage's 8 rows
+        const float v = warp_sum8_scatter(racc, lane);
+        if ((lane & 3) == 0) red[s][warp][lane >> 2] = v;
+        __syncwarp();
+        unsigned int last = 0u;
+        if (lane == 0) {
+          __threadfence_block();
+          last = atomicAdd(&red_cnt[s], 1u) == RB_CONSUMER_WARPS - 1 ? 1u : 0u;
+          if (last) {
+            __threadfence_block();
+            red_cnt[s] = 0u;
+          }
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last && lane < RB_ROWS && row0 + lane < n) {
+          __threadfence_block();
+          float t = 0.f;
+#pragma unroll
+          for (int w = 0; w < RB_CONSUMER_WARPS; ++w) t += *reinterpret_cast<volatile float*>(&red[s][w][lane]);
+          a.rowpart[int64_t(c) * n + row0 + lane] = t;
+        }
+        // the slot (tile and row sums) is released only now: the producer
+        // refills it, and the warps reuse its row-sum buffer, after every
+        // warp has finished this stage
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+      }
+      if (stop) break;
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int j = jbase + 128 * h + e;
+          if (j >= row_lo && j < n) a.colpart[int64_t(b) * n + j] = colacc[4 * h + e];
+        }
+    }
+    if (lane == 0) s_consumed[warp] = it;
+  }
+  __syncthreads();
+  // Drain: after a timeout, wait (bounded) for boxes still in flight.
+  if (s_abort && threadIdx.x == 0) {
+    int lo = s_issued;
+    for (int w = 0; w < RB_CONSUMER_WARPS; ++w) lo = min(lo, s_consumed[w]);
+    for (int it = lo; it < s_issued; ++it) mbar_wait_bounded(&full[it % RB_STAGES], (it / RB_STAGES) & 1);
+    record_timeout(st, 1);
+  }
+}
+
+// q_i = sum_{c >= c0(b_i)} rowpart[c n + i] + sum_{b <= b_i} colpart[b n + i]
+// and p^T q. A CTA takes 32 consecutive rows (lane = row) and its 8 warps
+// split the partial list of those rows (warp w: entries w, w + 8, ...), so
+// every load is one coalesced 128-byte line and many are in flight; the
+// warps' sums are combined in shared memory in a fixed order (the result
+// does not depend on scheduling). Float32 sums over at most
+// n / 64 + n / 2048 + 1 terms, four interleaved accumulators per thread.
+constexpr int SYF_ROWS = 32;  // rows per CTA of the finishing kernel (256 threads)
+static_assert(SY_H % SYF_ROWS == 0, "the rows of a finishing CTA lie in one band");
+__global__ void __launch_bounds__(256) k_symv_fin(SymvArgs a) {
+  DevState* st = a.st;
+  if (st && a.skip_if_done && st->done) return;
+  const int n = a.n, nc = a.nchunks;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row0 = blockIdx.x * SYF_ROWS;
+  const int i = row0 + lane;
+  // the CTA's rows share their band unless a band boundary falls inside the
+  // 32 rows (SY_H is a multiple of 32): one partial list for all of them
+  const int b = row0 / SY_H;
+  const int c0 = symv_c_lo(b);
+  const int nr = nc - c0, total = nr + b + 1;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  if (i < n) {
+#pragma unroll 4
+    for (int t = warp; t < total; t += 8) {
+      const float* src = t < nr ? a.rowpart + int64_t(c0 + t) * n : a.colpart + int64_t(t - nr) * n;
+      acc[(t >> 3) & 3] += src[i];
+    }
+  }
+  __shared__ float red[8][SYF_ROWS];
+  red[warp][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  __syncthreads();
+  double my = 0.0;
+  if (warp == 0 && i < n) {
+    float q = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) q += red[w][lane];
+    a.q[i] = q;
+    my = double(a.p[i]) * double(q);
+  }
+  __shared__ double s_part;
+  if (warp == 0) {
+    const double v = warp_sum(my);
+    if (lane == 0) s_part = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) a.partials[blockIdx.x] = s_part;
+  if (!arrive_last(a.ticket)) return;
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int j = threadIdx.x; j < int(gridDim.x); j += 32) t += __ldcg(a.partials + j);
+    t = warp_sum(t);
+    if (threadIdx.x == 0 && a.result) *a.result = t;
+  }
+}
+
+size_t symv_rowpart_floats(int n) { return size_t((n + RB_CHUNK - 1) / RB_CHUNK) * n; }
+size_t symv_colpart_floats(int n) { return size_t((n + SY_H - 1) / SY_H) * n; }
+int symv_fin_grid(int n, int) { return (n + SYF_ROWS - 1) / SYF_ROWS; }
+
+cudaError_t symv_configure() {
+  return cudaFuncSetAttribute(k_symv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(RB_SMEM));
+}
+
+// Work items (b, c) of the symmetric matvec and their assignment to `ctas`
+// CTAs: longest processing time first (the cost of an item is the boxes it
+// loads times its row groups), each item to the least loaded CTA.
+// off[g] .. off[g + 1] index the items of CTA g in `items` (b * nchunks + c).
+void symv_schedule(int n, int ctas, std::vector<int>& off, std::vector<int>& items) {
+  const int nb = (n + SY_H - 1) / SY_H, nc = (n + RB_CHUNK - 1) / RB_CHUNK;
+  std::vector<std::pair<long long, int>> all;  // (cost, item)
+  for (int b = 0; b < nb; ++b)
+    for (int c = (b * SY_H) / RB_CHUNK; c < nc; ++c) {
+      const int bx_lo = std::max(0, (b * SY_H - c * RB_CHUNK) / RB_BOXW);
+      const int bx_hi = std::min(RB_BOXES, (n - c * RB_CHUNK + RB_BOXW - 1) / RB_BOXW);
+      const int groups = (std::min(SY_H, n - b * SY_H) + RB_ROWS - 1) / RB_ROWS;
+      all.push_back({(long long)(bx_hi - bx_lo) * groups, b * nc + c});
+    }
+  std::stable_sort(all.begin(), all.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+  std::vector<long long> load(ctas, 0);
+  std::vector<std::vector<int>> per(ctas);
+  for (const auto& it : all) {
+    int g = 0;
+    for (int h = 1; h < ctas; ++h)
+      if (load[h] < load[g]) g = h;
+    load[g] += it.first;
+    per[g].push_back(it.second);
+  }
+  off.assign(1, 0);
+  items.clear();
+  for (int g = 0; g < ctas; ++g) {
+    items.insert(items.end(), per[g].begin(), per[g].end());
+    off.push_back(int(items.size()));
+  }
+}
+
+cudaError_t launch_symv(const CUtensorMap* tmap, SymvArgs a, int num_sms, cudaStream_t s) {
+  a.nbands = (a.n + SY_H - 1) / SY_H;
+  a.nchunks = (a.n + RB_CHUNK - 1) / RB_CHUNK;
+  k_symv_tma<<<num_sms, RB_THREADS, RB_SMEM, s>>>(*tmap, a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_symv_fin<<<symv_fin_grid(a.n, num_sms), 256, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -2,13 +2,14 @@
 // (the Sec. 3 kernel), never stored.
 //
 //   * k_rbf_mv<1>: q = A p with the fused p^T q (Algorithm 1).
-//     Persistent, warp-specialised: a TMA warp streams X_J tiles (128 rows,
-//     swizzled) with p_J and v_J = -c |x_j|^2 by bulk copies; one thread
-//     issues tcgen05.mma (BF16 or TF32 inputs, float32 accumulation) for
-//     S = X_I X_J^T into one of four TMEM buffers; sixteen epilogue warps read
-//     S with tcgen05.ld and accumulate q_i += exp2(u_i + v_j + 2c S_ij) p_j
-//     with the exponential on the SFU (ex2.approx), c = log2(e) / (2 l^2),
-//     u_i = log2(s^2) - c |x_i|^2. Padded columns carry v_j = -inf (K = 0).
+//     Persistent, warp-specialised: a TMA warp streams J tiles (128 rows,
+//     swizzled) with p_J by a bulk copy; one thread issues tcgen05.mma (BF16
+//     or TF32 inputs, float32 accumulation) for S~ = [X_I, 1] [X_J, -|x_j|^2/2]^T
+//     into one of four TMEM buffers; sixteen epilogue warps read S~ with
+//     tcgen05.ld and accumulate q_i += exp2(2c S~_ij + u_i) p_j with the
+//     exponential on the SFU (ex2.approx), c = log2(e) / (2 l^2),
+//     u_i = log2(s^2) - c |x_i|^2: one packed FMA per two exponents. Padded
+//     columns carry -|x_j|^2/2 = -2^100 (K = 0).
 //   * k_rbf_mv<8>: the start-of-solve product A W, eight columns of W per
 //     pass, each entry's exponential formed once and contracted with all
 //     eight (the same entries as the loop's matvec).
@@ -41,42 +42,68 @@ __device__ __forceinline__ float round_tf32(float x) {
   return __uint_as_float(u);
 }
 
-// Xr (n x d float32): X rounded to the chosen element format; Xt: the
-// 128-byte-per-row tile copy (BF16: 64 elements, TF32: 32 elements), zero
-// padded to n_pad rows; nsq[i] = |xr_i|^2 (float64 sum, rounded).
+// Xr (n x d float32): X rounded to the chosen element format. Xt: two
+// 128-byte-per-row tile copies (BF16: 64 elements, TF32: 32 elements) of
+// n_pad rows each, the operands of the tensor-core product
+//   S~_ij = x_i . x_j - |x_j|^2 / 2,
+// so that the exponent of an entry is one FMA, 2c S~_ij + (log2 s^2 - c |x_i|^2)
+// with c = log2(e) / (2 l^2), and S~ does not depend on l:
+//   rows of the first copy (I tiles):  [x_i, 1, 1, 1, 0 ...]
+//   rows of the second copy (J tiles): [x_j, h_j, m_j, l_j, 0 ...], h + m + l =
+//     -|x_j|^2 / 2 split into three pieces of the element format (24 bits for
+//     BF16, 33 for TF32); padding rows j >= n carry h = -2^100, so that their
+//     entries vanish.
+// nsq[i] = |xr_i|^2 (float64 sum, rounded).
+constexpr int kRbfAug = 3;  // extra coordinates of the tile copies
 __global__ void k_rbf_prep(const float* __restrict__ X, int n, int n_pad, int d, int xformat, float* Xr,
                            void* Xt, float* nsq) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x) {
     double ss = 0.0;
+    float v[64];
+    const int width = xformat == DCG_X_BF16 ? 64 : 32;
+    for (int m = 0; m < width; ++m) {
+      float x = 0.f;
+      if (i < n && m < d) {
+        x = xformat == DCG_X_BF16 ? round_bf16(X[int64_t(i) * d + m]) : round_tf32(X[int64_t(i) * d + m]);
+        Xr[int64_t(i) * d + m] = x;
+        ss += double(x) * double(x);
+      }
+      v[m] = x;
+    }
+    // -|x_i|^2 / 2 in three pieces of the element format
+    float piece[kRbfAug];
+    double rest = -0.5 * ss;
+    for (int k = 0; k < kRbfAug; ++k) {
+      piece[k] = xformat == DCG_X_BF16 ? round_bf16(float(rest)) : round_tf32(float(rest));
+      rest -= double(piece[k]);
+    }
+    if (i >= n) {
+      piece[0] = -0x1p100f;
+      piece[1] = piece[2] = 0.f;
+    }
     if (xformat == DCG_X_BF16) {
-      __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xt) + int64_t(i) * 64;
+      __nv_bfloat16* ra = reinterpret_cast<__nv_bfloat16*>(Xt) + int64_t(i) * 64;
+      __nv_bfloat16* rb = reinterpret_cast<__nv_bfloat16*>(Xt) + int64_t(n_pad + i) * 64;
       for (int m = 0; m < 64; ++m) {
-        float v = 0.f;
-        if (i < n && m < d) {
-          v = round_bf16(X[int64_t(i) * d + m]);
-          Xr[int64_t(i) * d + m] = v;
-          ss += double(v) * double(v);
-        }
-        row[m] = __float2bfloat16_rn(v);
+        const bool aug = m >= d && m < d + kRbfAug;
+        ra[m] = __float2bfloat16_rn(aug ? 1.f : v[m]);
+        rb[m] = __float2bfloat16_rn(aug ? piece[m - d] : v[m]);
       }
     } else {
-      float* row = reinterpret_cast<float*>(Xt) + int64_t(i) * 32;
+      float* ra = reinterpret_cast<float*>(Xt) + int64_t(i) * 32;
+      float* rb = reinterpret_cast<float*>(Xt) + int64_t(n_pad + i) * 32;
       for (int m = 0; m < 32; ++m) {
-        float v = 0.f;
-        if (i < n && m < d) {
-          v = round_tf32(X[int64_t(i) * d + m]);
-          Xr[int64_t(i) * d + m] = v;
-          ss += double(v) * double(v);
-        }
-        row[m] = v;
+        const bool aug = m >= d && m < d + kRbfAug;
+        ra[m] = aug ? 1.f : v[m];
+        rb[m] = aug ? piece[m - d] : v[m];
       }
     }
     nsq[i] = float(ss);
   }
 }
 
-// v_j = -c nsq[j] (c = log2(e) / (2 l^2)); padded rows get -inf so that their
-// kernel values are exactly zero. Also writes the scalar parameters.
+// vcol[i] = -c nsq[i] (c = log2(e) / (2 l^2)), the row term of the exponent
+// (padded rows: -inf). Also writes the scalar parameters.
 __global__ void k_rbf_params(const float* nsq, int n, int n_pad, int d, double l, double s2, double noise,
                              float* vcol, RbfParams* prm) {
   const double c = 1.4426950408889634 / (2.0 * l * l);
@@ -118,7 +145,23 @@ __host__ __device__ int rbf_row_bytes(int xformat, int d) {
   return bytes <= 32 ? 32 : (bytes <= 64 ? 64 : 128);
 }
 
+static bool make_rbf_tmap_one(CUtensorMap* map, const void* Xt, int n_pad, int xformat, int d,
+                              EncodeTiledFn encode);
+
+// Tensor maps of the two tile copies (map[0]: I-tile rows, map[1]: J-tile
+// rows), boxes of 128 rows x the row bytes the MMA reads (d + kRbfAug
+// coordinates).
 bool make_rbf_tmap(CUtensorMap* map, const void* Xt, int n_pad, int xformat, int d, EncodeTiledFn encode) {
+  for (int half = 0; half < 2; ++half) {
+    const void* base = static_cast<const unsigned char*>(Xt) + size_t(half) * n_pad * 128;
+    if (!make_rbf_tmap_one(&map[half], base, n_pad, xformat, d + kRbfAug, encode)) return false;
+  }
+  return true;
+}
+
+int rbf_max_d(int xformat) { return (xformat == DCG_X_BF16 ? 64 : 32) - kRbfAug; }
+
+static bool make_rbf_tmap_one(CUtensorMap* map, const void* Xt, int n_pad, int xformat, int d, EncodeTiledFn encode) {
   const bool bf = xformat == DCG_X_BF16;
   const int row_bytes = rbf_row_bytes(xformat, d);
   const int esize = bf ? 2 : 4;
@@ -150,12 +193,32 @@ constexpr int MV_TMEM_COLS = MV_TBUF * MV_TILE;  // all 512 columns: one CTA per
 // the swizzled X tiles
 constexpr int MV_BLOCK_NC = 8;  // columns per pass of the multi-column product
 __host__ __device__ constexpr int mv_stage_bytes(int nc) {
-  return (MV_TILE_BYTES + (nc + 1) * MV_TILE * 4 + 1023) / 1024 * 1024;
+  return (MV_TILE_BYTES + nc * MV_TILE * 4 + 1023) / 1024 * 1024;
 }
 __host__ __device__ constexpr size_t mv_smem(int nc) {
   return 1024 + MV_TILE_BYTES + size_t(MV_STAGES) * mv_stage_bytes(nc) + 256;
 }
 constexpr size_t MV_SMEM = mv_smem(1);
+
+// 16 entries of one row (lane) of the matvec epilogue: exponents from the
+// Gram values h (float bits) as 2c S~ + u in packed pairs, exponentials on the
+// SFU, contraction with p_j into two packed sums (entries j = 0, 1 mod 4 and
+// 2, 3 mod 4).
+__device__ __forceinline__ void mv_half(const uint32_t (&h)[16], const float* pj, unsigned long long c2x2,
+                                        unsigned long long uu, unsigned long long& sA, unsigned long long& sB) {
+#pragma unroll
+  for (int j = 0; j < 16; j += 4) {
+    const float4 p4 = *reinterpret_cast<const float4*>(pj + j);
+    const unsigned long long g01 =
+        tc::f2fma(c2x2, tc::f2pk(__uint_as_float(h[j + 0]), __uint_as_float(h[j + 1])), uu);
+    const unsigned long long g23 =
+        tc::f2fma(c2x2, tc::f2pk(__uint_as_float(h[j + 2]), __uint_as_float(h[j + 3])), uu);
+    const unsigned long long e01 = tc::f2pk(tc::ex2_approx(tc::f2lo(g01)), tc::ex2_approx(tc::f2hi(g01)));
+    const unsigned long long e23 = tc::f2pk(tc::ex2_approx(tc::f2lo(g23)), tc::ex2_approx(tc::f2hi(g23)));
+    sA = tc::f2fma(e01, tc::f2pk(p4.x, p4.y), sA);
+    sB = tc::f2fma(e23, tc::f2pk(p4.z, p4.w), sB);
+  }
+}
 
 // NC = 1: q = A p with the fused p^T q. NC > 1 (the start-of-solve product):
 // Y[:, col0 + c] = A V[:, col0 + c] for the NC columns of a group, each
@@ -163,7 +226,7 @@ constexpr size_t MV_SMEM = mv_smem(1);
 // (columns at or beyond k are read but not written).
 template <int NC>
 __global__ void __launch_bounds__(MV_THREADS, 1)
-    k_rbf_mv(const __grid_constant__ CUtensorMap tmap, RbfMvArgs a) {
+    k_rbf_mv(const __grid_constant__ CUtensorMap tmap_i, const __grid_constant__ CUtensorMap tmap_j, RbfMvArgs a) {
   constexpr int MV_STAGE_BYTES = mv_stage_bytes(NC);
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -189,8 +252,9 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = a.n, n_tiles = a.n_tiles;
   const int kind_tf32 = a.xformat != DCG_X_BF16;
-  const int ksteps = kind_tf32 ? (a.d + 7) / 8 : (a.d + 15) / 16;   // 32-byte K steps
-  const uint32_t row_bytes = uint32_t(rbf_row_bytes(a.xformat, a.d));
+  const int dk = a.d + kRbfAug;                                     // coordinates of the tile rows
+  const int ksteps = kind_tf32 ? (dk + 7) / 8 : (dk + 15) / 16;     // 32-byte K steps
+  const uint32_t row_bytes = uint32_t(rbf_row_bytes(a.xformat, dk));
   const uint32_t tile_bytes = MV_TILE * row_bytes;                  // bytes of one X tile in use
   const uint32_t idesc = tc::instr_desc(kind_tf32 ? tc::kFmtTF32 : tc::kFmtBF16, MV_TILE, MV_TILE);
 
@@ -218,13 +282,14 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
   if (warp == 0) {
     // -------------------------------- producer ------------------------------
     if (lane == 0) {
-      prefetch_tensormap(&tmap);
+      prefetch_tensormap(&tmap_i);
+      prefetch_tensormap(&tmap_j);
       long long it = 0;
       int rbc = 0;
       for (int rb = blockIdx.x; rb < n_tiles && !s_abort; rb += gridDim.x, ++rbc) {
         if (rbc > 0 && !mbar_wait_bounded(xi_empty, (rbc - 1) & 1)) { s_abort = 1; break; }
         mbar_arrive_expect_tx(xi_full, tile_bytes);
-        tma_load_2d(xi_tile, &tmap, xi_full, 0, rb * MV_TILE);
+        tma_load_2d(xi_tile, &tmap_i, xi_full, 0, rb * MV_TILE);
         for (int J = 0; J < n_tiles; ++J, ++it) {
           const int s = int(it % MV_STAGES);
           if (it >= MV_STAGES && !mbar_wait_bounded(&empty[s], uint32_t((it / MV_STAGES) - 1) & 1)) {
@@ -232,14 +297,12 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
             break;
           }
           unsigned char* stg = stages + size_t(s) * MV_STAGE_BYTES;
-          mbar_arrive_expect_tx(&full[s], tile_bytes + (NC + 1) * MV_TILE * 4);
-          tma_load_2d(stg, &tmap, &full[s], 0, J * MV_TILE);
+          mbar_arrive_expect_tx(&full[s], tile_bytes + NC * MV_TILE * 4);
+          tma_load_2d(stg, &tmap_j, &full[s], 0, J * MV_TILE);
 #pragma unroll 1
           for (int c = 0; c < NC; ++c)
             tc::bulk_load(stg + MV_TILE_BYTES + c * MV_TILE * 4, a.p + size_t(c) * a.ldp + size_t(J) * MV_TILE,
                           MV_TILE * 4, &full[s]);
-          tc::bulk_load(stg + MV_TILE_BYTES + NC * MV_TILE * 4, a.vcol + size_t(J) * MV_TILE, MV_TILE * 4,
-                        &full[s]);
         }
       }
     }
@@ -286,11 +349,67 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
     long long it = 0;
     for (int rb = blockIdx.x; rb < n_tiles; rb += gridDim.x) {
       const int row = rb * MV_TILE + row_l;
+      // exponent of an entry: c2 S~_ij + u_i, u_i = log2 s^2 - c |x_i|^2
       const float u = l2s + a.vcol[row];        // vcol has n_pad entries
       float acc[NC], comp[NC];                  // Kahan sums of per-tile partials
 #pragma unroll
       for (int c = 0; c < NC; ++c) acc[c] = comp[c] = 0.f;
       bool aborted = false;
+      if constexpr (NC == 1) {
+        // Software-pipelined in half slices of 16 columns: the TMEM load of
+        // the next half (or of the next tile's first half) is in flight while
+        // the current half is processed.
+        const unsigned long long c2x2 = tc::f2pk(c2, c2), uu = tc::f2pk(u, u);
+        const uint32_t lane_off = uint32_t(quarter * 32) << 16;
+        uint32_t ha[16], hb[16];
+        {
+          const int b = int(it % MV_TBUF);
+          if (!mbar_wait_bounded(&tfull[b], uint32_t(it / MV_TBUF) & 1)) {
+            s_abort = 1;
+            aborted = true;
+          } else {
+            tc::fence_after_sync();
+            tc::tmem_ld16_nowait(tmem + lane_off + uint32_t(b * MV_TILE + slice * 32), ha);
+            tc::tmem_wait_ld16(ha);
+          }
+        }
+        for (int J = 0; J < n_tiles && !aborted; ++J, ++it) {
+          const int s = int(it % MV_STAGES);
+          const int b = int(it % MV_TBUF);
+          const float* pj =
+              reinterpret_cast<const float*>(stages + size_t(s) * MV_STAGE_BYTES + MV_TILE_BYTES) + slice * 32;
+          tc::tmem_ld16_nowait(tmem + lane_off + uint32_t(b * MV_TILE + slice * 32 + 16), hb);
+          unsigned long long s0 = 0ull, s1 = 0ull, s2 = 0ull, s3 = 0ull;
+          mv_half(ha, pj, c2x2, uu, s0, s1);
+          tc::tmem_wait_ld16(hb);
+          // the whole slice is in registers: the accumulator goes back to the
+          // MMA warp (the stage with p is released after the math)
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[b]);
+          const bool next = J + 1 < n_tiles;
+          if (next) {
+            const int b2 = int((it + 1) % MV_TBUF);
+            if (!mbar_wait_bounded(&tfull[b2], uint32_t((it + 1) / MV_TBUF) & 1)) {
+              s_abort = 1;
+              aborted = true;
+            } else {
+              tc::fence_after_sync();
+              tc::tmem_ld16_nowait(tmem + lane_off + uint32_t(b2 * MV_TILE + slice * 32), ha);
+            }
+          }
+          mv_half(hb, pj + 16, c2x2, uu, s2, s3);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[s]);
+          if (next && !aborted) tc::tmem_wait_ld16(ha);
+          const float part = ((tc::f2lo(s0) + tc::f2hi(s0)) + (tc::f2lo(s1) + tc::f2hi(s1))) +
+                             ((tc::f2lo(s2) + tc::f2hi(s2)) + (tc::f2lo(s3) + tc::f2hi(s3)));
+          const float y = part - comp[0];
+          const float t = acc[0] + y;
+          comp[0] = (t - acc[0]) - y;
+          acc[0] = t;
+        }
+      } else {
       for (int J = 0; J < n_tiles; ++J, ++it) {
         const int s = int(it % MV_STAGES);
         const int b = int(it % MV_TBUF);
@@ -298,39 +417,16 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
         tc::fence_after_sync();
         const unsigned char* stg = stages + size_t(s) * MV_STAGE_BYTES;
         const float* pj = reinterpret_cast<const float*>(stg + MV_TILE_BYTES) + slice * 32;
-        const float* vj = reinterpret_cast<const float*>(stg + MV_TILE_BYTES + NC * MV_TILE * 4) + slice * 32;
         float sv[32];
         tc::tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * MV_TILE + slice * 32), sv);
         // the values are in registers: hand the accumulator back to the MMA
-        // warp before the math (the stage with p and v is released after it)
+        // warp before the math (the stage with p is released after it)
         tc::fence_before_sync();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[b]);
-        if constexpr (NC == 1) {
-          float pa = 0.f, pb = 0.f, pc = 0.f, pd = 0.f;
+        {
 #pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            const float4 p4 = *reinterpret_cast<const float4*>(pj + j);
-            const float4 v4 = *reinterpret_cast<const float4*>(vj + j);
-            pa = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 0], u + v4.x)), p4.x, pa);
-            pb = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 1], u + v4.y)), p4.y, pb);
-            pc = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 2], u + v4.z)), p4.z, pc);
-            pd = fmaf(tc::ex2_approx(fmaf(c2, sv[j + 3], u + v4.w)), p4.w, pd);
-          }
-          const float part = (pa + pb) + (pc + pd);
-          const float y = part - comp[0];
-          const float t = acc[0] + y;
-          comp[0] = (t - acc[0]) - y;
-          acc[0] = t;
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; j += 4) {  // the entries, once
-            const float4 v4 = *reinterpret_cast<const float4*>(vj + j);
-            sv[j + 0] = tc::ex2_approx(fmaf(c2, sv[j + 0], u + v4.x));
-            sv[j + 1] = tc::ex2_approx(fmaf(c2, sv[j + 1], u + v4.y));
-            sv[j + 2] = tc::ex2_approx(fmaf(c2, sv[j + 2], u + v4.z));
-            sv[j + 3] = tc::ex2_approx(fmaf(c2, sv[j + 3], u + v4.w));
-          }
+          for (int j = 0; j < 32; ++j) sv[j] = tc::ex2_approx(fmaf(c2, sv[j], u));  // the entries, once
 #pragma unroll
           for (int c = 0; c < NC; ++c) {  // contracted with every column
             const float* pc = pj + c * MV_TILE;
@@ -356,6 +452,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
+      }
       }
       if (aborted) break;
       // combine the four column slices of each row (named barrier: epilogue warps)
@@ -422,7 +519,7 @@ cudaError_t rbf_mv_configure() {
 int rbf_mv_grid(int n_tiles, int num_sms) { return n_tiles < num_sms ? n_tiles : num_sms; }
 
 cudaError_t launch_rbf_mv(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s) {
-  k_rbf_mv<1><<<grid, MV_THREADS, MV_SMEM, s>>>(*tmap, a);
+  k_rbf_mv<1><<<grid, MV_THREADS, MV_SMEM, s>>>(tmap[0], tmap[1], a);
   return cudaGetLastError();
 }
 
@@ -434,7 +531,7 @@ int rbf_block_nc() { return MV_BLOCK_NC; }
 // to write (a.col_idx = col0 with a solver state: the pass is skipped when
 // col0 >= k, and columns at or beyond k are not written).
 cudaError_t launch_rbf_mv_block(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s) {
-  k_rbf_mv<MV_BLOCK_NC><<<grid, MV_THREADS, mv_smem(MV_BLOCK_NC), s>>>(*tmap, a);
+  k_rbf_mv<MV_BLOCK_NC><<<grid, MV_THREADS, mv_smem(MV_BLOCK_NC), s>>>(tmap[0], tmap[1], a);
   return cudaGetLastError();
 }
 
@@ -634,10 +731,6 @@ __device__ __forceinline__ void anchored_step2(unsigned long long& T, unsigned l
   T = Tn;
 }
 
-__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
-  return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
-}
-
 // Partial residual sums of one row over the J tiles of split blockIdx.y:
 // part[(y * 3 + 0) * n + i] = s, [1] = c (the Dot2 pair of sum_j K_ij x_j),
 // [2] = sum_j (e_ij K_ij x_j)^2 (entry-error estimate, units of u^2).
@@ -685,14 +778,14 @@ __global__ void __launch_bounds__(EX_ROWS) k_rbf_resid(RbfExactArgs a) {
     __syncthreads();
     const int jn = min(EX_J, n - j0);
     for (int jq = 0; jq < jn; jq += 4) {
-      unsigned long long T01 = pk2(sigma, sigma), T23 = T01, L01 = 0ull, L23 = 0ull;
+      unsigned long long T01 = tc::f2pk(sigma, sigma), T23 = T01, L01 = 0ull, L23 = 0ull;
 #pragma unroll
       for (int m = 0; m < DMAX; ++m) {
         if (m < d) {
           const float4 x4 = *reinterpret_cast<const float4*>(&xs[m][jq]);
-          const unsigned long long xx = pk2(xi[m], xi[m]);
-          anchored_step2(T01, L01, xx, pk2(x4.x, x4.y));
-          anchored_step2(T23, L23, xx, pk2(x4.z, x4.w));
+          const unsigned long long xx = tc::f2pk(xi[m], xi[m]);
+          anchored_step2(T01, L01, xx, tc::f2pk(x4.x, x4.y));
+          anchored_step2(T23, L23, xx, tc::f2pk(x4.z, x4.w));
         }
       }
       const float Tv[4] = {__uint_as_float(unsigned(T01)), __uint_as_float(unsigned(T01 >> 32)),

@@ -114,13 +114,16 @@ class DefCG:
         _lib.check(st, self._ctx, what)
 
     # -- operators ----------------------------------------------------------
-    def set_operator_dense(self, A: torch.Tensor, lda: int | None = None):
-        """Borrow a stored row-major float32 operator (n x n, or n x lda)."""
+    def set_operator_dense(self, A: torch.Tensor, lda: int | None = None, symmetric: bool = False):
+        """Borrow a stored row-major float32 operator (n x n, or n x lda).
+        ``symmetric``: A is exactly symmetric and the matvec reads only its
+        upper triangle (dcg_set_operator_dense_sym), about half the bytes."""
         _dev_f32(A, "A")
         lda = _need_rows(A, self.n, "A", lda, min_cols=self.n)
         self._op_ref = A
-        self._check(self.lib.dcg_set_operator_dense(self._ctx, ctypes.c_void_p(A.data_ptr()), lda),
-                    "dcg_set_operator_dense")
+        fn = self.lib.dcg_set_operator_dense_sym if symmetric else self.lib.dcg_set_operator_dense
+        self._check(fn(self._ctx, ctypes.c_void_p(A.data_ptr()), lda),
+                    "dcg_set_operator_dense_sym" if symmetric else "dcg_set_operator_dense")
 
     def set_operator_rbf(self, X: torch.Tensor, lengthscale: float, signal_var: float, noise: float,
                          xformat: str = "bf16"):

@@ -194,3 +194,10 @@ def test_header_is_plain_c_and_links(lib_path, tmp_path):
                         "-o", str(exe), os.path.join(libdir, libname), f"-Wl,-rpath,{libdir}"],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_library_resolves_every_symbol_at_load(lib_path):
+    # RTLD_NOW binds every undefined symbol when the library loads (lazy
+    # binding would defer a missing one to its first call on a GPU machine)
+    import ctypes
+    ctypes.CDLL(lib_path, mode=os.RTLD_NOW)

@@ -114,6 +114,77 @@ def test_matvec_full_size_sampled_rows(dcg):
     assert abs(pAp - p.astype(np.float64) @ qq) <= 1e-12 * (np.abs(p) @ np.abs(qq))
 
 
+@pytest.mark.parametrize("n", [1, 5, 63, 64, 65, 1000, 2047, 2049, 4100, 9000])
+def test_symmetric_matvec_matches_oracle(dcg, n):
+    # dcg_set_operator_dense_sym: only the upper triangle is read. The strictly
+    # lower triangle and the padding columns hold NaN, so any read of them
+    # would show in q. Row sums run in float32 over <= 8 products per thread
+    # and stage and a 32-lane tree; the transposed contributions in float32
+    # over the 64 rows of a band; everything then adds up in float64:
+    # error <= 100 eps32 sum_j |a_ij p_j|.
+    rng = np.random.default_rng(10 + n)
+    lda = (n + 3) // 4 * 4 + 4
+    A32 = rng.standard_normal((n, n)).astype(np.float32)
+    A32 = (A32 + A32.T) * np.float32(0.5)
+    assert np.array_equal(A32, A32.T)
+    p = rng.standard_normal(n).astype(np.float32)
+    stored = np.full((n, lda), np.nan, dtype=np.float32)
+    stored[:, :n] = np.triu(A32) + np.tril(np.full((n, n), np.nan, dtype=np.float32), -1)
+    with dcg.DefCG(n, 0, 0, 1e-6) as s:
+        s.set_operator_dense(dev(stored), lda, symmetric=True)
+        for _ in range(2):   # the partial-sum buffers are reused
+            q, pAp = s.matvec(dev(p))
+            qh = q.cpu().numpy().astype(np.float64)
+            A64, p64 = A32.astype(np.float64), p.astype(np.float64)
+            ref = A64 @ p64
+            bound = 100 * 6e-8 * (np.abs(A64) @ np.abs(p64))
+            assert np.all(np.isfinite(qh))
+            assert np.all(np.abs(qh - ref) <= bound + 1e-30), np.max(np.abs(qh - ref) / (bound + 1e-30))
+            assert abs(pAp - p64 @ qh) <= 1e-12 * (np.abs(p64) @ np.abs(qh))
+
+
+def test_symmetric_operator_solves_like_the_full_one(dcg):
+    # The n = 16384 stored workload at its last lengthscale, plain CG and
+    # def-CG with a recycled subspace, once with the full-matrix matvec and
+    # once with the upper-triangle one: both certify tol (the true residual
+    # reads the full matrix) and take the same number of iterations within
+    # what the float32 recursion makes of the two summation orders (measured:
+    # 210 and 200 at kappa ~1e6): 10 % + 2.
+    cfg = S.DENSE_16384
+    X, bs = S.draw_sequence(cfg, T=2)
+    X32 = X.astype(np.float32)
+    A = dcg.form_rbf_dense(dev(X32), cfg.lengthscale(19), 1.0, cfg.noise)
+    res = {}
+    for sym in (False, True):
+        with dcg.DefCG(cfg.n, cfg.k, cfg.ell, cfg.tol) as s:
+            s.set_operator_dense(A, symmetric=sym)
+            _, i0 = s.solve(dev(bs[0]))
+            s.update_subspace()
+            x, i1 = s.solve(dev(bs[1]))
+            res[sym] = (i0, i1)
+            assert i0["status"] == 0 and i1["status"] == 0
+            assert i0["relres_true"] <= cfg.tol and i1["relres_true"] <= cfg.tol
+    for a, b in zip(res[False], res[True]):
+        assert abs(a["iters"] - b["iters"]) <= 2 + 0.1 * a["iters"], (a["iters"], b["iters"])
+
+
+def test_symmetric_matvec_full_size_sampled_rows(dcg):
+    cfg = S.DENSE_16384
+    X, bs = S.draw_sequence(cfg, T=1)
+    n = cfg.n
+    A = dcg.form_rbf_dense(dev(X.astype(np.float32)), cfg.lengthscale(19), 1.0, cfg.noise)
+    p = bs[0].astype(np.float32)
+    with dcg.DefCG(n, cfg.k, cfg.ell, cfg.tol) as s:
+        s.set_operator_dense(A, symmetric=True)
+        q, pAp = s.matvec(dev(p))
+    rows = np.random.default_rng(2).choice(n, 96, replace=False)
+    Arows = A[torch.tensor(rows, device="cuda")].cpu().numpy().astype(np.float64)
+    ref = Arows @ p.astype(np.float64)
+    got = q.cpu().numpy()[rows].astype(np.float64)
+    bound = 100 * 6e-8 * (np.abs(Arows) @ np.abs(p.astype(np.float64)))
+    assert np.all(np.abs(got - ref) <= bound)
+
+
 # ---------------------------------------------------------------------------
 # A2: multi-vector product Y = A V
 # ---------------------------------------------------------------------------

@@ -43,10 +43,10 @@ def gram_tol(Xr, l, K_abs_p):
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "tf32"])
-@pytest.mark.parametrize("n,d", [(1, 3), (100, 4), (1000, 8), (4096, 32), (2000, 17), (500, 40)])
+@pytest.mark.parametrize("n,d", [(1, 3), (100, 4), (1000, 8), (4096, 32), (2000, 17), (500, 40), (300, 29), (200, 61)])
 def test_rbf_matvec_matches_oracle(dcg, fmt, n, d):
-    if fmt == "tf32" and d > 32:
-        pytest.skip("tf32 tiles hold 32 coordinates")
+    if fmt == "tf32" and d > 29:
+        pytest.skip("tf32 tile rows hold 29 coordinates and three pieces of -|x|^2/2")
     rng = np.random.default_rng(n + d)
     X = rng.standard_normal((n, d)).astype(np.float32)
     Xr = ROUND[fmt](X)
@@ -73,8 +73,8 @@ def test_rbf_true_residual_matches_oracle(dcg, fmt, n, d):
     # (d^2 + 2) u g / (2 l^2) at d = 40, is ~3e-10). The reported |r| meets
     # the float64 |r| within the kernel's own error estimate: the quantity the
     # solve certifies convergence with.
-    if fmt == "tf32" and d > 32:
-        pytest.skip("tf32 tiles hold 32 coordinates")
+    if fmt == "tf32" and d > 29:
+        pytest.skip("tf32 tile rows hold 29 coordinates and three pieces of -|x|^2/2")
     rng = np.random.default_rng(10 * n + d)
     X = rng.standard_normal((n, d)).astype(np.float32)
     Xr = ROUND[fmt](X).astype(np.float64)
