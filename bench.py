@@ -136,7 +136,7 @@ def run_sequence(P, torch, solver, Xd, bs_dev, A, T, deflate, ev_pool, side=None
     P.form_rbf_dense(Xd, CFG.lengthscale(0), CFG.signal_var, CFG.noise, out=A)
     fe[0].record(stream)
     for t in range(T):
-        solver.set_operator_dense(A)
+        solver.set_operator_dense(A, symmetric=True)   # k_form_rbf writes A exactly symmetric
         ss[t].record(stream)
         x, info = solver.solve(bs_dev[t])
         infos.append(info)
@@ -256,14 +256,15 @@ def gpu_arm(args):
     plain_mv = sum(i["iters"] + i["matvecs_check"] for i in pinfos)
     plain.close()
 
-    # roofline of the dominant kernel: the TMA GEMV q = A p, timed with CUDA
-    # events on the solver's stream (same launch configuration as in the loop)
+    # roofline of the dominant kernel: the symmetric TMA matvec q = A p (two
+    # launches, k_symv_tma and k_symv_fin, timed together), CUDA events on the
+    # solver's stream, same launch configuration as in the loop
     hbm_peak, peak_kind = peaks()
     stream = torch.cuda.current_stream()
     p = bs_dev[0].clone()
     q = torch.empty_like(p)
     P.form_rbf_dense(Xd, CFG.lengthscale(T - 1), CFG.signal_var, CFG.noise, out=A)
-    solver.set_operator_dense(A)
+    solver.set_operator_dense(A, symmetric=True)
     for _ in range(3):
         solver.matvec(p, q, want_pAp=False)
     reps = 50
@@ -274,7 +275,7 @@ def gpu_arm(args):
     e1.record(stream)
     torch.cuda.synchronize()
     gemv_ms = e0.elapsed_time(e1) / reps
-    gemv_bytes = 4.0 * n * n + 8.0 * n        # A once, p read and q written
+    gemv_bytes = 2.0 * n * (n + 1) + 8.0 * n  # the upper triangle once, p read and q written
     achieved = gemv_bytes / (gemv_ms * 1e-3) / 1e9
 
     # end to end through the public API with host buffers: X and b_t from
@@ -290,7 +291,7 @@ def gpu_arm(args):
     cur = torch.cuda.current_stream()
     P.form_rbf_dense(Xd2, CFG.lengthscale(0), CFG.signal_var, CFG.noise, out=A)
     for t in range(T):
-        solver.set_operator_dense(A)
+        solver.set_operator_dense(A, symmetric=True)
         bd = bh[t].to("cuda", non_blocking=True)
         x, info = solver.solve(bd)
         xh[t].copy_(x, non_blocking=True)
@@ -306,7 +307,7 @@ def gpu_arm(args):
     solver.close()
 
     traffic = None
-    tf = os.path.join(ROOT, "profiles", "gemv_dense_n16384.md")
+    tf = os.path.join(ROOT, "profiles", "symv_dense_n16384.md")
     if os.path.exists(tf):
         for line in open(tf):
             if line.startswith("dram_bytes_per_launch:"):
@@ -353,7 +354,7 @@ def gpu_arm(args):
         },
         "speedup_vs_plain_cg": (plain_ms / 1e3) / seq_s,
         "roofline": {
-            "kernel": "k_rowop_tma<false> (q = A p, fused p^T q)",
+            "kernel": "k_symv_tma + k_symv_fin (q = A p from the upper triangle, fused p^T q)",
             "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": traffic,
             "algorithmic_bytes_per_launch": gemv_bytes, "launch_ms": gemv_ms,
@@ -366,12 +367,124 @@ def gpu_arm(args):
         "gpu_launches": launches_of(infos, True) * args.steps,
         "clocks": clk.summary(),
     }
+    if rank == 0 and world == 1 and args.matrix_free != "none":
+        out["matrix_free"] = matrix_free_block(P, torch, args.matrix_free)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(samples=2)
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
+# Matrix-free workloads (BF16 n = 131072 sequence; TF32 n = 262144 kernels)
+# ---------------------------------------------------------------------------
+def ex2_peak(P):
+    """Exponentials per second of the special-function units, measured now by
+    the library's probe (dcg_measure_ex2_rate)."""
+    import ctypes
+    lib = P.load()
+    ps, pc = ctypes.c_double(), ctypes.c_double()
+    st = lib.dcg_measure_ex2_rate(None, ctypes.byref(ps), ctypes.byref(pc))
+    if st != 0:
+        return None, None
+    return ps.value, pc.value
+
+
+def mf_kernels(P, torch, cfg, fmt, ex2_ps):
+    """The matvec and the exact-form true residual of a matrix-free workload at
+    full size, CUDA events over repeated launches on the current stream."""
+    X, bs = S.draw_sequence(cfg, T=2)
+    n = cfg.n
+    stream = torch.cuda.current_stream()
+    with P.DefCG(n, 0, 0, cfg.tol) as s:
+        s.set_operator_rbf(torch.tensor(X.astype(np.float32), device="cuda"), cfg.lengthscale(0), cfg.signal_var,
+                           cfg.noise, xformat=fmt)
+        p = torch.tensor(bs[0].astype(np.float32), device="cuda")
+        q = torch.empty_like(p)
+        x = torch.tensor(bs[1], device="cuda")
+
+        def timed(fn, reps):
+            fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        mv_ms = timed(lambda: s.matvec(p, q, want_pAp=False), 10)
+        res_ms = timed(lambda: s.residual(p, x), 3)
+    entries = float(n) * n
+    dk = cfg.d + 3                                   # coordinates of a tile row (with -|x|^2/2)
+    kpad = (dk + 15) // 16 * 16 if fmt == "bf16" else (dk + 7) // 8 * 8
+    tflops = 2.0 * entries * kpad / (mv_ms * 1e-3) / 1e12
+    tpeak, _ = tensor_peak(fmt)
+    out = {"n": n, "d": cfg.d, "x_format": fmt,
+           "matvec": {"kernel": "k_rbf_mv<1> (tcgen05 Gram tiles, exp on the SFU, fused contraction)",
+                      "launch_ms": mv_ms, "entries_per_s": entries / (mv_ms * 1e-3),
+                      "tensor_tflops": tflops, "tensor_frac": tflops / tpeak},
+           "true_residual": {"kernel": "k_rbf_resid + k_rbf_resid_fin (exact-form entries, Dot2 sums)",
+                             "launch_ms": res_ms, "matvec_equivalents": res_ms / mv_ms}}
+    if ex2_ps:
+        achieved = entries / (mv_ms * 1e-3)
+        out["matvec"]["roofline"] = {"bound": "sfu", "achieved": achieved, "peak": ex2_ps, "unit": "exp2/s",
+                                     "frac": achieved / ex2_ps,
+                                     "peak_kind": "measured now (dcg_measure_ex2_rate)"}
+    return out
+
+
+def mf_sequence(P, torch, cfg, deflate):
+    """One whole matrix-free sequence (set the lengthscale l_t, solve, extract
+    the next W asynchronously), CUDA events around the sequence."""
+    X, bs = S.draw_sequence(cfg)
+    n = cfg.n
+    bd = [torch.tensor(b.astype(np.float32), device="cuda") for b in bs]
+    solver = P.DefCG(n, cfg.k if deflate else 0, cfg.ell if deflate else 0, cfg.tol, max_iter=20000,
+                     refine_every=cfg.refine_every)
+    solver.set_operator_rbf(torch.tensor(X.astype(np.float32), device="cuda"), cfg.lengthscale(0),
+                            cfg.signal_var, cfg.noise, xformat=cfg.x_dtype)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for t in range(cfg.T):
+        solver.set_rbf_params(cfg.lengthscale(t), cfg.signal_var, cfg.noise)
+        _, info = solver.solve(bd[t], raise_on_error=False)
+        infos.append(info)
+        if deflate:
+            solver.update_subspace(wait=False)
+    solver.sync()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    solver.close()
+    secs = e0.elapsed_time(e1) / 1e3
+    return {"s_per_sequence": secs, "iters": sum(i["iters"] for i in infos),
+            "check_matvecs": sum(i["matvecs_check"] for i in infos),
+            "setup_columns": sum(i["matvecs_setup"] for i in infos),
+            "all_converged": all(i["status"] == 0 and i["relres_true"] <= cfg.tol for i in infos),
+            "iters_per_system": [i["iters"] for i in infos],
+            "checks_per_system": [i["matvecs_check"] for i in infos]}
+
+
+def matrix_free_block(P, torch, mode):
+    ex2_ps, ex2_pc = ex2_peak(P)
+    out = {"ex2_peak": {"per_s": ex2_ps, "per_clock_per_sm": ex2_pc, "kind": "measured now (dcg_measure_ex2_rate)"}}
+    c3, c5 = S.MF_131072, S.MF_262144
+    out[c3.name] = mf_kernels(P, torch, c3, "bf16", ex2_ps)
+    out[c5.name] = mf_kernels(P, torch, c5, "tf32", ex2_ps)
+    if mode == "all":
+        d = mf_sequence(P, torch, c3, True)
+        pl = mf_sequence(P, torch, c3, False)
+        out[c3.name].update({"defcg": d, "plain_cg": pl,
+                             "speedup_vs_plain_cg": pl["s_per_sequence"] / d["s_per_sequence"],
+                             "sequence": f"{c3.T} systems, k = {c3.k}, ell = {c3.ell}, refinement every "
+                                         f"{c3.refine_every}, tol {c3.tol}"})
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -632,6 +745,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--matrix-free", choices=["all", "kernels", "none"], default="all",
+                    help="after the stored headline: the matrix-free kernels at full size and (all) one whole "
+                         "BF16 n = 131072 sequence with def-CG and with plain CG")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the solve's kernels from the host instead of one CUDA graph "
                          "(profiling mode: ncu cannot list kernels inside conditional graphs)")

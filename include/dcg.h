@@ -334,6 +334,18 @@ dcg_status dcg_apply_block(dcg_ctx* ctx, const float* V, int32_t c, float* Y);
 /* Synchronises the context's stream. */
 dcg_status dcg_sync(dcg_ctx* ctx);
 
+/* Throughput of the exponential on the special-function units (ex2.approx),
+ * the pipe that binds the matrix-free matvec for small d (one exponential per
+ * kernel entry): a short probe kernel on `stream` (independent chains,
+ * 2048 threads per SM), best of two timed runs after a warm-up. The paper has
+ * no counterpart; the benchmark reports the matrix-free kernels against it.
+ *   per_second         host: exponentials per second on the current device.
+ *   per_clock_per_sm   host, may be NULL: the same per SM and clock cycle at
+ *                      the device's maximum SM clock.
+ * Allocates and frees a small device buffer; synchronises `stream`.
+ * Errors: INVALID_ARG, CUDA (message for dcg_last_error(NULL)). */
+dcg_status dcg_measure_ex2_rate(void* stream, double* per_second, double* per_clock_per_sm);
+
 /* Failure-handling test hook (no counterpart in the paper): arms the next
  * dcg_solve of this context so that, in its first iteration, CTA 0 of the
  * fused iteration kernel withholds its arrival at the grid barrier that

@@ -95,6 +95,7 @@ SIGNATURES = {
     "dcg_apply_block": (_I32, [_P, _P, _I32, _P]),
     "dcg_sync": (_I32, [_P]),
     "dcg_debug_arm_barrier_timeout": (_I32, [_P, _I32]),
+    "dcg_measure_ex2_rate": (_I32, [_P, _PD, _PD]),
 }
 
 _lib = None

@@ -1119,6 +1119,40 @@ extern "C" dcg_status dcg_debug_arm_barrier_timeout(dcg_ctx* c, int32_t polls) {
   return DCG_OK;
 }
 
+extern "C" dcg_status dcg_measure_ex2_rate(void* stream, double* per_second, double* per_clock_per_sm) {
+  dcg_ctx* c = nullptr;  // errors below are reported without a context
+  if (!per_second) return fail(nullptr, DCG_ERR_INVALID_ARG, "dcg_measure_ex2_rate: per_second is required");
+  int dev = 0, sms = 0, khz = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int blocks = 4 * sms, iters = 4096;
+  float* out = nullptr;
+  CK(cudaMalloc(&out, size_t(blocks) * 512 * sizeof(float)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  double count = 0.0;
+  float best = 0.f;
+  for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {  // the first run warms up
+    if ((e = cudaEventRecord(e0, s)) != cudaSuccess) break;
+    if ((e = launch_ex2_rate(out, blocks, iters, &count, s)) != cudaSuccess) break;
+    if ((e = cudaEventRecord(e1, s)) != cudaSuccess) break;
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+    if (rep > 0 && (best == 0.f || ms < best)) best = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  CK(e);
+  *per_second = count / (double(best) * 1e-3);
+  if (per_clock_per_sm) *per_clock_per_sm = *per_second / (double(sms) * double(khz) * 1e3);
+  return DCG_OK;
+}
+
 extern "C" dcg_status dcg_sync(dcg_ctx* c) {
   if (!c) return DCG_ERR_INVALID_ARG;
   { const dcg_status pend = finish_update(c); if (pend != DCG_OK) return pend; }

@@ -194,6 +194,7 @@ cudaError_t launch_rbf_params(const float* nsq, int n, int n_pad, int d, double 
 cudaError_t launch_rbf_anchor(const float* Xr, int n, int n_pad, int d, double* n64, unsigned int* maxbits,
                               RbfParams* prm, float* nh, float* nl, float* XrT, cudaStream_t s);
 int rbf_resid_splits(int n, int num_sms);
+cudaError_t launch_ex2_rate(float* out, int blocks, int iters, double* count, cudaStream_t s);
 bool make_rbf_tmap(CUtensorMap* map, const void* Xt, int n_pad, int xformat, int d, EncodeTiledFn encode);  // map[2]
 int rbf_max_d(int xformat);
 __host__ __device__ int rbf_row_bytes(int xformat, int d);

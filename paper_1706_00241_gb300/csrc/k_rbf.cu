@@ -1150,4 +1150,31 @@ cudaError_t launch_rbf_block(const RbfExactArgs& a, int cmax, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Throughput of ex2.approx (the special-function unit), the pipe that binds
+// the matrix-free matvec for small d: every thread runs 8 independent chains
+// v <- 2^v - 1 (one exponential and one add each), 2048 threads per SM.
+// ---------------------------------------------------------------------------
+constexpr int EXR_CHAINS = 8;
+__global__ void __launch_bounds__(512) k_ex2_rate(float* out, int iters) {
+  float v[EXR_CHAINS];
+#pragma unroll
+  for (int i = 0; i < EXR_CHAINS; ++i) v[i] = -0.001f * float(threadIdx.x + i);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < EXR_CHAINS; ++i) v[i] = tc::ex2_approx(v[i]) - 1.0f;
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < EXR_CHAINS; ++i) s += v[i];
+  out[int64_t(blockIdx.x) * blockDim.x + threadIdx.x] = s;
+}
+
+// out: blocks * 512 floats. Returns the number of exponentials executed.
+cudaError_t launch_ex2_rate(float* out, int blocks, int iters, double* count, cudaStream_t s) {
+  k_ex2_rate<<<blocks, 512, 0, s>>>(out, iters);
+  *count = double(blocks) * 512.0 * double(iters) * EXR_CHAINS;
+  return cudaGetLastError();
+}
+
 }  // namespace dcg
