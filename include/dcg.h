@@ -299,6 +299,43 @@ dcg_status dcg_get_subspace(dcg_ctx* ctx, float* W, int32_t* k);
 dcg_status dcg_get_history(dcg_ctx* ctx, double* relres, int32_t cap, int32_t* count);
 
 /* ------------------------------------------------------------------------ */
+/* The Sec. 3 experiment: Newton steps of the Laplace approximation          */
+/* ------------------------------------------------------------------------ */
+
+/* dcg_laplace_system: the linear system of one Newton step for the mode of
+ * the Laplace approximation in binary GP classification (Sec. 3, Eq. obj and
+ * Eq. linsys), logistic likelihood p(y_i | f_i) = sigma(y_i f_i):
+ *   pi = sigma(f), H = diag(pi (1 - pi)), s = H^{1/2} (elementwise, float64),
+ *   c = H f + grad log p(y | f) = H f + (y + 1)/2 - pi,
+ *   A = I + diag(s) K diag(s),   b = diag(s) K c.
+ * A is written in one pass over K (entries (s_i s_j) K_ij, exactly symmetric
+ * when K is), so it can be given to dcg_set_operator_dense_sym; K c uses the
+ * stored-operator GEMV. The eigenvalues of A lie in [1, 1 + lambda_max(K)/4].
+ *   K      device, row-major float32 n x n, leading dimension ldk (ldk >= n,
+ *          ldk % 4 == 0, 16-byte aligned): the kernel matrix, read.
+ *   y      device, n floats, labels -1 or +1.     f  device, n doubles.
+ *   A      device, row-major float32 n x lda (lda >= n, lda % 4 == 0,
+ *          16-byte aligned), written.
+ *   b      device, n floats; c device, n doubles; s device, n floats: written.
+ * Runs on the context's stream without synchronising; the context's own
+ * operator and subspace are not touched. The first call allocates 2 n floats
+ * of scratch. Errors: INVALID_ARG, NOMEM, CUDA. */
+dcg_status dcg_laplace_system(dcg_ctx* ctx, const float* K, int64_t ldk, const float* y, const double* f, float* A,
+                              int64_t lda, float* b, double* c, float* s);
+
+/* dcg_laplace_update: the Newton update from the solution x of A x = b:
+ *   a = c - s x (float64),  f = K a (stored-operator GEMV, float32 sums),
+ *   Psi = log p(y | f) - 1/2 f^T a (float64 sums; Eq. obj without the terms
+ *   that do not depend on f, since K^{-1} f = a).
+ *   K, y as for dcg_laplace_system; c, s its outputs; x device n doubles.
+ *   f, a   device, n doubles, written.
+ *   psi    host, may be NULL; receives Psi (the call then synchronises).
+ * The Newton loop stops when Psi rises by less than 1 (Sec. 3).
+ * Errors: INVALID_ARG, NOMEM, CUDA. */
+dcg_status dcg_laplace_update(dcg_ctx* ctx, const float* K, int64_t ldk, const float* y, const double* c,
+                              const float* s, const double* x, double* f, double* a, double* psi);
+
+/* ------------------------------------------------------------------------ */
 /* Single steps of the hot path, for testing and measurement                 */
 /* ------------------------------------------------------------------------ */
 

@@ -11,3 +11,4 @@ Python binding (torch supplies device memory and streams).
 from ._lib import DcgError, load  # noqa: F401
 from .solver import DefCG, form_rbf_dense, matvec_dense_noalloc  # noqa: F401
 from .autograd import DefCGSolve, LogDetProbes, fit_gp, gp_objective, rademacher_probes  # noqa: F401
+from .laplace import laplace_mode  # noqa: F401

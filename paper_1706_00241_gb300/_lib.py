@@ -96,6 +96,8 @@ SIGNATURES = {
     "dcg_sync": (_I32, [_P]),
     "dcg_debug_arm_barrier_timeout": (_I32, [_P, _I32]),
     "dcg_measure_ex2_rate": (_I32, [_P, _PD, _PD]),
+    "dcg_laplace_system": (_I32, [_P, _P, _I64, _P, _P, _P, _I64, _P, _P, _P]),
+    "dcg_laplace_update": (_I32, [_P, _P, _I64, _P, _P, _P, _P, _P, _P, _PD]),
 }
 
 _lib = None

@@ -48,6 +48,8 @@ struct dcg_ctx {
   int last_iters = 0;
 
   int test_barrier_polls = 0;  // > 0: the next solve withholds a grid-barrier arrival (test hook)
+  float* lap_v32 = nullptr;    // Laplace Newton step: float32 copies of c or a (n)
+  float* lap_kv = nullptr;     // and the GEMV result K c or K a (n)
   bool dense_sym = false;      // stored operator given as its upper triangle (symmetric matvec)
   float* sym_rowpart = nullptr;
   float* sym_colpart = nullptr;
@@ -1150,6 +1152,72 @@ extern "C" dcg_status dcg_measure_ex2_rate(void* stream, double* per_second, dou
   CK(e);
   *per_second = count / (double(best) * 1e-3);
   if (per_clock_per_sm) *per_clock_per_sm = *per_second / (double(sms) * double(khz) * 1e3);
+  return DCG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Newton step of the Laplace approximation (the Sec. 3 experiment)
+// ---------------------------------------------------------------------------
+static dcg_status lap_check(dcg_ctx* c, const float* K, int64_t ldk) {
+  if (!K) return fail(c, DCG_ERR_INVALID_ARG, "K is NULL");
+  if (ldk < c->w.n || (ldk % 4) != 0) return fail(c, DCG_ERR_INVALID_ARG, "ldk must be >= n and a multiple of 4");
+  if ((reinterpret_cast<uintptr_t>(K) & 15) != 0) return fail(c, DCG_ERR_INVALID_ARG, "K must be 16-byte aligned");
+  if (!c->lap_v32) {
+    CK(dalloc(c, &c->lap_v32, size_t(c->w.n)));
+    CK(dalloc(c, &c->lap_kv, size_t(c->w.n)));
+  }
+  return DCG_OK;
+}
+
+// out = K v (float32 stored K, the row-band TMA GEMV)
+static dcg_status lap_gemv(dcg_ctx* c, const float* K, int64_t ldk, const float* v, float* out) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return fail(c, DCG_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  CUtensorMap m;
+  if (!make_rowop_tmap(&m, K, c->w.n, ldk, enc)) return fail(c, DCG_ERR_INVALID_ARG, "tensor map encode failed");
+  RowOpArgs a{};
+  a.v = v;
+  a.out = out;
+  a.n = c->w.n;
+  a.partials = c->mv_partials;
+  a.ticket = c->mv_ticket;
+  a.result = c->mv_result;
+  CK(launch_rowop(&m, a, false, c->grid_rows, c->stream));
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_laplace_system(dcg_ctx* c, const float* K, int64_t ldk, const float* y, const double* f,
+                                         float* A, int64_t lda, float* b, double* cvec, float* s) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  { const dcg_status pend = finish_update(c); if (pend != DCG_OK) return pend; }
+  if (!y || !f || !A || !b || !cvec || !s) return fail(c, DCG_ERR_INVALID_ARG, "y, f, A, b, c and s are required");
+  if (lda < c->w.n || (lda % 4) != 0) return fail(c, DCG_ERR_INVALID_ARG, "lda must be >= n and a multiple of 4");
+  if ((reinterpret_cast<uintptr_t>(A) & 15) != 0) return fail(c, DCG_ERR_INVALID_ARG, "A must be 16-byte aligned");
+  dcg_status st = lap_check(c, K, ldk);
+  if (st != DCG_OK) return st;
+  const int n = c->w.n, grid = lap_grid(n, c->num_sms);
+  CK(launch_lap_prep(y, f, n, s, cvec, c->lap_v32, grid, c->stream));
+  if ((st = lap_gemv(c, K, ldk, c->lap_v32, c->lap_kv)) != DCG_OK) return st;
+  CK(launch_lap_scale(s, c->lap_kv, n, b, grid, c->stream));
+  CK(launch_lap_form(K, ldk, s, n, A, lda, c->stream));
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_laplace_update(dcg_ctx* c, const float* K, int64_t ldk, const float* y, const double* cvec,
+                                         const float* s, const double* x, double* f, double* a, double* psi) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  { const dcg_status pend = finish_update(c); if (pend != DCG_OK) return pend; }
+  if (!y || !cvec || !s || !x || !f || !a) return fail(c, DCG_ERR_INVALID_ARG, "y, c, s, x, f and a are required");
+  dcg_status st = lap_check(c, K, ldk);
+  if (st != DCG_OK) return st;
+  const int n = c->w.n, grid = lap_grid(n, c->num_sms);
+  CK(launch_lap_a(cvec, s, x, n, a, c->lap_v32, grid, c->stream));
+  if ((st = lap_gemv(c, K, ldk, c->lap_v32, c->lap_kv)) != DCG_OK) return st;
+  CK(launch_lap_psi(y, c->lap_kv, a, n, f, c->mv_partials, c->mv_ticket, c->mv_result + 1, grid, c->stream));
+  if (psi) {
+    CK(cudaMemcpyAsync(psi, c->mv_result + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
   return DCG_OK;
 }
 

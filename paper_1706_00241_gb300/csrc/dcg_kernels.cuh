@@ -231,6 +231,18 @@ cudaError_t apply_block_configure();
 cudaError_t launch_form_rbf(const float* X, int n, int d, double l, double s2, double noise, float* A, int64_t lda,
                             cudaStream_t s);
 
+// ---- Laplace-approximation Newton step of the Sec. 3 experiment (k_laplace.cu)
+int lap_grid(int n, int num_sms);
+cudaError_t launch_lap_prep(const float* y, const double* f, int n, float* s, double* c, float* c32, int grid,
+                            cudaStream_t st);
+cudaError_t launch_lap_scale(const float* s, const float* v, int n, float* out, int grid, cudaStream_t st);
+cudaError_t launch_lap_form(const float* K, int64_t ldk, const float* s, int n, float* A, int64_t lda,
+                            cudaStream_t st);
+cudaError_t launch_lap_a(const double* c, const float* s, const double* x, int n, double* a, float* a32, int grid,
+                         cudaStream_t st);
+cudaError_t launch_lap_psi(const float* y, const float* f32, const double* a, int n, double* f, double* partials,
+                           unsigned int* ticket, double* psi, int grid, cudaStream_t st);
+
 // ---- iteration kernels (k_iter.cu)
 cudaError_t launch_setup_r(const Ws& w, int grid, cudaStream_t s);
 cudaError_t launch_gram_E(const Ws& w, double* part, int num_sms, cudaStream_t s);

@@ -4,7 +4,9 @@ Calls only ``oracle/`` and ``dcg_synth`` (never the CUDA path). Each golden file
 records the workload, the oracle settings and per-system results of def-CG
 (Algorithm 1 with harmonic-Ritz recycling, Sec. 2.3) and plain CG.
 
-    python tests/golden/make_golden.py dense_16384     # ~10 min, 1 core-heavy
+    python tests/golden/make_golden.py dense_16384     # ~15 min, 1 core-heavy
+    (also writes dense_16384_oracle_x.npz: the oracle's x for systems 0, 10
+    and 19, with a Lanczos condition estimate of each in the JSON)
 """
 
 from __future__ import annotations
@@ -23,11 +25,27 @@ import dcg_synth as S  # noqa: E402
 from oracle import dcg_oracle as O  # noqa: E402
 
 
-def sequence_golden(cfg: S.RBFSequence, T: int, out_name: str):
+def lanczos_kappa(alpha, beta):
+    """Condition estimate of A from a plain CG run: the extreme eigenvalues of
+    the Lanczos tridiagonal that CG's step lengths and beta build (T_jj =
+    1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j);
+    at convergence they approximate A's extreme eigenvalues."""
+    m = len(alpha)
+    Tm = np.zeros((m, m))
+    for j in range(m):
+        Tm[j, j] = 1.0 / alpha[j] + (beta[j - 1] / alpha[j - 1] if j > 0 else 0.0)
+        if j + 1 < m:
+            Tm[j, j + 1] = Tm[j + 1, j] = np.sqrt(beta[j]) / alpha[j]
+    ev = np.linalg.eigvalsh(Tm)
+    return float(ev[-1] / ev[0]), float(ev[0]), float(ev[-1])
+
+
+def sequence_golden(cfg: S.RBFSequence, T: int, out_name: str, keep_x=()):
     X, bs = S.draw_sequence(cfg, T=T)
     X32 = X.astype(np.float32).astype(np.float64)   # the operator both sides see
     W = None
     rows = []
+    xs = {}
     t_solve = 0.0
     t_cg = 0.0
     for t in range(T):
@@ -39,6 +57,14 @@ def sequence_golden(cfg: S.RBFSequence, T: int, out_name: str):
         t1 = time.perf_counter()
         cg = O.cg(A, b, tol=cfg.tol)
         t2 = time.perf_counter()
+        extra = {}
+        if t in keep_x:
+            # plain CG through defcg (k = 0 reproduces cg iterate by iterate)
+            # keeping every step length, for the Lanczos condition estimate
+            full = O.defcg(A, b, tol=cfg.tol, ell=10 ** 9, window="first")
+            kappa, lmin, lmax = lanczos_kappa(full.alpha, full.beta)
+            extra = {"kappa_lanczos": kappa, "lambda_min_lanczos": lmin, "lambda_max_lanczos": lmax}
+            xs[f"x_{t}"] = res.x
         t_solve += t1 - t0
         t_cg += t2 - t1
         W = rr.W
@@ -53,6 +79,7 @@ def sequence_golden(cfg: S.RBFSequence, T: int, out_name: str):
             "theta_top": [float(v) for v in rr.theta_selected[:8]],
             "defcg_seconds": t1 - t0,
             "cg_seconds": t2 - t1,
+            **extra,
         })
         print(json.dumps(rows[-1]), flush=True)
     out = {
@@ -69,12 +96,14 @@ def sequence_golden(cfg: S.RBFSequence, T: int, out_name: str):
     }
     with open(os.path.join(HERE, out_name), "w") as f:
         json.dump(out, f, indent=1)
+    if xs:
+        np.savez_compressed(os.path.join(HERE, out_name.replace(".json", "_x.npz")), **xs)
 
 
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "dense_16384"
     if which == "dense_16384":
-        sequence_golden(S.DENSE_16384, S.DENSE_16384.T, "dense_16384_oracle.json")
+        sequence_golden(S.DENSE_16384, S.DENSE_16384.T, "dense_16384_oracle.json", keep_x=(0, 10, 19))
     elif which == "small_1024":
         cfg = S.SMALL_1024
         small = S.RBFSequence(**{**cfg.__dict__, "tol": 1e-6})

@@ -499,7 +499,7 @@ def test_rayleigh_ritz_sequence_small_matches_oracle(dcg):
 
 
 def _sequence_gpu(dcg, cfg, T, tol, deflate=True, refine_every=0, host_loop=False, keep_A=False,
-                  extraction="harmonic"):
+                  extraction="harmonic", symmetric=False):
     X, bs = S.draw_sequence(cfg, T=T)
     Xd = dev(X.astype(np.float32))
     n = cfg.n
@@ -509,7 +509,7 @@ def _sequence_gpu(dcg, cfg, T, tol, deflate=True, refine_every=0, host_loop=Fals
         A = torch.empty((n, n), dtype=torch.float32, device="cuda")
         for t in range(T):
             dcg.form_rbf_dense(Xd, cfg.lengthscale(t), cfg.signal_var, cfg.noise, out=A)
-            s.set_operator_dense(A)
+            s.set_operator_dense(A, symmetric=symmetric)
             x, info = s.solve(dev(bs[t]))
             if deflate:
                 s.update_subspace()
@@ -569,16 +569,33 @@ def test_sequence_small_error_against_cholesky(dcg):
         assert rel_a <= np.sqrt(lam[-1] / lam[0]) * relres * (1 + 1e-6), (t, rel_a, lam[-1] / lam[0])
 
 
-def test_sequence_dense_16384_full_size(dcg):
-    # The benchmark workload at full size (first 8 systems, n = 16384, k = 32,
-    # ell = 64): each solve reaches the true relative residual 1e-6, and the
-    # per-system iteration counts follow the float64 oracle's (tests/golden,
-    # written by tests/golden/make_golden.py) within 6 % + 2.
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_sequence_dense_16384_full_size(dcg, symmetric):
+    # The benchmark workload at full size, all 20 systems (n = 16384, k = 32,
+    # ell = 64), with the full-matrix and with the upper-triangle matvec
+    # (the benchmark's): each solve reaches the true relative residual 1e-6;
+    # per-system iteration counts follow the float64 oracle's
+    # (tests/golden, written by tests/golden/make_golden.py) within 10 % + 2
+    # (float32 recursion, reading G8); for systems 0, 10 and 19 the solution
+    # error against the oracle's x is within kappa (2 tol + 5e-7), with kappa
+    # the oracle's Lanczos estimate and 5e-7 the float32 operator's entry
+    # error (float32 distances, the 2-ulp exponential): 6e-6 at t = 0 (kappa
+    # 2.5, inside the 1e-5 float32 target), 4e-4 at t = 10 (kappa 164),
+    # 1.2e-2 at t = 19 (kappa 4.8e3). Measured: 1.1e-7, 4.2e-7 and 3.4e-6,
+    # so the 1e-5 float32 target holds on all three and is asserted too.
     g = json.load(open(os.path.join(HERE, "golden", "dense_16384_oracle.json")))
-    got = _sequence_gpu(dcg, S.DENSE_16384, 8, 1e-6)
+    gx = np.load(os.path.join(HERE, "golden", "dense_16384_oracle_x.npz"))
+    got = _sequence_gpu(dcg, S.DENSE_16384, 20, 1e-6, symmetric=symmetric)
     for info, ref in zip(got, g["systems"]):
-        assert info["status"] == 0 and info["relres_true"] <= 1e-6
-        assert abs(info["iters"] - ref["defcg_iters"]) <= 2 + 0.06 * ref["defcg_iters"], (info["iters"], ref)
+        assert info["status"] == 0 and info["relres_true"] <= 1e-6, (ref["t"], info)
+        assert abs(info["iters"] - ref["defcg_iters"]) <= 2 + 0.1 * ref["defcg_iters"], (info["iters"], ref)
+        key = f"x_{ref['t']}"
+        if key in gx:
+            xo = gx[key]
+            err = np.linalg.norm(info["x"] - xo) / np.linalg.norm(xo)
+            bound = ref["kappa_lanczos"] * (2e-6 + 5e-7)
+            print("t=%d kappa=%.3g err=%.2e bound=%.2e" % (ref["t"], ref["kappa_lanczos"], err, bound))
+            assert err <= bound and err <= 1e-5, (ref["t"], err, bound)
 
 
 @pytest.mark.parametrize("refine_every", [0, 7])
