@@ -152,16 +152,29 @@ def gp_targets(X: np.ndarray, seed: int = 0) -> np.ndarray:
     return np.sin(6.0 * X[:, 0]) + 0.1 * rng.standard_normal(X.shape[0])
 
 
-def classification_data(n: int, d: int, seed: int = 0, spread: float = 0.15):
+def classification_data(n: int, d: int, seed: int = 0, spread: float = 0.15, latent: int = 0,
+                        latent_spread: float = 0.15):
     """Binary classification inputs in the shape of the Sec. 3 experiment
     (images of two digits, pixel values in [0, 1], labels +-1): two classes
     around seeded centres in [0.3, 0.7]^d with Gaussian spread, clipped to
     [0, 1], labels alternating +1, -1. A synthetic stand-in for the infinite
     MNIST threes and fives, which are not available here.
-    Returns X (n, d) float64 and y (n,) float64."""
+
+    With ``latent`` > 0 each class also varies along its own ``latent``
+    seeded directions (coordinates N(0, latent_spread^2) per direction after
+    a 1/sqrt(latent) scaling of the directions), with ``spread`` then the
+    isotropic noise: images of a digit lie near a low-dimensional manifold,
+    which spreads the kernel's spectrum the way real digits do (isotropic
+    noise alone in many dimensions makes all distances nearly equal).
+    The draws with latent = 0 are unchanged. Returns X (n, d) float64 and y
+    (n,) float64."""
     rng = np.random.default_rng(seed)
     centres = rng.uniform(0.3, 0.7, size=(2, d))
     y = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
     cls = (y < 0).astype(int)
-    X = np.clip(centres[cls] + spread * rng.standard_normal((n, d)), 0.0, 1.0)
-    return X, y
+    X = centres[cls] + spread * rng.standard_normal((n, d))
+    if latent > 0:
+        dirs = rng.standard_normal((2, latent, d)) / np.sqrt(latent)
+        z = latent_spread * rng.standard_normal((n, latent))
+        X = X + np.einsum("nl,nld->nd", z, dirs[cls])
+    return np.clip(X, 0.0, 1.0), y

@@ -220,8 +220,10 @@ dcg_status dcg_rbf_dtheta(dcg_ctx* ctx, const float* U, const float* V, int32_t 
  * exp(-|x_i - x_j|^2 / (2 l^2)) + noise * [i == j], float32, computed from X
  * (device, row-major float32 n x d) with float32 difference-form distances.
  * A: device, n x lda. No context needed; runs on `stream`.
+ * The squared distance is a float32 sum over the d coordinates (relative
+ * error up to d u, u = 2^-24, and typically sqrt(d) u).
  * Errors: INVALID_ARG (X or A NULL, n outside [1, 2^30], lda < n, d outside
- * [1, 256], lengthscale <= 0, a non-finite parameter), CUDA. The message is
+ * [1, 4096], lengthscale <= 0, a non-finite parameter), CUDA. The message is
  * kept for dcg_last_error(NULL). */
 dcg_status dcg_form_rbf_dense(const float* X, int64_t n, int32_t d, double lengthscale,
                               double signal_var, double noise, float* A, int64_t lda,

@@ -478,7 +478,7 @@ extern "C" dcg_status dcg_form_rbf_dense(const float* X, int64_t n, int32_t d, d
   if (!X || !A) return fail(nullptr, DCG_ERR_INVALID_ARG, "dcg_form_rbf_dense: X and A are required");
   if (n < 1 || n > (int64_t(1) << 30) || lda < n)
     return fail(nullptr, DCG_ERR_INVALID_ARG, "dcg_form_rbf_dense: need 1 <= n <= 2^30 and lda >= n");
-  if (d < 1 || d > 256) return fail(nullptr, DCG_ERR_INVALID_ARG, "dcg_form_rbf_dense: d must be in [1, 256]");
+  if (d < 1 || d > 4096) return fail(nullptr, DCG_ERR_INVALID_ARG, "dcg_form_rbf_dense: d must be in [1, 4096]");
   if (!(l > 0.0) || !std::isfinite(l) || !std::isfinite(s2) || !std::isfinite(noise))
     return fail(nullptr, DCG_ERR_INVALID_ARG, "dcg_form_rbf_dense: lengthscale > 0 and finite parameters");
   cudaError_t e = launch_form_rbf(X, int(n), d, l, s2, noise, A, lda, static_cast<cudaStream_t>(stream));
