@@ -284,9 +284,21 @@ dcg_status dcg_update_subspace(dcg_ctx* ctx, int32_t* k_new);
  * since the last update), CUDA (enqueueing failed). */
 dcg_status dcg_update_subspace_async(dcg_ctx* ctx);
 
-/* (Harmonic) Ritz values of the last update, descending (float64, host).
+/* (Harmonic) Ritz values of the last update, descending (float64, host): the
+ * kept ones are float64 Rayleigh quotients of the pencil (dcg_get_pencil) at
+ * the float32 eigenvectors; the others come from the float32 eigen-solve.
  *   theta host, capacity cap; m host: number of values (cols(Z)). */
 dcg_status dcg_get_ritz_values(dcg_ctx* ctx, double* theta, int32_t cap, int32_t* m);
+
+/* The float64 pencil (F, G) of the last update, row-major m x m each, m =
+ * columns of Z = [W, P] (F = (AZ)^T Z and G = (AZ)^T AZ for the harmonic
+ * extraction of Eq. 7; Z^T Z and Z^T A Z for the orthogonal one). The
+ * eigen-solve runs in float32 on the scaled pencil and the kept values are
+ * then the float64 Rayleigh quotients of this pencil at the float32 vectors,
+ * so dcg_get_ritz_values can be checked against a float64 solve of (F, G).
+ *   F, G   host, capacity cap doubles each (cap >= m * m), or NULL to query m.
+ *   m      host, may be NULL. */
+dcg_status dcg_get_pencil(dcg_ctx* ctx, double* F, double* G, int32_t cap, int32_t* m);
 
 /* Prior knowledge for the next solve or a checkpoint restore (Fig. 1 caption):
  * W device, column-major n x k (0 <= k <= cfg.k), copied. */

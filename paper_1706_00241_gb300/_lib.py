@@ -85,6 +85,7 @@ SIGNATURES = {
     "dcg_update_subspace": (_I32, [_P, _PI32]),
     "dcg_update_subspace_async": (_I32, [_P]),
     "dcg_get_ritz_values": (_I32, [_P, _PD, _I32, _PI32]),
+    "dcg_get_pencil": (_I32, [_P, _PD, _PD, _I32, _PI32]),
     "dcg_set_subspace": (_I32, [_P, _P, _I32]),
     "dcg_get_subspace": (_I32, [_P, _P, _PI32]),
     "dcg_get_history": (_I32, [_P, _PD, _I32, _PI32]),

@@ -43,6 +43,7 @@ struct dcg_ctx {
   int *k_out = nullptr, *ritz_status = nullptr;
   int k_active = 0;
   int m_last = 0;        // number of harmonic Ritz values of the last update
+  int m_pencil = 0;      // order of the last update's pencil F, G (columns of Z)
   bool have_solve = false;
   bool ritz_pending = false;  // an update was enqueued and its result not yet read
   int last_iters = 0;
@@ -942,6 +943,7 @@ static dcg_status enqueue_update(dcg_ctx* c) {
   a.colscale = c->colscale;
   cudaStream_t s = c->stream;
   CK(launch_ritz(a, c->num_sms, c->w.XW + c->w.n, s));
+  c->m_pencil = kk + ns;
   CK(cudaMemcpyAsync(c->h_small, c->k_out, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(c->h_small + 2, c->ritz_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   c->have_solve = false;
@@ -1008,6 +1010,19 @@ extern "C" dcg_status dcg_get_ritz_values(dcg_ctx* c, double* theta, int32_t cap
   if (!theta || cap <= 0 || c->m_last == 0) return DCG_OK;
   const int cnt = std::min(cap, c->m_last);
   CK(cudaMemcpyAsync(theta, c->theta, size_t(cnt) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_get_pencil(dcg_ctx* c, double* F, double* G, int32_t cap, int32_t* m) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  { const dcg_status pend = finish_update(c); if (pend != DCG_OK) return pend; }
+  const int mp = c->m_last > 0 ? c->m_pencil : 0;
+  if (m) *m = mp;
+  if (mp == 0 || !F || !G) return DCG_OK;
+  if (cap < mp * mp) return fail(c, DCG_ERR_INVALID_ARG, "cap is below m * m");
+  CK(cudaMemcpyAsync(F, c->F, size_t(mp) * mp * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(G, c->G, size_t(mp) * mp * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return DCG_OK;
 }

@@ -890,6 +890,50 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_ritz_eig(RitzArgs a, int m, 
   }
 }
 
+// Float64 refinement of the kept (harmonic) Ritz values: for every selected
+// coefficient vector u = U[:, c] (float32 from the eigen-solve above) the
+// pencil's Rayleigh quotient theta = (u^T G u) / (u^T F u) in float64, with
+// F and G the float64 matrices of Eq. 7 (or of the orthogonal projection).
+// For the symmetric pencil the quotient's error is quadratic in the vector's
+// (a float32 vector good to ~1e-5 gives theta to ~1e-10), so the values the
+// selection keeps are float64-accurate; the basis W itself is that of the
+// float32 vectors. One CTA per selected vector; the quadratic forms see the
+// symmetric part of F and G whatever the rounding of their two triangles.
+__global__ void __launch_bounds__(256) k_ritz_rq(RitzArgs a, int m_orig) {
+  if (*a.status != DCG_OK) return;
+  const int k_new = a.k_out[0], m = a.k_out[1];
+  const int c = blockIdx.x;
+  if (c >= k_new) return;
+  __shared__ double u[kMaxM];
+  for (int i = threadIdx.x; i < m_orig; i += blockDim.x) u[i] = double(a.U[int64_t(c) * m_orig + i]);
+  __syncthreads();
+  double sf = 0.0, sg = 0.0;
+  for (int idx = threadIdx.x; idx < m_orig * m_orig; idx += blockDim.x) {
+    const int i = idx / m_orig, j = idx % m_orig;
+    const double w = u[i] * u[j];
+    sf = fma(w, a.F[idx], sf);
+    sg = fma(w, a.G[idx], sg);
+  }
+  __shared__ double s_f[8], s_g[8];
+  sf = warp_sum(sf);
+  sg = warp_sum(sg);
+  if ((threadIdx.x & 31) == 0) {
+    s_f[threadIdx.x >> 5] = sf;
+    s_g[threadIdx.x >> 5] = sg;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tf = 0.0, tg = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      tf += s_f[w];
+      tg += s_g[w];
+    }
+    // the c-th selected value: descending index c (largest) or m - 1 - c
+    const int idx = a.select == DCG_SELECT_SMALLEST ? m - 1 - c : c;
+    if (tf > 0.0) a.theta[idx] = tg / tf;
+  }
+}
+
 // W_out[:, c] = Z U[:, c] for c < k_new (Z = [W | P]); thread per row, 32
 // output columns per pass.
 __global__ void __launch_bounds__(256) k_zu(RitzArgs a, int m, int k_new) {
@@ -1010,6 +1054,8 @@ cudaError_t launch_ritz(const RitzArgs& a, int num_sms, float* dstW, cudaStream_
     if (e != cudaSuccess) return e;
   }
   k_ritz_eig<<<1, EIG_THREADS, EIG_SMEM_MAX, s>>>(a, m, k_new);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_ritz_rq<<<k_new, 256, 0, s>>>(a, m);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_zu<<<num_sms, 256, size_t(m) * 32 * sizeof(float), s>>>(a, m, k_new);  // k_new is an upper bound; k_zu reads k_out
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

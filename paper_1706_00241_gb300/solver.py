@@ -187,6 +187,18 @@ class DefCG:
                 "dcg_get_ritz_values")
         return out[:m.value]
 
+    def pencil(self):
+        """(F, G) of the last extraction as float64 numpy arrays (m x m)."""
+        m = ctypes.c_int32()
+        self._check(self.lib.dcg_get_pencil(self._ctx, None, None, 0, ctypes.byref(m)), "dcg_get_pencil")
+        F = np.zeros(m.value * m.value, dtype=np.float64)
+        G = np.zeros_like(F)
+        if m.value:
+            pd = ctypes.POINTER(ctypes.c_double)
+            self._check(self.lib.dcg_get_pencil(self._ctx, F.ctypes.data_as(pd), G.ctypes.data_as(pd), F.size,
+                                                ctypes.byref(m)), "dcg_get_pencil")
+        return F.reshape(m.value, m.value), G.reshape(m.value, m.value)
+
     def get_subspace(self) -> torch.Tensor:
         """Current W as a (k_active, n) tensor (row j is column j of W)."""
         k = ctypes.c_int32(0)
