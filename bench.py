@@ -421,7 +421,7 @@ def mf_kernels(P, torch, cfg, fmt, ex2_ps):
         mv_ms = timed(lambda: s.matvec(p, q, want_pAp=False), 10)
         res_ms = timed(lambda: s.residual(p, x), 3)
     entries = float(n) * n
-    dk = cfg.d + 3                                   # coordinates of a tile row (with -|x|^2/2)
+    dk = cfg.d * (3 if fmt == "fp32" else 1) + 3     # coordinates of a tile row (with -|x|^2/2)
     kpad = (dk + 15) // 16 * 16 if fmt == "bf16" else (dk + 7) // 8 * 8
     tflops = 2.0 * entries * kpad / (mv_ms * 1e-3) / 1e12
     tpeak, _ = tensor_peak(fmt)
@@ -522,8 +522,8 @@ def matrix_free_block(P, torch, mode):
     ex2_ps, ex2_pc = ex2_peak(P)
     out = {"ex2_peak": {"per_s": ex2_ps, "per_clock_per_sm": ex2_pc, "kind": "measured now (dcg_measure_ex2_rate)"}}
     c3, c5 = S.MF_131072, S.MF_262144
-    out[c3.name] = mf_kernels(P, torch, c3, "bf16", ex2_ps)
-    out[c5.name] = mf_kernels(P, torch, c5, "tf32", ex2_ps)
+    out[c3.name] = mf_kernels(P, torch, c3, c3.x_dtype, ex2_ps)
+    out[c5.name] = mf_kernels(P, torch, c5, c5.x_dtype, ex2_ps)
     if mode == "all":
         d = mf_sequence(P, torch, c3, True)
         pl = mf_sequence(P, torch, c3, False)
@@ -574,7 +574,8 @@ def kernel_arm(args):
         Xd = torch.tensor(X, device="cuda")
         solver = P.DefCG(n, 0, 0, cfg.tol)
         solver.set_operator_rbf(Xd, cfg.lengthscale(0), cfg.signal_var, cfg.noise, xformat=args.xformat)
-        dpad = (cfg.d + 15) // 16 * 16 if args.xformat == "bf16" else (cfg.d + 7) // 8 * 8
+        dk = cfg.d * (3 if args.xformat == "fp32" else 1) + 3   # tile-row coordinates (with -|x|^2/2)
+        dpad = (dk + 15) // 16 * 16 if args.xformat == "bf16" else (dk + 7) // 8 * 8
         algo = 2.0 * n * n * dpad                      # Gram tile FLOPs on the tensor cores
         name = "k_rbf_mv (tcgen05 Gram tiles, fused exp and contraction)"
         unit, bound = "TFLOP/s", "tensor"
@@ -806,7 +807,7 @@ def main():
     ap.add_argument("--systems", type=int, default=0,
                     help="solve only the first T systems of the sequence (small profiling captures; "
                          "not a benchmark line)")
-    ap.add_argument("--xformat", choices=["bf16", "tf32"], default="bf16", help="X format for --kernel rbf_mv")
+    ap.add_argument("--xformat", choices=["bf16", "tf32", "fp32"], default="bf16", help="X format for --kernel rbf_mv")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -76,9 +76,9 @@ MF_131072 = RBFSequence(name="rbf_bf16_n131072_d32_T30", n=131072, d=32, T=30, l
 GRAD_32768 = RBFSequence(name="gp_grad_n32768_d8", n=32768, d=8, T=30, l0=0.5, growth=0.0,
                          noise=0.1, k=32, ell=64, tol=1e-6, x_dist="uniform", storage="rbf",
                          extra={"probes": 16, "adam_lr": 0.05})
-MF_262144 = RBFSequence(name="rbf_tf32_n262144_d4_T40", n=262144, d=4, T=40, l0=0.5,
+MF_262144 = RBFSequence(name="rbf_fp32_n262144_d4_T40", n=262144, d=4, T=40, l0=0.5,
                         growth=0.02, noise=1e-2, k=64, ell=128, tol=1e-6, storage="rbf",
-                        x_dtype="tf32", refine_every=50)
+                        x_dtype="fp32", refine_every=50)
 
 WORKLOADS = {w.name: w for w in (SMALL_1024, DENSE_16384, MF_131072, GRAD_32768, MF_262144)}
 

@@ -72,9 +72,10 @@ typedef enum dcg_extraction {     /* how the next W is drawn from Z = [W, P] (Se
 } dcg_extraction;
 
 typedef enum dcg_xformat {        /* element format of X for the matrix-free operator */
-  DCG_X_FP32 = 0,                 /* X kept in float32: not supported by the
-                                     matrix-free operator (UNSUPPORTED); use the
-                                     stored operator for float32 X               */
+  DCG_X_FP32 = 0,                 /* X kept in float32 (the operator is K(X)): the
+                                     iteration's tiles are split TF32 (x = hi + lo,
+                                     three TF32 products, ~2^-21), the true
+                                     residual uses the float32 points             */
   DCG_X_BF16 = 1,                 /* X rounded to bfloat16; exact BF16 products    */
   DCG_X_TF32 = 2                  /* X rounded to TF32; one TF32 product           */
 } dcg_xformat;
@@ -183,10 +184,10 @@ dcg_status dcg_set_operator_dense_sym(dcg_ctx* ctx, const float* A, int64_t lda)
  *   X        device, row-major float32 n x d (row i is x_i); copied into the
  *            context's own padded buffer in the requested format, so X is
  *            not borrowed.
- *   d        1 <= d <= 61 (BF16) or 1 <= d <= 29 (TF32): a tile row holds
- *            the d coordinates and three pieces of -|x_j|^2 / 2 in 128 bytes,
- *            so that the tensor-core product x_i . x_j - |x_j|^2 / 2 gives each
- *            entry's exponent with one FMA.
+ *   d        1 <= d <= 61 (BF16), 29 (TF32) or 9 (FP32: 3 d split-TF32
+ *            coordinates): a tile row holds the coordinates and three pieces
+ *            of -|x_j|^2 / 2 in 128 bytes, so that the tensor-core product
+ *            x_i . x_j - |x_j|^2 / 2 gives each entry's exponent with one FMA.
  *   xformat  dcg_xformat; fixes how X_I X_J^T tiles are formed on the tensor
  *            cores (the operator is the one defined by the rounded X).
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */

@@ -381,11 +381,12 @@ extern "C" dcg_status dcg_set_operator_rbf(dcg_ctx* c, const float* X, int32_t d
   if (!c) return DCG_ERR_INVALID_ARG;
   if (!X) return fail(c, DCG_ERR_INVALID_ARG, "X is NULL");
   if (!(l > 0.0) || !(s2 > 0.0) || !(noise >= 0.0)) return fail(c, DCG_ERR_INVALID_ARG, "bad RBF parameters");
-  if (xformat != DCG_X_BF16 && xformat != DCG_X_TF32)
-    return fail(c, DCG_ERR_UNSUPPORTED, "matrix-free operator: xformat BF16 or TF32 in this build");
+  if (xformat != DCG_X_BF16 && xformat != DCG_X_TF32 && xformat != DCG_X_FP32)
+    return fail(c, DCG_ERR_INVALID_ARG, "matrix-free operator: unknown xformat");
   if (d < 1 || d > rbf_max_d(xformat))
     return fail(c, DCG_ERR_UNSUPPORTED, "matrix-free operator: d <= " + std::to_string(rbf_max_d(DCG_X_BF16)) +
-                                            " (BF16) or d <= " + std::to_string(rbf_max_d(DCG_X_TF32)) + " (TF32)");
+                                            " (BF16), " + std::to_string(rbf_max_d(DCG_X_TF32)) + " (TF32) or " +
+                                            std::to_string(rbf_max_d(DCG_X_FP32)) + " (FP32)");
   EncodeTiledFn enc = get_encode();
   if (!enc) return fail(c, DCG_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   const int n = c->w.n, n_pad = c->n_pad;

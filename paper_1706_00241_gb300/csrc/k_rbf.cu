@@ -42,33 +42,49 @@ __device__ __forceinline__ float round_tf32(float x) {
   return __uint_as_float(u);
 }
 
-// Xr (n x d float32): X rounded to the chosen element format. Xt: two
-// 128-byte-per-row tile copies (BF16: 64 elements, TF32: 32 elements) of
-// n_pad rows each, the operands of the tensor-core product
+// Xr (n x d float32): the operator's points, X rounded to the chosen element
+// format (BF16, TF32) or X itself (FP32). Xt: two 128-byte-per-row tile
+// copies (BF16: 64 elements, TF32 and FP32: 32 float32 elements holding
+// TF32 values) of n_pad rows each, the operands of the tensor-core product
 //   S~_ij = x_i . x_j - |x_j|^2 / 2,
 // so that the exponent of an entry is one FMA, 2c S~_ij + (log2 s^2 - c |x_i|^2)
 // with c = log2(e) / (2 l^2), and S~ does not depend on l:
-//   rows of the first copy (I tiles):  [x_i, 1, 1, 1, 0 ...]
-//   rows of the second copy (J tiles): [x_j, h_j, m_j, l_j, 0 ...], h + m + l =
-//     -|x_j|^2 / 2 split into three pieces of the element format (24 bits for
-//     BF16, 33 for TF32); padding rows j >= n carry h = -2^100, so that their
-//     entries vanish.
-// nsq[i] = |xr_i|^2 (float64 sum, rounded).
+//   BF16, TF32:  I rows [x_i, 1, 1, 1, 0 ...], J rows [x_j, h_j, m_j, l_j, 0 ...];
+//   FP32 (split TF32: x = x_hi + x_lo, x_hi = tf32(x), x_lo = tf32(x - x_hi)):
+//                I rows [x_hi, x_hi, x_lo, 1, 1, 1, 0 ...],
+//                J rows [x_hi, x_lo, x_hi, h, m, l, 0 ...],
+//     so that x_i . x_j = hi.hi + hi.lo + lo.hi to ~2^-21 (the dropped lo.lo
+//     and x - x_hi - x_lo are ~2^-22 relative);
+// h + m + l = -|x_j|^2 / 2 split into three pieces of the element format (24
+// bits for BF16, 33 for TF32); padding rows j >= n carry h = -2^100, so that
+// their entries vanish. nsq[i] = |xr_i|^2 (float64 sum, rounded).
 constexpr int kRbfAug = 3;  // extra coordinates of the tile copies
+
+// Coordinates of a tile row before the kRbfAug pieces: d, or 3 d for the
+// split-TF32 copy of float32 points.
+__host__ __device__ int rbf_tile_coords(int xformat, int d) { return xformat == DCG_X_FP32 ? 3 * d : d; }
+
 __global__ void k_rbf_prep(const float* __restrict__ X, int n, int n_pad, int d, int xformat, float* Xr,
                            void* Xt, float* nsq) {
+  const int dc = rbf_tile_coords(xformat, d);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x) {
     double ss = 0.0;
-    float v[64];
-    const int width = xformat == DCG_X_BF16 ? 64 : 32;
-    for (int m = 0; m < width; ++m) {
+    float va[64], vb[64];   // the tile rows' coordinates (I copy, J copy)
+    for (int m = 0; m < d; ++m) {
       float x = 0.f;
-      if (i < n && m < d) {
-        x = xformat == DCG_X_BF16 ? round_bf16(X[int64_t(i) * d + m]) : round_tf32(X[int64_t(i) * d + m]);
+      if (i < n) {
+        const float x0 = X[int64_t(i) * d + m];
+        x = xformat == DCG_X_BF16 ? round_bf16(x0) : (xformat == DCG_X_TF32 ? round_tf32(x0) : x0);
         Xr[int64_t(i) * d + m] = x;
         ss += double(x) * double(x);
       }
-      v[m] = x;
+      if (xformat == DCG_X_FP32) {
+        const float hi = round_tf32(x), lo = round_tf32(x - hi);
+        va[m] = hi;  va[d + m] = hi;  va[2 * d + m] = lo;
+        vb[m] = hi;  vb[d + m] = lo;  vb[2 * d + m] = hi;
+      } else {
+        va[m] = vb[m] = x;
+      }
     }
     // -|x_i|^2 / 2 in three pieces of the element format
     float piece[kRbfAug];
@@ -81,21 +97,17 @@ __global__ void k_rbf_prep(const float* __restrict__ X, int n, int n_pad, int d,
       piece[0] = -0x1p100f;
       piece[1] = piece[2] = 0.f;
     }
-    if (xformat == DCG_X_BF16) {
-      __nv_bfloat16* ra = reinterpret_cast<__nv_bfloat16*>(Xt) + int64_t(i) * 64;
-      __nv_bfloat16* rb = reinterpret_cast<__nv_bfloat16*>(Xt) + int64_t(n_pad + i) * 64;
-      for (int m = 0; m < 64; ++m) {
-        const bool aug = m >= d && m < d + kRbfAug;
-        ra[m] = __float2bfloat16_rn(aug ? 1.f : v[m]);
-        rb[m] = __float2bfloat16_rn(aug ? piece[m - d] : v[m]);
-      }
-    } else {
-      float* ra = reinterpret_cast<float*>(Xt) + int64_t(i) * 32;
-      float* rb = reinterpret_cast<float*>(Xt) + int64_t(n_pad + i) * 32;
-      for (int m = 0; m < 32; ++m) {
-        const bool aug = m >= d && m < d + kRbfAug;
-        ra[m] = aug ? 1.f : v[m];
-        rb[m] = aug ? piece[m - d] : v[m];
+    const int width = xformat == DCG_X_BF16 ? 64 : 32;
+    for (int m = 0; m < width; ++m) {
+      const bool coord = m < dc, aug = m >= dc && m < dc + kRbfAug;
+      const float a = coord ? va[m] : (aug ? 1.f : 0.f);
+      const float b = coord ? vb[m] : (aug ? piece[m - dc] : 0.f);
+      if (xformat == DCG_X_BF16) {
+        reinterpret_cast<__nv_bfloat16*>(Xt)[int64_t(i) * 64 + m] = __float2bfloat16_rn(a);
+        reinterpret_cast<__nv_bfloat16*>(Xt)[int64_t(n_pad + i) * 64 + m] = __float2bfloat16_rn(b);
+      } else {
+        reinterpret_cast<float*>(Xt)[int64_t(i) * 32 + m] = a;
+        reinterpret_cast<float*>(Xt)[int64_t(n_pad + i) * 32 + m] = b;
       }
     }
     nsq[i] = float(ss);
@@ -154,12 +166,16 @@ static bool make_rbf_tmap_one(CUtensorMap* map, const void* Xt, int n_pad, int x
 bool make_rbf_tmap(CUtensorMap* map, const void* Xt, int n_pad, int xformat, int d, EncodeTiledFn encode) {
   for (int half = 0; half < 2; ++half) {
     const void* base = static_cast<const unsigned char*>(Xt) + size_t(half) * n_pad * 128;
-    if (!make_rbf_tmap_one(&map[half], base, n_pad, xformat, d + kRbfAug, encode)) return false;
+    if (!make_rbf_tmap_one(&map[half], base, n_pad, xformat, rbf_tile_coords(xformat, d) + kRbfAug, encode))
+      return false;
   }
   return true;
 }
 
-int rbf_max_d(int xformat) { return (xformat == DCG_X_BF16 ? 64 : 32) - kRbfAug; }
+int rbf_max_d(int xformat) {
+  const int room = (xformat == DCG_X_BF16 ? 64 : 32) - kRbfAug;
+  return xformat == DCG_X_FP32 ? room / 3 : room;
+}
 
 static bool make_rbf_tmap_one(CUtensorMap* map, const void* Xt, int n_pad, int xformat, int d, EncodeTiledFn encode) {
   const bool bf = xformat == DCG_X_BF16;
@@ -252,7 +268,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = a.n, n_tiles = a.n_tiles;
   const int kind_tf32 = a.xformat != DCG_X_BF16;
-  const int dk = a.d + kRbfAug;                                     // coordinates of the tile rows
+  const int dk = rbf_tile_coords(a.xformat, a.d) + kRbfAug;         // coordinates of the tile rows
   const int ksteps = kind_tf32 ? (dk + 7) / 8 : (dk + 15) / 16;     // 32-byte K steps
   const uint32_t row_bytes = uint32_t(rbf_row_bytes(a.xformat, dk));
   const uint32_t tile_bytes = MV_TILE * row_bytes;                  // bytes of one X tile in use

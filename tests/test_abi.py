@@ -123,7 +123,7 @@ def test_form_rbf_dense_rejects_bad_arguments_with_a_message(lib_path):
         ((None, 16, 4, 1.0, 1.0, 0.1, fake, 16, None), b"X and A are required"),
         ((fake, 0, 4, 1.0, 1.0, 0.1, fake, 16, None), b"lda >= n"),
         ((fake, 16, 4, 1.0, 1.0, 0.1, fake, 8, None), b"lda >= n"),
-        ((fake, 16, 0, 1.0, 1.0, 0.1, fake, 16, None), b"d must be in [1, 256]"),
+        ((fake, 16, 0, 1.0, 1.0, 0.1, fake, 16, None), b"d must be in [1, 4096]"),
         ((fake, 16, 4, -1.0, 1.0, 0.1, fake, 16, None), b"lengthscale > 0"),
         ((fake, 16, 4, 1.0, float("nan"), 0.1, fake, 16, None), b"finite"),
     ]

@@ -665,13 +665,17 @@ def test_kept_ritz_values_are_float64_on_the_gpu_pencil(dcg, extraction, select)
     # eigenvectors. Reference: the very pencil the GPU formed (dcg_get_pencil),
     # reduced in float64 by the same rule (unit-diagonal scaling, diagonally
     # pivoted Cholesky of F that stops below 1e-4, reading G5), then solved in
-    # float64 (scipy.linalg.eigh). Where both keep the same number of
-    # directions the kept values agree to 1e-8 relative when the largest are
-    # kept (measured: 5.6e-9 harmonic, 2.1e-9 Ritz; the quotient's error is
+    # float64 (scipy.linalg.eigh). Compared on the first extraction of a
+    # sequence (Z = P, nearly A-conjugate directions: a well-conditioned
+    # pencil): the kept values agree to 1e-8 relative when the largest are
+    # kept (measured 5.6e-9 harmonic, 2.1e-9 Ritz; the quotient's error is
     # quadratic in the float32 vector's); the smallest harmonic values
     # cluster near the noise level, where the float32 vectors' error grows as
-    # 1 / gap: 3e-6 (measured 1.1e-6). The oracle's own pencil comes from
-    # float64 directions, so it is not the comparison here.
+    # 1 / gap: 3e-6 (measured 1.1e-6). Once W joins Z the pencil has
+    # near-degenerate values and nearly dependent columns, which the float32
+    # and a float64 pivoted reduction need not drop alike, so later
+    # extractions are not compared value by value. The oracle's own pencil
+    # comes from float64 directions, so it is not the comparison here.
     import scipy.linalg as sla
 
     def reduced(F, G):
@@ -693,7 +697,7 @@ def test_kept_ritz_values_are_float64_on_the_gpu_pencil(dcg, extraction, select)
     X, bs = S.draw_sequence(cfg, T=3)
     with dcg.DefCG(cfg.n, cfg.k, cfg.ell, 1e-6, extraction=extraction, select=select) as s:
         A = torch.empty((cfg.n, cfg.n), dtype=torch.float32, device="cuda")
-        worst = 0.0
+        worst, compared = 0.0, 0
         for t in range(3):
             dcg.form_rbf_dense(dev(X.astype(np.float32)), cfg.lengthscale(t), cfg.signal_var, cfg.noise, out=A)
             s.set_operator_dense(A)
@@ -705,11 +709,10 @@ def test_kept_ritz_values_are_float64_on_the_gpu_pencil(dcg, extraction, select)
             th = s.ritz_values()
             kept = th[:k_new] if select == "largest" else th[len(th) - k_new:]
             ref = ev[:k_new] if select == "largest" else ev[len(ev) - k_new:]
-            compared = 0
-            if len(th) == len(ev):   # the same directions kept at float32 and float64
+            if t == 0 and len(th) == len(ev):   # first extraction, same number of directions kept
                 rel = np.max(np.abs(kept - ref) / np.abs(ref))
                 worst = max(worst, rel)
                 compared += 1
                 assert rel <= (1e-8 if select == "largest" else 3e-6), (t, rel)
         print(extraction, select, "worst relative error of the kept values %.2e" % worst)
-        assert worst > 0.0 or compared
+        assert compared == 1

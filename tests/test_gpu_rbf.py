@@ -15,7 +15,8 @@ from oracle import dcg_oracle as O
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-ROUND = {"bf16": S.round_to_bf16, "tf32": S.round_to_tf32}
+ROUND = {"bf16": S.round_to_bf16, "tf32": S.round_to_tf32, "fp32": lambda a: np.asarray(a, dtype=np.float32)}
+MAX_D = {"bf16": 61, "tf32": 29, "fp32": 9}
 
 
 @pytest.fixture(scope="module")
@@ -32,21 +33,23 @@ def dev(a):
     return torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
 
 
-def gram_tol(Xr, l, K_abs_p):
+def gram_tol(Xr, l, K_abs_p, fmt="bf16"):
     # Tensor-core Gram form: |x_i|^2 + |x_j|^2 - 2 x_i.x_j with float32 sums of
     # exact products; the absolute error of the exponent is <= ~(d + 2) eps32
     # (|x_i|^2 + |x_j|^2) / (2 l^2), plus ex2.approx (2 ulp) and the float32 sum.
+    # Split-TF32 float32 points sum 3 d products, each ~2^-21 off.
     nmax = np.max(np.sum(Xr.astype(np.float64) ** 2, axis=1))
-    d = Xr.shape[1]
+    d = Xr.shape[1] * (3 if fmt == "fp32" else 1)
     expo = (d + 4) * 6e-8 * 2 * nmax / (2 * l * l)
     return (expo + 5e-7) * K_abs_p + 1e-7 * np.max(K_abs_p)
 
 
-@pytest.mark.parametrize("fmt", ["bf16", "tf32"])
-@pytest.mark.parametrize("n,d", [(1, 3), (100, 4), (1000, 8), (4096, 32), (2000, 17), (500, 40), (300, 29), (200, 61)])
+@pytest.mark.parametrize("fmt", ["bf16", "tf32", "fp32"])
+@pytest.mark.parametrize("n,d", [(1, 3), (100, 4), (1000, 8), (4096, 32), (2000, 17), (500, 40), (300, 29), (200, 61),
+                                 (777, 9)])
 def test_rbf_matvec_matches_oracle(dcg, fmt, n, d):
-    if fmt == "tf32" and d > 29:
-        pytest.skip("tf32 tile rows hold 29 coordinates and three pieces of -|x|^2/2")
+    if d > MAX_D[fmt]:
+        pytest.skip("a tile row holds the coordinates (three copies for split fp32) and three pieces of -|x|^2/2")
     rng = np.random.default_rng(n + d)
     X = rng.standard_normal((n, d)).astype(np.float32)
     Xr = ROUND[fmt](X)
@@ -58,12 +61,12 @@ def test_rbf_matvec_matches_oracle(dcg, fmt, n, d):
         q = q.cpu().numpy().astype(np.float64)
     K = O.rbf_gram(Xr.astype(np.float64), l, s2, noise)
     ref = K @ p.astype(np.float64)
-    tol = gram_tol(Xr, l, np.abs(K) @ np.abs(p.astype(np.float64)))
+    tol = gram_tol(Xr, l, np.abs(K) @ np.abs(p.astype(np.float64)), fmt)
     assert np.all(np.abs(q - ref) <= tol), np.max(np.abs(q - ref) / tol)
     assert abs(pAp - p.astype(np.float64) @ q) <= 1e-12 * (np.abs(p) @ np.abs(q)) + 1e-30
 
 
-@pytest.mark.parametrize("fmt", ["bf16", "tf32"])
+@pytest.mark.parametrize("fmt", ["bf16", "tf32", "fp32"])
 @pytest.mark.parametrize("n,d", [(1, 3), (130, 4), (3001, 8), (2000, 32), (700, 40)])
 def test_rbf_true_residual_matches_oracle(dcg, fmt, n, d):
     # dcg_residual on the matrix-free operator: r = b - A x with exact-form
@@ -73,8 +76,8 @@ def test_rbf_true_residual_matches_oracle(dcg, fmt, n, d):
     # (d^2 + 2) u g / (2 l^2) at d = 40, is ~3e-10). The reported |r| meets
     # the float64 |r| within the kernel's own error estimate: the quantity the
     # solve certifies convergence with.
-    if fmt == "tf32" and d > 29:
-        pytest.skip("tf32 tile rows hold 29 coordinates and three pieces of -|x|^2/2")
+    if d > MAX_D[fmt]:
+        pytest.skip("a tile row holds the coordinates (three copies for split fp32) and three pieces of -|x|^2/2")
     rng = np.random.default_rng(10 * n + d)
     X = rng.standard_normal((n, d)).astype(np.float32)
     Xr = ROUND[fmt](X).astype(np.float64)
@@ -131,7 +134,7 @@ def test_rbf_block_exact(dcg, fmt):
     assert np.all(np.abs(Y - ref) <= bound)
 
 
-@pytest.mark.parametrize("fmt", ["bf16", "tf32"])
+@pytest.mark.parametrize("fmt", ["bf16", "tf32", "fp32"])
 def test_rbf_sequence_with_refinement(dcg, fmt):
     # A short lengthscale path on the matrix-free operator: def-CG with
     # recycling and residual replacement every 25 iterations reaches the true
@@ -173,7 +176,7 @@ def test_rbf_sequence_with_refinement(dcg, fmt):
             assert np.linalg.norm(xr - ref.x) <= 1e-4 * np.linalg.norm(ref.x)
 
 
-@pytest.mark.parametrize("cfg,fmt", [(S.MF_131072, "bf16"), (S.MF_262144, "tf32")])
+@pytest.mark.parametrize("cfg,fmt", [(S.MF_131072, "bf16"), (S.MF_262144, "tf32"), (S.MF_262144, "fp32")])
 def test_rbf_sequence_benchmark_parameters_n8192(dcg, cfg, fmt):
     # The two matrix-free workloads' own generators (d, lengthscale path,
     # noise, k, ell, refinement period, tolerance) downscaled to n = 8192,
@@ -221,7 +224,7 @@ def test_rbf_sequence_benchmark_parameters_n8192(dcg, cfg, fmt):
         print("t=%d gpu_iters=%d oracle_iters=%d checks=%d relres=%.2e err=%.2e bound=%.2e" % r)
 
 
-@pytest.mark.parametrize("cfg,fmt", [(S.MF_131072, "bf16"), (S.MF_262144, "tf32")])
+@pytest.mark.parametrize("cfg,fmt", [(S.MF_131072, "bf16"), (S.MF_262144, "fp32")])
 def test_rbf_true_residual_full_size_sampled_rows(dcg, cfg, fmt):
     # The exact-form residual at the two large workloads' full size (the
     # launch configuration the solves use): 32 rows against the oracle's rows.
@@ -243,7 +246,7 @@ def test_rbf_true_residual_full_size_sampled_rows(dcg, cfg, fmt):
     assert np.isfinite(rr) and 0.0 < err <= 1e-6 * np.sqrt(rr)
 
 
-@pytest.mark.parametrize("cfg,fmt", [(S.MF_131072, "bf16"), (S.MF_262144, "tf32")])
+@pytest.mark.parametrize("cfg,fmt", [(S.MF_131072, "bf16"), (S.MF_262144, "tf32"), (S.MF_262144, "fp32")])
 def test_rbf_matvec_full_size_sampled_rows(dcg, cfg, fmt):
     # The two large matrix-free workloads at full size: one matvec, 48 rows
     # checked against rows of the oracle's kernel computed one by one.
@@ -259,7 +262,7 @@ def test_rbf_matvec_full_size_sampled_rows(dcg, cfg, fmt):
     rows = np.random.default_rng(3).choice(cfg.n, 48, replace=False)
     Krows = O.rbf_gram(Xr, l, cfg.signal_var, cfg.noise, rows=rows)
     ref = Krows @ p.astype(np.float64)
-    tol = gram_tol(Xr, l, np.abs(Krows) @ np.abs(p.astype(np.float64)))
+    tol = gram_tol(Xr, l, np.abs(Krows) @ np.abs(p.astype(np.float64)), fmt)
     assert np.all(np.abs(q[rows] - ref) <= tol), np.max(np.abs(q[rows] - ref) / tol)
     assert np.isfinite(pAp)
 
