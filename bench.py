@@ -171,10 +171,10 @@ def launches_of(infos, deflate):
         fin = 1 if i["status"] != 0 else 0
         total += 1                       # form A_t
         total += 8 + 1                   # start of solve + loop gate
-        total += 3 * i["iters"] + 3 * checks
+        total += 4 * i["iters"] + 3 * checks   # symmetric matvec (2 launches), fused kernel, gate
         total += 2 + fin                 # final gate, final residual, finalize
         if deflate:
-            total += 8                   # harmonic Ritz extraction
+            total += 9                   # harmonic Ritz extraction (with the float64 refinement)
     return total
 
 
@@ -566,6 +566,32 @@ def kernel_arm(args):
         workload = f"stored dense fp32 n={n}"
     elif args.kernel in ("apply_block", "form", "iter"):
         return kernel_arm_dense(args, P, torch, stream)
+    elif args.kernel == "resid":
+        # the exact-form true residual of the matrix-free operator (k_rbf_resid
+        # + k_rbf_resid_fin), on the bf16 n = 131072 workload's generator
+        cfg = S.MF_131072 if args.xformat == "bf16" else S.MF_262144
+        n = args.n or cfg.n
+        X, bs = S.draw_sequence(cfg.scaled(n, T=2) if n != cfg.n else cfg, T=2)
+        solver = P.DefCG(n, 0, 0, cfg.tol)
+        solver.set_operator_rbf(torch.tensor(X.astype(np.float32), device="cuda"), cfg.lengthscale(0),
+                                cfg.signal_var, cfg.noise, xformat=args.xformat)
+        b = torch.tensor(bs[1].astype(np.float32), device="cuda")
+        x = torch.tensor(bs[0], device="cuda")
+        for _ in range(args.warmup):
+            solver.residual(b, x)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            solver.residual(b, x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        solver.close()
+        print(json.dumps({"kernel": "k_rbf_resid + k_rbf_resid_fin (exact-form true residual)",
+                          "workload": f"matrix-free rbf n={n} d={cfg.d} {args.xformat}", "launch_ms": ms,
+                          "launches": args.steps, "entries_per_s": float(n) * n / (ms * 1e-3)}))
+        return
     else:
         cfg = S.MF_131072 if args.xformat == "bf16" else S.MF_262144
         n = args.n or cfg.n
@@ -801,7 +827,7 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the solve's kernels from the host instead of one CUDA graph "
                          "(profiling mode: ncu cannot list kernels inside conditional graphs)")
-    ap.add_argument("--kernel", choices=["gemv", "symv", "rbf_mv", "apply_block", "form", "iter"], default=None,
+    ap.add_argument("--kernel", choices=["gemv", "symv", "rbf_mv", "resid", "apply_block", "form", "iter"], default=None,
                     help="time one hot kernel alone (q = A p) instead of the sequence")
     ap.add_argument("--n", type=int, default=0, help="system size for --kernel (default: the workload's)")
     ap.add_argument("--systems", type=int, default=0,
