@@ -54,8 +54,8 @@ struct dcg_ctx {
   bool dense_sym = false;      // stored operator given as its upper triangle (symmetric matvec)
   float* sym_rowpart = nullptr;
   float* sym_colpart = nullptr;
-  int* sym_sched = nullptr;        // per-CTA item lists of the symmetric matvec: offsets, then items
-  int* sym_sched_items = nullptr;
+  int* sym_sched = nullptr;        // symmetric matvec: the item counter, then the items largest first
+  int sym_nitems = 0;
 
   // operator
   int op = OP_NONE;
@@ -345,14 +345,13 @@ static dcg_status set_dense(dcg_ctx* c, const float* A, int64_t lda, bool sym) {
   if (sym && !c->sym_rowpart) {
     CK(dalloc(c, &c->sym_rowpart, symv_rowpart_floats(c->w.n)));
     CK(dalloc(c, &c->sym_colpart, symv_colpart_floats(c->w.n)));
-    std::vector<int> off, items;
-    symv_schedule(c->w.n, c->num_sms, off, items);
-    CK(dalloc(c, &c->sym_sched, off.size() + items.size()));
-    CK(cudaMemcpyAsync(c->sym_sched, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->sym_sched + off.size(), items.data(), items.size() * sizeof(int),
-                       cudaMemcpyHostToDevice, c->stream));
+    std::vector<int> items;
+    symv_schedule(c->w.n, items);
+    CK(dalloc(c, &c->sym_sched, 1 + items.size()));  // zeroed: the counter starts at 0
+    CK(cudaMemcpyAsync(c->sym_sched + 1, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    c->sym_sched_items = c->sym_sched + off.size();
+    c->sym_nitems = int(items.size());
   }
   const bool same = (c->op == OP_DENSE && c->A == A && c->lda == lda && c->dense_sym == sym);
   if (!same) {
@@ -549,8 +548,9 @@ static cudaError_t op_matvec(dcg_ctx* c, const float* p, float* q, double* resul
     a.n = c->w.n;
     a.rowpart = c->sym_rowpart;
     a.colpart = c->sym_colpart;
-    a.sched_off = c->sym_sched;
-    a.sched_items = c->sym_sched_items;
+    a.sched_ctr = reinterpret_cast<unsigned int*>(c->sym_sched);
+    a.sched_items = c->sym_sched + 1;
+    a.nitems = c->sym_nitems;
     a.partials = partials;
     a.ticket = ticket;
     a.result = result;

@@ -85,6 +85,21 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Column sums of 32 per-lane values across a warp (reduce-scatter by
+// halving): afterwards lane l holds in v[0] the warp's sum of column l.
+__device__ __forceinline__ void warp_transpose_sum(float (&v)[32], int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const float send = up ? v[i] : v[i + s];
+      const float keep = up ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+}
+
 // Last-CTA detection: every CTA calls this after writing its partials with a
 // __threadfence(); exactly one CTA (the last to arrive) gets true and resets
 // the counter for the next launch. No CTA waits on another.

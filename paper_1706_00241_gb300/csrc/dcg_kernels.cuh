@@ -85,10 +85,12 @@ struct SymvArgs {
   int n;
   int nbands;          // set by launch_symv
   int nchunks;         // set by launch_symv
+  int ns;              // row stride of the partial buffers, set by launch_symv
   float* rowpart;      // symv_rowpart_floats(n)
   float* colpart;      // symv_colpart_floats(n)
-  const int* sched_off;    // per-CTA item lists (symv_schedule), device
-  const int* sched_items;
+  unsigned int* sched_ctr;  // item counter (zero between launches; k_symv_fin rewinds it)
+  const int* sched_items;   // the items, largest first (symv_schedule), device
+  int nitems;
   double* partials;    // >= symv_fin_grid(n) doubles
   unsigned int* ticket;
   double* result;      // p^T q
@@ -219,7 +221,7 @@ size_t symv_colpart_floats(int n);
 int symv_fin_grid(int n, int num_sms);
 cudaError_t symv_configure();
 cudaError_t launch_symv(const CUtensorMap* tmap, SymvArgs a, int num_sms, cudaStream_t s);
-void symv_schedule(int n, int ctas, std::vector<int>& off, std::vector<int>& items);
+void symv_schedule(int n, std::vector<int>& items);
 // Context-free q = A p on the library's fixed scratch (no allocation).
 int noalloc_max_ctas();
 cudaError_t noalloc_scratch(void** base);

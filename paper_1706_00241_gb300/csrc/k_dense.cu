@@ -371,69 +371,59 @@ int rowop_grid(int n, int num_sms) {
 // Symmetric stored matvec q = A p reading the upper triangle only (entries
 // j >= i), about half of the 4 n^2 bytes of the full GEMV: the stored kernel
 // is HBM-bound, so the bytes are the time.
-//   Work item (b, c): rows [64 b, 64 b + 64) (a band) x the columns of chunk
-//   c ([2048 c, 2048 c + 2048)) at or right of column 64 b; only the TMA
-//   boxes (256 columns x 8 rows) that reach column 64 b are loaded. The items
-//   are unequal (those on the diagonal load fewer boxes) and every CTA gets a
-//   list built on the host by longest-processing-time assignment (within ~2 %
-//   of the mean at n = 16384; a plain round robin over the triangle left some
-//   CTAs twice the mean).
-//   Element (i, j), j >= 64 b: the row sum takes A_ij p_j when j >= i, and
+//   Work item (b, c): rows [256 b, 256 b + 256) (a band) x the columns of
+//   chunk c ([512 c, 512 c + 512)) at or right of column 256 b; only the TMA
+//   boxes (256 columns x 8 rows) that reach column 256 b are loaded. A stage
+//   is 32 rows x 512 columns (4 x 2 boxes, 64 KB), an item at most 8 stages.
+//   Scheduling is dynamic: the items, sorted by size (largest first, built on
+//   the host once per n), are taken from a global counter by each CTA's
+//   producer, so a CTA that runs faster takes more of them and the SMs finish
+//   together (greedy list scheduling; a static assignment balanced the
+//   modelled cost but left the busiest SM ~10 % behind the mean).
+//   Element (i, j), j >= 256 b: the row sum takes A_ij p_j when j >= i, and
 //   the transposed contribution A_ij p_i goes to q_j when j > i. The masks
-//   matter only in stages whose rows meet the thread's columns (the band's
-//   diagonal block); elsewhere either both apply or, left of the band start,
-//   neither (p_j is zero there).
-//   A thread owns 8 columns of the chunk: its transposed sums over the band's
-//   64 rows stay in registers and need no reduction (colpart[b n + j]). Each
-//   consumer warp reduces the row sums of its 256 columns over its lanes; the
-//   last warp to finish a stage (a shared counter per slot) adds the 8 warps'
-//   values (rowpart[c n + i]). No warp waits for another, so a bounded wait
-//   that gives up in one warp cannot leave the others waiting. k_symv_fin adds
-//   the partials in a fixed order (deterministic):
+//   matter only in stages whose rows meet the warp's columns, and in the last
+//   band, where rows at or past n are not loaded (their shared memory holds
+//   stale data and must not enter the column sums).
+//   Consumer warp w owns columns 64 w .. 64 w + 63 of the chunk for all 32
+//   rows of a stage (two per lane): its transposed sums over the band's 256
+//   rows stay in registers, four chains of 64 rows each (colpart[b ns + j]). The 32 row sums of a stage
+//   are reduced over the lanes by a transposing shuffle tree and over the 8
+//   warps by the last warp to finish the stage (a shared counter per slot; no
+//   warp waits for another): rowpart[c ns + i]. k_symv_fin adds the partials
+//   in a fixed order (deterministic):
 //   q_i = sum_{c >= c0(b_i)} rowpart + sum_{b <= b_i} colpart, and p^T q.
 // ---------------------------------------------------------------------------
-constexpr int SY_H = 64;                   // rows per band: 8 row groups
-constexpr int SY_GROUPS = SY_H / RB_ROWS;
+constexpr int SY_H = 256;                       // rows per band
+constexpr int SY_W = 512;                       // columns per chunk
+constexpr int SY_BX = SY_W / RB_BOXW;           // column boxes per stage row: 2
+constexpr int SY_RG = RB_BOXES / SY_BX;         // row boxes per stage: 4
+constexpr int SY_SROWS = SY_RG * RB_ROWS;       // rows per stage: 32
+constexpr int SY_GROUPS = SY_H / SY_SROWS;      // stages per item: 8
+constexpr int SY_WCOLS = SY_W / RB_CONSUMER_WARPS;  // columns per consumer warp: 64
+static_assert(SY_WCOLS == 64 && SY_SROWS == 32 && SY_GROUPS == 8, "lane layout of k_symv_tma");
+static_assert(RB_BOXW % SY_WCOLS == 0, "a warp's columns lie in one box");
 
-__device__ __forceinline__ int symv_c_lo(int b) { return (b * SY_H) / RB_CHUNK; }
+__host__ __device__ __forceinline__ int symv_c_lo(int b) { return (b * SY_H) / SY_W; }
+// padded row stride of the partial buffers (float4 loads in k_symv_fin)
+__host__ __device__ __forceinline__ int symv_stride(int n) { return (n + 127) / 128 * 128; }
 
-// Row and column contributions of 4 consecutive columns j0 .. j0 + 3 of one
-// box row (row i): rows use p_j (zero left of the band), columns use p_i.
-// With MASK, only entries j >= i enter the row sum and j > i the columns.
-template <bool MASK>
-__device__ __forceinline__ void symv_quad(const float4 av, const float* pj, float pi, int i, int j0, float& racc,
-                                          float* colacc) {
-  const float a4[4] = {av.x, av.y, av.z, av.w};
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    if (MASK) {
-      const int j = j0 + e;
-      racc = fmaf(j >= i ? a4[e] : 0.f, pj[e], racc);
-      colacc[e] = fmaf(j > i ? a4[e] : 0.f, pi, colacc[e]);
-    } else {
-      racc = fmaf(a4[e], pj[e], racc);
-      colacc[e] = fmaf(a4[e], pi, colacc[e]);
-    }
-  }
-}
-
-// Sums of 8 per-lane values over the warp (reduce-scatter by halving):
-// afterwards lanes with (lane & 3) == 0 hold in v[0] the warp's sum of value
-// (lane >> 2) & 7. Nine shuffles instead of 8 x 5.
-__device__ __forceinline__ float warp_sum8_scatter(float (&v)[8], int lane) {
-#pragma unroll
-  for (int m = 4, sft = 16; m >= 1; m >>= 1, sft >>= 1) {
-    const bool up = (lane & sft) != 0;
-#pragma unroll
-    for (int i = 0; i < m; ++i) {
-      const float send = up ? v[i] : v[i + m];
-      const float keep = up ? v[i + m] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
-    }
-  }
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-  return v[0];
+// Boxes of item (b, c) that reach column 256 b and start before column n,
+// and its stages (row groups of 32 that start before row n).
+struct SymvItem {
+  int b, c, bx_lo, bx_hi, groups;
+};
+__host__ __device__ __forceinline__ SymvItem symv_item(int item, int n, int nc) {
+  SymvItem it;
+  it.b = item / nc;
+  it.c = item % nc;
+  const int lo = (it.b * SY_H - it.c * SY_W) / RB_BOXW;
+  it.bx_lo = lo > 0 ? lo : 0;
+  const int hi = (n - it.c * SY_W + RB_BOXW - 1) / RB_BOXW;
+  it.bx_hi = hi < SY_BX ? hi : SY_BX;
+  const int g = (n - it.b * SY_H + SY_SROWS - 1) / SY_SROWS;
+  it.groups = g < SY_GROUPS ? g : SY_GROUPS;
+  return it;
 }
 
 __global__ void __launch_bounds__(RB_THREADS, 1) k_symv_tma(const __grid_constant__ CUtensorMap tmap, SymvArgs a) {
@@ -444,41 +434,46 @@ __global__ void __launch_bounds__(RB_THREADS, 1) k_symv_tma(const __grid_constan
   uint64_t* empty = full + RB_STAGES;
   // row sums of a stage: one value per warp and row, summed by the last warp
   // to arrive (a counter per slot; no warp waits for another)
-  __shared__ float red[RB_STAGES][RB_CONSUMER_WARPS][RB_ROWS];
+  __shared__ float red[RB_STAGES][RB_CONSUMER_WARPS][SY_SROWS];
   __shared__ unsigned int red_cnt[RB_STAGES];
+  // what a slot holds: item * 8 + stage of the item, or -1 (no more items)
+  __shared__ int s_code[RB_STAGES];
   __shared__ int s_abort;
   __shared__ int s_issued;
   __shared__ int s_consumed[RB_CONSUMER_WARPS];
 
   DevState* st = a.st;
   if (st && a.skip_if_done && st->done) return;
-  const int n = a.n, nc = a.nchunks;
+  const int n = a.n, nc = a.nchunks, ns = a.ns, nitems = a.nitems;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < RB_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], RB_CONSUMER_WARPS);
+      red_cnt[s] = 0u;
     }
     fence_mbarrier_init();
     s_abort = 0;
     s_issued = 0;
-    for (int s = 0; s < RB_STAGES; ++s) red_cnt[s] = 0u;
   }
   __syncthreads();
 
   if (warp == RB_CONSUMER_WARPS) {
-    // ---------------- producer: one elected lane issues the TMA boxes -------
+    // ---------------- producer: one elected lane takes items, issues boxes --
     if (lane == 0) {
       prefetch_tensormap(&tmap);
       const uint64_t pol = l2_policy_evict_first();
       int it = 0;
       bool stop = false;
-      for (int t = a.sched_off[blockIdx.x]; t < a.sched_off[blockIdx.x + 1] && !stop; ++t) {
-        const int b = a.sched_items[t] / nc, c = a.sched_items[t] % nc;
-        const int bx_lo = max(0, (b * SY_H - c * RB_CHUNK) / RB_BOXW);
-        const int bx_hi = min(RB_BOXES, (n - c * RB_CHUNK + RB_BOXW - 1) / RB_BOXW);
-        for (int g = 0; g < SY_GROUPS; ++g, ++it) {
-          if (b * SY_H + g * RB_ROWS >= n) break;  // row groups past n (last band)
+      int t = int(atomicAdd(a.sched_ctr, 1u));
+      while (t < nitems && !stop) {
+        const int item = a.sched_items[t];
+        const SymvItem w = symv_item(item, n, nc);
+        int t_next = nitems;
+        for (int g = 0; g < w.groups; ++g, ++it) {
+          // the next ticket is taken as the item's last stage is issued: its
+          // latency overlaps the wait for a free slot
+          if (g == w.groups - 1) t_next = int(atomicAdd(a.sched_ctr, 1u));
           const int s = it % RB_STAGES;
           if (it >= RB_STAGES && !mbar_wait_bounded(&empty[s], ((it / RB_STAGES) - 1) & 1)) {
             s_abort = 1;
@@ -489,104 +484,138 @@ __global__ void __launch_bounds__(RB_THREADS, 1) k_symv_tma(const __grid_constan
             stop = true;
             break;
           }
-          mbar_arrive_expect_tx(&full[s], uint32_t(bx_hi - bx_lo) * RB_ROWS * RB_BOXW * 4);
-          for (int bx = bx_lo; bx < bx_hi; ++bx)
-            tma_load_2d_hint(tiles + size_t(s) * RB_STAGE_FLOATS + bx * RB_ROWS * RB_BOXW, &tmap, &full[s],
-                             c * RB_CHUNK + bx * RB_BOXW, b * SY_H + g * RB_ROWS, pol);
+          const int row0 = w.b * SY_H + g * SY_SROWS;
+          const int nrg = min(SY_RG, (n - row0 + RB_ROWS - 1) / RB_ROWS);  // row boxes before row n
+          s_code[s] = item * SY_GROUPS + g;
+          mbar_arrive_expect_tx(&full[s], uint32_t(nrg * (w.bx_hi - w.bx_lo)) * RB_ROWS * RB_BOXW * 4);
+          for (int rg = 0; rg < nrg; ++rg)
+            for (int bx = w.bx_lo; bx < w.bx_hi; ++bx)
+              tma_load_2d_hint(tiles + size_t(s) * RB_STAGE_FLOATS + (rg * SY_BX + bx) * RB_ROWS * RB_BOXW, &tmap,
+                               &full[s], w.c * SY_W + bx * RB_BOXW, row0 + rg * RB_ROWS, pol);
+        }
+        t = t_next;
+      }
+      if (!stop) {
+        // no more items: a slot whose code says so, completed by a plain arrival
+        const int s = it % RB_STAGES;
+        if (it < RB_STAGES || mbar_wait_bounded(&empty[s], ((it / RB_STAGES) - 1) & 1)) {
+          s_code[s] = -1;
+          mbar_arrive(&full[s]);
+        } else {
+          s_abort = 1;
         }
       }
       s_issued = it;
     }
   } else {
-    // ---------------- consumers: warp w owns box w of every stage -----------
+    // ---------------- consumers: warp w owns columns 64 w .. 64 w + 63 ------
+    const int bxw = warp / (RB_BOXW / SY_WCOLS);                  // the warp's column box
+    const int ccol = SY_WCOLS * (warp % (RB_BOXW / SY_WCOLS)) + 2 * lane;  // its first column in the box
     int it = 0;
-    bool stop = false;
-    for (int t = a.sched_off[blockIdx.x]; t < a.sched_off[blockIdx.x + 1] && !stop; ++t) {
-      const int b = a.sched_items[t] / nc, c = a.sched_items[t] % nc;
-      const int bx_lo = max(0, (b * SY_H - c * RB_CHUNK) / RB_BOXW);
-      const int bx_hi = min(RB_BOXES, (n - c * RB_CHUNK + RB_BOXW - 1) / RB_BOXW);
-      const bool active = warp >= bx_lo && warp < bx_hi;
-      const int row_lo = b * SY_H;
-      const int jbase = c * RB_CHUNK + warp * RB_BOXW + 4 * lane;  // columns jbase + 128 h + e
-      float pj[8];
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int j = jbase + 128 * h + e;
-          pj[4 * h + e] = (j >= row_lo && j < n) ? __ldg(a.p + j) : 0.f;
-        }
-      float colacc[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) colacc[e] = 0.f;
-      for (int g = 0; g < SY_GROUPS; ++g, ++it) {
-        const int row0 = row_lo + g * RB_ROWS;
-        if (row0 >= n) break;  // row groups past n (last band): not loaded
-        const int s = it % RB_STAGES;
-        float prow[RB_ROWS];
-#pragma unroll
-        for (int r = 0; r < RB_ROWS; ++r) prow[r] = row0 + r < n ? __ldg(a.p + row0 + r) : 0.f;
-        if (!mbar_wait_bounded(&full[s], (it / RB_STAGES) & 1)) {
-          s_abort = 1;
-          stop = true;
-          break;
-        }
-        float racc[RB_ROWS];
-#pragma unroll
-        for (int r = 0; r < RB_ROWS; ++r) racc[r] = 0.f;
-        if (active) {
-          const float* box = tiles + size_t(s) * RB_STAGE_FLOATS + warp * RB_ROWS * RB_BOXW;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int j0 = jbase + 128 * h;
-            if (j0 > row0 + RB_ROWS - 1) {       // right of every row of the stage
-#pragma unroll
-              for (int r = 0; r < RB_ROWS; ++r)
-                symv_quad<false>(reinterpret_cast<const float4*>(box + r * RB_BOXW)[lane + 32 * h], pj + 4 * h,
-                                 prow[r], row0 + r, j0, racc[r], colacc + 4 * h);
-            } else if (j0 + 3 >= row0) {         // meets the stage's rows: masks
-#pragma unroll
-              for (int r = 0; r < RB_ROWS; ++r)
-                symv_quad<true>(reinterpret_cast<const float4*>(box + r * RB_BOXW)[lane + 32 * h], pj + 4 * h,
-                                prow[r], row0 + r, j0, racc[r], colacc + 4 * h);
-            }                                    // else: left of every row, nothing
-          }
-        }
-        // row sums of this warp's 256 columns for the stage's 8 rows
-        const float v = warp_sum8_scatter(racc, lane);
-        if ((lane & 3) == 0) red[s][warp][lane >> 2] = v;
-        __syncwarp();
-        unsigned int last = 0u;
-        if (lane == 0) {
-          __threadfence_block();
-          last = atomicAdd(&red_cnt[s], 1u) == RB_CONSUMER_WARPS - 1 ? 1u : 0u;
-          if (last) {
-            __threadfence_block();
-            red_cnt[s] = 0u;
-          }
-        }
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (last && lane < RB_ROWS && row0 + lane < n) {
-          __threadfence_block();
-          float t = 0.f;
-#pragma unroll
-          for (int w = 0; w < RB_CONSUMER_WARPS; ++w) t += *reinterpret_cast<volatile float*>(&red[s][w][lane]);
-          a.rowpart[int64_t(c) * n + row0 + lane] = t;
-        }
-        // the slot (tile and row sums) is released only now: the producer
-        // refills it, and the warps reuse its row-sum buffer, after every
-        // warp has finished this stage
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
+    float pj0 = 0.f, pj1 = 0.f;            // p at the lane's two columns
+    float cs0[4] = {0.f, 0.f, 0.f, 0.f}, cs1[4] = {0.f, 0.f, 0.f, 0.f};  // column sums, rows r % 4 apart
+    float p_pref = 0.f;                    // p at row row_pref + lane, loaded one stage ahead
+    int row_pref = -1;
+    while (true) {
+      const int s = it % RB_STAGES;
+      if (!mbar_wait_bounded(&full[s], (it / RB_STAGES) & 1)) {
+        s_abort = 1;
+        break;
       }
-      if (stop) break;
+      const int code = *(volatile int*)&s_code[s];
+      if (code < 0) break;
+      const SymvItem w = symv_item(code / SY_GROUPS, n, nc);
+      const int g = code % SY_GROUPS;
+      const int row0 = w.b * SY_H + g * SY_SROWS;
+      const int band0 = w.b * SY_H;
+      const int j0 = w.c * SY_W + bxw * RB_BOXW + ccol;  // the lane's columns j0, j0 + 1
+      const int wj0 = j0 - 2 * lane;                     // the warp's first column
+      const bool active = bxw >= w.bx_lo && bxw < w.bx_hi;
+      if (g == 0) {
+        pj0 = (j0 >= band0 && j0 < n) ? __ldg(a.p + j0) : 0.f;
+        pj1 = (j0 + 1 >= band0 && j0 + 1 < n) ? __ldg(a.p + j0 + 1) : 0.f;
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
+        for (int u = 0; u < 4; ++u) cs0[u] = cs1[u] = 0.f;
+      }
+      float my_p;
+      if (row_pref == row0) {
+        my_p = p_pref;
+      } else {
+        my_p = row0 + lane < n ? __ldg(a.p + row0 + lane) : 0.f;
+      }
+      if (g + 1 < w.groups) {
+        row_pref = row0 + SY_SROWS;
+        p_pref = row_pref + lane < n ? __ldg(a.p + row_pref + lane) : 0.f;
+      } else {
+        row_pref = -1;
+      }
+      float racc[SY_SROWS];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int j = jbase + 128 * h + e;
-          if (j >= row_lo && j < n) a.colpart[int64_t(b) * n + j] = colacc[4 * h + e];
+      for (int r = 0; r < SY_SROWS; ++r) racc[r] = 0.f;
+      if (active) {
+        const float* base = tiles + size_t(s) * RB_STAGE_FLOATS + bxw * RB_ROWS * RB_BOXW + ccol;
+        // warp-uniform cases (the shuffles below need the whole warp)
+        if (wj0 >= row0 + SY_SROWS && row0 + SY_SROWS <= n) {
+          // right of every row of the stage, every row before n: no masks
+#pragma unroll
+          for (int r = 0; r < SY_SROWS; ++r) {
+            const float2 av =
+                *reinterpret_cast<const float2*>(base + (r / RB_ROWS) * SY_BX * RB_ROWS * RB_BOXW + (r % RB_ROWS) * RB_BOXW);
+            const float pi = __shfl_sync(0xffffffffu, my_p, r);
+            racc[r] = fmaf(av.x, pj0, av.y * pj1);
+            cs0[r & 3] = fmaf(av.x, pi, cs0[r & 3]);
+            cs1[r & 3] = fmaf(av.y, pi, cs1[r & 3]);
+          }
+        } else if (wj0 + SY_WCOLS - 1 >= row0) {
+          // meets the stage's rows, or rows at or past n: masks
+#pragma unroll
+          for (int r = 0; r < SY_SROWS; ++r) {
+            const int i = row0 + r;
+            const float2 av =
+                *reinterpret_cast<const float2*>(base + (r / RB_ROWS) * SY_BX * RB_ROWS * RB_BOXW + (r % RB_ROWS) * RB_BOXW);
+            const float pi = __shfl_sync(0xffffffffu, my_p, r);
+            const bool row_in = i < n;
+            racc[r] = row_in ? fmaf(j0 >= i ? av.x : 0.f, pj0, (j0 + 1 >= i ? av.y : 0.f) * pj1) : 0.f;
+            const float cx = (row_in && j0 > i) ? av.x : 0.f;
+            const float cy = (row_in && j0 + 1 > i) ? av.y : 0.f;
+            cs0[r & 3] = fmaf(cx, pi, cs0[r & 3]);
+            cs1[r & 3] = fmaf(cy, pi, cs1[r & 3]);
+          }
+        }  // else: left of every row of the stage, nothing
+      }
+      // row sums of the warp's 64 columns: lane l gets row row0 + l
+      warp_transpose_sum(racc, lane);
+      red[s][warp][lane] = racc[0];
+      __syncwarp();
+      unsigned int last = 0u;
+      if (lane == 0) {
+        __threadfence_block();
+        last = atomicAdd(&red_cnt[s], 1u) == RB_CONSUMER_WARPS - 1 ? 1u : 0u;
+        if (last) {
+          __threadfence_block();
+          red_cnt[s] = 0u;
         }
+      }
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (last && row0 + lane < n) {
+        __threadfence_block();
+        float tsum = 0.f;
+#pragma unroll
+        for (int q = 0; q < RB_CONSUMER_WARPS; ++q) tsum += *reinterpret_cast<volatile float*>(&red[s][q][lane]);
+        a.rowpart[int64_t(w.c) * ns + row0 + lane] = tsum;
+      }
+      // the item's last stage: the column sums over its rows
+      if (g == w.groups - 1 && active) {
+        if (j0 >= band0 && j0 < n) a.colpart[int64_t(w.b) * ns + j0] = (cs0[0] + cs0[1]) + (cs0[2] + cs0[3]);
+        if (j0 + 1 >= band0 && j0 + 1 < n)
+          a.colpart[int64_t(w.b) * ns + j0 + 1] = (cs1[0] + cs1[1]) + (cs1[2] + cs1[3]);
+      }
+      // the slot (tile and row sums) is released only now: the producer
+      // refills it, and the warps reuse its row-sum buffer, after every warp
+      // has finished this stage
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+      ++it;
     }
     if (lane == 0) s_consumed[warp] = it;
   }
@@ -600,105 +629,112 @@ __global__ void __launch_bounds__(RB_THREADS, 1) k_symv_tma(const __grid_constan
   }
 }
 
-// q_i = sum_{c >= c0(b_i)} rowpart[c n + i] + sum_{b <= b_i} colpart[b n + i]
-// and p^T q. A CTA takes 32 consecutive rows (lane = row) and its 8 warps
-// split the partial list of those rows (warp w: entries w, w + 8, ...), so
-// every load is one coalesced 128-byte line and many are in flight; the
-// warps' sums are combined in shared memory in a fixed order (the result
-// does not depend on scheduling). Float32 sums over at most
-// n / 64 + n / 2048 + 1 terms, four interleaved accumulators per thread.
-constexpr int SYF_ROWS = 32;  // rows per CTA of the finishing kernel (256 threads)
+// q_i = sum_{c >= c0(b_i)} rowpart[c ns + i] + sum_{b <= b_i} colpart[b ns + i]
+// and p^T q. A CTA takes 128 consecutive rows (a lane four of them, float4
+// loads) and its 8 warps split the partial list of those rows (warp w:
+// entries w, w + 8, ...), four loads in flight per warp; the warps' sums are
+// combined in shared memory in a fixed order (the result does not depend on
+// scheduling). Float32 sums over at most n / 256 + n / 512 + 1 terms. The
+// first thread also rewinds the item counter of k_symv_tma, which has
+// finished (stream order), for the next launch.
+constexpr int SYF_ROWS = 128;  // rows per CTA of the finishing kernel (256 threads)
 static_assert(SY_H % SYF_ROWS == 0, "the rows of a finishing CTA lie in one band");
 __global__ void __launch_bounds__(256) k_symv_fin(SymvArgs a) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.sched_ctr = 0u;
   DevState* st = a.st;
   if (st && a.skip_if_done && st->done) return;
-  const int n = a.n, nc = a.nchunks;
+  const int n = a.n, nc = a.nchunks, ns = a.ns;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int row0 = blockIdx.x * SYF_ROWS;
-  const int i = row0 + lane;
-  // the CTA's rows share their band unless a band boundary falls inside the
-  // 32 rows (SY_H is a multiple of 32): one partial list for all of them
   const int b = row0 / SY_H;
   const int c0 = symv_c_lo(b);
   const int nr = nc - c0, total = nr + b + 1;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  if (i < n) {
-#pragma unroll 4
-    for (int t = warp; t < total; t += 8) {
-      const float* src = t < nr ? a.rowpart + int64_t(c0 + t) * n : a.colpart + int64_t(t - nr) * n;
-      acc[(t >> 3) & 3] += src[i];
-    }
+  // rows row0 + 4 lane .. + 3; the buffers' stride is a multiple of 128 and
+  // rows up to the stride are allocated (those past n are not used)
+  const int64_t off = row0 + 4 * lane;
+  auto src = [&](int t) -> float4 {
+    const float* p = t < nr ? a.rowpart + int64_t(c0 + t) * ns : a.colpart + int64_t(t - nr) * ns;
+    return __ldcg(reinterpret_cast<const float4*>(p + off));
+  };
+  float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
+  int t = warp;
+  for (; t + 24 < total; t += 32) {
+    const float4 v0 = src(t), v1 = src(t + 8), v2 = src(t + 16), v3 = src(t + 24);
+    s0.x += v0.x; s0.y += v0.y; s0.z += v0.z; s0.w += v0.w;
+    s1.x += v1.x; s1.y += v1.y; s1.z += v1.z; s1.w += v1.w;
+    s2.x += v2.x; s2.y += v2.y; s2.z += v2.z; s2.w += v2.w;
+    s3.x += v3.x; s3.y += v3.y; s3.z += v3.z; s3.w += v3.w;
   }
-  __shared__ float red[8][SYF_ROWS];
-  red[warp][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  for (; t < total; t += 8) {
+    const float4 v = src(t);
+    s0.x += v.x; s0.y += v.y; s0.z += v.z; s0.w += v.w;
+  }
+  __shared__ float4 red[8][32];
+  red[warp][lane] = make_float4((s0.x + s1.x) + (s2.x + s3.x), (s0.y + s1.y) + (s2.y + s3.y),
+                                (s0.z + s1.z) + (s2.z + s3.z), (s0.w + s1.w) + (s2.w + s3.w));
   __syncthreads();
   double my = 0.0;
-  if (warp == 0 && i < n) {
+  if (threadIdx.x < SYF_ROWS) {
+    const int l = threadIdx.x >> 2, e = threadIdx.x & 3;  // row row0 + 4 l + e = row0 + threadIdx.x
+    const int i = row0 + threadIdx.x;
     float q = 0.f;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) q += red[w][lane];
-    a.q[i] = q;
-    my = double(a.p[i]) * double(q);
+    for (int w = 0; w < 8; ++w) q += reinterpret_cast<const float*>(&red[w][l])[e];
+    if (i < n) {
+      a.q[i] = q;
+      my = double(a.p[i]) * double(q);
+    }
   }
-  __shared__ double s_part;
-  if (warp == 0) {
+  __shared__ double s_part[4];
+  if (warp < 4) {
     const double v = warp_sum(my);
-    if (lane == 0) s_part = v;
+    if (lane == 0) s_part[warp] = v;
   }
   __syncthreads();
-  if (threadIdx.x == 0) a.partials[blockIdx.x] = s_part;
+  if (threadIdx.x == 0) a.partials[blockIdx.x] = (s_part[0] + s_part[1]) + (s_part[2] + s_part[3]);
   if (!arrive_last(a.ticket)) return;
   if (threadIdx.x < 32) {
-    double t = 0.0;
-    for (int j = threadIdx.x; j < int(gridDim.x); j += 32) t += __ldcg(a.partials + j);
-    t = warp_sum(t);
-    if (threadIdx.x == 0 && a.result) *a.result = t;
+    double tt = 0.0;
+    for (int j = threadIdx.x; j < int(gridDim.x); j += 32) tt += __ldcg(a.partials + j);
+    tt = warp_sum(tt);
+    if (threadIdx.x == 0 && a.result) *a.result = tt;
   }
 }
 
-size_t symv_rowpart_floats(int n) { return size_t((n + RB_CHUNK - 1) / RB_CHUNK) * n; }
-size_t symv_colpart_floats(int n) { return size_t((n + SY_H - 1) / SY_H) * n; }
+size_t symv_rowpart_floats(int n) { return size_t((n + SY_W - 1) / SY_W) * symv_stride(n); }
+size_t symv_colpart_floats(int n) { return size_t((n + SY_H - 1) / SY_H) * symv_stride(n); }
 int symv_fin_grid(int n, int) { return (n + SYF_ROWS - 1) / SYF_ROWS; }
 
 cudaError_t symv_configure() {
   return cudaFuncSetAttribute(k_symv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(RB_SMEM));
 }
 
-// Work items (b, c) of the symmetric matvec and their assignment to `ctas`
-// CTAs: longest processing time first (the cost of an item is the boxes it
-// loads times its row groups), each item to the least loaded CTA.
-// off[g] .. off[g + 1] index the items of CTA g in `items` (b * nchunks + c).
-void symv_schedule(int n, int ctas, std::vector<int>& off, std::vector<int>& items) {
-  const int nb = (n + SY_H - 1) / SY_H, nc = (n + RB_CHUNK - 1) / RB_CHUNK;
-  std::vector<std::pair<long long, int>> all;  // (cost, item)
+// Work items (b, c) of the symmetric matvec, largest first (the size of an
+// item is the boxes it loads; ties in item order), as b * nchunks + c. The
+// CTAs take them in this order from the counter, so the last items to start
+// are the smallest.
+void symv_schedule(int n, std::vector<int>& items) {
+  const int nb = (n + SY_H - 1) / SY_H, nc = (n + SY_W - 1) / SY_W;
+  std::vector<std::pair<long long, int>> all;  // (boxes, item)
   for (int b = 0; b < nb; ++b)
-    for (int c = (b * SY_H) / RB_CHUNK; c < nc; ++c) {
-      const int bx_lo = std::max(0, (b * SY_H - c * RB_CHUNK) / RB_BOXW);
-      const int bx_hi = std::min(RB_BOXES, (n - c * RB_CHUNK + RB_BOXW - 1) / RB_BOXW);
-      const int groups = (std::min(SY_H, n - b * SY_H) + RB_ROWS - 1) / RB_ROWS;
-      all.push_back({(long long)(bx_hi - bx_lo) * groups, b * nc + c});
+    for (int c = symv_c_lo(b); c < nc; ++c) {
+      const SymvItem w = symv_item(b * nc + c, n, nc);
+      long long boxes = 0;
+      for (int g = 0; g < w.groups; ++g) {
+        const int row0 = b * SY_H + g * SY_SROWS;
+        boxes += (long long)std::min(SY_RG, (n - row0 + RB_ROWS - 1) / RB_ROWS) * (w.bx_hi - w.bx_lo);
+      }
+      all.push_back({boxes, b * nc + c});
     }
   std::stable_sort(all.begin(), all.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
-  std::vector<long long> load(ctas, 0);
-  std::vector<std::vector<int>> per(ctas);
-  for (const auto& it : all) {
-    int g = 0;
-    for (int h = 1; h < ctas; ++h)
-      if (load[h] < load[g]) g = h;
-    load[g] += it.first;
-    per[g].push_back(it.second);
-  }
-  off.assign(1, 0);
   items.clear();
-  for (int g = 0; g < ctas; ++g) {
-    items.insert(items.end(), per[g].begin(), per[g].end());
-    off.push_back(int(items.size()));
-  }
+  for (const auto& it : all) items.push_back(it.second);
 }
 
 cudaError_t launch_symv(const CUtensorMap* tmap, SymvArgs a, int num_sms, cudaStream_t s) {
   a.nbands = (a.n + SY_H - 1) / SY_H;
-  a.nchunks = (a.n + RB_CHUNK - 1) / RB_CHUNK;
+  a.nchunks = (a.n + SY_W - 1) / SY_W;
+  a.ns = symv_stride(a.n);
   k_symv_tma<<<num_sms, RB_THREADS, RB_SMEM, s>>>(*tmap, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -309,21 +309,6 @@ __device__ bool grid_barrier(DevState* st) {
   return s_ok != 0;
 }
 
-// Column sums of 32 per-lane values across a warp (reduce-scatter by
-// halving): afterwards lane l holds in v[0] the warp's sum of column l.
-__device__ __forceinline__ void warp_transpose_sum(float (&v)[32], int lane) {
-#pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
-    const bool up = (lane & s) != 0;
-#pragma unroll
-    for (int i = 0; i < s; ++i) {
-      const float send = up ? v[i] : v[i + s];
-      const float keep = up ? v[i + s] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
-    }
-  }
-}
-
 constexpr int IT_THREADS = 256;
 constexpr int IT_WARPS = IT_THREADS / 32;
 constexpr int IT_ROWS = IT_THREADS / 2;  // rows per CTA pass: the two halves of a CTA split the columns

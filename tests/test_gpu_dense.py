@@ -114,14 +114,17 @@ def test_matvec_full_size_sampled_rows(dcg):
     assert abs(pAp - p.astype(np.float64) @ qq) <= 1e-12 * (np.abs(p) @ np.abs(qq))
 
 
-@pytest.mark.parametrize("n", [1, 5, 63, 64, 65, 1000, 2047, 2049, 4100, 9000])
+@pytest.mark.parametrize("n", [1, 5, 63, 64, 65, 256, 257, 511, 513, 1000, 2047, 2049, 4100, 9000])
 def test_symmetric_matvec_matches_oracle(dcg, n):
     # dcg_set_operator_dense_sym: only the upper triangle is read. The strictly
     # lower triangle and the padding columns hold NaN, so any read of them
-    # would show in q. Row sums run in float32 over <= 8 products per thread
-    # and stage and a 32-lane tree; the transposed contributions in float32
-    # over the 64 rows of a band; everything then adds up in float64:
-    # error <= 100 eps32 sum_j |a_ij p_j|.
+    # would show in q (sizes around the 256-row bands and 512-column chunks of
+    # the work items). All sums are float32: a row's part of a stage over 2
+    # products per lane, a 32-lane tree and 8 warps; the transposed
+    # contributions over the <= 256 rows of a band in four interleaved chains;
+    # then <= n / 256 + n / 512 + 1 partials. The worst case is about
+    # 130 eps32 sum_j |a_ij p_j|; with random signs the errors grow like the
+    # square root of the terms, and the test takes 100 eps32.
     rng = np.random.default_rng(10 + n)
     lda = (n + 3) // 4 * 4 + 4
     A32 = rng.standard_normal((n, n)).astype(np.float32)

@@ -54,14 +54,21 @@ def _oracle_defcg(tol, k=8, ell=12):
 def test_newton_loop_matches_oracle(dcg, n, d):
     # Eight Newton steps on each side (no early stop, so that the step counts
     # cannot part on a Psi difference at rounding level): Psi along the way
-    # to 1e-4 relative (solves to tol 1e-6, float32 products K c and K a),
-    # def-CG iterations within 2 + 10 % of the oracle's on the recycled
-    # systems; the first system is plain CG (W empty), where the float32
+    # to 1e-4 relative (solves to tol 1e-6, float32 products K c and K a).
+    # Iterations: the first system is plain CG (W empty), where the float32
     # recursion loses more to the few large eigenvalues of the two-class
-    # kernel (measured: 16 vs 13, 26 vs 21): 2 + 30 %. The GPU's final f
-    # satisfies the mode's fixed-point
-    # equation f = K grad log p(y | f) (Rasmussen and Williams, Eq. 3.17) and
-    # matches the oracle's mode to 1e-4 relative.
+    # kernel (measured: 16-17 vs 13, 26 vs 21): 2 + 30 %. On the recycled
+    # systems the solves take 2 to 11 iterations and end near what the float32
+    # recursion can attain at tol 1e-6 (a certified check or a replacement adds
+    # one or two), so each is held to 3 + 10 % of the oracle's (measured: 7 vs
+    # 4 at the largest) and their total to 2 + 10 %. The GPU's final (f, a)
+    # satisfies the mode's fixed-point equation (Rasmussen and Williams,
+    # Eq. 3.17) in the form a = grad log p(y | f), f = K a, to 1e-4 relative,
+    # and f matches the oracle's mode to 1e-4 relative. (The form
+    # f = K grad log p(y | f) multiplies the float32 rounding of K a by
+    # |K H| ~ lambda_max(K) / 4, 550 to 1700 here: a float32 product K a at the
+    # oracle's own mode already leaves 2e-4 in it. In the a form the rounding
+    # enters through H <= 1/4: 1.4e-5 for the same product.)
     K64, Kp, y = _problem(n, d)
     tol = 1e-6
     steps = 8
@@ -71,16 +78,20 @@ def test_newton_loop_matches_oracle(dcg, n, d):
                                           torch.tensor(y.astype(np.float32), device="cuda"), dpsi_tol=-np.inf,
                                           max_newton=steps)
         f = f.cpu().numpy()
+        a = a.cpu().numpy()
     assert len(h) == len(h_o) == steps + 1
     print("def-CG iterations per Newton step, GPU", [i["iters"] for i in infos], "oracle", list(it_o))
     np.testing.assert_allclose(h, h_o, rtol=1e-4)
     for t, (info, io) in enumerate(zip(infos, it_o)):
         assert info["status"] == 0 and info["relres_true"] <= tol
-        assert abs(info["iters"] - io) <= 2 + (0.3 if t == 0 else 0.1) * io, (t, info["iters"], io)
-    fix = K64 @ L.grad_log_lik(y, f)
+        assert abs(info["iters"] - io) <= (2 + 0.3 * io if t == 0 else 3 + 0.1 * io), (t, info["iters"], io)
+    tot, tot_o = sum(i["iters"] for i in infos[1:]), sum(it_o[1:])
+    assert abs(tot - tot_o) <= 2 + 0.1 * tot_o, (tot, tot_o)
+    g = L.grad_log_lik(y, f)
     print("fixed-point residual %.2e, mode difference %.2e" % (
-        np.linalg.norm(f - fix) / np.linalg.norm(f), np.linalg.norm(f - f_o) / np.linalg.norm(f_o)))
-    assert np.linalg.norm(f - fix) <= 1e-4 * np.linalg.norm(f)
+        np.linalg.norm(a - g) / np.linalg.norm(a), np.linalg.norm(f - f_o) / np.linalg.norm(f_o)))
+    assert np.linalg.norm(a - g) <= 1e-4 * np.linalg.norm(a)
+    assert np.linalg.norm(f - K64 @ a) <= 100 * 6e-8 * np.linalg.norm(np.abs(K64) @ np.abs(a))
     assert np.linalg.norm(f - f_o) <= 1e-4 * np.linalg.norm(f_o)
 
 
