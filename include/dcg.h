@@ -71,6 +71,27 @@ typedef enum dcg_extraction {     /* how the next W is drawn from Z = [W, P] (Se
                                      Eq. 7)                                          */
 } dcg_extraction;
 
+typedef enum dcg_fg_form {        /* how the harmonic pencil's F, G are formed (Sec. 2.3) */
+  DCG_FG_EXPLICIT = 0,            /* Gram products over Z = [W, P] and AZ = [AW, AP]:
+                                     two tall passes over n x (k + ell) per update  */
+  DCG_FG_SPARSE = 1               /* Saad et al.'s sparse forms from scalars the solve
+                                     records per stored direction p_j: d_j, alpha_j,
+                                     |r_j|^2, |r_{j+1}|^2, (AW)^T r_j, (AW)^T r_{j+1},
+                                     with E and (AW)^T AW: F = diag(E, d_j),
+                                     G tridiagonal in the P block. Exact in exact
+                                     arithmetic (A-conjugacy, orthogonal residuals);
+                                     in float32 it neglects what those identities lose.
+                                     An update takes the Gram products instead when
+                                     a replacement (reading R13) fell inside the
+                                     window (it breaks the coupling of the two
+                                     directions around it) or the solve had no W
+                                     (plain CG: once a Ritz value converges the
+                                     float32 directions lose orthogonality and the
+                                     tridiagonal model holds ghost copies of it);
+                                     dcg_get_pencil_form tells which. Harmonic
+                                     extraction only.                               */
+} dcg_fg_form;
+
 typedef enum dcg_xformat {        /* element format of X for the matrix-free operator */
   DCG_X_FP32 = 0,                 /* X kept in float32 (the operator is K(X)): the
                                      iteration's tiles are split TF32 (x = hi + lo,
@@ -98,7 +119,8 @@ typedef struct dcg_config {
                            iteration (slower; for profilers that cannot see
                            kernels inside conditional graphs, and for debugging) */
   int32_t extraction;   /* dcg_extraction (0 = harmonic, the paper's choice)     */
-  int32_t reserved[5];  /* must be zero                                          */
+  int32_t fg_form;      /* dcg_fg_form (0 = explicit Gram products)              */
+  int32_t reserved[4];  /* must be zero                                          */
   double tol;           /* relative residual target |b - A x| <= tol |b|         */
 } dcg_config;
 
@@ -300,6 +322,13 @@ dcg_status dcg_get_ritz_values(dcg_ctx* ctx, double* theta, int32_t cap, int32_t
  *   F, G   host, capacity cap doubles each (cap >= m * m), or NULL to query m.
  *   m      host, may be NULL. */
 dcg_status dcg_get_pencil(dcg_ctx* ctx, double* F, double* G, int32_t cap, int32_t* m);
+
+/* How the last update formed its pencil (a dcg_fg_form, host): with
+ * cfg.fg_form = DCG_FG_SPARSE it is DCG_FG_EXPLICIT when a residual
+ * replacement (reading R13) fell inside the window of stored directions, when
+ * the solve had no W (see DCG_FG_SPARSE), and for an update that extracted
+ * nothing. Errors: INVALID_ARG (NULL), or the pending update's. */
+dcg_status dcg_get_pencil_form(dcg_ctx* ctx, int32_t* form);
 
 /* Prior knowledge for the next solve or a checkpoint restore (Fig. 1 caption):
  * W device, column-major n x k (0 <= k <= cfg.k), copied. */

@@ -21,6 +21,7 @@ STATUS_NAMES = {
 WINDOW = {"first": 0, "last": 1}
 SELECT = {"largest": 0, "smallest": 1}
 EXTRACTION = {"harmonic": 0, "ritz": 1}
+FG_FORM = {"explicit": 0, "sparse": 1}
 XFORMAT = {"fp32": 0, "bf16": 1, "tf32": 2}
 
 
@@ -38,7 +39,8 @@ class DcgConfig(ctypes.Structure):
         ("record_history", ctypes.c_int32),
         ("host_loop", ctypes.c_int32),
         ("extraction", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("fg_form", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
         ("tol", ctypes.c_double),
     ]
 
@@ -86,6 +88,7 @@ SIGNATURES = {
     "dcg_update_subspace_async": (_I32, [_P]),
     "dcg_get_ritz_values": (_I32, [_P, _PD, _I32, _PI32]),
     "dcg_get_pencil": (_I32, [_P, _PD, _PD, _I32, _PI32]),
+    "dcg_get_pencil_form": (_I32, [_P, _PI32]),
     "dcg_set_subspace": (_I32, [_P, _P, _I32]),
     "dcg_get_subspace": (_I32, [_P, _P, _PI32]),
     "dcg_get_history": (_I32, [_P, _PD, _I32, _PI32]),

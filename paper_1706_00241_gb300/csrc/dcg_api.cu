@@ -56,6 +56,7 @@ struct dcg_ctx {
   float* sym_colpart = nullptr;
   int* sym_sched = nullptr;        // symmetric matvec: the item counter, then the items largest first
   int sym_nitems = 0;
+  bool fg_sparse_used = false;     // the last extraction formed F, G from the recorded scalars
 
   // operator
   int op = OP_NONE;
@@ -205,7 +206,7 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   if (!cfg || !out) return fail(nullptr, DCG_ERR_INVALID_ARG, "cfg and out must not be NULL");
   *out = nullptr;
   const dcg_config& g = *cfg;
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < 4; ++i)
     if (g.reserved[i]) return fail(nullptr, DCG_ERR_INVALID_ARG, "reserved fields must be zero");
   if (g.host_loop != 0 && g.host_loop != 1) return fail(nullptr, DCG_ERR_INVALID_ARG, "host_loop must be 0 or 1");
   if (g.n < 1 || g.n > (int64_t(1) << 30)) return fail(nullptr, DCG_ERR_INVALID_ARG, "n out of range");
@@ -226,6 +227,10 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
     return fail(nullptr, DCG_ERR_INVALID_ARG, "bad select");
   if (g.extraction != DCG_EXTRACT_HARMONIC && g.extraction != DCG_EXTRACT_RITZ)
     return fail(nullptr, DCG_ERR_INVALID_ARG, "bad extraction");
+  if (g.fg_form != DCG_FG_EXPLICIT && g.fg_form != DCG_FG_SPARSE)
+    return fail(nullptr, DCG_ERR_INVALID_ARG, "bad fg_form");
+  if (g.fg_form == DCG_FG_SPARSE && g.extraction != DCG_EXTRACT_HARMONIC)
+    return fail(nullptr, DCG_ERR_INVALID_ARG, "fg_form sparse needs the harmonic extraction");
   if (g.refine_every < 0) return fail(nullptr, DCG_ERR_INVALID_ARG, "refine_every must be >= 0");
   if (g.k > kMaxK || g.ell > kMaxEll)
     return fail(nullptr, DCG_ERR_UNSUPPORTED, "k <= 96 and ell <= 128 in this build");
@@ -297,6 +302,7 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   CKC(dalloc(c, &w.partials, size_t(std::max(c->grid_iter, c->grid_rows)) * kReduceSlots));
   const int hist_cap = g.record_history ? g.max_iter + 2 : 1;
   CKC(dalloc(c, &w.hist, size_t(hist_cap)));
+  if (ellmax > 0) CKC(dalloc(c, &w.fg, fg_doubles(ellmax, kmax)));
   CKC(dalloc(c, &c->st, 1));
   w.st = c->st;
   CKC(dalloc(c, &c->gramE_part, gram_partials_doubles(n, kk, c->num_sms)));
@@ -926,6 +932,29 @@ static dcg_status enqueue_update(dcg_ctx* c) {
   a.k_want = c->cfg.k;
   a.select = c->cfg.select;
   a.extraction = c->cfg.extraction;
+  a.fg_form = c->cfg.fg_form;
+  if (a.fg_form == DCG_FG_SPARSE) {
+    // The sparse forms need what their identities assume. A replacement
+    // inside the window (reading R13) breaks the coupling of the directions
+    // around it. A solve without W is plain CG, whose float32 directions lose
+    // orthogonality as soon as a Ritz value converges: the tridiagonal model
+    // then carries ghost copies of that value (measured: four kept values
+    // equal to 5 digits, the Gram products giving four distinct ones) and
+    // the next W would be singular. Either way this extraction takes the
+    // Gram products.
+    const DevState* hs = c->h_st;
+    const bool broken = kk == 0 || (c->cfg.window == DCG_WINDOW_FIRST ? (hs->repl_first > 0 && hs->repl_first < ns)
+                                                                      : (hs->repl_last > hs->iter - ns));
+    if (broken) a.fg_form = DCG_FG_EXPLICIT;
+    c->fg_sparse_used = !broken;
+  } else {
+    c->fg_sparse_used = false;
+  }
+  a.fg = c->w.fg;
+  a.ellmax = c->w.ellmax;
+  a.kmax = c->w.kmax;
+  a.E = c->w.E;
+  a.GW = c->w.GW;
   a.W = c->w.XW + c->w.n;
   a.AW = c->w.Y + c->w.n;
   a.P = c->w.P;
@@ -1025,6 +1054,13 @@ extern "C" dcg_status dcg_get_pencil(dcg_ctx* c, double* F, double* G, int32_t c
   CK(cudaMemcpyAsync(F, c->F, size_t(mp) * mp * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(G, c->G, size_t(mp) * mp * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  return DCG_OK;
+}
+
+extern "C" dcg_status dcg_get_pencil_form(dcg_ctx* c, int32_t* form) {
+  if (!c || !form) return DCG_ERR_INVALID_ARG;
+  { const dcg_status pend = finish_update(c); if (pend != DCG_OK) return pend; }
+  *form = (c->m_last > 0 && c->fg_sparse_used) ? DCG_FG_SPARSE : DCG_FG_EXPLICIT;
   return DCG_OK;
 }
 

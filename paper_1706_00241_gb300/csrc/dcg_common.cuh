@@ -67,6 +67,10 @@ struct DevState {
   // CTA gives up after spin_limit polls.
   int test_skip_arrival;
   long long spin_limit;
+  // residual replacements inside the loop (reading R13): the iteration index
+  // of the first and of the last in this solve, 0 if none. The sparse F, G
+  // of Sec. 2.3 hold only while no replacement falls inside the window.
+  int repl_first, repl_last;
 };
 
 // --------------------------------------------------------------------------

@@ -48,9 +48,32 @@ struct Ws {
   float* gamma_f;  // kmax
   double* partials;  // grid x kReduceSlots
   double* hist;    // hist_cap
+  double* fg;      // fg_doubles(ellmax, kmax): scalars of the stored directions (null if ellmax = 0)
   DevState* st;
   double tol;
 };
+
+// Scalars the fused iteration kernel records per stored direction p_j for the
+// sparse F, G of Sec. 2.3 (Saad et al.): slot s of the direction ring holds
+//   fg[FG_REC s + 0..4] = d_j, alpha_j, |r_j|^2, |r'_{j+1}|^2, j,
+// (AW)^T r_j at fg_ha(s) and (AW)^T r'_{j+1} at fg_hb(s), where r_j is the
+// residual the iteration starts from and r'_{j+1} = r_j - alpha_j A p_j the
+// one it forms (before the float32 re-deflation), so that
+// A p_j = (r_j - r'_{j+1}) / alpha_j. After the slots, fg_hprev holds
+// (AW)^T r of the residual the next iteration starts from.
+constexpr int FG_REC = 5;
+__host__ __device__ inline size_t fg_doubles(int ellmax, int kmax) {
+  return size_t(ellmax) * (FG_REC + 2 * size_t(kmax)) + size_t(kmax);
+}
+__host__ __device__ inline double* fg_ha(double* fg, int ellmax, int kmax, int s) {
+  return fg + size_t(ellmax) * FG_REC + size_t(s) * kmax;
+}
+__host__ __device__ inline double* fg_hb(double* fg, int ellmax, int kmax, int s) {
+  return fg + size_t(ellmax) * (FG_REC + kmax) + size_t(s) * kmax;
+}
+__host__ __device__ inline double* fg_hprev(double* fg, int ellmax, int kmax) {
+  return fg + size_t(ellmax) * (FG_REC + 2 * size_t(kmax));
+}
 
 // Conditional-node handles of the solve graph (see dcg_api.cu).
 struct Handles {
@@ -271,6 +294,11 @@ struct RitzArgs {
   int k_want;
   int select;       // dcg_select
   int extraction;   // dcg_extraction: which pencil F, G hold
+  int fg_form;      // dcg_fg_form: Gram products, or the recorded scalars (harmonic only)
+  double* fg;       // the scalars (Ws::fg), ring of ellmax slots, kmax-wide h records
+  int ellmax, kmax;
+  const double* E;  // k_act x k_act, W^T A W of the solve
+  const double* GW; // k_act x k_act, (AW)^T AW of the solve
   const float* W;   // n x k_act
   const float* AW;
   const float* P;   // n x nstored

@@ -203,6 +203,11 @@ __global__ void __launch_bounds__(256) k_check_update(Ws w, int pre_loop, int se
 
   __shared__ double red[1 + 2 * kMaxK], tmp[kMaxK], y[kMaxK];
   reduce_partials(w.partials, (setup || pre_loop) ? 1 + k : 1 + 2 * k, red);
+  // (AW)^T r of the residual the next direction starts from (sparse F, G)
+  if (w.fg) {
+    double* hprev = fg_hprev(w.fg, w.ellmax, w.kmax);
+    for (int c = threadIdx.x; c < k; c += blockDim.x) hprev[c] = red[1 + c];
+  }
   const double rho_new = red[0];
   __shared__ double s_beta;
   if (threadIdx.x == 0) {
@@ -243,6 +248,10 @@ __global__ void __launch_bounds__(256) k_check_update(Ws w, int pre_loop, int se
     } else {
       st->beta = s_beta;
       st->mode = 0;
+      if (!pre_loop) {
+        if (st->repl_first == 0) st->repl_first = st->iter;
+        st->repl_last = st->iter;
+      }
       if (!pre_loop && st->iter >= st->max_iter) {
         st->status = DCG_ERR_MAXITER;
         st->done = 1;
@@ -538,7 +547,7 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
   // warp w reduces values w * 13 .. w * 13 + 12 of each round of 104, all
   // their loads in flight at once
   __shared__ df sred[1 + 3 * kMaxK];
-  __shared__ double gam[kMaxK], av[kMaxK], bv[kMaxK];
+  __shared__ double gam[kMaxK], av[kMaxK], bv[kMaxK], uu[kMaxK];
   __shared__ int s_mode, s_done;
   __shared__ double s_beta;
   for (int v0 = warp * IT_RED_U; v0 < count; v0 += IT_WARPS * IT_RED_U) {
@@ -606,6 +615,7 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
       s0 = df_add(s0, s2);
       s1 = df_add(s1, s3);
       gam[c] = df_to_double(s0);
+      uu[c] = df_to_double(s1);
       const df hm2 = {-2.f * h[c].hi, -2.f * h[c].lo};  // exact scaling
       corr = df_add(corr, df_mul(s0, df_add(s1, hm2)));
     }
@@ -684,6 +694,28 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
     }
   }
   __syncthreads();
+  // scalars of the stored direction for the sparse F, G (Sec. 2.3); the
+  // residual the next iteration starts from is r~ = r' - AW gamma, with
+  // (AW)^T r~ = h - G_W gamma = h - u (a check that follows overwrites it)
+  if (blockIdx.x == 0 && slot >= 0 && w.fg) {
+    double* ha = fg_ha(w.fg, w.ellmax, w.kmax, slot);
+    double* hb = fg_hb(w.fg, w.ellmax, w.kmax, slot);
+    double* hprev = fg_hprev(w.fg, w.ellmax, w.kmax);
+    if (t == 0) {
+      double* rec = w.fg + slot * FG_REC;
+      rec[0] = d;
+      rec[1] = alpha_d;
+      rec[2] = rho_old;
+      rec[3] = df_to_double(sred[0]);
+      rec[4] = double(iter - 1);
+    }
+    for (int c = t; c < k; c += IT_THREADS) {
+      const double hc = df_to_double(h[c]);
+      ha[c] = hprev[c];
+      hb[c] = hc;
+      hprev[c] = hc - uu[c];
+    }
+  }
   if (s_mode != 0 || s_done) return;  // the check branch recomputes gamma, beta and mu
 
   // ---- C. the direction update on this CTA's rows ----

@@ -1026,6 +1026,55 @@ cudaError_t ritz_configure() {
   return cudaFuncSetAttribute(k_zu, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxM * 32 * 4);
 }
 
+// F and G of Eq. 7 from the scalars the solve recorded (the sparse forms of
+// Saad et al. that Sec. 2.3 refers to), instead of the Gram products over
+// Z = [W, P] and AZ = [AW, AP]. Columns: W (k_act), then the direction slots
+// in ring order. With A-conjugate directions ((AW)^T p_j = 0 and
+// p_i^T A p_j = 0) and mutually orthogonal residuals:
+//   F = diag(E, d_j);
+//   G_WW = (AW)^T AW, G_{W,j} = (AW)^T A p_j = ((AW)^T r_j - (AW)^T r'_{j+1}) / alpha_j,
+//   G_{jj} = (|r_j|^2 + |r'_{j+1}|^2) / alpha_j^2,
+//   G_{j,j+1} = -|r'_{j+1}|^2 / (alpha_j alpha_{j+1}) for consecutive stored
+//   directions, zero between others.
+// E and G_W are symmetrised as the Gram path's products are. One CTA.
+__global__ void __launch_bounds__(256) k_fg_sparse(RitzArgs a) {
+  const int k = a.k_act, ns = a.nstored, m = k + ns;
+  const int t = threadIdx.x;
+  const double* rec = a.fg;
+  for (int idx = t; idx < m * m; idx += blockDim.x) {
+    const int i = idx / m, j = idx - i * m;
+    double f = 0.0, g = 0.0;
+    if (i < k && j < k) {
+      f = 0.5 * (a.E[i * k + j] + a.E[j * k + i]);
+      g = 0.5 * (a.GW[i * k + j] + a.GW[j * k + i]);
+    }
+    a.F[idx] = f;
+    a.G[idx] = g;
+  }
+  __syncthreads();
+  for (int sl = t; sl < ns; sl += blockDim.x) {
+    const double d = rec[sl * FG_REC + 0], al = rec[sl * FG_REC + 1];
+    const double ra = rec[sl * FG_REC + 2], rb = rec[sl * FG_REC + 3], jj = rec[sl * FG_REC + 4];
+    const int c = k + sl;
+    a.F[int64_t(c) * m + c] = d;
+    a.G[int64_t(c) * m + c] = (ra + rb) / (al * al);
+    for (int s2 = 0; s2 < ns; ++s2) {
+      if (rec[s2 * FG_REC + 4] == jj + 1.0) {  // the next direction is stored too
+        const double v = -rb / (al * rec[s2 * FG_REC + 1]);
+        a.G[int64_t(c) * m + (k + s2)] = v;
+        a.G[int64_t(k + s2) * m + c] = v;
+      }
+    }
+  }
+  for (int idx = t; idx < k * ns; idx += blockDim.x) {
+    const int sl = idx / k, cw = idx - sl * k;
+    const double al = rec[sl * FG_REC + 1];
+    const double v = (fg_ha(a.fg, a.ellmax, a.kmax, sl)[cw] - fg_hb(a.fg, a.ellmax, a.kmax, sl)[cw]) / al;
+    a.G[int64_t(cw) * m + (k + sl)] = v;
+    a.G[int64_t(k + sl) * m + cw] = v;
+  }
+}
+
 cudaError_t launch_ritz(const RitzArgs& a, int num_sms, float* dstW, cudaStream_t s) {
   const int m = a.k_act + a.nstored;
   const int k_new = min(a.k_want, m);
@@ -1043,6 +1092,10 @@ cudaError_t launch_ritz(const RitzArgs& a, int num_sms, float* dstW, cudaStream_
     g.b1 = a.AW; g.b2 = a.Q;
     e = launch_gram(g, m, m, num_sms, a.G, nullptr, s);
     if (e != cudaSuccess) return e;
+  } else if (a.fg_form == DCG_FG_SPARSE) {
+    // harmonic projection (Eq. 7) from the recorded scalars
+    k_fg_sparse<<<1, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   } else {
     // harmonic projection (Eq. 7): F = Z^T (AZ), G = (AZ)^T (AZ)
     g.a1 = a.W; g.ka1 = a.k_act; g.a2 = a.P; g.ka2 = a.nstored;

@@ -57,7 +57,9 @@ class DefCG:
     Parameters follow ``dcg_config`` in include/dcg.h: ``window`` is "last" or
     "first" (which directions Algorithm 1 stores), ``select`` "largest" or "smallest"
     (Sec. 2.3), ``extraction`` "harmonic" (Eq. 7) or "ritz" (the orthogonal
-    projection of Sec. 2.3), ``refine_every`` the residual-replacement period (0 = only the
+    projection of Sec. 2.3), ``fg_form`` "explicit" (Gram products over Z and AZ)
+    or "sparse" (Saad et al.'s forms from the scalars the solve records, Sec. 2.3;
+    harmonic extraction only), ``refine_every`` the residual-replacement period (0 = only the
     final true-residual confirmation). ``reproject`` (default on) takes mu from
     (AW)^T (beta p + r), equal to (AW)^T r in exact arithmetic, which keeps the
     float32 directions A-conjugate to W.
@@ -65,7 +67,7 @@ class DefCG:
 
     def __init__(self, n: int, k: int, ell: int, tol: float, max_iter: int | None = None,
                  window: str = "last", select: str = "largest", refine_every: int = 0,
-                 extraction: str = "harmonic",
+                 extraction: str = "harmonic", fg_form: str = "explicit",
                  warm_start: bool = False, reproject: bool = True,
                  record_history: bool = False, host_loop: bool = False, stream=None):
         self.lib = _lib.load()
@@ -77,6 +79,7 @@ class DefCG:
         cfg.window = _lib.WINDOW[window]
         cfg.select = _lib.SELECT[select]
         cfg.extraction = _lib.EXTRACTION[extraction]
+        cfg.fg_form = _lib.FG_FORM[fg_form]
         cfg.refine_every = int(refine_every)
         cfg.max_iter = int(max_iter if max_iter is not None else 10 * self.n)
         cfg.warm_start = int(bool(warm_start))
@@ -198,6 +201,12 @@ class DefCG:
             self._check(self.lib.dcg_get_pencil(self._ctx, F.ctypes.data_as(pd), G.ctypes.data_as(pd), F.size,
                                                 ctypes.byref(m)), "dcg_get_pencil")
         return F.reshape(m.value, m.value), G.reshape(m.value, m.value)
+
+    def pencil_form(self) -> str:
+        """How the last update formed F and G: "explicit" or "sparse"."""
+        f = ctypes.c_int32()
+        self._check(self.lib.dcg_get_pencil_form(self._ctx, ctypes.byref(f)), "dcg_get_pencil_form")
+        return {v: k for k, v in _lib.FG_FORM.items()}[f.value]
 
     def get_subspace(self) -> torch.Tensor:
         """Current W as a (k_active, n) tensor (row j is column j of W)."""

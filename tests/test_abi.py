@@ -49,9 +49,10 @@ def test_binding_covers_header(lib_path):
 
 def test_config_struct_layout():
     from paper_1706_00241_gb300 import _lib
-    # int64 n, eleven int32 fields, int32 reserved[5], then a double: 8 + 64 + 8
+    # int64 n, twelve int32 fields, int32 reserved[4], then a double: 8 + 64 + 8
     assert ctypes.sizeof(_lib.DcgConfig) == 80
     assert _lib.DcgConfig.extraction.offset == 48
+    assert _lib.DcgConfig.fg_form.offset == 52
     assert _lib.DcgConfig.tol.offset == 72
     assert ctypes.sizeof(_lib.DcgSolveInfo) == 64
 
@@ -106,7 +107,14 @@ def test_create_rejects_unknown_extraction_without_gpu(lib_path):
     assert lib.dcg_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) == 1
     assert b"bad extraction" in lib.dcg_last_error(None)
     cfg.extraction = 0
-    cfg.reserved[4] = 1
+    cfg.fg_form = 2
+    assert lib.dcg_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) == 1
+    assert b"bad fg_form" in lib.dcg_last_error(None)
+    cfg.fg_form, cfg.extraction = 1, 1
+    assert lib.dcg_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) == 1
+    assert b"harmonic" in lib.dcg_last_error(None)
+    cfg.fg_form, cfg.extraction = 0, 0
+    cfg.reserved[3] = 1
     assert lib.dcg_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) == 1
     assert b"reserved" in lib.dcg_last_error(None)
     assert not ctx.value
