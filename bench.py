@@ -120,7 +120,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def run_sequence(P, torch, solver, Xd, bs_dev, A, T, deflate, ev_pool, side=None):
+def run_sequence(P, torch, solver, Xd, bs_dev, A, T, deflate, ev_pool, side=None, forms=None):
     """One sequence; returns per-system infos and device-timed (form, solve) ms.
 
     With a side stream and deflation, A_{t+1} is formed on the side stream
@@ -143,6 +143,8 @@ def run_sequence(P, torch, solver, Xd, bs_dev, A, T, deflate, ev_pool, side=None
         if overlap:
             side.wait_stream(stream)      # the solve is complete (A free); the update is not waited for
             solver.update_subspace(wait=False)
+            if forms is not None:         # waits for the update (untimed passes only)
+                forms.append(solver.pencil_form())
             se[t].record(stream)
             if t + 1 < T:
                 fs[t + 1].record(side)
@@ -210,9 +212,9 @@ def gpu_arm(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def make(deflate):
+    def make(deflate, fg_form="explicit"):
         return P.DefCG(n, CFG.k if deflate else 0, CFG.ell if deflate else 0, CFG.tol,
-                       max_iter=20000, window="last", select="largest", host_loop=args.host_loop)
+                       max_iter=20000, window="last", select="largest", host_loop=args.host_loop, fg_form=fg_form)
 
     # warm-up (builds the graph, first-touch of buffers)
     solver = make(True)
@@ -255,6 +257,20 @@ def gpu_arm(args):
     plain_ms = pe0.elapsed_time(pe1)   # whole sequence: forming A_t and solving
     plain_mv = sum(i["iters"] + i["matvecs_check"] for i in pinfos)
     plain.close()
+
+    # def-CG with the sparse F, G of Sec. 2.3 on the same sequence: one
+    # untimed pass that also records which form each update took, one timed
+    sparse = make(True, "sparse")
+    forms = []
+    run_sequence(P, torch, sparse, Xd, bs_dev, A, T, True, ev_pool, side, forms=forms)
+    sparse.set_subspace(torch.zeros((0, n), device="cuda"))
+    se0, se1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    se0.record()
+    sinfos, _, _ = run_sequence(P, torch, sparse, Xd, bs_dev, A, T, True, ev_pool, side)
+    se1.record()
+    torch.cuda.synchronize()
+    sparse_ms = se0.elapsed_time(se1)
+    sparse.close()
 
     # roofline of the dominant kernel: the symmetric TMA matvec q = A p (two
     # launches, k_symv_tma and k_symv_fin, timed together), CUDA events on the
@@ -353,6 +369,14 @@ def gpu_arm(args):
             "iters_per_system": [i["iters"] for i in pinfos],
         },
         "speedup_vs_plain_cg": (plain_ms / 1e3) / seq_s,
+        "defcg_sparse_fg": {
+            "what": "def-CG with F, G of Eq. 7 from the recorded scalars (Sec. 2.3, fg_form sparse); "
+                    "one timed sequence",
+            "s_per_sequence": sparse_ms / 1e3, "iters": sum(i["iters"] for i in sinfos),
+            "iters_per_system": [i["iters"] for i in sinfos],
+            "all_converged": all(i["status"] == 0 and i["relres_true"] <= CFG.tol for i in sinfos),
+            "updates_sparse": sum(f == "sparse" for f in forms), "updates": len(forms),
+        },
         "roofline": {
             "kernel": "k_symv_tma + k_symv_fin (q = A p from the upper triangle, fused p^T q)",
             "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

@@ -462,6 +462,12 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
   const int G = gridDim.x;
   const int stride = G * IT_ROWS;
   const int row0 = blockIdx.x * IT_ROWS + rt;
+  // (AW)^T r of the residual this iteration starts from, for the record of
+  // the stored direction (sparse F, G): loaded now, used after the barrier
+  const bool record = blockIdx.x == 0 && slot >= 0 && w.fg != nullptr;
+  __shared__ double s_hprev[kMaxK];
+  if (record)
+    for (int c = t; c < k; c += IT_THREADS) s_hprev[c] = fg_hprev(w.fg, w.ellmax, w.kmax)[c];
 
   // ---- A. x, r update, window store, rho' ----
   float acc = 0.f;
@@ -697,7 +703,7 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
   // scalars of the stored direction for the sparse F, G (Sec. 2.3); the
   // residual the next iteration starts from is r~ = r' - AW gamma, with
   // (AW)^T r~ = h - G_W gamma = h - u (a check that follows overwrites it)
-  if (blockIdx.x == 0 && slot >= 0 && w.fg) {
+  if (record) {
     double* ha = fg_ha(w.fg, w.ellmax, w.kmax, slot);
     double* hb = fg_hb(w.fg, w.ellmax, w.kmax, slot);
     double* hprev = fg_hprev(w.fg, w.ellmax, w.kmax);
@@ -711,7 +717,7 @@ __global__ void __launch_bounds__(IT_THREADS) k_iter_fused(Ws w, Handles hd, int
     }
     for (int c = t; c < k; c += IT_THREADS) {
       const double hc = df_to_double(h[c]);
-      ha[c] = hprev[c];
+      ha[c] = s_hprev[c];
       hb[c] = hc;
       hprev[c] = hc - uu[c];
     }
