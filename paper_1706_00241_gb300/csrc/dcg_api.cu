@@ -57,6 +57,12 @@ struct dcg_ctx {
   int* sym_sched = nullptr;        // symmetric matvec: the item counter, then the items largest first
   int sym_nitems = 0;
   bool fg_sparse_used = false;     // the last extraction formed F, G from the recorded scalars
+  // tensor-core block product (k_apply_tc): A's map (set with the stored
+  // operator) and the map of W (columns 1.. of XW, fixed at create)
+  CUtensorMap tmap_ab{};
+  CUtensorMap tmap_w{};
+  bool ab_tc = false;               // tmap_ab holds the current operator
+  bool w_tc = false;                // tmap_w is valid
 
   // operator
   int op = OP_NONE;
@@ -257,6 +263,7 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   CKC(cudaEventCreate(&c->ev2));
   CKC(rowop_configure());
   CKC(symv_configure());
+  CKC(apply_tc_configure());
   CKC(apply_block_configure());
   CKC(iter_configure());
   CKC(rbf_mv_configure());
@@ -324,8 +331,13 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
               2 * size_t(std::max(std::max(c->grid_rows, 2 * c->num_sms),
                                   std::max(rbf_exact_grid(n), symv_fin_grid(n, c->num_sms)))) + 2));
   {
-    const size_t bs = apply_block_scratch_floats(n, kMaxBlockCols, c->num_sms);
+    const size_t bs = std::max(apply_block_scratch_floats(n, kMaxBlockCols, c->num_sms),
+                               apply_tc_scratch_floats(n, kMaxBlockCols, c->num_sms));
     if (bs) CKC(dalloc(c, &c->block_scratch, bs));
+  }
+  if (kmax > 0 && apply_tc_supported(n, kmax)) {
+    EncodeTiledFn enc = get_encode();
+    c->w_tc = enc && make_apply_tc_tmaps(nullptr, &c->tmap_w, nullptr, 0, w.XW + n, n, kmax, enc);
   }
   CKC(dalloc(c, &c->mv_result, 2));
   CKC(dalloc(c, &c->mv_ticket, 1));
@@ -368,6 +380,8 @@ static dcg_status set_dense(dcg_ctx* c, const float* A, int64_t lda, bool sym) {
     c->lda = lda;
     c->op = OP_DENSE;
     c->dense_sym = sym;
+    c->ab_tc = apply_tc_supported(c->cfg.n, std::max(c->w.kmax, 1)) &&
+               make_apply_tc_tmaps(&c->tmap_ab, nullptr, A, lda, nullptr, c->cfg.n, 0, enc);
     destroy_graph(c);
   }
   return DCG_OK;
@@ -676,6 +690,18 @@ static cudaError_t op_block(dcg_ctx* c, const float* V, int ncols, float* Y, Dev
   a.c = ncols;
   a.st = st;
   a.skip_if_done = st ? 1 : 0;
+  // tensor cores (split TF32) where the operands allow TMA; the FP32-pipe
+  // kernel otherwise
+  if (c->ab_tc) {
+    if (st && c->w_tc)
+      return launch_apply_tc(&c->tmap_ab, &c->tmap_w, a, c->w.kmax, c->block_scratch, st, c->num_sms, s);
+    if (!st && apply_tc_supported(c->w.n, ncols) && (reinterpret_cast<uintptr_t>(V) & 15) == 0) {
+      EncodeTiledFn enc = get_encode();
+      CUtensorMap mv;
+      if (enc && make_apply_tc_tmaps(nullptr, &mv, nullptr, 0, V, c->w.n, ncols, enc))
+        return launch_apply_tc(&c->tmap_ab, &mv, a, ncols, c->block_scratch, c->st, c->num_sms, s);
+    }
+  }
   return launch_apply_block(a, st ? c->w.kmax : ncols, c->block_scratch, c->num_sms, s);
 }
 
@@ -842,6 +868,7 @@ static const char* timeout_site_name(int site) {
     case 3: return "site 3, pipeline wait of the matrix-free matvec";
     case 4: return "site 4, grid barrier of the fused iteration kernel";
     case 5: return "site 5, staged k x k matrices of the fused iteration kernel";
+    case 6: return "site 6, pipeline wait of the tensor-core block product";
     default: return "unknown site";
   }
 }

@@ -149,6 +149,15 @@ __device__ __forceinline__ void note_check(DevState* st, double rho_true, int mo
   st->rho_prev_chk = rho_true;
 }
 
+// Nearest TF32 value of a finite float32 (ties to even at 10 mantissa bits):
+// the element format of kind::tf32 tensor-core operands.
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t u = __float_as_uint(x);
+  const uint32_t lsb = (u >> 13) & 1u;
+  u = (u + 0xFFFu + lsb) & 0xFFFFE000u;
+  return __uint_as_float(u);
+}
+
 // --------------------------------------------------------------------------
 // mbarrier and TMA (bulk tensor copy) helpers, sm_90+ PTX used on sm_103a
 // --------------------------------------------------------------------------

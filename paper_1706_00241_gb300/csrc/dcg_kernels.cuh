@@ -253,6 +253,17 @@ cudaError_t launch_matvec_noalloc(const CUtensorMap* tmap, const float* p, float
 cudaError_t launch_apply_block(const ApplyBlockArgs& a, int cmax, float* scratch, int num_sms, cudaStream_t s);
 size_t apply_block_scratch_floats(int n, int cmax, int num_sms);
 cudaError_t apply_block_configure();
+// Y = A V on the tensor cores (split TF32, k_apply_tc): usable when n % 4 == 0,
+// n >= 32 and cmax <= 160; V column-major with leading dimension n, 16-byte
+// aligned. The maps come from make_apply_tc_tmaps (A: the operator; V: the
+// block, cols = cmax columns). tst: where a timeout is recorded when b.st is null.
+bool apply_tc_supported(int n, int cmax);
+size_t apply_tc_scratch_floats(int n, int cmax, int num_sms);
+bool make_apply_tc_tmaps(CUtensorMap* ma, CUtensorMap* mv, const float* A, int64_t lda, const float* V, int n,
+                         int cols, EncodeTiledFn encode);
+cudaError_t apply_tc_configure();
+cudaError_t launch_apply_tc(const CUtensorMap* ma, const CUtensorMap* mv, const ApplyBlockArgs& b, int cmax,
+                            float* scratch, DevState* tst, int num_sms, cudaStream_t s);
 cudaError_t launch_form_rbf(const float* X, int n, int d, double l, double s2, double noise, float* A, int64_t lda,
                             cudaStream_t s);
 

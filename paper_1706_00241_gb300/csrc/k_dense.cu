@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "dcg_kernels.cuh"
+#include "tc.cuh"
 
 namespace dcg {
 
@@ -1012,6 +1013,411 @@ cudaError_t launch_apply_block(const ApplyBlockArgs& a, int cmax, float* scratch
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || used == 1) return e;
   k_block_reduce<<<2 * num_sms, 256, 0, s>>>(a, used, colblocks, scratch);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Y = A V on the tensor cores (the start-of-solve product A W of Algorithm 1
+// and dcg_apply_block), split TF32 so that the product keeps float32
+// accuracy: A = A_hi + A_lo and V = V_hi + V_lo with A_hi = tf32(A),
+// A_lo = tf32(A - A_hi) (both rounded to nearest; A - A_hi is exact in
+// float32), so that A V = A_hi V_hi + A_hi V_lo + A_lo V_hi + O(2^-22) per
+// product, three kind::tf32 MMAs per K step. The hardware accumulates one
+// MMA chain with a bias that grows with its length (measured ~2e-8 per step
+// over long chains), so each 32-column K stage (4 K steps x 3 MMAs) goes to
+// its own TMEM accumulator and is added into float32 registers, rounded to
+// nearest, by the epilogue: the bias is bounded by one stage.
+//   Persistent CTAs take work items (128-row block, K range) in a fixed
+// stride; a K range's result goes to Y directly (one range) or to a partial
+// buffer that k_block_reduce sums in a fixed order. Roles (14 warps):
+//   warp 0   TMA: A box 32 x 128 and V box 32 x NPAD (128-byte swizzle) per stage;
+//   warp 1   MMA issue (one thread), TMEM owner;
+//   warps 2-5   split the stage in shared memory: hi in place, lo beside it
+//               (elementwise, so the swizzle does not matter), then a proxy
+//               fence so that the tensor core sees the generic stores;
+//   warps 6-13  read the stage's accumulator (two warps per TMEM lane quarter,
+//               each half of the columns) and add it into registers.
+// Every wait is bounded; a CTA that gives up fills its outputs with NaN and
+// records a timeout in the state given.
+// ---------------------------------------------------------------------------
+constexpr int AT_M = 128;                 // rows per item (MMA M)
+constexpr int AT_K = 32;                  // K per stage: one 128-byte swizzle row of float32
+constexpr int AT_CONV_WARPS = 4;
+constexpr int AT_EPI_WARPS = 8;
+constexpr int AT_THREADS = (2 + AT_CONV_WARPS + AT_EPI_WARPS) * 32;
+constexpr int AT_A_BYTES = AT_M * AT_K * 4;   // 16 KB
+constexpr int AT_MAX_NPAD = 160;          // columns of V (c <= 129) rounded up to 32
+__host__ __device__ constexpr int at_stage_bytes(int npad) { return 2 * AT_A_BYTES + 2 * npad * AT_K * 4; }
+__host__ __device__ constexpr int at_stages(int npad) { return npad <= 32 ? 5 : (npad <= 64 ? 4 : 3); }
+__host__ __device__ constexpr size_t at_smem(int npad) {
+  return 1024 + size_t(at_stages(npad)) * at_stage_bytes(npad) + 256;
+}
+__host__ __device__ constexpr uint32_t at_tmem_cols(int npad) {
+  return 2 * npad <= 64 ? 64u : (2 * npad <= 128 ? 128u : (2 * npad <= 256 ? 256u : 512u));
+}
+
+struct ApplyTcArgs {
+  int n;
+  int c;              // columns written (c <= NPAD); with st: read from st->k
+  int splits;         // K ranges per row block
+  int kchunk;         // K per range (multiple of AT_K)
+  int items;          // row blocks x splits
+  float* Y;           // column-major, leading dimension n (column 0 of the output)
+  float* part;        // splits > 1: part[r * NPAD * n + col * n + row]
+  DevState* st;       // in a solve: the state (k, done); also where a timeout is recorded
+  DevState* tst;      // where a timeout is recorded when st is null (may be null)
+  int skip_if_done;
+};
+
+__device__ __forceinline__ void at_split4(float4& hi, float4& lo) {
+  float4 h;
+  h.x = round_tf32(hi.x);
+  h.y = round_tf32(hi.y);
+  h.z = round_tf32(hi.z);
+  h.w = round_tf32(hi.w);
+  lo.x = round_tf32(hi.x - h.x);
+  lo.y = round_tf32(hi.y - h.y);
+  lo.z = round_tf32(hi.z - h.z);
+  lo.w = round_tf32(hi.w - h.w);
+  hi = h;
+}
+
+template <int NPAD>
+__global__ void __launch_bounds__(AT_THREADS, 1)
+    k_apply_tc(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_v, ApplyTcArgs a) {
+  constexpr int ST = at_stages(NPAD);
+  constexpr int SB = at_stage_bytes(NPAD);
+  constexpr int V_BYTES = NPAD * AT_K * 4;
+  constexpr int HC = NPAD / 2;              // columns per epilogue warp
+  static_assert(NPAD % 32 == 0 && NPAD <= AT_MAX_NPAD && HC % 16 == 0, "column tiling");
+  static_assert(AT_A_BYTES % 1024 == 0 && V_BYTES % 1024 == 0, "1024-byte aligned operand tiles");
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + size_t(ST) * SB);
+  uint64_t* full = bars;             // [ST] TMA landed
+  uint64_t* conv = full + ST;        // [ST] split done
+  uint64_t* empty = conv + ST;       // [ST] MMAs done with the stage
+  uint64_t* tfull = empty + ST;      // [2] accumulator ready
+  uint64_t* tempty = tfull + 2;      // [2] accumulator read
+  uint64_t* mdone = tempty + 2;      // all MMAs retired
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  __shared__ int s_issued;
+  __shared__ int s_cprog[AT_CONV_WARPS];  // stages each split warp has taken, for the drain
+
+  DevState* st = a.st;
+  if (st && a.skip_if_done && st->done) return;
+  const int c = st ? st->k : a.c;
+  if (c <= 0) return;
+  const int n = a.n, S = a.splits, G = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], AT_CONV_WARPS);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], AT_EPI_WARPS);
+    }
+    mbar_init(mdone, 1);
+    fence_mbarrier_init();
+    s_abort = 0;
+    s_issued = 0;
+  }
+  if (warp == 1) tc::tmem_alloc(&s_tmem, at_tmem_cols(NPAD));
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+
+  auto steps_of = [&](int item) {
+    const int sp = item % S;
+    const int k0 = sp * a.kchunk;
+    const int k1 = min(n, k0 + a.kchunk);
+    return k0 < k1 ? (k1 - k0 + AT_K - 1) / AT_K : 0;
+  };
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      prefetch_tensormap(&tmap_a);
+      prefetch_tensormap(&tmap_v);
+      const uint64_t pol = l2_policy_evict_first();
+      int it = 0;
+      bool stop = false;
+      for (int item = blockIdx.x; item < a.items && !stop; item += G) {
+        const int rb = item / S, k0 = (item % S) * a.kchunk, ns = steps_of(item);
+        for (int j = 0; j < ns; ++j, ++it) {
+          const int s = it % ST;
+          if (it >= ST && !mbar_wait_bounded(&empty[s], ((it / ST) - 1) & 1)) {
+            s_abort = 1;
+            stop = true;
+            break;
+          }
+          if (*(volatile int*)&s_abort) {
+            stop = true;
+            break;
+          }
+          unsigned char* stg = base + size_t(s) * SB;
+          mbar_arrive_expect_tx(&full[s], uint32_t(AT_A_BYTES + V_BYTES));
+          tma_load_2d_hint(stg, &tmap_a, &full[s], k0 + AT_K * j, rb * AT_M, pol);
+          tma_load_2d(stg + 2 * AT_A_BYTES, &tmap_v, &full[s], k0 + AT_K * j, 0);
+        }
+      }
+      s_issued = it;
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = tc::instr_desc(tc::kFmtTF32, AT_M, NPAD);
+      int it = 0;
+      bool stop = false;
+      for (int item = blockIdx.x; item < a.items && !stop; item += G) {
+        const int ns = steps_of(item);
+        for (int j = 0; j < ns; ++j, ++it) {
+          const int s = it % ST, b = it & 1;
+          if (!mbar_wait_bounded(&conv[s], (it / ST) & 1) ||
+              (it >= 2 && !mbar_wait_bounded(&tempty[b], ((it >> 1) - 1) & 1))) {
+            s_abort = 1;
+            stop = true;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t sa = smem_u32(base + size_t(s) * SB);
+          const uint32_t d = tmem + uint32_t(b * NPAD);
+#pragma unroll
+          for (int kk = 0; kk < AT_K / 8; ++kk) {
+            const uint64_t ahi = tc::smem_desc_kmajor(sa + 32 * kk, 128);
+            const uint64_t alo = tc::smem_desc_kmajor(sa + AT_A_BYTES + 32 * kk, 128);
+            const uint64_t vhi = tc::smem_desc_kmajor(sa + 2 * AT_A_BYTES + 32 * kk, 128);
+            const uint64_t vlo = tc::smem_desc_kmajor(sa + 2 * AT_A_BYTES + V_BYTES + 32 * kk, 128);
+            tc::mma_tf32(d, ahi, vhi, idesc, kk > 0);
+            tc::mma_tf32(d, ahi, vlo, idesc, 1);
+            tc::mma_tf32(d, alo, vhi, idesc, 1);
+          }
+          tc::mma_commit(&empty[s]);
+          tc::mma_commit(&tfull[b]);
+        }
+      }
+      tc::mma_commit(mdone);  // arrives once every MMA issued above has completed
+    }
+  } else if (warp < 2 + AT_CONV_WARPS) {
+    // ---------------- split into hi and lo ----------------
+    const int t = threadIdx.x - 64;
+    int it = 0;
+    bool stop = false;
+    for (int item = blockIdx.x; item < a.items && !stop; item += G) {
+      const int ns = steps_of(item);
+      for (int j = 0; j < ns; ++j, ++it) {
+        const int s = it % ST;
+        if (!mbar_wait_bounded(&full[s], (it / ST) & 1)) {
+          s_abort = 1;
+          stop = true;
+          break;
+        }
+        unsigned char* stg = base + size_t(s) * SB;
+        float4* ah = reinterpret_cast<float4*>(stg);
+        float4* al = reinterpret_cast<float4*>(stg + AT_A_BYTES);
+#pragma unroll
+        for (int q = t; q < AT_A_BYTES / 16; q += AT_CONV_WARPS * 32) {
+          float4 h = ah[q], l;
+          at_split4(h, l);
+          ah[q] = h;
+          al[q] = l;
+        }
+        float4* vh = reinterpret_cast<float4*>(stg + 2 * AT_A_BYTES);
+        float4* vl = reinterpret_cast<float4*>(stg + 2 * AT_A_BYTES + V_BYTES);
+#pragma unroll
+        for (int q = t; q < V_BYTES / 16; q += AT_CONV_WARPS * 32) {
+          float4 h = vh[q], l;
+          at_split4(h, l);
+          vh[q] = h;
+          vl[q] = l;
+        }
+        fence_proxy_async_smem();  // the tensor core (async proxy) reads what these stores wrote
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&conv[s]);
+      }
+    }
+    if (lane == 0) s_cprog[warp - 2] = it;
+  } else {
+    // ---------------- epilogue: accumulate the stages in registers ----------------
+    const int e = warp - (2 + AT_CONV_WARPS);
+    const int quarter = warp & 3;                // TMEM lanes this warp may read
+    const int col0 = (e / 4) * HC;
+    const uint32_t lane_off = uint32_t(quarter * 32) << 16;
+    int it = 0;
+    bool stop = false;
+    for (int item = blockIdx.x; item < a.items && !stop; item += G) {
+      const int rb = item / S, sp = item % S, ns = steps_of(item);
+      float acc[HC];
+#pragma unroll
+      for (int q = 0; q < HC; ++q) acc[q] = 0.f;
+      for (int j = 0; j < ns; ++j, ++it) {
+        const int b = it & 1;
+        if (!mbar_wait_bounded(&tfull[b], (it >> 1) & 1)) {
+          s_abort = 1;
+          stop = true;
+          break;
+        }
+        tc::fence_after_sync();
+#pragma unroll
+        for (int q = 0; q < HC; q += 16) {
+          uint32_t r[16];
+          tc::tmem_ld16_nowait(tmem + lane_off + uint32_t(b * NPAD + col0 + q), r);
+          tc::tmem_wait_ld16(r);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) acc[q + u] += __uint_as_float(r[u]);
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
+      }
+      if (stop) break;
+      const int row = rb * AT_M + quarter * 32 + lane;
+      float* dst = S > 1 ? a.part + int64_t(sp) * NPAD * n : a.Y;
+      if (row < n) {
+#pragma unroll
+        for (int q = 0; q < HC; ++q)
+          if (col0 + q < c) dst[int64_t(col0 + q) * n + row] = acc[q];
+      }
+    }
+  }
+  __syncthreads();
+  if (s_abort) {
+    // drain: wait (bounded) for the copies still in flight (issued, not yet
+    // taken by every split warp), then fill every output of this CTA's items
+    // with NaN and record the timeout
+    if (threadIdx.x == 0) {
+      int lo = s_issued;
+      for (int w = 0; w < AT_CONV_WARPS; ++w) lo = min(lo, s_cprog[w]);
+      for (int it = lo; it < s_issued; ++it) mbar_wait_bounded(&full[it % ST], (it / ST) & 1);
+      record_timeout(st ? st : a.tst, 6);
+    }
+    for (int item = blockIdx.x; item < a.items; item += G) {
+      const int rb = item / S, sp = item % S;
+      float* dst = S > 1 ? a.part + int64_t(sp) * NPAD * n : a.Y;
+      for (int idx = threadIdx.x; idx < AT_M * c; idx += blockDim.x) {
+        const int row = rb * AT_M + idx % AT_M, col = idx / AT_M;
+        if (row < n) dst[int64_t(col) * n + row] = __int_as_float(0x7fc00000);
+      }
+    }
+  }
+  if (warp == 1) {
+    if (lane == 0) mbar_wait_bounded(mdone, 0);
+    __syncwarp();
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, at_tmem_cols(NPAD));
+  }
+}
+
+// K ranges per 128-row block for the tensor-core product: persistent CTAs
+// (one per SM) take items (row block, K range) in a fixed stride, so the
+// item count should fill whole rounds of CTAs; the smallest count within 2 %
+// of the best round efficiency, at least 8 stages per range, at most 8
+// ranges (the partial buffer holds ranges x NPAD x n floats).
+int apply_tc_splits(int n, int num_sms) {
+  const int rowblocks = (n + AT_M - 1) / AT_M;
+  int smax = (n + AT_K * 8 - 1) / (AT_K * 8);
+  smax = std::max(1, std::min(smax, 8));
+  double eff[9] = {0.0};
+  double best = 0.0;
+  for (int sp = 1; sp <= smax; ++sp) {
+    const long long items = (long long)rowblocks * sp;
+    const long long rounds = (items + num_sms - 1) / num_sms;
+    eff[sp] = double(items) / double(rounds * num_sms);
+    best = std::max(best, eff[sp]);
+  }
+  for (int sp = 1; sp <= smax; ++sp)
+    if (eff[sp] >= best - 0.02) return sp;
+  return 1;
+}
+
+int apply_tc_npad(int c) { return (c + 31) / 32 * 32; }
+
+bool apply_tc_supported(int n, int cmax) { return n % 4 == 0 && n >= AT_K && apply_tc_npad(cmax) <= AT_MAX_NPAD; }
+
+size_t apply_tc_scratch_floats(int n, int cmax, int num_sms) {
+  if (!apply_tc_supported(n, cmax)) return 0;
+  const int s = apply_tc_splits(n, num_sms);
+  return s > 1 ? size_t(s) * apply_tc_npad(cmax) * size_t(n) : 0;
+}
+
+// Tensor maps of the two operands: A (row-major, leading dimension lda) in
+// boxes of 32 columns x 128 rows, V (column-major n x cols, leading dimension
+// n, i.e. rows of n floats) in boxes of 32 x npad; 128-byte swizzle, zero
+// fill outside the matrices.
+bool make_apply_tc_tmaps(CUtensorMap* ma, CUtensorMap* mv, const float* A, int64_t lda, const float* V, int n,
+                         int cols, EncodeTiledFn encode) {
+  if (A) {
+    cuuint64_t gdim[2] = {cuuint64_t(n), cuuint64_t(n)};
+    cuuint64_t gstride[1] = {cuuint64_t(lda) * 4};
+    cuuint32_t box[2] = {AT_K, AT_M};
+    cuuint32_t estride[2] = {1, 1};
+    if (encode(ma, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), gdim, gstride, box, estride,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  if (V) {
+    cuuint64_t gdim[2] = {cuuint64_t(n), cuuint64_t(cols)};
+    cuuint64_t gstride[1] = {cuuint64_t(n) * 4};
+    cuuint32_t box[2] = {AT_K, cuuint32_t(apply_tc_npad(cols))};
+    cuuint32_t estride[2] = {1, 1};
+    if (encode(mv, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(V), gdim, gstride, box, estride,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
+cudaError_t apply_tc_configure() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_apply_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(at_smem(32)))) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_apply_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(at_smem(64)))) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_apply_tc<96>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(at_smem(96)))) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_apply_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(at_smem(128)))) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_apply_tc<160>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(at_smem(160)));
+}
+
+// Y = A V with the maps above; cmax: the column count the maps were made for
+// (in a solve the kernel reads the active count from the state). scratch:
+// apply_tc_scratch_floats(n, cmax) floats (or null with one K range).
+cudaError_t launch_apply_tc(const CUtensorMap* ma, const CUtensorMap* mv, const ApplyBlockArgs& b, int cmax,
+                            float* scratch, DevState* tst, int num_sms, cudaStream_t s) {
+  const int n = b.n;
+  const int npad = apply_tc_npad(cmax);
+  int splits = scratch ? apply_tc_splits(n, num_sms) : 1;
+  int kchunk = (n + splits - 1) / splits;
+  kchunk = (kchunk + AT_K - 1) / AT_K * AT_K;
+  splits = (n + kchunk - 1) / kchunk;
+  ApplyTcArgs a{};
+  a.n = n;
+  a.c = b.c;
+  a.splits = splits;
+  a.kchunk = kchunk;
+  a.items = ((n + AT_M - 1) / AT_M) * splits;
+  a.Y = b.st ? b.Y + b.n : b.Y;
+  a.part = scratch;
+  a.st = b.st;
+  a.tst = tst;
+  a.skip_if_done = b.skip_if_done;
+  const int grid = std::min(a.items, num_sms);
+  switch (npad) {
+    case 32: k_apply_tc<32><<<grid, AT_THREADS, at_smem(32), s>>>(*ma, *mv, a); break;
+    case 64: k_apply_tc<64><<<grid, AT_THREADS, at_smem(64), s>>>(*ma, *mv, a); break;
+    case 96: k_apply_tc<96><<<grid, AT_THREADS, at_smem(96), s>>>(*ma, *mv, a); break;
+    case 128: k_apply_tc<128><<<grid, AT_THREADS, at_smem(128), s>>>(*ma, *mv, a); break;
+    case 160: k_apply_tc<160><<<grid, AT_THREADS, at_smem(160), s>>>(*ma, *mv, a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  ApplyBlockArgs r = b;
+  k_block_reduce<<<2 * num_sms, 256, 0, s>>>(r, splits, npad / AB_CB, scratch);
   return cudaGetLastError();
 }
 

@@ -4,8 +4,9 @@
 //   * k_rbf_mv<1>: q = A p with the fused p^T q (Algorithm 1).
 //     Persistent, warp-specialised: a TMA warp streams J tiles (128 rows,
 //     swizzled) with p_J by a bulk copy; one thread issues tcgen05.mma (BF16
-//     or TF32 inputs, float32 accumulation) for S~ = [X_I, 1] [X_J, -|x_j|^2/2]^T
-//     into one of four TMEM buffers; sixteen epilogue warps read S~ with
+//     or TF32 inputs, float32 accumulation) for S~_ij = x_i . x_j - |x_j|^2 / 2
+//     (augmented tile rows, below) into one of four TMEM buffers; sixteen
+//     epilogue warps read S~ with
 //     tcgen05.ld and accumulate q_i += exp2(2c S~_ij + u_i) p_j with the
 //     exponential on the SFU (ex2.approx), c = log2(e) / (2 l^2),
 //     u_i = log2(s^2) - c |x_i|^2: one packed FMA per two exponents. Padded
@@ -13,15 +14,15 @@
 //   * k_rbf_mv<8>: the start-of-solve product A W, eight columns of W per
 //     pass, each entry's exponential formed once and contracted with all
 //     eight (the same entries as the loop's matvec).
-//   * k_rbf_exact: the same operator on CUDA cores in the difference form
-//     sum_m (x_im - x_jm)^2 (float32 pair: exact squares, compensated sum).
-//     For the true residual b - A x the exponential is a float32 pair too
-//     (entries to ~1e-12 relative; error model below; compensated Dot2 sums
-//     with x = xh + xl) and the convergence test includes the entry-error
-//     bound; the block product A V uses expf (entries to ~2 ulp).
-//     The tensor-core Gram form n_i + n_j - 2 S_ij carries ~1e-5 relative
-//     error on close pairs; the residual recomputation in this exact form is
-//     the refinement that wins the accuracy back.
+//   * k_rbf_resid + k_rbf_resid_fin: the true residual b - A x on CUDA
+//     cores, entries as float32 pairs from distances that are exact up to a
+//     small remainder (Gram sums on a fixed grid, see below), a
+//     table-driven exponential pair and compensated (Dot2) sums with
+//     x = xh + xl; the convergence test includes the entry-error bound.
+//     k_rbf_block: the block product A V (dcg_apply_block), entries to ~2 ulp.
+//     The tensor-core tiles carry ~1e-5 relative error on close pairs (BF16,
+//     TF32 operands); the residual recomputation in the exact form is the
+//     refinement that wins the accuracy back.
 #include <cuda_bf16.h>
 
 #include "dcg_kernels.cuh"
@@ -35,12 +36,6 @@ namespace dcg {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-__device__ __forceinline__ float round_tf32(float x) {
-  uint32_t u = __float_as_uint(x);
-  const uint32_t lsb = (u >> 13) & 1u;
-  u = (u + 0xFFFu + lsb) & 0xFFFFE000u;  // round to nearest even at 10 mantissa bits
-  return __uint_as_float(u);
-}
 
 // Xr (n x d float32): the operator's points, X rounded to the chosen element
 // format (BF16, TF32) or X itself (FP32). Xt: two 128-byte-per-row tile
