@@ -559,6 +559,55 @@ def matrix_free_block(P, torch, mode):
 
 
 # ---------------------------------------------------------------------------
+# Gradient workload (opt-in): Adam on the GP hyperparameters through def-CG
+# solves of the matrix-free operator, n = 32768, d = 8, 16 probes per step
+# ---------------------------------------------------------------------------
+def gradient_arm(args):
+    import torch
+
+    import paper_1706_00241_gb300 as P
+    from paper_1706_00241_gb300 import build as B
+
+    torch.cuda.set_device(0)
+    B.build()
+    cfg = S.GRAD_32768
+    n = args.n if args.n else cfg.n
+    X, bs = S.draw_sequence(cfg, T=1)
+    Xd = torch.tensor(X[:n].astype(np.float32), device="cuda")
+    y = torch.tensor(bs[0][:n].astype(np.float32), device="cuda")
+    theta0 = (cfg.l0, cfg.signal_var, cfg.noise)
+    out = {"workload": cfg.name, "n": n, "d": cfg.d, "adam_steps": args.gradient_steps,
+           "probes": cfg.extra["probes"], "tol": cfg.tol, "refine_every": 50, "x_format": "bf16",
+           "per_step": "1 forward + 1 adjoint + 16 probe solves, one derivative-form pass each"}
+    short = max(1, args.gradient_steps // 10)
+    runs = (("defcg", cfg.k, cfg.ell, args.gradient_steps), ("defcg_first_steps", cfg.k, cfg.ell, short),
+            ("plain_cg", 0, 0, short))
+    for name, k, ell, steps in runs:
+        s = P.DefCG(n, k, ell, cfg.tol, refine_every=50, max_iter=20000)
+        s.set_operator_rbf(Xd, *theta0, xformat="bf16")
+        iters = []
+        orig_solve = s.solve
+
+        def counted(b, x=None, _f=orig_solve):
+            r = _f(b, x) if x is not None else _f(b)
+            iters.append(r[1]["iters"] + r[1]["matvecs_check"])
+            return r
+        s.solve = counted
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        path, grads = P.fit_gp(s, y, theta0, steps=steps, lr=cfg.extra["adam_lr"], probes=cfg.extra["probes"])
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - w0
+        s.close()
+        out[name] = {"steps": steps, "s_total": dt, "s_per_step": dt / steps, "solves": len(iters),
+                     "matvecs": int(sum(iters)), "matvecs_per_step": sum(iters) / steps,
+                     "theta_final": [float(v) for v in path[-1]]}
+    # the same first steps of the Adam path (the systems change along it)
+    out["speedup_first_steps_vs_plain_cg"] = out["plain_cg"]["s_total"] / out["defcg_first_steps"]["s_total"]
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------------
 # Kernel-only mode: one hot kernel on its own (for ncu captures of a small case)
 # ---------------------------------------------------------------------------
 def kernel_arm(args):
@@ -858,6 +907,11 @@ def main():
                     help="solve only the first T systems of the sequence (small profiling captures; "
                          "not a benchmark line)")
     ap.add_argument("--xformat", choices=["bf16", "tf32", "fp32"], default="bf16", help="X format for --kernel rbf_mv")
+    ap.add_argument("--gradient", action="store_true",
+                    help="instead of the sequence: Adam on the GP hyperparameters through def-CG solves "
+                         "(matrix-free, n = 32768, 16 probes per step); def-CG and plain CG also over the "
+                         "first tenth of the steps")
+    ap.add_argument("--gradient-steps", type=int, default=30)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -865,6 +919,8 @@ def main():
         reference_arm(args)
     elif args.kernel:
         kernel_arm(args)
+    elif args.gradient:
+        gradient_arm(args)
     else:
         gpu_arm(args)
 
