@@ -57,6 +57,11 @@ struct dcg_ctx {
   int* sym_sched = nullptr;        // symmetric matvec: the item counter, then the items largest first
   int sym_nitems = 0;
   bool fg_sparse_used = false;     // the last extraction formed F, G from the recorded scalars
+  // symmetric matrix-free matvec: row sums, column sums of the tile pairs,
+  // the row-block counter
+  float* mf_rowpart = nullptr;
+  float* mf_colpart = nullptr;
+  unsigned int* mf_ctr = nullptr;
   // tensor-core block product (k_apply_tc): A's map (set with the stored
   // operator) and the map of W (columns 1.. of XW, fixed at create)
   CUtensorMap tmap_ab{};
@@ -267,6 +272,7 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   CKC(apply_block_configure());
   CKC(iter_configure());
   CKC(rbf_mv_configure());
+  CKC(rbf_mv_sym_configure());
   CKC(chol_configure(96));
   CKC(ritz_configure());
 
@@ -417,6 +423,9 @@ extern "C" dcg_status dcg_set_operator_rbf(dcg_ctx* c, const float* X, int32_t d
     CK(dalloc(c, &c->prm, 1));
     CK(dalloc(c, &c->pmv, size_t(n_pad)));
     CK(dalloc(c, &c->pmvb, size_t(rbf_block_nc()) * n_pad));
+    CK(dalloc(c, &c->mf_rowpart, size_t(n_pad)));
+    CK(dalloc(c, &c->mf_colpart, rbf_mv_sym_colpart_floats(n_pad)));
+    CK(dalloc(c, &c->mf_ctr, 1));  // zeroed: the counter starts at 0
     c->resid_splits = rbf_resid_splits(n, c->num_sms);
     CK(dalloc(c, &c->XrT, size_t(64) * n_pad));
     CK(dalloc(c, &c->n64, size_t(n_pad)));
@@ -559,7 +568,10 @@ static cudaError_t op_matvec(dcg_ctx* c, const float* p, float* q, double* resul
     a.st = st;
     a.skip_if_done = st ? 1 : 0;
     a.col_idx = -1;
-    return launch_rbf_mv(c->rbf_tmap, a, c->rbf_grid, s);
+    a.rowpart = c->mf_rowpart;
+    a.colpart = c->mf_colpart;
+    a.sched_ctr = c->mf_ctr;
+    return launch_rbf_mv_sym(c->rbf_tmap, a, c->rbf_grid, s);
   }
   if (c->dense_sym) {
     SymvArgs a{};

@@ -165,6 +165,9 @@ struct RbfMvArgs {
   int64_t ldp;         // multi-column product: leading dimension of the padded columns in p
   int64_t ldq;         // multi-column product: leading dimension of q
   int ncols;           // multi-column product: columns to write
+  float* rowpart;      // symmetric matvec: row sums (n_pad floats)
+  float* colpart;      // symmetric matvec: column sums, n_tiles x n_pad floats
+  unsigned int* sched_ctr;  // symmetric matvec: row-block counter (zero between launches)
 };
 
 struct RbfExactArgs {
@@ -225,7 +228,11 @@ int rbf_max_d(int xformat);
 __host__ __device__ int rbf_row_bytes(int xformat, int d);
 cudaError_t rbf_mv_configure();
 int rbf_mv_grid(int n_tiles, int num_sms);
-cudaError_t launch_rbf_mv(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s);  // tmap[2]
+cudaError_t launch_rbf_mv(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s);
+// q = A p from the tile pairs (I, J >= I), each formed once (k_rbf_mv_sym + k_rbf_mv_fin)
+cudaError_t rbf_mv_sym_configure();
+size_t rbf_mv_sym_colpart_floats(int n_pad);
+cudaError_t launch_rbf_mv_sym(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s);  // tmap[2]
 int rbf_exact_grid(int n);
 cudaError_t launch_copy_cols(const float* src, float* dst, int n, int64_t ldd, int col0, int nc, const DevState* st,
                              cudaStream_t s);

@@ -518,6 +518,408 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Symmetric matrix-free matvec: each pair of tiles (I, J), J >= I, is formed
+// once (one MMA chain, one exponential per entry) and used twice: the row
+// sums q_I += E_IJ p_J as in k_rbf_mv, and, off the diagonal, the column sums
+// q_J += E_IJ^T p_I. The entry is exp2(2c S~_ij + u_i) with
+// S~_ij = x_i.x_j - |x_j|^2 / 2 and u_i = log2 s^2 - c |x_i|^2, i.e.
+// s^2 exp(-c' |x_i - x_j|^2): the same value for (i, j) and (j, i) up to
+// rounding, so the operator applied is exactly symmetric.
+//   Row blocks I (128 rows) are taken from a global counter in order, the
+// largest (most J tiles) first; every CTA then sweeps J = I .. n_tiles - 1.
+// The row sums of a block go to rowpart, the column sums of tile (I, J) to
+// colpart[I n_pad + j]: per warp (32 rows x 32 columns) a transposing
+// shuffle tree, then the four warps of a column slice (the TMEM lane
+// quarters) are added by the last of them to arrive (a counter per ring slot
+// and slice; no warp waits for another). k_rbf_mv_fin adds, per row, its row
+// part and the column parts of the blocks before its own in a fixed order,
+// the noise term and p^T q, and rewinds the counter.
+// ---------------------------------------------------------------------------
+constexpr int MVS_RB_RING = 8;   // row-block ids published ahead (producer <= 5 blocks ahead)
+constexpr int MVS_RED_RING = 8;  // column-sum slots (warps <= 4 tiles apart)
+
+// 16 entries of one row (lane): as mv_half, and the column contributions
+// c[k] = (entries 2k, 2k + 1) * p_i as packed pairs.
+__device__ __forceinline__ void mv_half_sym(const uint32_t (&h)[16], const float* pj, unsigned long long c2x2,
+                                            unsigned long long uu, unsigned long long pii, unsigned long long& sA,
+                                            unsigned long long& sB, unsigned long long (&c)[8], bool cols) {
+#pragma unroll
+  for (int j = 0; j < 16; j += 4) {
+    const float4 p4 = *reinterpret_cast<const float4*>(pj + j);
+    const unsigned long long g01 =
+        tc::f2fma(c2x2, tc::f2pk(__uint_as_float(h[j + 0]), __uint_as_float(h[j + 1])), uu);
+    const unsigned long long g23 =
+        tc::f2fma(c2x2, tc::f2pk(__uint_as_float(h[j + 2]), __uint_as_float(h[j + 3])), uu);
+    const unsigned long long e01 = tc::f2pk(tc::ex2_approx(tc::f2lo(g01)), tc::ex2_approx(tc::f2hi(g01)));
+    const unsigned long long e23 = tc::f2pk(tc::ex2_approx(tc::f2lo(g23)), tc::ex2_approx(tc::f2hi(g23)));
+    sA = tc::f2fma(e01, tc::f2pk(p4.x, p4.y), sA);
+    sB = tc::f2fma(e23, tc::f2pk(p4.z, p4.w), sB);
+    if (cols) {
+      c[j / 2] = tc::f2mul(e01, pii);
+      c[j / 2 + 1] = tc::f2mul(e23, pii);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(MV_THREADS, 1)
+    k_rbf_mv_sym(const __grid_constant__ CUtensorMap tmap_i, const __grid_constant__ CUtensorMap tmap_j, RbfMvArgs a) {
+  constexpr int SB = mv_stage_bytes(1);
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* xi_tile = base;
+  unsigned char* stages = base + MV_TILE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stages + size_t(MV_STAGES) * SB);
+  uint64_t* full = bars;                       // [MV_STAGES]
+  uint64_t* empty = full + MV_STAGES;          // [MV_STAGES]
+  uint64_t* tfull = empty + MV_STAGES;         // [MV_TBUF]
+  uint64_t* tempty = tfull + MV_TBUF;          // [MV_TBUF]
+  uint64_t* xi_full = tempty + MV_TBUF;
+  uint64_t* xi_empty = xi_full + 1;
+  uint64_t* rbfull = xi_empty + 1;             // [MVS_RB_RING] a row-block id is published
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  __shared__ int s_rb[MVS_RB_RING];
+  __shared__ float s_red[MVS_RED_RING][4][MV_TILE];     // column sums: [slot][TMEM lane quarter][column]
+  __shared__ unsigned int s_red_cnt[MVS_RED_RING][4];    // [slot][column slice]
+  __shared__ float s_rowred[MVS_RED_RING][4][MV_TILE];  // row sums: [slot][column slice][row]
+  __shared__ unsigned int s_row_cnt[MVS_RED_RING][4];    // [slot][TMEM lane quarter]
+
+  DevState* st = a.st;
+  if (st && a.skip_if_done && st->done) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_tiles = a.n_tiles;
+  const int64_t ldc = int64_t(n_tiles) * MV_TILE;  // n_pad: row stride of colpart
+  const int kind_tf32 = a.xformat != DCG_X_BF16;
+  const int dk = rbf_tile_coords(a.xformat, a.d) + kRbfAug;
+  const int ksteps = kind_tf32 ? (dk + 7) / 8 : (dk + 15) / 16;
+  const uint32_t row_bytes = uint32_t(rbf_row_bytes(a.xformat, dk));
+  const uint32_t tile_bytes = MV_TILE * row_bytes;
+  const uint32_t idesc = tc::instr_desc(kind_tf32 ? tc::kFmtTF32 : tc::kFmtBF16, MV_TILE, MV_TILE);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < MV_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], MV_EPI_WARPS);
+    }
+    for (int b = 0; b < MV_TBUF; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], MV_EPI_WARPS);
+    }
+    mbar_init(xi_full, 1);
+    mbar_init(xi_empty, 1);
+    for (int r = 0; r < MVS_RB_RING; ++r) mbar_init(&rbfull[r], 1);
+    fence_mbarrier_init();
+    s_abort = 0;
+  }
+  for (int idx = threadIdx.x; idx < MVS_RED_RING * 4; idx += blockDim.x) {
+    s_red_cnt[idx / 4][idx % 4] = 0u;
+    s_row_cnt[idx / 4][idx % 4] = 0u;
+  }
+  if (warp == 1) tc::tmem_alloc(&s_tmem, MV_TMEM_COLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0) {
+    // ---------------- producer: takes row blocks, publishes their ids ----------------
+    if (lane == 0) {
+      prefetch_tensormap(&tmap_i);
+      prefetch_tensormap(&tmap_j);
+      long long it = 0;
+      int rbc = 0;
+      while (true) {
+        int rb = int(atomicAdd(a.sched_ctr, 1u));
+        if (rb >= n_tiles) rb = -1;
+        // the X_I slot is free once the MMAs of the previous block are done
+        if (rb >= 0 && rbc > 0 && !mbar_wait_bounded(xi_empty, (rbc - 1) & 1)) {
+          s_abort = 1;
+          rb = -1;
+        }
+        s_rb[rbc % MVS_RB_RING] = rb;   // -1: no more blocks (the consumers leave)
+        mbar_arrive(&rbfull[rbc % MVS_RB_RING]);
+        if (rb < 0) break;
+        mbar_arrive_expect_tx(xi_full, tile_bytes);
+        tma_load_2d(xi_tile, &tmap_i, xi_full, 0, rb * MV_TILE);
+        bool stop = false;
+        for (int J = rb; J < n_tiles; ++J, ++it) {
+          const int s = int(it % MV_STAGES);
+          if (it >= MV_STAGES && !mbar_wait_bounded(&empty[s], uint32_t((it / MV_STAGES) - 1) & 1)) {
+            s_abort = 1;
+            stop = true;
+            break;
+          }
+          unsigned char* stg = stages + size_t(s) * SB;
+          mbar_arrive_expect_tx(&full[s], tile_bytes + MV_TILE * 4);
+          tma_load_2d(stg, &tmap_j, &full[s], 0, J * MV_TILE);
+          tc::bulk_load(stg + MV_TILE_BYTES, a.p + size_t(J) * MV_TILE, MV_TILE * 4, &full[s]);
+        }
+        ++rbc;
+        if (stop) {
+          s_rb[rbc % MVS_RB_RING] = -1;
+          mbar_arrive(&rbfull[rbc % MVS_RB_RING]);
+          break;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      long long it = 0;
+      const uint32_t a_base = smem_u32(xi_tile);
+      for (int rbc = 0;; ++rbc) {
+        if (!mbar_wait_bounded(&rbfull[rbc % MVS_RB_RING], (rbc / MVS_RB_RING) & 1)) { s_abort = 1; break; }
+        const int rb = *(volatile int*)&s_rb[rbc % MVS_RB_RING];
+        if (rb < 0) break;
+        if (!mbar_wait_bounded(xi_full, rbc & 1)) { s_abort = 1; break; }
+        tc::fence_after_sync();
+        bool stop = false;
+        for (int J = rb; J < n_tiles; ++J, ++it) {
+          const int s = int(it % MV_STAGES);
+          const int b = int(it % MV_TBUF);
+          if (!mbar_wait_bounded(&full[s], uint32_t(it / MV_STAGES) & 1) ||
+              (it >= MV_TBUF && !mbar_wait_bounded(&tempty[b], uint32_t((it / MV_TBUF) - 1) & 1))) {
+            s_abort = 1;
+            stop = true;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t b_base = smem_u32(stages + size_t(s) * SB);
+          const uint32_t d_tmem = tmem + uint32_t(b * MV_TILE);
+          for (int kk = 0; kk < ksteps; ++kk) {
+            const uint64_t ad = tc::smem_desc_kmajor(a_base + 32 * kk, row_bytes);
+            const uint64_t bd = tc::smem_desc_kmajor(b_base + 32 * kk, row_bytes);
+            if (kind_tf32)
+              tc::mma_tf32(d_tmem, ad, bd, idesc, kk > 0);
+            else
+              tc::mma_bf16(d_tmem, ad, bd, idesc, kk > 0);
+          }
+          tc::mma_commit(&tfull[b]);
+        }
+        tc::mma_commit(xi_empty);
+        if (stop) break;
+      }
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int ew = warp - 2;                  // 0..15
+    const int quarter = warp & 3;             // TMEM lane quarter this warp may read
+    const int slice = ew >> 2;                // 32-column slice of the tile
+    const int row_l = quarter * 32 + lane;    // row within the I block
+    const float c2 = a.prm->c2, l2s = a.prm->l2s;
+    const unsigned long long c2x2 = tc::f2pk(c2, c2);
+    const uint32_t lane_off = uint32_t(quarter * 32) << 16;
+    long long it = 0;
+    bool aborted = false;
+    for (int rbc = 0; !aborted; ++rbc) {
+      if (!mbar_wait_bounded(&rbfull[rbc % MVS_RB_RING], (rbc / MVS_RB_RING) & 1)) { s_abort = 1; break; }
+      const int rb = *(volatile int*)&s_rb[rbc % MVS_RB_RING];
+      if (rb < 0) break;
+      const int row = rb * MV_TILE + row_l;
+      const float u = l2s + a.vcol[row];        // vcol has n_pad entries
+      const float pi = a.p[row];                // p has n_pad entries, zero beyond n
+      const unsigned long long uu = tc::f2pk(u, u), pii = tc::f2pk(pi, pi);
+      float acc = 0.f, comp = 0.f;              // Kahan sum of the row's per-tile partials
+      uint32_t ha[16], hb[16];
+      {
+        const int b = int(it % MV_TBUF);
+        if (!mbar_wait_bounded(&tfull[b], uint32_t(it / MV_TBUF) & 1)) {
+          s_abort = 1;
+          aborted = true;
+        } else {
+          tc::fence_after_sync();
+          tc::tmem_ld16_nowait(tmem + lane_off + uint32_t(b * MV_TILE + slice * 32), ha);
+          tc::tmem_wait_ld16(ha);
+        }
+      }
+      for (int J = rb; J < n_tiles && !aborted; ++J, ++it) {
+        const int s = int(it % MV_STAGES);
+        const int b = int(it % MV_TBUF);
+        const bool cols = J > rb;               // off the diagonal: the transposed part too
+        const float* pj =
+            reinterpret_cast<const float*>(stages + size_t(s) * SB + MV_TILE_BYTES) + slice * 32;
+        tc::tmem_ld16_nowait(tmem + lane_off + uint32_t(b * MV_TILE + slice * 32 + 16), hb);
+        unsigned long long s0 = 0ull, s1 = 0ull, s2 = 0ull, s3 = 0ull;
+        unsigned long long cA[8], cB[8];
+        mv_half_sym(ha, pj, c2x2, uu, pii, s0, s1, cA, cols);
+        tc::tmem_wait_ld16(hb);
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
+        const bool next = J + 1 < n_tiles;
+        if (next) {
+          const int b2 = int((it + 1) % MV_TBUF);
+          if (!mbar_wait_bounded(&tfull[b2], uint32_t((it + 1) / MV_TBUF) & 1)) {
+            s_abort = 1;
+            aborted = true;
+          } else {
+            tc::fence_after_sync();
+            tc::tmem_ld16_nowait(tmem + lane_off + uint32_t(b2 * MV_TILE + slice * 32), ha);
+          }
+        }
+        mv_half_sym(hb, pj + 16, c2x2, uu, pii, s2, s3, cB, cols);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (next && !aborted) tc::tmem_wait_ld16(ha);
+        const float part = ((tc::f2lo(s0) + tc::f2hi(s0)) + (tc::f2lo(s1) + tc::f2hi(s1))) +
+                           ((tc::f2lo(s2) + tc::f2hi(s2)) + (tc::f2lo(s3) + tc::f2hi(s3)));
+        const float y = part - comp;
+        const float tt = acc + y;
+        comp = (tt - acc) - y;
+        acc = tt;
+        if (cols) {
+          // column sums of the warp's 32 rows: lane l ends with column 32 slice + l
+          float v[32];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            v[2 * k] = tc::f2lo(cA[k]);
+            v[2 * k + 1] = tc::f2hi(cA[k]);
+            v[16 + 2 * k] = tc::f2lo(cB[k]);
+            v[16 + 2 * k + 1] = tc::f2hi(cB[k]);
+          }
+          warp_transpose_sum(v, lane);
+          const int slot = int(it % MVS_RED_RING);
+          s_red[slot][quarter][slice * 32 + lane] = v[0];
+          __syncwarp();
+          unsigned int last = 0u;
+          if (lane == 0) {
+            __threadfence_block();
+            last = atomicAdd(&s_red_cnt[slot][slice], 1u) == 3u ? 1u : 0u;
+            if (last) {
+              __threadfence_block();
+              s_red_cnt[slot][slice] = 0u;
+            }
+          }
+          last = __shfl_sync(0xffffffffu, last, 0);
+          if (last) {
+            __threadfence_block();
+            const int col = slice * 32 + lane;
+            float t4 = 0.f;
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) t4 += *reinterpret_cast<volatile float*>(&s_red[slot][q4][col]);
+            a.colpart[int64_t(rb) * ldc + int64_t(J) * MV_TILE + col] = t4;
+          }
+        }
+      }
+      if (aborted) break;
+      // the four column slices of each row, added by the last of the four
+      // warps of the lane quarter to arrive (no warp waits for another)
+      const int rslot = rbc % MVS_RED_RING;
+      s_rowred[rslot][slice][row_l] = acc;
+      __syncwarp();
+      unsigned int lastr = 0u;
+      if (lane == 0) {
+        __threadfence_block();
+        lastr = atomicAdd(&s_row_cnt[rslot][quarter], 1u) == 3u ? 1u : 0u;
+        if (lastr) {
+          __threadfence_block();
+          s_row_cnt[rslot][quarter] = 0u;
+        }
+      }
+      lastr = __shfl_sync(0xffffffffu, lastr, 0);
+      if (lastr) {
+        __threadfence_block();
+        const volatile float* rr = &s_rowred[rslot][0][row_l];
+        a.rowpart[row] = (rr[0] + rr[MV_TILE]) + (rr[2 * MV_TILE] + rr[3 * MV_TILE]);
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, MV_TMEM_COLS);
+  }
+  if (s_abort && threadIdx.x == 0 && st) {
+    st->status = DCG_ERR_TIMEOUT;
+    st->timeout_site = 3;
+    st->done = 1;
+  }
+}
+
+// q_i = rowpart_i + sum_{I' < I(i)} colpart[I' n_pad + i] + noise p_i and p^T q.
+// One CTA per row block (128 rows, a lane four of them, float4 loads); its
+// 16 warps split the column parts of the blocks before it (warp w: w, w + 16,
+// ...), four loads in flight per warp, combined in a fixed order. The first
+// thread rewinds the row-block counter of k_rbf_mv_sym, which has finished.
+constexpr int MVF_WARPS = 16;
+__global__ void __launch_bounds__(MVF_WARPS * 32) k_rbf_mv_fin(RbfMvArgs a) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.sched_ctr = 0u;
+  DevState* st = a.st;
+  if (st && a.skip_if_done && st->done) return;
+  const int n = a.n;
+  const int64_t ldc = int64_t(a.n_tiles) * MV_TILE;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int I = blockIdx.x;
+  const int64_t off = int64_t(I) * MV_TILE + 4 * lane;
+  auto ld = [&](int t) { return __ldcg(reinterpret_cast<const float4*>(a.colpart + int64_t(t) * ldc + off)); };
+  float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
+  int t = warp;
+  for (; t + 3 * MVF_WARPS < I; t += 4 * MVF_WARPS) {
+    const float4 v0 = ld(t), v1 = ld(t + MVF_WARPS), v2 = ld(t + 2 * MVF_WARPS), v3 = ld(t + 3 * MVF_WARPS);
+    s0.x += v0.x; s0.y += v0.y; s0.z += v0.z; s0.w += v0.w;
+    s1.x += v1.x; s1.y += v1.y; s1.z += v1.z; s1.w += v1.w;
+    s2.x += v2.x; s2.y += v2.y; s2.z += v2.z; s2.w += v2.w;
+    s3.x += v3.x; s3.y += v3.y; s3.z += v3.z; s3.w += v3.w;
+  }
+  for (; t < I; t += MVF_WARPS) {
+    const float4 v = ld(t);
+    s0.x += v.x; s0.y += v.y; s0.z += v.z; s0.w += v.w;
+  }
+  __shared__ float4 red[MVF_WARPS][32];
+  red[warp][lane] = make_float4((s0.x + s1.x) + (s2.x + s3.x), (s0.y + s1.y) + (s2.y + s3.y),
+                                (s0.z + s1.z) + (s2.z + s3.z), (s0.w + s1.w) + (s2.w + s3.w));
+  __syncthreads();
+  double my = 0.0;
+  if (threadIdx.x < MV_TILE) {
+    const int l = threadIdx.x >> 2, e = threadIdx.x & 3;
+    const int row = I * MV_TILE + threadIdx.x;
+    float cs = 0.f;
+#pragma unroll
+    for (int w = 0; w < MVF_WARPS; ++w) cs += reinterpret_cast<const float*>(&red[w][l])[e];
+    if (row < n) {
+      const float pi = a.p[row];
+      const float q = (a.rowpart[row] + cs) + a.prm->noise * pi;
+      a.q[row] = q;
+      my = double(pi) * double(q);
+    }
+  }
+  __shared__ double s_part[MV_TILE / 32];
+  if (warp < MV_TILE / 32) {
+    const double v = warp_sum(my);
+    if (lane == 0) s_part[warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) a.partials[blockIdx.x] = (s_part[0] + s_part[1]) + (s_part[2] + s_part[3]);
+  if (!arrive_last(a.ticket)) return;
+  if (threadIdx.x < 32) {
+    double tt = 0.0;
+    for (int j = threadIdx.x; j < int(gridDim.x); j += 32) tt += __ldcg(a.partials + j);
+    tt = warp_sum(tt);
+    if (threadIdx.x == 0 && a.result) *a.result = tt;
+  }
+}
+
+constexpr size_t MVS_SMEM = MV_SMEM + 256;  // the row-block ring's barriers
+
+cudaError_t rbf_mv_sym_configure() {
+  return cudaFuncSetAttribute(k_rbf_mv_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, int(MVS_SMEM));
+}
+
+size_t rbf_mv_sym_colpart_floats(int n_pad) { return size_t(n_pad / MV_TILE) * size_t(n_pad); }
+
+// q = A p with the symmetric tile pairs; a.rowpart (n_pad floats), a.colpart
+// (rbf_mv_sym_colpart_floats), a.sched_ctr (zero between launches) and
+// a.partials (>= n_tiles doubles) set by the caller.
+cudaError_t launch_rbf_mv_sym(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s) {
+  k_rbf_mv_sym<<<grid, MV_THREADS, MVS_SMEM, s>>>(tmap[0], tmap[1], a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_rbf_mv_fin<<<a.n_tiles, MVF_WARPS * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t rbf_mv_configure() {
   cudaError_t e = cudaFuncSetAttribute(k_rbf_mv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(MV_SMEM));
   if (e != cudaSuccess) return e;
