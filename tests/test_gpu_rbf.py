@@ -161,7 +161,9 @@ def test_rbf_sequence_with_refinement(dcg, fmt):
             A = O.rbf_gram(Xr, cfg.lengthscale(t), 1.0, cfg.noise)
             xr = x.cpu().numpy()
             relres = np.linalg.norm(b - A @ xr) / np.linalg.norm(b)
-            assert info["status"] == 0 and relres <= 1.05e-6, (info, relres)
+            # certified: the exact-form residual plus its error estimate met tol
+            assert info["status"] == 0 and info["relres_true"] <= cfg.tol, info
+            assert relres <= cfg.tol * (1 + 1e-6), (info, relres)
             # The exact-form residual the GPU certified with agrees with the
             # float64 residual of the returned x to the kernel's own error
             # estimate (the one its convergence test adds to |r|).
@@ -171,7 +173,7 @@ def test_rbf_sequence_with_refinement(dcg, fmt):
             assert abs(info["relres_true"] - relres) <= est + 1e-13, (info["relres_true"], relres, est)
             ref = O.defcg(A, b.astype(np.float64), W=W, tol=cfg.tol, ell=cfg.ell, refine_every=25)
             W = O.harmonic_ritz(ref.W, ref.AW, ref.P, ref.Q, cfg.k).W
-            assert info["iters"] <= 10 + 1.25 * ref.iters, (info["iters"], ref.iters)
+            assert 0.9 * ref.iters - 2 <= info["iters"] <= 10 + 1.25 * ref.iters, (info["iters"], ref.iters)
             assert info["matvecs_check"] >= 1
             assert np.linalg.norm(xr - ref.x) <= 1e-4 * np.linalg.norm(ref.x)
 
