@@ -1147,8 +1147,15 @@ __device__ __forceinline__ void anchored_step2(unsigned long long& T, unsigned l
 // Partial residual sums of one row over the J tiles of split blockIdx.y:
 // part[(y * 3 + 0) * n + i] = s, [1] = c (the Dot2 pair of sum_j K_ij x_j),
 // [2] = sum_j (e_ij K_ij x_j)^2 (entry-error estimate, units of u^2).
+// Resident CTAs per SM the register budget is set for: x_i lives in
+// registers, so the budget grows with DMAX; more CTAs than the kernel's own
+// register need allows trades the unrolled inner loop for occupancy.
+__host__ __device__ constexpr int ex_resid_min_blocks(int dmax) {
+  return dmax <= 8 ? 6 : (dmax <= 16 ? 4 : (dmax <= 32 ? 3 : 2));
+}
+
 template <int DMAX>
-__global__ void __launch_bounds__(EX_ROWS) k_rbf_resid(RbfExactArgs a) {
+__global__ void __launch_bounds__(EX_ROWS, ex_resid_min_blocks(DMAX)) k_rbf_resid(RbfExactArgs a) {
   __shared__ __align__(16) float xs[DMAX][EX_J];
   __shared__ __align__(16) float sh_xh[EX_J], sh_xl[EX_J], sh_nh[EX_J], sh_nl[EX_J];
   __shared__ float2 exp_tab[64];
