@@ -741,12 +741,23 @@ def kernel_arm_dense(args, P, torch, stream):
         return
     if args.kernel == "apply_block":
         solver = P.DefCG(n, 0, 0, CFG.tol)
-        solver.set_operator_dense(A)
-        V = torch.tensor(np.random.default_rng(1).standard_normal((CFG.k, n)).astype(np.float32), device="cuda")
+        lda = (n + 3) // 4 * 4    # rows start on 16-byte boundaries (TMA)
+        if lda != n:
+            Ap = torch.zeros((n, lda), dtype=torch.float32, device="cuda")
+            Ap[:, :n] = A
+            A = Ap
+        solver.set_operator_dense(A, lda)
+        cols = args.cols or CFG.k
+        V = torch.tensor(np.random.default_rng(1).standard_normal((cols, n)).astype(np.float32), device="cuda")
         fn = lambda: solver.apply_block(V)
-        algo, unit, bound = 2.0 * n * n * CFG.k, "TFLOP/s", "alu"
-        peak, kind = 152 * 128 * 2 * hz / 1e12, "nominal FP32 FMA (152 SMs x 128 lanes x 2070 MHz)"
-        name = f"k_apply_block (Y = A W, {CFG.k} columns)"
+        if cols >= 32:
+            algo, unit, bound = 2.0 * n * n * cols, "TFLOP/s", "alu"
+            peak, kind = 152 * 128 * 2 * hz / 1e12, "nominal FP32 FMA (152 SMs x 128 lanes x 2070 MHz)"
+        else:
+            # a few columns: A read once bounds it
+            algo, unit, bound = 4.0 * n * n, "GB/s", "hbm"
+            peak, kind = peaks()
+        name = f"Y = A W, {cols} columns (k_apply_tc where n % 4 == 0, else k_apply_block)"
     else:
         solver = None
         fn = lambda: P.form_rbf_dense(Xd, CFG.lengthscale(0), CFG.signal_var, CFG.noise, out=A)
@@ -910,6 +921,7 @@ def main():
                          "(profiling mode: ncu cannot list kernels inside conditional graphs)")
     ap.add_argument("--kernel", choices=["gemv", "symv", "rbf_mv", "resid", "apply_block", "form", "iter"], default=None,
                     help="time one hot kernel alone (q = A p) instead of the sequence")
+    ap.add_argument("--cols", type=int, default=None, help="columns of W for --kernel apply_block (default k)")
     ap.add_argument("--n", type=int, default=0, help="system size for --kernel (default: the workload's)")
     ap.add_argument("--systems", type=int, default=0,
                     help="solve only the first T systems of the sequence (small profiling captures; "

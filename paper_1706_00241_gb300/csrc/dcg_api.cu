@@ -341,7 +341,7 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
                                apply_tc_scratch_floats(n, kMaxBlockCols, c->num_sms));
     if (bs) CKC(dalloc(c, &c->block_scratch, bs));
   }
-  if (kmax > 0 && apply_tc_supported(n, kmax)) {
+  if (kmax > 0 && apply_tc_supported(n, kmax) && apply_tc_preferred(kmax)) {
     EncodeTiledFn enc = get_encode();
     c->w_tc = enc && make_apply_tc_tmaps(nullptr, &c->tmap_w, nullptr, 0, w.XW + n, n, kmax, enc);
   }
@@ -702,9 +702,9 @@ static cudaError_t op_block(dcg_ctx* c, const float* V, int ncols, float* Y, Dev
   a.c = ncols;
   a.st = st;
   a.skip_if_done = st ? 1 : 0;
-  // tensor cores (split TF32) where the operands allow TMA; the FP32-pipe
-  // kernel otherwise
-  if (c->ab_tc) {
+  // tensor cores (split TF32) where the operands allow TMA and there are more
+  // than 16 columns; the FP32-pipe kernel otherwise
+  if (c->ab_tc && apply_tc_preferred(st ? c->w.kmax : ncols)) {
     if (st && c->w_tc)
       return launch_apply_tc(&c->tmap_ab, &c->tmap_w, a, c->w.kmax, c->block_scratch, st, c->num_sms, s);
     if (!st && apply_tc_supported(c->w.n, ncols) && (reinterpret_cast<uintptr_t>(V) & 15) == 0) {

@@ -265,6 +265,7 @@ cudaError_t apply_block_configure();
 // aligned. The maps come from make_apply_tc_tmaps (A: the operator; V: the
 // block, cols = cmax columns). tst: where a timeout is recorded when b.st is null.
 bool apply_tc_supported(int n, int cmax);
+bool apply_tc_preferred(int cmax);
 size_t apply_tc_scratch_floats(int n, int cmax, int num_sms);
 bool make_apply_tc_tmaps(CUtensorMap* ma, CUtensorMap* mv, const float* A, int64_t lda, const float* V, int n,
                          int cols, EncodeTiledFn encode);

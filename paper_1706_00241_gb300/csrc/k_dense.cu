@@ -811,28 +811,32 @@ bool make_rowop_tmap(CUtensorMap* map, const float* A, int64_t n, int64_t lda, E
 
 // ---------------------------------------------------------------------------
 // Y = A V, V and Y column-major n x c (leading dimension n), c <= 129.
-// A CTA computes 256 rows x 32 columns of Y over a K range (blockIdx.y; the
+// A CTA computes 256 rows x CB columns of Y over a K range (blockIdx.y; the
 // split partials are summed in a fixed order by k_block_reduce: no atomics,
-// deterministic). Per K-step of 32, the A tile (256 rows x 32, row-major, row
-// stride 36 floats) and the V tile (32 columns x 32, stride 36) arrive in
-// shared memory by asynchronous copies (cp.async, 16 bytes for A, 4 bytes for
-// V, whose columns need not be 16-byte aligned), two stages in flight.
+// deterministic). CB is 8, 16 or 32, the narrowest that covers the launch's
+// largest column count (wider counts take several blocks of 32), so that a
+// few columns stream A at its read rate instead of paying for 32. Per K-step
+// of 32, the A tile (256 rows x 32, row-major, row stride 36 floats) and the
+// V tile (CB columns x 32, stride 36) arrive in shared memory by asynchronous
+// copies (cp.async, 16 bytes for A, 4 bytes for V, whose columns need not be
+// 16-byte aligned), two stages in flight.
 // 128 threads; thread t computes rows rg, rg + 64, rg + 128, rg + 192 (rg =
 // t % 64; at a row stride of 36 floats, 8 consecutive lanes read 8 different
-// 16-byte bank groups) and columns 16 cg .. 16 cg + 15 (cg = t / 64, a
-// broadcast within the warp): per 4 K-values, 4 float4 loads of A and 16 of V
-// feed 256 FMAs. (Measured at n = 16384, 32 columns: 408 us, against 440 us
-// for 8 columns per thread with 256 threads and 438 us for a 4-stage pipeline
-// of 16-wide K-steps.)
+// 16-byte bank groups) and the CB / 2 columns of half cg = t / 64 (a
+// broadcast within the warp): per 4 K-values, 4 float4 loads of A and CB / 2
+// of V feed 8 CB FMAs. (Measured at n = 16384, 32 columns: 408 us, against
+// 440 us for 8 columns per thread with 256 threads and 438 us for a 4-stage
+// pipeline of 16-wide K-steps.)
 // In a solve (st set) the columns are the k active columns of W.
 // ---------------------------------------------------------------------------
 constexpr int AB_ROWS = 256;
 constexpr int AB_K = 32;
-constexpr int AB_CB = 32;
 constexpr int AB_LD = AB_K + 4;  // row stride of both tiles (floats)
 constexpr int AB_THREADS = 128;
-constexpr int AB_STAGE_FLOATS = AB_ROWS * AB_LD + AB_CB * AB_LD;
-constexpr size_t AB_SMEM = size_t(2) * AB_STAGE_FLOATS * sizeof(float);
+__host__ __device__ constexpr int ab_stage_floats(int cb) { return AB_ROWS * AB_LD + cb * AB_LD; }
+__host__ __device__ constexpr size_t ab_smem(int cb) { return size_t(2) * ab_stage_floats(cb) * sizeof(float); }
+// Column block of a launch whose largest column count is cmax.
+static int ab_cb(int cmax) { return cmax <= 8 ? 8 : (cmax <= 16 ? 16 : 32); }
 
 __device__ __forceinline__ void cp_async16(float* dst, const float* src, int src_bytes) {
   const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
@@ -846,8 +850,11 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+template <int CB>
 __global__ void __launch_bounds__(AB_THREADS, 2) k_apply_block(ApplyBlockArgs a, int kchunk, float* part) {
-  extern __shared__ __align__(16) float ab_smem[];
+  constexpr int CPT = CB / 2;  // columns per thread
+  constexpr int STAGE = ab_stage_floats(CB);
+  extern __shared__ __align__(16) float ab_smem_raw[];
   int c = a.c;
   const float* V = a.V;
   float* Y = a.Y;
@@ -858,19 +865,19 @@ __global__ void __launch_bounds__(AB_THREADS, 2) k_apply_block(ApplyBlockArgs a,
     Y += a.n;
   }
   const int n = a.n;
-  const int col0 = blockIdx.z * AB_CB;
+  const int col0 = blockIdx.z * CB;
   if (col0 >= c) return;
-  const int cw = min(AB_CB, c - col0);
+  const int cw = min(CB, c - col0);
   const int row0 = blockIdx.x * AB_ROWS;
   const int k_lo = blockIdx.y * kchunk, k_hi = min(n, k_lo + kchunk);
   const int t = threadIdx.x;
-  const int rg = t & 63, cg = t >> 6;  // cg in {0, 1}: columns 16 cg ..
+  const int rg = t & 63, cg = t >> 6;  // cg in {0, 1}: columns CPT cg ..
   const int64_t lda = a.lda;
-  // copies of one K-step into stage b: A chunk idx = q * 256 + t is row idx / 8,
-  // 16-byte column chunk idx % 8; V element idx = q * 256 + t is column idx / 32,
+  // copies of one K-step into stage b: A chunk idx = q * 128 + t is row idx / 8,
+  // 16-byte column chunk idx % 8; V element idx = q * 128 + t is column idx / 32,
   // K offset idx % 32. Out-of-range parts are zero-filled (source size 0 .. 16).
   auto issue = [&](int b, int k0) {
-    float* as = ab_smem + b * AB_STAGE_FLOATS;
+    float* as = ab_smem_raw + b * STAGE;
     float* vs = as + AB_ROWS * AB_LD;
 #pragma unroll
     for (int q = 0; q < (AB_ROWS * AB_K / 4) / AB_THREADS; ++q) {
@@ -882,7 +889,7 @@ __global__ void __launch_bounds__(AB_THREADS, 2) k_apply_block(ApplyBlockArgs a,
       cp_async16(as + r * AB_LD + 4 * c4, src, nb);
     }
 #pragma unroll
-    for (int q = 0; q < (AB_CB * AB_K) / AB_THREADS; ++q) {
+    for (int q = 0; q < (CB * AB_K) / AB_THREADS; ++q) {
       const int idx = q * AB_THREADS + t;
       const int j = idx >> 5, kk = idx & 31;
       const int gk = k0 + kk;
@@ -892,11 +899,11 @@ __global__ void __launch_bounds__(AB_THREADS, 2) k_apply_block(ApplyBlockArgs a,
     cp_async_commit();
   };
 
-  float acc[4][16];
+  float acc[4][CPT];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 16; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < CPT; ++j) acc[i][j] = 0.f;
   const int nsteps = k_lo < k_hi ? (k_hi - k_lo + AB_K - 1) / AB_K : 0;
   if (nsteps > 0) issue(0, k_lo);
   for (int s = 0; s < nsteps; ++s) {
@@ -907,7 +914,7 @@ __global__ void __launch_bounds__(AB_THREADS, 2) k_apply_block(ApplyBlockArgs a,
       cp_async_wait<0>();
     }
     __syncthreads();
-    const float* as = ab_smem + (s & 1) * AB_STAGE_FLOATS;
+    const float* as = ab_smem_raw + (s & 1) * STAGE;
     const float* vs = as + AB_ROWS * AB_LD;
 #pragma unroll 1
     for (int kq = 0; kq < AB_K; kq += 4) {
@@ -915,8 +922,8 @@ __global__ void __launch_bounds__(AB_THREADS, 2) k_apply_block(ApplyBlockArgs a,
 #pragma unroll
       for (int i = 0; i < 4; ++i) a4[i] = *reinterpret_cast<const float4*>(as + (rg + 64 * i) * AB_LD + kq);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float4 v4 = *reinterpret_cast<const float4*>(vs + (16 * cg + j) * AB_LD + kq);
+      for (int j = 0; j < CPT; ++j) {
+        const float4 v4 = *reinterpret_cast<const float4*>(vs + (CPT * cg + j) * AB_LD + kq);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           acc[i][j] = fmaf(a4[i].x, v4.x, acc[i][j]);
@@ -929,10 +936,10 @@ __global__ void __launch_bounds__(AB_THREADS, 2) k_apply_block(ApplyBlockArgs a,
     __syncthreads();
   }
   float* dst = Y;
-  if (gridDim.y > 1) dst = part + int64_t(blockIdx.y) * (int64_t(gridDim.z) * AB_CB) * n;
+  if (gridDim.y > 1) dst = part + int64_t(blockIdx.y) * (int64_t(gridDim.z) * CB) * n;
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int cj = 16 * cg + j;
+  for (int j = 0; j < CPT; ++j) {
+    const int cj = CPT * cg + j;
     if (cj >= cw) continue;
     float* colp = dst + int64_t(col0 + cj) * n;
 #pragma unroll
@@ -944,11 +951,17 @@ __global__ void __launch_bounds__(AB_THREADS, 2) k_apply_block(ApplyBlockArgs a,
 }
 
 cudaError_t apply_block_configure() {
-  return cudaFuncSetAttribute(k_apply_block, cudaFuncAttributeMaxDynamicSharedMemorySize, int(AB_SMEM));
+  cudaError_t e = cudaFuncSetAttribute(k_apply_block<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ab_smem(8)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_apply_block<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ab_smem(16)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_apply_block<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ab_smem(32)));
+  return e;
 }
 
-// Y[:, j] = sum over the K splits of the partials (fixed order).
-__global__ void __launch_bounds__(256) k_block_reduce(ApplyBlockArgs a, int splits, int colblocks, const float* part) {
+// Y[:, j] = sum over the K splits of the partials (fixed order); split sp of
+// column j, row i is part[sp * sstride + j * n + i].
+__global__ void __launch_bounds__(256) k_block_reduce(ApplyBlockArgs a, int splits, int64_t sstride, const float* part) {
   int c = a.c;
   float* Y = a.Y;
   if (a.st) {
@@ -957,7 +970,6 @@ __global__ void __launch_bounds__(256) k_block_reduce(ApplyBlockArgs a, int spli
     Y += a.n;
   }
   const int64_t total = int64_t(c) * a.n;
-  const int64_t sstride = int64_t(colblocks) * AB_CB * a.n;
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
        idx += int64_t(gridDim.x) * blockDim.x) {
     float s = 0.f;
@@ -970,8 +982,9 @@ __global__ void __launch_bounds__(256) k_block_reduce(ApplyBlockArgs a, int spli
 // fill whole waves of two CTAs per SM (the smallest split count within 2% of
 // the best wave efficiency), with at least 8 K-steps per split, at most 16.
 int apply_block_splits(int n, int cmax, int num_sms) {
+  const int cb = ab_cb(cmax);
   const int rowblocks = (n + AB_ROWS - 1) / AB_ROWS;
-  const int colblocks = (cmax + AB_CB - 1) / AB_CB;
+  const int colblocks = (cmax + cb - 1) / cb;
   const int base = rowblocks * colblocks;
   const int slots = 2 * num_sms;
   int kmax_splits = (n + AB_K * 8 - 1) / (AB_K * 8);
@@ -993,9 +1006,10 @@ int apply_block_splits(int n, int cmax, int num_sms) {
 // Largest split-K partial buffer any column count up to cmax can need.
 size_t apply_block_scratch_floats(int n, int cmax, int num_sms) {
   size_t best = 0;
-  for (int cb = 1; cb <= (cmax + AB_CB - 1) / AB_CB; ++cb) {
-    const int splits = apply_block_splits(n, cb * AB_CB, num_sms);
-    if (splits > 1) best = std::max(best, size_t(splits) * cb * AB_CB * size_t(n));
+  for (int c = 1; c <= cmax; ++c) {
+    const int cb = ab_cb(c);
+    const int splits = apply_block_splits(n, c, num_sms);
+    if (splits > 1) best = std::max(best, size_t(splits) * size_t((c + cb - 1) / cb) * cb * size_t(n));
   }
   return best;
 }
@@ -1003,16 +1017,22 @@ size_t apply_block_scratch_floats(int n, int cmax, int num_sms) {
 cudaError_t launch_apply_block(const ApplyBlockArgs& a, int cmax, float* scratch, int num_sms, cudaStream_t s) {
   if (cmax <= 0) return cudaSuccess;
   const int n = a.n;
+  const int cb = ab_cb(cmax);
   const int splits = scratch ? apply_block_splits(n, cmax, num_sms) : 1;
   int kchunk = (n + splits - 1) / splits;
   kchunk = (kchunk + AB_K - 1) / AB_K * AB_K;
   const int used = (n + kchunk - 1) / kchunk;
-  const int colblocks = (cmax + AB_CB - 1) / AB_CB;
+  const int colblocks = (cmax + cb - 1) / cb;
   dim3 grid((n + AB_ROWS - 1) / AB_ROWS, used, colblocks);
-  k_apply_block<<<grid, AB_THREADS, AB_SMEM, s>>>(a, kchunk, scratch);
+  if (cb == 8)
+    k_apply_block<8><<<grid, AB_THREADS, ab_smem(8), s>>>(a, kchunk, scratch);
+  else if (cb == 16)
+    k_apply_block<16><<<grid, AB_THREADS, ab_smem(16), s>>>(a, kchunk, scratch);
+  else
+    k_apply_block<32><<<grid, AB_THREADS, ab_smem(32), s>>>(a, kchunk, scratch);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || used == 1) return e;
-  k_block_reduce<<<2 * num_sms, 256, 0, s>>>(a, used, colblocks, scratch);
+  k_block_reduce<<<2 * num_sms, 256, 0, s>>>(a, used, int64_t(colblocks) * cb * n, scratch);
   return cudaGetLastError();
 }
 
@@ -1339,6 +1359,11 @@ int apply_tc_npad(int c) { return (c + 31) / 32 * 32; }
 
 bool apply_tc_supported(int n, int cmax) { return n % 4 == 0 && n >= AT_K && apply_tc_npad(cmax) <= AT_MAX_NPAD; }
 
+// Up to 16 columns the FP32-pipe kernel's 8- and 16-column blocks stream A
+// faster than the tensor-core kernel, whose W operand is padded to 32 columns
+// (measured at n = 16384, 8 columns: 0.21 against 0.35 ms).
+bool apply_tc_preferred(int cmax) { return cmax > 16; }
+
 size_t apply_tc_scratch_floats(int n, int cmax, int num_sms) {
   if (!apply_tc_supported(n, cmax)) return 0;
   const int s = apply_tc_splits(n, num_sms);
@@ -1417,7 +1442,7 @@ cudaError_t launch_apply_tc(const CUtensorMap* ma, const CUtensorMap* mv, const 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   ApplyBlockArgs r = b;
-  k_block_reduce<<<2 * num_sms, 256, 0, s>>>(r, splits, npad / AB_CB, scratch);
+  k_block_reduce<<<2 * num_sms, 256, 0, s>>>(r, splits, int64_t(npad) * r.n, scratch);
   return cudaGetLastError();
 }
 

@@ -192,12 +192,14 @@ def test_symmetric_matvec_full_size_sampled_rows(dcg):
 # A2: multi-vector product Y = A V
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("n,c", [(5, 1), (1001, 7), (2048, 33), (3001, 65), (700, 129), (1024, 32), (4100, 96),
-                                 (2000, 1), (516, 129), (16384, 32)])
+                                 (2000, 1), (516, 129), (16384, 32), (3001, 8), (1999, 16), (2047, 12), (4097, 9),
+                                 (36551, 8)])
 def test_apply_block_matches_oracle(dcg, n, c):
-    # n % 4 == 0 runs on the tensor cores (split TF32, one TMEM accumulator per
-    # 32-wide K stage added into float32 registers: per product ~3 2^-22 from
-    # the split, accumulation within a stage, then float32 sums of n / 32
-    # stage results), otherwise on the FP32 pipe (float32 chains); both within
+    # n % 4 == 0 with more than 16 columns runs on the tensor cores (split
+    # TF32, one TMEM accumulator per 32-wide K stage added into float32
+    # registers: per product ~3 2^-22 from the split, accumulation within a
+    # stage, then float32 sums of n / 32 stage results), otherwise on the FP32
+    # pipe (float32 chains, 8-, 16- or 32-column blocks); both within
     # (n / 32 + 32) eps32 sum |v_j a_ij|.
     rng = np.random.default_rng(c)
     lda = (n + 3) // 4 * 4
