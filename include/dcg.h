@@ -282,6 +282,32 @@ dcg_status dcg_form_rbf_dense(const float* X, int64_t n, int32_t d, double lengt
  * SUBSPACE_SINGULAR, TIMEOUT, STATE (no operator), INVALID_ARG, CUDA. */
 dcg_status dcg_solve(dcg_ctx* ctx, const float* b, double* x, dcg_solve_info* info);
 
+/* dcg_solve_multi: nrhs independent solves A x_c = b_c (c < nrhs), each the
+ * Deflated-CG(k)(A, b_c, x_{-1,c}, W, AW, tol) of dcg_solve (Algorithm 1,
+ * Sec. 2.2) with the context's W, run in lockstep: every iteration forms one
+ * block product A [p_c1 p_c2 ...] over the systems still running (matrix-free
+ * operator: one pass over the kernel entries per 8 systems, each exponential
+ * shared by them; stored operator: one read of A), then each system takes
+ * its own step, its convergence checks, refinements and final true residual
+ * exactly as dcg_solve does. Systems leave the block as they converge. The
+ * iterates are those of dcg_solve up to the rounding of the block product.
+ *   B      device, nrhs x n floats, row c = b_c (read).
+ *   X      device, nrhs x n doubles, row c = x_c; in: x_{-1,c} if
+ *          cfg.warm_start, else ignored; out: the solutions.
+ *   infos  host, nrhs entries, may be NULL; infos[c] as dcg_solve's info.
+ *   1 <= nrhs <= DCG_MAX_RHS. The first call with a larger nrhs than before
+ *   allocates the per-system workspace (about 5 n floats and 3 n doubles per
+ *   system) on the context's device.
+ * Stores no directions and records no history; dcg_update_subspace after it
+ * returns DCG_ERR_STATE until the next dcg_solve. The iteration is driven
+ * from the host (one state read per iteration), whatever cfg.host_loop says.
+ * Returns OK if every system returned OK, else the first other status in
+ * system order (MAXITER, BREAKDOWN, SUBSPACE_SINGULAR, TIMEOUT, STAGNATION);
+ * STATE (no operator), INVALID_ARG, CUDA as dcg_solve; NOMEM if the
+ * per-system workspace cannot be allocated. */
+#define DCG_MAX_RHS 32
+dcg_status dcg_solve_multi(dcg_ctx* ctx, int nrhs, const float* B, double* X, dcg_solve_info* infos);
+
 /* dcg_update_subspace: harmonic-Ritz extraction (Sec. 2.3, Eq. 7) from the
  * last solve: Z = [W, P], AZ = [AW, AP], F = Z^T AZ (symmetrised),
  * G = AZ^T AZ (float64 sums), G u = theta F u solved in float32 after scaling

@@ -13,6 +13,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libdcg.so")
 
 DCG_OK = 0
+DCG_MAX_RHS = 32  # include/dcg.h
 STATUS_NAMES = {
     0: "OK", 1: "INVALID_ARG", 2: "NOMEM", 3: "CUDA", 4: "BREAKDOWN",
     5: "SUBSPACE_SINGULAR", 6: "MAXITER", 7: "TIMEOUT", 8: "STATE", 9: "UNSUPPORTED",
@@ -84,6 +85,7 @@ SIGNATURES = {
     "dcg_set_rbf_params": (_I32, [_P, _D, _D, _D]),
     "dcg_form_rbf_dense": (_I32, [_P, _I64, _I32, _D, _D, _D, _P, _I64, _P]),
     "dcg_solve": (_I32, [_P, _P, _P, ctypes.POINTER(DcgSolveInfo)]),
+    "dcg_solve_multi": (_I32, [_P, _I32, _P, _P, ctypes.POINTER(DcgSolveInfo)]),
     "dcg_update_subspace": (_I32, [_P, _PI32]),
     "dcg_update_subspace_async": (_I32, [_P]),
     "dcg_get_ritz_values": (_I32, [_P, _PD, _I32, _PI32]),

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(PKG)
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdcg.so")
 
-SOURCES = ["dcg_api.cu", "k_dense.cu", "k_iter.cu", "k_ritz.cu", "k_rbf.cu", "k_laplace.cu"]
+SOURCES = ["dcg_api.cu", "k_dense.cu", "k_iter.cu", "k_ritz.cu", "k_rbf.cu", "k_laplace.cu", "k_multi.cu"]
 HEADERS = ["dcg_common.cuh", "dcg_kernels.cuh", "tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", f"-I{os.path.join(ROOT, 'include')}"]

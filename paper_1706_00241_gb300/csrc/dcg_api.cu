@@ -103,6 +103,20 @@ struct dcg_ctx {
   // split-K partials of the block product
   float* block_scratch = nullptr;
 
+  // lockstep solves of several right-hand sides (dcg_solve_multi): per-system
+  // vectors and states, allocated by the first call that needs them
+  int mr_cap = 0;              // systems the buffers hold
+  size_t mr_vs = 0;            // stride of the per-system vectors (n rounded up to 64)
+  std::vector<void*> mr_allocs;
+  float* mr_p = nullptr;       // mr_cap x n_pad directions (zero tails)
+  float *mr_xh = nullptr, *mr_xl = nullptr, *mr_r = nullptr, *mr_b = nullptr;  // mr_cap x n
+  double *mr_xd = nullptr, *mr_xbest = nullptr;                                  // mr_cap x n
+  double* mr_small = nullptr;  // mr_cap x 4 kk: h, hp, mu, gamma
+  float* mr_small_f = nullptr; // mr_cap x 2 kk: mu_f, gamma_f
+  float *mr_P = nullptr, *mr_Q = nullptr;  // gathered directions and their products, mr_ld x (mr_cap rounded up to 8)
+  DevState* mr_st = nullptr;   // mr_cap + 1 states; the last records timeouts of the shared kernels
+  DevState* mr_hst = nullptr;  // pinned copies
+
   // standalone matvec scratch
   double* mv_partials = nullptr;
   double* mv_result = nullptr;
@@ -202,6 +216,8 @@ extern "C" dcg_status dcg_destroy(dcg_ctx* c) {
   cudaStreamSynchronize(c->stream);
   destroy_graph(c);
   for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->mr_allocs) cudaFree(p);
+  if (c->mr_hst) cudaFreeHost(c->mr_hst);
   if (c->h_st) cudaFreeHost(c->h_st);
   if (c->h_small) cudaFreeHost(c->h_small);
   for (auto& s : c->cap)
@@ -621,37 +637,47 @@ static RbfExactArgs rbf_resid_args(dcg_ctx* c) {
 
 // r = b - A x for the float64 iterate (compensated sums), with the state's
 // check / refinement bookkeeping; mode as in RowOpArgs::resid_mode.
-static cudaError_t op_resid(dcg_ctx* c, int mode, int skip_if_done, cudaStream_t s) {
-  cudaError_t e = launch_split_x(c->w, c->grid_iter, skip_if_done, s);
+// w: the workspace of the solve (the context's, or one system of a lockstep
+// multi-right-hand-side solve).
+static cudaError_t op_resid_w(dcg_ctx* c, const Ws& w, int mode, int skip_if_done, cudaStream_t s) {
+  cudaError_t e = launch_split_x(w, c->grid_iter, skip_if_done, s);
   if (e != cudaSuccess) return e;
   if (c->op == OP_RBF) {
     RbfExactArgs a = rbf_resid_args(c);
-    a.xh = c->w.xh;
-    a.xl = c->w.xl;
-    a.b = c->w.b;
-    a.r = c->w.r;
-    a.ticket = &c->st->ticket[T_CHECK_RES];
-    a.st = c->st;
+    a.xh = w.xh;
+    a.xl = w.xl;
+    a.b = w.b;
+    a.r = w.r;
+    a.ticket = &w.st->ticket[T_CHECK_RES];
+    a.st = w.st;
     a.skip_if_done = skip_if_done;
     a.resid_mode = mode;
     return launch_rbf_resid(a, c->resid_splits, s);
   }
   RowOpArgs a{};
-  a.xh = c->w.xh;
-  a.xl = c->w.xl;
-  a.out = c->w.r;
-  a.b = c->w.b;
-  a.n = c->w.n;
+  a.xh = w.xh;
+  a.xl = w.xl;
+  a.out = w.r;
+  a.b = w.b;
+  a.n = w.n;
   a.partials = c->mv_partials;
-  a.ticket = &c->st->ticket[T_CHECK_RES];
+  a.ticket = &w.st->ticket[T_CHECK_RES];
   a.result = nullptr;
-  a.st = c->st;
+  a.st = w.st;
   a.skip_if_done = skip_if_done;
   a.resid_mode = mode;
   return launch_rowop(&c->tmap, a, true, c->grid_rows, s);
 }
 
-static cudaError_t op_block(dcg_ctx* c, const float* V, int ncols, float* Y, DevState* st, cudaStream_t s) {
+static cudaError_t op_resid(dcg_ctx* c, int mode, int skip_if_done, cudaStream_t s) {
+  return op_resid_w(c, c->w, mode, skip_if_done, s);
+}
+
+// st: the solve's state (start-of-solve product AW, k = st->k columns of W);
+// null for a plain block of ncols columns, whose bounded waits record a
+// timeout in tst (the context's state if null).
+static cudaError_t op_block(dcg_ctx* c, const float* V, int ncols, float* Y, DevState* st, cudaStream_t s,
+                            DevState* tst = nullptr) {
   if (c->op == OP_RBF && st) {
     // Start of a solve: AW with the same tensor-core operator the iteration
     // applies, so that the deflation (E, mu, the re-deflation of r) is
@@ -711,7 +737,7 @@ static cudaError_t op_block(dcg_ctx* c, const float* V, int ncols, float* Y, Dev
       EncodeTiledFn enc = get_encode();
       CUtensorMap mv;
       if (enc && make_apply_tc_tmaps(nullptr, &mv, nullptr, 0, V, c->w.n, ncols, enc))
-        return launch_apply_tc(&c->tmap_ab, &mv, a, ncols, c->block_scratch, c->st, c->num_sms, s);
+        return launch_apply_tc(&c->tmap_ab, &mv, a, ncols, c->block_scratch, tst ? tst : c->st, c->num_sms, s);
     }
   }
   return launch_apply_block(a, st ? c->w.kmax : ncols, c->block_scratch, c->num_sms, s);
@@ -885,6 +911,37 @@ static const char* timeout_site_name(int site) {
   }
 }
 
+// The solver state at the start of a solve. store: the solve keeps its
+// directions for the next extraction and its residual history (dcg_solve);
+// the systems of a lockstep multi-right-hand-side solve keep neither.
+static void init_state(const dcg_ctx* c, DevState* hs, bool store) {
+  memset(hs, 0, sizeof(DevState));
+  hs->max_iter = c->cfg.max_iter;
+  hs->refine_every = c->cfg.refine_every;
+  hs->k = c->k_active;
+  hs->ell = store ? c->cfg.ell : 0;
+  hs->window = c->cfg.window;
+  hs->reproject = c->cfg.reproject;
+  hs->hist_on = store ? c->cfg.record_history : 0;
+  hs->hist_cap = hs->hist_on ? c->cfg.max_iter + 2 : 0;
+  hs->warm_start = c->cfg.warm_start;
+  hs->status = DCG_OK;
+}
+
+static void fill_info(const DevState* hs, float ms, dcg_solve_info* info) {
+  memset(info, 0, sizeof(*info));
+  info->status = hs->status;
+  info->iters = hs->iter;
+  info->matvecs_loop = hs->iter;
+  info->matvecs_setup = hs->k + hs->warm_start;
+  info->matvecs_check = hs->matvecs_check;
+  info->k_used = hs->k;
+  info->stored = hs->nstored;
+  info->relres_recursive = hs->bnorm2 > 0.0 ? sqrt(hs->rho / hs->bnorm2) : 0.0;
+  info->relres_true = hs->relres_true;
+  info->ms_total = ms;
+}
+
 // ---------------------------------------------------------------------------
 // Solve
 // ---------------------------------------------------------------------------
@@ -899,17 +956,7 @@ extern "C" dcg_status dcg_solve(dcg_ctx* c, const float* b, double* x, dcg_solve
   }
   const int n = c->w.n;
   DevState* hs = c->h_st;
-  memset(hs, 0, sizeof(DevState));
-  hs->max_iter = c->cfg.max_iter;
-  hs->refine_every = c->cfg.refine_every;
-  hs->k = c->k_active;
-  hs->ell = c->cfg.ell;
-  hs->window = c->cfg.window;
-  hs->reproject = c->cfg.reproject;
-  hs->hist_on = c->cfg.record_history;
-  hs->hist_cap = c->cfg.record_history ? c->cfg.max_iter + 2 : 0;
-  hs->warm_start = c->cfg.warm_start;
-  hs->status = DCG_OK;
+  init_state(c, hs, true);
   if (c->test_barrier_polls > 0) {  // one-shot failure-handling test hook
     hs->test_skip_arrival = 1;
     hs->spin_limit = c->test_barrier_polls;
@@ -937,19 +984,7 @@ extern "C" dcg_status dcg_solve(dcg_ctx* c, const float* b, double* x, dcg_solve
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   c->have_solve = (hs->status == DCG_OK || hs->status == DCG_ERR_MAXITER);
   c->last_iters = hs->iter;
-  if (info) {
-    memset(info, 0, sizeof(*info));
-    info->status = hs->status;
-    info->iters = hs->iter;
-    info->matvecs_loop = hs->iter;
-    info->matvecs_setup = hs->k + hs->warm_start;
-    info->matvecs_check = hs->matvecs_check;
-    info->k_used = hs->k;
-    info->stored = hs->nstored;
-    info->relres_recursive = hs->bnorm2 > 0.0 ? sqrt(hs->rho / hs->bnorm2) : 0.0;
-    info->relres_true = hs->relres_true;
-    info->ms_total = ms;
-  }
+  if (info) fill_info(hs, ms, info);
   if (hs->status != DCG_OK) {
     char buf[256];
     std::string where;
@@ -959,6 +994,242 @@ extern "C" dcg_status dcg_solve(dcg_ctx* c, const float* b, double* x, dcg_solve
     c->err = buf;
   }
   return dcg_status(hs->status);
+}
+
+// ---------------------------------------------------------------------------
+// Lockstep solves of several right-hand sides (dcg_solve_multi)
+// ---------------------------------------------------------------------------
+template <typename T>
+static cudaError_t mr_alloc(dcg_ctx* c, T** p, size_t count) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(T) + 16);
+  if (e != cudaSuccess) return e;
+  c->mr_allocs.push_back(v);
+  *p = static_cast<T*>(v);
+  return cudaMemsetAsync(v, 0, count * sizeof(T) + 16, c->stream);
+}
+
+// Per-system buffers for cap systems (replacing smaller ones).
+static dcg_status mr_reserve(dcg_ctx* c, int cap) {
+  if (cap <= c->mr_cap) return DCG_OK;
+  CK(cudaStreamSynchronize(c->stream));
+  for (void* p : c->mr_allocs) cudaFree(p);
+  c->mr_allocs.clear();
+  if (c->mr_hst) cudaFreeHost(c->mr_hst);
+  c->mr_hst = nullptr;
+  c->mr_cap = 0;
+  const size_t n = size_t(c->w.n), np = size_t(c->n_pad), vs = (n + 63) / 64 * 64;
+  const size_t kk = size_t(std::max(c->w.kmax, 1)), ncap = size_t(cap), cap8 = (ncap + 7) / 8 * 8;
+  CK(mr_alloc(c, &c->mr_p, ncap * np));
+  CK(mr_alloc(c, &c->mr_xh, ncap * vs));
+  CK(mr_alloc(c, &c->mr_xl, ncap * vs));
+  CK(mr_alloc(c, &c->mr_r, ncap * vs));
+  CK(mr_alloc(c, &c->mr_b, ncap * vs));
+  CK(mr_alloc(c, &c->mr_xd, ncap * vs));
+  CK(mr_alloc(c, &c->mr_xbest, ncap * vs));
+  CK(mr_alloc(c, &c->mr_small, ncap * 4 * kk));
+  CK(mr_alloc(c, &c->mr_small_f, ncap * 2 * kk));
+  CK(mr_alloc(c, &c->mr_P, cap8 * np));
+  CK(mr_alloc(c, &c->mr_Q, cap8 * np));
+  CK(mr_alloc(c, &c->mr_st, ncap + 1));
+  CK(cudaMallocHost(&c->mr_hst, sizeof(DevState) * (ncap + 1)));
+  c->mr_vs = vs;
+  c->mr_cap = cap;
+  return DCG_OK;
+}
+
+// The workspace of system j: its own vectors and state; W, AW, E and the
+// small matrices of the context; no direction store, no history.
+static Ws mr_lane_ws(const dcg_ctx* c, int j) {
+  Ws w = c->w;
+  const size_t vs = c->mr_vs, kk = size_t(std::max(c->w.kmax, 1));
+  w.xd = c->mr_xd + j * vs;
+  w.xbest = c->mr_xbest + j * vs;
+  w.xh = c->mr_xh + j * vs;
+  w.xl = c->mr_xl + j * vs;
+  w.r = c->mr_r + j * vs;
+  w.b = c->mr_b + j * vs;
+  w.p = c->mr_p + j * size_t(c->n_pad);
+  w.q = c->mr_Q + j * size_t(c->n_pad);  // set to the system's column of the block in each iteration
+  w.P = nullptr;
+  w.Q = nullptr;
+  w.ellmax = 0;
+  w.fg = nullptr;
+  w.h = c->mr_small + j * 4 * kk;
+  w.hp = w.h + kk;
+  w.mu = w.h + 2 * kk;
+  w.gamma = w.h + 3 * kk;
+  w.mu_f = c->mr_small_f + j * 2 * kk;
+  w.gamma_f = w.mu_f + kk;
+  w.st = c->mr_st + j;
+  return w;
+}
+
+// Q[:, j] = A P[:, j] for the na gathered directions (leading dimension ld):
+// the operator pass the systems of a lockstep solve share. The matrix-free
+// operator applies the loop's tensor-core entries, each exponential formed
+// once per pass of rbf_block_nc() columns; a bounded wait that gives up
+// records a timeout in the shared state (the last of mr_st).
+static cudaError_t op_multi(dcg_ctx* c, int na, int64_t ld, cudaStream_t s) {
+  DevState* tst = c->mr_st + c->mr_cap;
+  if (c->op == OP_RBF) {
+    const int nc = rbf_block_nc();
+    for (int j0 = 0; j0 < na; j0 += nc) {
+      RbfMvArgs a{};
+      a.p = c->mr_P + j0 * ld;
+      a.ldp = ld;
+      a.vcol = c->vcol;
+      a.q = c->mr_Q + j0 * ld;
+      a.ldq = ld;
+      a.ncols = std::min(nc, na - j0);
+      a.n = c->w.n;
+      a.n_tiles = c->n_pad / 128;
+      a.d = c->rbf_d;
+      a.xformat = c->rbf_xformat;
+      a.prm = c->prm;
+      a.st = tst;  // never done; col_idx < 0: all ncols columns are written
+      a.skip_if_done = 0;
+      a.col_idx = -1;
+      cudaError_t e = launch_rbf_mv_block(c->rbf_tmap, a, c->rbf_grid, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  return op_block(c, c->mr_P, na, c->mr_Q, nullptr, s, tst);
+}
+
+extern "C" dcg_status dcg_solve_multi(dcg_ctx* c, int nrhs, const float* B, double* X, dcg_solve_info* infos) {
+  if (!c) return DCG_ERR_INVALID_ARG;
+  { const dcg_status pend = finish_update(c); if (pend != DCG_OK) return pend; }
+  if (!B || !X) return fail(c, DCG_ERR_INVALID_ARG, "B and X must not be NULL");
+  if (nrhs < 1 || nrhs > DCG_MAX_RHS)
+    return fail(c, DCG_ERR_INVALID_ARG, "nrhs must lie in [1, " + std::to_string(DCG_MAX_RHS) + "]");
+  if (c->op == OP_NONE) return fail(c, DCG_ERR_STATE, "no operator set");
+  { const dcg_status r = mr_reserve(c, nrhs); if (r != DCG_OK) return r; }
+  // AW and E are recomputed below: the directions of the last dcg_solve no
+  // longer belong to the context's AW
+  c->have_solve = false;
+  const int n = c->w.n;
+  const int64_t ld = c->op == OP_RBF ? c->n_pad : n;  // the stored block product takes leading dimension n
+  const int rows = c->op == OP_RBF ? c->n_pad : n;
+  const int sh = c->mr_cap;  // index of the shared state
+  cudaStream_t s = c->stream;
+  Handles h0{};
+  DevState* hs = c->mr_hst;
+  for (int j = 0; j < nrhs; ++j) init_state(c, hs + j, false);
+  memset(hs + sh, 0, sizeof(DevState));
+  hs[sh].status = DCG_OK;
+  CK(cudaMemcpyAsync(c->mr_st, hs, sizeof(DevState) * size_t(sh + 1), cudaMemcpyHostToDevice, s));
+  std::vector<Ws> w(nrhs);
+  for (int j = 0; j < nrhs; ++j) {
+    w[j] = mr_lane_ws(c, j);
+    CK(cudaMemcpyAsync(w[j].b, B + int64_t(j) * n, size_t(n) * 4, cudaMemcpyDeviceToDevice, s));
+    if (c->cfg.warm_start)
+      CK(cudaMemcpyAsync(w[j].xd, X + int64_t(j) * n, size_t(n) * 8, cudaMemcpyDeviceToDevice, s));
+    else
+      CK(cudaMemsetAsync(w[j].xd, 0, size_t(n) * 8, s));
+  }
+  auto read_states = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(hs, c->mr_st, sizeof(DevState) * size_t(sh + 1), cudaMemcpyDeviceToHost, s);
+    return e != cudaSuccess ? e : cudaStreamSynchronize(s);
+  };
+  CK(cudaEventRecord(c->ev0, s));
+  // Start of the solves: AW, E = W^T AW, its factor and the small products,
+  // once for all systems (through system 0's state, before any system can be
+  // done); a singular E ends every system.
+  CK(op_block(c, c->w.XW, 0, c->w.Y, w[0].st, s));
+  CK(launch_gram_E(w[0], c->gramE_part, c->num_sms, s));
+  CK(launch_gram_GW(w[0], c->gramE_part, c->num_sms, s));
+  CK(launch_chol_E(w[0], s));
+  CK(launch_small_prods(w[0], s));
+  CK(read_states());
+  int shared_status = hs[0].status;
+  std::vector<char> hit(nrhs, shared_status != DCG_OK ? 1 : 0);  // systems a shared failure ended
+  if (shared_status == DCG_OK) {
+    // per system: r_{-1}, the initial projection and the first direction
+    for (int j = 0; j < nrhs; ++j) {
+      if (c->cfg.warm_start) CK(op_resid_w(c, w[j], 0, 1, s));
+      CK(launch_setup_r(w[j], c->grid_iter, s));
+      CK(launch_check_dots(w[j], c->grid_iter, s));
+      CK(launch_check_update(w[j], c->grid_iter, 0, 1, h0, s));
+      CK(launch_phase2_setup(w[j], c->grid_iter, s));
+    }
+    CK(read_states());
+    bool again = false;
+    for (int j = 0; j < nrhs; ++j) {
+      if (hs[j].mode != 1) continue;
+      CK(op_resid_w(c, w[j], -1, 1, s));
+      CK(launch_check_dots(w[j], c->grid_iter, s));
+      CK(launch_check_update(w[j], c->grid_iter, 1, 0, h0, s));
+      again = true;
+    }
+    if (again) CK(read_states());
+    MultiLanes lanes{};
+    for (;;) {
+      if (hs[sh].status != DCG_OK) {  // a wait of the shared block product gave up
+        shared_status = hs[sh].status;
+        for (int j = 0; j < nrhs; ++j) hit[j] = !hs[j].done;
+        break;
+      }
+      int na = 0;
+      for (int j = 0; j < nrhs; ++j)
+        if (!hs[j].done) lanes.idx[na++] = j;
+      if (na == 0) break;
+      CK(launch_multi_gather(c->mr_p, c->n_pad, lanes, na, rows, c->mr_P, ld, s));
+      CK(op_multi(c, na, ld, s));
+      CK(launch_multi_pq(c->mr_P, c->mr_Q, ld, n, lanes, na, c->mr_st, s));
+      for (int a = 0; a < na; ++a) {
+        Ws& wj = w[lanes.idx[a]];
+        wj.q = c->mr_Q + int64_t(a) * ld;
+        CK(launch_iter_fused(wj, c->num_sms, h0, s));
+      }
+      CK(read_states());
+      bool chk = false;
+      for (int a = 0; a < na; ++a) {
+        const int j = lanes.idx[a];
+        if (hs[j].mode == 0 || hs[j].done) continue;
+        CK(op_resid_w(c, w[j], -1, 1, s));
+        CK(launch_check_dots(w[j], c->grid_iter, s));
+        CK(launch_check_update(w[j], c->grid_iter, 0, 0, h0, s));
+        CK(launch_phase2(w[j], c->grid_iter, h0, s));
+        chk = true;
+      }
+      if (chk) CK(read_states());
+    }
+    for (int j = 0; j < nrhs; ++j) {
+      if (shared_status == DCG_OK && !hs[j].true_valid && !hs[j].zero_rhs) CK(op_resid_w(c, w[j], 3, 0, s));
+      CK(launch_finalize(w[j], c->grid_iter, s));
+    }
+  }
+  CK(cudaEventRecord(c->ev1, s));
+  for (int j = 0; j < nrhs; ++j)
+    CK(cudaMemcpyAsync(X + int64_t(j) * n, w[j].xd, size_t(n) * 8, cudaMemcpyDeviceToDevice, s));
+  CK(read_states());
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  dcg_status first = DCG_OK;
+  int first_j = -1;
+  for (int j = 0; j < nrhs; ++j) {
+    // a failure of the shared steps (E singular, a wait of the block product)
+    // is the status of every system it ended
+    if (hit[j]) hs[j].status = shared_status;
+    if (infos) fill_info(hs + j, ms, infos + j);
+    if (first == DCG_OK && hs[j].status != DCG_OK) {
+      first = dcg_status(hs[j].status);
+      first_j = j;
+    }
+  }
+  if (first != DCG_OK) {
+    char buf[256];
+    const DevState& f = hs[first_j];
+    std::string where;
+    const int site = f.timeout_site ? f.timeout_site : hs[sh].timeout_site;
+    if (f.status == DCG_ERR_TIMEOUT) where = std::string(" (bounded wait gave up: ") + timeout_site_name(site) + ")";
+    snprintf(buf, sizeof(buf), "system %d of %d ended with status %d (%s) after %d iterations%s", first_j, nrhs,
+             f.status, dcg_status_string(first), f.iter, where.c_str());
+    c->err = buf;
+  }
+  return first;
 }
 
 // Enqueues the harmonic-Ritz update on the context's stream (no host wait).

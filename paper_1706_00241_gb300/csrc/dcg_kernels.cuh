@@ -305,6 +305,16 @@ cudaError_t launch_final_gate(const Ws& w, Handles h, cudaStream_t s);
 cudaError_t launch_finalize(const Ws& w, int grid, cudaStream_t s);
 cudaError_t launch_split_x(const Ws& w, int grid, int skip_if_done, cudaStream_t s);
 
+// ---- lockstep multi-right-hand-side solves (k_multi.cu)
+// Systems of one block, by column: column j holds system idx[j].
+struct MultiLanes {
+  int idx[DCG_MAX_RHS];
+};
+cudaError_t launch_multi_gather(const float* src, int64_t lds, const MultiLanes& lanes, int na, int rows, float* dst,
+                                int64_t ldd, cudaStream_t s);
+cudaError_t launch_multi_pq(const float* P, const float* Q, int64_t ld, int n, const MultiLanes& lanes, int na,
+                            DevState* states, cudaStream_t s);
+
 // ---- harmonic Ritz (k_ritz.cu)
 struct RitzArgs {
   int n;

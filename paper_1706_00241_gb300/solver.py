@@ -166,6 +166,35 @@ class DefCG:
             self._check(st, "dcg_solve")
         return x, d
 
+    def solve_multi(self, B: torch.Tensor, X: torch.Tensor | None = None, raise_on_error: bool = True):
+        """Independent solves A x_c = b_c for the rows b_c of B (nrhs x n,
+        float32), run in lockstep so that each operator pass serves every
+        system still iterating (dcg_solve_multi); returns (X, list of info
+        dicts), X float64 nrhs x n. Stores no directions: update_subspace
+        needs a dcg_solve after it."""
+        _dev_f32(B, "B")
+        if B.dim() != 2 or B.shape[1] != self.n:
+            raise ValueError(f"B must be (nrhs, {self.n}), got {tuple(B.shape)}")
+        nrhs = B.shape[0]
+        if not 1 <= nrhs <= _lib.DCG_MAX_RHS:
+            raise ValueError(f"nrhs must lie in [1, {_lib.DCG_MAX_RHS}], got {nrhs}")
+        if X is None:
+            X = torch.zeros(B.shape, dtype=torch.float64, device=B.device)
+        if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float64 and X.is_contiguous()
+                and tuple(X.shape) == tuple(B.shape)):
+            raise TypeError("X must be a contiguous float64 CUDA tensor shaped like B")
+        infos = (_lib.DcgSolveInfo * nrhs)()
+        st = self.lib.dcg_solve_multi(self._ctx, nrhs, ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(X.data_ptr()),
+                                      infos)
+        out = []
+        for i in range(nrhs):
+            d = infos[i].as_dict()
+            d["status_name"] = _lib.STATUS_NAMES.get(d["status"], str(d["status"]))
+            out.append(d)
+        if raise_on_error and st != _lib.DCG_OK:
+            self._check(st, "dcg_solve_multi")
+        return X, out
+
     def update_subspace(self, wait: bool = True) -> int | None:
         """Harmonic-Ritz extraction of the next W (Sec. 2.3); returns its width.
 

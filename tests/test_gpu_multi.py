@@ -1,0 +1,215 @@
+"""GPU parity of the lockstep multi-right-hand-side solve (dcg_solve_multi).
+
+Each system of a lockstep solve is Algorithm 1 on its own right-hand side
+with the context's W; the systems share only the operator pass. Parity is
+therefore per column: against the float64 oracle's def-CG on that column
+(iterations, solution, true residual) and against the GPU's own single solve
+of the same system (the block product rounds differently from the
+single-vector matvec, so the counts agree to a couple of iterations).
+"""
+
+import numpy as np
+import pytest
+
+import dcg_synth as S
+from oracle import dcg_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dcg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1706_00241_gb300 import build
+    build.build()
+    import paper_1706_00241_gb300 as P
+    return P
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+def padded(A32, lda):
+    n = A32.shape[0]
+    out = np.zeros((n, lda), dtype=np.float32)
+    out[:, :n] = A32
+    return out
+
+
+def spd32(n, lo, hi, seed):
+    A, _ = S.spd_with_spectrum(np.geomspace(lo, hi, n), seed=seed)
+    return A.astype(np.float32)
+
+
+ROUND = {
+    "bf16": lambda X: torch.tensor(X).to(torch.bfloat16).to(torch.float32).numpy(),
+    "fp32": lambda X: X,
+}
+
+
+@pytest.mark.parametrize("n,k,nrhs", [(1001, 8, 5), (2048, 16, 17), (777, 0, 3), (1500, 8, 1)])
+def test_multi_dense_matches_oracle_and_single(dcg, n, k, nrhs):
+    # kappa = 10: a relative residual of 1e-6 bounds the solution error by
+    # ~1e-5 on either side (as for the single solve). Covers the 8-, 16- and
+    # 32-column blocks of the stored product (nrhs 5, 17 -> 17 then fewer as
+    # systems converge), plain CG (k = 0) and one system.
+    A32 = spd32(n, 1.0, 10.0, seed=n + k)
+    A64 = A32.astype(np.float64)
+    rng = np.random.default_rng(n + nrhs)
+    B = rng.standard_normal((nrhs, n)).astype(np.float32)
+    B *= rng.uniform(0.1, 10.0, size=(nrhs, 1)).astype(np.float32)   # the stopping test is relative
+    W = rng.standard_normal((k, n)).astype(np.float32)
+    lda = (n + 3) // 4 * 4
+    tol = 1e-6
+    with dcg.DefCG(n, max(k, 1), 16, tol) as s:
+        s.set_operator_dense(dev(padded(A32, lda)), lda)
+        if k:
+            s.set_subspace(dev(W))
+        X, infos = s.solve_multi(dev(B))
+        single = [s.solve(dev(B[c]))[1] for c in range(nrhs)]
+    X = X.cpu().numpy()
+    for c in range(nrhs):
+        info = infos[c]
+        ref = O.defcg(A64, B[c].astype(np.float64), W=W.T.astype(np.float64) if k else None, tol=tol)
+        relres = np.linalg.norm(B[c] - A64 @ X[c]) / np.linalg.norm(B[c])
+        assert info["status"] == 0, info
+        assert relres <= tol * 1.001
+        assert abs(info["relres_true"] - relres) <= 1e-3 * relres + 1e-12
+        assert abs(info["iters"] - ref.iters) <= 2, (c, info["iters"], ref.iters)
+        assert abs(info["iters"] - single[c]["iters"]) <= 2, (c, info["iters"], single[c]["iters"])
+        assert np.linalg.norm(X[c] - ref.x) <= 1e-5 * np.linalg.norm(ref.x)
+        assert info["matvecs_setup"] == k and info["stored"] == 0
+
+
+def test_multi_dense_ill_conditioned_with_refinement(dcg):
+    # kappa = 1e4 and residual replacement every 20 iterations: every system
+    # reaches the true residual. Over ~700 float32 iterations the block
+    # product's rounding (FP32-pipe k_apply_block against the single solve's
+    # GEMV) moves the count by a few: within 3 + 1 % of the single solve's.
+    n, k = 1536, 12
+    A32 = spd32(n, 1e-2, 1e2, seed=5)
+    A64 = A32.astype(np.float64)
+    rng = np.random.default_rng(5)
+    B = rng.standard_normal((7, n)).astype(np.float32)
+    W = rng.standard_normal((k, n)).astype(np.float32)
+    with dcg.DefCG(n, k, 0, 1e-6, refine_every=20) as s:
+        s.set_operator_dense(dev(A32))
+        s.set_subspace(dev(W))
+        X, infos = s.solve_multi(dev(B))
+        single = [s.solve(dev(B[c]))[1] for c in range(B.shape[0])]
+    X = X.cpu().numpy()
+    for c in range(B.shape[0]):
+        relres = np.linalg.norm(B[c] - A64 @ X[c]) / np.linalg.norm(B[c])
+        assert infos[c]["status"] == 0 and relres <= 1e-6 * 1.001, (infos[c], relres)
+        assert infos[c]["matvecs_check"] >= 1
+        assert abs(infos[c]["iters"] - single[c]["iters"]) <= 3 + 0.01 * single[c]["iters"], \
+            (infos[c]["iters"], single[c]["iters"])
+        ref = O.defcg(A64, B[c].astype(np.float64), W=W.T.astype(np.float64), tol=1e-6, refine_every=20)
+        assert abs(infos[c]["iters"] - ref.iters) <= max(3, 0.05 * ref.iters), (infos[c]["iters"], ref.iters)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp32"])
+def test_multi_rbf_with_refinement(dcg, fmt):
+    # The matrix-free operator: W from one solve and its update, then 10
+    # Rademacher right-hand sides (the gradient workload's probes) in one
+    # lockstep solve, iterating with the tensor-core entries of k_rbf_mv<8>
+    # (passes of 8 systems) and refined by the exact-form residual every 25
+    # iterations. Bars as for the single matrix-free solve: certified true
+    # residual <= tol, float64 residual of x <= tol, iterations within
+    # 0.9 oracle - 2 .. 1.25 oracle + 10 and within 10 % + 3 of the GPU's
+    # single solves, x within 1e-4 of the oracle's.
+    n, d, k, ell, l, noise, tol = 2048, 8, 8, 24, 1.0, 1e-2, 1e-6
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Xr = ROUND[fmt](X).astype(np.float64)
+    A = O.rbf_gram(Xr, l, 1.0, noise)
+    b0 = rng.standard_normal(n).astype(np.float32)
+    Z = (rng.integers(0, 2, size=(10, n)) * 2 - 1).astype(np.float32)
+    with dcg.DefCG(n, k, ell, tol, refine_every=25) as s:
+        s.set_operator_rbf(dev(X), l, 1.0, noise, xformat=fmt)
+        s.solve(dev(b0))
+        s.update_subspace()
+        W = s.get_subspace().cpu().numpy().astype(np.float64)   # (k, n)
+        U, infos = s.solve_multi(dev(Z))
+        single = [s.solve(dev(Z[c]))[1] for c in range(Z.shape[0])]
+    U = U.cpu().numpy()
+    for c in range(Z.shape[0]):
+        info = infos[c]
+        relres = np.linalg.norm(Z[c] - A @ U[c]) / np.linalg.norm(Z[c])
+        assert info["status"] == 0 and info["relres_true"] <= tol, info
+        assert relres <= tol * (1 + 1e-6), (info, relres)
+        ref = O.defcg(A, Z[c].astype(np.float64), W=W.T, tol=tol, refine_every=25)
+        assert 0.9 * ref.iters - 2 <= info["iters"] <= 10 + 1.25 * ref.iters, (info["iters"], ref.iters)
+        assert abs(info["iters"] - single[c]["iters"]) <= 3 + 0.1 * single[c]["iters"], \
+            (info["iters"], single[c]["iters"])
+        assert np.linalg.norm(U[c] - ref.x) <= 1e-4 * np.linalg.norm(ref.x)
+
+
+def test_multi_zero_rows_warm_start_and_state(dcg):
+    # Zero right-hand sides return x = 0 after no iteration (reading R2) while
+    # the others run; a warm start takes each row of X as its x_{-1} (oracle's
+    # x_init); the lockstep solve stores no directions, so an update after it
+    # is out of order until the next single solve.
+    n, k = 1200, 4
+    A32 = spd32(n, 1.0, 10.0, seed=9)
+    A64 = A32.astype(np.float64)
+    rng = np.random.default_rng(9)
+    B = rng.standard_normal((4, n)).astype(np.float32)
+    B[1] = 0.0
+    X0 = rng.standard_normal((4, n))
+    W = rng.standard_normal((k, n)).astype(np.float32)
+    with dcg.DefCG(n, k, 8, 1e-6, warm_start=True) as s:
+        s.set_operator_dense(dev(A32))
+        s.set_subspace(dev(W))
+        X, infos = s.solve_multi(dev(B), torch.tensor(X0, device="cuda"))
+        with pytest.raises(dcg.DcgError) as e:
+            s.update_subspace()
+        assert e.value.status == 8
+        s.solve(dev(B[0]), torch.tensor(X0[0], device="cuda"))
+        assert s.update_subspace() > 0
+    X = X.cpu().numpy()
+    for c in (0, 2, 3):
+        ref = O.defcg(A64, B[c].astype(np.float64), x_init=X0[c], W=W.T.astype(np.float64), tol=1e-6)
+        assert infos[c]["status"] == 0 and infos[c]["matvecs_setup"] == k + 1
+        assert abs(infos[c]["iters"] - ref.iters) <= 2
+        assert np.linalg.norm(X[c] - ref.x) <= 1e-5 * np.linalg.norm(ref.x)
+    # b = 0: x = 0 whatever x_{-1} was
+    assert infos[1]["status"] == 0 and infos[1]["iters"] == 0
+    assert np.all(X[1] == 0.0)
+
+
+def test_multi_singular_subspace_ends_every_system(dcg):
+    # W with two equal columns: E = W^T A W is singular, which the shared
+    # start of the lockstep solve detects once; every system reports it.
+    n = 600
+    A32 = spd32(n, 1.0, 10.0, seed=2)
+    rng = np.random.default_rng(2)
+    W = rng.standard_normal((3, n)).astype(np.float32)
+    W[2] = W[0]
+    B = rng.standard_normal((3, n)).astype(np.float32)
+    with dcg.DefCG(n, 3, 0, 1e-6) as s:
+        s.set_operator_dense(dev(A32))
+        s.set_subspace(dev(W))
+        _, infos = s.solve_multi(dev(B), raise_on_error=False)
+        assert [i["status"] for i in infos] == [5, 5, 5]
+        assert "system 0 of 3" in s.last_error()
+
+
+def test_multi_argument_checks(dcg):
+    n = 256
+    with dcg.DefCG(n, 2, 0, 1e-6) as s:
+        B = torch.zeros((2, n), dtype=torch.float32, device="cuda")
+        with pytest.raises(dcg.DcgError) as e:    # no operator yet
+            s.solve_multi(B)
+        assert e.value.status == 8
+        s.set_operator_dense(dev(np.eye(n)))
+        for bad in (0, 33):
+            st = s.lib.dcg_solve_multi(s._ctx, bad, B.data_ptr(), B.data_ptr(), None)
+            assert st == 1
+        with pytest.raises(ValueError):
+            s.solve_multi(torch.zeros((33, n), dtype=torch.float32, device="cuda"))
+        X, infos = s.solve_multi(torch.ones((2, n), dtype=torch.float32, device="cuda"))
+        assert torch.allclose(X, torch.ones_like(X)) and all(i["iters"] == 1 for i in infos)
