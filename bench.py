@@ -585,24 +585,34 @@ def gradient_arm(args):
     theta0 = (cfg.l0, cfg.signal_var, cfg.noise)
     out = {"workload": cfg.name, "n": n, "d": cfg.d, "adam_steps": args.gradient_steps,
            "probes": cfg.extra["probes"], "tol": cfg.tol, "refine_every": 50, "x_format": "bf16",
-           "per_step": "1 forward + 1 adjoint + 16 probe solves, one derivative-form pass each"}
+           "per_step": "1 forward + 1 adjoint + 16 probe solves (in lockstep: one operator pass per iteration "
+                       "for all probes still iterating), one derivative-form pass each"}
     short = max(1, args.gradient_steps // 10)
-    runs = (("defcg", cfg.k, cfg.ell, args.gradient_steps), ("defcg_first_steps", cfg.k, cfg.ell, short),
-            ("plain_cg", 0, 0, short))
-    for name, k, ell, steps in runs:
+    # probes in lockstep (dcg_solve_multi) unless the run's name says otherwise
+    runs = (("defcg", cfg.k, cfg.ell, args.gradient_steps, True),
+            ("defcg_first_steps", cfg.k, cfg.ell, short, True),
+            ("defcg_first_steps_probes_one_by_one", cfg.k, cfg.ell, short, False),
+            ("plain_cg", 0, 0, short, True))
+    for name, k, ell, steps, block in runs:
         s = P.DefCG(n, k, ell, cfg.tol, refine_every=50, max_iter=20000)
         s.set_operator_rbf(Xd, *theta0, xformat="bf16")
         iters = []
-        orig_solve = s.solve
+        orig_solve, orig_multi = s.solve, s.solve_multi
 
         def counted(b, x=None, _f=orig_solve):
             r = _f(b, x) if x is not None else _f(b)
             iters.append(r[1]["iters"] + r[1]["matvecs_check"])
             return r
-        s.solve = counted
+
+        def counted_multi(B, X=None, _f=orig_multi):
+            r = _f(B, X) if X is not None else _f(B)
+            iters.extend(i["iters"] + i["matvecs_check"] for i in r[1])
+            return r
+        s.solve, s.solve_multi = counted, counted_multi
         torch.cuda.synchronize()
         w0 = time.perf_counter()
-        path, grads = P.fit_gp(s, y, theta0, steps=steps, lr=cfg.extra["adam_lr"], probes=cfg.extra["probes"])
+        path, grads = P.fit_gp(s, y, theta0, steps=steps, lr=cfg.extra["adam_lr"], probes=cfg.extra["probes"],
+                               block_probes=block)
         torch.cuda.synchronize()
         dt = time.perf_counter() - w0
         s.close()
@@ -611,6 +621,8 @@ def gradient_arm(args):
                      "theta_final": [float(v) for v in path[-1]]}
     # the same first steps of the Adam path (the systems change along it)
     out["speedup_first_steps_vs_plain_cg"] = out["plain_cg"]["s_total"] / out["defcg_first_steps"]["s_total"]
+    out["speedup_lockstep_probes"] = (out["defcg_first_steps_probes_one_by_one"]["s_total"]
+                                      / out["defcg_first_steps"]["s_total"])
     print(json.dumps(out))
 
 

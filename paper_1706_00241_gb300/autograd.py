@@ -25,6 +25,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
+from ._lib import DCG_MAX_RHS
 from .solver import DefCG
 
 
@@ -70,18 +71,26 @@ class DefCGSolve(torch.autograd.Function):
 class LogDetProbes(torch.autograd.Function):
     """Value 0 (log det A is not evaluated); gradient 1/2 mean_p u_p^T
     (dA/dtheta) z_p with A u_p = z_p solved by def-CG. Z: (P, n) float32
-    probes on the device (rows are probes)."""
+    probes on the device (rows are probes). With ``block`` the probes are
+    solved in lockstep (dcg_solve_multi, up to DCG_MAX_RHS at a time), each
+    operator pass serving all of them; otherwise one after another."""
 
     @staticmethod
-    def forward(ctx, theta, solver: DefCG, Z):
+    def forward(ctx, theta, solver: DefCG, Z, block: bool = True):
         params = _params(theta)
         solver.set_rbf_params(*params)
         U = torch.empty_like(Z, dtype=torch.float32)
         infos = []
-        for p in range(Z.shape[0]):
-            u, info = solver.solve(Z[p].contiguous())
-            U[p] = u.to(torch.float32)
-            infos.append(info)
+        if block:
+            for c0 in range(0, Z.shape[0], DCG_MAX_RHS):
+                Uc, inf = solver.solve_multi(Z[c0:c0 + DCG_MAX_RHS].contiguous())
+                U[c0:c0 + Uc.shape[0]] = Uc.to(torch.float32)
+                infos += inf
+        else:
+            for p in range(Z.shape[0]):
+                u, info = solver.solve(Z[p].contiguous())
+                U[p] = u.to(torch.float32)
+                infos.append(info)
         solver.last_probe_infos = infos
         ctx.solver = solver
         ctx.params = params
@@ -96,17 +105,17 @@ class LogDetProbes(torch.autograd.Function):
         solver.set_rbf_params(*ctx.params)
         forms = solver.rbf_dtheta(U.contiguous(), Z.to(torch.float32).contiguous())
         grad = 0.5 * forms.mean(axis=0)
-        return g * torch.tensor(grad, dtype=ctx.theta_dtype, device=ctx.theta_device), None, None
+        return g * torch.tensor(grad, dtype=ctx.theta_dtype, device=ctx.theta_device), None, None, None
 
 
 def gp_objective(theta: torch.Tensor, y: torch.Tensor, solver: DefCG, Z: torch.Tensor | None = None,
-                 recycle: bool = True) -> torch.Tensor:
+                 recycle: bool = True, block_probes: bool = True) -> torch.Tensor:
     """1/2 y^T A(theta)^{-1} y (+ LogDetProbes when probes Z are given)."""
     x = DefCGSolve.apply(theta, y, solver, recycle)
     fit = 0.5 * torch.dot(y.detach().to(torch.float64), x)
     if Z is None:
         return fit
-    return fit + LogDetProbes.apply(theta, solver, Z).to(fit.device)
+    return fit + LogDetProbes.apply(theta, solver, Z, block_probes).to(fit.device)
 
 
 def rademacher_probes(n: int, count: int, seed: int, device="cuda") -> torch.Tensor:
@@ -118,11 +127,12 @@ def rademacher_probes(n: int, count: int, seed: int, device="cuda") -> torch.Ten
 
 
 def fit_gp(solver: DefCG, y: torch.Tensor, theta0, steps: int = 30, lr: float = 0.05, probes=16,
-           probe_seed: int = 1000):
+           probe_seed: int = 1000, block_probes: bool = True):
     """Adam on phi = log(theta) with the gp_objective gradient.
 
     ``probes`` is a probe count (Rademacher rows from ``rademacher_probes``
-    with seed probe_seed + step) or a callable step -> (P, n) tensor. Returns
+    with seed probe_seed + step) or a callable step -> (P, n) tensor;
+    ``block_probes`` solves them in lockstep (see LogDetProbes). Returns
     (list of theta after each step, list of dL/dtheta per step).
     """
     phi = torch.tensor(np.log(np.asarray(theta0, dtype=np.float64)), dtype=torch.float64, requires_grad=True)
@@ -137,7 +147,7 @@ def fit_gp(solver: DefCG, y: torch.Tensor, theta0, steps: int = 30, lr: float = 
             Z = None
         opt.zero_grad()
         theta = phi.exp()
-        loss = gp_objective(theta, y, solver, Z)
+        loss = gp_objective(theta, y, solver, Z, block_probes=block_probes)
         loss.backward()
         grads.append((phi.grad.detach().numpy() / np.exp(phi.detach().numpy())).copy())
         opt.step()

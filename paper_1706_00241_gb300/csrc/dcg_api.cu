@@ -114,6 +114,7 @@ struct dcg_ctx {
   double* mr_small = nullptr;  // mr_cap x 4 kk: h, hp, mu, gamma
   float* mr_small_f = nullptr; // mr_cap x 2 kk: mu_f, gamma_f
   float *mr_P = nullptr, *mr_Q = nullptr;  // gathered directions and their products, mr_ld x (mr_cap rounded up to 8)
+  float* mr_resid_part = nullptr;  // matrix-free residuals of EX_NL systems per pass: EX_NL x 3 x splits x n
   DevState* mr_st = nullptr;   // mr_cap + 1 states; the last records timeouts of the shared kernels
   DevState* mr_hst = nullptr;  // pinned copies
 
@@ -1031,6 +1032,7 @@ static dcg_status mr_reserve(dcg_ctx* c, int cap) {
   CK(mr_alloc(c, &c->mr_small_f, ncap * 2 * kk));
   CK(mr_alloc(c, &c->mr_P, cap8 * np));
   CK(mr_alloc(c, &c->mr_Q, cap8 * np));
+  CK(mr_alloc(c, &c->mr_resid_part, size_t(EX_NL) * 3 * size_t(rbf_resid_splits(c->w.n, c->num_sms)) * n));
   CK(mr_alloc(c, &c->mr_st, ncap + 1));
   CK(cudaMallocHost(&c->mr_hst, sizeof(DevState) * (ncap + 1)));
   c->mr_vs = vs;
@@ -1063,6 +1065,50 @@ static Ws mr_lane_ws(const dcg_ctx* c, int j) {
   w.gamma_f = w.mu_f + kk;
   w.st = c->mr_st + j;
   return w;
+}
+
+// r = b - A x for the systems js of a lockstep solve (mode, skip_if_done as
+// in op_resid). The matrix-free operator forms each exact-form entry once per
+// EX_NL systems (k_rbf_resid_multi), then finishes each system on its own;
+// the stored operator takes one compensated residual per system.
+static cudaError_t op_resid_lanes(dcg_ctx* c, const std::vector<Ws>& w, const std::vector<int>& js, int mode,
+                                  int skip_if_done, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (c->op != OP_RBF || js.size() == 1) {
+    for (int j : js)
+      if ((e = op_resid_w(c, w[j], mode, skip_if_done, s)) != cudaSuccess) return e;
+    return e;
+  }
+  const int n = c->w.n, splits = c->resid_splits;
+  for (int j : js)
+    if ((e = launch_split_x(w[j], c->grid_iter, skip_if_done, s)) != cudaSuccess) return e;
+  for (size_t g0 = 0; g0 < js.size(); g0 += EX_NL) {
+    RbfResidMultiArgs m{};
+    m.base = rbf_resid_args(c);
+    m.nl = int(std::min(js.size() - g0, size_t(EX_NL)));
+    for (int l = 0; l < m.nl; ++l) {
+      const Ws& wj = w[js[g0 + l]];
+      m.xh[l] = wj.xh;
+      m.xl[l] = wj.xl;
+      m.part[l] = c->mr_resid_part + size_t(l) * 3 * splits * n;
+    }
+    if ((e = launch_rbf_resid_multi(m, splits, s)) != cudaSuccess) return e;
+    for (int l = 0; l < m.nl; ++l) {
+      const Ws& wj = w[js[g0 + l]];
+      RbfExactArgs a = rbf_resid_args(c);
+      a.partials_f = m.part[l];
+      a.xh = wj.xh;
+      a.xl = wj.xl;
+      a.b = wj.b;
+      a.r = wj.r;
+      a.ticket = &wj.st->ticket[T_CHECK_RES];
+      a.st = wj.st;
+      a.skip_if_done = skip_if_done;
+      a.resid_mode = mode;
+      if ((e = launch_rbf_resid_fin(a, splits, s)) != cudaSuccess) return e;
+    }
+  }
+  return e;
 }
 
 // Q[:, j] = A P[:, j] for the na gathered directions (leading dimension ld):
@@ -1147,23 +1193,29 @@ extern "C" dcg_status dcg_solve_multi(dcg_ctx* c, int nrhs, const float* B, doub
   std::vector<char> hit(nrhs, shared_status != DCG_OK ? 1 : 0);  // systems a shared failure ended
   if (shared_status == DCG_OK) {
     // per system: r_{-1}, the initial projection and the first direction
+    std::vector<int> js;
+    if (c->cfg.warm_start) {
+      for (int j = 0; j < nrhs; ++j) js.push_back(j);
+      CK(op_resid_lanes(c, w, js, 0, 1, s));
+    }
     for (int j = 0; j < nrhs; ++j) {
-      if (c->cfg.warm_start) CK(op_resid_w(c, w[j], 0, 1, s));
       CK(launch_setup_r(w[j], c->grid_iter, s));
       CK(launch_check_dots(w[j], c->grid_iter, s));
       CK(launch_check_update(w[j], c->grid_iter, 0, 1, h0, s));
       CK(launch_phase2_setup(w[j], c->grid_iter, s));
     }
     CK(read_states());
-    bool again = false;
-    for (int j = 0; j < nrhs; ++j) {
-      if (hs[j].mode != 1) continue;
-      CK(op_resid_w(c, w[j], -1, 1, s));
-      CK(launch_check_dots(w[j], c->grid_iter, s));
-      CK(launch_check_update(w[j], c->grid_iter, 1, 0, h0, s));
-      again = true;
+    js.clear();
+    for (int j = 0; j < nrhs; ++j)
+      if (hs[j].mode == 1) js.push_back(j);
+    if (!js.empty()) {
+      CK(op_resid_lanes(c, w, js, -1, 1, s));
+      for (int j : js) {
+        CK(launch_check_dots(w[j], c->grid_iter, s));
+        CK(launch_check_update(w[j], c->grid_iter, 1, 0, h0, s));
+      }
+      CK(read_states());
     }
-    if (again) CK(read_states());
     MultiLanes lanes{};
     for (;;) {
       if (hs[sh].status != DCG_OK) {  // a wait of the shared block product gave up
@@ -1184,22 +1236,28 @@ extern "C" dcg_status dcg_solve_multi(dcg_ctx* c, int nrhs, const float* B, doub
         CK(launch_iter_fused(wj, c->num_sms, h0, s));
       }
       CK(read_states());
-      bool chk = false;
+      // the systems whose check or replacement is due: their true residuals
+      // in shared passes, then each one's check branch
+      js.clear();
       for (int a = 0; a < na; ++a) {
         const int j = lanes.idx[a];
-        if (hs[j].mode == 0 || hs[j].done) continue;
-        CK(op_resid_w(c, w[j], -1, 1, s));
-        CK(launch_check_dots(w[j], c->grid_iter, s));
-        CK(launch_check_update(w[j], c->grid_iter, 0, 0, h0, s));
-        CK(launch_phase2(w[j], c->grid_iter, h0, s));
-        chk = true;
+        if (hs[j].mode != 0 && !hs[j].done) js.push_back(j);
       }
-      if (chk) CK(read_states());
+      if (!js.empty()) {
+        CK(op_resid_lanes(c, w, js, -1, 1, s));
+        for (int j : js) {
+          CK(launch_check_dots(w[j], c->grid_iter, s));
+          CK(launch_check_update(w[j], c->grid_iter, 0, 0, h0, s));
+          CK(launch_phase2(w[j], c->grid_iter, h0, s));
+        }
+        CK(read_states());
+      }
     }
-    for (int j = 0; j < nrhs; ++j) {
-      if (shared_status == DCG_OK && !hs[j].true_valid && !hs[j].zero_rhs) CK(op_resid_w(c, w[j], 3, 0, s));
-      CK(launch_finalize(w[j], c->grid_iter, s));
-    }
+    js.clear();
+    for (int j = 0; j < nrhs; ++j)
+      if (shared_status == DCG_OK && !hs[j].true_valid && !hs[j].zero_rhs) js.push_back(j);
+    if (!js.empty()) CK(op_resid_lanes(c, w, js, 3, 0, s));
+    for (int j = 0; j < nrhs; ++j) CK(launch_finalize(w[j], c->grid_iter, s));
   }
   CK(cudaEventRecord(c->ev1, s));
   for (int j = 0; j < nrhs; ++j)

@@ -239,6 +239,21 @@ cudaError_t launch_copy_cols(const float* src, float* dst, int n, int64_t ldd, i
 cudaError_t launch_rbf_mv_block(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s);
 int rbf_block_nc();
 cudaError_t launch_rbf_resid(const RbfExactArgs& a, int splits, cudaStream_t s);
+// Residual sums of up to EX_NL systems in one pass over the exact-form
+// entries (k_rbf_resid_multi): base carries the operator (points, norms,
+// parameters); system l reads x = xh[l] + xl[l] and writes its per-split
+// partials to part[l] (3 x splits x n floats), which launch_rbf_resid_fin
+// (with a.partials_f = part[l] and the system's b, r, state) turns into r.
+constexpr int EX_NL = 8;
+struct RbfResidMultiArgs {
+  RbfExactArgs base;
+  int nl;
+  const float* xh[EX_NL];
+  const float* xl[EX_NL];
+  float* part[EX_NL];
+};
+cudaError_t launch_rbf_resid_multi(const RbfResidMultiArgs& m, int splits, cudaStream_t s);
+cudaError_t launch_rbf_resid_fin(const RbfExactArgs& a, int splits, cudaStream_t s);
 cudaError_t launch_rbf_block(const RbfExactArgs& a, int cmax, cudaStream_t s);
 
 // ---- dense operator (k_dense.cu)

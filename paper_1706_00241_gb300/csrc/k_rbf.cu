@@ -1563,6 +1563,150 @@ cudaError_t launch_rbf_resid(const RbfExactArgs& a, int splits, cudaStream_t s) 
   return cudaGetLastError();
 }
 
+// Residuals of several systems in one pass over the exact-form entries (the
+// checks of a lockstep multi-right-hand-side solve): each entry K_ij is formed
+// once, as in k_rbf_resid, and contracted with the iterates of up to EX_NL
+// systems, each with its own Dot2 pair, entry-error sum and per-split
+// partials; k_rbf_resid_fin then finishes each system on its own. The entry
+// costs ~65 float32 instructions at d = 8 and each system ~13 more, so eight
+// systems take about a third of eight separate passes.
+__host__ __device__ constexpr int ex_resid_multi_min_blocks(int dmax) {
+  return dmax <= 8 ? 4 : (dmax <= 16 ? 3 : (dmax <= 32 ? 2 : 1));
+}
+
+template <int DMAX>
+__global__ void __launch_bounds__(EX_ROWS, ex_resid_multi_min_blocks(DMAX)) k_rbf_resid_multi(RbfResidMultiArgs m) {
+  __shared__ __align__(16) float xs[DMAX][EX_J];
+  __shared__ __align__(16) float sh_xh[EX_NL][EX_J], sh_xl[EX_NL][EX_J];
+  __shared__ __align__(16) float sh_nh[EX_J], sh_nl[EX_J];
+  __shared__ float2 exp_tab[64];
+  if (threadIdx.x < 64) {
+    const double t = exp2(double(threadIdx.x) / 64.0);
+    exp_tab[threadIdx.x] = make_float2(float(t), float(t - double(float(t))));
+  }
+  const RbfExactArgs& a = m.base;
+  const int nl = m.nl;
+  const int n = a.n, d = a.d, n_pad = a.n_pad;
+  const int i = blockIdx.x * EX_ROWS + threadIdx.x;
+  const float k_hi = a.prm->neg_inv2l2, k_lo = a.prm->neg_inv2l2_lo;
+  const float s2 = a.prm->s2, s2_lo = a.prm->s2_lo;
+  const float sigma = a.prm->sigma_anchor;
+  const float err0 = kEntryErrC0 + a.prm->err_dist;
+  float xi[DMAX];
+#pragma unroll
+  for (int mm = 0; mm < DMAX; ++mm) xi[mm] = (i < n && mm < d) ? a.XrT[int64_t(mm) * n_pad + i] : 0.f;
+  const float nh_i = a.nh[min(i, n_pad - 1)], nl_i = a.nl[min(i, n_pad - 1)];
+  float acc[EX_NL], cmp[EX_NL], esq[EX_NL];
+#pragma unroll
+  for (int l = 0; l < EX_NL; ++l) acc[l] = cmp[l] = esq[l] = 0.f;
+  const int ntiles = (n + EX_J - 1) / EX_J;
+  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+    const int j0 = tile * EX_J;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < d * (EX_J / 4); idx += EX_ROWS) {
+      const int mm = idx / (EX_J / 4), q = idx % (EX_J / 4);
+      *reinterpret_cast<float4*>(&xs[mm][4 * q]) =
+          *reinterpret_cast<const float4*>(a.XrT + int64_t(mm) * n_pad + j0 + 4 * q);
+    }
+    if (threadIdx.x < EX_J) {
+      const int j = j0 + threadIdx.x;
+      const bool in = j < n;
+#pragma unroll
+      for (int l = 0; l < EX_NL; ++l) {
+        if (l < nl) {
+          sh_xh[l][threadIdx.x] = in ? m.xh[l][j] : 0.f;
+          sh_xl[l][threadIdx.x] = in ? m.xl[l][j] : 0.f;
+        }
+      }
+      sh_nh[threadIdx.x] = a.nh[j];  // j < n_pad: zero beyond n
+      sh_nl[threadIdx.x] = a.nl[j];
+    }
+    __syncthreads();
+    const int jn = min(EX_J, n - j0);
+    for (int jq = 0; jq < jn; jq += 4) {
+      unsigned long long T01 = tc::f2pk(sigma, sigma), T23 = T01, L01 = 0ull, L23 = 0ull;
+#pragma unroll
+      for (int mm = 0; mm < DMAX; ++mm) {
+        if (mm < d) {
+          const float4 x4 = *reinterpret_cast<const float4*>(&xs[mm][jq]);
+          const unsigned long long xx = tc::f2pk(xi[mm], xi[mm]);
+          anchored_step2(T01, L01, xx, tc::f2pk(x4.x, x4.y));
+          anchored_step2(T23, L23, xx, tc::f2pk(x4.z, x4.w));
+        }
+      }
+      const float Tv[4] = {__uint_as_float(unsigned(T01)), __uint_as_float(unsigned(T01 >> 32)),
+                           __uint_as_float(unsigned(T23)), __uint_as_float(unsigned(T23 >> 32))};
+      const float Lv[4] = {__uint_as_float(unsigned(L01)), __uint_as_float(unsigned(L01 >> 32)),
+                           __uint_as_float(unsigned(L23)), __uint_as_float(unsigned(L23 >> 32))};
+#pragma unroll
+      for (int e4 = 0; e4 < 4; ++e4) {
+        const int jj = jq + e4;
+        if (jj >= jn) break;
+        const float ghi = __fsub_rn(Tv[e4], sigma);
+        const float dh = __fmaf_rn(-2.f, ghi, __fadd_rn(nh_i, sh_nh[jj]));
+        const float dl = __fmaf_rn(-2.f, Lv[e4], __fadd_rn(nl_i, sh_nl[jj]));
+        const float a_hi = __fmul_rn(dh, k_hi);
+        const float a_lo = __fmaf_rn(dh, k_hi, -a_hi) + dl * k_hi + dh * k_lo;
+        if (a_hi < kExpMinArg) continue;
+        float e_hi, e_lo;
+        int k2;
+        exp_tang(a_hi, a_lo, exp_tab, e_hi, e_lo, k2);
+        const float m_hi = __fmul_rn(s2, e_hi);
+        const float m_lo = __fmaf_rn(s2, e_hi, -m_hi) + __fmaf_rn(s2, e_lo, s2_lo * e_hi);
+        const float scale = __int_as_float((k2 + 127) << 23);
+        const float kv_hi = __fmul_rn(m_hi, scale), kv_lo = __fmul_rn(m_lo, scale);
+        const float fac = fmaf(3.f, fabsf(a_hi), err0);
+#pragma unroll
+        for (int l = 0; l < EX_NL; ++l) {
+          if (l < nl) {
+            const float xhv = sh_xh[l][jj];
+            const float p = __fmul_rn(kv_hi, xhv);
+            const float pe = __fmaf_rn(kv_hi, xhv, -p);
+            two_sum_add(acc[l], cmp[l], p);
+            cmp[l] = __fadd_rn(cmp[l], pe);
+            cmp[l] = __fmaf_rn(kv_hi, sh_xl[l][jj], __fmaf_rn(kv_lo, xhv, cmp[l]));
+            const float e_ij = fac * p;
+            esq[l] = fmaf(e_ij, e_ij, esq[l]);
+          }
+        }
+      }
+    }
+  }
+  if (i < n) {
+#pragma unroll
+    for (int l = 0; l < EX_NL; ++l) {
+      if (l < nl) {
+        float* part = m.part[l] + int64_t(blockIdx.y) * 3 * n;
+        part[i] = acc[l];
+        part[n + i] = cmp[l];
+        part[2 * n + i] = esq[l];
+      }
+    }
+  }
+}
+
+cudaError_t launch_rbf_resid_multi(const RbfResidMultiArgs& m, int splits, cudaStream_t s) {
+  const RbfExactArgs& a = m.base;
+  if (splits < 1 || splits > EX_MAX_SPLITS || a.d < 1 || a.d > EX_MAXD || m.nl < 1 || m.nl > EX_NL)
+    return cudaErrorInvalidValue;
+  const dim3 grid(rbf_exact_grid(a.n), splits);
+  if (a.d <= 8)
+    k_rbf_resid_multi<8><<<grid, EX_ROWS, 0, s>>>(m);
+  else if (a.d <= 16)
+    k_rbf_resid_multi<16><<<grid, EX_ROWS, 0, s>>>(m);
+  else if (a.d <= 32)
+    k_rbf_resid_multi<32><<<grid, EX_ROWS, 0, s>>>(m);
+  else
+    k_rbf_resid_multi<64><<<grid, EX_ROWS, 0, s>>>(m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rbf_resid_fin(const RbfExactArgs& a, int splits, cudaStream_t s) {
+  if (splits < 1 || splits > EX_MAX_SPLITS) return cudaErrorInvalidValue;
+  k_rbf_resid_fin<<<rbf_exact_grid(a.n), EX_ROWS, 0, s>>>(a, splits);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rbf_block(const RbfExactArgs& a, int cmax, cudaStream_t s) {
   if (cmax <= 0) return cudaSuccess;
   dim3 grid(rbf_exact_grid(a.n), (cmax + EX_CB - 1) / EX_CB);

@@ -124,3 +124,22 @@ def test_adam_path_matches_oracle(dcg):
     ref = G.adam_path(lambda t, th: G.gp_nll_grad_probes(Xr, y64, *th, probes[t]), np.log(THETA), steps, lr=0.05)
     for t in range(steps + 1):
         assert np.allclose(np.log(path[t]), ref[t], rtol=0, atol=1e-6), (t, np.log(path[t]), ref[t])
+
+
+def test_lockstep_probes_match_one_by_one(dcg):
+    # The probe solves of the log-determinant term in lockstep (one operator
+    # pass per iteration for all of them) and one after another are the same
+    # solves up to the rounding of the block product: the probe gradients
+    # agree to the solves' accuracy (tol 1e-9, kappa ~ 3e3: ~3e-6 relative
+    # in each u_p, averaged over the probes).
+    n, P = 1500, 12
+    cfg, X, Xr, y = _grad_problem(n)
+    Zd = dev(S.rademacher(n, P, seed=7).T)
+    grads = []
+    for block in (True, False):
+        with _solver(dcg, cfg, X, n) as s:
+            th = torch.tensor(THETA, dtype=torch.float64, requires_grad=True)
+            dcg.gp_objective(th, dev(y), s, Zd, block_probes=block).backward()
+            assert len(s.last_probe_infos) == P and all(i["status"] == 0 for i in s.last_probe_infos)
+            grads.append(th.grad.numpy().copy())
+    assert np.all(np.abs(grads[0] - grads[1]) <= 1e-5 * np.abs(grads[1])), grads
