@@ -115,6 +115,10 @@ struct dcg_ctx {
   float* mr_small_f = nullptr; // mr_cap x 2 kk: mu_f, gamma_f
   float *mr_P = nullptr, *mr_Q = nullptr;  // gathered directions and their products, mr_ld x (mr_cap rounded up to 8)
   float* mr_resid_part = nullptr;  // matrix-free residuals of EX_NL systems per pass: EX_NL x 3 x splits x n
+  uint16_t* mr_phl = nullptr;  // float16 parts of the gathered directions (rbf_p16_halfs(n_pad))
+  float* mr_pscale = nullptr;  // their power-of-two column scales (32)
+  CUtensorMap mr_pmaps[2];     // maps of mr_phl for 16 and 32 columns
+  bool mr_tc = false;          // the maps are valid: the block product contracts on the tensor cores
   DevState* mr_st = nullptr;   // mr_cap + 1 states; the last records timeouts of the shared kernels
   DevState* mr_hst = nullptr;  // pinned copies
 
@@ -290,6 +294,7 @@ extern "C" dcg_status dcg_create(const dcg_config* cfg, void* stream, dcg_ctx** 
   CKC(iter_configure());
   CKC(rbf_mv_configure());
   CKC(rbf_mv_sym_configure());
+  CKC(rbf_mv_tc_configure());
   CKC(chol_configure(96));
   CKC(ritz_configure());
 
@@ -1033,8 +1038,15 @@ static dcg_status mr_reserve(dcg_ctx* c, int cap) {
   CK(mr_alloc(c, &c->mr_P, cap8 * np));
   CK(mr_alloc(c, &c->mr_Q, cap8 * np));
   CK(mr_alloc(c, &c->mr_resid_part, size_t(EX_NL) * 3 * size_t(rbf_resid_splits(c->w.n, c->num_sms)) * n));
+  CK(mr_alloc(c, &c->mr_phl, rbf_p16_halfs(c->n_pad)));
+  CK(mr_alloc(c, &c->mr_pscale, size_t(DCG_MAX_RHS)));
   CK(mr_alloc(c, &c->mr_st, ncap + 1));
   CK(cudaMallocHost(&c->mr_hst, sizeof(DevState) * (ncap + 1)));
+  {
+    EncodeTiledFn enc = get_encode();
+    c->mr_tc = enc && make_rbf_p16_tmap(&c->mr_pmaps[0], c->mr_phl, c->n_pad, 16, enc) &&
+               make_rbf_p16_tmap(&c->mr_pmaps[1], c->mr_phl, c->n_pad, 32, enc);
+  }
   c->mr_vs = vs;
   c->mr_cap = cap;
   return DCG_OK;
@@ -1113,11 +1125,31 @@ static cudaError_t op_resid_lanes(dcg_ctx* c, const std::vector<Ws>& w, const st
 
 // Q[:, j] = A P[:, j] for the na gathered directions (leading dimension ld):
 // the operator pass the systems of a lockstep solve share. The matrix-free
-// operator applies the loop's tensor-core entries, each exponential formed
-// once per pass of rbf_block_nc() columns; a bounded wait that gives up
-// records a timeout in the shared state (the last of mr_st).
+// operator forms the loop's tensor-core entries once for all na <= 32
+// columns and contracts them on the tensor cores (k_rbf_mv_tc; k_rbf_mv<8>
+// passes if its float16 maps could not be made); a bounded wait that gives
+// up records a timeout in the shared state (the last of mr_st).
 static cudaError_t op_multi(dcg_ctx* c, int na, int64_t ld, cudaStream_t s) {
   DevState* tst = c->mr_st + c->mr_cap;
+  if (c->op == OP_RBF && c->mr_tc) {
+    // one pass for all na <= 32 columns, the contraction on the tensor cores
+    RbfMvArgs a{};
+    a.p = c->mr_P;
+    a.ldp = ld;
+    a.vcol = c->vcol;
+    a.q = c->mr_Q;
+    a.ldq = ld;
+    a.ncols = na;
+    a.n = c->w.n;
+    a.n_tiles = c->n_pad / 128;
+    a.d = c->rbf_d;
+    a.xformat = c->rbf_xformat;
+    a.prm = c->prm;
+    a.st = tst;
+    a.skip_if_done = 0;
+    a.col_idx = -1;
+    return launch_rbf_mv_tc(c->rbf_tmap, c->mr_pmaps, a, c->mr_phl, c->mr_pscale, c->rbf_grid, s);
+  }
   if (c->op == OP_RBF) {
     const int nc = rbf_block_nc();
     for (int j0 = 0; j0 < na; j0 += nc) {

@@ -237,6 +237,14 @@ int rbf_exact_grid(int n);
 cudaError_t launch_copy_cols(const float* src, float* dst, int n, int64_t ldd, int col0, int nc, const DevState* st,
                              cudaStream_t s);
 cudaError_t launch_rbf_mv_block(const CUtensorMap* tmap, const RbfMvArgs& a, int grid, cudaStream_t s);
+// Q = A P for up to 32 columns with the contraction on the tensor cores
+// (k_rbf_p16 + k_rbf_mv_tc): PHL holds rbf_p16_halfs(n_pad) float16, pmaps[0],
+// [1] its maps for 16 and 32 columns (make_rbf_p16_tmap), pscale 32 floats.
+cudaError_t rbf_mv_tc_configure();
+bool make_rbf_p16_tmap(CUtensorMap* map, const void* PHL, int n_pad, int ncp, EncodeTiledFn encode);
+size_t rbf_p16_halfs(int n_pad);
+cudaError_t launch_rbf_mv_tc(const CUtensorMap* tmap, const CUtensorMap* pmaps, const RbfMvArgs& a, void* PHL,
+                             float* pscale, int grid, cudaStream_t s);
 int rbf_block_nc();
 cudaError_t launch_rbf_resid(const RbfExactArgs& a, int splits, cudaStream_t s);
 // Residual sums of up to EX_NL systems in one pass over the exact-form

@@ -24,6 +24,7 @@
 //     TF32 operands); the residual recomputation in the exact form is the
 //     refinement that wins the accuracy back.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "dcg_kernels.cuh"
 #include "tc.cuh"
@@ -436,26 +437,30 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[b]);
         {
+          // the entries, once, as packed pairs (j, j + 1); then per column two
+          // packed sums (pairs 0, 2 mod 4 and 1, 3 mod 4): one FMA
+          // instruction per two entries
+          const unsigned long long c2x2 = tc::f2pk(c2, c2), uu = tc::f2pk(u, u);
+          unsigned long long e2[16];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) sv[j] = tc::ex2_approx(fmaf(c2, sv[j], u));  // the entries, once
+          for (int j = 0; j < 32; j += 2) {
+            const unsigned long long g = tc::f2fma(c2x2, tc::f2pk(sv[j], sv[j + 1]), uu);
+            e2[j / 2] = tc::f2pk(tc::ex2_approx(tc::f2lo(g)), tc::ex2_approx(tc::f2hi(g)));
+          }
 #pragma unroll
           for (int c = 0; c < NC; ++c) {  // contracted with every column
             const float* pc = pj + c * MV_TILE;
-            float s0 = 0.f, s1 = 0.f;
+            unsigned long long s0 = 0ull, s1 = 0ull;
 #pragma unroll
             for (int j = 0; j < 32; j += 8) {
               const float4 pa4 = *reinterpret_cast<const float4*>(pc + j);
               const float4 pb4 = *reinterpret_cast<const float4*>(pc + j + 4);
-              s0 = fmaf(sv[j + 0], pa4.x, s0);
-              s1 = fmaf(sv[j + 1], pa4.y, s1);
-              s0 = fmaf(sv[j + 2], pa4.z, s0);
-              s1 = fmaf(sv[j + 3], pa4.w, s1);
-              s0 = fmaf(sv[j + 4], pb4.x, s0);
-              s1 = fmaf(sv[j + 5], pb4.y, s1);
-              s0 = fmaf(sv[j + 6], pb4.z, s0);
-              s1 = fmaf(sv[j + 7], pb4.w, s1);
+              s0 = tc::f2fma(e2[j / 2 + 0], tc::f2pk(pa4.x, pa4.y), s0);
+              s1 = tc::f2fma(e2[j / 2 + 1], tc::f2pk(pa4.z, pa4.w), s1);
+              s0 = tc::f2fma(e2[j / 2 + 2], tc::f2pk(pb4.x, pb4.y), s0);
+              s1 = tc::f2fma(e2[j / 2 + 3], tc::f2pk(pb4.z, pb4.w), s1);
             }
-            const float y = (s0 + s1) - comp[c];
+            const float y = ((tc::f2lo(s0) + tc::f2hi(s0)) + (tc::f2lo(s1) + tc::f2hi(s1))) - comp[c];
             const float t = acc[c] + y;
             comp[c] = (t - acc[c]) - y;
             acc[c] = t;
@@ -467,7 +472,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
       }
       if (aborted) break;
       // combine the four column slices of each row (named barrier: epilogue warps)
-#pragma unroll 1
+#pragma unroll
       for (int c = 0; c < NC; ++c) {
         if (slice > 0) s_slice[slice - 1][row_l] = acc[c];
         asm volatile("bar.sync 1, %0;" ::"r"(MV_EPI_WARPS * 32));
@@ -516,6 +521,426 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
     s = warp_sum(s);
     if (lane == 0 && a.result) *a.result = s;
   }
+}
+
+
+// ---------------------------------------------------------------------------
+// Block product Q = A P for up to 32 columns with the contraction on the
+// tensor cores (k_rbf_mv_tc): the systems of a lockstep solve share one pass
+// over the kernel entries per iteration. k_rbf_mv<8> contracts the entries
+// with the columns of P on the FP32 pipe, where every p_j reaches the 32 rows
+// of a warp as a shared-memory broadcast (one wavefront per float per warp,
+// 4096 per 128 x 128 tile for 8 columns: the pass is bound by the shared
+// memory pipe). Here the entries go to shared memory once and a second MMA
+// contracts them with all columns:
+//   MMA 1  S~ = X_I X_J^T (as in k_rbf_mv) into one of three TMEM buffers;
+//   epilogue  E_ij = exp2(c2 S~_ij + u'_i) = K_ij / s^2 (in [0, 1]), split
+//          E = E_hi + E_lo into two float16 parts (E_hi = fp16(E) rounded to
+//          nearest, E_lo = fp16(E - E_hi); E - E_hi is exact in float32) and
+//          stored as the A operand (K-major, 128-byte swizzle, two 64-column
+//          halves per part);
+//   MMA 2  D += E_hi P_hi + E_hi P_lo + E_lo P_hi over the 128 columns of the
+//          tile (K = 16 per MMA, 24 MMAs), D (128 x NCP float32) in one of two
+//          TMEM buffers; P = P_hi + P_lo is each column of P scaled by a power
+//          of two sigma_c (max |p| sigma_c in [1/2, 1)) and split like E
+//          (k_rbf_p16, once per pass);
+//   flush  each epilogue warp reads its NCP / 4 columns of D one tile behind
+//          and adds them into float32 registers (Kahan), so the tensor core
+//          accumulates one tile (8 K steps) at a time;
+//   end    q_c = s^2 / sigma_c (D sum) + noise p_c per row.
+// The dropped E_lo P_lo term and the float16 roundings of the parts leave
+// ~2^-22 relative per product plus 2^-25 absolute (E_lo below the float16
+// normal range), far inside the BF16 and TF32 tiles' own entry errors.
+// ---------------------------------------------------------------------------
+constexpr int TC_SBUF = 3;                    // TMEM buffers of S~
+constexpr int TC_STAGES = 4;
+constexpr int TC_MAXC = 32;                   // columns per pass (NCP = 16 or 32)
+constexpr int TC_E_PART = 2 * MV_TILE * 128;  // one part of E: two halves of 128 rows x 128 bytes = 32 KB
+__host__ __device__ constexpr int tc_stage_bytes(int ncp) { return MV_TILE_BYTES + 4 * ncp * 128; }
+__host__ __device__ constexpr size_t tc_smem(int ncp) {
+  return 1024 + MV_TILE_BYTES + size_t(TC_STAGES) * tc_stage_bytes(ncp) + 2 * size_t(TC_E_PART) + 256;
+}
+
+namespace tc {
+// 32 lanes x 4 / 8 consecutive 32-bit columns (lane l: row lane base + l).
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+constexpr uint32_t kFmtF16 = 0;  // A / B format code of kind::f16 for float16
+}  // namespace tc
+
+// P (ncols columns of length n_pad, leading dimension ldp, zero beyond n) to
+// the float16 parts of the contraction's B operand: rows c of PHL hold
+// fp16(sigma_c p_c), rows TC_MAXC + c fp16(sigma_c p_c - that), rows of
+// columns >= ncols zero; sigma_c = 2^-e with max_j |p_cj| = f 2^e, f in
+// [1/2, 1) (1 for a zero column), into pscale[c]. One CTA per column.
+__global__ void __launch_bounds__(1024) k_rbf_p16(const float* __restrict__ P, int64_t ldp, int ncols, int n_pad,
+                                                  __half* __restrict__ PHL, float* __restrict__ pscale) {
+  __shared__ float red[32];
+  const int c = blockIdx.x;
+  __half* hi = PHL + int64_t(c) * n_pad;
+  __half* lo = PHL + int64_t(TC_MAXC + c) * n_pad;
+  if (c >= ncols) {
+    for (int j = threadIdx.x; j < n_pad; j += blockDim.x) hi[j] = lo[j] = __float2half_rn(0.f);
+    if (threadIdx.x == 0) pscale[c] = 1.f;
+    return;
+  }
+  const float* p = P + int64_t(c) * ldp;
+  float m = 0.f;
+  for (int j = threadIdx.x; j < n_pad; j += blockDim.x) m = fmaxf(m, fabsf(p[j]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < int(blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) {
+      int e = 0;
+      if (v > 0.f && isfinite(v)) frexpf(v, &e);
+      red[0] = ldexpf(1.f, -e);
+    }
+  }
+  __syncthreads();
+  const float sigma = red[0];
+  for (int j = threadIdx.x; j < n_pad; j += blockDim.x) {
+    const float v = p[j] * sigma;  // exact: a power of two
+    const __half h = __float2half_rn(v);
+    hi[j] = h;
+    lo[j] = __float2half_rn(v - __half2float(h));
+  }
+  if (threadIdx.x == 0) pscale[c] = sigma;
+}
+
+// Roles as in k_rbf_mv: warp 0 TMA (X_I per row block; per tile X_J and the
+// four float16 boxes of P_J), warp 1 MMA issue (MMA 1 up to two tiles ahead of
+// MMA 2), warps 2..17 epilogue (TMEM lane quarter warp % 4, 32-column slice
+// (warp - 2) / 4; D columns slice * NCP / 4 .. + NCP / 4). Every wait is
+// bounded; a CTA that gives up records a timeout in a.st (site 3).
+template <int NCP>
+__global__ void __launch_bounds__(MV_THREADS, 1)
+    k_rbf_mv_tc(const __grid_constant__ CUtensorMap tmap_i, const __grid_constant__ CUtensorMap tmap_j,
+                const __grid_constant__ CUtensorMap tmap_p, RbfMvArgs a, const float* __restrict__ pscale) {
+  constexpr int SB = tc_stage_bytes(NCP);
+  constexpr int PB = NCP * 128;  // one box of P_J: NCP rows x 64 float16 (128 bytes)
+  constexpr int CPW = NCP / 4;   // D columns per epilogue warp
+  constexpr uint32_t D_COL = TC_SBUF * MV_TILE;  // TMEM column of the first D buffer (buffers 32 apart)
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* xi_tile = base;
+  unsigned char* stages = base + MV_TILE_BYTES;
+  unsigned char* e_tile = stages + size_t(TC_STAGES) * SB;  // E_hi halves 0, 1, then E_lo halves 0, 1
+  uint64_t* bars = reinterpret_cast<uint64_t*>(e_tile + 2 * TC_E_PART);
+  uint64_t* full = bars;                 // [TC_STAGES]
+  uint64_t* empty = full + TC_STAGES;    // [TC_STAGES] released by MMA 2 of the tile
+  uint64_t* tfull = empty + TC_STAGES;   // [TC_SBUF]
+  uint64_t* tempty = tfull + TC_SBUF;    // [TC_SBUF]
+  uint64_t* efull = tempty + TC_SBUF;    // E of the tile written
+  uint64_t* eempty = efull + 1;          // MMA 2 done with E
+  uint64_t* dfull = eempty + 1;          // [2]
+  uint64_t* dempty = dfull + 2;          // [2]
+  uint64_t* xi_full = dempty + 2;
+  uint64_t* xi_empty = xi_full + 1;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+
+  DevState* st = a.st;
+  if (st && a.skip_if_done && st->done) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = a.n, n_tiles = a.n_tiles;
+  const int nrb = int(blockIdx.x) < n_tiles ? (n_tiles - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
+  const long long T = (long long)nrb * n_tiles;  // tiles of this CTA
+  const int kind_tf32 = a.xformat != DCG_X_BF16;
+  const int dk = rbf_tile_coords(a.xformat, a.d) + kRbfAug;
+  const int ksteps = kind_tf32 ? (dk + 7) / 8 : (dk + 15) / 16;
+  const uint32_t row_bytes = uint32_t(rbf_row_bytes(a.xformat, dk));
+  const uint32_t tile_bytes = MV_TILE * row_bytes;
+  const uint32_t idesc1 = tc::instr_desc(kind_tf32 ? tc::kFmtTF32 : tc::kFmtBF16, MV_TILE, MV_TILE);
+  const uint32_t idesc2 = tc::instr_desc(tc::kFmtF16, MV_TILE, NCP);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < TC_SBUF; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], MV_EPI_WARPS);
+    }
+    mbar_init(efull, MV_EPI_WARPS);
+    mbar_init(eempty, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&dfull[b], 1);
+      mbar_init(&dempty[b], MV_EPI_WARPS);
+    }
+    mbar_init(xi_full, 1);
+    mbar_init(xi_empty, 1);
+    fence_mbarrier_init();
+    s_abort = 0;
+  }
+  if (warp == 1) tc::tmem_alloc(&s_tmem, MV_TMEM_COLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0) {
+    // -------------------------------- producer ------------------------------
+    if (lane == 0) {
+      prefetch_tensormap(&tmap_i);
+      prefetch_tensormap(&tmap_j);
+      prefetch_tensormap(&tmap_p);
+      long long t = 0;
+      for (int rbc = 0; rbc < nrb && !s_abort; ++rbc) {
+        const int rb = int(blockIdx.x) + rbc * int(gridDim.x);
+        if (rbc > 0 && !mbar_wait_bounded(xi_empty, uint32_t(rbc - 1) & 1)) { s_abort = 1; break; }
+        mbar_arrive_expect_tx(xi_full, tile_bytes);
+        tma_load_2d(xi_tile, &tmap_i, xi_full, 0, rb * MV_TILE);
+        bool stop = false;
+        for (int J = 0; J < n_tiles; ++J, ++t) {
+          const int s = int(t % TC_STAGES);
+          if (t >= TC_STAGES && !mbar_wait_bounded(&empty[s], uint32_t((t / TC_STAGES) - 1) & 1)) {
+            s_abort = 1;
+            stop = true;
+            break;
+          }
+          unsigned char* stg = stages + size_t(s) * SB;
+          mbar_arrive_expect_tx(&full[s], tile_bytes + 4 * PB);
+          tma_load_2d(stg, &tmap_j, &full[s], 0, J * MV_TILE);
+          tma_load_2d(stg + MV_TILE_BYTES, &tmap_p, &full[s], J * MV_TILE, 0);                    // P_hi j 0..63
+          tma_load_2d(stg + MV_TILE_BYTES + PB, &tmap_p, &full[s], J * MV_TILE + 64, 0);          // P_hi j 64..127
+          tma_load_2d(stg + MV_TILE_BYTES + 2 * PB, &tmap_p, &full[s], J * MV_TILE, TC_MAXC);     // P_lo j 0..63
+          tma_load_2d(stg + MV_TILE_BYTES + 3 * PB, &tmap_p, &full[s], J * MV_TILE + 64, TC_MAXC);
+        }
+        if (stop) break;
+      }
+    }
+  } else if (warp == 1) {
+    // -------------------------------- MMA issuer -----------------------------
+    if (lane == 0) {
+      const uint32_t a1 = smem_u32(xi_tile);
+      const uint32_t e_base = smem_u32(e_tile);
+      long long m1 = 0;  // next tile of MMA 1
+      for (long long u = 0; u < T; ++u) {
+        bool ok = true;
+        // MMA 1 (the Gram tile S~) up to TC_SBUF - 1 tiles ahead of MMA 2
+        while (ok && m1 < T && m1 <= u + TC_SBUF - 1) {
+          const int J = int(m1 % n_tiles), rbc = int(m1 / n_tiles);
+          const int s = int(m1 % TC_STAGES), b = int(m1 % TC_SBUF);
+          if ((J == 0 && !mbar_wait_bounded(xi_full, uint32_t(rbc) & 1)) ||
+              !mbar_wait_bounded(&full[s], uint32_t(m1 / TC_STAGES) & 1) ||
+              (m1 >= TC_SBUF && !mbar_wait_bounded(&tempty[b], uint32_t((m1 / TC_SBUF) - 1) & 1))) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t b1 = smem_u32(stages + size_t(s) * SB);
+          const uint32_t d1 = tmem + uint32_t(b * MV_TILE);
+          for (int kk = 0; kk < ksteps; ++kk) {
+            const uint64_t ad = tc::smem_desc_kmajor(a1 + 32 * kk, row_bytes);
+            const uint64_t bd = tc::smem_desc_kmajor(b1 + 32 * kk, row_bytes);
+            if (kind_tf32)
+              tc::mma_tf32(d1, ad, bd, idesc1, kk > 0);
+            else
+              tc::mma_bf16(d1, ad, bd, idesc1, kk > 0);
+          }
+          tc::mma_commit(&tfull[b]);
+          if (J == n_tiles - 1) tc::mma_commit(xi_empty);
+          ++m1;
+        }
+        if (!ok) { s_abort = 1; break; }
+        // MMA 2 of tile u: D = E_hi P_hi + E_hi P_lo + E_lo P_hi over its 128 columns
+        const int s = int(u % TC_STAGES), bd = int(u & 1);
+        if (!mbar_wait_bounded(efull, uint32_t(u & 1)) ||
+            (u >= 2 && !mbar_wait_bounded(&dempty[bd], uint32_t((u >> 1) - 1) & 1))) {
+          s_abort = 1;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t pb = smem_u32(stages + size_t(s) * SB + MV_TILE_BYTES);
+        const uint32_t d2 = tmem + D_COL + uint32_t(bd * 32);
+#pragma unroll 1
+        for (int kk = 0; kk < 8; ++kk) {
+          const uint32_t h = uint32_t(kk >> 2), ko = uint32_t(kk & 3) * 32;
+          const uint64_t eh = tc::smem_desc_kmajor(e_base + h * (MV_TILE * 128) + ko, 128);
+          const uint64_t el = tc::smem_desc_kmajor(e_base + TC_E_PART + h * (MV_TILE * 128) + ko, 128);
+          const uint64_t ph = tc::smem_desc_kmajor(pb + h * PB + ko, 128);
+          const uint64_t pl = tc::smem_desc_kmajor(pb + 2 * PB + h * PB + ko, 128);
+          tc::mma_bf16(d2, eh, ph, idesc2, kk > 0);  // kind::f16; the formats come from idesc2
+          tc::mma_bf16(d2, eh, pl, idesc2, 1);
+          tc::mma_bf16(d2, el, ph, idesc2, 1);
+        }
+        tc::mma_commit(&empty[s]);
+        tc::mma_commit(eempty);
+        tc::mma_commit(&dfull[bd]);
+      }
+    }
+  } else {
+    // -------------------------------- epilogue -------------------------------
+    const int ew = warp - 2;
+    const int quarter = warp & 3;
+    const int slice = ew >> 2;
+    const int row_l = quarter * 32 + lane;
+    const float c2 = a.prm->c2, s2 = a.prm->s2, noise = a.prm->noise;
+    const unsigned long long c2x2 = tc::f2pk(c2, c2);
+    const uint32_t lane_off = uint32_t(quarter * 32) << 16;
+    // this row's 128-byte line of E_hi in the half holding the slice's columns
+    // (E_lo TC_E_PART further); 16-byte chunk m of the slice lands at chunk
+    // ((slice & 1) * 4 + m) ^ (row & 7) (128-byte swizzle)
+    unsigned char* e_row = e_tile + (slice >> 1) * (MV_TILE * 128) + row_l * 128;
+    const int ch0 = (slice & 1) * 4, sw = row_l & 7;
+    float acc[CPW], comp[CPW];
+    // adds D of tile tt (its NCP / 4 columns of this warp) into acc
+    auto flush = [&](long long tt) -> bool {
+      const int bd = int(tt & 1);
+      if (!mbar_wait_bounded(&dfull[bd], uint32_t(tt >> 1) & 1)) return false;
+      tc::fence_after_sync();
+      float dv[CPW];
+      const uint32_t ta = tmem + lane_off + D_COL + uint32_t(bd * 32 + slice * CPW);
+      if constexpr (CPW == 4)
+        tc::tmem_ld4(ta, dv);
+      else
+        tc::tmem_ld8(ta, dv);
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&dempty[bd]);
+#pragma unroll
+      for (int k = 0; k < CPW; ++k) {
+        const float y = dv[k] - comp[k];
+        const float t2 = acc[k] + y;
+        comp[k] = (t2 - acc[k]) - y;
+        acc[k] = t2;
+      }
+      return true;
+    };
+    long long t = 0;
+    bool aborted = false;
+    for (int rbc = 0; rbc < nrb && !aborted; ++rbc) {
+      const int rb = int(blockIdx.x) + rbc * int(gridDim.x);
+      const int row = rb * MV_TILE + row_l;
+      const float u = a.vcol[row];  // -c |x_i|^2 (n_pad entries, -inf beyond n): E = K / s^2
+      const unsigned long long uu = tc::f2pk(u, u);
+#pragma unroll
+      for (int k = 0; k < CPW; ++k) acc[k] = comp[k] = 0.f;
+      for (int J = 0; J < n_tiles; ++J, ++t) {
+        const int b = int(t % TC_SBUF);
+        if (!mbar_wait_bounded(&tfull[b], uint32_t(t / TC_SBUF) & 1)) { aborted = true; break; }
+        tc::fence_after_sync();
+        float sv[32];
+        tc::tmem_ld32(tmem + lane_off + uint32_t(b * MV_TILE + slice * 32), sv);
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
+        // the entries of the row's 32 columns, split into float16 parts
+        uint32_t hi2[16], lo2[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const unsigned long long g = tc::f2fma(c2x2, tc::f2pk(sv[2 * k], sv[2 * k + 1]), uu);
+          const float e0 = tc::ex2_approx(tc::f2lo(g)), e1 = tc::ex2_approx(tc::f2hi(g));
+          const __half2 h = __floats2half2_rn(e0, e1);
+          const float2 hf = __half22float2(h);
+          const __half2 l = __floats2half2_rn(e0 - hf.x, e1 - hf.y);  // exact differences
+          hi2[k] = *reinterpret_cast<const uint32_t*>(&h);
+          lo2[k] = *reinterpret_cast<const uint32_t*>(&l);
+        }
+        // E of the previous tile has been read by its MMA 2
+        if (t > 0 && !mbar_wait_bounded(eempty, uint32_t(t - 1) & 1)) { aborted = true; break; }
+        tc::fence_after_sync();
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int ch = (ch0 + m) ^ sw;
+          *reinterpret_cast<uint4*>(e_row + ch * 16) =
+              make_uint4(hi2[4 * m], hi2[4 * m + 1], hi2[4 * m + 2], hi2[4 * m + 3]);
+          *reinterpret_cast<uint4*>(e_row + TC_E_PART + ch * 16) =
+              make_uint4(lo2[4 * m], lo2[4 * m + 1], lo2[4 * m + 2], lo2[4 * m + 3]);
+        }
+        fence_proxy_async_smem();  // the stores, visible to the tensor core's reads
+        __syncwarp();
+        if (lane == 0) mbar_arrive(efull);
+        // D of the previous tile of this row block (one tile behind, so that
+        // MMA 2 of it has long finished)
+        if (J > 0 && !flush(t - 1)) { aborted = true; break; }
+      }
+      if (aborted) break;
+      if (!flush(t - 1)) { aborted = true; break; }  // the row block's last tile
+      if (row < n) {
+#pragma unroll
+        for (int k = 0; k < CPW; ++k) {
+          const int c = slice * CPW + k;
+          if (c < a.ncols)
+            a.q[int64_t(c) * a.ldq + row] = acc[k] * (s2 / pscale[c]) + noise * a.p[int64_t(c) * a.ldp + row];
+        }
+      }
+    }
+    if (aborted) s_abort = 1;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, MV_TMEM_COLS);
+  }
+  if (s_abort && threadIdx.x == 0 && st) {
+    st->status = DCG_ERR_TIMEOUT;
+    st->timeout_site = 3;
+    st->done = 1;
+  }
+}
+
+cudaError_t rbf_mv_tc_configure() {
+  cudaError_t e = cudaFuncSetAttribute(k_rbf_mv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc_smem(16)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_rbf_mv_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc_smem(32)));
+}
+
+// The float16 parts of P for the contraction: 2 TC_MAXC rows of n_pad float16
+// (rows c: the high parts, rows TC_MAXC + c: the low parts), row-major; boxes of
+// 64 x ncp (128 bytes x ncp rows) with 128-byte swizzle, the B operand layout.
+bool make_rbf_p16_tmap(CUtensorMap* map, const void* PHL, int n_pad, int ncp, EncodeTiledFn encode) {
+  cuuint64_t gdim[2] = {cuuint64_t(n_pad), cuuint64_t(2 * TC_MAXC)};
+  cuuint64_t gstride[1] = {cuuint64_t(n_pad) * 2};
+  cuuint32_t box[2] = {64, cuuint32_t(ncp)};
+  cuuint32_t estride[2] = {1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(PHL), gdim, gstride, box, estride,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+size_t rbf_p16_halfs(int n_pad) { return size_t(2) * TC_MAXC * n_pad; }
+
+// Q[:, c] = A P[:, c] for c < a.ncols <= 32 (a.p, a.ldp: the columns, zero
+// beyond n; a.q, a.ldq): k_rbf_p16 then one k_rbf_mv_tc pass. pmaps[0], [1]:
+// the maps of PHL for 16 and 32 columns; pscale: TC_MAXC floats.
+cudaError_t launch_rbf_mv_tc(const CUtensorMap* tmap, const CUtensorMap* pmaps, const RbfMvArgs& a, void* PHL,
+                             float* pscale, int grid, cudaStream_t s) {
+  if (a.ncols < 1 || a.ncols > TC_MAXC) return cudaErrorInvalidValue;
+  const int ncp = a.ncols <= 16 ? 16 : 32;
+  const int n_pad = a.n_tiles * MV_TILE;
+  k_rbf_p16<<<ncp, 1024, 0, s>>>(a.p, a.ldp, a.ncols, n_pad, static_cast<__half*>(PHL), pscale);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (ncp == 16)
+    k_rbf_mv_tc<16><<<grid, MV_THREADS, tc_smem(16), s>>>(tmap[0], tmap[1], pmaps[0], a, pscale);
+  else
+    k_rbf_mv_tc<32><<<grid, MV_THREADS, tc_smem(32), s>>>(tmap[0], tmap[1], pmaps[1], a, pscale);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
