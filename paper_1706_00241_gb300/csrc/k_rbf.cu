@@ -540,13 +540,16 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
 //          stored as the A operand (K-major, 128-byte swizzle, two 64-column
 //          halves per part);
 //   MMA 2  D += E_hi P_hi + E_hi P_lo + E_lo P_hi over the 128 columns of the
-//          tile (K = 16 per MMA, 24 MMAs), D (128 x NCP float32) in one of two
-//          TMEM buffers; P = P_hi + P_lo is each column of P scaled by a power
-//          of two sigma_c (max |p| sigma_c in [1/2, 1)) and split like E
-//          (k_rbf_p16, once per pass);
-//   flush  each epilogue warp reads its NCP / 4 columns of D one tile behind
-//          and adds them into float32 registers (Kahan), so the tensor core
-//          accumulates one tile (8 K steps) at a time;
+//          tile (K = 16 per MMA; per K step one MMA of N = 2 NCP against
+//          [P_hi; P_lo] stacked as one operand and one of N = NCP against
+//          P_hi: 16 MMAs), D (128 x 2 NCP float32: [E_hi P_hi + E_lo P_hi |
+//          E_hi P_lo]) in one of two TMEM buffers; P = P_hi + P_lo is each
+//          column of P scaled by a power of two sigma_c (max |p| sigma_c in
+//          [1/2, 1)) and split like E (k_rbf_p16, once per pass);
+//   flush  each epilogue warp reads its NCP / 4 columns of both groups of D
+//          one tile behind, adds the groups and adds the sum into float32
+//          registers (Kahan), so the tensor core accumulates one tile (8 K
+//          steps) at a time;
 //   end    q_c = s^2 / sigma_c (D sum) + noise p_c per row.
 // The dropped E_lo P_lo term and the float16 roundings of the parts leave
 // ~2^-22 relative per product plus 2^-25 absolute (E_lo below the float16
@@ -640,7 +643,9 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
   constexpr int SB = tc_stage_bytes(NCP);
   constexpr int PB = NCP * 128;  // one box of P_J: NCP rows x 64 float16 (128 bytes)
   constexpr int CPW = NCP / 4;   // D columns per epilogue warp
-  constexpr uint32_t D_COL = TC_SBUF * MV_TILE;  // TMEM column of the first D buffer (buffers 32 apart)
+  // TMEM column of the first D buffer; buffers 64 apart, each 2 NCP columns:
+  // [E_hi P_hi + E_lo P_hi | E_hi P_lo]
+  constexpr uint32_t D_COL = TC_SBUF * MV_TILE;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* xi_tile = base;
@@ -672,7 +677,8 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
   const uint32_t row_bytes = uint32_t(rbf_row_bytes(a.xformat, dk));
   const uint32_t tile_bytes = MV_TILE * row_bytes;
   const uint32_t idesc1 = tc::instr_desc(kind_tf32 ? tc::kFmtTF32 : tc::kFmtBF16, MV_TILE, MV_TILE);
-  const uint32_t idesc2 = tc::instr_desc(tc::kFmtF16, MV_TILE, NCP);
+  const uint32_t idesc2 = tc::instr_desc(tc::kFmtF16, MV_TILE, NCP);       // E_lo P_hi
+  const uint32_t idesc2w = tc::instr_desc(tc::kFmtF16, MV_TILE, 2 * NCP);  // E_hi [P_hi | P_lo]
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -723,9 +729,10 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
           unsigned char* stg = stages + size_t(s) * SB;
           mbar_arrive_expect_tx(&full[s], tile_bytes + 4 * PB);
           tma_load_2d(stg, &tmap_j, &full[s], 0, J * MV_TILE);
+          // per half of the tile's columns, P_hi then P_lo: one B operand of 2 NCP rows
           tma_load_2d(stg + MV_TILE_BYTES, &tmap_p, &full[s], J * MV_TILE, 0);                    // P_hi j 0..63
-          tma_load_2d(stg + MV_TILE_BYTES + PB, &tmap_p, &full[s], J * MV_TILE + 64, 0);          // P_hi j 64..127
-          tma_load_2d(stg + MV_TILE_BYTES + 2 * PB, &tmap_p, &full[s], J * MV_TILE, TC_MAXC);     // P_lo j 0..63
+          tma_load_2d(stg + MV_TILE_BYTES + PB, &tmap_p, &full[s], J * MV_TILE, TC_MAXC);         // P_lo j 0..63
+          tma_load_2d(stg + MV_TILE_BYTES + 2 * PB, &tmap_p, &full[s], J * MV_TILE + 64, 0);      // P_hi j 64..127
           tma_load_2d(stg + MV_TILE_BYTES + 3 * PB, &tmap_p, &full[s], J * MV_TILE + 64, TC_MAXC);
         }
         if (stop) break;
@@ -774,17 +781,15 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
         }
         tc::fence_after_sync();
         const uint32_t pb = smem_u32(stages + size_t(s) * SB + MV_TILE_BYTES);
-        const uint32_t d2 = tmem + D_COL + uint32_t(bd * 32);
+        const uint32_t d2 = tmem + D_COL + uint32_t(bd * 64);
 #pragma unroll 1
         for (int kk = 0; kk < 8; ++kk) {
           const uint32_t h = uint32_t(kk >> 2), ko = uint32_t(kk & 3) * 32;
           const uint64_t eh = tc::smem_desc_kmajor(e_base + h * (MV_TILE * 128) + ko, 128);
           const uint64_t el = tc::smem_desc_kmajor(e_base + TC_E_PART + h * (MV_TILE * 128) + ko, 128);
-          const uint64_t ph = tc::smem_desc_kmajor(pb + h * PB + ko, 128);
-          const uint64_t pl = tc::smem_desc_kmajor(pb + 2 * PB + h * PB + ko, 128);
-          tc::mma_bf16(d2, eh, ph, idesc2, kk > 0);  // kind::f16; the formats come from idesc2
-          tc::mma_bf16(d2, eh, pl, idesc2, 1);
-          tc::mma_bf16(d2, el, ph, idesc2, 1);
+          const uint64_t phl = tc::smem_desc_kmajor(pb + h * (2 * PB) + ko, 128);  // [P_hi; P_lo], 2 NCP rows
+          tc::mma_bf16(d2, eh, phl, idesc2w, kk > 0);  // kind::f16; the formats come from the descriptor
+          tc::mma_bf16(d2, el, phl, idesc2, 1);        // the first NCP rows of the same operand: P_hi
         }
         tc::mma_commit(&empty[s]);
         tc::mma_commit(eempty);
@@ -811,12 +816,17 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
       const int bd = int(tt & 1);
       if (!mbar_wait_bounded(&dfull[bd], uint32_t(tt >> 1) & 1)) return false;
       tc::fence_after_sync();
-      float dv[CPW];
-      const uint32_t ta = tmem + lane_off + D_COL + uint32_t(bd * 32 + slice * CPW);
-      if constexpr (CPW == 4)
+      float dv[CPW], dw[CPW];
+      const uint32_t ta = tmem + lane_off + D_COL + uint32_t(bd * 64 + slice * CPW);
+      if constexpr (CPW == 4) {
         tc::tmem_ld4(ta, dv);
-      else
+        tc::tmem_ld4(ta + NCP, dw);
+      } else {
         tc::tmem_ld8(ta, dv);
+        tc::tmem_ld8(ta + NCP, dw);
+      }
+#pragma unroll
+      for (int k = 0; k < CPW; ++k) dv[k] += dw[k];  // + E_hi P_lo
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive(&dempty[bd]);
