@@ -61,6 +61,24 @@ def test_methods_reject_mis_sized_tensors(bare):
         s.apply_block(torch.zeros(3, 6), torch.zeros(2, 6))
 
 
+def test_solve_multi_rejects_bad_blocks(bare):
+    # lockstep solves: B is (nrhs, n) with 1 <= nrhs <= DCG_MAX_RHS, X float64
+    # on the device and shaped like B; all checked before the library is called
+    s = bare
+    with pytest.raises(ValueError, match=r"B must be \(nrhs, 6\)"):
+        s.solve_multi(torch.zeros(3, 5))
+    with pytest.raises(ValueError, match=r"B must be \(nrhs, 6\)"):
+        s.solve_multi(torch.zeros(18))
+    with pytest.raises(ValueError, match="nrhs must lie in"):
+        s.solve_multi(torch.zeros(0, 6))
+    with pytest.raises(ValueError, match="nrhs must lie in"):
+        s.solve_multi(torch.zeros(33, 6))
+    with pytest.raises(TypeError, match="X must be"):
+        s.solve_multi(torch.zeros(3, 6), torch.zeros(3, 6, dtype=torch.float64))   # not on the device
+    with pytest.raises(TypeError, match="X must be"):
+        s.solve_multi(torch.zeros(3, 6), torch.zeros(2, 6, dtype=torch.float64))
+
+
 def test_free_functions_reject_mis_sized_tensors(monkeypatch):
     monkeypatch.setattr(SV, "_dev_f32", lambda t, name: t)
     monkeypatch.setattr(SV._lib, "load", lambda: None)
