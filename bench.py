@@ -658,6 +658,8 @@ def kernel_arm(args):
         workload = f"stored dense fp32 n={n}"
     elif args.kernel in ("apply_block", "form", "iter"):
         return kernel_arm_dense(args, P, torch, stream)
+    elif args.kernel == "multi":
+        return kernel_arm_multi(args, P, torch)
     elif args.kernel == "resid":
         # the exact-form true residual of the matrix-free operator (k_rbf_resid
         # + k_rbf_resid_fin), on the bf16 n = 131072 workload's generator
@@ -719,6 +721,50 @@ def kernel_arm(args):
                       "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                                    "frac": achieved / peak, "peak_kind": kind,
                                    "algorithmic_per_launch": algo}}))
+
+
+def kernel_arm_multi(args, P, torch):
+    """One lockstep solve (dcg_solve_multi) of the gradient workload's probes:
+    n = 32768, d = 8, BF16 points, k = 32, refinement every 50, W from one
+    solve of the targets and its update; --cols probes (default 16). Times
+    the lockstep solve (median of --steps after --warmup, wall clock: the
+    loop is driven from the host) and the same probes solved one after
+    another, for profiling captures of its kernels (k_rbf_mv_tc,
+    k_rbf_resid_multi)."""
+    cfg = S.GRAD_32768
+    n = args.n or cfg.n
+    X, _ = S.draw_sequence(cfg.scaled(n, T=1) if n != cfg.n else cfg, T=1)
+    nprobe = args.cols or cfg.extra["probes"]
+    Xd = torch.tensor(X.astype(np.float32), device="cuda")
+    y = torch.tensor(S.gp_targets(X).astype(np.float32), device="cuda")
+    Z = torch.tensor(np.ascontiguousarray(S.rademacher(n, nprobe, seed=1000).T.astype(np.float32)), device="cuda")
+    with P.DefCG(n, cfg.k, cfg.ell, cfg.tol, refine_every=50, max_iter=20000) as s:
+        s.set_operator_rbf(Xd, cfg.l0, cfg.signal_var, cfg.noise, xformat="bf16")
+        s.solve(y)
+        s.update_subspace()
+        for _ in range(args.warmup):          # also allocates the per-system buffers
+            s.solve_multi(Z)
+        times = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            _, infos = s.solve_multi(Z)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - w0)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        single = [s.solve(Z[c].contiguous())[1] for c in range(nprobe)]
+        torch.cuda.synchronize()
+        t_single = time.perf_counter() - w0
+    t_multi = statistics.median(times)
+    its = [i["iters"] for i in infos]
+    print(json.dumps({"kernel": "dcg_solve_multi (lockstep: k_rbf_mv_tc block product, k_iter_fused per system, "
+                                "k_rbf_resid_multi checks)",
+                      "workload": f"{cfg.name}: {nprobe} Rademacher probes, n={n}, d={cfg.d}, bf16, k={cfg.k}",
+                      "s_lockstep": t_multi, "s_one_by_one": t_single, "speedup": t_single / t_multi,
+                      "iters_max": max(its), "ms_per_lockstep_iteration": 1e3 * t_multi / max(its),
+                      "iters": its, "iters_one_by_one": [i["iters"] for i in single],
+                      "all_converged": all(i["status"] == 0 for i in infos)}))
 
 
 def kernel_arm_dense(args, P, torch, stream):
@@ -931,9 +977,11 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the solve's kernels from the host instead of one CUDA graph "
                          "(profiling mode: ncu cannot list kernels inside conditional graphs)")
-    ap.add_argument("--kernel", choices=["gemv", "symv", "rbf_mv", "resid", "apply_block", "form", "iter"], default=None,
+    ap.add_argument("--kernel", choices=["gemv", "symv", "rbf_mv", "resid", "apply_block", "form", "iter", "multi"],
+                    default=None,
                     help="time one hot kernel alone (q = A p) instead of the sequence")
-    ap.add_argument("--cols", type=int, default=None, help="columns of W for --kernel apply_block (default k)")
+    ap.add_argument("--cols", type=int, default=None,
+                    help="columns of W for --kernel apply_block (default k); probes for --kernel multi (default 16)")
     ap.add_argument("--n", type=int, default=0, help="system size for --kernel (default: the workload's)")
     ap.add_argument("--systems", type=int, default=0,
                     help="solve only the first T systems of the sequence (small profiling captures; "
