@@ -286,8 +286,9 @@ dcg_status dcg_solve(dcg_ctx* ctx, const float* b, double* x, dcg_solve_info* in
  * Deflated-CG(k)(A, b_c, x_{-1,c}, W, AW, tol) of dcg_solve (Algorithm 1,
  * Sec. 2.2) with the context's W, run in lockstep: every iteration forms one
  * block product A [p_c1 p_c2 ...] over the systems still running (matrix-free
- * operator: one pass over the kernel entries per 8 systems, each exponential
- * shared by them; stored operator: one read of A), then each system takes
+ * operator: one pass over the kernel entries for all of them, each entry
+ * formed once and contracted with every system's direction on the tensor
+ * cores; stored operator: one read of A), then each system takes
  * its own step, its convergence checks, refinements and final true residual
  * exactly as dcg_solve does. Systems leave the block as they converge. The
  * iterates are those of dcg_solve up to the rounding of the block product.

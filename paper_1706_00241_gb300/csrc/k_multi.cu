@@ -5,7 +5,8 @@
 //   k_multi_gather  copies the directions p of the systems still running into
 //                   the columns of one block (the matrix-free product reads
 //                   whole 128-row tiles: the padded length, zero beyond n);
-//   (block product  Q = A P: k_rbf_mv<8> passes or the stored block product)
+//   (block product  Q = A P: k_rbf_p16 + k_rbf_mv_tc for the matrix-free
+//                   operator, the stored block product otherwise)
 //   k_multi_pq      p^T q of every column into its system's state, the d of
 //                   Algorithm 1 that the fused iteration kernel divides by.
 #include <algorithm>

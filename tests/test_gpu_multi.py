@@ -115,8 +115,9 @@ def test_multi_dense_ill_conditioned_with_refinement(dcg):
 def test_multi_rbf_with_refinement(dcg, fmt):
     # The matrix-free operator: W from one solve and its update, then 10
     # Rademacher right-hand sides (the gradient workload's probes) in one
-    # lockstep solve, iterating with the tensor-core entries of k_rbf_mv<8>
-    # (passes of 8 systems) and refined by the exact-form residual every 25
+    # lockstep solve, iterating with the block product k_rbf_mv_tc (the
+    # tensor-core entries, contracted with all 10 directions on the tensor
+    # cores in float16 parts) and refined by the exact-form residual every 25
     # iterations. Bars as for the single matrix-free solve: certified true
     # residual <= tol, float64 residual of x <= tol, iterations within
     # 0.9 oracle - 2 .. 1.25 oracle + 10 and within 10 % + 3 of the GPU's
